@@ -1,0 +1,233 @@
+/*
+ * fpdqt.h -- C ABI of the packed small-prime-field library (GB300, sm_103a).
+ *
+ * The library computes exact products over F_p (p prime, 2 <= p <= 251) and over small
+ * extension fields GF(p^k) by packing several residues into one machine word with the
+ * Discrete Q-adic Transform (DQT, the map sum a_i X^i -> sum a_i q^i of Eq. dqt, Sec. 1),
+ * multiplying and accumulating those words with delayed reduction (Sec. 2.2-2.3), and
+ * recovering the residues with REDQ simultaneous reduction (Algorithm 2, Sec. 3) in which the
+ * one division is an FP multiply by a rounded inverse (Algorithm FDIV, Table "fdiv", Sec. 4).
+ * Here q = Q = 2^b always (the restriction at the end of Sec. 3).
+ *
+ * Conventions shared by every call
+ *  - All array pointers are DEVICE pointers owned by the caller unless stated otherwise; the
+ *    library never frees them.  Arrays are dense, row-major, uint8 per F_p residue.
+ *  - Every compute call is asynchronous on the given CUDA stream (NULL = legacy default).
+ *    Host-side argument checks happen before anything is enqueued; a failing check returns
+ *    its status and enqueues nothing.
+ *  - Residue inputs must lie in [0, p-1].  Kernels check this on the device; a violation
+ *    sets the context's sticky error flag (results are then unspecified but every memory
+ *    access stays in bounds).  fp_ctx_status() synchronises the stream and reports it.
+ *  - No C++ exception crosses the ABI.  fp_last_error() gives a thread-local message for
+ *    the last non-FP_OK status of the calling thread.
+ *  - Status codes: FP_EINVAL (bad argument), FP_EBOUND (forced parameters violate the
+ *    exactness bounds of Eq. bounds / Eq. lower / Eq. upper), FP_ENOMEM, FP_ECUDA (a CUDA
+ *    runtime call failed), FP_ETIMEOUT (a bounded device wait gave up), FP_EUNSUPPORTED.
+ */
+#ifndef FPDQT_H
+#define FPDQT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FP_OK = 0,
+  FP_EINVAL = 1,
+  FP_EBOUND = 2,
+  FP_ENOMEM = 3,
+  FP_ECUDA = 4,
+  FP_ETIMEOUT = 5,
+  FP_EUNSUPPORTED = 6
+} fp_status;
+
+/* Machine word holding a packed value.  beta = exact integer range used for the bounds:
+ * F64 52 bits (FDIV case 3 of Table "fdiv" is exact below 2^(53-1)), F32 23 bits (same rule
+ * with a 24-bit mantissa), U64 64 bits, U32 32 bits. */
+typedef enum { FP_WORD_F64 = 0, FP_WORD_U64 = 1, FP_WORD_F32 = 2, FP_WORD_U32 = 3 } fp_word;
+
+/* Algorithm selectors for fp_polymul_batched / fp_dot. */
+enum {
+  FP_ALGO_AUTO = 0,    /* planner's choice (fastest exact packed word) */
+  FP_ALGO_PLAIN = 1,   /* unpacked schoolbook with delayed reduction (Eq. delayed) */
+  FP_ALGO_DQT_F64 = 2, /* packed words of the given type */
+  FP_ALGO_DQT_U64 = 3,
+  FP_ALGO_DQT_F32 = 4,
+  FP_ALGO_DQT_U32 = 5
+};
+
+/* Algorithm selectors for fp_matmul. */
+enum {
+  FP_MM_AUTO = 0,       /* planner: fastest packed (DQT + REDQ) variant valid for (p, k) */
+  FP_MM_RIGHT_F64 = 1,  /* right compression (Sec. 7.4), FP64 words, FP64 tensor cores (DMMA) */
+  FP_MM_RIGHT_F32 = 2,  /* right compression, FP32 words, FFMA, inner dimension split so the
+                           digit bound holds per chunk; chunks folded into an integer word */
+  FP_MM_PLAIN_F64 = 3,  /* unpacked, FP64 DMMA, delayed reduction, mod p epilogue */
+  FP_MM_PLAIN_F32 = 4,  /* unpacked, FFMA, delayed reduction, mod p epilogue */
+  FP_MM_PLAIN_I8 = 5,   /* unpacked, u8 x u8 -> s32 tensor cores (mma.sync), mod p epilogue */
+  FP_MM_PLAIN_TC = 6,   /* unpacked, tcgen05 kind::f16 (bf16 operands, fp32 accumulate) */
+  FP_MM_RIGHT_TC = 7,   /* right compression on tcgen05 kind::f16: fp16 operands holding two
+                           centred residues at Q = 2^10, inner dimension chunked (p <= 3) */
+  FP_MM_LEFT_F32 = 8    /* left compression (Sec. 7.4, by transposition), FP32 words */
+};
+
+/* Parameters of one packed representation (Sec. 2.3): q = 2^b, k residues packed per
+ * operand word, ndig residues recovered per result word, n_accum products accumulated. */
+typedef struct {
+  uint32_t p;
+  uint32_t k;
+  uint32_t b;
+  uint32_t ndig;
+  uint32_t word;     /* fp_word */
+  uint32_t reserved;
+  uint64_t n_accum;
+} fp_dqt_params;
+
+typedef struct fp_ctx_s* fp_ctx;
+typedef struct fp_gf_s* fp_gf;
+
+/* ---------------------------------------------------------------- context and errors */
+
+/* Create a context on CUDA device `device` (made current on the calling thread).  The
+ * context owns: the sticky device error flag, scratch for packed operands (grown on demand
+ * with cudaMalloc), REDQ correction tables and the plan cache.  *out receives the handle.
+ * Errors: FP_EINVAL (null out / bad device), FP_ECUDA, FP_ENOMEM. */
+fp_status fp_ctx_create(fp_ctx* out, int device);
+
+/* Destroy a context and free everything it owns (synchronises its device first).  NULL ok. */
+void fp_ctx_destroy(fp_ctx ctx);
+
+/* Synchronise `stream`, then read and clear the context's sticky device error flag.
+ * Returns FP_EINVAL if any kernel saw a residue outside [0, p-1] (or a GF index outside
+ * [0, p^k)), FP_ETIMEOUT if a bounded device wait gave up, FP_ECUDA on a CUDA error. */
+fp_status fp_ctx_status(fp_ctx ctx, void* stream);
+
+/* Thread-local message describing the last error of the calling thread ("" if none). */
+const char* fp_last_error(void);
+
+/* ---------------------------------------------------------------- planner (host only) */
+
+/* Choose packing parameters for products of two polynomials with k coefficients each,
+ * n_accum of them summed per result word, in words of type `word`.
+ * Rule (Theorem of Sec. 2.3, Eq. bounds, strict reading): q = 2^b is the smallest power of
+ * two with q > n_accum * k * (p-1)^2; ndig = 2k-1; the largest possible packed result,
+ * sum_j n_accum * min(j+1, 2k-1-j, k) (p-1)^2 q^j, must fit the word's exact range.
+ * Errors: FP_EINVAL (p not prime / out of range, k == 0, n_accum == 0, null out),
+ * FP_EBOUND (no q fits the word).  Pure host computation: no device needed. */
+fp_status fp_dqt_choose(uint32_t p, uint32_t k, uint64_t n_accum, uint32_t word,
+                        fp_dqt_params* out);
+
+/* Compression parameters of the right-compressed product (Sec. 7.2-7.4 and 7.6.1) for an
+ * inner dimension kdim: Q = 2^b the smallest power of two with kdim (p-1)^2 < Q (Eq. lower,
+ * strict), e = the largest number of residues per word whose largest packed value fits the
+ * word (Eq. upper; e = floor(beta / log2 Q) up to the exact-range refinement).  For FP32
+ * words the inner dimension is chunked: *chunk receives the chunk length (kdim when no
+ * chunking is needed) and b, e refer to one chunk.  Host only. */
+fp_status fp_mm_choose(uint32_t p, uint64_t kdim, uint32_t algo, uint32_t* b, uint32_t* e,
+                       uint32_t* chunk);
+
+/* ---------------------------------------------------------------- DQT pack / unpack */
+
+/* DQT (Eq. dqt): words[i] = sum_{j<k} coeffs[i*k + j] * q^j, for i < count.
+ * coeffs: device uint8 [count][k] with entries in [0, p-1]; words: device array of count
+ * words of type prm->word (double, uint64_t, float or uint32_t).  prm->k <= 64 and
+ * (p-1) * sum_j q^j must fit the word (else FP_EBOUND). */
+fp_status fp_dqt_pack(fp_ctx ctx, const fp_dqt_params* prm, const uint8_t* coeffs, void* words,
+                      size_t count, void* stream);
+
+/* Inverse DQT by REDQ (Algorithm 2 with the FDIV division of Sec. 4 and tabulated
+ * correction, Sec. 3.5): coeffs[i*ndig + j] = (j-th base-q digit of words[i]) mod p, where
+ * the top digit (j = ndig-1) takes all remaining high bits.  Each word must be a
+ * non-negative integer < the word's exact range (2^52 for F64, 2^23 for F32) whose lower
+ * ndig-1 base-q digits are < q -- which holds whenever it was produced under the planner's
+ * bounds.  words: device [count] of prm->word; coeffs: device uint8 [count][ndig]. */
+fp_status fp_dqt_unpack_redq(fp_ctx ctx, const fp_dqt_params* prm, const void* words,
+                             uint8_t* coeffs, size_t count, void* stream);
+
+/* ---------------------------------------------------------------- polynomial product */
+
+/* Batched product over F_p[X] (Sec. 5): for each of `batch` pairs, C = A * B mod p.
+ * A: device uint8 [batch][dega+1], B: [batch][degb+1], C: [batch][dega+degb+1], coefficients
+ * lowest degree first.  DQT algos pack each operand in one word when the product fits one
+ * word, else split into blocks of d+1 coefficients (FQT, Sec. 5.2) and accumulate the block
+ * products in words before one REDQ per result block.  dega, degb <= 1023.
+ * Errors: FP_EINVAL, FP_EBOUND (a forced word type cannot hold even d = 0). */
+fp_status fp_polymul_batched(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t dega,
+                             const uint8_t* B, uint32_t degb, uint8_t* C, size_t batch, int algo,
+                             void* stream);
+
+/* ---------------------------------------------------------------- dot product */
+
+/* Modular dot product (Algorithm 1 with degree-0 entries): *out = (sum u_i v_i) mod p.
+ * u, v: device uint8 [n]; out: device uint32 scalar.  DQT algos use the middle-product
+ * packing of Sec. 7.1 (d+1 entries per word, reversed on the left), PLAIN uses delayed
+ * reduction.  n <= 2^40.  Uses context scratch for per-block partial results. */
+fp_status fp_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v, size_t n,
+                 uint32_t* out, int algo, void* stream);
+
+/* ---------------------------------------------------------------- matrix product */
+
+/* C = A * B mod p (Sec. 7).  A: device uint8 m x k (leading dimension lda >= k), B: k x n
+ * (ldb >= n), C: m x n (ldc >= n).  m, n, k in [1, 2^20]; k also bounded by the algorithm's
+ * exactness rule (FP_EBOUND beyond it: e.g. PLAIN_TC needs k (p-1)^2 < 2^24).  Packed
+ * algorithms keep the compressed B (k x ceil(n/e) words) in context scratch. */
+fp_status fp_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
+                    const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, void* stream);
+
+/* Right compression of B alone (Sec. 7.4): CB[l][j] = sum_{t<e} B[l][j e + t] Q^t with
+ * Q = 2^b, missing columns of the last block taken as zero (partial compression, Sec. 7.1).
+ * CB: device array k x ceil(n/e) of `word` (F64 or F32 or U64).  Exposed for tests and reuse. */
+fp_status fp_pack_cb(fp_ctx ctx, uint32_t p, int k, int n, const uint8_t* B, int ldb,
+                     uint32_t b, uint32_t e, uint32_t word, void* CB, void* stream);
+
+/* ---------------------------------------------------------------- GF(p^k) */
+
+/* Build GF(p^k) (Sec. 6): p prime <= 251, k >= 1, p^k <= 65536.  The modulus is the monic
+ * irreducible of degree k with the smallest key sum_{i<k} c_i p^i (brute-force
+ * irreducibility test); q = 2^b is the smallest power of two above k (p-1)^2; the tables of
+ * Algorithm FGDP (element -> packed word, L and H folding the REDQ correction and the
+ * reduction by the modulus) are built on the host and copied to the device.  Elements are
+ * indices sum_i c_i p^i: uint8 when p^k <= 256, else uint16. */
+fp_status fp_gf_create(fp_ctx ctx, uint32_t p, uint32_t k, fp_gf* out);
+void fp_gf_destroy(fp_gf gf);
+
+/* Query a field: modulus coefficients (k+1 values, constant term first) into `modulus`
+ * (may be NULL), q exponent b, packed word type, and element width in bytes. */
+fp_status fp_gf_info(fp_gf gf, uint32_t* modulus, uint32_t* b, uint32_t* word,
+                     uint32_t* elem_bytes);
+
+/* Batched multiply c[i] = a[i] * b[i] in GF(p^k) by Algorithm FGDP with n = 1: table DQT,
+ * one word product, REDQ compression, two lookups (L, H) and one field addition.
+ * a, b, c: device arrays of `count` element indices (width per fp_gf_info). */
+fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf gf, const void* a, const void* b, void* c,
+                            size_t count, void* stream);
+
+/* ---------------------------------------------------------------- uneven batches */
+
+/* One instance of an uneven batch: kind 0 = matmul (C = A B mod p, dense row-major,
+ * A m x k, B k x n, C m x n), kind 1 = dot (n = 1, m = 1, A = u[k], B = v[k], C = uint32
+ * result stored as 4 bytes).  All pointers are device pointers owned by the caller. */
+typedef struct {
+  uint32_t kind;
+  uint32_t p;
+  uint32_t m, n, k;
+  uint32_t reserved;
+  const uint8_t* A;
+  const uint8_t* B;
+  uint8_t* C;
+} fp_instance;
+
+/* Run all `count` instances in ONE persistent kernel launch: CTAs take tiles from a device
+ * work queue (an atomic counter over a tile list the host planner sorts by cost); packing
+ * degree e and word are chosen per (p, k) by the planner; per-instance tile shapes by the
+ * autotuner cache in the context.  `instances` is a HOST array; it is copied to context
+ * scratch.  Errors: FP_EINVAL, FP_EBOUND, FP_ECUDA. */
+fp_status fp_batch_run(fp_ctx ctx, const fp_instance* instances, size_t count, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPDQT_H */

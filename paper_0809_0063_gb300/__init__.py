@@ -1,0 +1,193 @@
+"""Python binding of libfpdqt (packed small-prime-field arithmetic on GB300, sm_103a).
+
+Argument marshalling only: every function here forwards to the C ABI entry point of the same
+name declared in include/fpdqt.h.  Arrays are torch tensors on the CUDA device (their
+data_ptr() is passed); streams default to torch's current stream.  A non-FP_OK status raises
+FpError with the library's message.  There is no CPU fallback: if libfpdqt.so is missing or
+cannot be loaded, importing the compute functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfpdqt.so")
+
+# status codes (fp_status)
+FP_OK, FP_EINVAL, FP_EBOUND, FP_ENOMEM, FP_ECUDA, FP_ETIMEOUT, FP_EUNSUPPORTED = range(7)
+STATUS_NAMES = ["FP_OK", "FP_EINVAL", "FP_EBOUND", "FP_ENOMEM", "FP_ECUDA", "FP_ETIMEOUT", "FP_EUNSUPPORTED"]
+# word types (fp_word)
+FP_WORD_F64, FP_WORD_U64, FP_WORD_F32, FP_WORD_U32 = range(4)
+# polymul / dot algorithms
+FP_ALGO_AUTO, FP_ALGO_PLAIN, FP_ALGO_DQT_F64, FP_ALGO_DQT_U64, FP_ALGO_DQT_F32, FP_ALGO_DQT_U32 = range(6)
+# matmul algorithms
+(FP_MM_AUTO, FP_MM_RIGHT_F64, FP_MM_RIGHT_F32, FP_MM_PLAIN_F64, FP_MM_PLAIN_F32, FP_MM_PLAIN_I8,
+ FP_MM_PLAIN_TC, FP_MM_RIGHT_TC, FP_MM_LEFT_F32) = range(9)
+
+
+class FpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+        self.status = status
+
+
+class fp_dqt_params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_uint32), ("k", ctypes.c_uint32), ("b", ctypes.c_uint32),
+                ("ndig", ctypes.c_uint32), ("word", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("n_accum", ctypes.c_uint64)]
+
+
+class fp_instance(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("p", ctypes.c_uint32), ("m", ctypes.c_uint32),
+                ("n", ctypes.c_uint32), ("k", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p)]
+
+
+_lib = None
+_V, _U32, _U64, _SZ, _I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_int
+_SIGS = {
+    "fp_ctx_create": (_I, [ctypes.POINTER(_V), _I]),
+    "fp_ctx_destroy": (None, [_V]),
+    "fp_ctx_status": (_I, [_V, _V]),
+    "fp_last_error": (ctypes.c_char_p, []),
+    "fp_dqt_choose": (_I, [_U32, _U32, _U64, _U32, ctypes.POINTER(fp_dqt_params)]),
+    "fp_mm_choose": (_I, [_U32, _U64, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
+    "fp_dqt_pack": (_I, [_V, ctypes.POINTER(fp_dqt_params), _V, _V, _SZ, _V]),
+    "fp_dqt_unpack_redq": (_I, [_V, ctypes.POINTER(fp_dqt_params), _V, _V, _SZ, _V]),
+    "fp_polymul_batched": (_I, [_V, _U32, _V, _U32, _V, _U32, _V, _SZ, _I, _V]),
+    "fp_dot": (_I, [_V, _U32, _V, _V, _SZ, _V, _I, _V]),
+    "fp_matmul": (_I, [_V, _U32, _I, _I, _I, _V, _I, _V, _I, _V, _I, _I, _V]),
+    "fp_pack_cb": (_I, [_V, _U32, _I, _I, _V, _I, _U32, _U32, _U32, _V, _V]),
+    "fp_gf_create": (_I, [_V, _U32, _U32, ctypes.POINTER(_V)]),
+    "fp_gf_destroy": (None, [_V]),
+    "fp_gf_info": (_I, [_V, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
+    "fp_gf_mul_batched": (_I, [_V, _V, _V, _V, _V, _SZ, _V]),
+    "fp_batch_run": (_I, [_V, ctypes.POINTER(fp_instance), _SZ, _V]),
+}
+
+
+def lib():
+    """Load libfpdqt.so (built in-tree by build.build()).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libfpdqt.so not built at {LIB_PATH}; run paper_0809_0063_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != FP_OK:
+        raise FpError(status, lib().fp_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ context
+
+def fp_ctx_create(device: int = 0):
+    h = _V()
+    _check(lib().fp_ctx_create(ctypes.byref(h), device))
+    return h
+
+
+def fp_ctx_destroy(ctx):
+    lib().fp_ctx_destroy(ctx)
+
+
+def fp_ctx_status(ctx, stream=None):
+    _check(lib().fp_ctx_status(ctx, _stream(stream)))
+
+
+def fp_last_error() -> str:
+    return lib().fp_last_error().decode()
+
+
+# ------------------------------------------------------------------ planner
+
+def fp_dqt_choose(p: int, k: int, n_accum: int, word: int) -> fp_dqt_params:
+    out = fp_dqt_params()
+    _check(lib().fp_dqt_choose(p, k, n_accum, word, ctypes.byref(out)))
+    return out
+
+
+def fp_mm_choose(p: int, kdim: int, algo: int):
+    b, e, c = _U32(), _U32(), _U32()
+    _check(lib().fp_mm_choose(p, kdim, algo, ctypes.byref(b), ctypes.byref(e), ctypes.byref(c)))
+    return b.value, e.value, c.value
+
+
+# ------------------------------------------------------------------ compute
+
+def fp_dqt_pack(ctx, prm: fp_dqt_params, coeffs, words, count: int, stream=None):
+    _check(lib().fp_dqt_pack(ctx, ctypes.byref(prm), _ptr(coeffs), _ptr(words), count, _stream(stream)))
+
+
+def fp_dqt_unpack_redq(ctx, prm: fp_dqt_params, words, coeffs, count: int, stream=None):
+    _check(lib().fp_dqt_unpack_redq(ctx, ctypes.byref(prm), _ptr(words), _ptr(coeffs), count, _stream(stream)))
+
+
+def fp_polymul_batched(ctx, p: int, A, dega: int, B, degb: int, C, batch: int, algo: int = FP_ALGO_AUTO,
+                       stream=None):
+    _check(lib().fp_polymul_batched(ctx, p, _ptr(A), dega, _ptr(B), degb, _ptr(C), batch, algo, _stream(stream)))
+
+
+def fp_dot(ctx, p: int, u, v, n: int, out, algo: int = FP_ALGO_AUTO, stream=None):
+    _check(lib().fp_dot(ctx, p, _ptr(u), _ptr(v), n, _ptr(out), algo, _stream(stream)))
+
+
+def fp_matmul(ctx, p: int, m: int, n: int, k: int, A, lda: int, B, ldb: int, C, ldc: int,
+              algo: int = FP_MM_AUTO, stream=None):
+    _check(lib().fp_matmul(ctx, p, m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, algo, _stream(stream)))
+
+
+def fp_pack_cb(ctx, p: int, k: int, n: int, B, ldb: int, b: int, e: int, word: int, CB, stream=None):
+    _check(lib().fp_pack_cb(ctx, p, k, n, _ptr(B), ldb, b, e, word, _ptr(CB), _stream(stream)))
+
+
+def fp_gf_create(ctx, p: int, k: int):
+    h = _V()
+    _check(lib().fp_gf_create(ctx, p, k, ctypes.byref(h)))
+    return h
+
+
+def fp_gf_destroy(gf):
+    lib().fp_gf_destroy(gf)
+
+
+def fp_gf_info(gf, k: int):
+    mod = (_U32 * (k + 1))()
+    b, w, eb = _U32(), _U32(), _U32()
+    _check(lib().fp_gf_info(gf, mod, ctypes.byref(b), ctypes.byref(w), ctypes.byref(eb)))
+    return {"modulus": list(mod), "b": b.value, "word": w.value, "elem_bytes": eb.value}
+
+
+def fp_gf_mul_batched(ctx, gf, a, b, c, count: int, stream=None):
+    _check(lib().fp_gf_mul_batched(ctx, gf, _ptr(a), _ptr(b), _ptr(c), count, _stream(stream)))
+
+
+def fp_batch_run(ctx, instances, stream=None):
+    arr = (fp_instance * len(instances))(*instances)
+    _check(lib().fp_batch_run(ctx, arr, len(instances), _stream(stream)))

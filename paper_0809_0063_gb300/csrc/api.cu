@@ -1,0 +1,389 @@
+// C ABI entry points of libfpdqt: context, errors, planner (Sec. 2.3, 7.2, 7.6.1) and the
+// argument checks in front of every kernel launcher.
+#include <math.h>
+#include <stdarg.h>
+#include <string.h>
+
+#include "fpdqt_internal.cuh"
+
+namespace fpd {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+fp_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("CUDA error %s (%d) in %s", cudaGetErrorString(e), (int)e, what);
+  return FP_ECUDA;
+}
+
+bool is_prime(uint32_t p) {
+  if (p < 2) return false;
+  for (uint32_t d = 2; d * d <= p; ++d)
+    if (p % d == 0) return false;
+  return true;
+}
+
+DivP make_divp(uint32_t p) {
+  DivP d{};
+  uint32_t l = 0;
+  while ((1ull << l) < p) ++l;
+  d.l = l;
+  d.pow2 = (p & (p - 1)) == 0;
+  d.sh = 0;
+  if (d.pow2) {
+    while ((1u << d.sh) < p) ++d.sh;
+    return d;
+  }
+  unsigned __int128 two_l = (unsigned __int128)1 << l;
+  unsigned __int128 m64 = (((unsigned __int128)1 << 64) * (two_l - p)) / p + 1;
+  d.m64 = (uint64_t)m64;
+  uint64_t m32 = ((((uint64_t)1) << 32) * ((1ull << l) - p)) / p + 1;
+  d.m32 = (uint32_t)m32;
+  return d;
+}
+
+int word_beta(uint32_t word) {
+  switch (word) {
+    case FP_WORD_F64: return 52;
+    case FP_WORD_U64: return 64;
+    case FP_WORD_F32: return 23;
+    case FP_WORD_U32: return 32;
+    default: return 0;
+  }
+}
+
+size_t word_bytes(uint32_t word) {
+  return (word == FP_WORD_F64 || word == FP_WORD_U64) ? 8 : 4;
+}
+
+// Round-up reciprocals by the exact-residual test: fma(x, p, -1) is the exact sign of
+// x p - 1, so x < 1/p exactly when it is negative, and then the next float up is RU(1/p).
+static double ru_recip_d(uint32_t p) {
+  double x = 1.0 / (double)p;
+  if (fma(x, (double)p, -1.0) < 0.0) x = nextafter(x, INFINITY);
+  return x;
+}
+static float ru_recip_f(uint32_t p) {
+  float x = 1.0f / (float)p;
+  if (fmaf(x, (float)p, -1.0f) < 0.0f) x = nextafterf(x, INFINITY);
+  return x;
+}
+
+RedqParams make_redq(uint32_t p, uint32_t b, uint32_t ndig) {
+  RedqParams P{};
+  P.p = p;
+  P.b = b;
+  P.ndig = ndig;
+  uint64_t qmodp = (b >= 64) ? 0 : ((1ull << b) % p);
+  P.c = (uint32_t)((p - qmodp) % p);
+  if (qmodp == 0) P.mode = CORR_NONE;
+  else if (p * p * p <= 32) P.mode = CORR_SHFL3;
+  else if (p * p <= 32) P.mode = CORR_SHFL2;
+  else if (p <= 31) P.mode = CORR_SMEM2;
+  else P.mode = CORR_ARITH;
+  P.invp_d = ru_recip_d(p);
+  P.invp_f = ru_recip_f(p);
+  P.dv = make_divp(p);
+  return P;
+}
+
+fp_status ensure_scratch(fp_ctx ctx, size_t bytes, int which) {
+  void** ptr = which ? &ctx->scratch2 : &ctx->scratch;
+  size_t* cap = which ? &ctx->scratch2_bytes : &ctx->scratch_bytes;
+  if (*cap >= bytes) return FP_OK;
+  if (*ptr) {
+    FP_CUDA(cudaDeviceSynchronize());
+    FP_CUDA(cudaFree(*ptr));
+    *ptr = nullptr;
+    *cap = 0;
+  }
+  size_t want = bytes < (1u << 20) ? (1u << 20) : bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(ptr, want);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    set_error("cudaMalloc of %zu bytes of scratch failed: %s", want, cudaGetErrorString(e));
+    return FP_ENOMEM;
+  }
+  *cap = want;
+  return FP_OK;
+}
+
+// Largest packed value when n_accum products of two k-coefficient polynomials with entries
+// in [0, p-1] are summed: digit j collects n_accum * min(j+1, 2k-1-j, k) products.
+static bool poly_word_fits(uint32_t p, uint32_t k, uint64_t n_accum, uint32_t b, int beta) {
+  unsigned __int128 total = 0;
+  unsigned __int128 lim = ((unsigned __int128)1 << beta);  // values must be < 2^beta
+  uint32_t nd = 2 * k - 1;
+  for (uint32_t j = 0; j < nd; ++j) {
+    uint64_t terms = j + 1;
+    if (nd - j < terms) terms = nd - j;
+    if (k < terms) terms = k;
+    unsigned __int128 dig = (unsigned __int128)n_accum * terms * (uint64_t)(p - 1) * (p - 1);
+    if ((uint64_t)j * b >= 128) return dig == 0;
+    unsigned __int128 sh = dig << (j * b);
+    if ((sh >> (j * b)) != dig) return false;
+    total += sh;
+    if (total >= lim) return false;
+  }
+  return total < lim;
+}
+
+}  // namespace fpd
+
+using namespace fpd;
+
+// ------------------------------------------------------------------ context
+
+extern "C" fp_status fp_ctx_create(fp_ctx* out, int device) {
+  FP_CHECK(out != nullptr, FP_EINVAL, "fp_ctx_create: out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  FP_CUDA(cudaGetDeviceCount(&ndev));
+  FP_CHECK(device >= 0 && device < ndev, FP_EINVAL, "fp_ctx_create: device %d of %d", device, ndev);
+  FP_CUDA(cudaSetDevice(device));
+  fp_ctx c = new (std::nothrow) fp_ctx_s();
+  FP_CHECK(c != nullptr, FP_ENOMEM, "fp_ctx_create: out of host memory");
+  c->device = device;
+  cudaDeviceProp pr;
+  cudaError_t e = cudaGetDeviceProperties(&pr, device);
+  if (e == cudaSuccess) c->num_sms = pr.multiProcessorCount;
+  e = cudaMalloc(&c->d_err, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "fp_ctx_create");
+  }
+  *out = c;
+  return FP_OK;
+}
+
+extern "C" void fp_ctx_destroy(fp_ctx ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->scratch2) cudaFree(ctx->scratch2);
+  delete ctx;
+}
+
+extern "C" fp_status fp_ctx_status(fp_ctx ctx, void* stream) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_ctx_status: ctx is NULL");
+  FP_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  uint32_t h = 0;
+  FP_CUDA(cudaMemcpy(&h, ctx->d_err, sizeof h, cudaMemcpyDeviceToHost));
+  FP_CUDA(cudaMemset(ctx->d_err, 0, sizeof h));
+  if (h & ERR_TIMEOUT) {
+    set_error("a bounded device wait gave up (timeout)");
+    return FP_ETIMEOUT;
+  }
+  if (h & ERR_RANGE) {
+    set_error("an input residue or element index was out of range");
+    return FP_EINVAL;
+  }
+  return FP_OK;
+}
+
+extern "C" const char* fp_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------ planner
+
+extern "C" fp_status fp_dqt_choose(uint32_t p, uint32_t k, uint64_t n_accum, uint32_t word,
+                                   fp_dqt_params* out) {
+  FP_CHECK(out != nullptr, FP_EINVAL, "fp_dqt_choose: out is NULL");
+  FP_CHECK(p >= 2 && p <= 251 && is_prime(p), FP_EINVAL, "fp_dqt_choose: p=%u is not a prime <= 251", p);
+  FP_CHECK(k >= 1 && k <= 64, FP_EINVAL, "fp_dqt_choose: k=%u outside [1, 64]", k);
+  FP_CHECK(n_accum >= 1, FP_EINVAL, "fp_dqt_choose: n_accum must be >= 1");
+  int beta = word_beta(word);
+  FP_CHECK(beta > 0, FP_EINVAL, "fp_dqt_choose: bad word type %u", word);
+  // Theorem (Eq. bounds), strict: q > n k (p-1)^2.
+  unsigned __int128 bound = (unsigned __int128)n_accum * k * (uint64_t)(p - 1) * (p - 1);
+  uint32_t b = 0;
+  while (((unsigned __int128)1 << b) <= bound) ++b;
+  if (b == 0) b = 1;
+  FP_CHECK(poly_word_fits(p, k, n_accum, b, beta), FP_EBOUND,
+           "fp_dqt_choose: p=%u k=%u n=%llu needs q=2^%u and %u digits: exceeds %d exact bits",
+           p, k, (unsigned long long)n_accum, b, 2 * k - 1, beta);
+  out->p = p;
+  out->k = k;
+  out->b = b;
+  out->ndig = 2 * k - 1;
+  out->word = word;
+  out->reserved = 0;
+  out->n_accum = n_accum;
+  return FP_OK;
+}
+
+namespace fpd {
+// Right compression parameters (Sec. 7.2-7.4): see fp_mm_choose in the header.
+fp_status mm_choose(uint32_t p, uint64_t kdim, uint32_t algo, uint32_t* b_out, uint32_t* e_out,
+                    uint32_t* chunk_out) {
+  uint64_t pp = (uint64_t)(p - 1) * (p - 1);
+  if (algo == FP_MM_RIGHT_F32 || algo == FP_MM_LEFT_F32) {
+    // Per chunk: two residues at Qc = 2^12 in one binary32 accumulator; chunk digits
+    // kc (p-1)^2 <= 4095 < Qc (Eq. lower, strict) so the word stays <= 4095 * 4097 < 2^24.
+    uint32_t kc = pp ? (uint32_t)(4095 / pp) : 4095u;
+    kc &= ~7u;  // whole K-steps of the kernel
+    if (kc == 0) {
+      set_error("RIGHT_F32 needs (p-1)^2 <= 511 (p=%u)", p);
+      return FP_EBOUND;
+    }
+    if ((uint64_t)kc > kdim) kc = (uint32_t)((kdim + 7) & ~7ull);
+    *b_out = 12;
+    *e_out = 2;
+    *chunk_out = kc;
+    return FP_OK;
+  }
+  if (algo == FP_MM_RIGHT_TC) {
+    // centred residues {-1,0,1}: |digit| <= chunk < Q/2 with Q = 2^10; fp16 operands hold
+    // b0 + 2^10 b1 exactly (11 significant bits).
+    if (p > 3) {
+      set_error("RIGHT_TC needs p <= 3 (p=%u)", p);
+      return FP_EBOUND;
+    }
+    *b_out = 10;
+    *e_out = 2;
+    *chunk_out = 448;
+    return FP_OK;
+  }
+  int beta = (algo == FP_MM_RIGHT_F64 || algo == FP_MM_PLAIN_F64) ? 52 : 64;
+  unsigned __int128 D = (unsigned __int128)kdim * pp;  // largest digit
+  uint32_t b = 1;
+  while (((unsigned __int128)1 << b) <= D) ++b;
+  unsigned __int128 lim = (unsigned __int128)1 << beta;
+  uint32_t e = 0;
+  unsigned __int128 total = 0;
+  while (true) {
+    if ((uint64_t)(e) * b >= 100) break;
+    unsigned __int128 nt = total + (D << (e * b));
+    if (nt >= lim) break;
+    total = nt;
+    ++e;
+  }
+  if (e == 0) {
+    set_error("no packing fits: k=%llu p=%u", (unsigned long long)kdim, p);
+    return FP_EBOUND;
+  }
+  if (algo == FP_MM_PLAIN_F64) e = 1;
+  *b_out = b;
+  *e_out = e;
+  *chunk_out = (uint32_t)(kdim > 0xffffffffull ? 0xffffffffu : kdim);
+  return FP_OK;
+}
+}  // namespace fpd
+
+extern "C" fp_status fp_mm_choose(uint32_t p, uint64_t kdim, uint32_t algo, uint32_t* b,
+                                  uint32_t* e, uint32_t* chunk) {
+  FP_CHECK(b && e && chunk, FP_EINVAL, "fp_mm_choose: null output");
+  FP_CHECK(p >= 2 && p <= 251 && is_prime(p), FP_EINVAL, "fp_mm_choose: p=%u not a prime <= 251", p);
+  FP_CHECK(kdim >= 1, FP_EINVAL, "fp_mm_choose: kdim must be >= 1");
+  return mm_choose(p, kdim, algo, b, e, chunk);
+}
+
+// ------------------------------------------------------------------ DQT pack / unpack
+
+static fp_status check_params(const fp_dqt_params* prm, bool pack) {
+  FP_CHECK(prm != nullptr, FP_EINVAL, "params is NULL");
+  FP_CHECK(prm->p >= 2 && prm->p <= 251 && is_prime(prm->p), FP_EINVAL, "p=%u not a prime <= 251", prm->p);
+  int beta = word_beta(prm->word);
+  FP_CHECK(beta > 0, FP_EINVAL, "bad word type %u", prm->word);
+  FP_CHECK(prm->b >= 1 && prm->b <= 32, FP_EINVAL, "b=%u outside [1, 32]", prm->b);
+  FP_CHECK((1ull << prm->b) >= prm->p, FP_EINVAL, "q=2^%u below p=%u", prm->b, prm->p);
+  if (pack) {
+    FP_CHECK(prm->k >= 1 && prm->k <= 64, FP_EINVAL, "k=%u outside [1, 64]", prm->k);
+    // largest packed operand (p-1) sum_{j<k} q^j must be < 2^beta
+    unsigned __int128 tot = 0;
+    for (uint32_t j = 0; j < prm->k; ++j) {
+      FP_CHECK((uint64_t)j * prm->b < 100, FP_EBOUND, "packed operand exceeds the word");
+      tot += ((unsigned __int128)(prm->p - 1)) << (j * prm->b);
+    }
+    FP_CHECK(tot < ((unsigned __int128)1 << beta), FP_EBOUND,
+             "packing k=%u residues at q=2^%u exceeds %d exact bits", prm->k, prm->b, beta);
+  } else {
+    FP_CHECK(prm->ndig >= 1 && prm->ndig <= 64, FP_EINVAL, "ndig=%u outside [1, 64]", prm->ndig);
+  }
+  return FP_OK;
+}
+
+extern "C" fp_status fp_dqt_pack(fp_ctx ctx, const fp_dqt_params* prm, const uint8_t* coeffs,
+                                 void* words, size_t count, void* stream) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_dqt_pack: ctx is NULL");
+  fp_status s = check_params(prm, true);
+  if (s != FP_OK) return s;
+  if (count == 0) return FP_OK;
+  FP_CHECK(coeffs && words, FP_EINVAL, "fp_dqt_pack: null array");
+  return launch_pack(ctx, *prm, coeffs, words, count, as_stream(stream));
+}
+
+extern "C" fp_status fp_dqt_unpack_redq(fp_ctx ctx, const fp_dqt_params* prm, const void* words,
+                                        uint8_t* coeffs, size_t count, void* stream) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_dqt_unpack_redq: ctx is NULL");
+  fp_status s = check_params(prm, false);
+  if (s != FP_OK) return s;
+  if (count == 0) return FP_OK;
+  FP_CHECK(coeffs && words, FP_EINVAL, "fp_dqt_unpack_redq: null array");
+  return launch_unpack(ctx, *prm, words, coeffs, count, as_stream(stream));
+}
+
+extern "C" fp_status fp_polymul_batched(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t dega,
+                                        const uint8_t* B, uint32_t degb, uint8_t* C, size_t batch,
+                                        int algo, void* stream) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_polymul_batched: ctx is NULL");
+  FP_CHECK(p >= 2 && p <= 251 && is_prime(p), FP_EINVAL, "p=%u not a prime <= 251", p);
+  FP_CHECK(dega <= 1023 && degb <= 1023, FP_EINVAL, "degrees must be <= 1023");
+  FP_CHECK(algo >= FP_ALGO_AUTO && algo <= FP_ALGO_DQT_U32, FP_EINVAL, "bad algo %d", algo);
+  if (batch == 0) return FP_OK;
+  FP_CHECK(A && B && C, FP_EINVAL, "fp_polymul_batched: null array");
+  return launch_polymul(ctx, p, A, dega, B, degb, C, batch, algo, as_stream(stream));
+}
+
+extern "C" fp_status fp_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v, size_t n,
+                            uint32_t* out, int algo, void* stream) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_dot: ctx is NULL");
+  FP_CHECK(p >= 2 && p <= 251 && is_prime(p), FP_EINVAL, "p=%u not a prime <= 251", p);
+  FP_CHECK(out != nullptr, FP_EINVAL, "fp_dot: out is NULL");
+  FP_CHECK(n <= (1ull << 40), FP_EINVAL, "fp_dot: n too large");
+  FP_CHECK(algo >= FP_ALGO_AUTO && algo <= FP_ALGO_DQT_U32, FP_EINVAL, "bad algo %d", algo);
+  FP_CHECK(n == 0 || (u && v), FP_EINVAL, "fp_dot: null array");
+  return launch_dot(ctx, p, u, v, n, out, algo, as_stream(stream));
+}
+
+extern "C" fp_status fp_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
+                               const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, void* stream) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_matmul: ctx is NULL");
+  FP_CHECK(p >= 2 && p <= 251 && is_prime(p), FP_EINVAL, "p=%u not a prime <= 251", p);
+  FP_CHECK(m >= 1 && n >= 1 && k >= 1 && m <= (1 << 20) && n <= (1 << 20) && k <= (1 << 20),
+           FP_EINVAL, "fp_matmul: sizes m=%d n=%d k=%d outside [1, 2^20]", m, n, k);
+  FP_CHECK(lda >= k && ldb >= n && ldc >= n, FP_EINVAL, "fp_matmul: leading dimensions too small");
+  FP_CHECK(A && B && C, FP_EINVAL, "fp_matmul: null array");
+  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_LEFT_F32, FP_EINVAL, "bad algo %d", algo);
+  return launch_matmul(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, algo, as_stream(stream));
+}
+
+extern "C" fp_status fp_pack_cb(fp_ctx ctx, uint32_t p, int k, int n, const uint8_t* B, int ldb,
+                                uint32_t b, uint32_t e, uint32_t word, void* CB, void* stream) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_pack_cb: ctx is NULL");
+  FP_CHECK(p >= 2 && p <= 251 && is_prime(p), FP_EINVAL, "p=%u not a prime <= 251", p);
+  FP_CHECK(k >= 1 && n >= 1 && ldb >= n, FP_EINVAL, "fp_pack_cb: bad sizes");
+  FP_CHECK(e >= 1 && e <= 16 && b >= 1 && b <= 32, FP_EINVAL, "fp_pack_cb: bad b/e");
+  FP_CHECK(word == FP_WORD_F64 || word == FP_WORD_F32 || word == FP_WORD_U64, FP_EINVAL,
+           "fp_pack_cb: word must be F64, F32 or U64");
+  int beta = word_beta(word);
+  unsigned __int128 tot = 0;
+  for (uint32_t t = 0; t < e; ++t) {
+    FP_CHECK((uint64_t)t * b < 100, FP_EBOUND, "fp_pack_cb: packed word exceeds the word");
+    tot += ((unsigned __int128)(p - 1)) << (t * b);
+  }
+  FP_CHECK(tot < ((unsigned __int128)1 << (word == FP_WORD_F32 ? 24 : beta)), FP_EBOUND,
+           "fp_pack_cb: e=%u residues at Q=2^%u exceed the word", e, b);
+  FP_CHECK(B && CB, FP_EINVAL, "fp_pack_cb: null array");
+  return launch_pack_cb(ctx, p, k, n, B, ldb, b, e, word, CB, as_stream(stream));
+}

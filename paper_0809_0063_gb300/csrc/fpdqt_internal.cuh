@@ -1,0 +1,267 @@
+// Internal declarations shared by the CUDA translation units of libfpdqt.
+//
+// Device side: the REDQ routine (Algorithm 2) with the FDIV division (Algorithm FDIV,
+// case 3 of Table "fdiv": inverse rounded up, product rounded down, exact below 2^(beta-1))
+// and the tabulated correction (Sec. 3.4-3.5), for FP64, FP32, u64 and u32 words.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/fpdqt.h"
+
+#define FP_NUM_SMS_HINT 152
+
+// ------------------------------------------------------------------ host error plumbing
+namespace fpd {
+
+void set_error(const char* fmt, ...);
+fp_status cuda_fail(cudaError_t e, const char* what);
+
+#define FP_CUDA(call)                                          \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return fpd::cuda_fail(e_, #call);   \
+  } while (0)
+
+#define FP_CHECK(cond, status, ...)          \
+  do {                                       \
+    if (!(cond)) {                           \
+      fpd::set_error(__VA_ARGS__);           \
+      return (status);                       \
+    }                                        \
+  } while (0)
+
+// Device-side sticky error bits (ORed into ctx->d_err).
+enum : uint32_t { ERR_RANGE = 1u, ERR_TIMEOUT = 2u };
+
+bool is_prime(uint32_t p);
+
+// Invariant integer division by p (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", PLDI 1994, Sec. 4): for p not a power of two, with l = ceil(log2 p),
+// m = floor(2^N (2^l - p) / p) + 1, floor(n/p) = (t + ((n - t) >> 1)) >> (l - 1) where
+// t = mulhi(m, n).  For p a power of two it is a shift by sh.
+struct DivP {
+  uint64_t m64;   // multiplier for 64-bit dividends
+  uint32_t m32;   // multiplier for 32-bit dividends
+  uint32_t l;     // ceil(log2 p)
+  uint32_t pow2;  // 1 if p is a power of two
+  uint32_t sh;    // log2 p when pow2
+};
+DivP make_divp(uint32_t p);
+
+// Word helpers.
+int word_beta(uint32_t word);      // exact integer range in bits (52, 64, 23, 32)
+size_t word_bytes(uint32_t word);
+
+}  // namespace fpd
+
+// ------------------------------------------------------------------ context
+struct fp_ctx_s {
+  int device = 0;
+  int num_sms = FP_NUM_SMS_HINT;
+  uint32_t* d_err = nullptr;        // sticky device error flag
+  void* scratch = nullptr;          // packed operands, partials
+  size_t scratch_bytes = 0;
+  void* scratch2 = nullptr;
+  size_t scratch2_bytes = 0;
+  std::mutex mu;
+  // autotuner cache: key -> chosen variant
+  std::unordered_map<uint64_t, int> tune;
+};
+
+namespace fpd {
+fp_status ensure_scratch(fp_ctx ctx, size_t bytes, int which = 0);
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+}  // namespace fpd
+
+// ------------------------------------------------------------------ device REDQ
+namespace fpd {
+
+// Parameters of one REDQ instance, passed by value to kernels.
+struct RedqParams {
+  uint32_t p;       // prime
+  uint32_t b;       // q = 2^b
+  uint32_t ndig;    // residues recovered per word
+  uint32_t c;       // (-q) mod p: superdiagonal of the correction matrix Q_k (Sec. 3.4)
+  uint32_t mode;    // correction: 0 none (p | q), 1 shuffle Q_2 table (p^3 <= 32),
+                    // 2 shuffle pair table (p^2 <= 32), 3 shared-memory pair table, 4 arithmetic
+  uint32_t pad;
+  double invp_d;    // RU(1/p) in binary64
+  float invp_f;     // RU(1/p) in binary32
+  DivP dv;
+};
+
+RedqParams make_redq(uint32_t p, uint32_t b, uint32_t ndig);
+
+enum : uint32_t { CORR_NONE = 0, CORR_SHFL3 = 1, CORR_SHFL2 = 2, CORR_SMEM2 = 3, CORR_ARITH = 4 };
+
+// floor(n / p) for the invariant p.
+__device__ __forceinline__ uint32_t divp32(uint32_t n, const DivP& d) {
+  if (d.pow2) return n >> d.sh;
+  uint32_t t = __umulhi(d.m32, n);
+  return (t + ((n - t) >> 1)) >> (d.l - 1);
+}
+__device__ __forceinline__ uint64_t divp64(uint64_t n, const DivP& d) {
+  if (d.pow2) return n >> d.sh;
+  uint64_t t = __umul64hi(d.m64, n);
+  return (t + ((n - t) >> 1)) >> (d.l - 1);
+}
+__device__ __forceinline__ uint32_t modp32(uint32_t n, const DivP& d, uint32_t p) {
+  return n - p * divp32(n, d);
+}
+
+// REDQ COMPRESSION quotient s = floor(r / p) (Algorithm 2, first line) per word type.
+// FP words use Algorithm FDIV in case 3 of Table "fdiv": x = RD(r * RU(1/p)), floor(x);
+// exact for r < 2^(beta-1), which the planner guarantees for every packed word.
+template <typename W> struct WordOps;
+
+template <> struct WordOps<double> {
+  __device__ __forceinline__ static uint64_t to_u64(double r) { return (uint64_t)r; }
+  __device__ __forceinline__ static uint64_t quot(double r, const RedqParams& P) {
+    return (uint64_t)__dmul_rd(r, P.invp_d);
+  }
+  __device__ __forceinline__ static double from_u64(uint64_t v) { return __ull2double_rn(v); }
+};
+template <> struct WordOps<float> {
+  __device__ __forceinline__ static uint64_t to_u64(float r) { return (uint64_t)__float2uint_rz(r); }
+  __device__ __forceinline__ static uint64_t quot(float r, const RedqParams& P) {
+    return (uint64_t)__float2uint_rz(__fmul_rd(r, P.invp_f));
+  }
+  __device__ __forceinline__ static float from_u64(uint64_t v) { return __uint2float_rn((uint32_t)v); }
+};
+template <> struct WordOps<uint64_t> {
+  __device__ __forceinline__ static uint64_t to_u64(uint64_t r) { return r; }
+  __device__ __forceinline__ static uint64_t quot(uint64_t r, const RedqParams& P) { return divp64(r, P.dv); }
+  __device__ __forceinline__ static uint64_t from_u64(uint64_t v) { return v; }
+};
+template <> struct WordOps<uint32_t> {
+  __device__ __forceinline__ static uint64_t to_u64(uint32_t r) { return r; }
+  __device__ __forceinline__ static uint64_t quot(uint32_t r, const RedqParams& P) {
+    return divp32(r, P.dv);
+  }
+  __device__ __forceinline__ static uint32_t from_u64(uint64_t v) { return (uint32_t)v; }
+};
+
+// Per-thread state of the correction lookup.  Built once per kernel (the shuffle tables
+// hold one entry per lane; the shared table is filled by the caller's block).
+struct Corrector {
+  uint32_t lane_val;           // shuffle-table entry held by this lane
+  const uint8_t* smem;         // pair table in shared memory (mode CORR_SMEM2)
+
+  __device__ __forceinline__ void init(const RedqParams& P, const uint8_t* sm) {
+    smem = sm;
+    lane_val = 0;
+    uint32_t lane = threadIdx.x & 31u;
+    uint32_t p = P.p;
+    if (P.mode == CORR_SHFL3 && lane < p * p * p) {
+      // Example tmto: the 2x3 map underline{Q}_2 on (u0,u1,u2) -> (u0-q u1, u1-q u2) mod p,
+      // indexed by u0 + u1 p + u2 p^2 (Note on Indexing).
+      uint32_t u0 = lane % p, u1 = (lane / p) % p, u2 = lane / (p * p);
+      uint32_t a = (u0 + P.c * u1) % p, b2 = (u1 + P.c * u2) % p;
+      lane_val = a | (b2 << 8);
+    } else if (P.mode == CORR_SHFL2 && lane < p * p) {
+      uint32_t u0 = lane % p, u1 = lane / p;
+      lane_val = (u0 + P.c * u1) % p;
+    }
+  }
+  // mu_i = (u_i - q u_{i+1}) mod p for one pair.
+  __device__ __forceinline__ uint32_t pair(uint32_t ui, uint32_t un, const RedqParams& P) const {
+    switch (P.mode) {
+      case CORR_SHFL2: return __shfl_sync(0xffffffffu, lane_val, ui + P.p * un);
+      case CORR_SMEM2: return smem[ui + P.p * un];
+      case CORR_ARITH: return modp32(ui + P.c * un, P.dv, P.p);
+      default: return ui;
+    }
+  }
+};
+
+// i-th REDQ compression residue u_i = floor(r/q^i) - p floor(s/q^i) (Algorithm 2).  Since
+// 0 <= u_i < p <= q (Theorem REDQ), only the low b bits of the difference are needed, so the
+// subtraction is done modulo 2^32 and masked.
+__device__ __forceinline__ uint32_t redq_u(uint64_t r, uint64_t s, uint32_t i, const RedqParams& P) {
+  uint32_t sh = i * P.b;
+  uint32_t rr = sh < 64 ? (uint32_t)(r >> sh) : 0u;
+  uint32_t ss = sh < 64 ? (uint32_t)(s >> sh) : 0u;
+  return (rr - P.p * ss) & ((P.b >= 32) ? 0xffffffffu : ((1u << P.b) - 1u));
+}
+
+// Full REDQ_ndig of one word: calls emit(i, mu_i) for i = 0..ndig-1 in increasing order.
+// All 32 lanes of the warp must call this together (shuffle tables); ndig, mode uniform.
+template <typename W, typename Emit>
+__device__ __forceinline__ void redq_word(W rw, const RedqParams& P, const Corrector& C, Emit emit) {
+  uint64_t r = WordOps<W>::to_u64(rw);
+  uint64_t s = WordOps<W>::quot(rw, P);
+  const uint32_t nd = P.ndig;
+  if (P.mode == CORR_NONE) {
+    for (uint32_t i = 0; i < nd; ++i) emit(i, redq_u(r, s, i, P));
+    return;
+  }
+  if (P.mode == CORR_SHFL3) {
+    // two residues per lookup (Example tmto with j = 3)
+    uint32_t u0 = redq_u(r, s, 0, P);
+    uint32_t i = 0;
+    for (; i + 1 < nd; i += 2) {
+      uint32_t u1 = redq_u(r, s, i + 1, P);
+      uint32_t u2 = (i + 2 < nd) ? redq_u(r, s, i + 2, P) : 0u;
+      uint32_t v = __shfl_sync(0xffffffffu, C.lane_val, u0 + P.p * u1 + P.p * P.p * u2);
+      emit(i, v & 0xffu);
+      if (i + 2 < nd) {
+        emit(i + 1, v >> 8);
+      } else {
+        emit(i + 1, u1);       // top residue: mu_d = u_d
+      }
+      u0 = u2;
+    }
+    if (i < nd) emit(i, u0);   // nd odd: the last one is the top residue
+    return;
+  }
+  uint32_t u = redq_u(r, s, 0, P);
+  for (uint32_t i = 0; i < nd; ++i) {
+    if (i + 1 < nd) {
+      uint32_t un = redq_u(r, s, i + 1, P);
+      emit(i, C.pair(u, un, P));
+      u = un;
+    } else {
+      emit(i, u);
+    }
+  }
+}
+
+// Fill the shared pair table (mode CORR_SMEM2) cooperatively: T[u0 + p u1] = (u0 + c u1) mod p.
+__device__ __forceinline__ void fill_pair_table(uint8_t* T, const RedqParams& P) {
+  if (P.mode != CORR_SMEM2) return;
+  for (uint32_t idx = threadIdx.x; idx < P.p * P.p; idx += blockDim.x) {
+    uint32_t u0 = idx % P.p, u1 = idx / P.p;
+    T[idx] = (uint8_t)((u0 + P.c * u1) % P.p);
+  }
+}
+
+// Sticky error reporting from device code.
+__device__ __forceinline__ void flag_error(uint32_t* err, uint32_t bits) {
+  if (err) atomicOr(err, bits);
+}
+
+}  // namespace fpd
+
+// ------------------------------------------------------------------ launchers (per .cu)
+namespace fpd {
+fp_status launch_pack(fp_ctx ctx, const fp_dqt_params& prm, const uint8_t* coeffs, void* words,
+                      size_t count, cudaStream_t st);
+fp_status launch_unpack(fp_ctx ctx, const fp_dqt_params& prm, const void* words, uint8_t* coeffs,
+                        size_t count, cudaStream_t st);
+fp_status launch_polymul(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t da, const uint8_t* B,
+                         uint32_t db, uint8_t* C, size_t batch, int algo, cudaStream_t st);
+fp_status launch_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
+                        const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st);
+fp_status launch_pack_cb(fp_ctx ctx, uint32_t p, int k, int n, const uint8_t* B, int ldb, uint32_t b,
+                         uint32_t e, uint32_t word, void* CB, cudaStream_t st);
+fp_status launch_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v, size_t n,
+                     uint32_t* out, int algo, cudaStream_t st);
+}  // namespace fpd

@@ -1,0 +1,433 @@
+// DQT pack (Eq. dqt), REDQ unpack (Algorithm 2) and the batched polynomial product over F_p
+// (Sec. 5): single-word DQT (one word per operand, one word product, one REDQ), blocked FQT
+// (Sec. 5.2) for larger degrees, and the plain delayed-reduction baseline (Eq. delayed).
+//
+// Every kernel stages its contiguous byte tiles through shared memory with 16-byte global
+// accesses and runs a grid-stride loop over tiles of 256 items (grid = a multiple of the SM
+// count), so HBM traffic is coalesced whatever the number of coefficients per item.
+#include "fpdqt_internal.cuh"
+
+namespace fpd {
+
+static constexpr int TILE = 256;  // items per tile; one thread per item
+
+// Copy nbytes from global to shared (16-byte vectors when the source is aligned).
+__device__ __forceinline__ void stage_in(uint8_t* __restrict__ sm, const uint8_t* __restrict__ g,
+                                         uint32_t nbytes) {
+  if ((((uintptr_t)g) & 15u) == 0) {
+    uint32_t nv = nbytes >> 4;
+    for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x)
+      reinterpret_cast<uint4*>(sm)[i] = __ldg(reinterpret_cast<const uint4*>(g) + i);
+    for (uint32_t i = (nv << 4) + threadIdx.x; i < nbytes; i += blockDim.x) sm[i] = g[i];
+  } else {
+    for (uint32_t i = threadIdx.x; i < nbytes; i += blockDim.x) sm[i] = g[i];
+  }
+}
+
+__device__ __forceinline__ void stage_out(uint8_t* __restrict__ g, const uint8_t* __restrict__ sm,
+                                          uint32_t nbytes) {
+  if ((((uintptr_t)g) & 15u) == 0) {
+    uint32_t nv = nbytes >> 4;
+    for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x)
+      reinterpret_cast<uint4*>(g)[i] = reinterpret_cast<const uint4*>(sm)[i];
+    for (uint32_t i = (nv << 4) + threadIdx.x; i < nbytes; i += blockDim.x) g[i] = sm[i];
+  } else {
+    for (uint32_t i = threadIdx.x; i < nbytes; i += blockDim.x) g[i] = sm[i];
+  }
+}
+
+// Horner evaluation at q = 2^b done with shifts (Sec. 2.1: "the Horner like evaluation of a
+// polynomial at q is just a left shift"); the exact integer is then converted to the word.
+__device__ __forceinline__ uint64_t pack_bits(const uint8_t* c, uint32_t k, uint32_t b, uint32_t p,
+                                              uint32_t& bad) {
+  uint64_t w = 0;
+  for (int j = (int)k - 1; j >= 0; --j) {
+    uint32_t v = c[j];
+    bad |= (v >= p);
+    w = (w << b) | v;
+  }
+  return w;
+}
+
+// ------------------------------------------------------------------ pack
+
+template <typename W>
+__global__ void __launch_bounds__(TILE) k_pack(const uint8_t* __restrict__ coeffs, W* __restrict__ words,
+                                               uint64_t count, uint32_t k, uint32_t b, uint32_t p,
+                                               uint32_t* err) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  uint64_t ntiles = (count + TILE - 1) / TILE;
+  uint32_t bad = 0;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint64_t i0 = t * TILE;
+    uint32_t nit = (uint32_t)((count - i0) < (uint64_t)TILE ? (count - i0) : (uint64_t)TILE);
+    __syncthreads();
+    stage_in(sm, coeffs + i0 * k, nit * k);
+    __syncthreads();
+    if (threadIdx.x < nit) {
+      uint64_t w = pack_bits(sm + threadIdx.x * k, k, b, p, bad);
+      words[i0 + threadIdx.x] = WordOps<W>::from_u64(w);
+    }
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// ------------------------------------------------------------------ unpack (REDQ)
+
+template <typename W>
+__global__ void __launch_bounds__(TILE) k_unpack(const W* __restrict__ words, uint8_t* __restrict__ coeffs,
+                                                 uint64_t count, RedqParams P) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ uint8_t ptab[1024];
+  fill_pair_table(ptab, P);
+  __syncthreads();
+  Corrector C;
+  C.init(P, ptab);
+  const uint32_t nd = P.ndig;
+  uint64_t ntiles = (count + TILE - 1) / TILE;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint64_t i0 = t * TILE;
+    uint32_t nit = (uint32_t)((count - i0) < (uint64_t)TILE ? (count - i0) : (uint64_t)TILE);
+    W w = threadIdx.x < nit ? words[i0 + threadIdx.x] : W(0);
+    __syncthreads();  // previous tile's stage_out done
+    uint8_t* out = sm + threadIdx.x * nd;
+    redq_word<W>(w, P, C, [&](uint32_t i, uint32_t mu) { out[i] = (uint8_t)mu; });
+    __syncthreads();
+    stage_out(coeffs + i0 * nd, sm, nit * nd);
+  }
+}
+
+// ------------------------------------------------------------------ polymul, one word each
+
+// C = A B for small degrees: pack A and B rows (shifts), one word product, REDQ_{ka+kb-1}.
+template <typename W>
+__global__ void __launch_bounds__(TILE) k_polymul_word(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
+                                                       uint8_t* __restrict__ Cout, uint64_t batch, uint32_t ka,
+                                                       uint32_t kb, RedqParams P, uint32_t* err) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ uint8_t ptab[1024];
+  fill_pair_table(ptab, P);
+  __syncthreads();
+  Corrector C;
+  C.init(P, ptab);
+  const uint32_t kc = ka + kb - 1;
+  uint8_t* sa = sm;
+  uint8_t* sb = sm + ((TILE * ka + 15) & ~15u);
+  uint8_t* sc = sb + ((TILE * kb + 15) & ~15u);
+  uint64_t ntiles = (batch + TILE - 1) / TILE;
+  uint32_t bad = 0;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint64_t i0 = t * TILE;
+    uint32_t nit = (uint32_t)((batch - i0) < (uint64_t)TILE ? (batch - i0) : (uint64_t)TILE);
+    __syncthreads();
+    stage_in(sa, A + i0 * ka, nit * ka);
+    stage_in(sb, B + i0 * kb, nit * kb);
+    __syncthreads();
+    W r = W(0);
+    if (threadIdx.x < nit) {
+      W wa = WordOps<W>::from_u64(pack_bits(sa + threadIdx.x * ka, ka, P.b, P.p, bad));
+      W wb = WordOps<W>::from_u64(pack_bits(sb + threadIdx.x * kb, kb, P.b, P.p, bad));
+      r = wa * wb;  // Eq. mult: one machine product carries all convolution sums
+    }
+    uint8_t* out = sc + threadIdx.x * kc;
+    redq_word<W>(r, P, C, [&](uint32_t i, uint32_t mu) { out[i] = (uint8_t)mu; });
+    __syncthreads();
+    stage_out(Cout + i0 * kc, sc, nit * kc);
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// Plain baseline: c_j = sum_i a_i b_{j-i} accumulated without reduction (delayed reduction,
+// Eq. delayed: the sums stay far below 2^32), then one reduction mod p per coefficient.
+__global__ void __launch_bounds__(TILE) k_polymul_plain_small(const uint8_t* __restrict__ A,
+                                                              const uint8_t* __restrict__ B,
+                                                              uint8_t* __restrict__ Cout, uint64_t batch,
+                                                              uint32_t ka, uint32_t kb, uint32_t p, DivP dv,
+                                                              uint32_t* err) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  const uint32_t kc = ka + kb - 1;
+  uint8_t* sa = sm;
+  uint8_t* sb = sm + ((TILE * ka + 15) & ~15u);
+  uint8_t* sc = sb + ((TILE * kb + 15) & ~15u);
+  uint64_t ntiles = (batch + TILE - 1) / TILE;
+  uint32_t bad = 0;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint64_t i0 = t * TILE;
+    uint32_t nit = (uint32_t)((batch - i0) < (uint64_t)TILE ? (batch - i0) : (uint64_t)TILE);
+    __syncthreads();
+    stage_in(sa, A + i0 * ka, nit * ka);
+    stage_in(sb, B + i0 * kb, nit * kb);
+    __syncthreads();
+    if (threadIdx.x < nit) {
+      const uint8_t* a = sa + threadIdx.x * ka;
+      const uint8_t* bb = sb + threadIdx.x * kb;
+      uint8_t* out = sc + threadIdx.x * kc;
+      for (uint32_t i = 0; i < ka; ++i) bad |= a[i] >= p;
+      for (uint32_t i = 0; i < kb; ++i) bad |= bb[i] >= p;
+      for (uint32_t j = 0; j < kc; ++j) {
+        uint32_t lo = j + 1 > kb ? j + 1 - kb : 0;
+        uint32_t hi = j < ka - 1 ? j : ka - 1;
+        uint32_t s = 0;
+        for (uint32_t i = lo; i <= hi; ++i) s += (uint32_t)a[i] * bb[j - i];
+        out[j] = (uint8_t)modp32(s, dv, p);
+      }
+    }
+    __syncthreads();
+    stage_out(Cout + i0 * kc, sc, nit * kc);
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// Plain baseline for large degrees: one block per pair, one thread per output coefficient.
+__global__ void __launch_bounds__(256) k_polymul_plain_big(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
+                                                           uint8_t* __restrict__ Cout, uint64_t batch, uint32_t ka,
+                                                           uint32_t kb, uint32_t p, DivP dv, uint32_t* err) {
+  __shared__ __align__(16) uint8_t sa[1024];
+  __shared__ __align__(16) uint8_t sb[1024];
+  uint32_t bad = 0;
+  const uint32_t kc = ka + kb - 1;
+  for (uint64_t t = blockIdx.x; t < batch; t += gridDim.x) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < ka; i += blockDim.x) { sa[i] = A[t * ka + i]; bad |= sa[i] >= p; }
+    for (uint32_t i = threadIdx.x; i < kb; i += blockDim.x) { sb[i] = B[t * kb + i]; bad |= sb[i] >= p; }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < kc; j += blockDim.x) {
+      uint32_t lo = j + 1 > kb ? j + 1 - kb : 0;
+      uint32_t hi = j < ka - 1 ? j : ka - 1;
+      uint32_t s = 0;
+      for (uint32_t i = lo; i <= hi; ++i) s += (uint32_t)sa[i] * sb[j - i];
+      Cout[t * kc + j] = (uint8_t)modp32(s, dv, p);
+    }
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// Blocked FQT (Sec. 5.2): P = sum_i P_i (X^{d+1})^i with each P_i (d+1 coefficients) in one
+// u64 word at q = 2^b; output word t = sum_i P_i Q_{t-i} accumulated in the word (delayed
+// reduction, the planner keeps every digit below q), then REDQ_{2d+1}; the residues of words t
+// and t-1 overlap on d coefficients and are added mod p.  One block per pair.
+__global__ void __launch_bounds__(256) k_polymul_fqt(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
+                                                     uint8_t* __restrict__ Cout, uint64_t batch, uint32_t ka,
+                                                     uint32_t kb, uint32_t d1, RedqParams P, uint32_t* err) {
+  __shared__ uint64_t wa[1024];
+  __shared__ uint64_t wb[1024];
+  __shared__ uint8_t res[4096 + 64];   // residues of output block words, (2d+1) each
+  __shared__ uint8_t ptab[1024];
+  fill_pair_table(ptab, P);
+  __syncthreads();
+  Corrector C;
+  C.init(P, ptab);
+  uint32_t bad = 0;
+  const uint32_t na = (ka + d1 - 1) / d1, nb = (kb + d1 - 1) / d1;
+  const uint32_t nw = na + nb - 1;              // output words
+  const uint32_t kc = ka + kb - 1;
+  const uint32_t nd = 2 * d1 - 1;               // residues per output word
+  for (uint64_t t = blockIdx.x; t < batch; t += gridDim.x) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < na; i += blockDim.x) {
+      uint64_t w = 0;
+      for (int j = (int)d1 - 1; j >= 0; --j) {
+        uint32_t idx = i * d1 + j;
+        uint32_t v = idx < ka ? A[t * ka + idx] : 0u;
+        bad |= v >= P.p;
+        w = (w << P.b) | v;
+      }
+      wa[i] = w;
+    }
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
+      uint64_t w = 0;
+      for (int j = (int)d1 - 1; j >= 0; --j) {
+        uint32_t idx = i * d1 + j;
+        uint32_t v = idx < kb ? B[t * kb + idx] : 0u;
+        bad |= v >= P.p;
+        w = (w << P.b) | v;
+      }
+      wb[i] = w;
+    }
+    __syncthreads();
+    // whole warps iterate so that the shuffle-table lookups see 32 active lanes
+    for (uint32_t base = 0; base < nw; base += blockDim.x) {
+      uint32_t o = base + threadIdx.x;
+      uint64_t acc = 0;
+      if (o < nw) {
+        uint32_t lo = o + 1 > nb ? o + 1 - nb : 0;
+        uint32_t hi = o < na - 1 ? o : na - 1;
+        for (uint32_t i = lo; i <= hi; ++i) acc += wa[i] * wb[o - i];
+      }
+      uint8_t* out = res + (o < nw ? o : 0) * nd;
+      bool own = o < nw;
+      redq_word<uint64_t>(acc, P, C, [&](uint32_t i, uint32_t mu) { if (own) out[i] = (uint8_t)mu; });
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < kc; j += blockDim.x) {
+      uint32_t o = j / d1, r = j - o * d1;
+      uint32_t v = o < nw ? res[o * nd + r] : 0u;
+      if (o >= 1 && r + d1 < nd) v += res[(o - 1) * nd + r + d1];
+      if (v >= P.p) v -= P.p;
+      Cout[t * kc + j] = (uint8_t)v;
+    }
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// ------------------------------------------------------------------ launchers
+
+static int grid_for(fp_ctx ctx, uint64_t ntiles, int per_sm) {
+  uint64_t g = (uint64_t)ctx->num_sms * per_sm;
+  if (ntiles < g) g = ntiles;
+  return (int)(g ? g : 1);
+}
+
+template <typename W>
+static fp_status pack_t(fp_ctx ctx, const fp_dqt_params& prm, const uint8_t* coeffs, void* words,
+                        size_t count, cudaStream_t st) {
+  size_t smem = TILE * prm.k;
+  int grid = grid_for(ctx, (count + TILE - 1) / TILE, 8);
+  k_pack<W><<<grid, TILE, smem, st>>>(coeffs, (W*)words, count, prm.k, prm.b, prm.p, ctx->d_err);
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
+fp_status launch_pack(fp_ctx ctx, const fp_dqt_params& prm, const uint8_t* coeffs, void* words,
+                      size_t count, cudaStream_t st) {
+  switch (prm.word) {
+    case FP_WORD_F64: return pack_t<double>(ctx, prm, coeffs, words, count, st);
+    case FP_WORD_F32: return pack_t<float>(ctx, prm, coeffs, words, count, st);
+    case FP_WORD_U64: return pack_t<uint64_t>(ctx, prm, coeffs, words, count, st);
+    default: return pack_t<uint32_t>(ctx, prm, coeffs, words, count, st);
+  }
+}
+
+template <typename W>
+static fp_status unpack_t(fp_ctx ctx, const fp_dqt_params& prm, const void* words, uint8_t* coeffs,
+                          size_t count, cudaStream_t st) {
+  RedqParams P = make_redq(prm.p, prm.b, prm.ndig);
+  size_t smem = TILE * prm.ndig;
+  int grid = grid_for(ctx, (count + TILE - 1) / TILE, 8);
+  k_unpack<W><<<grid, TILE, smem, st>>>((const W*)words, coeffs, count, P);
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
+fp_status launch_unpack(fp_ctx ctx, const fp_dqt_params& prm, const void* words, uint8_t* coeffs,
+                        size_t count, cudaStream_t st) {
+  switch (prm.word) {
+    case FP_WORD_F64: return unpack_t<double>(ctx, prm, words, coeffs, count, st);
+    case FP_WORD_F32: return unpack_t<float>(ctx, prm, words, coeffs, count, st);
+    case FP_WORD_U64: return unpack_t<uint64_t>(ctx, prm, words, coeffs, count, st);
+    default: return unpack_t<uint32_t>(ctx, prm, words, coeffs, count, st);
+  }
+}
+
+// Exact largest packed product of a (ka coefficients) by b (kb coefficients) at q = 2^bq:
+// digit j holds at most min(j+1, ka, kb, ka+kb-1-j) products of (p-1)^2.
+static bool product_fits(uint32_t p, uint32_t ka, uint32_t kb, uint32_t bq, int beta) {
+  uint32_t kc = ka + kb - 1;
+  unsigned __int128 tot = 0, lim = (unsigned __int128)1 << beta;
+  for (uint32_t j = 0; j < kc; ++j) {
+    uint32_t t = j + 1;
+    t = t < ka ? t : ka;
+    t = t < kb ? t : kb;
+    t = t < kc - j ? t : kc - j;
+    if ((uint64_t)j * bq >= 100) return false;
+    tot += ((unsigned __int128)t * (p - 1) * (p - 1)) << (j * bq);
+    if (tot >= lim) return false;
+  }
+  return true;
+}
+
+// q for a single-word product: smallest 2^b above the largest digit min(ka, kb) (p-1)^2
+// (Eq. bounds with n = 1, strict); b >= 1 and q >= p.
+static uint32_t poly_qbits(uint32_t p, uint32_t ka, uint32_t kb) {
+  uint64_t D = (uint64_t)(ka < kb ? ka : kb) * (p - 1) * (p - 1);
+  uint32_t b = 1;
+  while ((1ull << b) <= D || (1ull << b) < p) ++b;
+  return b;
+}
+
+template <typename W>
+static fp_status polymul_word_t(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t ka, const uint8_t* B,
+                                uint32_t kb, uint8_t* C, size_t batch, uint32_t bq, cudaStream_t st) {
+  uint32_t kc = ka + kb - 1;
+  RedqParams P = make_redq(p, bq, kc);
+  size_t smem = ((TILE * ka + 15) & ~15u) + ((TILE * kb + 15) & ~15u) + TILE * kc;
+  int grid = grid_for(ctx, (batch + TILE - 1) / TILE, 8);
+  k_polymul_word<W><<<grid, TILE, smem, st>>>(A, B, C, batch, ka, kb, P, ctx->d_err);
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
+fp_status launch_polymul(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t da, const uint8_t* B,
+                         uint32_t db, uint8_t* C, size_t batch, int algo, cudaStream_t st) {
+  uint32_t ka = da + 1, kb = db + 1, kc = ka + kb - 1;
+  if (algo == FP_ALGO_PLAIN) {
+    DivP dv = make_divp(p);
+    if (kc <= 64) {
+      size_t smem = ((TILE * ka + 15) & ~15u) + ((TILE * kb + 15) & ~15u) + TILE * kc;
+      int grid = grid_for(ctx, (batch + TILE - 1) / TILE, 8);
+      k_polymul_plain_small<<<grid, TILE, smem, st>>>(A, B, C, batch, ka, kb, p, dv, ctx->d_err);
+    } else {
+      int grid = grid_for(ctx, batch, 16);
+      k_polymul_plain_big<<<grid, 256, 0, st>>>(A, B, C, batch, ka, kb, p, dv, ctx->d_err);
+    }
+    FP_CUDA(cudaGetLastError());
+    return FP_OK;
+  }
+  uint32_t bq = poly_qbits(p, ka, kb);
+  // word order for AUTO: integer words first (no FP64 pipe, which is slow on this part)
+  static const int order_auto[4] = {FP_WORD_U32, FP_WORD_F32, FP_WORD_U64, FP_WORD_F64};
+  int forced = -1;
+  if (algo == FP_ALGO_DQT_F64) forced = FP_WORD_F64;
+  if (algo == FP_ALGO_DQT_U64) forced = FP_WORD_U64;
+  if (algo == FP_ALGO_DQT_F32) forced = FP_WORD_F32;
+  if (algo == FP_ALGO_DQT_U32) forced = FP_WORD_U32;
+  if (kc <= 64) {
+    for (int oi = 0; oi < 4; ++oi) {
+      int w = forced >= 0 ? forced : order_auto[oi];
+      if (product_fits(p, ka, kb, bq, word_beta(w))) {
+        switch (w) {
+          case FP_WORD_F64: return polymul_word_t<double>(ctx, p, A, ka, B, kb, C, batch, bq, st);
+          case FP_WORD_F32: return polymul_word_t<float>(ctx, p, A, ka, B, kb, C, batch, bq, st);
+          case FP_WORD_U64: return polymul_word_t<uint64_t>(ctx, p, A, ka, B, kb, C, batch, bq, st);
+          default: return polymul_word_t<uint32_t>(ctx, p, A, ka, B, kb, C, batch, bq, st);
+        }
+      }
+      if (forced >= 0) break;
+    }
+  }
+  // Blocked FQT in u64 words (Sec. 5.2): largest block size d+1 whose accumulated output word
+  // fits 64 bits; digit bound: min(#blocks) (d+1) (p-1)^2 < q.
+  if (forced == FP_WORD_F64 || forced == FP_WORD_F32 || forced == FP_WORD_U32) {
+    set_error("polymul: degrees %u x %u do not fit one word of the forced type; use DQT_U64 or AUTO",
+              da, db);
+    return FP_EBOUND;
+  }
+  uint32_t best_d1 = 0, best_b = 0;
+  for (uint32_t d1 = 1; d1 <= 32; ++d1) {
+    uint32_t na = (ka + d1 - 1) / d1, nb = (kb + d1 - 1) / d1;
+    uint64_t nterms = na < nb ? na : nb;
+    uint64_t D = nterms * d1 * (uint64_t)(p - 1) * (p - 1);
+    uint32_t b = 1;
+    while ((1ull << b) <= D || (1ull << b) < p) ++b;
+    // largest output word: all 2d+1 digits at D (upper bound)
+    unsigned __int128 tot = 0;
+    bool ok = true;
+    for (uint32_t j = 0; j < 2 * d1 - 1 && ok; ++j) {
+      if ((uint64_t)j * b >= 100) { ok = false; break; }
+      tot += (unsigned __int128)D << (j * b);
+      if (tot >> 64) ok = false;
+    }
+    if (!ok) break;
+    if (na + nb - 1 > 2048 || (na + nb - 1) * (2 * d1 - 1) > 4096) continue;
+    best_d1 = d1;
+    best_b = b;
+  }
+  FP_CHECK(best_d1 >= 1, FP_EBOUND, "polymul: no FQT block size fits a 64-bit word (p=%u)", p);
+  RedqParams P = make_redq(p, best_b, 2 * best_d1 - 1);
+  int grid = grid_for(ctx, batch, 16);
+  k_polymul_fqt<<<grid, 256, 0, st>>>(A, B, C, batch, ka, kb, best_d1, P, ctx->d_err);
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
+}  // namespace fpd

@@ -1,0 +1,249 @@
+// GF(p^k) multiplication by Algorithm FGDP (Sec. 6) with n = 1, on the device:
+//   1. table DQT: element index -> u64 word sum_i c_i q^i (one shared-memory lookup),
+//   2. one word product,
+//   3. REDQ COMPRESSION: u_i = floor(r/q^i) - p floor(s/q^i), i = 0..2k-2 (no correction),
+//   4./5. L[u_0..u_{k-1}] and H[u_{k-1}..u_{2k-2}] (Theorem fgdp), each already reduced modulo
+//      the field's modulus, indexed in the binary format sum u_i 2^{c i}, c = ceil(log2 p)
+//      (Note on Indexing),
+//   6. one field addition.
+// L and H entries hold the coefficient vector "spread" in 4-bit fields (p <= 7) or 8-bit fields,
+// so the field addition is one integer add and a per-field conditional subtraction of p.
+#include <algorithm>
+#include <vector>
+
+#include "fpdqt_internal.cuh"
+
+struct fp_gf_s {
+  uint32_t p = 0, k = 0, b = 0, c = 0, fb = 0;  // q = 2^b; index bits per residue c; field bits fb
+  uint32_t order = 0;                            // p^k
+  uint32_t elem_bytes = 1;
+  std::vector<uint32_t> modulus;                 // k+1 coefficients, constant first, monic
+  uint64_t* d_word = nullptr;                    // [p^k]
+  uint32_t* d_L = nullptr;                       // [2^{c k}]
+  uint32_t* d_H = nullptr;                       // [2^{c k}]
+  fpd::RedqParams P{};
+  int device = 0;
+};
+
+namespace fpd {
+
+// ---------------------------------------------------------------- host field construction
+
+static std::vector<uint32_t> poly_rem(std::vector<uint32_t> a, const std::vector<uint32_t>& m, uint32_t p) {
+  int k = (int)m.size() - 1;
+  for (int d = (int)a.size() - 1; d >= k; --d) {
+    uint32_t lead = a[d] % p;
+    if (!lead) continue;
+    for (int i = 0; i <= k; ++i) a[d - k + i] = (a[d - k + i] + (p - lead) * m[i]) % p;
+  }
+  a.resize(k);
+  return a;
+}
+
+static bool irreducible(const std::vector<uint32_t>& f, uint32_t p) {
+  int k = (int)f.size() - 1;
+  for (int deg = 1; deg <= k / 2; ++deg) {
+    uint64_t cnt = 1;
+    for (int i = 0; i < deg; ++i) cnt *= p;
+    for (uint64_t key = 0; key < cnt; ++key) {
+      std::vector<uint32_t> g(deg + 1);
+      uint64_t x = key;
+      for (int i = 0; i < deg; ++i) { g[i] = (uint32_t)(x % p); x /= p; }
+      g[deg] = 1;
+      std::vector<uint32_t> r = poly_rem(f, g, p);
+      bool zero = true;
+      for (uint32_t v : r) zero &= v == 0;
+      if (zero) return false;
+    }
+  }
+  return true;
+}
+
+static uint32_t spread(const std::vector<uint32_t>& coeffs, uint32_t fb) {
+  uint32_t s = 0;
+  for (size_t i = 0; i < coeffs.size(); ++i) s |= coeffs[i] << (i * fb);
+  return s;
+}
+
+// ---------------------------------------------------------------- kernel
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_gf_mul(const E* __restrict__ a, const E* __restrict__ b, E* __restrict__ c,
+                                                uint64_t count, const uint64_t* __restrict__ gword,
+                                                const uint32_t* __restrict__ gL, const uint32_t* __restrict__ gH,
+                                                uint32_t order, uint32_t k, uint32_t cbits, uint32_t fb,
+                                                RedqParams P, uint32_t* err) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  uint64_t* sw = reinterpret_cast<uint64_t*>(sm);
+  const uint32_t tsz = 1u << (cbits * k);
+  uint32_t* sL = reinterpret_cast<uint32_t*>(sw + order);
+  uint32_t* sH = sL + tsz;
+  for (uint32_t i = threadIdx.x; i < order; i += blockDim.x) sw[i] = gword[i];
+  for (uint32_t i = threadIdx.x; i < tsz; i += blockDim.x) { sL[i] = gL[i]; sH[i] = gH[i]; }
+  __syncthreads();
+  const uint32_t p = P.p, bq = P.b;
+  const uint32_t qmask = (1u << bq) - 1u;
+  const uint32_t fmask = (1u << fb) - 1u;
+  uint32_t ones = 0;
+  for (uint32_t i = 0; i < k; ++i) ones |= 1u << (i * fb);
+  const uint32_t hb = fb - 1;                 // bit tested after adding 2^hb - p per field
+  uint32_t bad = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t xa = a[i], xb = b[i];
+    bad |= (xa >= order) | (xb >= order);
+    xa = xa < order ? xa : 0u;
+    xb = xb < order ? xb : 0u;
+    uint64_t r = sw[xa] * sw[xb];             // lines 1-2
+    uint64_t s = divp64(r, P.dv);             // REDQ compression quotient (line 3)
+    uint32_t il = 0, ih = 0;
+    for (uint32_t j = 0; j < 2 * k - 1; ++j) {
+      uint32_t sh = j * bq;
+      uint32_t uj = ((uint32_t)(r >> sh) - p * (uint32_t)(s >> sh)) & qmask;
+      if (j < k) il |= uj << (j * cbits);
+      if (j >= k - 1) ih |= uj << ((j - (k - 1)) * cbits);
+    }
+    uint32_t x = sL[il] + sH[ih];              // lines 4-6: two lookups, one field add
+    uint32_t ge = ((x + ((1u << hb) - p) * ones) >> hb) & ones;
+    x -= p * ge;
+    uint32_t idx = 0;
+    for (int j = (int)k - 1; j >= 0; --j) idx = idx * p + ((x >> (j * fb)) & fmask);
+    c[i] = (E)idx;
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+}  // namespace fpd
+
+using namespace fpd;
+
+extern "C" fp_status fp_gf_create(fp_ctx ctx, uint32_t p, uint32_t k, fp_gf* out) {
+  FP_CHECK(ctx && out, FP_EINVAL, "fp_gf_create: null argument");
+  *out = nullptr;
+  FP_CHECK(p >= 2 && p <= 251 && is_prime(p), FP_EINVAL, "fp_gf_create: p=%u not a prime <= 251", p);
+  FP_CHECK(k >= 1 && k <= 16, FP_EINVAL, "fp_gf_create: k=%u outside [1, 16]", k);
+  uint64_t order = 1;
+  for (uint32_t i = 0; i < k; ++i) order *= p;
+  FP_CHECK(order <= 65536, FP_EINVAL, "fp_gf_create: p^k = %llu > 65536", (unsigned long long)order);
+  uint32_t cbits = 0;
+  while ((1u << cbits) < p) ++cbits;
+  FP_CHECK(cbits * k <= 12, FP_EUNSUPPORTED,
+           "fp_gf_create: binary-indexed L/H tables would need 2^%u entries", cbits * k);
+  // field bits: each field must hold 2p-2 plus headroom for the compare trick (2^(fb-1) >= p)
+  uint32_t fb = 1;
+  while ((1u << (fb - 1)) < p || (1u << fb) <= 2 * p - 2 + (1u << (fb - 1)) - p) ++fb;
+  FP_CHECK(fb * k <= 32, FP_EUNSUPPORTED, "fp_gf_create: spread form needs %u bits", fb * k);
+  // q: smallest 2^b above the largest digit k (p-1)^2 of a product of two field elements
+  uint64_t D = (uint64_t)k * (p - 1) * (p - 1);
+  uint32_t b = 1;
+  while ((1ull << b) <= D || (1ull << b) < p) ++b;
+  // largest word product must fit 64 bits
+  unsigned __int128 tot = 0;
+  for (uint32_t j = 0; j < 2 * k - 1; ++j) {
+    uint32_t t = std::min<uint32_t>(std::min<uint32_t>(j + 1, 2 * k - 1 - j), k);
+    FP_CHECK((uint64_t)j * b < 100, FP_EUNSUPPORTED, "fp_gf_create: product exceeds 64 bits");
+    tot += ((unsigned __int128)t * (p - 1) * (p - 1)) << (j * b);
+  }
+  FP_CHECK(tot < ((unsigned __int128)1 << 64), FP_EUNSUPPORTED,
+           "fp_gf_create: GF(%u^%u) product does not fit a 64-bit word", p, k);
+
+  fp_gf g = new (std::nothrow) fp_gf_s();
+  FP_CHECK(g != nullptr, FP_ENOMEM, "fp_gf_create: out of host memory");
+  g->p = p; g->k = k; g->b = b; g->c = cbits; g->fb = fb; g->order = (uint32_t)order;
+  g->elem_bytes = order <= 256 ? 1 : 2;
+  g->device = ctx->device;
+  // modulus: smallest key sum_{i<k} c_i p^i among monic irreducibles
+  for (uint64_t key = 0; key < order; ++key) {
+    std::vector<uint32_t> f(k + 1);
+    uint64_t x = key;
+    for (uint32_t i = 0; i < k; ++i) { f[i] = (uint32_t)(x % p); x /= p; }
+    f[k] = 1;
+    if (k == 1 || irreducible(f, p)) { g->modulus = f; break; }
+  }
+  if (g->modulus.empty()) { delete g; set_error("fp_gf_create: no irreducible found"); return FP_EINVAL; }
+
+  // tables
+  std::vector<uint64_t> word(order);
+  for (uint64_t x = 0; x < order; ++x) {
+    uint64_t w = 0, y = x;
+    std::vector<uint32_t> cf(k);
+    for (uint32_t i = 0; i < k; ++i) { cf[i] = (uint32_t)(y % p); y /= p; }
+    for (int i = (int)k - 1; i >= 0; --i) w = (w << b) | cf[i];
+    word[x] = w;
+  }
+  const uint32_t tsz = 1u << (cbits * k);
+  const uint32_t cq = (uint32_t)((p - ((1ull << b) % p)) % p);  // -q mod p
+  std::vector<uint32_t> L(tsz, 0), H(tsz, 0);
+  for (uint32_t idx = 0; idx < tsz; ++idx) {
+    std::vector<uint32_t> u(k);
+    bool valid = true;
+    for (uint32_t i = 0; i < k; ++i) {
+      u[i] = (idx >> (i * cbits)) & ((1u << cbits) - 1);
+      valid &= u[i] < p;
+    }
+    if (!valid) continue;
+    // L = sum_{i=0}^{k-2} (u_i - q u_{i+1} mod p) X^i  (u = u_0..u_{k-1})
+    std::vector<uint32_t> pl(2 * k - 1, 0);
+    for (uint32_t i = 0; i + 1 < k; ++i) pl[i] = (u[i] + cq * u[i + 1]) % p;
+    L[idx] = spread(poly_rem(pl, g->modulus, p), fb);
+    // H = u_{2k-2} X^{2k-2} + sum_{i=k-1}^{2k-3} (u_i - q u_{i+1} mod p) X^i  (u = u_{k-1}..)
+    std::vector<uint32_t> ph(2 * k - 1, 0);
+    ph[2 * k - 2] = u[k - 1];
+    for (uint32_t j = 0; j + 1 < k; ++j) ph[k - 1 + j] = (u[j] + cq * u[j + 1]) % p;
+    H[idx] = spread(poly_rem(ph, g->modulus, p), fb);
+  }
+  g->P = make_redq(p, b, 2 * k - 1);
+  cudaError_t e = cudaMalloc(&g->d_word, order * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_L, tsz * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_H, tsz * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_word, word.data(), order * sizeof(uint64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_L, L.data(), tsz * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_H, H.data(), tsz * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    fp_gf_destroy(g);
+    return cuda_fail(e, "fp_gf_create tables");
+  }
+  *out = g;
+  return FP_OK;
+}
+
+extern "C" void fp_gf_destroy(fp_gf g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  if (g->d_word) cudaFree(g->d_word);
+  if (g->d_L) cudaFree(g->d_L);
+  if (g->d_H) cudaFree(g->d_H);
+  delete g;
+}
+
+extern "C" fp_status fp_gf_info(fp_gf g, uint32_t* modulus, uint32_t* b, uint32_t* word, uint32_t* elem_bytes) {
+  FP_CHECK(g != nullptr, FP_EINVAL, "fp_gf_info: gf is NULL");
+  if (modulus)
+    for (uint32_t i = 0; i <= g->k; ++i) modulus[i] = g->modulus[i];
+  if (b) *b = g->b;
+  if (word) *word = FP_WORD_U64;
+  if (elem_bytes) *elem_bytes = g->elem_bytes;
+  return FP_OK;
+}
+
+extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const void* b, void* c, size_t count,
+                                       void* stream) {
+  FP_CHECK(ctx && g, FP_EINVAL, "fp_gf_mul_batched: null ctx or field");
+  if (count == 0) return FP_OK;
+  FP_CHECK(a && b && c, FP_EINVAL, "fp_gf_mul_batched: null array");
+  cudaStream_t st = as_stream(stream);
+  const uint32_t tsz = 1u << (g->c * g->k);
+  size_t smem = g->order * sizeof(uint64_t) + 2 * tsz * sizeof(uint32_t);
+  int grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)ctx->num_sms * 4);
+  if (g->elem_bytes == 1) {
+    FP_CUDA(cudaFuncSetAttribute(k_gf_mul<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_gf_mul<uint8_t><<<grid, 256, smem, st>>>((const uint8_t*)a, (const uint8_t*)b, (uint8_t*)c, count, g->d_word,
+                                               g->d_L, g->d_H, g->order, g->k, g->c, g->fb, g->P, ctx->d_err);
+  } else {
+    FP_CUDA(cudaFuncSetAttribute(k_gf_mul<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_gf_mul<uint16_t><<<grid, 256, smem, st>>>((const uint16_t*)a, (const uint16_t*)b, (uint16_t*)c, count,
+                                                g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb, g->P,
+                                                ctx->d_err);
+  }
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}

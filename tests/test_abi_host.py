@@ -1,0 +1,100 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point the header declares,
+its host-only planner agrees with the oracle's bounds, and device calls fail loudly (with a
+status, not a fallback) when no GPU is present."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fp():
+    import __graft_entry__ as g
+    g.build()
+    import paper_0809_0063_gb300 as m
+    return m
+
+
+def header_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(fp_\w+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_header_symbol(fp):
+    L = fp.lib()
+    names = header_functions()
+    assert len(names) >= 15
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding wraps each of them under the same name
+    assert all(n in fp._SIGS for n in names), sorted(names - set(fp._SIGS))
+
+
+def test_dqt_choose_matches_theorem_bounds(fp):
+    """q is the Theorem's (Eq. bounds) smallest power of two above n k (p-1)^2; the word is
+    accepted exactly when the largest packed result n DQT(all p-1)^2 fits the word's exact
+    range (the Theorem's (2k-1) log2 q <= beta is a sufficient form of that condition)."""
+    from oracle import bounds, dqt
+    for p in (2, 3, 5, 7, 31, 251):
+        for k in (1, 2, 3, 5, 8):
+            for n in (1, 7, 1000):
+                for word, beta in ((fp.FP_WORD_F64, 52), (fp.FP_WORD_U64, 64), (fp.FP_WORD_F32, 23), (fp.FP_WORD_U32, 32)):
+                    q = max(bounds.smallest_pow2_q(n * k * (p - 1) ** 2), 2)
+                    largest = n * dqt.dqt([p - 1] * k, q) ** 2
+                    theorem_ok = bounds.thm_bounds_ok(q, n, k, p, beta)
+                    try:
+                        prm = fp.fp_dqt_choose(p, k, n, word)
+                    except fp.FpError as e:
+                        assert e.status == fp.FP_EBOUND
+                        assert largest >= 2 ** beta and not theorem_ok
+                        continue
+                    assert (1 << prm.b) == q and prm.ndig == 2 * k - 1
+                    assert largest < 2 ** beta
+
+
+def test_mm_choose_matches_eq_lower_upper(fp):
+    from oracle import bounds
+    for p in (2, 3, 7, 17, 31):
+        for kdim in (16, 255, 256, 1024, 2047, 2048, 4096, 32767):
+            b, e, _ = fp.fp_mm_choose(p, kdim, fp.FP_MM_RIGHT_F64)
+            Q = bounds.cmm_Q(kdim, p)
+            assert (1 << b) == max(Q, 2)
+            D = kdim * (p - 1) ** 2
+            # the largest packed word fits below 2^52 and one more residue would not
+            assert D * sum(Q ** t for t in range(e)) < 2 ** 52
+            assert D * sum(Q ** t for t in range(e + 1)) >= 2 ** 52
+            assert e <= bounds.compression_factor(53, Q) + 1
+    # Table "comprange" column n <= 2047 (strict reading of the 2048 column): Q = 2^13, e = 4
+    assert fp.fp_mm_choose(3, 2047, fp.FP_MM_RIGHT_F64)[:2] == (13, 4)
+    assert fp.fp_mm_choose(3, 2048, fp.FP_MM_RIGHT_F64)[:2] == (14, 3)
+    # FP32 words: two residues at 2^12 per chunk, chunk digit bound below 2^12
+    b, e, c = fp.fp_mm_choose(3, 4096, fp.FP_MM_RIGHT_F32)
+    assert (b, e) == (12, 2) and c * 4 < 4096 and c % 8 == 0
+    with pytest.raises(fp.FpError):
+        fp.fp_mm_choose(31, 4096, fp.FP_MM_RIGHT_F32)
+
+
+def test_bad_arguments_are_rejected_on_host(fp):
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_dqt_choose(4, 3, 1, fp.FP_WORD_F64)       # not prime
+    assert ei.value.status == fp.FP_EINVAL
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_dqt_choose(251, 40, 10 ** 6, fp.FP_WORD_F32)
+    assert ei.value.status == fp.FP_EBOUND
+    assert "exceeds" in fp.fp_last_error()
+
+
+def test_device_calls_fail_loudly_without_gpu(fp):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_ctx_create(0)
+    assert ei.value.status in (fp.FP_ECUDA, fp.FP_EINVAL)

@@ -1,0 +1,145 @@
+"""GPU parity of DQT pack, REDQ unpack and the batched polynomial product against the oracle
+(bit-exact).  Calls go through the C ABI via the thin binding."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import dqt as odqt
+from oracle import field
+from tests._gpu import to_dev, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch, dev = torch_dev()
+    import __graft_entry__ as g
+    g.build()
+    import paper_0809_0063_gb300 as fp
+    ctx = fp.fp_ctx_create(0)
+    yield fp, torch, dev, ctx
+    fp.fp_ctx_destroy(ctx)
+
+
+WORDS = {0: (np.float64, 52), 1: (np.uint64, 64), 2: (np.float32, 23), 3: (np.uint32, 32)}
+
+
+def _as_int(arr):
+    return [int(x) for x in np.asarray(arr).astype(np.float64 if arr.dtype.kind == "f" else arr.dtype)] \
+        if arr.dtype.kind == "f" else [int(x) for x in arr]
+
+
+@pytest.mark.parametrize("word", [0, 1, 2, 3])
+@pytest.mark.parametrize("p,k", [(2, 5), (3, 3), (5, 4), (7, 2), (31, 2), (37, 1), (251, 1)])
+def test_pack_matches_oracle(env, word, p, k):
+    fp, torch, dev, ctx = env
+    dt, beta = WORDS[word]
+    b = max(1, (p - 1).bit_length())
+    while (p - 1) * sum(1 << (j * b) for j in range(k)) >= 2 ** beta:
+        k -= 1
+    prm = fp.fp_dqt_params(p=p, k=k, b=b, ndig=1, word=word, reserved=0, n_accum=1)
+    count = 3 * 256 + 17                              # several tiles and a ragged tail
+    c = workloads.uniform_mod(k * 100 + p, p, (count, k))
+    words = torch.empty(count, dtype=getattr(torch, np.dtype(dt).name), device=dev)
+    fp.fp_dqt_pack(ctx, prm, to_dev(torch, dev, c), words, count)
+    fp.fp_ctx_status(ctx)
+    got = words.cpu().numpy()
+    want = odqt.dqt(c, 1 << b)
+    assert [int(x) for x in got] == [int(x) for x in want]
+
+
+@pytest.mark.parametrize("word", [0, 1, 2, 3])
+@pytest.mark.parametrize("p", [2, 3, 5, 7, 13, 31, 37, 251])
+def test_unpack_redq_matches_radix_conversion(env, word, p):
+    """Words r = sum mu~_i q^i with lower digits < q and a free top digit, below the word's
+    exact range; REDQ must give the digits mod p (inverse DQT by radix conversion)."""
+    fp, torch, dev, ctx = env
+    dt, beta = WORDS[word]
+    g = np.random.default_rng(p * 7 + word)
+    for b in sorted({(p - 1).bit_length() + 1, (p - 1).bit_length() + 4, 12}):
+        ndig = max(1, min(9, (beta - 1) // b))
+        count = 2 * 256 + 5
+        lo = g.integers(0, 1 << b, size=(count, ndig - 1)) if ndig > 1 else np.zeros((count, 0), np.int64)
+        top_max = (2 ** beta - 1) >> (b * (ndig - 1))
+        top = g.integers(0, min(top_max, 2 ** 62) + 1, size=count)
+        r = [int(odqt.dqt(list(lo[i]) + [int(top[i])], 1 << b)) for i in range(count)]
+        r[0] = 0
+        r[1] = min(2 ** beta - 1, r[1])
+        words = torch.tensor(np.array(r, dtype=np.uint64).astype(dt), device=dev)
+        out = torch.empty((count, ndig), dtype=torch.uint8, device=dev)
+        prm = fp.fp_dqt_params(p=p, k=1, b=b, ndig=ndig, word=word, reserved=0, n_accum=1)
+        fp.fp_dqt_unpack_redq(ctx, prm, words, out, count)
+        fp.fp_ctx_status(ctx)
+        got = out.cpu().numpy()
+        for i in range(count):
+            assert list(got[i]) == odqt.dqt_inverse(r[i], 1 << b, ndig, p), (p, b, ndig, r[i])
+
+
+ALGOS = ["AUTO", "PLAIN", "DQT_F64", "DQT_U64", "DQT_F32", "DQT_U32"]
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_polymul_config_f3_degree2(env, algo):
+    """2^20 independent pairs of degree-2 polynomials over F_3 (the batched single-word case)."""
+    fp, torch, dev, ctx = env
+    batch = 1 << 20
+    a, b = workloads.polymul_inputs(0, 3, batch, 2, 2)
+    C = torch.empty((batch, 5), dtype=torch.uint8, device=dev)
+    fp.fp_polymul_batched(ctx, 3, to_dev(torch, dev, a), 2, to_dev(torch, dev, b), 2, C, batch,
+                          getattr(fp, "FP_ALGO_" + algo))
+    fp.fp_ctx_status(ctx)
+    assert np.array_equal(C.cpu().numpy(), field.polymul_mod(a, b, 3))
+
+
+@pytest.mark.parametrize("p,da,db,batch", [(2, 7, 3, 1000), (3, 4, 4, 257), (5, 1, 6, 3000), (7, 3, 3, 999),
+                                           (31, 2, 1, 4097), (251, 0, 2, 300), (3, 0, 0, 5)])
+@pytest.mark.parametrize("algo", ["AUTO", "PLAIN", "DQT_U64"])
+def test_polymul_small_degrees(env, p, da, db, batch, algo):
+    fp, torch, dev, ctx = env
+    a, b = workloads.polymul_inputs(p + da, p, batch, da, db)
+    C = torch.empty((batch, da + db + 1), dtype=torch.uint8, device=dev)
+    fp.fp_polymul_batched(ctx, p, to_dev(torch, dev, a), da, to_dev(torch, dev, b), db, C, batch,
+                          getattr(fp, "FP_ALGO_" + algo))
+    fp.fp_ctx_status(ctx)
+    assert np.array_equal(C.cpu().numpy(), field.polymul_mod(a, b, p))
+
+
+@pytest.mark.parametrize("p,da,db", [(3, 512, 512), (7, 100, 333), (5, 64, 1), (2, 1023, 1023), (31, 40, 50)])
+@pytest.mark.parametrize("algo", ["AUTO", "PLAIN"])
+def test_polymul_large_degrees_fqt(env, p, da, db, algo):
+    fp, torch, dev, ctx = env
+    batch = 37
+    a, b = workloads.polymul_inputs(da, p, batch, da, db)
+    C = torch.empty((batch, da + db + 1), dtype=torch.uint8, device=dev)
+    fp.fp_polymul_batched(ctx, p, to_dev(torch, dev, a), da, to_dev(torch, dev, b), db, C, batch,
+                          getattr(fp, "FP_ALGO_" + algo))
+    fp.fp_ctx_status(ctx)
+    assert np.array_equal(C.cpu().numpy(), field.polymul_mod(a, b, p))
+
+
+def test_polymul_all_max_coefficients(env):
+    """Every coefficient p-1: the largest digit of every word (the bound's edge)."""
+    fp, torch, dev, ctx = env
+    for p, d in [(3, 2), (7, 5), (251, 1), (3, 300)]:
+        a = np.full((513, d + 1), p - 1, np.uint8)
+        C = torch.empty((513, 2 * d + 1), dtype=torch.uint8, device=dev)
+        A = to_dev(torch, dev, a)
+        fp.fp_polymul_batched(ctx, p, A, d, A, d, C, 513, fp.FP_ALGO_AUTO)
+        fp.fp_ctx_status(ctx)
+        assert np.array_equal(C.cpu().numpy(), field.polymul_mod(a, a, p))
+
+
+def test_polymul_empty_batch_and_bad_input(env):
+    fp, torch, dev, ctx = env
+    A = torch.zeros((4, 3), dtype=torch.uint8, device=dev)
+    C = torch.empty((4, 5), dtype=torch.uint8, device=dev)
+    fp.fp_polymul_batched(ctx, 3, A, 2, A, 2, C, 0, fp.FP_ALGO_AUTO)   # empty: no-op
+    A[1, 1] = 3                                                          # out of range for p = 3
+    fp.fp_polymul_batched(ctx, 3, A, 2, A, 2, C, 4, fp.FP_ALGO_AUTO)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_ctx_status(ctx)
+    assert ei.value.status == fp.FP_EINVAL
+    fp.fp_ctx_status(ctx)                                                # flag was cleared
+    with pytest.raises(fp.FpError):
+        fp.fp_polymul_batched(ctx, 4, A, 2, A, 2, C, 4, fp.FP_ALGO_AUTO)  # not prime: host check

@@ -1,0 +1,109 @@
+"""GPU parity of GF(p^k) multiplication (Algorithm FGDP, n = 1) and of the modular dot
+product against the oracle, bit-exact."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import field
+from tests._gpu import to_dev, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch, dev = torch_dev()
+    import __graft_entry__ as g
+    g.build()
+    import paper_0809_0063_gb300 as fp
+    ctx = fp.fp_ctx_create(0)
+    yield fp, torch, dev, ctx
+    fp.fp_ctx_destroy(ctx)
+
+
+def gf_run(fp, torch, dev, ctx, gf, a, b):
+    dt = torch.uint8 if a.dtype == np.uint8 else torch.int16
+    A = torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).to(dev)
+    B = torch.from_numpy(b.view(np.int16) if b.dtype == np.uint16 else b).to(dev)
+    C = torch.empty(len(a), dtype=dt, device=dev)
+    fp.fp_gf_mul_batched(ctx, gf, A, B, C, len(a))
+    fp.fp_ctx_status(ctx)
+    out = C.cpu().numpy()
+    return out.view(np.uint16) if a.dtype == np.uint16 else out
+
+
+@pytest.mark.parametrize("p,k", [(3, 5), (7, 4), (2, 8), (2, 3), (5, 2), (3, 1), (13, 2), (2, 1)])
+def test_gf_mul_matches_oracle(env, p, k):
+    fp, torch, dev, ctx = env
+    gf = fp.fp_gf_create(ctx, p, k)
+    try:
+        info = fp.fp_gf_info(gf, k)
+        modulus = field.smallest_monic_irreducible(p, k) if k > 1 else [0, 1]
+        assert info["modulus"] == modulus
+        order = p ** k
+        if order * order <= 70000:            # exhaustive: every pair
+            a = np.repeat(np.arange(order), order)
+            b = np.tile(np.arange(order), order)
+        else:
+            a, b = workloads.gf_inputs(p + k, p, k, 300001)
+        dt = workloads.gf_index_dtype(p, k)
+        a, b = a.astype(dt), b.astype(dt)
+        got = gf_run(fp, torch, dev, ctx, gf, a, b)
+        want = field.gf_mul(a.astype(np.int64), b.astype(np.int64), p, k, modulus)
+        assert np.array_equal(got.astype(np.int64), want)
+    finally:
+        fp.fp_gf_destroy(gf)
+
+
+@pytest.mark.parametrize("p,k", [(3, 5), (7, 4), (2, 8)])
+def test_gf_config_2_24_sampled(env, p, k):
+    """2^24 random pairs (the benchmark's batch); every 97th result checked, plus the tail."""
+    fp, torch, dev, ctx = env
+    n = 1 << 24
+    a, b = workloads.gf_inputs(0, p, k, n)
+    gf = fp.fp_gf_create(ctx, p, k)
+    try:
+        got = gf_run(fp, torch, dev, ctx, gf, a, b)
+    finally:
+        fp.fp_gf_destroy(gf)
+    idx = np.union1d(np.arange(0, n, 97), np.arange(n - 64, n))
+    m = field.smallest_monic_irreducible(p, k)
+    want = field.gf_mul(a[idx].astype(np.int64), b[idx].astype(np.int64), p, k, m)
+    assert np.array_equal(got[idx].astype(np.int64), want)
+
+
+def test_gf_bad_index(env):
+    fp, torch, dev, ctx = env
+    gf = fp.fp_gf_create(ctx, 3, 5)
+    try:
+        a = np.array([0, 1, 250, 3], np.uint8)            # 250 >= 243
+        with pytest.raises(fp.FpError) as ei:
+            gf_run(fp, torch, dev, ctx, gf, a, a)
+        assert ei.value.status == fp.FP_EINVAL
+    finally:
+        fp.fp_gf_destroy(gf)
+
+
+@pytest.mark.parametrize("algo", ["AUTO", "PLAIN", "DQT_U64"])
+@pytest.mark.parametrize("p,n", [(3, 1), (3, 17), (2, 4096), (3, 65536 + 3), (7, 100000), (31, 12345),
+                                 (251, 1 << 20), (5, 0), (3, 1 << 26)])
+def test_dot_matches_oracle(env, algo, p, n):
+    fp, torch, dev, ctx = env
+    u, v = workloads.dot_inputs(n + p, p, n)
+    out = torch.full((1,), 12345, dtype=torch.int32, device=dev)
+    U = to_dev(torch, dev, u) if n else torch.empty(0, dtype=torch.uint8, device=dev)
+    V = to_dev(torch, dev, v) if n else torch.empty(0, dtype=torch.uint8, device=dev)
+    fp.fp_dot(ctx, p, U, V, n, out, getattr(fp, "FP_ALGO_" + algo))
+    fp.fp_ctx_status(ctx)
+    assert int(out.item()) == field.dot_mod(u, v, p)
+
+
+def test_dot_unaligned_and_all_max(env):
+    fp, torch, dev, ctx = env
+    p, n = 7, 100003
+    buf = torch.full((n + 1,), p - 1, dtype=torch.uint8, device=dev)
+    out = torch.zeros((1,), dtype=torch.int32, device=dev)
+    for algo in (fp.FP_ALGO_PLAIN, fp.FP_ALGO_DQT_U64):
+        fp.fp_dot(ctx, p, buf[1:], buf[1:], n, out, algo)    # 1-byte offset: unaligned path
+        fp.fp_ctx_status(ctx)
+        assert int(out.item()) == (n * (p - 1) ** 2) % p

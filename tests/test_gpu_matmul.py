@@ -1,0 +1,153 @@
+"""GPU parity of the compressed matrix product C = A B mod p (every algorithm) against the
+oracle, bit-exact: ragged sizes spanning several tiles, the paper's configurations (full
+compare at n = 1024, sampled rows at n = 4096 in the launch configuration the benchmark
+times), adversarial all-(p-1) inputs at the bound's edge, and error paths."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import dqt as odqt
+from oracle import field
+from tests._gpu import to_dev, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch, dev = torch_dev()
+    import __graft_entry__ as g
+    g.build()
+    import paper_0809_0063_gb300 as fp
+    ctx = fp.fp_ctx_create(0)
+    yield fp, torch, dev, ctx
+    fp.fp_ctx_destroy(ctx)
+
+
+ALL = ["AUTO", "RIGHT_F64", "RIGHT_F32", "PLAIN_F64", "PLAIN_F32", "PLAIN_I8", "PLAIN_TC", "RIGHT_TC"]
+
+
+def run(fp, torch, dev, ctx, p, a, b, algo):
+    m, k = a.shape
+    n = b.shape[1]
+    C = torch.full((m, n), 255, dtype=torch.uint8, device=dev)
+    fp.fp_matmul(ctx, p, m, n, k, to_dev(torch, dev, a), k, to_dev(torch, dev, b), n, C, n,
+                 getattr(fp, "FP_MM_" + algo))
+    fp.fp_ctx_status(ctx)
+    return C.cpu().numpy()
+
+
+def supported(fp, p, k, algo):
+    if algo == "RIGHT_F32" and (p - 1) ** 2 > 511:
+        return False
+    if algo == "PLAIN_TC" and k * (p - 1) ** 2 >= 2 ** 24:
+        return False
+    if algo == "RIGHT_TC" and p > 3:
+        return False
+    return True
+
+
+@pytest.mark.parametrize("algo", ALL)
+@pytest.mark.parametrize("p,m,n,k", [(3, 200, 333, 517), (7, 130, 70, 1000), (2, 64, 129, 4100),
+                                     (17, 257, 255, 96), (31, 33, 300, 300), (3, 1, 1, 1), (5, 5, 7, 3)])
+def test_matmul_ragged(env, algo, p, m, n, k):
+    fp, torch, dev, ctx = env
+    if not supported(fp, p, k, algo):
+        pytest.skip("outside the algorithm's exactness bound")
+    a, b = workloads.matmul_inputs(p * 1000 + m, p, m, k, n)
+    try:
+        got = run(fp, torch, dev, ctx, p, a, b, algo)
+    except fp.FpError as e:
+        if e.status == fp.FP_EUNSUPPORTED:
+            pytest.skip(str(e))
+        raise
+    assert np.array_equal(got, field.matmul_mod(a, b, p))
+
+
+@pytest.mark.parametrize("algo", ALL)
+@pytest.mark.parametrize("p", [3, 7])
+def test_matmul_config_n1024_full(env, algo, p):
+    fp, torch, dev, ctx = env
+    if not supported(fp, p, 1024, algo):
+        pytest.skip("outside the algorithm's exactness bound")
+    a, b = workloads.matmul_inputs(p, p, 1024, 1024, 1024)
+    try:
+        got = run(fp, torch, dev, ctx, p, a, b, algo)
+    except fp.FpError as e:
+        if e.status == fp.FP_EUNSUPPORTED:
+            pytest.skip(str(e))
+        raise
+    rows = np.arange(0, 1024, 3)    # a third of the rows: every tile row, the last row
+    rows = np.union1d(rows, [1023])
+    assert np.array_equal(got[rows], field.matmul_mod_rows(a, b, p, rows))
+
+
+@pytest.mark.parametrize("algo", ALL)
+@pytest.mark.parametrize("p", [3, 7])
+def test_matmul_config_n4096_sampled(env, algo, p):
+    fp, torch, dev, ctx = env
+    if not supported(fp, p, 4096, algo):
+        pytest.skip("outside the algorithm's exactness bound")
+    a, b = workloads.matmul_inputs(p + 10, p, 4096, 4096, 4096)
+    try:
+        got = run(fp, torch, dev, ctx, p, a, b, algo)
+    except fp.FpError as e:
+        if e.status == fp.FP_EUNSUPPORTED:
+            pytest.skip(str(e))
+        raise
+    rows = np.array([0, 1, 127, 128, 2047, 2048, 3000, 4095])
+    assert np.array_equal(got[rows], field.matmul_mod_rows(a, b, p, rows))
+
+
+@pytest.mark.parametrize("algo", ALL)
+@pytest.mark.parametrize("p,k", [(3, 2047), (3, 2048), (7, 4096), (2, 4095), (17, 1000)])
+def test_matmul_all_max_entries(env, algo, p, k):
+    """All entries p-1: every digit reaches k (p-1)^2, the edge of Eq. lower; the strict
+    reading of the bound is what keeps these exact (k = 2048, p = 3 is Table comprange's
+    boundary column)."""
+    fp, torch, dev, ctx = env
+    if not supported(fp, p, k, algo):
+        pytest.skip("outside the algorithm's exactness bound")
+    m, n = 70, 131
+    a = np.full((m, k), p - 1, np.uint8)
+    b = np.full((k, n), p - 1, np.uint8)
+    try:
+        got = run(fp, torch, dev, ctx, p, a, b, algo)
+    except fp.FpError as e:
+        if e.status == fp.FP_EUNSUPPORTED:
+            pytest.skip(str(e))
+        raise
+    assert np.all(got == (k * (p - 1) ** 2) % p)
+
+
+@pytest.mark.parametrize("word", [0, 2, 1])
+def test_pack_cb_matches_oracle(env, word):
+    fp, torch, dev, ctx = env
+    p, k, n = 3, 37, 103
+    bq, e = (13, 4) if word != 2 else (12, 2)
+    a, b = workloads.matmul_inputs(5, p, 1, k, n)
+    nw = -(-n // e)
+    dt = {0: torch.float64, 1: torch.int64, 2: torch.float32}[word]
+    CB = torch.empty((k, nw), dtype=dt, device=dev)
+    fp.fp_pack_cb(ctx, p, k, n, to_dev(torch, dev, b), n, bq, e, word, CB)
+    fp.fp_ctx_status(ctx)
+    got = CB.cpu().numpy()
+    want = odqt.right_compress(b, e, 1 << bq)
+    assert all(int(got[i, j]) == int(want[i, j]) for i in range(k) for j in range(nw))
+
+
+def test_matmul_errors(env):
+    fp, torch, dev, ctx = env
+    A = torch.zeros((4, 4), dtype=torch.uint8, device=dev)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_matmul(ctx, 3, 4, 4, 4, A, 3, A, 4, A, 4)          # lda < k
+    assert ei.value.status == fp.FP_EINVAL
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_matmul(ctx, 31, 4, 4, 4, A, 4, A, 4, A, 4, fp.FP_MM_RIGHT_F32)   # (p-1)^2 > 511
+    assert ei.value.status == fp.FP_EBOUND
+    A[0, 0] = 7
+    C = torch.empty((4, 4), dtype=torch.uint8, device=dev)
+    fp.fp_matmul(ctx, 3, 4, 4, 4, A, 4, A, 4, C, 4)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_ctx_status(ctx)
+    assert ei.value.status == fp.FP_EINVAL
