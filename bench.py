@@ -1,0 +1,412 @@
+"""Benchmark of the packed F_p hot path on GB300: exact F_p MACs/s of the compressed matrix
+product C = A B mod p (p in {3, 7}, n in {1024, 4096}), packed DQT + REDQ against the plain
+mod-p kernels, with the roofline of the dominant kernel, an end-to-end number through the
+C ABI with host buffers, and the CPU oracle timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--algo NAME]
+
+One step = the four products of the configuration, each one fp_matmul call (pack of B into
+words, word contraction, REDQ unpack into C).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+PROBLEMS = [(3, 1024), (7, 1024), (3, 4096), (7, 4096)]
+WORKLOAD = "compressed matmul C=A*B mod p, square uint8, p in {3,7} x n in {1024,4096}"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+L2_FLUSH_BYTES = 512 << 20
+
+# Peaks (per GPU).  FP32 FFMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (unit counts and
+# maximum clock); FP64: measured bf16 dense peak x the nominal FP64:bf16 ratio 1.25/2250;
+# u8 IMMA via mma.sync has no separate figure: measured bf16 peak x nominal int8:bf16 dense of
+# the legacy path is unknown, so the probe's measured 150.6 TOP/s is used and labelled so.
+FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6792.7), d.get("bf16_tflops", 1928.9), d.get("bf16_tflops_sustained", 1750.5), "measured"
+    except OSError:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def kernel_table(bf16_tf):
+    """name -> (bound, peak TFLOP/s, peak label, algorithmic flops of one launch for (p, n, e))."""
+    fp64 = bf16_tf * 1.25 / 2250.0
+    return {
+        "k_mm_ffma": ("alu", FFMA_PEAK_TFLOPS, "FFMA peak from unit counts and 2.07 GHz",
+                      lambda n, e: 2.0 * n * n * (-(-n // e))),
+        "k_mm_dmma": ("tensor", fp64, "FP64 = measured bf16 x 1.25/2250",
+                      lambda n, e: 2.0 * n * n * (-(-n // e))),
+        "k_mm_imma": ("tensor", 150.6, "u8 mma.sync measured by the pipe probe",
+                      lambda n, e: 2.0 * n * n * n),
+        "k_mm_tc": ("tensor", bf16_tf, "measured bf16 dense",
+                    lambda n, e: 2.0 * n * n * (-(-n // e))),
+    }
+
+
+def kernel_source_hash(name):
+    """Hash of the CUDA file holding `name`, used to invalidate stored ncu traffic."""
+    csrc = os.path.join(ROOT, "paper_0809_0063_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        path = os.path.join(csrc, fn)
+        with open(path, "rb") as f:
+            data = f.read()
+        if (name + "(").encode() in data or (name + "<").encode() in data:
+            return hashlib.sha256(data).hexdigest()[:16]
+    return None
+
+
+def stored_traffic(name, per_launch_units):
+    """DRAM bytes per launch from a committed ncu summary, scaled to this launch's units;
+    None when absent or when the kernel's source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f).get(name)
+    except (OSError, ValueError):
+        return None
+    if not d or d.get("source_hash") != kernel_source_hash(name):
+        return None
+    return d["bytes_per_unit"] * per_launch_units
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(budget_s=12.0, rows_per_chunk=32):
+    """Oracle matmul (numpy int64, single thread) on a bounded sample: row chunks of the same
+    four problems, round robin, until the time budget is spent.  Returns (MAC/s, sample)."""
+    from oracle import field
+    inputs = [(p, n) + workloads.matmul_inputs(100 + p + n, p, n, n, n) for p, n in PROBLEMS]
+    macs = 0
+    rows_done = {(p, n): 0 for p, n in PROBLEMS}
+    t0 = time.perf_counter()
+    i = 0
+    while time.perf_counter() - t0 < budget_s:
+        p, n, a, b = inputs[i % len(inputs)]
+        r0 = (rows_done[(p, n)]) % n
+        rows = np.arange(r0, min(n, r0 + rows_per_chunk))
+        field.matmul_mod_rows(a, b, p, rows)
+        macs += len(rows) * n * n
+        rows_done[(p, n)] += len(rows)
+        i += 1
+    dt = time.perf_counter() - t0
+    sample = ", ".join(f"{v} rows of p={p} n={n}" for (p, n), v in rows_done.items())
+    return macs / dt, sample, dt
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the CPU oracle as it stands, each step a bounded sample of the
+    workload (4 rows of each of the four products)."""
+    if rank != 0:
+        return
+    from oracle import field
+    inputs = [(p, n) + workloads.matmul_inputs(100 + p + n, p, n, n, n) for p, n in PROBLEMS]
+
+    def step(s):
+        macs = 0
+        for p, n, a, b in inputs:
+            rows = np.arange((4 * s) % n, (4 * s) % n + 4)
+            field.matmul_mod_rows(a, b, p, rows)
+            macs += 4 * n * n
+        return macs
+
+    for s in range(args.warmup):
+        step(s)
+    t0 = time.perf_counter()
+    macs = 0
+    for s in range(args.steps):
+        macs += step(args.warmup + s)
+    dt = time.perf_counter() - t0
+    val = macs / dt
+    sample = "per step: 4 rows of each of the four products (p in {3,7} x n in {1024,4096})"
+    print(json.dumps({
+        "impl": "reference", "metric": "exact F_p MACs/s", "value": val, "unit": "F_p MAC/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "algo": "oracle (numpy int64 matmul, % p)"},
+        "cpu_baseline": {"value": val, "unit": "F_p MAC/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "F_p MAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="AUTO")
+    ap.add_argument("--no-compare", action="store_true", help="skip the per-variant comparison block")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_0809_0063_gb300 as fp
+
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    hbm, bf16, bf16s, peak_src = peaks()
+    ktab = kernel_table(bf16)
+    algo = getattr(fp, "FP_MM_" + args.algo)
+    ctx = fp.fp_ctx_create(local)
+
+    # resident inputs (seeded, identical on every rank: replicas)
+    prob = []
+    for p, n in PROBLEMS:
+        a, b = workloads.matmul_inputs(p * 7 + n, p, n, n, n)
+        prob.append(dict(p=p, n=n, a=a, b=b, A=torch.from_numpy(a).to(dev), B=torch.from_numpy(b).to(dev),
+                         C=torch.empty((n, n), dtype=torch.uint8, device=dev)))
+    macs_per_step = sum(n ** 3 for _, n in PROBLEMS)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(al=algo):
+        for q in prob:
+            fp.fp_matmul(ctx, q["p"], q["n"], q["n"], q["n"], q["A"], q["n"], q["B"], q["n"], q["C"], q["n"], al)
+
+    # parity gate on the resident buffers before timing (sampled rows against the oracle)
+    from oracle import field
+    step()
+    fp.fp_ctx_status(ctx)
+    for q in prob:
+        rows = np.array([0, q["n"] // 2 + 1, q["n"] - 1])
+        assert np.array_equal(q["C"][rows].cpu().numpy(), field.matmul_mod_rows(q["a"], q["b"], q["p"], rows)), \
+            f"parity failure p={q['p']} n={q['n']}"
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    l0 = fp.fp_ctx_launches(ctx)
+    fp.fp_ctx_profile(ctx, 2)
+    fp.fp_ctx_profile(ctx, 1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()                   # L2 flushed between steps (outside the events)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    fp.fp_ctx_profile(ctx, 0)
+    fp.fp_ctx_status(ctx)
+    launches = fp.fp_ctx_launches(ctx) - l0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * macs_per_step * args.steps / (total_ms / 1e3)
+
+    # dominant kernel and its roofline from the library's own per-launch events
+    dominant, dom_ms, dom_n = None, 0.0, 0
+    for name in ktab:
+        n_l, ms = fp.fp_ctx_profile_read(ctx, name)
+        if ms > dom_ms:
+            dominant, dom_ms, dom_n = name, ms, n_l
+    roof = None
+    if dominant:
+        bound, peak, peak_label, flops_fn = ktab[dominant]
+        flops = 0.0
+        units = 0
+        for p, n in PROBLEMS:
+            if dominant == "k_mm_ffma":
+                e = 2 if args.algo in ("AUTO", "RIGHT_F32") else 1
+            elif dominant == "k_mm_dmma":
+                e = fp.fp_mm_choose(p, n, fp.FP_MM_RIGHT_F64 if args.algo != "PLAIN_F64" else fp.FP_MM_PLAIN_F64)[1]
+            elif dominant == "k_mm_tc":
+                e = 2 if args.algo == "RIGHT_TC" and p <= 3 else 1
+            else:
+                e = 1
+            flops += flops_fn(n, e)
+            units += n ** 3
+        flops *= args.steps
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        traffic = stored_traffic(dominant, units / len(PROBLEMS))
+        roof = {"bound": bound, "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_label + f" ({peak_src})",
+                "launches": dom_n, "avg_launch_ms": dom_ms / max(1, dom_n)}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    hA = [torch.from_numpy(q["a"]).pin_memory() for q in prob]
+    hB = [torch.from_numpy(q["b"]).pin_memory() for q in prob]
+    hC = [torch.empty((q["n"], q["n"]), dtype=torch.uint8).pin_memory() for q in prob]
+    h2d = sum(q["a"].nbytes + q["b"].nbytes for q in prob)
+    d2h = sum(q["n"] * q["n"] for q in prob)
+
+    def e2e_step():
+        for i, q in enumerate(prob):
+            q["A"].copy_(hA[i], non_blocking=True)
+            q["B"].copy_(hB[i], non_blocking=True)
+            fp.fp_matmul(ctx, q["p"], q["n"], q["n"], q["n"], q["A"], q["n"], q["B"], q["n"], q["C"], q["n"], algo)
+            hC[i].copy_(q["C"], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        e_ms.append(a0.elapsed_time(a1))
+    fp.fp_ctx_status(ctx)
+    for i, q in enumerate(prob):
+        rows = np.array([1, q["n"] - 2])
+        assert np.array_equal(hC[i][rows].numpy(), field.matmul_mod_rows(q["a"], q["b"], q["p"], rows))
+    e2e_val = ws * macs_per_step / (statistics.mean(e_ms) / 1e3)
+
+    # packed vs plain on the same inputs (one timed repetition each, after the headline)
+    compare = None
+    if not args.no_compare and rank == 0:
+        compare = {}
+        for name in ["RIGHT_F32", "PLAIN_F32", "RIGHT_F64", "PLAIN_F64", "PLAIN_I8", "PLAIN_TC", "RIGHT_TC"]:
+            row = {}
+            for q in prob:
+                al = getattr(fp, "FP_MM_" + name)
+                if name == "PLAIN_F64" and q["n"] > 1024:
+                    continue
+                try:
+                    fn = (lambda q=q, al=al: fp.fp_matmul(ctx, q["p"], q["n"], q["n"], q["n"], q["A"], q["n"],
+                                                          q["B"], q["n"], q["C"], q["n"], al))
+                    fn()
+                    torch.cuda.synchronize()
+                    flush.zero_()
+                    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a0.record(stream)
+                    fn()
+                    a1.record(stream)
+                    torch.cuda.synchronize()
+                    fp.fp_ctx_status(ctx)
+                    row[f"p{q['p']}_n{q['n']}"] = q["n"] ** 3 / (a0.elapsed_time(a1) / 1e3)
+                except fp.FpError as ex:
+                    row[f"p{q['p']}_n{q['n']}"] = f"unavailable: {ex.args[0][:60]}"
+            compare[name] = row
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, sample, secs = cpu_oracle_rate()
+        cpu = {"value": rate, "unit": "F_p MAC/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sample} ({secs:.1f} s, numpy int64 matmul + % p, single thread)"}
+
+    dtype = {"AUTO": "f32", "RIGHT_F32": "f32", "PLAIN_F32": "f32", "RIGHT_F64": "f64", "PLAIN_F64": "f64",
+             "PLAIN_I8": "u8", "PLAIN_TC": "bf16", "RIGHT_TC": "f16"}.get(args.algo, "f32")
+    if rank == 0:
+        out = {
+            "metric": "exact F_p MACs/s (packed DQT + REDQ compressed matmul)",
+            "value": value, "unit": "F_p MAC/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "algo": args.algo, "problems": [f"p={p} n={n}" for p, n in PROBLEMS],
+                       "macs_per_step": macs_per_step, "l2": "flushed between steps (512 MiB write)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "F_p MAC/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "compare_same_inputs": compare,
+        }
+        print(json.dumps(out))
+    fp.fp_ctx_destroy(ctx)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

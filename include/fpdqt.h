@@ -108,6 +108,16 @@ fp_status fp_ctx_status(fp_ctx ctx, void* stream);
 /* Thread-local message describing the last error of the calling thread ("" if none). */
 const char* fp_last_error(void);
 
+/* Instrumentation.  fp_ctx_profile(ctx, 1) starts recording a CUDA event pair around every
+ * kernel the library launches on this context (on the launch stream), 0 stops, 2 clears the
+ * records.  fp_ctx_profile_read synchronises those events and returns, for the kernels whose
+ * name starts with `prefix` (NULL or "" = all), the number of recorded launches and their
+ * summed device time in milliseconds.  fp_ctx_launches returns the total number of kernels
+ * the library has launched on this context since creation (recorded or not). */
+fp_status fp_ctx_profile(fp_ctx ctx, int mode);
+fp_status fp_ctx_profile_read(fp_ctx ctx, const char* prefix, uint64_t* launches, double* total_ms);
+fp_status fp_ctx_launches(fp_ctx ctx, uint64_t* count);
+
 /* ---------------------------------------------------------------- planner (host only) */
 
 /* Choose packing parameters for products of two polynomials with k coefficients each,

@@ -52,6 +52,9 @@ _SIGS = {
     "fp_ctx_destroy": (None, [_V]),
     "fp_ctx_status": (_I, [_V, _V]),
     "fp_last_error": (ctypes.c_char_p, []),
+    "fp_ctx_profile": (_I, [_V, _I]),
+    "fp_ctx_profile_read": (_I, [_V, ctypes.c_char_p, ctypes.POINTER(_U64), ctypes.POINTER(ctypes.c_double)]),
+    "fp_ctx_launches": (_I, [_V, ctypes.POINTER(_U64)]),
     "fp_dqt_choose": (_I, [_U32, _U32, _U64, _U32, ctypes.POINTER(fp_dqt_params)]),
     "fp_mm_choose": (_I, [_U32, _U64, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
     "fp_dqt_pack": (_I, [_V, ctypes.POINTER(fp_dqt_params), _V, _V, _SZ, _V]),
@@ -123,6 +126,22 @@ def fp_ctx_status(ctx, stream=None):
 
 def fp_last_error() -> str:
     return lib().fp_last_error().decode()
+
+
+def fp_ctx_profile(ctx, mode: int):
+    _check(lib().fp_ctx_profile(ctx, mode))
+
+
+def fp_ctx_profile_read(ctx, prefix: str = ""):
+    n, ms = _U64(), ctypes.c_double()
+    _check(lib().fp_ctx_profile_read(ctx, prefix.encode(), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+def fp_ctx_launches(ctx) -> int:
+    n = _U64()
+    _check(lib().fp_ctx_launches(ctx, ctypes.byref(n)))
+    return n.value
 
 
 # ------------------------------------------------------------------ planner

@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
             if rc != 0:
                 raise RuntimeError(f"nvcc failed on {os.path.basename(s)}")
     tmp = LIB + ".tmp"
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lcuda"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

@@ -136,9 +136,81 @@ static bool poly_word_fits(uint32_t p, uint32_t k, uint64_t n_accum, uint32_t b,
   return total < lim;
 }
 
+static cudaEvent_t pool_get(fp_ctx ctx) {
+  if (!ctx->pool.empty()) {
+    cudaEvent_t e = ctx->pool.back();
+    ctx->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void launch_begin(fp_ctx ctx, const char* name, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(ctx->pmu);
+  ctx->launches++;
+  if (!ctx->prof) return;
+  fp_ctx_s::Rec r{name, pool_get(ctx), pool_get(ctx)};
+  if (!r.a || !r.b) return;
+  cudaEventRecord(r.a, st);
+  ctx->recs.push_back(r);
+}
+
+void launch_end(fp_ctx ctx, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(ctx->pmu);
+  if (!ctx->prof || ctx->recs.empty()) return;
+  cudaEventRecord(ctx->recs.back().b, st);
+}
+
 }  // namespace fpd
 
 using namespace fpd;
+
+// ------------------------------------------------------------------ instrumentation
+
+extern "C" fp_status fp_ctx_profile(fp_ctx ctx, int mode) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_ctx_profile: ctx is NULL");
+  std::lock_guard<std::mutex> lk(ctx->pmu);
+  if (mode == 2) {
+    for (auto& r : ctx->recs) {
+      cudaEventSynchronize(r.b);
+      ctx->pool.push_back(r.a);
+      ctx->pool.push_back(r.b);
+    }
+    ctx->recs.clear();
+    return FP_OK;
+  }
+  FP_CHECK(mode == 0 || mode == 1, FP_EINVAL, "fp_ctx_profile: mode must be 0, 1 or 2");
+  ctx->prof = mode;
+  return FP_OK;
+}
+
+extern "C" fp_status fp_ctx_profile_read(fp_ctx ctx, const char* prefix, uint64_t* launches, double* total_ms) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_ctx_profile_read: ctx is NULL");
+  std::lock_guard<std::mutex> lk(ctx->pmu);
+  uint64_t n = 0;
+  double ms = 0;
+  size_t pl = prefix ? strlen(prefix) : 0;
+  for (auto& r : ctx->recs) {
+    if (pl && strncmp(r.name, prefix, pl) != 0) continue;
+    FP_CUDA(cudaEventSynchronize(r.b));
+    float t = 0;
+    FP_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    ms += t;
+    ++n;
+  }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  return FP_OK;
+}
+
+extern "C" fp_status fp_ctx_launches(fp_ctx ctx, uint64_t* count) {
+  FP_CHECK(ctx && count, FP_EINVAL, "fp_ctx_launches: null argument");
+  std::lock_guard<std::mutex> lk(ctx->pmu);
+  *count = ctx->launches;
+  return FP_OK;
+}
 
 // ------------------------------------------------------------------ context
 
@@ -172,6 +244,8 @@ extern "C" void fp_ctx_destroy(fp_ctx ctx) {
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->scratch2) cudaFree(ctx->scratch2);
+  for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : ctx->pool) cudaEventDestroy(e);
   delete ctx;
 }
 

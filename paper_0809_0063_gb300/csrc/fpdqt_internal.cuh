@@ -74,10 +74,26 @@ struct fp_ctx_s {
   std::mutex mu;
   // autotuner cache: key -> chosen variant
   std::unordered_map<uint64_t, int> tune;
+  // instrumentation: launch count and optional per-launch event pairs
+  uint64_t launches = 0;
+  int prof = 0;
+  struct Rec { const char* name; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  std::mutex pmu;
 };
 
 namespace fpd {
 fp_status ensure_scratch(fp_ctx ctx, size_t bytes, int which = 0);
+void launch_begin(fp_ctx ctx, const char* name, cudaStream_t st);
+void launch_end(fp_ctx ctx, cudaStream_t st);
+// Launch a kernel through the context's instrumentation (launch count, optional events).
+#define FP_LAUNCH(ctx, name, st, ...)      \
+  do {                                     \
+    fpd::launch_begin((ctx), (name), (st)); \
+    __VA_ARGS__;                           \
+    fpd::launch_end((ctx), (st));          \
+  } while (0)
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 }  // namespace fpd
 

@@ -16,8 +16,6 @@ __global__ void __launch_bounds__(256) k_dot_plain(const uint8_t* __restrict__ u
                                                    uint32_t* err) {
   uint64_t acc = 0;
   uint32_t bad = 0;
-  const uint32_t lim = 0x01010101u * (p - 1);  // per-byte range check via SWAR compare below
-  (void)lim;
   bool aligned = ((((uintptr_t)u) | ((uintptr_t)v)) & 15u) == 0;
   uint64_t nv = aligned ? n / 16 : 0;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nv; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -147,18 +145,18 @@ fp_status launch_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v,
     return FP_EBOUND;
   }
   if (dqt && algo != FP_ALGO_AUTO) {
-    k_dot_dqt<<<grid, 256, 0, st>>>(u, v, n, partial, p, D1, b, F, ctx->d_err);
+    FP_LAUNCH(ctx, "k_dot_dqt", st, k_dot_dqt<<<grid, 256, 0, st>>>(u, v, n, partial, p, D1, b, F, ctx->d_err));
   } else if (algo == FP_ALGO_AUTO && dqt) {
     // both are HBM streams; the packed one issues fewer multiplies per byte only for small p,
     // the plain dp4a stream is the cheaper instruction mix: AUTO takes the packed route
     // (the method) when it packs at least 4 entries per word.
-    if (D1 >= 4) k_dot_dqt<<<grid, 256, 0, st>>>(u, v, n, partial, p, D1, b, F, ctx->d_err);
-    else k_dot_plain<<<grid, 256, 0, st>>>(u, v, n, partial, p, ctx->d_err);
+    if (D1 >= 4) FP_LAUNCH(ctx, "k_dot_dqt", st, k_dot_dqt<<<grid, 256, 0, st>>>(u, v, n, partial, p, D1, b, F, ctx->d_err));
+    else FP_LAUNCH(ctx, "k_dot_plain", st, k_dot_plain<<<grid, 256, 0, st>>>(u, v, n, partial, p, ctx->d_err));
   } else {
-    k_dot_plain<<<grid, 256, 0, st>>>(u, v, n, partial, p, ctx->d_err);
+    FP_LAUNCH(ctx, "k_dot_plain", st, k_dot_plain<<<grid, 256, 0, st>>>(u, v, n, partial, p, ctx->d_err));
   }
   FP_CUDA(cudaGetLastError());
-  k_dot_final<<<1, 1024, 0, st>>>(partial, grid, out, p);
+  FP_LAUNCH(ctx, "k_dot_final", st, k_dot_final<<<1, 1024, 0, st>>>(partial, grid, out, p));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }

@@ -283,7 +283,7 @@ static fp_status pack_t(fp_ctx ctx, const fp_dqt_params& prm, const uint8_t* coe
                         size_t count, cudaStream_t st) {
   size_t smem = TILE * prm.k;
   int grid = grid_for(ctx, (count + TILE - 1) / TILE, 8);
-  k_pack<W><<<grid, TILE, smem, st>>>(coeffs, (W*)words, count, prm.k, prm.b, prm.p, ctx->d_err);
+  FP_LAUNCH(ctx, "k_pack", st, k_pack<W><<<grid, TILE, smem, st>>>(coeffs, (W*)words, count, prm.k, prm.b, prm.p, ctx->d_err));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }
@@ -304,7 +304,7 @@ static fp_status unpack_t(fp_ctx ctx, const fp_dqt_params& prm, const void* word
   RedqParams P = make_redq(prm.p, prm.b, prm.ndig);
   size_t smem = TILE * prm.ndig;
   int grid = grid_for(ctx, (count + TILE - 1) / TILE, 8);
-  k_unpack<W><<<grid, TILE, smem, st>>>((const W*)words, coeffs, count, P);
+  FP_LAUNCH(ctx, "k_unpack", st, k_unpack<W><<<grid, TILE, smem, st>>>((const W*)words, coeffs, count, P));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }
@@ -352,7 +352,7 @@ static fp_status polymul_word_t(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32
   RedqParams P = make_redq(p, bq, kc);
   size_t smem = ((TILE * ka + 15) & ~15u) + ((TILE * kb + 15) & ~15u) + TILE * kc;
   int grid = grid_for(ctx, (batch + TILE - 1) / TILE, 8);
-  k_polymul_word<W><<<grid, TILE, smem, st>>>(A, B, C, batch, ka, kb, P, ctx->d_err);
+  FP_LAUNCH(ctx, "k_polymul_word", st, k_polymul_word<W><<<grid, TILE, smem, st>>>(A, B, C, batch, ka, kb, P, ctx->d_err));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }
@@ -365,10 +365,10 @@ fp_status launch_polymul(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t da, 
     if (kc <= 64) {
       size_t smem = ((TILE * ka + 15) & ~15u) + ((TILE * kb + 15) & ~15u) + TILE * kc;
       int grid = grid_for(ctx, (batch + TILE - 1) / TILE, 8);
-      k_polymul_plain_small<<<grid, TILE, smem, st>>>(A, B, C, batch, ka, kb, p, dv, ctx->d_err);
+      FP_LAUNCH(ctx, "k_polymul_plain_small", st, k_polymul_plain_small<<<grid, TILE, smem, st>>>(A, B, C, batch, ka, kb, p, dv, ctx->d_err));
     } else {
       int grid = grid_for(ctx, batch, 16);
-      k_polymul_plain_big<<<grid, 256, 0, st>>>(A, B, C, batch, ka, kb, p, dv, ctx->d_err);
+      FP_LAUNCH(ctx, "k_polymul_plain_big", st, k_polymul_plain_big<<<grid, 256, 0, st>>>(A, B, C, batch, ka, kb, p, dv, ctx->d_err));
     }
     FP_CUDA(cudaGetLastError());
     return FP_OK;
@@ -425,7 +425,7 @@ fp_status launch_polymul(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t da, 
   FP_CHECK(best_d1 >= 1, FP_EBOUND, "polymul: no FQT block size fits a 64-bit word (p=%u)", p);
   RedqParams P = make_redq(p, best_b, 2 * best_d1 - 1);
   int grid = grid_for(ctx, batch, 16);
-  k_polymul_fqt<<<grid, 256, 0, st>>>(A, B, C, batch, ka, kb, best_d1, P, ctx->d_err);
+  FP_LAUNCH(ctx, "k_polymul_fqt", st, k_polymul_fqt<<<grid, 256, 0, st>>>(A, B, C, batch, ka, kb, best_d1, P, ctx->d_err));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }

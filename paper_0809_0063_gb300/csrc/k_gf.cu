@@ -236,13 +236,13 @@ extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const
   int grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)ctx->num_sms * 4);
   if (g->elem_bytes == 1) {
     FP_CUDA(cudaFuncSetAttribute(k_gf_mul<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_gf_mul<uint8_t><<<grid, 256, smem, st>>>((const uint8_t*)a, (const uint8_t*)b, (uint8_t*)c, count, g->d_word,
-                                               g->d_L, g->d_H, g->order, g->k, g->c, g->fb, g->P, ctx->d_err);
+    FP_LAUNCH(ctx, "k_gf_mul", st, k_gf_mul<uint8_t><<<grid, 256, smem, st>>>((const uint8_t*)a, (const uint8_t*)b, (uint8_t*)c, count, g->d_word,
+                                               g->d_L, g->d_H, g->order, g->k, g->c, g->fb, g->P, ctx->d_err));
   } else {
     FP_CUDA(cudaFuncSetAttribute(k_gf_mul<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_gf_mul<uint16_t><<<grid, 256, smem, st>>>((const uint16_t*)a, (const uint16_t*)b, (uint16_t*)c, count,
+    FP_LAUNCH(ctx, "k_gf_mul", st, k_gf_mul<uint16_t><<<grid, 256, smem, st>>>((const uint16_t*)a, (const uint16_t*)b, (uint16_t*)c, count,
                                                 g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb, g->P,
-                                                ctx->d_err);
+                                                ctx->d_err));
   }
   FP_CUDA(cudaGetLastError());
   return FP_OK;

@@ -409,7 +409,7 @@ static fp_status pack_cb_t(fp_ctx ctx, uint32_t p, int k, int n, const uint8_t* 
   int nw = (n + (int)e - 1) / (int)e;
   uint64_t total = (uint64_t)k * ldcb;
   int grid = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->num_sms * 16);
-  k_pack_cb<W><<<grid, 256, 0, st>>>(B, ldb, CB, ldcb, k, n, nw, e, b, p, ctx->d_err);
+  FP_LAUNCH(ctx, "k_pack_cb", st, k_pack_cb<W><<<grid, 256, 0, st>>>(B, ldb, CB, ldcb, k, n, nw, e, b, p, ctx->d_err));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }
@@ -440,10 +440,10 @@ static fp_status mm_dmma(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
   uint64_t warps_big = (uint64_t)((m + 31) / 32) * ((nw + 31) / 32);
   if (warps_big >= (uint64_t)ctx->num_sms * 8) {
     dim3 grid((nw + 63) / 64, (m + 63) / 64);
-    k_mm_dmma<4, 4><<<grid, 128, 0, st>>>(A, lda, CB, nw, C, ldc, m, n, k, nw, e, P, ctx->d_err);
+    FP_LAUNCH(ctx, "k_mm_dmma", st, k_mm_dmma<4, 4><<<grid, 128, 0, st>>>(A, lda, CB, nw, C, ldc, m, n, k, nw, e, P, ctx->d_err));
   } else {
     dim3 grid((nw + 31) / 32, (m + 31) / 32);
-    k_mm_dmma<2, 2><<<grid, 128, 0, st>>>(A, lda, CB, nw, C, ldc, m, n, k, nw, e, P, ctx->d_err);
+    FP_LAUNCH(ctx, "k_mm_dmma", st, k_mm_dmma<2, 2><<<grid, 128, 0, st>>>(A, lda, CB, nw, C, ldc, m, n, k, nw, e, P, ctx->d_err));
   }
   FP_CUDA(cudaGetLastError());
   return FP_OK;
@@ -478,9 +478,9 @@ static fp_status mm_ffma(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
   FP_CUDA(cudaFuncSetAttribute(k_mm_ffma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FF_DYN_SMEM));
   FP_CUDA(cudaFuncSetAttribute(k_mm_ffma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FF_DYN_SMEM));
   if (E == 2)
-    k_mm_ffma<2><<<grid, 256, FF_DYN_SMEM, st>>>(A, lda, CB, ldcb, C, ldc, m, n, k, nw, chunk_tiles, Pr, ctx->d_err);
+    FP_LAUNCH(ctx, "k_mm_ffma", st, k_mm_ffma<2><<<grid, 256, FF_DYN_SMEM, st>>>(A, lda, CB, ldcb, C, ldc, m, n, k, nw, chunk_tiles, Pr, ctx->d_err));
   else
-    k_mm_ffma<1><<<grid, 256, FF_DYN_SMEM, st>>>(A, lda, CB, ldcb, C, ldc, m, n, k, nw, chunk_tiles, Pr, ctx->d_err);
+    FP_LAUNCH(ctx, "k_mm_ffma", st, k_mm_ffma<1><<<grid, 256, FF_DYN_SMEM, st>>>(A, lda, CB, ldcb, C, ldc, m, n, k, nw, chunk_tiles, Pr, ctx->d_err));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }
@@ -496,11 +496,11 @@ static fp_status mm_imma(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
   uint8_t* A2 = (uint8_t*)ctx->scratch;
   uint8_t* Bt = A2 + abytes;
   dim3 ga((kp + 31) / 32, (m + 31) / 32);
-  k_copy_pad<<<ga, 256, 0, st>>>(A, lda, A2, m, k, kp, 0, p, ctx->d_err);
+  FP_LAUNCH(ctx, "k_copy_pad", st, k_copy_pad<<<ga, 256, 0, st>>>(A, lda, A2, m, k, kp, 0, p, ctx->d_err));
   dim3 gb((kp + 31) / 32, (n + 31) / 32);
-  k_copy_pad<<<gb, 256, 0, st>>>(B, ldb, Bt, n, k, kp, 1, p, ctx->d_err);
+  FP_LAUNCH(ctx, "k_copy_pad", st, k_copy_pad<<<gb, 256, 0, st>>>(B, ldb, Bt, n, k, kp, 1, p, ctx->d_err));
   dim3 grid((n + IM_BN - 1) / IM_BN, (m + IM_BM - 1) / IM_BM);
-  k_mm_imma<<<grid, 256, 0, st>>>(A2, Bt, kp, C, ldc, m, n, p, make_divp(p));
+  FP_LAUNCH(ctx, "k_mm_imma", st, k_mm_imma<<<grid, 256, 0, st>>>(A2, Bt, kp, C, ldc, m, n, p, make_divp(p)));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }

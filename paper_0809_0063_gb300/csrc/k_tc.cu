@@ -1,10 +1,453 @@
-// tcgen05 (5th-generation tensor core) matrix products: placeholder until the kernels land.
+// Matrix products mod p on the 5th-generation tensor cores (tcgen05, TMEM accumulators, TMA).
+//
+//  PLAIN_TC  C = A B mod p with A, B converted to bf16 (entries < p <= 256 are exact), one
+//            tcgen05.mma kind::f16 contraction with fp32 accumulation in TMEM (exact while the
+//            integer sums stay below 2^24, i.e. k (p-1)^2 < 2^24), then mod p in the epilogue.
+//  RIGHT_TC  right compression (Sec. 7.4) on the tensor cores: B's columns are packed two per
+//            fp16 operand at Q = 2^10 with centred residues (p <= 3: {-1, 0, 1}), so one MMA
+//            column carries two residues of C.  Each chunk of 448 inner-dimension steps keeps
+//            every digit in (-512, 512) (Eq. lower per chunk, centred); its TMEM accumulator is
+//            drained by the epilogue warps into a 32-bit word R = D0 + 2^16 D1 while the MMA
+//            warp fills the other TMEM buffer (delayed reduction, Sec. 2.2).  At the end an
+//            offset makes both digits non-negative and REDQ_2 (Algorithm 2) recovers them mod p.
+//
+// Kernel roles (one CTA = one 128 x 256 output tile of words, 1 CTA per SM):
+//   warp 0       TMA producer: A tile 128 x 64 and B tile 256 x 64 (bf16/fp16, 128-byte
+//                swizzle) per stage into a 4-stage shared-memory ring (mbarrier full/empty),
+//   warp 1       TMEM allocation and the single MMA-issuing thread,
+//   warps 2..9   epilogue: tcgen05.ld of the accumulator, decode / mod p, stores to C.
+// Every mbarrier wait is bounded; a wait that gives up sets the context's error flag
+// (ERR_TIMEOUT), lets the other roles drain, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "fpdqt_internal.cuh"
 
 namespace fpd {
-fp_status launch_mm_tc(fp_ctx, uint32_t, int, int, int, const uint8_t*, int, const uint8_t*, int, uint8_t*, int,
-                       int algo, cudaStream_t) {
-  set_error("fp_matmul: tcgen05 algorithm %d not built", algo);
-  return FP_EUNSUPPORTED;
+
+static constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64, TC_STAGES = 4;
+static constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;            // 16 KB
+static constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;            // 32 KB
+static constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;  // 48 KB
+static constexpr int TC_THREADS = 320;                          // 10 warps
+static constexpr int TC_CHUNK_KT = 7;                           // 448 inner steps per packed chunk
+static constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;             // try_wait polls before giving up
+static constexpr uint32_t TC_DRAIN_LIMIT = 1u << 20;            // polls for own in-flight work
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
 }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false (and the abort flag set) if the phase did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag) {
+  for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 1023u) == 1023u && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+// Drain wait: bounded, does not give up early on the abort flag (own copies / MMAs in flight).
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < TC_DRAIN_LIMIT; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          su32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major tile with 128-byte swizzle: 8-row core
+// groups 1024 bytes apart (stride byte offset), descriptor version 1, layout SWIZZLE_128B.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
+  uint64_t a = (su32(p) & 0x3FFFFu) >> 4;
+  uint64_t d = a;
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: fp32 accumulate, A/B type (0 f16, 1 bf16), both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_type, int M, int N) {
+  return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- operand conversion
+
+// dst[r][c] (rows x kp, 16-bit, zero padded) from src (u8).  trans: dst[r][c] = src[c][r].
+// mode 0: bf16 of the residue; mode 1: fp16 of the centred residue (p <= 3);
+// mode 2: fp16 of the two centred residues src[c][2r] + 2^10 src[c][2r+1] (trans only, the
+//         right-compressed B; column 2r+1 beyond n counts as 0).
+__global__ void k_tc_convert(const uint8_t* __restrict__ src, int lds, uint16_t* __restrict__ dst, int rows, int cols,
+                             int src_cols, int kp, int trans, int mode, uint32_t p, uint32_t* err) {
+  __shared__ uint16_t tile[32][33];
+  uint32_t bad = 0;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  auto centred = [&](uint32_t v) -> float { return (p == 3 && v == 2) ? -1.0f : (float)v; };
+  for (int yy = ty; yy < 32; yy += 8) {
+    uint16_t out = 0;
+    if (!trans) {
+      int r = r0 + yy, c = c0 + tx;
+      if (r < rows && c < cols) {
+        uint32_t v = src[(size_t)r * lds + c];
+        bad |= v >= p;
+        out = mode == 0 ? __bfloat16_as_ushort(__float2bfloat16_rn((float)v)) : __half_as_ushort(__float2half_rn(centred(v)));
+      }
+      tile[yy][tx] = out;
+    } else {
+      int sr = c0 + yy, dr = r0 + tx;  // source row (inner index of dst), destination row
+      if (sr < cols && dr < rows) {
+        if (mode == 2) {
+          int c = 2 * dr;
+          uint32_t v0 = c < src_cols ? src[(size_t)sr * lds + c] : 0u;
+          uint32_t v1 = c + 1 < src_cols ? src[(size_t)sr * lds + c + 1] : 0u;
+          bad |= (v0 >= p) | (v1 >= p);
+          out = __half_as_ushort(__float2half_rn(centred(v0) + 1024.0f * centred(v1)));
+        } else {
+          uint32_t v = src[(size_t)sr * lds + dr];
+          bad |= v >= p;
+          out = mode == 0 ? __bfloat16_as_ushort(__float2bfloat16_rn((float)v))
+                          : __half_as_ushort(__float2half_rn(centred(v)));
+        }
+      }
+      tile[tx][yy] = out;
+    }
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    int r = r0 + yy, c = c0 + tx;
+    if (r < rows && c < kp) dst[(size_t)r * kp + c] = tile[yy][tx];
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// ---------------------------------------------------------------- the GEMM kernel
+
+template <bool PACKED>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_mm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, uint8_t* __restrict__ C,
+            int ldc, int m, int n, int nw, int ktiles, RedqParams P, uint32_t offset_mod_p, uint32_t koffset,
+            uint32_t* err) {
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + TC_STAGES * TC_STAGE_BYTES);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* tfull = empty + TC_STAGES;   // [2] accumulator ready
+  uint64_t* tempty = tfull + 2;          // [2] accumulator drained
+  uint64_t* drainb = tempty + 2;         // MMA completion on the abort path
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drainb + 1);
+  volatile uint32_t* abort_flag = tmem_slot + 1;
+  __shared__ uint8_t ptab[1024];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+  constexpr uint32_t TMEM_COLS = PACKED ? 512 : 256;
+  const int nchunks = PACKED ? (ktiles + TC_CHUNK_KT - 1) / TC_CHUNK_KT : 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 8);      // one arrival per epilogue warp
+    }
+    mbar_init(drainb, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fill_pair_table(ptab, P);
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int armed = 0;
+      for (int kt = 0; kt < ktiles && !*abort_flag; ++kt) {
+        const int s = kt % TC_STAGES;
+        const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+        uint8_t* sa = smem + s * TC_STAGE_BYTES;
+        uint8_t* sb = sa + TC_A_BYTES;
+        mbar_expect_tx(&full[s], TC_STAGE_BYTES);
+        tma_load_2d(sa, &tmA, kt * TC_BK, m0, &full[s]);
+        tma_load_2d(sb, &tmB, kt * TC_BK, n0, &full[s]);
+        armed = kt + 1;
+      }
+      // every armed stage must have landed before the CTA may exit (its shared memory is reused)
+      for (int kt = (armed > TC_STAGES ? armed - TC_STAGES : 0); kt < armed; ++kt)
+        mbar_drain(&full[kt % TC_STAGES], (uint32_t)(kt / TC_STAGES) & 1u);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16(PACKED ? 0u : 1u, TC_BM, TC_BN);
+      int kt = 0;
+      for (int c = 0; c < nchunks && !*abort_flag; ++c) {
+        const int buf = c & 1;
+        const uint32_t dtm = tmem + (uint32_t)(buf * 256);
+        if (c >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((c - 2) >> 1) & 1u, abort_flag)) break;
+        tc_fence_after();
+        const int kend = PACKED ? min(ktiles, kt + TC_CHUNK_KT) : ktiles;
+        bool first = true;
+        for (; kt < kend; ++kt) {
+          const int s = kt % TC_STAGES;
+          if (!mbar_wait(&full[s], (uint32_t)(kt / TC_STAGES) & 1u, abort_flag)) break;
+          tc_fence_after();
+          const uint8_t* sa = smem + s * TC_STAGE_BYTES;
+          const uint8_t* sb = sa + TC_A_BYTES;
+          const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sb);
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            // advance 16 elements (32 bytes) along K inside the swizzled 128-byte rows
+            mma_f16(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, first ? 0u : 1u);
+            first = false;
+          }
+          mma_commit(&empty[s]);    // stage s free once these MMAs have read it
+        }
+        mma_commit(&tfull[buf]);    // accumulator buffer ready once all MMAs completed
+      }
+      if (*abort_flag) {            // wait for every MMA issued so far before TMEM is freed
+        mma_commit(drainb);
+        mbar_drain(drainb, 0);
+      }
+    }
+  } else {
+    // ------------------------------------------------ epilogue (warps 2..9)
+    Corrector corr;
+    corr.init(P, ptab);
+    const int q = warp & 3;                      // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;            // column half (0: 0..127, 1: 128..255)
+    const int row = m0 + q * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    if (!PACKED) {
+      bool ok = mbar_wait(&tfull[0], 0, abort_flag);
+      tc_fence_after();
+      for (int cb = 0; cb < 4 && ok; ++cb) {
+        const int col0 = half * 128 + cb * 32;
+        uint32_t v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)col0, v);
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          uint32_t w = 0;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            uint32_t x = __float2uint_rn(__uint_as_float(v[j + t]));
+            w |= modp32(x, P.dv, P.p) << (8 * t);
+          }
+          packed[j >> 2] = w;
+        }
+        const int c0 = n0 + col0;
+        if (row < m) {
+          uint8_t* dst = C + (size_t)row * ldc + c0;
+          if (c0 + 32 <= n && ((((uintptr_t)dst) & 15u) == 0)) {
+            reinterpret_cast<uint4*>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            reinterpret_cast<uint4*>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+          } else {
+            for (int j = 0; j < 32 && c0 + j < n; ++j) dst[j] = (uint8_t)(packed[j >> 2] >> (8 * (j & 3)));
+          }
+        }
+      }
+      tc_fence_before();
+    } else {
+      // R = D0 + 2^16 D1 per word of this thread's 128 columns, accumulated over the chunks
+      int32_t R[128];
+#pragma unroll
+      for (int j = 0; j < 128; ++j) R[j] = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        if (ok) ok = mbar_wait(&tfull[buf], (uint32_t)(c >> 1) & 1u, abort_flag);
+        tc_fence_after();
+        if (ok) {
+#pragma unroll
+          for (int cb = 0; cb < 4; ++cb) {
+            uint32_t v[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)(buf * 256 + half * 128 + cb * 32), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              // chunk word v = d0 + 2^10 d1 with |d0|, |d1| <= 448: d1 = round(v / 2^10)
+              const int32_t x = __float2int_rn(__uint_as_float(v[j]));
+              const int32_t d1 = (x + 512) >> 10;
+              R[cb * 32 + j] += x + d1 * (65536 - 1024);
+            }
+          }
+        }
+        tc_fence_before();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+      }
+      // offset both digits by koffset (>= every |digit|) so the word is non-negative, then
+      // REDQ_2 with q = 2^16 and remove the offset's residue
+      const int cw0 = n0 + half * 128;
+#pragma unroll 1
+      for (int j = 0; j < 128; ++j) {
+        const uint32_t w = (uint32_t)R[j] + koffset * 65537u;
+        const int colw = cw0 + j;
+        const bool own = ok && row < m && colw < nw;
+        uint8_t* dst = C + (size_t)(own ? row : 0) * ldc;
+        redq_word<uint32_t>(w, P, corr, [&](uint32_t t, uint32_t mu) {
+          const int cc = 2 * colw + (int)t;
+          uint32_t r = mu + P.p - offset_mod_p;
+          r = r >= P.p ? r - P.p : r;
+          if (own && cc < n) dst[cc] = (uint8_t)r;
+        });
+      }
+    }
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) flag_error(err, ERR_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 2-D map of a rows x kp 16-bit row-major matrix, box = box_rows x 64 elements, 128B swizzle.
+static fp_status make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t kp, uint32_t box_rows) {
+  EncodeTiledFn enc = get_encode();
+  FP_CHECK(enc != nullptr, FP_ECUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[2] = {kp, rows};
+  cuuint64_t strides[1] = {kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  FP_CHECK(r == CUDA_SUCCESS, FP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return FP_OK;
+}
+
+fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda, const uint8_t* B,
+                       int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st) {
+  const bool packed = algo == FP_MM_RIGHT_TC;
+  uint64_t pp = (uint64_t)(p - 1) * (p - 1);
+  if (packed) {
+    FP_CHECK(p <= 3, FP_EBOUND, "RIGHT_TC needs p <= 3 (p=%u)", p);
+    FP_CHECK(k <= 32767, FP_EBOUND, "RIGHT_TC needs k <= 32767");
+  } else {
+    FP_CHECK((uint64_t)k * pp < (1ull << 24), FP_EBOUND, "PLAIN_TC needs k (p-1)^2 < 2^24");
+  }
+  const int kp = (k + TC_BK - 1) / TC_BK * TC_BK;
+  const int nw = packed ? (n + 1) / 2 : n;
+  const size_t abytes = (size_t)m * kp * 2, bbytes = (size_t)nw * kp * 2;
+  fp_status s = ensure_scratch(ctx, abytes + bbytes + 1024);
+  if (s != FP_OK) return s;
+  uint16_t* A16 = (uint16_t*)ctx->scratch;
+  uint16_t* B16 = (uint16_t*)((uint8_t*)ctx->scratch + ((abytes + 1023) & ~(size_t)1023));
+  dim3 ga((kp + 31) / 32, (m + 31) / 32);
+  FP_LAUNCH(ctx, "k_tc_convert", st,
+            k_tc_convert<<<ga, 256, 0, st>>>(A, lda, A16, m, k, k, kp, 0, packed ? 1 : 0, p, ctx->d_err));
+  dim3 gb((kp + 31) / 32, (nw + 31) / 32);
+  FP_LAUNCH(ctx, "k_tc_convert", st,
+            k_tc_convert<<<gb, 256, 0, st>>>(B, ldb, B16, nw, k, n, kp, 1, packed ? 2 : 0, p, ctx->d_err));
+  FP_CUDA(cudaGetLastError());
+  CUtensorMap ma, mb;
+  s = make_map(&ma, A16, (uint64_t)m, (uint64_t)kp, TC_BM);
+  if (s != FP_OK) return s;
+  s = make_map(&mb, B16, (uint64_t)nw, (uint64_t)kp, TC_BN);
+  if (s != FP_OK) return s;
+  const size_t smem = 1024 + TC_STAGES * TC_STAGE_BYTES + 256;
+  dim3 grid((nw + TC_BN - 1) / TC_BN, (m + TC_BM - 1) / TC_BM);
+  const int ktiles = kp / TC_BK;
+  if (packed) {
+    RedqParams P = make_redq(p, 16, 2);
+    uint32_t koff = (uint32_t)k;
+    FP_CUDA(cudaFuncSetAttribute(k_mm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FP_LAUNCH(ctx, "k_mm_tc", st,
+              k_mm_tc<true><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, m, n, nw, ktiles, P, koff % p, koff,
+                                                             ctx->d_err));
+  } else {
+    RedqParams P = make_redq(p, 16, 1);
+    FP_CUDA(cudaFuncSetAttribute(k_mm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FP_LAUNCH(ctx, "k_mm_tc", st,
+              k_mm_tc<false><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, m, n, nw, ktiles, P, 0, 0, ctx->d_err));
+  }
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
 }  // namespace fpd
