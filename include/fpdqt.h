@@ -178,6 +178,22 @@ fp_status fp_polymul_batched(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t 
 fp_status fp_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v, size_t n,
                  uint32_t* out, int algo, void* stream);
 
+/* Allocation-free variant of fp_dot (the paper has no counterpart: this is an interface for
+ * callers that cannot allocate device memory, e.g. code running under an allocator owned by
+ * someone else, or a real-time path where cudaMalloc's implicit synchronisation and failure
+ * modes are not allowed).  It needs no context and calls no cudaMalloc / cudaFree.  Its
+ * scratch (per-block partial sums plus one error word, FP_DOT_NOALLOC_MAX_PARTIALS slots) is a
+ * fixed array in the library's device image, present on every GPU that loads the library
+ * until the process exits.  The first call on each device looks up that array's device
+ * address (with the device current); make that first call before any stream capture.
+ * All calls on a device share the array: calls whose work overlaps on the GPU (different
+ * streams without ordering) race and may return wrong results.  *out = (sum u_i v_i) mod p,
+ * or 0xFFFFFFFF if an input residue was outside [0, p-1].  n <= 2^40 (FP_EINVAL beyond);
+ * FP_EUNSUPPORTED if the device would need more partial slots than the array holds. */
+#define FP_DOT_NOALLOC_MAX_PARTIALS 4096
+fp_status fp_dot_noalloc(uint32_t p, const uint8_t* u, const uint8_t* v, size_t n, uint32_t* out,
+                         int algo, void* stream);
+
 /* ---------------------------------------------------------------- matrix product */
 
 /* C = A * B mod p (Sec. 7).  A: device uint8 m x k (leading dimension lda >= k), B: k x n

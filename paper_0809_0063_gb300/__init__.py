@@ -61,6 +61,7 @@ _SIGS = {
     "fp_dqt_unpack_redq": (_I, [_V, ctypes.POINTER(fp_dqt_params), _V, _V, _SZ, _V]),
     "fp_polymul_batched": (_I, [_V, _U32, _V, _U32, _V, _U32, _V, _SZ, _I, _V]),
     "fp_dot": (_I, [_V, _U32, _V, _V, _SZ, _V, _I, _V]),
+    "fp_dot_noalloc": (_I, [_U32, _V, _V, _SZ, _V, _I, _V]),
     "fp_matmul": (_I, [_V, _U32, _I, _I, _I, _V, _I, _V, _I, _V, _I, _I, _V]),
     "fp_pack_cb": (_I, [_V, _U32, _I, _I, _V, _I, _U32, _U32, _U32, _V, _V]),
     "fp_gf_create": (_I, [_V, _U32, _U32, ctypes.POINTER(_V)]),
@@ -175,6 +176,12 @@ def fp_polymul_batched(ctx, p: int, A, dega: int, B, degb: int, C, batch: int, a
 
 def fp_dot(ctx, p: int, u, v, n: int, out, algo: int = FP_ALGO_AUTO, stream=None):
     _check(lib().fp_dot(ctx, p, _ptr(u), _ptr(v), n, _ptr(out), algo, _stream(stream)))
+
+
+def fp_dot_noalloc(p: int, u, v, n: int, out, algo: int = FP_ALGO_AUTO, stream=None):
+    """Allocation-free dot product: no context, scratch in a fixed array of the library's
+    device image (see include/fpdqt.h); *out = 0xFFFFFFFF flags an out-of-range residue."""
+    _check(lib().fp_dot_noalloc(p, _ptr(u), _ptr(v), n, _ptr(out), algo, _stream(stream)))
 
 
 def fp_matmul(ctx, p: int, m: int, n: int, k: int, A, lda: int, B, ldb: int, C, ldc: int,

@@ -161,4 +161,94 @@ fp_status launch_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v,
   return FP_OK;
 }
 
+// ------------------------------------------------------------------ allocation-free variant
+//
+// For callers that cannot allocate device memory.  The scratch is this file-scope array in the
+// device image: FP_DOT_NOALLOC_MAX_PARTIALS 64-bit partial sums followed by one 32-bit error
+// word.  Partials are always written before they are read, so only the error word is cleared
+// at the start of each call.
+
+static __device__ __align__(256) uint64_t g_dot_noalloc_scratch[FP_DOT_NOALLOC_MAX_PARTIALS + 32];
+
+// The name above is a host-side stand-in in host code; the device address is looked up once
+// per device (with that device current) and cached here.
+static constexpr int NOALLOC_MAX_DEVICES = 64;
+static uint64_t* g_dot_noalloc_ptr[NOALLOC_MAX_DEVICES];
+static int g_dot_noalloc_sms[NOALLOC_MAX_DEVICES];
+static std::mutex g_dot_noalloc_mu;
+
+static fp_status dot_noalloc_setup(int dev, uint64_t** ptr, int* sms) {
+  std::lock_guard<std::mutex> lk(g_dot_noalloc_mu);
+  if (!g_dot_noalloc_ptr[dev]) {
+    uint64_t* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&p, g_dot_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(fp_dot_noalloc scratch)");
+    int n_sms = 0;
+    e = cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    g_dot_noalloc_sms[dev] = n_sms;
+    g_dot_noalloc_ptr[dev] = p;
+  }
+  *ptr = g_dot_noalloc_ptr[dev];
+  *sms = g_dot_noalloc_sms[dev];
+  return FP_OK;
+}
+
+__global__ void k_dot_final_noalloc(const uint64_t* __restrict__ partial, int nparts, uint32_t* out, uint32_t p,
+                                    const uint32_t* err) {
+  uint64_t t = 0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) t += partial[i] % p;
+  for (int o = 16; o; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  __shared__ uint64_t ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+    *out = *err ? 0xFFFFFFFFu : (uint32_t)(s % p);
+  }
+}
+
 }  // namespace fpd
+
+extern "C" fp_status fp_dot_noalloc(uint32_t p, const uint8_t* u, const uint8_t* v, size_t n, uint32_t* out,
+                                    int algo, void* stream) {
+  using namespace fpd;
+  FP_CHECK(p >= 2 && p <= 251 && is_prime(p), FP_EINVAL, "fp_dot_noalloc: p=%u not a prime <= 251", p);
+  FP_CHECK(out != nullptr, FP_EINVAL, "fp_dot_noalloc: out is NULL");
+  FP_CHECK(n <= (1ull << 40), FP_EINVAL, "fp_dot_noalloc: n=%zu above the 2^40 limit", n);
+  FP_CHECK(algo >= FP_ALGO_AUTO && algo <= FP_ALGO_DQT_U32, FP_EINVAL, "fp_dot_noalloc: bad algo %d", algo);
+  FP_CHECK(n == 0 || (u && v), FP_EINVAL, "fp_dot_noalloc: null array");
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  FP_CHECK(dev >= 0 && dev < NOALLOC_MAX_DEVICES, FP_EUNSUPPORTED, "fp_dot_noalloc: device %d", dev);
+  uint64_t* scratch = nullptr;
+  int sms = 0;
+  fp_status s = dot_noalloc_setup(dev, &scratch, &sms);
+  if (s != FP_OK) return s;
+  const int grid = sms * 4;
+  FP_CHECK(grid >= 1 && grid <= FP_DOT_NOALLOC_MAX_PARTIALS, FP_EUNSUPPORTED,
+           "fp_dot_noalloc: %d partial sums needed, the fixed scratch holds %d", grid, FP_DOT_NOALLOC_MAX_PARTIALS);
+  cudaStream_t st = as_stream(stream);
+  if (n == 0) {
+    FP_CUDA(cudaMemsetAsync(out, 0, sizeof(uint32_t), st));
+    return FP_OK;
+  }
+  uint64_t* partial = scratch;
+  uint32_t* err = reinterpret_cast<uint32_t*>(scratch + FP_DOT_NOALLOC_MAX_PARTIALS);
+  FP_CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), st));
+  uint32_t D1 = 0, b = 0, F = 0;
+  bool dqt = algo != FP_ALGO_PLAIN && dot_dqt_params(p, D1, b, F);
+  if (algo != FP_ALGO_PLAIN && algo != FP_ALGO_AUTO && !dqt) {
+    set_error("fp_dot_noalloc: no middle-product packing fits for p=%u", p);
+    return FP_EBOUND;
+  }
+  if (dqt && (algo != FP_ALGO_AUTO || D1 >= 4))
+    k_dot_dqt<<<grid, 256, 0, st>>>(u, v, n, partial, p, D1, b, F, err);
+  else
+    k_dot_plain<<<grid, 256, 0, st>>>(u, v, n, partial, p, err);
+  FP_CUDA(cudaGetLastError());
+  k_dot_final_noalloc<<<1, 1024, 0, st>>>(partial, grid, out, p, err);
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
