@@ -217,8 +217,14 @@ def main():
     ap.add_argument("--algo", default="AUTO")
     ap.add_argument("--no-compare", action="store_true", help="skip the per-variant comparison block")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--problems", default="", help="subset, e.g. 3:4096,7:1024 (default: all four)")
+    ap.add_argument("--min-warmup-s", type=float, default=1.0,
+                    help="keep warming up at least this long (clock sampling under load)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    global PROBLEMS
+    if args.problems:
+        PROBLEMS = [tuple(int(x) for x in t.split(":")) for t in args.problems.split(",")]
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
@@ -263,9 +269,21 @@ def main():
         assert np.array_equal(q["C"][rows].cpu().numpy(), field.matmul_mod_rows(q["a"], q["b"], q["p"], rows)), \
             f"parity failure p={q['p']} n={q['n']}"
 
-    for _ in range(args.warmup):
+    # algorithm actually used per problem (the autotuner's cached choice under AUTO)
+    chosen = {}
+    for q in prob:
+        a = fp.fp_ctx_autotune_choice(ctx, q["p"], q["n"], q["n"], q["n"]) if args.algo == "AUTO" else algo
+        chosen[(q["p"], q["n"])] = a if a >= 0 else algo
+    names = {getattr(fp, k): k[6:] for k in dir(fp) if k.startswith("FP_MM_")}
+    clk = Clocks(local).__enter__()
+    t_w = time.perf_counter()
+    nw_steps = 0
+    while nw_steps < args.warmup or time.perf_counter() - t_w < args.min_warmup_s:   # >= W steps, >= 1 s loaded
         flush.zero_()
         step()
+        nw_steps += 1
+        if nw_steps % 8 == 0:
+            torch.cuda.synchronize()
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -273,13 +291,13 @@ def main():
     fp.fp_ctx_profile(ctx, 2)
     fp.fp_ctx_profile(ctx, 1)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with Clocks(local) as clk:
-        for i in range(args.steps):
-            flush.zero_()                   # L2 flushed between steps (outside the events)
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()                   # L2 flushed between steps (outside the events)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk.__exit__(None, None, None)
     fp.fp_ctx_profile(ctx, 0)
     fp.fp_ctx_status(ctx)
     launches = fp.fp_ctx_launches(ctx) - l0
@@ -302,20 +320,23 @@ def main():
         bound, peak, peak_label, flops_fn = ktab[dominant]
         flops = 0.0
         units = 0
+        kernel_of = {"RIGHT_F32": "k_mm_ffma", "PLAIN_F32": "k_mm_ffma", "RIGHT_F64": "k_mm_dmma",
+                     "PLAIN_F64": "k_mm_dmma", "PLAIN_I8": "k_mm_imma", "PLAIN_TC": "k_mm_tc", "RIGHT_TC": "k_mm_tc"}
         for p, n in PROBLEMS:
-            if dominant == "k_mm_ffma":
-                e = 2 if args.algo in ("AUTO", "RIGHT_F32") else 1
-            elif dominant == "k_mm_dmma":
-                e = fp.fp_mm_choose(p, n, fp.FP_MM_RIGHT_F64 if args.algo != "PLAIN_F64" else fp.FP_MM_PLAIN_F64)[1]
-            elif dominant == "k_mm_tc":
-                e = 2 if args.algo == "RIGHT_TC" and p <= 3 else 1
+            an = names[chosen[(p, n)]]
+            if kernel_of.get(an) != dominant:
+                continue
+            if an == "RIGHT_F64" or an == "PLAIN_F64":
+                e = fp.fp_mm_choose(p, n, getattr(fp, "FP_MM_" + an))[1]
+            elif an in ("RIGHT_F32", "RIGHT_TC"):
+                e = 2
             else:
                 e = 1
             flops += flops_fn(n, e)
             units += n ** 3
         flops *= args.steps
         achieved = flops / (dom_ms / 1e3) / 1e12
-        traffic = stored_traffic(dominant, units / len(PROBLEMS))
+        traffic = stored_traffic(dominant, units / max(1, dom_n / args.steps))
         roof = {"bound": bound, "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_label + f" ({peak_src})",
                 "launches": dom_n, "avg_launch_ms": dom_ms / max(1, dom_n)}
@@ -384,15 +405,17 @@ def main():
         cpu = {"value": rate, "unit": "F_p MAC/s", "cores": 1, "kind": "oracle",
                "sample": f"{sample} ({secs:.1f} s, numpy int64 matmul + % p, single thread)"}
 
-    dtype = {"AUTO": "f32", "RIGHT_F32": "f32", "PLAIN_F32": "f32", "RIGHT_F64": "f64", "PLAIN_F64": "f64",
-             "PLAIN_I8": "u8", "PLAIN_TC": "bf16", "RIGHT_TC": "f16"}.get(args.algo, "f32")
+    dt_of = {"RIGHT_F32": "f32", "PLAIN_F32": "f32", "RIGHT_F64": "f64", "PLAIN_F64": "f64",
+             "PLAIN_I8": "u8", "PLAIN_TC": "bf16", "RIGHT_TC": "f16"}
+    dtype = "/".join(sorted({dt_of[names[a]] for a in chosen.values()}))
     if rank == 0:
         out = {
             "metric": "exact F_p MACs/s (packed DQT + REDQ compressed matmul)",
             "value": value, "unit": "F_p MAC/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "algo": args.algo, "problems": [f"p={p} n={n}" for p, n in PROBLEMS],
+            "config": {"workload": WORKLOAD, "algo": args.algo,
+                       "problems": {f"p={p} n={n}": names[chosen[(p, n)]] for p, n in PROBLEMS},
                        "macs_per_step": macs_per_step, "l2": "flushed between steps (512 MiB write)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof,

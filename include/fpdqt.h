@@ -118,6 +118,16 @@ fp_status fp_ctx_profile(fp_ctx ctx, int mode);
 fp_status fp_ctx_profile_read(fp_ctx ctx, const char* prefix, uint64_t* launches, double* total_ms);
 fp_status fp_ctx_launches(fp_ctx ctx, uint64_t* count);
 
+/* AUTO-algorithm tuning for fp_matmul.  When enabled (the default), the first FP_MM_AUTO call
+ * for a new (p, size class) times every exact candidate (packed tensor-core, plain
+ * tensor-core, u8 tensor-core, packed FP32) once on the caller's own buffers -- all produce the
+ * same C -- synchronising the stream, and caches the fastest in the context; later calls of
+ * that class use the cached choice without timing.  Do not make that first call inside a
+ * stream capture.  With tuning disabled AUTO uses a fixed rule measured on GB300.
+ * fp_ctx_autotune_choice reports the cached algorithm for (p, m, n, k) or -1. */
+fp_status fp_ctx_autotune(fp_ctx ctx, int enable);
+fp_status fp_ctx_autotune_choice(fp_ctx ctx, uint32_t p, int m, int n, int k, int* algo);
+
 /* ---------------------------------------------------------------- planner (host only) */
 
 /* Choose packing parameters for products of two polynomials with k coefficients each,

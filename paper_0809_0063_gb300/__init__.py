@@ -55,6 +55,8 @@ _SIGS = {
     "fp_ctx_profile": (_I, [_V, _I]),
     "fp_ctx_profile_read": (_I, [_V, ctypes.c_char_p, ctypes.POINTER(_U64), ctypes.POINTER(ctypes.c_double)]),
     "fp_ctx_launches": (_I, [_V, ctypes.POINTER(_U64)]),
+    "fp_ctx_autotune": (_I, [_V, _I]),
+    "fp_ctx_autotune_choice": (_I, [_V, _U32, _I, _I, _I, ctypes.POINTER(_I)]),
     "fp_dqt_choose": (_I, [_U32, _U32, _U64, _U32, ctypes.POINTER(fp_dqt_params)]),
     "fp_mm_choose": (_I, [_U32, _U64, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
     "fp_dqt_pack": (_I, [_V, ctypes.POINTER(fp_dqt_params), _V, _V, _SZ, _V]),
@@ -137,6 +139,16 @@ def fp_ctx_profile_read(ctx, prefix: str = ""):
     n, ms = _U64(), ctypes.c_double()
     _check(lib().fp_ctx_profile_read(ctx, prefix.encode(), ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def fp_ctx_autotune(ctx, enable: int):
+    _check(lib().fp_ctx_autotune(ctx, enable))
+
+
+def fp_ctx_autotune_choice(ctx, p: int, m: int, n: int, k: int) -> int:
+    a = _I()
+    _check(lib().fp_ctx_autotune_choice(ctx, p, m, n, k, ctypes.byref(a)))
+    return a.value
 
 
 def fp_ctx_launches(ctx) -> int:

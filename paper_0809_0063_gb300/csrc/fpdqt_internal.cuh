@@ -74,6 +74,7 @@ struct fp_ctx_s {
   std::mutex mu;
   // autotuner cache: key -> chosen variant
   std::unordered_map<uint64_t, int> tune;
+  int autotune = 1;
   // instrumentation: launch count and optional per-launch event pairs
   uint64_t launches = 0;
   int prof = 0;
@@ -248,6 +249,20 @@ __device__ __forceinline__ void redq_word(W rw, const RedqParams& P, const Corre
       emit(i, u);
     }
   }
+}
+
+// REDQ_2 of a 32-bit word (two residues), unrolled for epilogues that pack results into
+// registers.  Same steps as redq_word; all lanes of the warp must call it together.
+__device__ __forceinline__ void redq2_u32(uint32_t w, const RedqParams& P, const Corrector& C, uint32_t& mu0,
+                                          uint32_t& mu1) {
+  const uint32_t s = divp32(w, P.dv);
+  const uint32_t mask = (P.b >= 32) ? 0xffffffffu : ((1u << P.b) - 1u);
+  const uint32_t u0 = (w - P.p * s) & mask;
+  const uint32_t u1 = ((w >> P.b) - P.p * (s >> P.b)) & mask;
+  mu1 = u1;
+  if (P.mode == CORR_NONE) mu0 = u0;
+  else if (P.mode == CORR_SHFL3) mu0 = __shfl_sync(0xffffffffu, C.lane_val, u0 + P.p * u1) & 0xffu;
+  else mu0 = C.pair(u0, u1, P);
 }
 
 // Fill the shared pair table (mode CORR_SMEM2) cooperatively: T[u0 + p u1] = (u0 + c u1) mod p.

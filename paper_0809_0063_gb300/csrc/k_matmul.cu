@@ -505,15 +505,8 @@ static fp_status mm_imma(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
   return FP_OK;
 }
 
-fp_status launch_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
-                        const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st) {
-  std::lock_guard<std::mutex> lk(ctx->mu);  // scratch is shared by calls on this context
-  if (algo == FP_MM_AUTO) {
-    // fastest packed variant whose bound holds: FP32 words (FFMA pipe) when (p-1)^2 <= 511,
-    // else FP64 words (DMMA)
-    uint32_t b, e, c;
-    algo = mm_choose(p, (uint64_t)k, FP_MM_RIGHT_F32, &b, &e, &c) == FP_OK ? FP_MM_RIGHT_F32 : FP_MM_RIGHT_F64;
-  }
+static fp_status run_algo(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
+                          const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st) {
   switch (algo) {
     case FP_MM_RIGHT_F64: return mm_dmma(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, false, st);
     case FP_MM_PLAIN_F64: return mm_dmma(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, true, st);
@@ -528,4 +521,77 @@ fp_status launch_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8
   }
 }
 
+// Exact candidates for (p, k), fastest first by the fixed rule measured on GB300: packed
+// tensor-core words (p <= 3, large products), plain tensor cores, u8 tensor cores, packed FP32
+// words, packed FP64 words (always valid for k (p-1)^2 < 2^52).
+static int candidates(uint32_t p, int m, int n, int k, int* out) {
+  uint64_t pp = (uint64_t)(p - 1) * (p - 1);
+  int c = 0;
+  bool big = (uint64_t)m * n >= (uint64_t)2048 * 2048;
+  if (p <= 3 && k <= 32767 && big) out[c++] = FP_MM_RIGHT_TC;
+  if ((uint64_t)k * pp < (1ull << 24)) out[c++] = FP_MM_PLAIN_TC;
+  if (p <= 3 && k <= 32767 && !big) out[c++] = FP_MM_RIGHT_TC;
+  if ((uint64_t)k * pp < (1ull << 31)) out[c++] = FP_MM_PLAIN_I8;
+  if (pp <= 511) out[c++] = FP_MM_RIGHT_F32;
+  out[c++] = FP_MM_RIGHT_F64;
+  return c;
+}
+
+static uint64_t tune_key(uint32_t p, int m, int n, int k) {
+  auto lg = [](int x) { uint64_t b = 0; while ((1 << b) < x) ++b; return b; };
+  return ((uint64_t)p << 32) | (lg(m) << 20) | (lg(n) << 10) | lg(k);
+}
+
+fp_status launch_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
+                        const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(ctx->mu);  // scratch is shared by calls on this context
+  if (algo != FP_MM_AUTO) return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, algo, st);
+  int cand[8];
+  const int nc = candidates(p, m, n, k, cand);
+  if (!ctx->autotune || nc == 1) return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, cand[0], st);
+  const uint64_t key = tune_key(p, m, n, k);
+  auto it = ctx->tune.find(key);
+  if (it != ctx->tune.end()) return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, it->second, st);
+  // autotune: time each exact candidate once (all write the same C), keep the fastest;
+  // FP64 words are only timed when nothing faster is valid
+  cudaEvent_t e0, e1;
+  FP_CUDA(cudaEventCreate(&e0));
+  FP_CUDA(cudaEventCreate(&e1));
+  int best = cand[0];
+  float best_ms = 1e30f;
+  for (int i = 0; i < nc; ++i) {
+    if (cand[i] == FP_MM_RIGHT_F64 && i > 0) break;
+    // warm (first-use costs such as scratch growth are not the kernel's)
+    fp_status s = run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, cand[i], st);
+    if (s != FP_OK) continue;
+    cudaEventRecord(e0, st);
+    s = run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, cand[i], st);
+    cudaEventRecord(e1, st);
+    if (s != FP_OK) continue;
+    float ms = 0;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+    if (ms < best_ms) { best_ms = ms; best = cand[i]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tune[key] = best;
+  return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, best, st);
+}
+
 }  // namespace fpd
+
+extern "C" fp_status fp_ctx_autotune(fp_ctx ctx, int enable) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_ctx_autotune: ctx is NULL");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->autotune = enable ? 1 : 0;
+  if (enable == 2) ctx->tune.clear();
+  return FP_OK;
+}
+
+extern "C" fp_status fp_ctx_autotune_choice(fp_ctx ctx, uint32_t p, int m, int n, int k, int* algo) {
+  FP_CHECK(ctx && algo, FP_EINVAL, "fp_ctx_autotune_choice: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->tune.find(fpd::tune_key(p, m, n, k));
+  *algo = it == ctx->tune.end() ? -1 : it->second;
+  return FP_OK;
+}

@@ -18,6 +18,9 @@
 //   warps 2..9   epilogue: tcgen05.ld of the accumulator, decode / mod p, stores to C.
 // Every mbarrier wait is bounded; a wait that gives up sets the context's error flag
 // (ERR_TIMEOUT), lets the other roles drain, frees TMEM and returns.
+#include <algorithm>
+#include <cstring>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -125,52 +128,111 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 16 columns per thread, no wait (the caller waits with tmem_wait before using v).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // ---------------------------------------------------------------- operand conversion
 
-// dst[r][c] (rows x kp, 16-bit, zero padded) from src (u8).  trans: dst[r][c] = src[c][r].
-// mode 0: bf16 of the residue; mode 1: fp16 of the centred residue (p <= 3);
-// mode 2: fp16 of the two centred residues src[c][2r] + 2^10 src[c][2r+1] (trans only, the
-//         right-compressed B; column 2r+1 beyond n counts as 0).
-__global__ void k_tc_convert(const uint8_t* __restrict__ src, int lds, uint16_t* __restrict__ dst, int rows, int cols,
-                             int src_cols, int kp, int trans, int mode, uint32_t p, uint32_t* err) {
-  __shared__ uint16_t tile[32][33];
+__device__ __forceinline__ uint16_t to16(uint32_t v, int mode, uint32_t p) {
+  if (mode == 0) return __bfloat16_as_ushort(__float2bfloat16_rn((float)v));
+  float c = (p == 3 && v == 2) ? -1.0f : (float)v;        // centred residue
+  return __half_as_ushort(__float2half_rn(c));
+}
+
+// A16[r][c] (m x kp, zero padded) = 16-bit form of A[r][c]; one thread per 16 columns.
+// mode 0 bf16, mode 1 fp16 of the centred residue (p <= 3).
+__global__ void __launch_bounds__(256) k_tc_convert_a(const uint8_t* __restrict__ A, int lda, uint16_t* __restrict__ dst,
+                                                      int m, int k, int kp, int mode, uint32_t p, uint32_t* err) {
+  const int chunks = kp >> 4;
   uint32_t bad = 0;
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  auto centred = [&](uint32_t v) -> float { return (p == 3 && v == 2) ? -1.0f : (float)v; };
-  for (int yy = ty; yy < 32; yy += 8) {
-    uint16_t out = 0;
-    if (!trans) {
-      int r = r0 + yy, c = c0 + tx;
-      if (r < rows && c < cols) {
-        uint32_t v = src[(size_t)r * lds + c];
-        bad |= v >= p;
-        out = mode == 0 ? __bfloat16_as_ushort(__float2bfloat16_rn((float)v)) : __half_as_ushort(__float2half_rn(centred(v)));
-      }
-      tile[yy][tx] = out;
+  const bool vec = (((uintptr_t)A) & 15u) == 0 && (lda & 15) == 0;
+  // blocks walk rows, threads walk the 16-column chunks of a row
+  for (int r = blockIdx.x; r < m; r += gridDim.x)
+  for (int ch = threadIdx.x; ch < chunks; ch += blockDim.x) {
+    const int c0 = ch * 16;
+    uint8_t b[16];
+    const uint8_t* src = A + (size_t)r * lda + c0;
+    if (vec && c0 + 16 <= k) {
+      uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
+      memcpy(b, &x, 16);
     } else {
-      int sr = c0 + yy, dr = r0 + tx;  // source row (inner index of dst), destination row
-      if (sr < cols && dr < rows) {
-        if (mode == 2) {
-          int c = 2 * dr;
-          uint32_t v0 = c < src_cols ? src[(size_t)sr * lds + c] : 0u;
-          uint32_t v1 = c + 1 < src_cols ? src[(size_t)sr * lds + c + 1] : 0u;
-          bad |= (v0 >= p) | (v1 >= p);
-          out = __half_as_ushort(__float2half_rn(centred(v0) + 1024.0f * centred(v1)));
-        } else {
-          uint32_t v = src[(size_t)sr * lds + dr];
-          bad |= v >= p;
-          out = mode == 0 ? __bfloat16_as_ushort(__float2bfloat16_rn((float)v))
-                          : __half_as_ushort(__float2half_rn(centred(v)));
-        }
-      }
-      tile[tx][yy] = out;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) b[j] = c0 + j < k ? src[j] : 0;
+    }
+    uint32_t o[8];
+#pragma unroll
+    for (int j = 0; j < 16; j += 2) {
+      bad |= (b[j] >= p) | (b[j + 1] >= p);
+      o[j >> 1] = (uint32_t)to16(b[j], mode, p) | ((uint32_t)to16(b[j + 1], mode, p) << 16);
+    }
+    uint4* d = reinterpret_cast<uint4*>(dst + (size_t)r * kp + c0);
+    d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// B16[w][c] (nw x kp, zero padded) from B (k x n): a 64 x 64 tile of B per block is staged
+// in shared memory and written transposed with 16-byte stores.  mode 0: bf16 of B[c][w]
+// (nw = n); mode 2: fp16 of the centred pair B[c][2w] + 2^10 B[c][2w+1] (nw = ceil(n/2)).
+__global__ void __launch_bounds__(256) k_tc_convert_b(const uint8_t* __restrict__ B, int ldb, uint16_t* __restrict__ dst,
+                                                      int k, int n, int nw, int kp, int mode, uint32_t p, uint32_t* err) {
+  __shared__ uint8_t tile[64][64 + 16];
+  const int c0 = blockIdx.x * 64;                  // k offset
+  const int n0 = blockIdx.y * 64;                  // B column offset
+  const int t = threadIdx.x;
+  uint32_t bad = 0;
+  {
+    const int rr = t >> 2, cc = (t & 3) * 16;      // 64 rows (k) x 4 chunks of 16 columns
+    const int kr = c0 + rr, col = n0 + cc;
+    uint8_t b[16];
+    const uint8_t* src = B + (size_t)kr * ldb + col;
+    if (kr < k && col + 16 <= n && (((uintptr_t)src) & 15u) == 0) {
+      uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
+      memcpy(b, &x, 16);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) b[j] = (kr < k && col + j < n) ? src[j] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      bad |= b[j] >= p;
+      tile[rr][cc + j] = b[j];
     }
   }
   __syncthreads();
-  for (int yy = ty; yy < 32; yy += 8) {
-    int r = r0 + yy, c = c0 + tx;
-    if (r < rows && c < kp) dst[(size_t)r * kp + c] = tile[yy][tx];
+  // output rows: 64 (mode 0) or 32 (mode 2) words, each 64 k-values = 128 bytes = 8 x 16 B
+  const int wrows = mode == 2 ? 32 : 64;
+  const int w0 = mode == 2 ? n0 / 2 : n0;
+  for (int id = t; id < wrows * 8; id += 256) {
+    const int wr = id >> 3, seg = (id & 7) * 8;    // 8 k-values per 16-byte store
+    const int w = w0 + wr;
+    if (w >= nw || c0 + seg >= kp) continue;
+    uint32_t o[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      uint16_t h[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int kk = seg + j + q;
+        if (mode == 2) {
+          uint32_t v0 = tile[kk][2 * wr], v1 = tile[kk][2 * wr + 1];
+          float c = ((p == 3 && v0 == 2) ? -1.0f : (float)v0) + 1024.0f * ((p == 3 && v1 == 2) ? -1.0f : (float)v1);
+          h[q] = __half_as_ushort(__float2half_rn(c));
+        } else {
+          h[q] = to16(tile[kk][wr], 0, p);
+        }
+      }
+      o[j >> 1] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+    }
+    *reinterpret_cast<uint4*>(dst + (size_t)w * kp + c0 + seg) = make_uint4(o[0], o[1], o[2], o[3]);
   }
   if (bad) flag_error(err, ERR_RANGE);
 }
@@ -180,7 +242,7 @@ __global__ void k_tc_convert(const uint8_t* __restrict__ src, int lds, uint16_t*
 template <bool PACKED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_mm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, uint8_t* __restrict__ C,
-            int ldc, int m, int n, int nw, int ktiles, RedqParams P, uint32_t offset_mod_p, uint32_t koffset,
+            int ldc, uint32_t* __restrict__ RW, int m, int n, int nw, int ktiles, RedqParams P, uint32_t koffset,
             uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -189,7 +251,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* tfull = empty + TC_STAGES;   // [2] accumulator ready
   uint64_t* tempty = tfull + 2;          // [2] accumulator drained
   uint64_t* drainb = tempty + 2;         // MMA completion on the abort path
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drainb + 1);
+  uint64_t* doneb = drainb + 1;          // every epilogue warp finished with TMEM
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(doneb + 1);
   volatile uint32_t* abort_flag = tmem_slot + 1;
   __shared__ uint8_t ptab[1024];
 
@@ -208,6 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&tempty[b], 8);      // one arrival per epilogue warp
     }
     mbar_init(drainb, 1);
+    mbar_init(doneb, 8);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -241,6 +305,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int kt = (armed > TC_STAGES ? armed - TC_STAGES : 0); kt < armed; ++kt)
         mbar_drain(&full[kt % TC_STAGES], (uint32_t)(kt / TC_STAGES) & 1u);
     }
+    __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
@@ -275,6 +340,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_drain(drainb, 0);
       }
     }
+    __syncwarp();
   } else {
     // ------------------------------------------------ epilogue (warps 2..9)
     Corrector corr;
@@ -312,10 +378,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
-      tc_fence_before();
     } else {
       // R = D0 + 2^16 D1 per word of this thread's 128 columns, accumulated over the chunks
-      int32_t R[128];
+      uint32_t R[128];   // unsigned: wraps modulo 2^32 (the magic offsets cancel at the end)
 #pragma unroll
       for (int j = 0; j < 128; ++j) R[j] = 0;
       bool ok = true;
@@ -324,45 +389,111 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (ok) ok = mbar_wait(&tfull[buf], (uint32_t)(c >> 1) & 1u, abort_flag);
         tc_fence_after();
         if (ok) {
+          // 8 blocks of 16 columns, loads double-buffered so each block's TMEM latency overlaps
+          // the previous block's arithmetic.  Chunk word v = d0 + 2^10 d1, |d0|, |d1| <= 448:
+          // adding 1.5 2^23 makes the float's bits 0x4B400000 + v exactly (|v| < 2^22), so
+          // y - 0x4B400000 = v without a conversion instruction; d1 = round(v / 2^10).
+          const uint32_t base = tmem + lane_base + (uint32_t)(buf * 256 + half * 128);
+          uint32_t va[16], vb[16];
+          tmem_ld16_nowait(base, va);
+          tmem_wait();
 #pragma unroll
-          for (int cb = 0; cb < 4; ++cb) {
-            uint32_t v[32];
-            tmem_ld32(tmem + lane_base + (uint32_t)(buf * 256 + half * 128 + cb * 32), v);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              // chunk word v = d0 + 2^10 d1 with |d0|, |d1| <= 448: d1 = round(v / 2^10)
-              const int32_t x = __float2int_rn(__uint_as_float(v[j]));
-              const int32_t d1 = (x + 512) >> 10;
-              R[cb * 32 + j] += x + d1 * (65536 - 1024);
+          for (int blk = 0; blk < 8; ++blk) {
+            if (blk + 1 < 8) {
+              if (blk & 1) tmem_ld16_nowait(base + (uint32_t)((blk + 1) * 16), va);
+              else tmem_ld16_nowait(base + (uint32_t)((blk + 1) * 16), vb);
             }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const uint32_t raw = (blk & 1) ? vb[j] : va[j];
+              const int32_t y = __float_as_int(__uint_as_float(raw) + 12582912.0f);
+              const int32_t d1 = (y - (0x4B400000 - 512)) >> 10;
+              R[blk * 16 + j] += (uint32_t)y + (uint32_t)(d1 * (65536 - 1024));
+            }
+            tmem_wait();
           }
         }
         tc_fence_before();
         if (lane == 0) mbar_arrive(&tempty[buf]);
       }
-      // offset both digits by koffset (>= every |digit|) so the word is non-negative, then
-      // REDQ_2 with q = 2^16 and remove the offset's residue
+      // The word CC = D0 + 2^16 D1 of this thread's row and 128 columns goes to global memory
+      // with both digits made non-negative by the offset koffset (>= every |digit|) and the
+      // per-chunk conversion constant removed; a separate pass applies REDQ (Eq. LeftComp:
+      // CC = A x CB, then REDQ(CC)).
+      const uint32_t fix = koffset * 65537u - (uint32_t)nchunks * 0x4B400000u;
       const int cw0 = n0 + half * 128;
-#pragma unroll 1
-      for (int j = 0; j < 128; ++j) {
-        const uint32_t w = (uint32_t)R[j] + koffset * 65537u;
-        const int colw = cw0 + j;
-        const bool own = ok && row < m && colw < nw;
-        uint8_t* dst = C + (size_t)(own ? row : 0) * ldc;
-        redq_word<uint32_t>(w, P, corr, [&](uint32_t t, uint32_t mu) {
-          const int cc = 2 * colw + (int)t;
-          uint32_t r = mu + P.p - offset_mod_p;
-          r = r >= P.p ? r - P.p : r;
-          if (own && cc < n) dst[cc] = (uint8_t)r;
-        });
+      if (ok && row < m) {
+        uint32_t* dst = RW + (size_t)row * nw + cw0;
+        if (cw0 + 128 <= nw && (nw & 3) == 0) {
+#pragma unroll
+          for (int j = 0; j < 128; j += 4)
+            *reinterpret_cast<uint4*>(dst + j) = make_uint4(R[j] + fix, R[j + 1] + fix, R[j + 2] + fix, R[j + 3] + fix);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 128; ++j)
+            if (cw0 + j < nw) dst[j] = R[j] + fix;
+        }
       }
     }
+    __syncwarp();
+    tc_fence_before();
+    if (lane == 0) mbar_arrive(doneb);
   }
   __syncthreads();
   if (*abort_flag && threadIdx.x == 0) flag_error(err, ERR_TIMEOUT);
   if (warp == 1) {
+    // TMEM is freed only after every epilogue warp has signalled that it is done with it
+    if (lane == 0) mbar_drain(doneb, 0);
+    __syncwarp();
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// REDQ_2 of the right-compressed product's words (q = 2^16, digits offset by koffset):
+// C[r][2w + t] = (digit_t(RW[r][w]) - koffset) mod p.  One thread per 8 words (16 residues,
+// one 16-byte store); whole warps iterate so the shuffle-table lookups see 32 lanes.
+__global__ void __launch_bounds__(256) k_tc_redq(const uint32_t* __restrict__ RW, uint8_t* __restrict__ C, int ldc,
+                                                 int m, int n, int nw, RedqParams P, uint32_t offset_mod_p) {
+  __shared__ uint8_t ptab[1024];
+  fill_pair_table(ptab, P);
+  __syncthreads();
+  Corrector corr;
+  corr.init(P, ptab);
+  const int groups = (nw + 7) / 8;
+  const int gblocks = (groups + (int)blockDim.x - 1) / (int)blockDim.x;   // blocks of threads per row
+  for (int rb = blockIdx.x; rb < m * gblocks; rb += gridDim.x) {
+    const int r = rb / gblocks, g = (rb - r * gblocks) * (int)blockDim.x + (int)threadIdx.x;
+    const bool own = g < groups;
+    const uint32_t* src = RW + (size_t)r * nw + g * 8;
+    uint32_t w[8];
+    if (own && g * 8 + 8 <= nw && (nw & 3) == 0) {
+      uint4 a = *reinterpret_cast<const uint4*>(src);
+      uint4 b = *reinterpret_cast<const uint4*>(src + 4);
+      w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[j] = (own && g * 8 + j < nw) ? src[j] : 0u;
+    }
+    uint32_t o[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      uint32_t mu0, mu1;
+      redq2_u32(w[j], P, corr, mu0, mu1);
+      uint32_t r0 = mu0 + P.p - offset_mod_p, r1 = mu1 + P.p - offset_mod_p;
+      r0 = r0 >= P.p ? r0 - P.p : r0;
+      r1 = r1 >= P.p ? r1 - P.p : r1;
+      o[j >> 1] |= (r0 | (r1 << 8)) << (16 * (j & 1));
+    }
+    if (own) {
+      const int c0 = 16 * g;
+      uint8_t* dst = C + (size_t)r * ldc + c0;
+      if (c0 + 16 <= n && ((((uintptr_t)dst) & 15u) == 0)) {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(o[0], o[1], o[2], o[3]);
+      } else {
+        for (int b = 0; b < 16 && c0 + b < n; ++b) dst[b] = (uint8_t)(o[b >> 2] >> (8 * (b & 3)));
+      }
+    }
   }
 }
 
@@ -413,17 +544,21 @@ fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_
   }
   const int kp = (k + TC_BK - 1) / TC_BK * TC_BK;
   const int nw = packed ? (n + 1) / 2 : n;
-  const size_t abytes = (size_t)m * kp * 2, bbytes = (size_t)nw * kp * 2;
-  fp_status s = ensure_scratch(ctx, abytes + bbytes + 1024);
+  const size_t abytes = ((size_t)m * kp * 2 + 1023) & ~(size_t)1023, bbytes = ((size_t)nw * kp * 2 + 1023) & ~(size_t)1023;
+  const size_t wbytes = packed ? (size_t)m * nw * 4 : 0;
+  fp_status s = ensure_scratch(ctx, abytes + bbytes + wbytes + 1024);
   if (s != FP_OK) return s;
   uint16_t* A16 = (uint16_t*)ctx->scratch;
-  uint16_t* B16 = (uint16_t*)((uint8_t*)ctx->scratch + ((abytes + 1023) & ~(size_t)1023));
-  dim3 ga((kp + 31) / 32, (m + 31) / 32);
-  FP_LAUNCH(ctx, "k_tc_convert", st,
-            k_tc_convert<<<ga, 256, 0, st>>>(A, lda, A16, m, k, k, kp, 0, packed ? 1 : 0, p, ctx->d_err));
-  dim3 gb((kp + 31) / 32, (nw + 31) / 32);
-  FP_LAUNCH(ctx, "k_tc_convert", st,
-            k_tc_convert<<<gb, 256, 0, st>>>(B, ldb, B16, nw, k, n, kp, 1, packed ? 2 : 0, p, ctx->d_err));
+  uint16_t* B16 = (uint16_t*)((uint8_t*)ctx->scratch + abytes);
+  uint32_t* RW = (uint32_t*)((uint8_t*)ctx->scratch + abytes + bbytes);
+  {
+    const int g1 = std::min(m, ctx->num_sms * 16);
+    FP_LAUNCH(ctx, "k_tc_convert_a", st,
+              k_tc_convert_a<<<g1, 256, 0, st>>>(A, lda, A16, m, k, kp, packed ? 1 : 0, p, ctx->d_err));
+    dim3 gb(kp / 64, (n + 63) / 64);
+    FP_LAUNCH(ctx, "k_tc_convert_b", st,
+              k_tc_convert_b<<<gb, 256, 0, st>>>(B, ldb, B16, k, n, nw, kp, packed ? 2 : 0, p, ctx->d_err));
+  }
   FP_CUDA(cudaGetLastError());
   CUtensorMap ma, mb;
   s = make_map(&ma, A16, (uint64_t)m, (uint64_t)kp, TC_BM);
@@ -438,13 +573,17 @@ fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_
     uint32_t koff = (uint32_t)k;
     FP_CUDA(cudaFuncSetAttribute(k_mm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FP_LAUNCH(ctx, "k_mm_tc", st,
-              k_mm_tc<true><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, m, n, nw, ktiles, P, koff % p, koff,
+              k_mm_tc<true><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, RW, m, n, nw, ktiles, P, koff,
                                                              ctx->d_err));
+    FP_CUDA(cudaGetLastError());
+    const int gblocks = ((nw + 7) / 8 + 255) / 256;
+    const int gr = (int)std::min<int64_t>((int64_t)m * gblocks, (int64_t)ctx->num_sms * 8);
+    FP_LAUNCH(ctx, "k_tc_redq", st, k_tc_redq<<<gr, 256, 0, st>>>(RW, C, ldc, m, n, nw, P, koff % p));
   } else {
     RedqParams P = make_redq(p, 16, 1);
     FP_CUDA(cudaFuncSetAttribute(k_mm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FP_LAUNCH(ctx, "k_mm_tc", st,
-              k_mm_tc<false><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, m, n, nw, ktiles, P, 0, 0, ctx->d_err));
+              k_mm_tc<false><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, nullptr, m, n, nw, ktiles, P, 0, ctx->d_err));
   }
   FP_CUDA(cudaGetLastError());
   return FP_OK;
