@@ -218,6 +218,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the per-variant comparison block")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--problems", default="", help="subset, e.g. 3:4096,7:1024 (default: all four)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="AUTO uses the fixed rule instead of timing candidates (for runs under a profiler)")
     ap.add_argument("--min-warmup-s", type=float, default=1.0,
                     help="keep warming up at least this long (clock sampling under load)")
     args = ap.parse_args()
@@ -245,6 +247,8 @@ def main():
     ktab = kernel_table(bf16)
     algo = getattr(fp, "FP_MM_" + args.algo)
     ctx = fp.fp_ctx_create(local)
+    if args.no_autotune:
+        fp.fp_ctx_autotune(ctx, 0)
 
     # resident inputs (seeded, identical on every rank: replicas)
     prob = []
@@ -273,6 +277,8 @@ def main():
     chosen = {}
     for q in prob:
         a = fp.fp_ctx_autotune_choice(ctx, q["p"], q["n"], q["n"], q["n"]) if args.algo == "AUTO" else algo
+        if a < 0 and args.algo == "AUTO":       # fixed rule (autotuning off): first exact candidate
+            a = fp.FP_MM_RIGHT_TC if (q["p"] <= 3 and q["n"] >= 2048) else fp.FP_MM_PLAIN_TC
         chosen[(q["p"], q["n"])] = a if a >= 0 else algo
     names = {getattr(fp, k): k[6:] for k in dir(fp) if k.startswith("FP_MM_")}
     clk = Clocks(local).__enter__()
