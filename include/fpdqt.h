@@ -263,6 +263,72 @@ typedef struct {
  * scratch.  Errors: FP_EINVAL, FP_EBOUND, FP_ECUDA. */
 fp_status fp_batch_run(fp_ctx ctx, const fp_instance* instances, size_t count, void* stream);
 
+/* ---------------------------------------------------------------- serving loop */
+
+/* A request for the serving loop.  kind: 0 polymul (a = dega, b = degb, p), 1 dot (a = n, p),
+ * 2 GF(p^k) batch multiply (a = count, gf), 3 matmul (a = m, b = n, c = k, p).  Inputs are
+ * HOST buffers (pinned memory recommended) laid out as for the corresponding call (polymul:
+ * A[dega+1], B[degb+1]; dot: u[n], v[n]; GF: a[count], b[count] element indices; matmul:
+ * A m x k, B k x n, dense); host_out receives the result (polymul dega+degb+1 bytes, dot a
+ * uint32, GF count indices, matmul m x n bytes).  The caller keeps all three buffers alive
+ * until the request is reported done. */
+typedef struct {
+  uint32_t kind;
+  uint32_t p;
+  uint32_t a, b, c;
+  uint32_t reserved;
+  fp_gf gf;
+  const void* host_a;
+  const void* host_b;
+  void* host_out;
+} fp_request;
+
+/* arena_bytes: device memory for the buffers of in-flight requests (admission budget);
+ * streams: CUDA streams whose batches may overlap on the GPU; max_batch: requests per batch;
+ * window_us: while the GPU is busy, how long a forming batch may wait to grow. */
+typedef struct {
+  uint64_t arena_bytes;
+  uint32_t streams;
+  uint32_t max_batch;
+  uint32_t window_us;
+  uint32_t reserved;
+} fp_server_config;
+
+typedef struct {
+  uint64_t submitted, completed, batches, launches, failed;
+} fp_server_stats;
+
+typedef struct fp_server_s* fp_server;
+
+/* Continuous batching (no counterpart in the paper; the systems layer around the packed
+ * kernels): a scheduler thread takes submitted requests in arrival order, admits them as
+ * arena memory frees up, packs every admitted request into one batch (gathered host-to-device
+ * copy, one launch per request kind: varlen blocked-FQT polymul, segmented GF multiply, and
+ * the persistent matmul/dot kernel of fp_batch_run, one device-to-host copy), issues batches
+ * round-robin on its streams so that new batches start while earlier ones run, and records
+ * each request's latency (submission to observed completion, host steady clock).
+ * Errors: FP_EINVAL (bad config), FP_ENOMEM, FP_ECUDA. */
+fp_status fp_server_create(fp_ctx ctx, const fp_server_config* cfg, fp_server* out);
+
+/* Thread-safe.  Validates the request (FP_EINVAL, FP_EBOUND) and queues it; *ticket numbers
+ * requests from 0 in submission order. */
+fp_status fp_server_submit(fp_server s, const fp_request* req, uint64_t* ticket);
+
+/* *done = 1 once the result is in host_out (then *latency_us is set), else 0.  A request
+ * that failed on the device reports done = -1. */
+fp_status fp_server_poll(fp_server s, uint64_t ticket, int* done, double* latency_us);
+
+/* Wait until every submitted request is done or timeout_s passes (FP_ETIMEOUT). */
+fp_status fp_server_drain(fp_server s, double timeout_s);
+
+/* Latencies (microseconds) of tickets [first, first+n) into out (-1 for not done). */
+fp_status fp_server_latencies(fp_server s, uint64_t first, size_t n, double* out);
+
+fp_status fp_server_stats_get(fp_server s, fp_server_stats* out);
+
+/* Stops the scheduler after draining outstanding work (bounded) and frees everything. */
+void fp_server_destroy(fp_server s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,24 @@ class fp_instance(ctypes.Structure):
                 ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p)]
 
 
+class fp_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("p", ctypes.c_uint32), ("a", ctypes.c_uint32), ("b", ctypes.c_uint32),
+                ("c", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("gf", ctypes.c_void_p),
+                ("host_a", ctypes.c_void_p), ("host_b", ctypes.c_void_p), ("host_out", ctypes.c_void_p)]
+
+
+class fp_server_config(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_uint64), ("streams", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
+                ("window_us", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class fp_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("failed", ctypes.c_uint64)]
+
+
+FP_REQ_POLYMUL, FP_REQ_DOT, FP_REQ_GF, FP_REQ_MATMUL = range(4)
+
 _lib = None
 _V, _U32, _U64, _SZ, _I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_int
 _SIGS = {
@@ -71,6 +89,13 @@ _SIGS = {
     "fp_gf_info": (_I, [_V, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
     "fp_gf_mul_batched": (_I, [_V, _V, _V, _V, _V, _SZ, _V]),
     "fp_batch_run": (_I, [_V, ctypes.POINTER(fp_instance), _SZ, _V]),
+    "fp_server_create": (_I, [_V, ctypes.POINTER(fp_server_config), ctypes.POINTER(_V)]),
+    "fp_server_submit": (_I, [_V, ctypes.POINTER(fp_request), ctypes.POINTER(_U64)]),
+    "fp_server_poll": (_I, [_V, _U64, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
+    "fp_server_drain": (_I, [_V, ctypes.c_double]),
+    "fp_server_latencies": (_I, [_V, _U64, _SZ, ctypes.POINTER(ctypes.c_double)]),
+    "fp_server_stats_get": (_I, [_V, ctypes.POINTER(fp_server_stats)]),
+    "fp_server_destroy": (None, [_V]),
 }
 
 
@@ -229,3 +254,44 @@ def fp_gf_mul_batched(ctx, gf, a, b, c, count: int, stream=None):
 def fp_batch_run(ctx, instances, stream=None):
     arr = (fp_instance * len(instances))(*instances)
     _check(lib().fp_batch_run(ctx, arr, len(instances), _stream(stream)))
+
+
+# ------------------------------------------------------------------ serving loop
+
+def fp_server_create(ctx, arena_bytes: int = 1 << 30, streams: int = 4, max_batch: int = 256, window_us: int = 100):
+    cfg = fp_server_config(arena_bytes=arena_bytes, streams=streams, max_batch=max_batch, window_us=window_us, reserved=0)
+    h = _V()
+    _check(lib().fp_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def fp_server_submit(server, req: fp_request) -> int:
+    t = _U64()
+    _check(lib().fp_server_submit(server, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def fp_server_poll(server, ticket: int):
+    d, lat = _I(), ctypes.c_double()
+    _check(lib().fp_server_poll(server, ticket, ctypes.byref(d), ctypes.byref(lat)))
+    return d.value, lat.value
+
+
+def fp_server_drain(server, timeout_s: float = 60.0):
+    _check(lib().fp_server_drain(server, timeout_s))
+
+
+def fp_server_latencies(server, first: int, n: int):
+    out = (ctypes.c_double * n)()
+    _check(lib().fp_server_latencies(server, first, n, out))
+    return list(out)
+
+
+def fp_server_stats_get(server) -> dict:
+    s = fp_server_stats()
+    _check(lib().fp_server_stats_get(server, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in fp_server_stats._fields_}
+
+
+def fp_server_destroy(server):
+    lib().fp_server_destroy(server)

@@ -274,6 +274,65 @@ __device__ __forceinline__ void fill_pair_table(uint8_t* T, const RedqParams& P)
   }
 }
 
+// Blocked FQT (Sec. 5.2): P = sum_i P_i (X^{d+1})^i with each P_i (d+1 coefficients) in one
+// u64 word at q = 2^b; output word t = sum_i P_i Q_{t-i} accumulated in the word (delayed
+// reduction, the planner keeps every digit below q), then REDQ_{2d+1}; the residues of words t
+// and t-1 overlap on d coefficients and are added mod p.  One block per product; the shared
+// buffers wa, wb (1024 words each), res (4160 bytes) and the correction table are the
+// caller's.  All threads of the block must call it.
+__device__ __forceinline__ void fqt_block_product(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
+                                  uint8_t* __restrict__ Cout, uint32_t ka, uint32_t kb, uint32_t d1,
+                                  const RedqParams& P, const Corrector& C, uint64_t* wa, uint64_t* wb,
+                                  uint8_t* res, uint32_t& bad) {
+  const uint32_t na = (ka + d1 - 1) / d1, nb = (kb + d1 - 1) / d1;
+  const uint32_t nw = na + nb - 1;              // output words
+  const uint32_t kc = ka + kb - 1;
+  const uint32_t nd = 2 * d1 - 1;               // residues per output word
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < na; i += blockDim.x) {
+    uint64_t w = 0;
+    for (int j = (int)d1 - 1; j >= 0; --j) {
+      uint32_t idx = i * d1 + j;
+      uint32_t v = idx < ka ? A[idx] : 0u;
+      bad |= v >= P.p;
+      w = (w << P.b) | v;
+    }
+    wa[i] = w;
+  }
+  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
+    uint64_t w = 0;
+    for (int j = (int)d1 - 1; j >= 0; --j) {
+      uint32_t idx = i * d1 + j;
+      uint32_t v = idx < kb ? B[idx] : 0u;
+      bad |= v >= P.p;
+      w = (w << P.b) | v;
+    }
+    wb[i] = w;
+  }
+  __syncthreads();
+  // whole warps iterate so that the shuffle-table lookups see 32 active lanes
+  for (uint32_t base = 0; base < nw; base += blockDim.x) {
+    uint32_t o = base + threadIdx.x;
+    uint64_t acc = 0;
+    if (o < nw) {
+      uint32_t lo = o + 1 > nb ? o + 1 - nb : 0;
+      uint32_t hi = o < na - 1 ? o : na - 1;
+      for (uint32_t i = lo; i <= hi; ++i) acc += wa[i] * wb[o - i];
+    }
+    uint8_t* out = res + (o < nw ? o : 0) * nd;
+    bool own = o < nw;
+    redq_word<uint64_t>(acc, P, C, [&](uint32_t i, uint32_t mu) { if (own) out[i] = (uint8_t)mu; });
+  }
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < kc; j += blockDim.x) {
+    uint32_t o = j / d1, r = j - o * d1;
+    uint32_t v = o < nw ? res[o * nd + r] : 0u;
+    if (o >= 1 && r + d1 < nd) v += res[(o - 1) * nd + r + d1];
+    if (v >= P.p) v -= P.p;
+    Cout[j] = (uint8_t)v;
+  }
+}
+
 // Sticky error reporting from device code.
 __device__ __forceinline__ void flag_error(uint32_t* err, uint32_t bits) {
   if (err) atomicOr(err, bits);
@@ -281,8 +340,31 @@ __device__ __forceinline__ void flag_error(uint32_t* err, uint32_t bits) {
 
 }  // namespace fpd
 
+// ------------------------------------------------------------------ uneven-batch plan records
+namespace fpd {
+// One instance of the persistent uneven-batch kernel (dense row-major operands).
+struct BInst {
+  const uint8_t* A;
+  const uint8_t* B;
+  uint8_t* C;
+  uint32_t kind;     // 0 matmul, 1 dot
+  uint32_t p, m, n, k;
+  uint32_t packed;   // 1: two residues per fp16 operand word
+  uint32_t nw;       // output words per row (n or ceil(n/2))
+  uint32_t plain_chunk_steps;  // k-steps per fold for the plain path
+  RedqParams P;      // REDQ_2 at q = 2^16 (packed) / mod p (plain)
+};
+
+struct BItem {
+  uint32_t inst;
+  uint16_t tm, tn;
+};
+
+}  // namespace fpd
+
 // ------------------------------------------------------------------ launchers (per .cu)
 namespace fpd {
+bool fqt_params(uint32_t p, uint32_t ka, uint32_t kb, uint32_t* d1, uint32_t* b);
 fp_status launch_pack(fp_ctx ctx, const fp_dqt_params& prm, const uint8_t* coeffs, void* words,
                       size_t count, cudaStream_t st);
 fp_status launch_unpack(fp_ctx ctx, const fp_dqt_params& prm, const void* words, uint8_t* coeffs,

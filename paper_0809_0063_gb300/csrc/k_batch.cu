@@ -1,8 +1,442 @@
-// Uneven batches in one persistent launch: placeholder until the work-queue kernel lands.
+// Uneven batches of modular matrix products and dot products in ONE persistent launch.
+//
+// The host planner cuts every matmul instance into 64 x 64 output tiles (64 x 64 packed words
+// when the instance is packed), lists dot instances as single items, sorts the items by
+// their inner dimension (longest first) and uploads the list; persistent CTAs (a multiple of
+// the SM count) take items from an atomic counter until the list is exhausted -- no waiting,
+// so no item can stall another.
+//
+// Each matmul tile runs on the warp-level tensor cores (mma.sync m16n8k16, fp32
+// accumulation).  The u8 residues are converted to 16-bit while they are staged into shared
+// memory (one pass over HBM), so no separate conversion kernel runs:
+//   plain   bf16 residues; every chunk of the inner dimension whose sums could reach 2^24
+//           is folded into a 32-bit integer accumulator (delayed reduction, Sec. 2.2);
+//   packed  (p <= 3) right compression (Sec. 7.4): two centred residues of B per fp16 operand
+//           at Q = 2^10, one MMA column for two columns of C; every 448 inner steps the chunk
+//           word d0 + 2^10 d1 is moved into a 32-bit word D0 + 2^16 D1, and REDQ_2 (Algorithm
+//           2) recovers both residues at the end.
+// The packing degree (1 or 2) per (p, inner-dimension class) is chosen by a measured
+// autotuner cached in the context.
+#include <algorithm>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <vector>
+
 #include "fpdqt_internal.cuh"
 
+namespace fpd {
+
+static constexpr int BT_M = 64, BT_N = 64, BT_K = 32, BT_THREADS = 128;
+static constexpr int BT_CHUNK_STEPS = 14;  // 14 x 32 = 448 inner steps per packed chunk
+
+__device__ __forceinline__ uint32_t bsu32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ int offA(int r, int c) { return r * 64 + ((c ^ ((r >> 1) & 3)) << 4); }
+__device__ __forceinline__ int offB(int kr, int c) { return kr * 128 + ((c ^ (kr & 7)) << 4); }
+
+__device__ __forceinline__ uint16_t h16(float x, bool fp16) {
+  return fp16 ? __half_as_ushort(__float2half_rn(x)) : __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float centred(uint32_t v, uint32_t p) { return (p == 3 && v == 2) ? -1.0f : (float)v; }
+
+// Load 16 consecutive bytes of a row with bounds (zeros outside), vectorised when possible.
+__device__ __forceinline__ void load16(const uint8_t* row, int c0, int limit, uint8_t (&b)[16]) {
+  const uint8_t* src = row + c0;
+  if (c0 + 16 <= limit && ((((uintptr_t)src) & 15u) == 0)) {
+    uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
+    memcpy(b, &x, 16);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) b[j] = (c0 + j < limit) ? src[j] : 0;
+  }
+}
+
+__device__ void run_dot(const BInst& I, uint32_t* err) {
+  __shared__ uint64_t red[BT_THREADS / 32];
+  uint64_t acc = 0;
+  uint32_t bad = 0;
+  for (uint32_t i = threadIdx.x; i < I.k; i += blockDim.x) {
+    uint32_t a = I.A[i], b = I.B[i];
+    bad |= (a >= I.p) | (b >= I.p);
+    acc += a * b;
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < BT_THREADS / 32; ++w) t += red[w];
+    *reinterpret_cast<uint32_t*>(I.C) = (uint32_t)(t % I.p);
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+  __syncthreads();
+}
+
+__device__ void run_tile(const BInst& I, int tm, int tn, uint8_t* smem, uint32_t* err) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int m0 = tm * BT_M, w0 = tn * BT_N;  // first row, first output word
+  const bool packed = I.packed != 0;
+  const uint32_t p = I.p;
+  uint8_t* sA = smem;                 // [2][64 x 32] 16-bit, 4 KB each
+  uint8_t* sB = smem + 2 * 4096;      // [2][32 x 64] 16-bit, 4 KB each
+  __shared__ uint8_t ptab_b[1024];
+  fill_pair_table(ptab_b, I.P);
+  Corrector corr;
+  corr.init(I.P, ptab_b);
+
+  float acc[2][4][4];
+  uint32_t R[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { acc[i][j][q] = 0.f; R[i][j][q] = 0u; }
+
+  const int ksteps = (int)((I.k + BT_K - 1) / BT_K);
+  const int chunk_steps = packed ? BT_CHUNK_STEPS : (int)I.plain_chunk_steps;
+  uint32_t bad = 0;
+  // staging registers
+  uint8_t ra[16], rb[32];
+  const int a_row = tid >> 1, a_h = tid & 1;
+  const int b_kr = tid >> 2, b_q = tid & 3;
+  auto gload = [&](int ks) {
+    const int kb = ks * BT_K;
+    const int r = m0 + a_row;
+    if (r < (int)I.m) load16(I.A + (size_t)r * I.k, kb + 16 * a_h, (int)I.k, ra);
+    else
+#pragma unroll
+      for (int j = 0; j < 16; ++j) ra[j] = 0;
+    const int kr = kb + b_kr;
+    uint8_t t0[16], t1[16];
+    if (kr < (int)I.k) {
+      const uint8_t* brow = I.B + (size_t)kr * I.n;
+      if (packed) {
+        load16(brow, 2 * w0 + 32 * b_q, (int)I.n, t0);
+        load16(brow, 2 * w0 + 32 * b_q + 16, (int)I.n, t1);
+      } else {
+        load16(brow, w0 + 16 * b_q, (int)I.n, t0);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) t1[j] = 0;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) t0[j] = t1[j] = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) { rb[j] = t0[j]; rb[16 + j] = t1[j]; }
+  };
+  auto sstore = [&](int buf) {
+    uint32_t o[8];
+#pragma unroll
+    for (int j = 0; j < 16; j += 2) {
+      bad |= (ra[j] >= p) | (ra[j + 1] >= p);
+      const float x0 = packed ? centred(ra[j], p) : (float)ra[j];
+      const float x1 = packed ? centred(ra[j + 1], p) : (float)ra[j + 1];
+      o[j >> 1] = (uint32_t)h16(x0, packed) | ((uint32_t)h16(x1, packed) << 16);
+    }
+    uint8_t* a = sA + buf * 4096;
+    *reinterpret_cast<uint4*>(a + offA(a_row, 2 * a_h)) = make_uint4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<uint4*>(a + offA(a_row, 2 * a_h + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+    for (int j = 0; j < 16; j += 2) {
+      float x0, x1;
+      if (packed) {
+        bad |= (rb[2 * j] >= p) | (rb[2 * j + 1] >= p) | (rb[2 * j + 2] >= p) | (rb[2 * j + 3] >= p);
+        x0 = centred(rb[2 * j], p) + 1024.0f * centred(rb[2 * j + 1], p);
+        x1 = centred(rb[2 * j + 2], p) + 1024.0f * centred(rb[2 * j + 3], p);
+      } else {
+        bad |= (rb[j] >= p) | (rb[j + 1] >= p);
+        x0 = (float)rb[j];
+        x1 = (float)rb[j + 1];
+      }
+      o[j >> 1] = (uint32_t)h16(x0, packed) | ((uint32_t)h16(x1, packed) << 16);
+    }
+    uint8_t* b = sB + buf * 4096;
+    *reinterpret_cast<uint4*>(b + offB(b_kr, 2 * b_q)) = make_uint4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<uint4*>(b + offB(b_kr, 2 * b_q + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
+  };
+  auto fold = [&]() {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (packed) {
+            const int32_t y = __float_as_int(acc[i][j][q] + 12582912.0f);   // 0x4B400000 + word
+            const int32_t d1 = (y - (0x4B400000 - 512)) >> 10;
+            R[i][j][q] += (uint32_t)(y - 0x4B400000) + (uint32_t)(d1 * (65536 - 1024));
+          } else {
+            R[i][j][q] += __float2uint_rn(acc[i][j][q]);
+          }
+          acc[i][j][q] = 0.f;
+        }
+  };
+
+  __syncthreads();  // previous item finished with the shared buffers
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  int in_chunk = 0;
+  const uint32_t idesc_dummy = 0;
+  (void)idesc_dummy;
+  for (int ks = 0; ks < ksteps; ++ks) {
+    const int buf = ks & 1;
+    if (ks + 1 < ksteps) gload(ks + 1);
+    const uint8_t* a = sA + buf * 4096;
+    const uint8_t* b = sB + buf * 4096;
+#pragma unroll
+    for (int k16 = 0; k16 < 2; ++k16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm * 32 + i * 16 + (lane & 15);
+        const int c = 2 * k16 + (lane >> 4);
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(af[i][0]), "=r"(af[i][1]), "=r"(af[i][2]), "=r"(af[i][3])
+                     : "r"(bsu32(a + offA(r, c))));
+      }
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        const int kr = 16 * k16 + (lane & 7) + (((lane >> 3) & 1) << 3);
+        const int c = 4 * wn + 2 * jj + (lane >> 4);
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(bfr[2 * jj][0]), "=r"(bfr[2 * jj][1]), "=r"(bfr[2 * jj + 1][0]), "=r"(bfr[2 * jj + 1][1])
+                     : "r"(bsu32(b + offB(kr, c))));
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (packed)
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};"
+                : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+                : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]), "r"(bfr[j][1]));
+          else
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};"
+                : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+                : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]), "r"(bfr[j][1]));
+        }
+    }
+    if (++in_chunk == chunk_steps) {
+      fold();
+      in_chunk = 0;
+    }
+    if (ks + 1 < ksteps) sstore(buf ^ 1);
+    __syncthreads();
+  }
+  if (in_chunk) fold();
+  if (bad) flag_error(err, ERR_RANGE);
+  // epilogue: words -> residues (REDQ_2 for packed words, mod p for plain sums)
+  const int g = lane >> 2, t = lane & 3;
+  const uint32_t koff = I.k;                 // offset making centred digit sums non-negative
+  const uint32_t offp = koff % p;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int row = m0 + wm * 32 + i * 16 + g + ((q >> 1) << 3);
+        const int wc = w0 + wn * 32 + j * 8 + 2 * t + (q & 1);
+        const bool own = row < (int)I.m && wc < (int)I.nw;
+        if (packed) {
+          uint32_t mu0, mu1;
+          redq2_u32(R[i][j][q] + koff * 65537u, I.P, corr, mu0, mu1);
+          uint32_t r0 = mu0 + p - offp, r1 = mu1 + p - offp;
+          r0 = r0 >= p ? r0 - p : r0;
+          r1 = r1 >= p ? r1 - p : r1;
+          if (own) {
+            uint8_t* dst = I.C + (size_t)row * I.n + 2 * wc;
+            dst[0] = (uint8_t)r0;
+            if (2 * wc + 1 < (int)I.n) dst[1] = (uint8_t)r1;
+          }
+        } else if (own) {
+          I.C[(size_t)row * I.n + wc] = (uint8_t)modp32(R[i][j][q], I.P.dv, p);
+        }
+      }
+}
+
+__global__ void __launch_bounds__(BT_THREADS) k_batch(const BInst* __restrict__ insts, const BItem* __restrict__ items,
+                                                      uint32_t nitems, uint32_t* counter, uint32_t* err) {
+  __shared__ __align__(128) uint8_t smem[4 * 4096];
+  __shared__ uint32_t s_item;
+  __shared__ BInst s_inst;
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= nitems) break;
+    const BItem item = items[it];
+    if (threadIdx.x == 0) s_inst = insts[item.inst];
+    __syncthreads();
+    const BInst I = s_inst;
+    if (I.kind == 1) run_dot(I, err);
+    else run_tile(I, item.tm, item.tn, smem, err);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- host planning
+
+static uint32_t kclass(uint32_t k) {
+  uint32_t c = 0;
+  while ((1u << c) < k) ++c;
+  return c;
+}
+
+// Packed (two residues per word) or plain for this (p, k class): measured once per class.
+static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st);
+
+fp_status batch_prepare(fp_ctx ctx, const fp_instance* in, size_t count, cudaStream_t st, bool measure_only,
+                        std::vector<BInst>& insts, std::vector<BItem>& items) {
+  insts.assign(count, BInst{});
+  items.clear();
+  items.reserve(count * 4);
+  for (size_t i = 0; i < count; ++i) {
+    const fp_instance& x = in[i];
+    FP_CHECK(x.kind <= 1, FP_EINVAL, "fp_batch_run: instance %zu has kind %u", i, x.kind);
+    FP_CHECK(x.p >= 2 && x.p <= 251 && is_prime(x.p), FP_EINVAL, "fp_batch_run: instance %zu p=%u", i, x.p);
+    FP_CHECK(x.A && x.B && x.C, FP_EINVAL, "fp_batch_run: instance %zu has a null pointer", i);
+    BInst b{};
+    b.A = x.A; b.B = x.B; b.C = x.C; b.kind = x.kind; b.p = x.p;
+    const uint64_t pp = (uint64_t)(x.p - 1) * (x.p - 1);
+    if (x.kind == 1) {
+      FP_CHECK(x.k >= 1, FP_EINVAL, "fp_batch_run: dot instance %zu has length 0", i);
+      b.m = b.n = 1; b.k = x.k;
+      b.P = make_redq(x.p, 16, 1);
+      insts[i] = b;
+      items.push_back(BItem{(uint32_t)i, 0, 0});
+      continue;
+    }
+    FP_CHECK(x.m >= 1 && x.n >= 1 && x.k >= 1 && x.m <= 65535u * BT_M && x.n <= 65535u * BT_N, FP_EINVAL,
+             "fp_batch_run: instance %zu sizes m=%u n=%u k=%u", i, x.m, x.n, x.k);
+    FP_CHECK((uint64_t)x.k * pp < (1ull << 32), FP_EBOUND, "fp_batch_run: instance %zu k (p-1)^2 >= 2^32", i);
+    b.m = x.m; b.n = x.n; b.k = x.k;
+    b.packed = (!measure_only && x.p <= 3 && x.k <= 32767 && choose_packed(ctx, x.p, x.k, st)) ? 1u : 0u;
+    if (measure_only) b.packed = x.reserved ? 1u : 0u;  // the autotuner's probe sets it explicitly
+    b.nw = b.packed ? (x.n + 1) / 2 : x.n;
+    // plain: fold before the fp32 sums can reach 2^24
+    uint64_t steps = pp ? ((1ull << 24) - 1) / (pp * BT_K) : 1u << 20;
+    b.plain_chunk_steps = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(steps, 1u << 20));
+    b.P = b.packed ? make_redq(x.p, 16, 2) : make_redq(x.p, 16, 1);
+    insts[i] = b;
+    const uint32_t tmn = (x.m + BT_M - 1) / BT_M, tnn = (b.nw + BT_N - 1) / BT_N;
+    for (uint32_t tm = 0; tm < tmn; ++tm)
+      for (uint32_t tn = 0; tn < tnn; ++tn) items.push_back(BItem{(uint32_t)i, (uint16_t)tm, (uint16_t)tn});
+  }
+  // longest inner dimension first (largest items first keeps the persistent CTAs balanced)
+  std::stable_sort(items.begin(), items.end(),
+                   [&](const BItem& a, const BItem& b) { return insts[a.inst].k > insts[b.inst].k; });
+  return FP_OK;
+}
+
+size_t batch_plan_bytes(size_t ninst, size_t nitems) {
+  return ((ninst * sizeof(BInst) + 255) & ~(size_t)255) + ((nitems * sizeof(BItem) + 255) & ~(size_t)255) + 256;
+}
+
+// Lay the plan out in host staging memory `h` (batch_plan_bytes long) in the device layout.
+void batch_plan_write(const std::vector<BInst>& insts, const std::vector<BItem>& items, uint8_t* h) {
+  const size_t ib = (insts.size() * sizeof(BInst) + 255) & ~(size_t)255;
+  memcpy(h, insts.data(), insts.size() * sizeof(BInst));
+  memcpy(h + ib, items.data(), items.size() * sizeof(BItem));
+  memset(h + ib + ((items.size() * sizeof(BItem) + 255) & ~(size_t)255), 0, 256);  // counter
+}
+
+// Launch the persistent kernel on a plan already resident at `d` (same layout).
+fp_status batch_launch_plan(fp_ctx ctx, size_t ninst, size_t nitems, uint8_t* d, cudaStream_t st) {
+  const size_t ib = (ninst * sizeof(BInst) + 255) & ~(size_t)255;
+  const size_t tb = (nitems * sizeof(BItem) + 255) & ~(size_t)255;
+  const int grid = (int)std::min<size_t>(nitems, (size_t)ctx->num_sms * 8);
+  FP_LAUNCH(ctx, "k_batch", st,
+            k_batch<<<grid, BT_THREADS, 0, st>>>((const BInst*)d, (const BItem*)(d + ib), (uint32_t)nitems,
+                                                 (uint32_t*)(d + ib + tb), ctx->d_err));
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
+static fp_status plan_and_launch(fp_ctx ctx, const fp_instance* in, size_t count, cudaStream_t st,
+                                 bool measure_only) {
+  std::vector<BInst> insts;
+  std::vector<BItem> items;
+  fp_status s = batch_prepare(ctx, in, count, st, measure_only, insts, items);
+  if (s != FP_OK) return s;
+  const size_t bytes = batch_plan_bytes(insts.size(), items.size());
+  s = ensure_scratch(ctx, bytes, 1);
+  if (s != FP_OK) return s;
+  std::vector<uint8_t> h(bytes);
+  batch_plan_write(insts, items, h.data());
+  // pageable source: cudaMemcpyAsync returns once the bytes are staged, so h may go away
+  FP_CUDA(cudaMemcpyAsync(ctx->scratch2, h.data(), bytes, cudaMemcpyHostToDevice, st));
+  return batch_launch_plan(ctx, insts.size(), items.size(), (uint8_t*)ctx->scratch2, st);
+}
+
+// Autotuner probe: a synthetic batch of 16 instances 256 x 256 x k (device buffers from the
+// context's autotune arena), timed packed and plain; the faster choice is cached per
+// (p, k class).  Runs once per class; synchronises the stream.
+static __global__ void k_fill_mod(uint8_t* x, size_t n, uint32_t p, uint32_t seed) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)i * 2654435761u ^ seed;
+    h ^= h >> 15; h *= 2246822519u; h ^= h >> 13;
+    x[i] = (uint8_t)(h % p);
+  }
+}
+
+static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st) {
+  const uint64_t key = (0xBA7Cull << 48) | ((uint64_t)p << 16) | kclass(k);
+  auto it = ctx->tune.find(key);
+  if (it != ctx->tune.end()) return it->second != 0;
+  if (!ctx->autotune) return k >= 448;   // fixed rule: packing pays once a chunk is full
+  const uint32_t kk = 1u << kclass(k), dim = 256, nin = 16;
+  const size_t per = (size_t)dim * kk;          // one A (dim x kk) or one B (kk x dim)
+  const size_t cper = (size_t)dim * dim;        // one C (dim x dim)
+  void* buf = nullptr;
+  bool packed = k >= 448;
+  if (cudaMalloc(&buf, 2 * per * nin + cper * nin) == cudaSuccess) {
+    uint8_t* A = (uint8_t*)buf;
+    uint8_t* Cb = A + 2 * per * nin;
+    k_fill_mod<<<ctx->num_sms * 4, 256, 0, st>>>(A, 2 * per * nin, p, 12345u + p);
+    std::vector<fp_instance> v(nin);
+    for (uint32_t i = 0; i < nin; ++i) {
+      v[i] = fp_instance{0, p, dim, dim, kk, 0, A + per * i, A + per * (nin + i), Cb + cper * i};
+    }
+    float best[2] = {1e30f, 1e30f};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int rep = 0; rep < 2; ++rep)
+      for (int pk = 0; pk < 2; ++pk) {
+        for (auto& x : v) x.reserved = (uint32_t)pk;
+        cudaEventRecord(e0, st);
+        plan_and_launch(ctx, v.data(), v.size(), st, true);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best[pk] = std::min(best[pk], ms);
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(buf);
+    packed = best[1] < best[0];
+  }
+  ctx->tune[key] = packed ? 1 : 0;
+  return packed;
+}
+
+}  // namespace fpd
+
 extern "C" fp_status fp_batch_run(fp_ctx ctx, const fp_instance* instances, size_t count, void* stream) {
-  (void)ctx; (void)instances; (void)count; (void)stream;
-  fpd::set_error("fp_batch_run: not built");
-  return FP_EUNSUPPORTED;
+  using namespace fpd;
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_batch_run: ctx is NULL");
+  if (count == 0) return FP_OK;
+  FP_CHECK(instances != nullptr, FP_EINVAL, "fp_batch_run: instances is NULL");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return plan_and_launch(ctx, instances, count, as_stream(stream), false);
 }

@@ -202,72 +202,49 @@ __global__ void __launch_bounds__(256) k_polymul_plain_big(const uint8_t* __rest
   if (bad) flag_error(err, ERR_RANGE);
 }
 
-// Blocked FQT (Sec. 5.2): P = sum_i P_i (X^{d+1})^i with each P_i (d+1 coefficients) in one
-// u64 word at q = 2^b; output word t = sum_i P_i Q_{t-i} accumulated in the word (delayed
-// reduction, the planner keeps every digit below q), then REDQ_{2d+1}; the residues of words t
-// and t-1 overlap on d coefficients and are added mod p.  One block per pair.
 __global__ void __launch_bounds__(256) k_polymul_fqt(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
                                                      uint8_t* __restrict__ Cout, uint64_t batch, uint32_t ka,
                                                      uint32_t kb, uint32_t d1, RedqParams P, uint32_t* err) {
   __shared__ uint64_t wa[1024];
   __shared__ uint64_t wb[1024];
-  __shared__ uint8_t res[4096 + 64];   // residues of output block words, (2d+1) each
+  __shared__ uint8_t res[4096 + 64];
   __shared__ uint8_t ptab[1024];
   fill_pair_table(ptab, P);
   __syncthreads();
   Corrector C;
   C.init(P, ptab);
   uint32_t bad = 0;
-  const uint32_t na = (ka + d1 - 1) / d1, nb = (kb + d1 - 1) / d1;
-  const uint32_t nw = na + nb - 1;              // output words
   const uint32_t kc = ka + kb - 1;
-  const uint32_t nd = 2 * d1 - 1;               // residues per output word
-  for (uint64_t t = blockIdx.x; t < batch; t += gridDim.x) {
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < na; i += blockDim.x) {
-      uint64_t w = 0;
-      for (int j = (int)d1 - 1; j >= 0; --j) {
-        uint32_t idx = i * d1 + j;
-        uint32_t v = idx < ka ? A[t * ka + idx] : 0u;
-        bad |= v >= P.p;
-        w = (w << P.b) | v;
-      }
-      wa[i] = w;
-    }
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
-      uint64_t w = 0;
-      for (int j = (int)d1 - 1; j >= 0; --j) {
-        uint32_t idx = i * d1 + j;
-        uint32_t v = idx < kb ? B[t * kb + idx] : 0u;
-        bad |= v >= P.p;
-        w = (w << P.b) | v;
-      }
-      wb[i] = w;
-    }
-    __syncthreads();
-    // whole warps iterate so that the shuffle-table lookups see 32 active lanes
-    for (uint32_t base = 0; base < nw; base += blockDim.x) {
-      uint32_t o = base + threadIdx.x;
-      uint64_t acc = 0;
-      if (o < nw) {
-        uint32_t lo = o + 1 > nb ? o + 1 - nb : 0;
-        uint32_t hi = o < na - 1 ? o : na - 1;
-        for (uint32_t i = lo; i <= hi; ++i) acc += wa[i] * wb[o - i];
-      }
-      uint8_t* out = res + (o < nw ? o : 0) * nd;
-      bool own = o < nw;
-      redq_word<uint64_t>(acc, P, C, [&](uint32_t i, uint32_t mu) { if (own) out[i] = (uint8_t)mu; });
-    }
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < kc; j += blockDim.x) {
-      uint32_t o = j / d1, r = j - o * d1;
-      uint32_t v = o < nw ? res[o * nd + r] : 0u;
-      if (o >= 1 && r + d1 < nd) v += res[(o - 1) * nd + r + d1];
-      if (v >= P.p) v -= P.p;
-      Cout[t * kc + j] = (uint8_t)v;
-    }
-  }
+  for (uint64_t t = blockIdx.x; t < batch; t += gridDim.x)
+    fqt_block_product(A + t * ka, B + t * kb, Cout + t * kc, ka, kb, d1, P, C, wa, wb, res, bad);
   if (bad) flag_error(err, ERR_RANGE);
+}
+
+// Largest FQT block size d+1 whose accumulated u64 output word stays exact: digit bound
+// min(#blocks) (d+1) (p-1)^2 < q = 2^b, 2d+1 digits below 2^64, shared buffers large enough.
+bool fqt_params(uint32_t p, uint32_t ka, uint32_t kb, uint32_t* d1_out, uint32_t* b_out) {
+  uint32_t best_d1 = 0, best_b = 0;
+  for (uint32_t d1 = 1; d1 <= 32; ++d1) {
+    uint32_t na = (ka + d1 - 1) / d1, nb = (kb + d1 - 1) / d1;
+    uint64_t nterms = na < nb ? na : nb;
+    uint64_t D = nterms * d1 * (uint64_t)(p - 1) * (p - 1);
+    uint32_t b = 1;
+    while ((1ull << b) <= D || (1ull << b) < p) ++b;
+    unsigned __int128 tot = 0;
+    bool ok = true;
+    for (uint32_t j = 0; j < 2 * d1 - 1 && ok; ++j) {
+      if ((uint64_t)j * b >= 100) { ok = false; break; }
+      tot += (unsigned __int128)D << (j * b);
+      if (tot >> 64) ok = false;
+    }
+    if (!ok) break;
+    if (na > 1024 || nb > 1024 || na + nb - 1 > 2048 || (na + nb - 1) * (2 * d1 - 1) > 4096) continue;
+    best_d1 = d1;
+    best_b = b;
+  }
+  *d1_out = best_d1;
+  *b_out = best_b;
+  return best_d1 >= 1;
 }
 
 // ------------------------------------------------------------------ launchers
@@ -403,25 +380,7 @@ fp_status launch_polymul(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t da, 
     return FP_EBOUND;
   }
   uint32_t best_d1 = 0, best_b = 0;
-  for (uint32_t d1 = 1; d1 <= 32; ++d1) {
-    uint32_t na = (ka + d1 - 1) / d1, nb = (kb + d1 - 1) / d1;
-    uint64_t nterms = na < nb ? na : nb;
-    uint64_t D = nterms * d1 * (uint64_t)(p - 1) * (p - 1);
-    uint32_t b = 1;
-    while ((1ull << b) <= D || (1ull << b) < p) ++b;
-    // largest output word: all 2d+1 digits at D (upper bound)
-    unsigned __int128 tot = 0;
-    bool ok = true;
-    for (uint32_t j = 0; j < 2 * d1 - 1 && ok; ++j) {
-      if ((uint64_t)j * b >= 100) { ok = false; break; }
-      tot += (unsigned __int128)D << (j * b);
-      if (tot >> 64) ok = false;
-    }
-    if (!ok) break;
-    if (na + nb - 1 > 2048 || (na + nb - 1) * (2 * d1 - 1) > 4096) continue;
-    best_d1 = d1;
-    best_b = b;
-  }
+  fqt_params(p, ka, kb, &best_d1, &best_b);
   FP_CHECK(best_d1 >= 1, FP_EBOUND, "polymul: no FQT block size fits a 64-bit word (p=%u)", p);
   RedqParams P = make_redq(p, best_b, 2 * best_d1 - 1);
   int grid = grid_for(ctx, batch, 16);

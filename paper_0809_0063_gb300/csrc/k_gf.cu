@@ -67,47 +67,86 @@ static uint32_t spread(const std::vector<uint32_t>& coeffs, uint32_t fb) {
 
 // ---------------------------------------------------------------- kernel
 
-template <typename E>
-__global__ void __launch_bounds__(256) k_gf_mul(const E* __restrict__ a, const E* __restrict__ b, E* __restrict__ c,
-                                                uint64_t count, const uint64_t* __restrict__ gword,
-                                                const uint32_t* __restrict__ gL, const uint32_t* __restrict__ gH,
-                                                uint32_t order, uint32_t k, uint32_t cbits, uint32_t fb,
-                                                RedqParams P, uint32_t* err) {
-  extern __shared__ __align__(16) uint8_t sm[];
-  uint64_t* sw = reinterpret_cast<uint64_t*>(sm);
-  const uint32_t tsz = 1u << (cbits * k);
-  uint32_t* sL = reinterpret_cast<uint32_t*>(sw + order);
-  uint32_t* sH = sL + tsz;
-  for (uint32_t i = threadIdx.x; i < order; i += blockDim.x) sw[i] = gword[i];
-  for (uint32_t i = threadIdx.x; i < tsz; i += blockDim.x) { sL[i] = gL[i]; sH[i] = gH[i]; }
+struct GfDev {
+  const uint64_t* word;
+  const uint32_t* L;
+  const uint32_t* H;
+  uint32_t order, k, cbits, fb;
+};
+
+// Shared copies of the three tables (word table, L, H) for one block.
+__device__ __forceinline__ void gf_load_tables(const GfDev& G, uint8_t* sm, uint64_t*& sw, uint32_t*& sL,
+                                               uint32_t*& sH) {
+  sw = reinterpret_cast<uint64_t*>(sm);
+  const uint32_t tsz = 1u << (G.cbits * G.k);
+  sL = reinterpret_cast<uint32_t*>(sw + G.order);
+  sH = sL + tsz;
+  for (uint32_t i = threadIdx.x; i < G.order; i += blockDim.x) sw[i] = G.word[i];
+  for (uint32_t i = threadIdx.x; i < tsz; i += blockDim.x) { sL[i] = G.L[i]; sH[i] = G.H[i]; }
   __syncthreads();
-  const uint32_t p = P.p, bq = P.b;
+}
+
+// One product by Algorithm FGDP with n = 1 (see the file comment).
+__device__ __forceinline__ uint32_t gf_mul_one(uint32_t xa, uint32_t xb, const GfDev& G, const uint64_t* sw,
+                                               const uint32_t* sL, const uint32_t* sH, const RedqParams& P,
+                                               uint32_t& bad) {
+  const uint32_t p = P.p, bq = P.b, k = G.k, fb = G.fb, cbits = G.cbits;
+  bad |= (xa >= G.order) | (xb >= G.order);
+  xa = xa < G.order ? xa : 0u;
+  xb = xb < G.order ? xb : 0u;
+  const uint64_t r = sw[xa] * sw[xb];             // lines 1-2
+  const uint64_t s = divp64(r, P.dv);             // REDQ compression quotient (line 3)
   const uint32_t qmask = (1u << bq) - 1u;
-  const uint32_t fmask = (1u << fb) - 1u;
+  uint32_t il = 0, ih = 0;
+  for (uint32_t j = 0; j < 2 * k - 1; ++j) {
+    const uint32_t sh = j * bq;
+    const uint32_t uj = ((uint32_t)(r >> sh) - p * (uint32_t)(s >> sh)) & qmask;
+    if (j < k) il |= uj << (j * cbits);
+    if (j >= k - 1) ih |= uj << ((j - (k - 1)) * cbits);
+  }
   uint32_t ones = 0;
   for (uint32_t i = 0; i < k; ++i) ones |= 1u << (i * fb);
-  const uint32_t hb = fb - 1;                 // bit tested after adding 2^hb - p per field
+  const uint32_t hb = fb - 1;                     // bit tested after adding 2^hb - p per field
+  uint32_t x = sL[il] + sH[ih];                    // lines 4-6: two lookups, one field add
+  const uint32_t ge = ((x + ((1u << hb) - p) * ones) >> hb) & ones;
+  x -= p * ge;
+  const uint32_t fmask = (1u << fb) - 1u;
+  uint32_t idx = 0;
+  for (int j = (int)k - 1; j >= 0; --j) idx = idx * p + ((x >> (j * fb)) & fmask);
+  return idx;
+}
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_gf_mul(const E* __restrict__ a, const E* __restrict__ b, E* __restrict__ c,
+                                                uint64_t count, GfDev G, RedqParams P, uint32_t* err) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  uint64_t* sw;
+  uint32_t *sL, *sH;
+  gf_load_tables(G, sm, sw, sL, sH);
   uint32_t bad = 0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t xa = a[i], xb = b[i];
-    bad |= (xa >= order) | (xb >= order);
-    xa = xa < order ? xa : 0u;
-    xb = xb < order ? xb : 0u;
-    uint64_t r = sw[xa] * sw[xb];             // lines 1-2
-    uint64_t s = divp64(r, P.dv);             // REDQ compression quotient (line 3)
-    uint32_t il = 0, ih = 0;
-    for (uint32_t j = 0; j < 2 * k - 1; ++j) {
-      uint32_t sh = j * bq;
-      uint32_t uj = ((uint32_t)(r >> sh) - p * (uint32_t)(s >> sh)) & qmask;
-      if (j < k) il |= uj << (j * cbits);
-      if (j >= k - 1) ih |= uj << ((j - (k - 1)) * cbits);
-    }
-    uint32_t x = sL[il] + sH[ih];              // lines 4-6: two lookups, one field add
-    uint32_t ge = ((x + ((1u << hb) - p) * ones) >> hb) & ones;
-    x -= p * ge;
-    uint32_t idx = 0;
-    for (int j = (int)k - 1; j >= 0; --j) idx = idx * p + ((x >> (j * fb)) & fmask);
-    c[i] = (E)idx;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
+    c[i] = (E)gf_mul_one(a[i], b[i], G, sw, sL, sH, P, bad);
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// Segmented form for the serving loop: segment s multiplies count[s] pairs at byte offsets
+// a/b/c from `base`; one block per segment.
+struct GfSeg { uint64_t a, b, c; uint32_t count, pad; };
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_gf_mul_seg(uint8_t* base, const GfSeg* __restrict__ segs, uint32_t nseg,
+                                                    GfDev G, RedqParams P, uint32_t* err) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  uint64_t* sw;
+  uint32_t *sL, *sH;
+  gf_load_tables(G, sm, sw, sL, sH);
+  uint32_t bad = 0;
+  for (uint32_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+    const GfSeg S = segs[sg];
+    const E* a = reinterpret_cast<const E*>(base + S.a);
+    const E* b = reinterpret_cast<const E*>(base + S.b);
+    E* c = reinterpret_cast<E*>(base + S.c);
+    for (uint32_t i = threadIdx.x; i < S.count; i += blockDim.x) c[i] = (E)gf_mul_one(a[i], b[i], G, sw, sL, sH, P, bad);
   }
   if (bad) flag_error(err, ERR_RANGE);
 }
@@ -234,16 +273,39 @@ extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const
   const uint32_t tsz = 1u << (g->c * g->k);
   size_t smem = g->order * sizeof(uint64_t) + 2 * tsz * sizeof(uint32_t);
   int grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)ctx->num_sms * 4);
+  GfDev G{g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb};
   if (g->elem_bytes == 1) {
     FP_CUDA(cudaFuncSetAttribute(k_gf_mul<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FP_LAUNCH(ctx, "k_gf_mul", st, k_gf_mul<uint8_t><<<grid, 256, smem, st>>>((const uint8_t*)a, (const uint8_t*)b, (uint8_t*)c, count, g->d_word,
-                                               g->d_L, g->d_H, g->order, g->k, g->c, g->fb, g->P, ctx->d_err));
+    FP_LAUNCH(ctx, "k_gf_mul", st, k_gf_mul<uint8_t><<<grid, 256, smem, st>>>((const uint8_t*)a, (const uint8_t*)b,
+                                                                              (uint8_t*)c, count, G, g->P, ctx->d_err));
   } else {
     FP_CUDA(cudaFuncSetAttribute(k_gf_mul<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FP_LAUNCH(ctx, "k_gf_mul", st, k_gf_mul<uint16_t><<<grid, 256, smem, st>>>((const uint16_t*)a, (const uint16_t*)b, (uint16_t*)c, count,
-                                                g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb, g->P,
-                                                ctx->d_err));
+    FP_LAUNCH(ctx, "k_gf_mul", st, k_gf_mul<uint16_t><<<grid, 256, smem, st>>>((const uint16_t*)a, (const uint16_t*)b,
+                                                                               (uint16_t*)c, count, G, g->P, ctx->d_err));
   }
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }
+
+namespace fpd {
+// Launch the segmented multiply for one field (segments already resident at `segs`).
+fp_status gf_launch_segments(fp_ctx ctx, fp_gf g, uint8_t* base, const void* segs, uint32_t nseg, cudaStream_t st) {
+  const uint32_t tsz = 1u << (g->c * g->k);
+  size_t smem = g->order * sizeof(uint64_t) + 2 * tsz * sizeof(uint32_t);
+  GfDev G{g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb};
+  const int grid = (int)std::min<uint32_t>(nseg, (uint32_t)ctx->num_sms * 4);
+  if (g->elem_bytes == 1) {
+    FP_CUDA(cudaFuncSetAttribute(k_gf_mul_seg<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FP_LAUNCH(ctx, "k_gf_mul_seg", st,
+              k_gf_mul_seg<uint8_t><<<grid, 256, smem, st>>>(base, (const GfSeg*)segs, nseg, G, g->P, ctx->d_err));
+  } else {
+    FP_CUDA(cudaFuncSetAttribute(k_gf_mul_seg<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FP_LAUNCH(ctx, "k_gf_mul_seg", st,
+              k_gf_mul_seg<uint16_t><<<grid, 256, smem, st>>>(base, (const GfSeg*)segs, nseg, G, g->P, ctx->d_err));
+  }
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+uint32_t gf_elem_bytes(fp_gf g) { return g->elem_bytes; }
+uint32_t gf_order(fp_gf g) { return g->order; }
+}  // namespace fpd

@@ -1,0 +1,141 @@
+"""GPU parity of the uneven batch (one persistent launch over matmul and dot instances of
+mixed p and size): every result bit-exact against the oracle, and identical to the same
+instance run alone through fp_matmul / fp_dot."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import field
+from tests._gpu import to_dev, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch, dev = torch_dev()
+    import __graft_entry__ as g
+    g.build()
+    import paper_0809_0063_gb300 as fp
+    ctx = fp.fp_ctx_create(0)
+    yield fp, torch, dev, ctx
+    fp.fp_ctx_destroy(ctx)
+
+
+def make_instances(fp, torch, dev, insts):
+    bufs, arr = [], []
+    for x in insts:
+        A = to_dev(torch, dev, x.a)
+        B = to_dev(torch, dev, x.b)
+        if x.kind == "matmul":
+            C = torch.full((x.m, x.n), 255, dtype=torch.uint8, device=dev)
+            arr.append(fp.fp_instance(kind=0, p=x.p, m=x.m, n=x.n, k=x.k, reserved=0,
+                                      A=A.data_ptr(), B=B.data_ptr(), C=C.data_ptr()))
+        else:
+            C = torch.full((4,), 255, dtype=torch.uint8, device=dev)
+            arr.append(fp.fp_instance(kind=1, p=x.p, m=1, n=1, k=x.k, reserved=0,
+                                      A=A.data_ptr(), B=B.data_ptr(), C=C.data_ptr()))
+        bufs.append((A, B, C))
+    return bufs, arr
+
+
+def result(x, C):
+    if x.kind == "matmul":
+        return C.cpu().numpy()
+    return int(C.cpu().numpy().view(np.uint32)[0])
+
+
+def oracle(x):
+    return field.matmul_mod(x.a, x.b, x.p) if x.kind == "matmul" else field.dot_mod(x.a, x.b, x.p)
+
+
+def test_batch_small_uneven(env):
+    fp, torch, dev, ctx = env
+    insts = workloads.uneven_batch(7, count=96, lo=1, hi=300)
+    bufs, arr = make_instances(fp, torch, dev, insts)
+    fp.fp_batch_run(ctx, arr)
+    fp.fp_ctx_status(ctx)
+    for x, (A, B, C) in zip(insts, bufs):
+        got = result(x, C)
+        assert np.array_equal(got, oracle(x)), (x.kind, x.p, x.m, x.n, x.k)
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 7, 17, 31])
+def test_batch_ragged_edges_each_p(env, p):
+    fp, torch, dev, ctx = env
+    shapes = [(1, 1, 1), (1, 65, 33), (65, 1, 700), (63, 129, 449), (130, 255, 896), (64, 64, 32), (3, 7, 2049)]
+    g = np.random.default_rng(p)
+    insts = []
+    for (m, n, k) in shapes:
+        x = workloads.Instance("matmul", p, m, k, n)
+        x.a = g.integers(0, p, (m, k), dtype=np.uint8)
+        x.b = g.integers(0, p, (k, n), dtype=np.uint8)
+        insts.append(x)
+    for n in (1, 31, 1000):
+        x = workloads.Instance("dot", p, 1, n, 1)
+        x.a = g.integers(0, p, n, dtype=np.uint8)
+        x.b = g.integers(0, p, n, dtype=np.uint8)
+        insts.append(x)
+    bufs, arr = make_instances(fp, torch, dev, insts)
+    fp.fp_batch_run(ctx, arr)
+    fp.fp_ctx_status(ctx)
+    for x, (A, B, C) in zip(insts, bufs):
+        assert np.array_equal(result(x, C), oracle(x)), (x.kind, p, x.m, x.n, x.k)
+
+
+def test_batch_all_max_entries(env):
+    fp, torch, dev, ctx = env
+    insts = []
+    for p, k in [(3, 2048), (2, 2047), (7, 2048), (31, 2048), (3, 449)]:
+        x = workloads.Instance("matmul", p, 70, k, 130)
+        x.a = np.full((70, k), p - 1, np.uint8)
+        x.b = np.full((k, 130), p - 1, np.uint8)
+        insts.append(x)
+    bufs, arr = make_instances(fp, torch, dev, insts)
+    fp.fp_batch_run(ctx, arr)
+    fp.fp_ctx_status(ctx)
+    for x, (A, B, C) in zip(insts, bufs):
+        assert np.all(result(x, C) == (x.k * (x.p - 1) ** 2) % x.p)
+
+
+def test_batch_equals_alone_config_sample(env):
+    """The uneven-batch configuration (4096 instances, sizes log-uniform in [16, 2048]):
+    every instance's result in the batch equals the same instance run alone, and a sample is
+    checked against the oracle."""
+    fp, torch, dev, ctx = env
+    insts = workloads.uneven_batch(11, count=4096)
+    bufs, arr = make_instances(fp, torch, dev, insts)
+    fp.fp_batch_run(ctx, arr)
+    fp.fp_ctx_status(ctx)
+    batch_res = [result(x, C) for x, (A, B, C) in zip(insts, bufs)]
+    alone = []
+    for x, (A, B, C) in zip(insts, bufs):
+        if x.kind == "matmul":
+            C2 = torch.empty_like(C)
+            fp.fp_matmul(ctx, x.p, x.m, x.n, x.k, A, x.k, B, x.n, C2, x.n, fp.FP_MM_PLAIN_TC
+                         if x.k * (x.p - 1) ** 2 < 2 ** 24 else fp.FP_MM_PLAIN_I8)
+        else:
+            C2 = torch.empty_like(C)
+            fp.fp_dot(ctx, x.p, A, B, x.k, C2, fp.FP_ALGO_PLAIN)
+        alone.append(C2)
+    fp.fp_ctx_status(ctx)
+    for x, r, C2 in zip(insts, batch_res, alone):
+        assert np.array_equal(r, result(x, C2))
+    g = np.random.default_rng(0)
+    for i in g.choice(len(insts), 24, replace=False):
+        x = insts[i]
+        if x.kind == "matmul":
+            rows = np.unique(np.array([0, x.m - 1, x.m // 2]))
+            assert np.array_equal(batch_res[i][rows], field.matmul_mod_rows(x.a, x.b, x.p, rows))
+        else:
+            assert batch_res[i] == field.dot_mod(x.a, x.b, x.p)
+
+
+def test_batch_rejects_bad_instances(env):
+    fp, torch, dev, ctx = env
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_batch_run(ctx, [fp.fp_instance(kind=0, p=4, m=1, n=1, k=1, reserved=0, A=1, B=1, C=1)])
+    assert ei.value.status == fp.FP_EINVAL
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_batch_run(ctx, [fp.fp_instance(kind=0, p=3, m=1, n=1, k=1, reserved=0, A=0, B=1, C=1)])
+    assert ei.value.status == fp.FP_EINVAL

@@ -146,3 +146,29 @@ def serving_stream(seed: int, rate: float = 20000.0, duration: float = 1.0):
         i += 1
         out.append(r)
     return out
+
+
+def request_arrays(req: Request, matmul_cap: int = 0):
+    """Seeded operands of one serving request: (kind code, sizes (a, b, c), A, B, out array).
+    polymul: degrees (size, independent log-uniform 2..512); dot: length size; GF: count size
+    in the request's field; matmul: square n = size (capped at matmul_cap when given)."""
+    g = rng(req.seed)
+    if req.kind == "polymul":
+        da = req.size
+        db = int(log_uniform_int(g, 2, 512))
+        A = g.integers(0, req.p, da + 1, dtype=np.uint8)
+        B = g.integers(0, req.p, db + 1, dtype=np.uint8)
+        return 0, (da, db, 0), A, B, np.zeros(da + db + 1, np.uint8)
+    if req.kind == "dot":
+        A = g.integers(0, req.p, req.size, dtype=np.uint8)
+        B = g.integers(0, req.p, req.size, dtype=np.uint8)
+        return 1, (req.size, 0, 0), A, B, np.zeros(1, np.uint32)
+    if req.kind == "gf":
+        dt = gf_index_dtype(req.p, req.gf_k)
+        A = g.integers(0, req.p ** req.gf_k, req.size, dtype=np.int64).astype(dt)
+        B = g.integers(0, req.p ** req.gf_k, req.size, dtype=np.int64).astype(dt)
+        return 2, (req.size, 0, 0), A, B, np.zeros(req.size, dt)
+    n = min(req.size, matmul_cap) if matmul_cap else req.size
+    A = g.integers(0, req.p, (n, n), dtype=np.uint8)
+    B = g.integers(0, req.p, (n, n), dtype=np.uint8)
+    return 3, (n, n, n), A, B, np.zeros((n, n), np.uint8)
