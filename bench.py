@@ -300,13 +300,130 @@ def run_batch(args, ws, rank, local):
     fp.fp_ctx_destroy(ctx)
 
 
+def req_macs(code, sz, gf_k):
+    if code == 0:
+        return (sz[0] + 1) * (sz[1] + 1)
+    if code == 1:
+        return sz[0]
+    if code == 2:
+        return sz[0] * gf_k * gf_k
+    return sz[0] ** 3
+
+
+def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0):
+    """Serving: a Poisson stream (20k requests/s offered for `duration` s; 50% polymul, 30% dot,
+    15% GF(p^k) batches, 5% matmul) through the continuous-batching server.  Reports latency
+    percentiles at the offered load, and capacity (the stream submitted at once) against a
+    per-request-launch server (one direct call per request, in order, synchronised)."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_0809_0063_gb300 as fp
+    from oracle import field
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = fp.fp_ctx_create(local)
+    gfs = {pk: fp.fp_gf_create(ctx, *pk) for pk in workloads.GF_FIELDS}
+    moduli = {pk: field.smallest_monic_irreducible(*pk) for pk in workloads.GF_FIELDS}
+    reqs = workloads.serving_stream(77, rate=rate, duration=duration)
+    data = [workloads.request_arrays(r) for r in reqs]
+    macs = sum(req_macs(c, sz, r.gf_k) for r, (c, sz, A, B, out) in zip(reqs, data))
+
+    def make_req(r, d):
+        code, sz, A, B, out = d
+        return fp.fp_request(kind=code, p=r.p, a=sz[0], b=sz[1], c=sz[2], reserved=0,
+                             gf=gfs[(r.p, r.gf_k)].value if code == 2 else None,
+                             host_a=A.ctypes.data, host_b=B.ctypes.data, host_out=out.ctypes.data)
+
+    def serve(paced):
+        srv = fp.fp_server_create(ctx, arena_bytes=8 << 30, streams=4, max_batch=512, window_us=100)
+        t0 = time.perf_counter()
+        first = None
+        for r, d in zip(reqs, data):
+            if paced:
+                while time.perf_counter() - t0 < r.t_arrival:
+                    pass
+            t = fp.fp_server_submit(srv, make_req(r, d))
+            first = t if first is None else first
+        fp.fp_server_drain(srv, 120.0)
+        wall = time.perf_counter() - t0
+        lat = np.array(fp.fp_server_latencies(srv, first, len(reqs)))
+        st = fp.fp_server_stats_get(srv)
+        fp.fp_server_destroy(srv)
+        return wall, lat, st
+
+    # warm-up (first-use costs: module load, tables), then the paced run and the capacity run
+    serve(False)
+    wall_p, lat_p, st_p = serve(True)
+    wall_c, lat_c, st_c = serve(False)
+    fp.fp_ctx_status(ctx)
+    # parity gate on a sample of the served results
+    for i in np.random.default_rng(3).choice(len(reqs), 40, replace=False):
+        r, (code, sz, A, B, out) = reqs[i], data[i]
+        if code == 0:
+            want = field.polymul_mod(A, B, r.p)
+        elif code == 1:
+            want = np.array([field.dot_mod(A, B, r.p)])
+        elif code == 2:
+            want = field.gf_mul(A.astype(np.int64), B.astype(np.int64), r.p, r.gf_k, moduli[(r.p, r.gf_k)])
+        else:
+            rows = np.array([0, sz[0] - 1])
+            assert np.array_equal(out[rows], field.matmul_mod_rows(A, B, r.p, rows))
+            continue
+        assert np.array_equal(out.astype(np.int64), np.asarray(want).astype(np.int64))
+
+    # per-request launches: one direct call per request, in arrival order, each synchronised
+    n_base = min(len(reqs), 3000)
+    to = lambda x: torch.from_numpy(x.view(np.int16) if x.dtype == np.uint16 else x).to(dev, non_blocking=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    base_lat = []
+    for r, (code, sz, A, B, out) in list(zip(reqs, data))[:n_base]:
+        if code == 0:
+            C = torch.empty(out.shape, dtype=torch.uint8, device=dev)
+            fp.fp_polymul_batched(ctx, r.p, to(A), sz[0], to(B), sz[1], C, 1)
+        elif code == 1:
+            C = torch.empty((1,), dtype=torch.int32, device=dev)
+            fp.fp_dot(ctx, r.p, to(A), to(B), sz[0], C)
+        elif code == 2:
+            C = torch.empty(out.shape, dtype=torch.uint8 if out.dtype == np.uint8 else torch.int16, device=dev)
+            fp.fp_gf_mul_batched(ctx, gfs[(r.p, r.gf_k)], to(A), to(B), C, sz[0])
+        else:
+            C = torch.empty(out.shape, dtype=torch.uint8, device=dev)
+            fp.fp_matmul(ctx, r.p, sz[0], sz[0], sz[0], to(A), sz[0], to(B), sz[0], C, sz[0])
+        C.cpu()
+        base_lat.append(time.perf_counter() - t0 - r.t_arrival)
+    base_wall = time.perf_counter() - t0
+    base_rps = n_base / base_wall
+    cap_rps = len(reqs) / wall_c
+    pct = lambda a, q: float(np.percentile(a[a >= 0], q))
+    out = {"metric": "served requests/s (continuous batching) with p50/p99 latency", "value": cap_rps,
+           "unit": "requests/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": wall_c * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
+           "config": {"workload": f"Poisson {rate:.0f} req/s for {duration} s: 50% polymul (deg 2-512, p in 3,5,7), "
+                                  "30% dot (64-65536), 15% GF(3^5)/GF(7^4)/GF(2^8) batches (1-4096), 5% matmul (64-1024)",
+                      "requests": len(reqs), "fp_macs": macs, "server": "4 streams, 8 GiB arena, max_batch 512, 100 us window"},
+           "latency_us_at_offered_load": {"p50": pct(lat_p, 50), "p99": pct(lat_p, 99), "p999": pct(lat_p, 99.9),
+                                          "max": float(lat_p.max()), "wall_s": wall_p, "batches": st_p["batches"]},
+           "capacity": {"requests_per_s": cap_rps, "fp_macs_per_s": macs / wall_c, "batches": st_c["batches"],
+                        "p50_us": pct(lat_c, 50), "p99_us": pct(lat_c, 99)},
+           "per_request_launches": {"requests_per_s": base_rps, "requests": n_base,
+                                    "p50_latency_us_at_offered_load": float(np.percentile(base_lat, 50)) * 1e6,
+                                    "p99_latency_us_at_offered_load": float(np.percentile(base_lat, 99)) * 1e6},
+           "capacity_vs_per_request": cap_rps / base_rps}
+    print(json.dumps(out))
+    for g2 in gfs.values():
+        fp.fp_gf_destroy(g2)
+    fp.fp_ctx_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="matmul", choices=["matmul", "batch"],
+    ap.add_argument("--workload", default="matmul", choices=["matmul", "batch", "serve"],
                     help="matmul: the compressed-matmul configuration (default line); batch: 4096 uneven instances")
     ap.add_argument("--algo", default="AUTO")
     ap.add_argument("--no-compare", action="store_true", help="skip the per-variant comparison block")
@@ -327,6 +444,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args, ws, rank, local)
+        return
+    if args.workload == "serve":
+        run_serve(args, ws, rank, local)
         return
 
     import torch
