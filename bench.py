@@ -143,6 +143,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def max_over_ranks(ms: float, device=None) -> float:
+    """Largest timed region over all ranks (the job finishes when its slowest replica does)."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device if device is not None else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return ms
+
+
+def whole_job_rate(units_per_step: float, steps: int, world_size: int, max_ms: float) -> float:
+    """Whole-job throughput: every replica processes units_per_step per step."""
+    return world_size * units_per_step * steps / (max_ms / 1e3)
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -525,12 +541,8 @@ def main():
     fp.fp_ctx_status(ctx)
     launches = fp.fp_ctx_launches(ctx) - l0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * macs_per_step * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    value = whole_job_rate(macs_per_step, args.steps, ws, total_ms)
 
     # dominant kernel and its roofline from the library's own per-launch events
     dominant, dom_ms, dom_n = None, 0.0, 0

@@ -263,6 +263,13 @@ typedef struct {
  * scratch.  Errors: FP_EINVAL, FP_EBOUND, FP_ECUDA. */
 fp_status fp_batch_run(fp_ctx ctx, const fp_instance* instances, size_t count, void* stream);
 
+/* Diagnostic (no counterpart in the paper): launches one warp that waits on a device barrier
+ * nothing will complete, using the library's bounded wait with a limit of `polls` polls
+ * (1 <= polls <= 2^22).  The wait gives up, the context's sticky flag records the timeout and
+ * the next fp_ctx_status returns FP_ETIMEOUT; the GPU context stays usable.  Exercises the
+ * failure path the tensor-core kernels take if a TMA or MMA completion never arrives. */
+fp_status fp_selftest_bounded_wait(fp_ctx ctx, uint32_t polls, void* stream);
+
 /* ---------------------------------------------------------------- serving loop */
 
 /* A request for the serving loop.  kind: 0 polymul (a = dega, b = degb, p), 1 dot (a = n, p),

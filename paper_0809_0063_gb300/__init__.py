@@ -89,6 +89,7 @@ _SIGS = {
     "fp_gf_info": (_I, [_V, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
     "fp_gf_mul_batched": (_I, [_V, _V, _V, _V, _V, _SZ, _V]),
     "fp_batch_run": (_I, [_V, ctypes.POINTER(fp_instance), _SZ, _V]),
+    "fp_selftest_bounded_wait": (_I, [_V, _U32, _V]),
     "fp_server_create": (_I, [_V, ctypes.POINTER(fp_server_config), ctypes.POINTER(_V)]),
     "fp_server_submit": (_I, [_V, ctypes.POINTER(fp_request), ctypes.POINTER(_U64)]),
     "fp_server_poll": (_I, [_V, _U64, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
@@ -249,6 +250,10 @@ def fp_gf_info(gf, k: int):
 
 def fp_gf_mul_batched(ctx, gf, a, b, c, count: int, stream=None):
     _check(lib().fp_gf_mul_batched(ctx, gf, _ptr(a), _ptr(b), _ptr(c), count, _stream(stream)))
+
+
+def fp_selftest_bounded_wait(ctx, polls: int, stream=None):
+    _check(lib().fp_selftest_bounded_wait(ctx, polls, _stream(stream)))
 
 
 def fp_batch_run(ctx, instances, stream=None):

@@ -5,7 +5,10 @@
 // Every kernel stages its contiguous byte tiles through shared memory with 16-byte global
 // accesses and runs a grid-stride loop over tiles of 256 items (grid = a multiple of the SM
 // count), so HBM traffic is coalesced whatever the number of coefficients per item.
+#include <algorithm>
+
 #include "fpdqt_internal.cuh"
+#include "stream.cuh"
 
 namespace fpd {
 
@@ -135,6 +138,38 @@ __global__ void __launch_bounds__(TILE) k_polymul_word(const uint8_t* __restrict
     stage_out(Cout + i0 * kc, sc, nit * kc);
   }
   if (bad) flag_error(err, ERR_RANGE);
+}
+
+// The same single-word product on the bulk-copy streaming loop (stream.cuh): 2048 pairs per
+// tile, whole tiles moved by the copy engine, double-buffered.
+template <typename W>
+struct PolymulWordOp {
+  static constexpr uint32_t IPT = 8;
+  uint32_t ka, kb, kc;
+  RedqParams P;
+  Corrector C;
+  uint32_t bad;
+  __device__ __forceinline__ void item(const uint8_t* a, const uint8_t* b, uint8_t* out) {
+    W wa = WordOps<W>::from_u64(pack_bits(a, ka, P.b, P.p, bad));
+    W wb = WordOps<W>::from_u64(pack_bits(b, kb, P.b, P.p, bad));
+    W r = wa * wb;
+    redq_word<W>(r, P, C, [&](uint32_t i, uint32_t mu) { out[i] = (uint8_t)mu; });
+  }
+};
+
+template <typename W>
+__global__ void __launch_bounds__(256) k_polymul_word_bulk(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
+                                                           uint8_t* __restrict__ Cout, uint64_t ntiles, uint32_t ka,
+                                                           uint32_t kb, RedqParams P, uint32_t* err) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  __shared__ uint8_t ptab[1024];
+  fill_pair_table(ptab, P);
+  __syncthreads();
+  PolymulWordOp<W> op;
+  op.ka = ka; op.kb = kb; op.kc = ka + kb - 1; op.P = P; op.bad = 0;
+  op.C.init(P, ptab);
+  stream_tiles(op, A, B, Cout, ntiles, ka, kb, ka + kb - 1, sm, err);
+  if (op.bad) flag_error(err, ERR_RANGE);
 }
 
 // Plain baseline: c_j = sum_i a_i b_{j-i} accumulated without reduction (delayed reduction,
@@ -327,6 +362,26 @@ static fp_status polymul_word_t(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32
                                 uint32_t kb, uint8_t* C, size_t batch, uint32_t bq, cudaStream_t st) {
   uint32_t kc = ka + kb - 1;
   RedqParams P = make_redq(p, bq, kc);
+  // full tiles of 2048 pairs on the bulk-copy path when the arrays are 16-byte aligned and a
+  // tile pair of buffers fits comfortably in shared memory; the rest on the per-thread path
+  constexpr uint64_t ITEMS = 256 * PolymulWordOp<W>::IPT;
+  const bool aligned = ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15u) == 0;
+  const size_t tile_bytes = ITEMS * (ka + kb + kc);
+  const uint64_t ntiles = batch / ITEMS;
+  if (aligned && ntiles > 0 && 2 * tile_bytes <= 96 * 1024) {
+    const size_t smem_b = 2 * tile_bytes + 64;
+    FP_CUDA(cudaFuncSetAttribute(k_polymul_word_bulk<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    const int grid_b = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 2);
+    FP_LAUNCH(ctx, "k_polymul_word_bulk", st,
+              k_polymul_word_bulk<W><<<grid_b, 256, smem_b, st>>>(A, B, C, ntiles, ka, kb, P, ctx->d_err));
+    FP_CUDA(cudaGetLastError());
+    const uint64_t done = ntiles * ITEMS;
+    A += done * ka;
+    B += done * kb;
+    C += done * kc;
+    batch -= done;
+    if (batch == 0) return FP_OK;
+  }
   size_t smem = ((TILE * ka + 15) & ~15u) + ((TILE * kb + 15) & ~15u) + TILE * kc;
   int grid = grid_for(ctx, (batch + TILE - 1) / TILE, 8);
   FP_LAUNCH(ctx, "k_polymul_word", st, k_polymul_word<W><<<grid, TILE, smem, st>>>(A, B, C, batch, ka, kb, P, ctx->d_err));

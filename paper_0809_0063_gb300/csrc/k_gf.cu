@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "fpdqt_internal.cuh"
+#include "stream.cuh"
 
 struct fp_gf_s {
   uint32_t p = 0, k = 0, b = 0, c = 0, fb = 0;  // q = 2^b; index bits per residue c; field bits fb
@@ -127,6 +128,35 @@ __global__ void __launch_bounds__(256) k_gf_mul(const E* __restrict__ a, const E
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
     c[i] = (E)gf_mul_one(a[i], b[i], G, sw, sL, sH, P, bad);
   if (bad) flag_error(err, ERR_RANGE);
+}
+
+// The batched multiply on the bulk-copy streaming loop: 4096 pairs per tile.
+template <typename E>
+struct GfOp {
+  static constexpr uint32_t IPT = 16;
+  GfDev G;
+  RedqParams P;
+  const uint64_t* sw;
+  const uint32_t *sL, *sH;
+  uint32_t bad;
+  __device__ __forceinline__ void item(const uint8_t* a, const uint8_t* b, uint8_t* out) {
+    *reinterpret_cast<E*>(out) = (E)gf_mul_one(*reinterpret_cast<const E*>(a), *reinterpret_cast<const E*>(b), G, sw,
+                                               sL, sH, P, bad);
+  }
+};
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_gf_mul_bulk(const E* __restrict__ a, const E* __restrict__ b, E* __restrict__ c,
+                                                     uint64_t ntiles, uint32_t table_bytes, GfDev G, RedqParams P,
+                                                     uint32_t* err) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint64_t* sw;
+  uint32_t *sL, *sH;
+  gf_load_tables(G, sm, sw, sL, sH);
+  GfOp<E> op{G, P, sw, sL, sH, 0};
+  stream_tiles(op, reinterpret_cast<const uint8_t*>(a), reinterpret_cast<const uint8_t*>(b),
+               reinterpret_cast<uint8_t*>(c), ntiles, sizeof(E), sizeof(E), sizeof(E), sm + table_bytes, err);
+  if (op.bad) flag_error(err, ERR_RANGE);
 }
 
 // Segmented form for the serving loop: segment s multiplies count[s] pairs at byte offsets
@@ -274,6 +304,33 @@ extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const
   size_t smem = g->order * sizeof(uint64_t) + 2 * tsz * sizeof(uint32_t);
   int grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)ctx->num_sms * 4);
   GfDev G{g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb};
+  // full tiles of 4096 pairs through the bulk-copy loop, the tail per thread
+  const uint64_t ITEMS = 256 * 16;
+  const bool aligned = ((((uintptr_t)a) | ((uintptr_t)b) | ((uintptr_t)c)) & 15u) == 0;
+  const uint64_t ntiles = aligned ? count / ITEMS : 0;
+  const size_t tbytes = ((smem + 127) / 128) * 128;
+  const size_t smem_b = tbytes + 6 * ITEMS * g->elem_bytes + 64;
+  const uint64_t done = ntiles * ITEMS;
+  if (ntiles) {
+    const int grid_b = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 2);
+    if (g->elem_bytes == 1) {
+      FP_CUDA(cudaFuncSetAttribute(k_gf_mul_bulk<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+      FP_LAUNCH(ctx, "k_gf_mul_bulk", st, k_gf_mul_bulk<uint8_t><<<grid_b, 256, smem_b, st>>>(
+                    (const uint8_t*)a, (const uint8_t*)b, (uint8_t*)c, ntiles, (uint32_t)tbytes, G, g->P, ctx->d_err));
+    } else {
+      FP_CUDA(cudaFuncSetAttribute(k_gf_mul_bulk<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+      FP_LAUNCH(ctx, "k_gf_mul_bulk", st, k_gf_mul_bulk<uint16_t><<<grid_b, 256, smem_b, st>>>(
+                    (const uint16_t*)a, (const uint16_t*)b, (uint16_t*)c, ntiles, (uint32_t)tbytes, G, g->P, ctx->d_err));
+    }
+    FP_CUDA(cudaGetLastError());
+    if (done == count) return FP_OK;
+  }
+  const size_t eb = g->elem_bytes;
+  a = (const uint8_t*)a + done * eb;
+  b = (const uint8_t*)b + done * eb;
+  c = (uint8_t*)c + done * eb;
+  count -= done;
+  grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)ctx->num_sms * 4);
   if (g->elem_bytes == 1) {
     FP_CUDA(cudaFuncSetAttribute(k_gf_mul<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FP_LAUNCH(ctx, "k_gf_mul", st, k_gf_mul<uint8_t><<<grid, 256, smem, st>>>((const uint8_t*)a, (const uint8_t*)b,

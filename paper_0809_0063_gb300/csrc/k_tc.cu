@@ -60,8 +60,9 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait: false (and the abort flag set) if the phase did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag) {
-  for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                          uint32_t limit = TC_WAIT_LIMIT) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try(bar, parity)) return true;
     if ((i & 1023u) == 1023u && *abort_flag) return false;
   }
@@ -497,6 +498,25 @@ __global__ void __launch_bounds__(256) k_tc_redq(const uint32_t* __restrict__ RW
   }
 }
 
+// Self-test of the bounded wait: one warp waits on an mbarrier that nothing will complete,
+// gives up after `polls` polls and reports ERR_TIMEOUT through the context's flag -- the
+// same path the tensor-core kernels take when a TMA or MMA completion never arrives.
+__global__ void k_selftest_wait(uint32_t polls, uint32_t* err) {
+  __shared__ uint64_t bar;
+  __shared__ uint32_t abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!mbar_wait(&bar, 0, &abort_flag, polls)) flag_error(err, ERR_TIMEOUT);
+    mbar_arrive(&bar);   // complete the phase so the barrier is left in a finished state
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- host side
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -590,3 +610,13 @@ fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_
 }
 
 }  // namespace fpd
+
+extern "C" fp_status fp_selftest_bounded_wait(fp_ctx ctx, uint32_t polls, void* stream) {
+  using namespace fpd;
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_selftest_bounded_wait: ctx is NULL");
+  FP_CHECK(polls >= 1 && polls <= (1u << 22), FP_EINVAL, "fp_selftest_bounded_wait: polls in [1, 2^22]");
+  cudaStream_t st = as_stream(stream);
+  FP_LAUNCH(ctx, "k_selftest_wait", st, k_selftest_wait<<<1, 32, 0, st>>>(polls, ctx->d_err));
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
