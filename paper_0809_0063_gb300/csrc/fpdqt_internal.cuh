@@ -209,24 +209,36 @@ __device__ __forceinline__ uint32_t redq_u(uint64_t r, uint64_t s, uint32_t i, c
   return (rr - P.p * ss) & ((P.b >= 32) ? 0xffffffffu : ((1u << P.b) - 1u));
 }
 
+// u_i for words below 2^32 (FP32 / u32 words): one 32-bit shift pair per residue.
+__device__ __forceinline__ uint32_t redq_u32(uint32_t r, uint32_t s, uint32_t i, const RedqParams& P) {
+  const uint32_t sh = i * P.b;
+  const uint32_t rr = sh < 32 ? (r >> sh) : 0u;
+  const uint32_t ss = sh < 32 ? (s >> sh) : 0u;
+  return (rr - P.p * ss) & ((P.b >= 32) ? 0xffffffffu : ((1u << P.b) - 1u));
+}
+
 // Full REDQ_ndig of one word: calls emit(i, mu_i) for i = 0..ndig-1 in increasing order.
 // All 32 lanes of the warp must call this together (shuffle tables); ndig, mode uniform.
 template <typename W, typename Emit>
 __device__ __forceinline__ void redq_word(W rw, const RedqParams& P, const Corrector& C, Emit emit) {
-  uint64_t r = WordOps<W>::to_u64(rw);
-  uint64_t s = WordOps<W>::quot(rw, P);
+  const uint64_t r64 = WordOps<W>::to_u64(rw);
+  const uint64_t s64 = WordOps<W>::quot(rw, P);
+  constexpr bool narrow = sizeof(W) == 4;      // word and quotient fit 32 bits
+  auto U = [&](uint32_t i) -> uint32_t {
+    return narrow ? redq_u32((uint32_t)r64, (uint32_t)s64, i, P) : redq_u(r64, s64, i, P);
+  };
   const uint32_t nd = P.ndig;
   if (P.mode == CORR_NONE) {
-    for (uint32_t i = 0; i < nd; ++i) emit(i, redq_u(r, s, i, P));
+    for (uint32_t i = 0; i < nd; ++i) emit(i, U(i));
     return;
   }
   if (P.mode == CORR_SHFL3) {
     // two residues per lookup (Example tmto with j = 3)
-    uint32_t u0 = redq_u(r, s, 0, P);
+    uint32_t u0 = U(0);
     uint32_t i = 0;
     for (; i + 1 < nd; i += 2) {
-      uint32_t u1 = redq_u(r, s, i + 1, P);
-      uint32_t u2 = (i + 2 < nd) ? redq_u(r, s, i + 2, P) : 0u;
+      uint32_t u1 = U(i + 1);
+      uint32_t u2 = (i + 2 < nd) ? U(i + 2) : 0u;
       uint32_t v = __shfl_sync(0xffffffffu, C.lane_val, u0 + P.p * u1 + P.p * P.p * u2);
       emit(i, v & 0xffu);
       if (i + 2 < nd) {
@@ -239,10 +251,10 @@ __device__ __forceinline__ void redq_word(W rw, const RedqParams& P, const Corre
     if (i < nd) emit(i, u0);   // nd odd: the last one is the top residue
     return;
   }
-  uint32_t u = redq_u(r, s, 0, P);
+  uint32_t u = U(0);
   for (uint32_t i = 0; i < nd; ++i) {
     if (i + 1 < nd) {
-      uint32_t un = redq_u(r, s, i + 1, P);
+      uint32_t un = U(i + 1);
       emit(i, C.pair(u, un, P));
       u = un;
     } else {

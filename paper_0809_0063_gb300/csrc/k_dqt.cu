@@ -51,6 +51,16 @@ __device__ __forceinline__ uint64_t pack_bits(const uint8_t* c, uint32_t k, uint
   }
   return w;
 }
+// The same for packed values below 2^32 (32-bit shifts).
+__device__ __forceinline__ uint32_t pack_bits32(const uint8_t* c, uint32_t k, uint32_t b, uint32_t p, uint32_t& bad) {
+  uint32_t w = 0;
+  for (int j = (int)k - 1; j >= 0; --j) {
+    uint32_t v = c[j];
+    bad |= (v >= p);
+    w = (w << b) | v;
+  }
+  return w;
+}
 
 // ------------------------------------------------------------------ pack
 
@@ -145,13 +155,20 @@ __global__ void __launch_bounds__(TILE) k_polymul_word(const uint8_t* __restrict
 template <typename W>
 struct PolymulWordOp {
   static constexpr uint32_t IPT = 8;
+  static constexpr uint32_t UNROLL = 2;
   uint32_t ka, kb, kc;
   RedqParams P;
   Corrector C;
   uint32_t bad;
   __device__ __forceinline__ void item(const uint8_t* a, const uint8_t* b, uint8_t* out) {
-    W wa = WordOps<W>::from_u64(pack_bits(a, ka, P.b, P.p, bad));
-    W wb = WordOps<W>::from_u64(pack_bits(b, kb, P.b, P.p, bad));
+    W wa, wb;
+    if (sizeof(W) == 4) {
+      wa = WordOps<W>::from_u64(pack_bits32(a, ka, P.b, P.p, bad));
+      wb = WordOps<W>::from_u64(pack_bits32(b, kb, P.b, P.p, bad));
+    } else {
+      wa = WordOps<W>::from_u64(pack_bits(a, ka, P.b, P.p, bad));
+      wb = WordOps<W>::from_u64(pack_bits(b, kb, P.b, P.p, bad));
+    }
     W r = wa * wb;
     redq_word<W>(r, P, C, [&](uint32_t i, uint32_t mu) { out[i] = (uint8_t)mu; });
   }

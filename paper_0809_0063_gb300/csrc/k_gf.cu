@@ -73,6 +73,7 @@ struct GfDev {
   const uint32_t* L;
   const uint32_t* H;
   uint32_t order, k, cbits, fb;
+  uint32_t ones;   // one bit at the bottom of each of the k fields of fb bits
 };
 
 // Shared copies of the three tables (word table, L, H) for one block.
@@ -97,19 +98,21 @@ __device__ __forceinline__ uint32_t gf_mul_one(uint32_t xa, uint32_t xb, const G
   xb = xb < G.order ? xb : 0u;
   const uint64_t r = sw[xa] * sw[xb];             // lines 1-2
   const uint64_t s = divp64(r, P.dv);             // REDQ compression quotient (line 3)
+  const uint32_t rl = (uint32_t)r, rh = (uint32_t)(r >> 32);
+  const uint32_t sl = (uint32_t)s, shh = (uint32_t)(s >> 32);
   const uint32_t qmask = (1u << bq) - 1u;
   uint32_t il = 0, ih = 0;
-  for (uint32_t j = 0; j < 2 * k - 1; ++j) {
-    const uint32_t sh = j * bq;
-    const uint32_t uj = ((uint32_t)(r >> sh) - p * (uint32_t)(s >> sh)) & qmask;
+  for (uint32_t j = 0, sh = 0; j < 2 * k - 1; ++j, sh += bq) {
+    // low 32 bits of r >> sh and s >> sh by funnel shifts (only the low bq bits matter)
+    const uint32_t rr = sh < 32 ? __funnelshift_r(rl, rh, sh) : (rh >> (sh - 32));
+    const uint32_t ss = sh < 32 ? __funnelshift_r(sl, shh, sh) : (shh >> (sh - 32));
+    const uint32_t uj = (rr - p * ss) & qmask;
     if (j < k) il |= uj << (j * cbits);
-    if (j >= k - 1) ih |= uj << ((j - (k - 1)) * cbits);
+    if (j + 1 >= k) ih |= uj << ((j + 1 - k) * cbits);
   }
-  uint32_t ones = 0;
-  for (uint32_t i = 0; i < k; ++i) ones |= 1u << (i * fb);
   const uint32_t hb = fb - 1;                     // bit tested after adding 2^hb - p per field
   uint32_t x = sL[il] + sH[ih];                    // lines 4-6: two lookups, one field add
-  const uint32_t ge = ((x + ((1u << hb) - p) * ones) >> hb) & ones;
+  const uint32_t ge = ((x + ((1u << hb) - p) * G.ones) >> hb) & G.ones;
   x -= p * ge;
   const uint32_t fmask = (1u << fb) - 1u;
   uint32_t idx = 0;
@@ -125,8 +128,16 @@ __global__ void __launch_bounds__(256) k_gf_mul(const E* __restrict__ a, const E
   uint32_t *sL, *sH;
   gf_load_tables(G, sm, sw, sL, sH);
   uint32_t bad = 0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
-    c[i] = (E)gf_mul_one(a[i], b[i], G, sw, sL, sH, P, bad);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  for (; i + stride < count; i += 2 * stride) {   // two independent products per trip (ILP)
+    const uint32_t x0 = a[i], y0 = b[i], x1 = a[i + stride], y1 = b[i + stride];
+    const uint32_t r0 = gf_mul_one(x0, y0, G, sw, sL, sH, P, bad);
+    const uint32_t r1 = gf_mul_one(x1, y1, G, sw, sL, sH, P, bad);
+    c[i] = (E)r0;
+    c[i + stride] = (E)r1;
+  }
+  if (i < count) c[i] = (E)gf_mul_one(a[i], b[i], G, sw, sL, sH, P, bad);
   if (bad) flag_error(err, ERR_RANGE);
 }
 
@@ -134,6 +145,7 @@ __global__ void __launch_bounds__(256) k_gf_mul(const E* __restrict__ a, const E
 template <typename E>
 struct GfOp {
   static constexpr uint32_t IPT = 16;
+  static constexpr uint32_t UNROLL = 4;
   GfDev G;
   RedqParams P;
   const uint64_t* sw;
@@ -303,7 +315,8 @@ extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const
   const uint32_t tsz = 1u << (g->c * g->k);
   size_t smem = g->order * sizeof(uint64_t) + 2 * tsz * sizeof(uint32_t);
   int grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)ctx->num_sms * 4);
-  GfDev G{g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb};
+  GfDev G{g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb, 0};
+  for (uint32_t i = 0; i < g->k; ++i) G.ones |= 1u << (i * g->fb);
   // full tiles of 4096 pairs through the bulk-copy loop, the tail per thread
   const uint64_t ITEMS = 256 * 16;
   const bool aligned = ((((uintptr_t)a) | ((uintptr_t)b) | ((uintptr_t)c)) & 15u) == 0;
@@ -349,7 +362,8 @@ namespace fpd {
 fp_status gf_launch_segments(fp_ctx ctx, fp_gf g, uint8_t* base, const void* segs, uint32_t nseg, cudaStream_t st) {
   const uint32_t tsz = 1u << (g->c * g->k);
   size_t smem = g->order * sizeof(uint64_t) + 2 * tsz * sizeof(uint32_t);
-  GfDev G{g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb};
+  GfDev G{g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb, 0};
+  for (uint32_t i = 0; i < g->k; ++i) G.ones |= 1u << (i * g->fb);
   const int grid = (int)std::min<uint32_t>(nseg, (uint32_t)ctx->num_sms * 4);
   if (g->elem_bytes == 1) {
     FP_CUDA(cudaFuncSetAttribute(k_gf_mul_seg<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -141,10 +141,19 @@ __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.syn
 
 // ---------------------------------------------------------------- operand conversion
 
-__device__ __forceinline__ uint16_t to16(uint32_t v, int mode, uint32_t p) {
-  if (mode == 0) return __bfloat16_as_ushort(__float2bfloat16_rn((float)v));
-  float c = (p == 3 && v == 2) ? -1.0f : (float)v;        // centred residue
-  return __half_as_ushort(__float2half_rn(c));
+// bf16 bits of a residue v <= 255: the float 2^23 + v has v in its low mantissa bits, so
+// subtracting 2^23 gives float(v) exactly; its top 16 bits are the bf16 (exact, 8 bits).
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t v0, uint32_t v1) {
+  const float f0 = __uint_as_float(0x4B000000u | v0) - 8388608.0f;
+  const float f1 = __uint_as_float(0x4B000000u | v1) - 8388608.0f;
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+// fp16 bits of a centred residue of p = 3 ({0,1,2} -> {0,1,-1}) and of a packed pair
+// c(v0) + 2^10 c(v1): 9 possible values, looked up from (v0, v1).
+__device__ __forceinline__ uint32_t h16_centred(uint32_t v) { return v == 0 ? 0u : (v == 1 ? 0x3C00u : 0xBC00u); }
+__device__ __forceinline__ uint32_t h16_pair_word(uint32_t v0, uint32_t v1) {
+  const float c0 = v0 == 2 ? -1.0f : (float)v0, c1 = v1 == 2 ? -1.0f : (float)v1;
+  return __half_as_ushort(__float2half_rn(fmaf(1024.0f, c1, c0)));
 }
 
 // A16[r][c] (m x kp, zero padded) = 16-bit form of A[r][c]; one thread per 16 columns.
@@ -154,86 +163,112 @@ __global__ void __launch_bounds__(256) k_tc_convert_a(const uint8_t* __restrict_
   const int chunks = kp >> 4;
   uint32_t bad = 0;
   const bool vec = (((uintptr_t)A) & 15u) == 0 && (lda & 15) == 0;
-  // blocks walk rows, threads walk the 16-column chunks of a row
   for (int r = blockIdx.x; r < m; r += gridDim.x)
-  for (int ch = threadIdx.x; ch < chunks; ch += blockDim.x) {
-    const int c0 = ch * 16;
-    uint8_t b[16];
-    const uint8_t* src = A + (size_t)r * lda + c0;
-    if (vec && c0 + 16 <= k) {
-      uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
-      memcpy(b, &x, 16);
-    } else {
+    for (int ch = threadIdx.x; ch < chunks; ch += blockDim.x) {
+      const int c0 = ch * 16;
+      uint32_t w[4];
+      const uint8_t* src = A + (size_t)r * lda + c0;
+      if (vec && c0 + 16 <= k) {
+        uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
+        w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+      } else {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) b[j] = c0 + j < k ? src[j] : 0;
-    }
-    uint32_t o[8];
+        for (int q = 0; q < 4; ++q) {
+          uint32_t t = 0;
 #pragma unroll
-    for (int j = 0; j < 16; j += 2) {
-      bad |= (b[j] >= p) | (b[j + 1] >= p);
-      o[j >> 1] = (uint32_t)to16(b[j], mode, p) | ((uint32_t)to16(b[j + 1], mode, p) << 16);
+          for (int j = 0; j < 4; ++j) t |= (uint32_t)(c0 + 4 * q + j < k ? src[4 * q + j] : 0) << (8 * j);
+          w[q] = t;
+        }
+      }
+      const uint32_t pp = 0x01010101u * p;
+      bad |= __vcmpgeu4(w[0], pp) | __vcmpgeu4(w[1], pp) | __vcmpgeu4(w[2], pp) | __vcmpgeu4(w[3], pp);
+      uint32_t o[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t x = w[q];
+        const uint32_t b0 = x & 0xffu, b1 = (x >> 8) & 0xffu, b2 = (x >> 16) & 0xffu, b3 = x >> 24;
+        if (mode == 0) {
+          o[2 * q] = bf16_pair(b0, b1);
+          o[2 * q + 1] = bf16_pair(b2, b3);
+        } else {
+          o[2 * q] = h16_centred(b0) | (h16_centred(b1) << 16);
+          o[2 * q + 1] = h16_centred(b2) | (h16_centred(b3) << 16);
+        }
+      }
+      uint4* d = reinterpret_cast<uint4*>(dst + (size_t)r * kp + c0);
+      d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+      d[1] = make_uint4(o[4], o[5], o[6], o[7]);
     }
-    uint4* d = reinterpret_cast<uint4*>(dst + (size_t)r * kp + c0);
-    d[0] = make_uint4(o[0], o[1], o[2], o[3]);
-    d[1] = make_uint4(o[4], o[5], o[6], o[7]);
-  }
   if (bad) flag_error(err, ERR_RANGE);
 }
 
-// B16[w][c] (nw x kp, zero padded) from B (k x n): a 64 x 64 tile of B per block is staged
-// in shared memory and written transposed with 16-byte stores.  mode 0: bf16 of B[c][w]
+// B16 (nw x kp, zero padded) from B (k x n): a 64 (k) x 64 (n) tile of B per block is staged
+// in shared memory as 32-bit words; each thread transposes one 4 x 4 byte block in registers
+// (__byte_perm) and writes 4 k-values for each of its 4 columns.  mode 0: bf16 of B[c][w]
 // (nw = n); mode 2: fp16 of the centred pair B[c][2w] + 2^10 B[c][2w+1] (nw = ceil(n/2)).
 __global__ void __launch_bounds__(256) k_tc_convert_b(const uint8_t* __restrict__ B, int ldb, uint16_t* __restrict__ dst,
                                                       int k, int n, int nw, int kp, int mode, uint32_t p, uint32_t* err) {
-  __shared__ uint8_t tile[64][64 + 16];
-  const int c0 = blockIdx.x * 64;                  // k offset
-  const int n0 = blockIdx.y * 64;                  // B column offset
+  __shared__ uint32_t tile[64][17];                 // 64 rows (k) x 64 bytes (n), row stride 17 words
+  const int c0 = blockIdx.x * 64;                   // k offset
+  const int n0 = blockIdx.y * 64;                   // B column offset
   const int t = threadIdx.x;
   uint32_t bad = 0;
   {
-    const int rr = t >> 2, cc = (t & 3) * 16;      // 64 rows (k) x 4 chunks of 16 columns
+    const int rr = t >> 2, cc = (t & 3) * 16;       // 64 rows x 4 chunks of 16 columns
     const int kr = c0 + rr, col = n0 + cc;
-    uint8_t b[16];
+    uint32_t w[4];
     const uint8_t* src = B + (size_t)kr * ldb + col;
     if (kr < k && col + 16 <= n && (((uintptr_t)src) & 15u) == 0) {
       uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
-      memcpy(b, &x, 16);
+      w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
     } else {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) b[j] = (kr < k && col + j < n) ? src[j] : 0;
-    }
+      for (int q = 0; q < 4; ++q) {
+        uint32_t v = 0;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      bad |= b[j] >= p;
-      tile[rr][cc + j] = b[j];
+        for (int j = 0; j < 4; ++j) v |= (uint32_t)((kr < k && col + 4 * q + j < n) ? src[4 * q + j] : 0) << (8 * j);
+        w[q] = v;
+      }
+    }
+    const uint32_t pp = 0x01010101u * p;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      bad |= __vcmpgeu4(w[q], pp);
+      tile[rr][(cc >> 2) + q] = w[q];
     }
   }
   __syncthreads();
-  // output rows: 64 (mode 0) or 32 (mode 2) words, each 64 k-values = 128 bytes = 8 x 16 B
-  const int wrows = mode == 2 ? 32 : 64;
-  const int w0 = mode == 2 ? n0 / 2 : n0;
-  for (int id = t; id < wrows * 8; id += 256) {
-    const int wr = id >> 3, seg = (id & 7) * 8;    // 8 k-values per 16-byte store
-    const int w = w0 + wr;
-    if (w >= nw || c0 + seg >= kp) continue;
-    uint32_t o[4];
+  const int bk = t & 15, bn = t >> 4;               // 4 x 4 block: k rows 4bk.., columns 4bn..
+  const uint32_t r0 = tile[4 * bk][bn], r1 = tile[4 * bk + 1][bn], r2 = tile[4 * bk + 2][bn], r3 = tile[4 * bk + 3][bn];
+  // transpose: column j gathers byte j of r0..r3 (k order)
+  const uint32_t lo01 = __byte_perm(r0, r1, 0x5140), hi01 = __byte_perm(r0, r1, 0x7362);
+  const uint32_t lo23 = __byte_perm(r2, r3, 0x5140), hi23 = __byte_perm(r2, r3, 0x7362);
+  uint32_t col[4];
+  col[0] = __byte_perm(lo01, lo23, 0x5410);         // bytes: r0[0] r1[0] r2[0] r3[0]
+  col[1] = __byte_perm(lo01, lo23, 0x7632);         // r0[1] r1[1] r2[1] r3[1]
+  col[2] = __byte_perm(hi01, hi23, 0x5410);
+  col[3] = __byte_perm(hi01, hi23, 0x7632);
+  const int kk = c0 + 4 * bk;                      // < kp: the grid covers kp / 64 tiles
+  if (mode == 0) {
 #pragma unroll
-    for (int j = 0; j < 8; j += 2) {
-      uint16_t h[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int kk = seg + j + q;
-        if (mode == 2) {
-          uint32_t v0 = tile[kk][2 * wr], v1 = tile[kk][2 * wr + 1];
-          float c = ((p == 3 && v0 == 2) ? -1.0f : (float)v0) + 1024.0f * ((p == 3 && v1 == 2) ? -1.0f : (float)v1);
-          h[q] = __half_as_ushort(__float2half_rn(c));
-        } else {
-          h[q] = to16(tile[kk][wr], 0, p);
-        }
-      }
-      o[j >> 1] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+    for (int j = 0; j < 4; ++j) {
+      const int w = n0 + 4 * bn + j;
+      if (w >= nw) break;
+      const uint32_t x = col[j];
+      uint2 o = make_uint2(bf16_pair(x & 0xffu, (x >> 8) & 0xffu), bf16_pair((x >> 16) & 0xffu, x >> 24));
+      *reinterpret_cast<uint2*>(dst + (size_t)w * kp + kk) = o;
     }
-    *reinterpret_cast<uint4*>(dst + (size_t)w * kp + c0 + seg) = make_uint4(o[0], o[1], o[2], o[3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int w = n0 / 2 + 2 * bn + j;
+      if (w >= nw) break;
+      const uint32_t x0 = col[2 * j], x1 = col[2 * j + 1];   // columns 2w and 2w+1
+      uint32_t h[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) h[q] = h16_pair_word((x0 >> (8 * q)) & 0xffu, (x1 >> (8 * q)) & 0xffu);
+      *reinterpret_cast<uint2*>(dst + (size_t)w * kp + kk) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+    }
   }
   if (bad) flag_error(err, ERR_RANGE);
 }
@@ -463,6 +498,7 @@ __global__ void __launch_bounds__(256) k_tc_redq(const uint32_t* __restrict__ RW
   corr.init(P, ptab);
   const int groups = (nw + 7) / 8;
   const int gblocks = (groups + (int)blockDim.x - 1) / (int)blockDim.x;   // blocks of threads per row
+#pragma unroll 2
   for (int rb = blockIdx.x; rb < m * gblocks; rb += gridDim.x) {
     const int r = rb / gblocks, g = (rb - r * gblocks) * (int)blockDim.x + (int)threadIdx.x;
     const bool own = g < groups;

@@ -103,7 +103,7 @@ __device__ void stream_tiles(Op& op, const uint8_t* __restrict__ A, const uint8_
     }
     __syncthreads();
     if (s_abort) break;
-#pragma unroll 1
+#pragma unroll Op::UNROLL
     for (uint32_t j = 0; j < Op::IPT; ++j) {
       const uint32_t it = j * 256 + tid;
       op.item(inA[buf] + it * sa, inB[buf] + it * sb, out[buf] + it * so);
