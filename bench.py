@@ -445,6 +445,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the per-variant comparison block")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--problems", default="", help="subset, e.g. 3:4096,7:1024 (default: all four)")
+    ap.add_argument("--no-graph", action="store_true", help="time plain launches instead of CUDA-graph replays")
     ap.add_argument("--no-autotune", action="store_true",
                     help="AUTO uses the fixed rule instead of timing candidates (for runs under a profiler)")
     ap.add_argument("--min-warmup-s", type=float, default=1.0,
@@ -524,6 +525,32 @@ def main():
         if nw_steps % 8 == 0:
             torch.cuda.synchronize()
     torch.cuda.synchronize()
+    # the step as one CUDA graph: every library call is capture-safe once warm (no host syncs,
+    # no scratch growth, AUTO choices cached), so a step replays all its kernels with one launch
+    graph = None
+    launches_per_step = None
+    if not args.no_graph:
+        l_a = fp.fp_ctx_launches(ctx)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        launches_per_step = fp.fp_ctx_launches(ctx) - l_a
+        graph.replay()
+        torch.cuda.synchronize()
+        fp.fp_ctx_status(ctx)
+        for q in prob:   # parity of the replayed graph
+            rows = np.array([2, q["n"] - 3])
+            assert np.array_equal(q["C"][rows].cpu().numpy(), field.matmul_mod_rows(q["a"], q["b"], q["p"], rows))
+    run_step = graph.replay if graph is not None else step
+    # plain launches timed too (reported beside the graph number)
+    ev0 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev0[i][0].record(stream)
+        step()
+        ev0[i][1].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = sum(a.elapsed_time(b) for a, b in ev0)
     if ws > 1:
         torch.distributed.barrier()
     l0 = fp.fp_ctx_launches(ctx)
@@ -533,17 +560,28 @@ def main():
     for i in range(args.steps):
         flush.zero_()                   # L2 flushed between steps (outside the events)
         ev[i][0].record(stream)
-        step()
+        run_step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     clk.__exit__(None, None, None)
     fp.fp_ctx_profile(ctx, 0)
     fp.fp_ctx_status(ctx)
     launches = fp.fp_ctx_launches(ctx) - l0
+    if graph is not None:          # graph replays do not pass through the library's counter
+        launches = launches_per_step * args.steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), dev)
     value = whole_job_rate(macs_per_step, args.steps, ws, total_ms)
 
+    if graph is not None:
+        # per-kernel events need the library's own launches: one profiled pass of plain steps
+        fp.fp_ctx_profile(ctx, 2)
+        fp.fp_ctx_profile(ctx, 1)
+        for i in range(args.steps):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        fp.fp_ctx_profile(ctx, 0)
     # dominant kernel and its roofline from the library's own per-launch events
     dominant, dom_ms, dom_n = None, 0.0, 0
     for name in ktab:
@@ -583,12 +621,33 @@ def main():
     h2d = sum(q["a"].nbytes + q["b"].nbytes for q in prob)
     d2h = sum(q["n"] * q["n"] for q in prob)
 
+    # three streams: host-to-device copies, compute, device-to-host copies; problem i computes
+    # as soon as its inputs have landed while later inputs are still in flight
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in prob]
+    ev_c = [torch.cuda.Event() for _ in prob]
+
     def e2e_step():
+        start = torch.cuda.Event()
+        start.record(stream)
+        s_in.wait_event(start)
+        with torch.cuda.stream(s_in):
+            for i, q in enumerate(prob):
+                q["A"].copy_(hA[i], non_blocking=True)
+                q["B"].copy_(hB[i], non_blocking=True)
+                ev_in[i].record(s_in)
         for i, q in enumerate(prob):
-            q["A"].copy_(hA[i], non_blocking=True)
-            q["B"].copy_(hB[i], non_blocking=True)
-            fp.fp_matmul(ctx, q["p"], q["n"], q["n"], q["n"], q["A"], q["n"], q["B"], q["n"], q["C"], q["n"], algo)
-            hC[i].copy_(q["C"], non_blocking=True)
+            stream.wait_event(ev_in[i])
+            fp.fp_matmul(ctx, q["p"], q["n"], q["n"], q["n"], q["A"], q["n"], q["B"], q["n"], q["C"], q["n"], algo,
+                         stream=stream)
+            ev_c[i].record(stream)
+        with torch.cuda.stream(s_out):
+            for i, q in enumerate(prob):
+                s_out.wait_event(ev_c[i])
+                hC[i].copy_(q["C"], non_blocking=True)
+        done = torch.cuda.Event()
+        done.record(s_out)
+        stream.wait_event(done)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -657,6 +716,8 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "F_p MAC/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
+            "timing": "CUDA graph replay of the step" if graph is not None else "plain launches",
+            "value_plain_launches": whole_job_rate(macs_per_step, args.steps, ws, max_over_ranks(plain_ms, dev)),
             "clocks": clk.summary(),
             "compare_same_inputs": compare,
         }
