@@ -512,7 +512,7 @@ def main():
     for q in prob:
         a = fp.fp_ctx_autotune_choice(ctx, q["p"], q["n"], q["n"], q["n"]) if args.algo == "AUTO" else algo
         if a < 0 and args.algo == "AUTO":       # fixed rule (autotuning off): first exact candidate
-            a = fp.FP_MM_RIGHT_TC if (q["p"] <= 3 and q["n"] >= 2048) else fp.FP_MM_PLAIN_TC
+            a = fp.FP_MM_PLAIN_F8 if q["p"] <= 17 else fp.FP_MM_PLAIN_TC
         chosen[(q["p"], q["n"])] = a if a >= 0 else algo
     names = {getattr(fp, k): k[6:] for k in dir(fp) if k.startswith("FP_MM_")}
     clk = Clocks(local).__enter__()
@@ -594,7 +594,9 @@ def main():
         flops = 0.0
         units = 0
         kernel_of = {"RIGHT_F32": "k_mm_ffma", "PLAIN_F32": "k_mm_ffma", "RIGHT_F64": "k_mm_dmma",
-                     "PLAIN_F64": "k_mm_dmma", "PLAIN_I8": "k_mm_imma", "PLAIN_TC": "k_mm_tc", "RIGHT_TC": "k_mm_tc"}
+                     "PLAIN_F64": "k_mm_dmma", "PLAIN_I8": "k_mm_imma", "PLAIN_TC": "k_mm_tc", "RIGHT_TC": "k_mm_tc",
+                     "PLAIN_F8": "k_mm_tc"}
+        ideal_s = 0.0   # sum over launches of flops / (that launch's own peak): mixed dtypes
         for p, n in PROBLEMS:
             an = names[chosen[(p, n)]]
             if kernel_of.get(an) != dominant:
@@ -605,10 +607,16 @@ def main():
                 e = 2
             else:
                 e = 1
-            flops += flops_fn(n, e)
+            f = flops_fn(n, e) * args.steps
+            flops += f / args.steps
             units += n ** 3
+            ideal_s += f / ((2.0 * bf16 if an == "PLAIN_F8" else peak) * 1e12)
         flops *= args.steps
         achieved = flops / (dom_ms / 1e3) / 1e12
+        if dominant == "k_mm_tc":       # fp8 launches count against the fp8 peak (2 x bf16, nominal ratio)
+            peak = flops / 1e12 / ideal_s
+            if all(names[a] == "PLAIN_F8" for a in chosen.values()):
+                peak_label = "fp8 = measured bf16 x 2 (nominal 4.5/2.25)"
         traffic = stored_traffic(dominant, units / max(1, dom_n / args.steps))
         roof = {"bound": bound, "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_label + f" ({peak_src})",
@@ -670,7 +678,7 @@ def main():
     compare = None
     if not args.no_compare and rank == 0:
         compare = {}
-        for name in ["RIGHT_F32", "PLAIN_F32", "RIGHT_F64", "PLAIN_F64", "PLAIN_I8", "PLAIN_TC", "RIGHT_TC"]:
+        for name in ["RIGHT_F32", "PLAIN_F32", "RIGHT_F64", "PLAIN_F64", "PLAIN_I8", "PLAIN_TC", "RIGHT_TC", "PLAIN_F8"]:
             row = {}
             for q in prob:
                 al = getattr(fp, "FP_MM_" + name)
@@ -700,7 +708,7 @@ def main():
                "sample": f"{sample} ({secs:.1f} s, numpy int64 matmul + % p, single thread)"}
 
     dt_of = {"RIGHT_F32": "f32", "PLAIN_F32": "f32", "RIGHT_F64": "f64", "PLAIN_F64": "f64",
-             "PLAIN_I8": "u8", "PLAIN_TC": "bf16", "RIGHT_TC": "f16"}
+             "PLAIN_I8": "u8", "PLAIN_TC": "bf16", "RIGHT_TC": "f16", "PLAIN_F8": "e4m3"}
     dtype = "/".join(sorted({dt_of[names[a]] for a in chosen.values()}))
     if rank == 0:
         out = {

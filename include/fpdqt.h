@@ -71,7 +71,9 @@ enum {
   FP_MM_PLAIN_TC = 6,   /* unpacked, tcgen05 kind::f16 (bf16 operands, fp32 accumulate) */
   FP_MM_RIGHT_TC = 7,   /* right compression on tcgen05 kind::f16: fp16 operands holding two
                            centred residues at Q = 2^10, inner dimension chunked (p <= 3) */
-  FP_MM_LEFT_F32 = 8    /* left compression (Sec. 7.4, by transposition), FP32 words */
+  FP_MM_LEFT_F32 = 8,   /* left compression (Sec. 7.4, by transposition), FP32 words */
+  FP_MM_PLAIN_F8 = 9    /* unpacked, tcgen05 kind::f8f6f4 (e4m3 operands, exact for residues
+                           <= 16), fp32 accumulate: p <= 17 and k (p-1)^2 < 2^24 */
 };
 
 /* Parameters of one packed representation (Sec. 2.3): q = 2^b, k residues packed per

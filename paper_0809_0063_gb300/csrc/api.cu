@@ -438,7 +438,7 @@ extern "C" fp_status fp_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, cons
            FP_EINVAL, "fp_matmul: sizes m=%d n=%d k=%d outside [1, 2^20]", m, n, k);
   FP_CHECK(lda >= k && ldb >= n && ldc >= n, FP_EINVAL, "fp_matmul: leading dimensions too small");
   FP_CHECK(A && B && C, FP_EINVAL, "fp_matmul: null array");
-  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_LEFT_F32, FP_EINVAL, "bad algo %d", algo);
+  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_PLAIN_F8, FP_EINVAL, "bad algo %d", algo);
   return launch_matmul(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, algo, as_stream(stream));
 }
 

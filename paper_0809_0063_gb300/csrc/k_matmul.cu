@@ -514,6 +514,7 @@ static fp_status run_algo(fp_ctx ctx, uint32_t p, int m, int n, int k, const uin
     case FP_MM_PLAIN_F32: return mm_ffma(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, true, st);
     case FP_MM_PLAIN_I8: return mm_imma(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, st);
     case FP_MM_PLAIN_TC:
+    case FP_MM_PLAIN_F8:
     case FP_MM_RIGHT_TC: return launch_mm_tc(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, algo, st);
     default:
       set_error("fp_matmul: algorithm %d not available", algo);
@@ -528,6 +529,7 @@ static int candidates(uint32_t p, int m, int n, int k, int* out) {
   uint64_t pp = (uint64_t)(p - 1) * (p - 1);
   int c = 0;
   bool big = (uint64_t)m * n >= (uint64_t)2048 * 2048;
+  if (p <= 17 && (uint64_t)k * pp < (1ull << 24)) out[c++] = FP_MM_PLAIN_F8;
   if (p <= 3 && k <= 32767 && big) out[c++] = FP_MM_RIGHT_TC;
   if ((uint64_t)k * pp < (1ull << 24)) out[c++] = FP_MM_PLAIN_TC;
   if (p <= 3 && k <= 32767 && !big) out[c++] = FP_MM_RIGHT_TC;

@@ -110,6 +110,18 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// kind::f8f6f4 with e4m3 A and B (format code 0), fp32 accumulate.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                : "memory");
@@ -273,9 +285,104 @@ __global__ void __launch_bounds__(256) k_tc_convert_b(const uint8_t* __restrict_
   if (bad) flag_error(err, ERR_RANGE);
 }
 
+// e4m3 bits of a residue v <= 16 (exact): exponent floor(log2 v) + 7, three mantissa bits.
+__device__ __forceinline__ uint32_t e4m3_of(uint32_t v) {
+  if (v == 0) return 0u;
+  const uint32_t e = 31u - __clz(v);
+  return ((e + 7u) << 3) | (((v << 3) >> e) & 7u);
+}
+__device__ __forceinline__ uint32_t e4m3_word(uint32_t x) {   // four bytes at once
+  return e4m3_of(x & 0xffu) | (e4m3_of((x >> 8) & 0xffu) << 8) | (e4m3_of((x >> 16) & 0xffu) << 16) |
+         (e4m3_of(x >> 24) << 24);
+}
+
+// A8[r][c] (m x kp, zero padded) = e4m3 of A[r][c]; one thread per 16 columns.
+__global__ void __launch_bounds__(256) k_tc_convert_a8(const uint8_t* __restrict__ A, int lda, uint8_t* __restrict__ dst,
+                                                       int m, int k, int kp, uint32_t p, uint32_t* err) {
+  const int chunks = kp >> 4;
+  uint32_t bad = 0;
+  const bool vec = (((uintptr_t)A) & 15u) == 0 && (lda & 15) == 0;
+  for (int r = blockIdx.x; r < m; r += gridDim.x)
+    for (int ch = threadIdx.x; ch < chunks; ch += blockDim.x) {
+      const int c0 = ch * 16;
+      uint32_t w[4];
+      const uint8_t* src = A + (size_t)r * lda + c0;
+      if (vec && c0 + 16 <= k) {
+        uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
+        w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint32_t t = 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) t |= (uint32_t)(c0 + 4 * q + j < k ? src[4 * q + j] : 0) << (8 * j);
+          w[q] = t;
+        }
+      }
+      const uint32_t pp = 0x01010101u * p;
+      bad |= __vcmpgeu4(w[0], pp) | __vcmpgeu4(w[1], pp) | __vcmpgeu4(w[2], pp) | __vcmpgeu4(w[3], pp);
+      *reinterpret_cast<uint4*>(dst + (size_t)r * kp + c0) =
+          make_uint4(e4m3_word(w[0]), e4m3_word(w[1]), e4m3_word(w[2]), e4m3_word(w[3]));
+    }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// B8 (n x kp, zero padded) = e4m3 of B transposed: 64 (k) x 64 (n) tiles, 4 x 4 byte blocks
+// transposed in registers, 4 k-values per column written as one 32-bit store.
+__global__ void __launch_bounds__(256) k_tc_convert_b8(const uint8_t* __restrict__ B, int ldb, uint8_t* __restrict__ dst,
+                                                       int k, int n, int kp, uint32_t p, uint32_t* err) {
+  __shared__ uint32_t tile[64][17];
+  const int c0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+  const int t = threadIdx.x;
+  uint32_t bad = 0;
+  {
+    const int rr = t >> 2, cc = (t & 3) * 16;
+    const int kr = c0 + rr, col = n0 + cc;
+    uint32_t w[4];
+    const uint8_t* src = B + (size_t)kr * ldb + col;
+    if (kr < k && col + 16 <= n && (((uintptr_t)src) & 15u) == 0) {
+      uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
+      w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v |= (uint32_t)((kr < k && col + 4 * q + j < n) ? src[4 * q + j] : 0) << (8 * j);
+        w[q] = v;
+      }
+    }
+    const uint32_t pp = 0x01010101u * p;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      bad |= __vcmpgeu4(w[q], pp);
+      tile[rr][(cc >> 2) + q] = w[q];
+    }
+  }
+  __syncthreads();
+  const int bk = t & 15, bn = t >> 4;
+  const uint32_t r0 = tile[4 * bk][bn], r1 = tile[4 * bk + 1][bn], r2 = tile[4 * bk + 2][bn], r3 = tile[4 * bk + 3][bn];
+  const uint32_t lo01 = __byte_perm(r0, r1, 0x5140), hi01 = __byte_perm(r0, r1, 0x7362);
+  const uint32_t lo23 = __byte_perm(r2, r3, 0x5140), hi23 = __byte_perm(r2, r3, 0x7362);
+  uint32_t col[4];
+  col[0] = __byte_perm(lo01, lo23, 0x5410);
+  col[1] = __byte_perm(lo01, lo23, 0x7632);
+  col[2] = __byte_perm(hi01, hi23, 0x5410);
+  col[3] = __byte_perm(hi01, hi23, 0x7632);
+  const int kk = c0 + 4 * bk;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int w = n0 + 4 * bn + j;
+    if (w >= n) break;
+    *reinterpret_cast<uint32_t*>(dst + (size_t)w * kp + kk) = e4m3_word(col[j]);
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
 // ---------------------------------------------------------------- the GEMM kernel
 
-template <bool PACKED>
+// MODE 0: bf16 plain, 1: fp16 packed (two centred residues per word), 2: e4m3 plain.
+template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_mm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, uint8_t* __restrict__ C,
             int ldc, uint32_t* __restrict__ RW, int m, int n, int nw, int ktiles, RedqParams P, uint32_t koffset,
@@ -292,6 +399,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   volatile uint32_t* abort_flag = tmem_slot + 1;
   __shared__ uint8_t ptab[1024];
 
+  constexpr bool PACKED = MODE == 1;
+  constexpr int KT_ELEMS = MODE == 2 ? 128 : 64;   // elements per 128-byte k-tile row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
   constexpr uint32_t TMEM_COLS = PACKED ? 512 : 256;
@@ -333,8 +442,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint8_t* sa = smem + s * TC_STAGE_BYTES;
         uint8_t* sb = sa + TC_A_BYTES;
         mbar_expect_tx(&full[s], TC_STAGE_BYTES);
-        tma_load_2d(sa, &tmA, kt * TC_BK, m0, &full[s]);
-        tma_load_2d(sb, &tmB, kt * TC_BK, n0, &full[s]);
+        tma_load_2d(sa, &tmA, kt * KT_ELEMS, m0, &full[s]);
+        tma_load_2d(sb, &tmB, kt * KT_ELEMS, n0, &full[s]);
         armed = kt + 1;
       }
       // every armed stage must have landed before the CTA may exit (its shared memory is reused)
@@ -345,7 +454,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_f16(PACKED ? 0u : 1u, TC_BM, TC_BN);
+      constexpr uint32_t idesc = MODE == 2 ? idesc_e4m3(TC_BM, TC_BN) : idesc_f16(PACKED ? 0u : 1u, TC_BM, TC_BN);
       int kt = 0;
       for (int c = 0; c < nchunks && !*abort_flag; ++c) {
         const int buf = c & 1;
@@ -362,9 +471,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint8_t* sb = sa + TC_A_BYTES;
           const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sb);
 #pragma unroll
-          for (int kk = 0; kk < TC_BK / 16; ++kk) {
-            // advance 16 elements (32 bytes) along K inside the swizzled 128-byte rows
-            mma_f16(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, first ? 0u : 1u);
+          for (int kk = 0; kk < 4; ++kk) {
+            // advance 32 bytes along K inside the swizzled 128-byte rows (16 x 16-bit or 32 x fp8)
+            if (MODE == 2) mma_f8(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, first ? 0u : 1u);
+            else mma_f16(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, first ? 0u : 1u);
             first = false;
           }
           mma_commit(&empty[s]);    // stage s free once these MMAs have read it
@@ -573,15 +683,18 @@ static EncodeTiledFn get_encode() {
   return fn;
 }
 
-// 2-D map of a rows x kp 16-bit row-major matrix, box = box_rows x 64 elements, 128B swizzle.
-static fp_status make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t kp, uint32_t box_rows) {
+// 2-D map of a rows x kp row-major matrix of 16-bit (esize 2) or 8-bit (esize 1) elements,
+// box = box_rows x (128 bytes of elements), 128-byte swizzle.
+static fp_status make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t kp, uint32_t box_rows,
+                          uint32_t esize = 2) {
   EncodeTiledFn enc = get_encode();
   FP_CHECK(enc != nullptr, FP_ECUDA, "cuTensorMapEncodeTiled is not available");
   cuuint64_t dims[2] = {kp, rows};
-  cuuint64_t strides[1] = {kp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)TC_BK, box_rows};
+  cuuint64_t strides[1] = {kp * esize};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esize), box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+  CUresult r = enc(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                   const_cast<void*>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   FP_CHECK(r == CUDA_SUCCESS, FP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -592,6 +705,36 @@ fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_
                        int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st) {
   const bool packed = algo == FP_MM_RIGHT_TC;
   uint64_t pp = (uint64_t)(p - 1) * (p - 1);
+  if (algo == FP_MM_PLAIN_F8) {
+    // residues <= 16 are exact in e4m3; fp32 accumulation exact below 2^24
+    FP_CHECK(p <= 17, FP_EBOUND, "PLAIN_F8 needs p <= 17 (p=%u)", p);
+    FP_CHECK((uint64_t)k * pp < (1ull << 24), FP_EBOUND, "PLAIN_F8 needs k (p-1)^2 < 2^24");
+    const int kp8 = (k + 127) / 128 * 128;
+    const size_t ab = ((size_t)m * kp8 + 1023) & ~(size_t)1023, bb = ((size_t)n * kp8 + 1023) & ~(size_t)1023;
+    fp_status s8 = ensure_scratch(ctx, ab + bb + 1024);
+    if (s8 != FP_OK) return s8;
+    uint8_t* A8 = (uint8_t*)ctx->scratch;
+    uint8_t* B8 = A8 + ab;
+    const int g1 = std::min(m, ctx->num_sms * 16);
+    FP_LAUNCH(ctx, "k_tc_convert_a", st, k_tc_convert_a8<<<g1, 256, 0, st>>>(A, lda, A8, m, k, kp8, p, ctx->d_err));
+    dim3 gb8(kp8 / 64, (n + 63) / 64);
+    FP_LAUNCH(ctx, "k_tc_convert_b", st, k_tc_convert_b8<<<gb8, 256, 0, st>>>(B, ldb, B8, k, n, kp8, p, ctx->d_err));
+    FP_CUDA(cudaGetLastError());
+    CUtensorMap ma8, mb8;
+    s8 = make_map(&ma8, A8, (uint64_t)m, (uint64_t)kp8, TC_BM, 1);
+    if (s8 != FP_OK) return s8;
+    s8 = make_map(&mb8, B8, (uint64_t)n, (uint64_t)kp8, TC_BN, 1);
+    if (s8 != FP_OK) return s8;
+    const size_t smem8 = 1024 + TC_STAGES * TC_STAGE_BYTES + 256;
+    dim3 grid8((n + TC_BN - 1) / TC_BN, (m + TC_BM - 1) / TC_BM);
+    RedqParams P8 = make_redq(p, 16, 1);
+    FP_CUDA(cudaFuncSetAttribute(k_mm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem8));
+    FP_LAUNCH(ctx, "k_mm_tc", st,
+              k_mm_tc<2><<<grid8, TC_THREADS, smem8, st>>>(ma8, mb8, C, ldc, nullptr, m, n, n, kp8 / 128, P8, 0,
+                                                        ctx->d_err));
+    FP_CUDA(cudaGetLastError());
+    return FP_OK;
+  }
   if (packed) {
     FP_CHECK(p <= 3, FP_EBOUND, "RIGHT_TC needs p <= 3 (p=%u)", p);
     FP_CHECK(k <= 32767, FP_EBOUND, "RIGHT_TC needs k <= 32767");
@@ -627,9 +770,9 @@ fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_
   if (packed) {
     RedqParams P = make_redq(p, 16, 2);
     uint32_t koff = (uint32_t)k;
-    FP_CUDA(cudaFuncSetAttribute(k_mm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FP_CUDA(cudaFuncSetAttribute(k_mm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FP_LAUNCH(ctx, "k_mm_tc", st,
-              k_mm_tc<true><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, RW, m, n, nw, ktiles, P, koff,
+              k_mm_tc<1><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, RW, m, n, nw, ktiles, P, koff,
                                                              ctx->d_err));
     FP_CUDA(cudaGetLastError());
     const int gblocks = ((nw + 7) / 8 + 255) / 256;
@@ -637,9 +780,9 @@ fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_
     FP_LAUNCH(ctx, "k_tc_redq", st, k_tc_redq<<<gr, 256, 0, st>>>(RW, C, ldc, m, n, nw, P, koff % p));
   } else {
     RedqParams P = make_redq(p, 16, 1);
-    FP_CUDA(cudaFuncSetAttribute(k_mm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FP_CUDA(cudaFuncSetAttribute(k_mm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FP_LAUNCH(ctx, "k_mm_tc", st,
-              k_mm_tc<false><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, nullptr, m, n, nw, ktiles, P, 0, ctx->d_err));
+              k_mm_tc<0><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, nullptr, m, n, nw, ktiles, P, 0, ctx->d_err));
   }
   FP_CUDA(cudaGetLastError());
   return FP_OK;

@@ -24,7 +24,7 @@ def env():
     fp.fp_ctx_destroy(ctx)
 
 
-ALL = ["AUTO", "RIGHT_F64", "RIGHT_F32", "PLAIN_F64", "PLAIN_F32", "PLAIN_I8", "PLAIN_TC", "RIGHT_TC"]
+ALL = ["AUTO", "RIGHT_F64", "RIGHT_F32", "PLAIN_F64", "PLAIN_F32", "PLAIN_I8", "PLAIN_TC", "RIGHT_TC", "PLAIN_F8"]
 
 
 def run(fp, torch, dev, ctx, p, a, b, algo):
@@ -43,6 +43,8 @@ def supported(fp, p, k, algo):
     if algo == "PLAIN_TC" and k * (p - 1) ** 2 >= 2 ** 24:
         return False
     if algo == "RIGHT_TC" and p > 3:
+        return False
+    if algo == "PLAIN_F8" and (p > 17 or k * (p - 1) ** 2 >= 2 ** 24):
         return False
     return True
 
