@@ -74,18 +74,24 @@ def kernel_source_hash(name):
     return None
 
 
-def stored_traffic(name, per_launch_units):
-    """DRAM bytes per launch from a committed ncu summary, scaled to this launch's units;
-    None when absent or when the kernel's source changed since the counters were taken."""
+def stored_traffic(name, shapes, launches):
+    """Average DRAM bytes per launch of `name` from committed ncu captures: `shapes` lists the
+    (variant, n) of every launch in one step; each needs a capture of that exact shape (traffic
+    does not grow in proportion to n^3, so no scaling across sizes).  None when a shape has no
+    capture or the kernel's source changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f).get(name)
     except (OSError, ValueError):
         return None
-    if not d or d.get("source_hash") != kernel_source_hash(name):
+    if not d or d.get("source_hash") != kernel_source_hash(name) or not shapes:
         return None
-    return d["bytes_per_unit"] * per_launch_units
+    per = d.get("bytes_per_launch", {})
+    keys = [f"{a}:{n}" for a, n in shapes]
+    if any(k not in per for k in keys):
+        return None
+    return sum(per[k] for k in keys) / max(1, launches)
 
 
 class Clocks:
@@ -592,7 +598,7 @@ def main():
     if dominant:
         bound, peak, peak_label, flops_fn = ktab[dominant]
         flops = 0.0
-        units = 0
+        shapes = []
         kernel_of = {"RIGHT_F32": "k_mm_ffma", "PLAIN_F32": "k_mm_ffma", "RIGHT_F64": "k_mm_dmma",
                      "PLAIN_F64": "k_mm_dmma", "PLAIN_I8": "k_mm_imma", "PLAIN_TC": "k_mm_tc", "RIGHT_TC": "k_mm_tc",
                      "PLAIN_F8": "k_mm_tc"}
@@ -609,7 +615,7 @@ def main():
                 e = 1
             f = flops_fn(n, e) * args.steps
             flops += f / args.steps
-            units += n ** 3
+            shapes.append((an, n))
             ideal_s += f / ((2.0 * bf16 if an == "PLAIN_F8" else peak) * 1e12)
         flops *= args.steps
         achieved = flops / (dom_ms / 1e3) / 1e12
@@ -617,7 +623,7 @@ def main():
             peak = flops / 1e12 / ideal_s
             if all(names[a] == "PLAIN_F8" for a in chosen.values()):
                 peak_label = "fp8 = measured bf16 x 2 (nominal 4.5/2.25)"
-        traffic = stored_traffic(dominant, units / max(1, dom_n / args.steps))
+        traffic = stored_traffic(dominant, shapes, max(1, dom_n // args.steps))
         roof = {"bound": bound, "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_label + f" ({peak_src})",
                 "launches": dom_n, "avg_launch_ms": dom_ms / max(1, dom_n)}

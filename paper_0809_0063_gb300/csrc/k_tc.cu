@@ -10,6 +10,13 @@
 //            drained by the epilogue warps into a 32-bit word R = D0 + 2^16 D1 while the MMA
 //            warp fills the other TMEM buffer (delayed reduction, Sec. 2.2).  At the end an
 //            offset makes both digits non-negative and REDQ_2 (Algorithm 2) recovers them mod p.
+//  PLAIN_F8  C = A B mod p on kind::f8f6f4 with e4m3 operands, p <= 17.  Residues 0..16 read
+//            as e4m3 bit patterns are exactly r 2^-9 (codes 0..7 subnormal, 8..15 the first
+//            binade, 16 = 2^-5), so when A and B are 16-byte aligned with leading dimensions
+//            a multiple of 16 the kernel streams the caller's bytes directly: A K-major, B
+//            MN-major (its rows are k), no conversion pass.  The fp32 sums are then
+//            2^-18 times the integer sums (exact below 2^24) and the epilogue scales back.
+//            Other layouts go through a conversion to e4m3 of the integer values.
 //
 // Kernel roles (one CTA = one 128 x 256 output tile of words, 1 CTA per SM):
 //   warp 0       TMA producer: A tile 128 x 64 and B tile 256 x 64 (bf16/fp16, 128-byte
@@ -97,6 +104,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
   return d;
 }
 
+// Shared-memory matrix descriptor for an MN-major tile with 128-byte swizzle: 128-byte rows
+// along MN, one row per k; 8-row core groups 1024 bytes apart along K (stride byte offset)
+// and 128-element MN blocks `mn_block_bytes` apart (leading byte offset).
+__device__ __forceinline__ uint64_t smem_desc_mn_sw128(const void* p, uint32_t mn_block_bytes) {
+  uint64_t d = (su32(p) & 0x3FFFFu) >> 4;
+  d |= (uint64_t)((mn_block_bytes >> 4) & 0x3FFFu) << 16;  // leading byte offset
+  d |= (uint64_t)(1024 >> 4) << 32;                       // stride byte offset
+  d |= (uint64_t)1 << 46;                                 // version
+  d |= (uint64_t)2 << 61;                                 // SWIZZLE_128B
+  return d;
+}
+
 // Instruction descriptor, kind::f16: fp32 accumulate, A/B type (0 f16, 1 bf16), both K-major.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_type, int M, int N) {
   return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -110,9 +129,9 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-// kind::f8f6f4 with e4m3 A and B (format code 0), fp32 accumulate.
-__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// kind::f8f6f4 with e4m3 A and B (format code 0), fp32 accumulate; b_mn: B is MN-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N, bool b_mn = false) {
+  return (1u << 4) | ((b_mn ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 __device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                        uint32_t accumulate) {
@@ -381,7 +400,12 @@ __global__ void __launch_bounds__(256) k_tc_convert_b8(const uint8_t* __restrict
 
 // ---------------------------------------------------------------- the GEMM kernel
 
-// MODE 0: bf16 plain, 1: fp16 packed (two centred residues per word), 2: e4m3 plain.
+// MODE 0: bf16 plain, 1: fp16 packed (two centred residues per word), 2: e4m3 plain from
+// converted operands, 3: e4m3 plain on the caller's residue bytes (A K-major, B MN-major; the
+// values are r 2^-9).  In MODE 3 warp 2 also checks a slice of every stage for residues >= p
+// before releasing it: the A tile of (row block, k tile) is loaded by gridDim.x CTAs and the
+// B tile by gridDim.y CTAs, so each CTA checks 1/gridDim.x of its A bytes and 1/gridDim.y of
+// its B bytes and every input byte is checked once.
 template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_mm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, uint8_t* __restrict__ C,
@@ -400,7 +424,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ uint8_t ptab[1024];
 
   constexpr bool PACKED = MODE == 1;
-  constexpr int KT_ELEMS = MODE == 2 ? 128 : 64;   // elements per 128-byte k-tile row
+  constexpr bool RAW = MODE == 3;
+  constexpr int KT_ELEMS = MODE >= 2 ? 128 : 64;   // elements per 128-byte k-tile row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
   constexpr uint32_t TMEM_COLS = PACKED ? 512 : 256;
@@ -409,7 +434,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], RAW ? 2 : 1);   // MODE 3: the MMA commit and the range checker
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -443,7 +468,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint8_t* sb = sa + TC_A_BYTES;
         mbar_expect_tx(&full[s], TC_STAGE_BYTES);
         tma_load_2d(sa, &tmA, kt * KT_ELEMS, m0, &full[s]);
-        tma_load_2d(sb, &tmB, kt * KT_ELEMS, n0, &full[s]);
+        if (RAW) {   // B rows are k: two 128-column boxes of 128 rows
+          tma_load_2d(sb, &tmB, n0, kt * KT_ELEMS, &full[s]);
+          tma_load_2d(sb + TC_B_BYTES / 2, &tmB, n0 + 128, kt * KT_ELEMS, &full[s]);
+        } else {
+          tma_load_2d(sb, &tmB, kt * KT_ELEMS, n0, &full[s]);
+        }
         armed = kt + 1;
       }
       // every armed stage must have landed before the CTA may exit (its shared memory is reused)
@@ -454,7 +484,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = MODE == 2 ? idesc_e4m3(TC_BM, TC_BN) : idesc_f16(PACKED ? 0u : 1u, TC_BM, TC_BN);
+      constexpr uint32_t idesc =
+          MODE >= 2 ? idesc_e4m3(TC_BM, TC_BN, RAW) : idesc_f16(PACKED ? 0u : 1u, TC_BM, TC_BN);
       int kt = 0;
       for (int c = 0; c < nchunks && !*abort_flag; ++c) {
         const int buf = c & 1;
@@ -469,12 +500,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tc_fence_after();
           const uint8_t* sa = smem + s * TC_STAGE_BYTES;
           const uint8_t* sb = sa + TC_A_BYTES;
-          const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sb);
+          const uint64_t ad = smem_desc_sw128(sa);
+          const uint64_t bd = RAW ? smem_desc_mn_sw128(sb, TC_B_BYTES / 2) : smem_desc_sw128(sb);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            // advance 32 bytes along K inside the swizzled 128-byte rows (16 x 16-bit or 32 x fp8)
-            if (MODE == 2) mma_f8(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, first ? 0u : 1u);
-            else mma_f16(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, first ? 0u : 1u);
+            // K-major: advance 32 bytes along K inside the swizzled 128-byte rows (16 x 16-bit
+            // or 32 x fp8).  MN-major B: advance 32 rows of 128 bytes (4 core groups).
+            const uint64_t bk = RAW ? (uint64_t)(kk * 256) : (uint64_t)(kk * 2);
+            if (MODE >= 2) mma_f8(dtm, ad + (uint64_t)(kk * 2), bd + bk, idesc, first ? 0u : 1u);
+            else mma_f16(dtm, ad + (uint64_t)(kk * 2), bd + bk, idesc, first ? 0u : 1u);
             first = false;
           }
           mma_commit(&empty[s]);    // stage s free once these MMAs have read it
@@ -495,6 +529,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int half = (warp - 2) >> 2;            // column half (0: 0..127, 1: 128..255)
     const int row = m0 + q * 32 + lane;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    if (RAW && warp == 2) {
+      // range check of this CTA's slice of every stage, then release the stage
+      const uint32_t a_units = TC_A_BYTES / 16, b_units = TC_B_BYTES / 16;
+      const uint32_t a_per = (a_units + gridDim.x - 1) / gridDim.x, b_per = (b_units + gridDim.y - 1) / gridDim.y;
+      const uint32_t a_lo = min(a_units, blockIdx.x * a_per), a_hi = min(a_units, a_lo + a_per);
+      const uint32_t b_lo = min(b_units, blockIdx.y * b_per), b_hi = min(b_units, b_lo + b_per);
+      const uint32_t pp = 0x01010101u * P.p;
+      uint32_t bad = 0;
+      for (int kt = 0; kt < ktiles; ++kt) {
+        const int s = kt % TC_STAGES;
+        if (!mbar_wait(&full[s], (uint32_t)(kt / TC_STAGES) & 1u, abort_flag)) break;
+        const uint4* sa = reinterpret_cast<const uint4*>(smem + s * TC_STAGE_BYTES);
+        const uint4* sb = reinterpret_cast<const uint4*>(smem + s * TC_STAGE_BYTES + TC_A_BYTES);
+        for (uint32_t u = a_lo + lane; u < a_hi; u += 32) {
+          const uint4 x = sa[u];
+          bad |= __vcmpgeu4(x.x, pp) | __vcmpgeu4(x.y, pp) | __vcmpgeu4(x.z, pp) | __vcmpgeu4(x.w, pp);
+        }
+        for (uint32_t u = b_lo + lane; u < b_hi; u += 32) {
+          const uint4 x = sb[u];
+          bad |= __vcmpgeu4(x.x, pp) | __vcmpgeu4(x.y, pp) | __vcmpgeu4(x.z, pp) | __vcmpgeu4(x.w, pp);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+      }
+      if (bad) flag_error(err, ERR_RANGE);
+    }
     if (!PACKED) {
       bool ok = mbar_wait(&tfull[0], 0, abort_flag);
       tc_fence_after();
@@ -508,7 +568,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           uint32_t w = 0;
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
-            uint32_t x = __float2uint_rn(__uint_as_float(v[j + t]));
+            // MODE 3 sums are 2^-18 times the integer sums (operands r 2^-9): scale back exactly
+            const float f = RAW ? __uint_as_float(v[j + t]) * 262144.0f : __uint_as_float(v[j + t]);
+            uint32_t x = __float2uint_rn(f);
             w |= modp32(x, P.dv, P.p) << (8 * t);
           }
           packed[j >> 2] = w;
@@ -683,14 +745,15 @@ static EncodeTiledFn get_encode() {
   return fn;
 }
 
-// 2-D map of a rows x kp row-major matrix of 16-bit (esize 2) or 8-bit (esize 1) elements,
-// box = box_rows x (128 bytes of elements), 128-byte swizzle.
-static fp_status make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t kp, uint32_t box_rows,
-                          uint32_t esize = 2) {
+// 2-D map of a rows x cols row-major matrix of 16-bit (esize 2) or 8-bit (esize 1) elements
+// with leading dimension ld elements (ld * esize a multiple of 16, base 16-byte aligned),
+// box = box_rows x (128 bytes of elements), 128-byte swizzle; reads past cols or rows return 0.
+static fp_status make_map_ld(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
+                             uint32_t box_rows, uint32_t esize) {
   EncodeTiledFn enc = get_encode();
   FP_CHECK(enc != nullptr, FP_ECUDA, "cuTensorMapEncodeTiled is not available");
-  cuuint64_t dims[2] = {kp, rows};
-  cuuint64_t strides[1] = {kp * esize};
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld * esize};
   cuuint32_t box[2] = {(cuuint32_t)(128 / esize), box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
@@ -699,6 +762,10 @@ static fp_status make_map(CUtensorMap* map, const void* base, uint64_t rows, uin
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   FP_CHECK(r == CUDA_SUCCESS, FP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return FP_OK;
+}
+static fp_status make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t kp, uint32_t box_rows,
+                          uint32_t esize = 2) {
+  return make_map_ld(map, base, rows, kp, kp, box_rows, esize);
 }
 
 fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda, const uint8_t* B,
@@ -710,6 +777,23 @@ fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_
     FP_CHECK(p <= 17, FP_EBOUND, "PLAIN_F8 needs p <= 17 (p=%u)", p);
     FP_CHECK((uint64_t)k * pp < (1ull << 24), FP_EBOUND, "PLAIN_F8 needs k (p-1)^2 < 2^24");
     const int kp8 = (k + 127) / 128 * 128;
+    const size_t smem8 = 1024 + TC_STAGES * TC_STAGE_BYTES + 256;
+    dim3 grid8((n + TC_BN - 1) / TC_BN, (m + TC_BM - 1) / TC_BM);
+    RedqParams P8 = make_redq(p, 16, 1);
+    if ((((uintptr_t)A | (uintptr_t)B) & 15u) == 0 && (lda & 15) == 0 && (ldb & 15) == 0) {
+      // the caller's bytes are the e4m3 operands (r 2^-9): A K-major, B MN-major, no conversion
+      CUtensorMap mar, mbr;
+      fp_status sr = make_map_ld(&mar, A, (uint64_t)m, (uint64_t)k, (uint64_t)lda, TC_BM, 1);
+      if (sr != FP_OK) return sr;
+      sr = make_map_ld(&mbr, B, (uint64_t)k, (uint64_t)n, (uint64_t)ldb, 128, 1);
+      if (sr != FP_OK) return sr;
+      FP_CUDA(cudaFuncSetAttribute(k_mm_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem8));
+      FP_LAUNCH(ctx, "k_mm_tc", st,
+                k_mm_tc<3><<<grid8, TC_THREADS, smem8, st>>>(mar, mbr, C, ldc, nullptr, m, n, n, kp8 / 128, P8, 0,
+                                                          ctx->d_err));
+      FP_CUDA(cudaGetLastError());
+      return FP_OK;
+    }
     const size_t ab = ((size_t)m * kp8 + 1023) & ~(size_t)1023, bb = ((size_t)n * kp8 + 1023) & ~(size_t)1023;
     fp_status s8 = ensure_scratch(ctx, ab + bb + 1024);
     if (s8 != FP_OK) return s8;
@@ -725,9 +809,6 @@ fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_
     if (s8 != FP_OK) return s8;
     s8 = make_map(&mb8, B8, (uint64_t)n, (uint64_t)kp8, TC_BN, 1);
     if (s8 != FP_OK) return s8;
-    const size_t smem8 = 1024 + TC_STAGES * TC_STAGE_BYTES + 256;
-    dim3 grid8((n + TC_BN - 1) / TC_BN, (m + TC_BM - 1) / TC_BM);
-    RedqParams P8 = make_redq(p, 16, 1);
     FP_CUDA(cudaFuncSetAttribute(k_mm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem8));
     FP_LAUNCH(ctx, "k_mm_tc", st,
               k_mm_tc<2><<<grid8, TC_THREADS, smem8, st>>>(ma8, mb8, C, ldc, nullptr, m, n, n, kp8 / 128, P8, 0,

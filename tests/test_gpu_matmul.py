@@ -153,3 +153,61 @@ def test_matmul_errors(env):
     with pytest.raises(fp.FpError) as ei:
         fp.fp_ctx_status(ctx)
     assert ei.value.status == fp.FP_EINVAL
+
+
+def _padded(torch, dev, x, ld, fill):
+    """x (rows x cols) stored with leading dimension ld; the pad bytes hold `fill`."""
+    rows, cols = x.shape
+    buf = np.full((rows, ld), fill, np.uint8)
+    buf[:, :cols] = x
+    return torch.from_numpy(buf).to(dev)
+
+
+@pytest.mark.parametrize("p,m,n,k", [(3, 200, 333, 517), (7, 130, 70, 1000), (2, 64, 129, 4100),
+                                     (17, 257, 255, 96), (5, 1, 1, 1), (13, 300, 600, 129)])
+def test_matmul_f8_direct_operands(env, p, m, n, k):
+    """PLAIN_F8 on 16-byte aligned leading dimensions streams the caller's residue bytes as
+    e4m3 (r 2^-9) with B MN-major: ragged m, n, k, the pad bytes past k and n set to 255
+    (out of range, so reading them would also raise the range error), no conversion pass."""
+    fp, torch, dev, ctx = env
+    a, b = workloads.matmul_inputs(p * 77 + k, p, m, k, n)
+    lda, ldb, ldc = -(-k // 16) * 16 + 16, -(-n // 16) * 16, n + 3
+    A, B = _padded(torch, dev, a, lda, 255), _padded(torch, dev, b, ldb, 255)
+    C = torch.full((m, ldc), 254, dtype=torch.uint8, device=dev)
+    fp.fp_ctx_profile(ctx, 2)
+    fp.fp_ctx_profile(ctx, 1)
+    fp.fp_matmul(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, fp.FP_MM_PLAIN_F8)
+    fp.fp_ctx_status(ctx)
+    conv, _ = fp.fp_ctx_profile_read(ctx, "k_tc_convert")
+    mm, _ = fp.fp_ctx_profile_read(ctx, "k_mm_tc")
+    fp.fp_ctx_profile(ctx, 0)
+    got = C.cpu().numpy()
+    assert (conv, mm) == (0, 1)
+    assert np.array_equal(got[:, :n], field.matmul_mod(a, b, p))
+    assert np.all(got[:, n:] == 254)                  # nothing written past n
+
+
+@pytest.mark.parametrize("where", ["A_first", "A_last", "B_first", "B_last", "B_mid"])
+def test_matmul_f8_direct_range_check(env, where):
+    """The direct e4m3 path checks every input byte on the device (each CTA a slice of the
+    tiles it loads): one residue equal to p anywhere, in any tile, raises the range error."""
+    fp, torch, dev, ctx = env
+    p, m, n, k = 7, 300, 520, 700
+    a, b = workloads.matmul_inputs(3, p, m, k, n)
+    a, b = a.copy(), b.copy()
+    pos = {"A_first": ("a", 0, 0), "A_last": ("a", m - 1, k - 1), "B_first": ("b", 0, 0),
+           "B_last": ("b", k - 1, n - 1), "B_mid": ("b", 333, 261)}[where]
+    (a if pos[0] == "a" else b)[pos[1], pos[2]] = p
+    lda, ldb = -(-k // 16) * 16, -(-n // 16) * 16
+    A, B = _padded(torch, dev, a, lda, 0), _padded(torch, dev, b, ldb, 0)
+    C = torch.empty((m, n), dtype=torch.uint8, device=dev)
+    fp.fp_matmul(ctx, p, m, n, k, A, lda, B, ldb, C, n, fp.FP_MM_PLAIN_F8)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_ctx_status(ctx)
+    assert ei.value.status == fp.FP_EINVAL
+    # the context is usable afterwards: the same product with the entry fixed is exact
+    (a if pos[0] == "a" else b)[pos[1], pos[2]] = p - 1
+    A, B = _padded(torch, dev, a, lda, 0), _padded(torch, dev, b, ldb, 0)
+    fp.fp_matmul(ctx, p, m, n, k, A, lda, B, ldb, C, n, fp.FP_MM_PLAIN_F8)
+    fp.fp_ctx_status(ctx)
+    assert np.array_equal(C.cpu().numpy(), field.matmul_mod(a, b, p))
