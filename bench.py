@@ -59,6 +59,8 @@ def kernel_table(bf16_tf):
                       lambda n, e: 2.0 * n * n * n),
         "k_mm_tc": ("tensor", bf16_tf, "measured bf16 dense",
                     lambda n, e: 2.0 * n * n * (-(-n // e))),
+        "k_mm_f8g": ("tensor", 2.0 * bf16_tf, "fp8 = measured bf16 x 2 (nominal 4.5/2.25)",
+                     lambda n, e: 2.0 * n * n * n),
     }
 
 
@@ -75,10 +77,11 @@ def kernel_source_hash(name):
 
 
 def stored_traffic(name, shapes, launches):
-    """Average DRAM bytes per launch of `name` from committed ncu captures: `shapes` lists the
-    (variant, n) of every launch in one step; each needs a capture of that exact shape (traffic
-    does not grow in proportion to n^3, so no scaling across sizes).  None when a shape has no
-    capture or the kernel's source changed since the counters were taken."""
+    """Average DRAM bytes per launch of `name` from a committed ncu capture of the same step:
+    `shapes` lists the (variant, n) of every product the kernel ran in one step, and the
+    capture is keyed by that list (traffic does not grow in proportion to n^3, so nothing is
+    scaled across sizes).  None when the step has no capture or the kernel's source changed
+    since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -87,11 +90,9 @@ def stored_traffic(name, shapes, launches):
         return None
     if not d or d.get("source_hash") != kernel_source_hash(name) or not shapes:
         return None
-    per = d.get("bytes_per_launch", {})
-    keys = [f"{a}:{n}" for a, n in shapes]
-    if any(k not in per for k in keys):
-        return None
-    return sum(per[k] for k in keys) / max(1, launches)
+    key = ",".join(sorted(f"{a}:{n}" for a, n in shapes))
+    per_step = d.get("bytes_per_step", {}).get(key)
+    return None if per_step is None else per_step / max(1, launches)
 
 
 class Clocks:
@@ -500,9 +501,13 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    # one grouped call per step: the products that fit the e4m3 tensor-core path share one
+    # persistent launch, any other goes through fp_matmul with the same algo
+    descs = [fp.fp_mm_problem_of(q["p"], q["n"], q["n"], q["n"], q["A"], q["n"], q["B"], q["n"], q["C"], q["n"])
+             for q in prob]
+
     def step(al=algo):
-        for q in prob:
-            fp.fp_matmul(ctx, q["p"], q["n"], q["n"], q["n"], q["A"], q["n"], q["B"], q["n"], q["C"], q["n"], al)
+        fp.fp_matmul_grouped(ctx, descs, al)
 
     # parity gate on the resident buffers before timing (sampled rows against the oracle)
     from oracle import field
@@ -516,6 +521,10 @@ def main():
     # algorithm actually used per problem (the autotuner's cached choice under AUTO)
     chosen = {}
     for q in prob:
+        grouped = args.algo in ("AUTO", "PLAIN_F8") and q["p"] <= 17 and q["n"] * (q["p"] - 1) ** 2 < 2 ** 24
+        if grouped:
+            chosen[(q["p"], q["n"])] = fp.FP_MM_PLAIN_F8
+            continue
         a = fp.fp_ctx_autotune_choice(ctx, q["p"], q["n"], q["n"], q["n"]) if args.algo == "AUTO" else algo
         if a < 0 and args.algo == "AUTO":       # fixed rule (autotuning off): first exact candidate
             a = fp.FP_MM_PLAIN_F8 if q["p"] <= 17 else fp.FP_MM_PLAIN_TC
@@ -601,8 +610,7 @@ def main():
         shapes = []
         kernel_of = {"RIGHT_F32": "k_mm_ffma", "PLAIN_F32": "k_mm_ffma", "RIGHT_F64": "k_mm_dmma",
                      "PLAIN_F64": "k_mm_dmma", "PLAIN_I8": "k_mm_imma", "PLAIN_TC": "k_mm_tc", "RIGHT_TC": "k_mm_tc",
-                     "PLAIN_F8": "k_mm_tc"}
-        ideal_s = 0.0   # sum over launches of flops / (that launch's own peak): mixed dtypes
+                     "PLAIN_F8": "k_mm_f8g"}
         for p, n in PROBLEMS:
             an = names[chosen[(p, n)]]
             if kernel_of.get(an) != dominant:
@@ -616,13 +624,8 @@ def main():
             f = flops_fn(n, e) * args.steps
             flops += f / args.steps
             shapes.append((an, n))
-            ideal_s += f / ((2.0 * bf16 if an == "PLAIN_F8" else peak) * 1e12)
         flops *= args.steps
         achieved = flops / (dom_ms / 1e3) / 1e12
-        if dominant == "k_mm_tc":       # fp8 launches count against the fp8 peak (2 x bf16, nominal ratio)
-            peak = flops / 1e12 / ideal_s
-            if all(names[a] == "PLAIN_F8" for a in chosen.values()):
-                peak_label = "fp8 = measured bf16 x 2 (nominal 4.5/2.25)"
         traffic = stored_traffic(dominant, shapes, max(1, dom_n // args.steps))
         roof = {"bound": bound, "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_label + f" ({peak_src})",

@@ -215,6 +215,36 @@ fp_status fp_dot_noalloc(uint32_t p, const uint8_t* u, const uint8_t* v, size_t 
 fp_status fp_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
                     const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, void* stream);
 
+/* One product of a group (see fp_matmul_grouped); fields as in fp_matmul. */
+typedef struct {
+  uint32_t p;
+  int m, n, k;
+  const uint8_t* A;
+  int lda;
+  const uint8_t* B;
+  int ldb;
+  uint8_t* C;
+  int ldc;
+} fp_mm_problem;
+
+/* Problems per persistent launch of fp_matmul_grouped. */
+#define FP_GROUP_MAX 16
+
+/* Several independent products C_i = A_i B_i mod p_i (the paper has no counterpart: it treats
+ * one product at a time; this call schedules Sec. 7's plain product, with the delayed
+ * reduction of Sec. 2.2, over many of them).  `problems` is a HOST array of `count` entries
+ * (count = 0 is a no-op); every entry is checked as fp_matmul checks its arguments before
+ * anything is enqueued.  Output ranges must not overlap one another or any input.
+ * With algo FP_MM_AUTO or FP_MM_PLAIN_F8, the problems with p <= 17, k (p-1)^2 < 2^24, A and
+ * B 16-byte aligned and lda, ldb multiples of 16 run together in persistent tensor-core
+ * launches of up to FP_GROUP_MAX problems: one CTA per SM takes 128 x 256 output tiles from
+ * all of them (longest inner dimension first), its epilogue overlapping the next tile's
+ * multiplications; the residue bytes are read in place as e4m3 operands.  Every other problem
+ * runs through fp_matmul with the same algo, in order, on the same stream.  Residues >= p set
+ * the context's range error (fp_ctx_status). */
+fp_status fp_matmul_grouped(fp_ctx ctx, const fp_mm_problem* problems, size_t count, int algo,
+                            void* stream);
+
 /* Right compression of B alone (Sec. 7.4): CB[l][j] = sum_{t<e} B[l][j e + t] Q^t with
  * Q = 2^b, missing columns of the last block taken as zero (partial compression, Sec. 7.1).
  * CB: device array k x ceil(n/e) of `word` (F64 or F32 or U64).  Exposed for tests and reuse. */

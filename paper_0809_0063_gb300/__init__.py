@@ -24,6 +24,7 @@ FP_ALGO_AUTO, FP_ALGO_PLAIN, FP_ALGO_DQT_F64, FP_ALGO_DQT_U64, FP_ALGO_DQT_F32, 
 # matmul algorithms
 (FP_MM_AUTO, FP_MM_RIGHT_F64, FP_MM_RIGHT_F32, FP_MM_PLAIN_F64, FP_MM_PLAIN_F32, FP_MM_PLAIN_I8,
  FP_MM_PLAIN_TC, FP_MM_RIGHT_TC, FP_MM_LEFT_F32, FP_MM_PLAIN_F8) = range(10)
+FP_GROUP_MAX = 16
 
 
 class FpError(RuntimeError):
@@ -43,6 +44,12 @@ class fp_instance(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("p", ctypes.c_uint32), ("m", ctypes.c_uint32),
                 ("n", ctypes.c_uint32), ("k", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p)]
+
+
+class fp_mm_problem(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_uint32), ("m", ctypes.c_int), ("n", ctypes.c_int), ("k", ctypes.c_int),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int)]
 
 
 class fp_request(ctypes.Structure):
@@ -89,6 +96,7 @@ _SIGS = {
     "fp_gf_info": (_I, [_V, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
     "fp_gf_mul_batched": (_I, [_V, _V, _V, _V, _V, _SZ, _V]),
     "fp_batch_run": (_I, [_V, ctypes.POINTER(fp_instance), _SZ, _V]),
+    "fp_matmul_grouped": (_I, [_V, ctypes.POINTER(fp_mm_problem), _SZ, _I, _V]),
     "fp_selftest_bounded_wait": (_I, [_V, _U32, _V]),
     "fp_server_create": (_I, [_V, ctypes.POINTER(fp_server_config), ctypes.POINTER(_V)]),
     "fp_server_submit": (_I, [_V, ctypes.POINTER(fp_request), ctypes.POINTER(_U64)]),
@@ -225,6 +233,17 @@ def fp_dot_noalloc(p: int, u, v, n: int, out, algo: int = FP_ALGO_AUTO, stream=N
 def fp_matmul(ctx, p: int, m: int, n: int, k: int, A, lda: int, B, ldb: int, C, ldc: int,
               algo: int = FP_MM_AUTO, stream=None):
     _check(lib().fp_matmul(ctx, p, m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, algo, _stream(stream)))
+
+
+def fp_mm_problem_of(p: int, m: int, n: int, k: int, A, lda: int, B, ldb: int, C, ldc: int) -> fp_mm_problem:
+    return fp_mm_problem(p=p, m=m, n=n, k=k, A=_ptr(A), lda=lda, B=_ptr(B), ldb=ldb, C=_ptr(C), ldc=ldc)
+
+
+def fp_matmul_grouped(ctx, problems, algo: int = FP_MM_AUTO, stream=None):
+    """problems: sequence of fp_mm_problem (see fp_mm_problem_of); the tensors they point to
+    must stay alive until the work has run."""
+    arr = (fp_mm_problem * len(problems))(*problems)
+    _check(lib().fp_matmul_grouped(ctx, arr, len(problems), algo, _stream(stream)))
 
 
 def fp_pack_cb(ctx, p: int, k: int, n: int, B, ldb: int, b: int, e: int, word: int, CB, stream=None):

@@ -430,16 +430,53 @@ extern "C" fp_status fp_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint
   return launch_dot(ctx, p, u, v, n, out, algo, as_stream(stream));
 }
 
-extern "C" fp_status fp_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
-                               const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, void* stream) {
-  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_matmul: ctx is NULL");
+static fp_status check_matmul(uint32_t p, int m, int n, int k, const uint8_t* A, int lda, const uint8_t* B,
+                              int ldb, const uint8_t* C, int ldc, int algo) {
   FP_CHECK(p >= 2 && p <= 251 && is_prime(p), FP_EINVAL, "p=%u not a prime <= 251", p);
   FP_CHECK(m >= 1 && n >= 1 && k >= 1 && m <= (1 << 20) && n <= (1 << 20) && k <= (1 << 20),
            FP_EINVAL, "fp_matmul: sizes m=%d n=%d k=%d outside [1, 2^20]", m, n, k);
   FP_CHECK(lda >= k && ldb >= n && ldc >= n, FP_EINVAL, "fp_matmul: leading dimensions too small");
   FP_CHECK(A && B && C, FP_EINVAL, "fp_matmul: null array");
   FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_PLAIN_F8, FP_EINVAL, "bad algo %d", algo);
+  return FP_OK;
+}
+
+extern "C" fp_status fp_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
+                               const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, void* stream) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_matmul: ctx is NULL");
+  fp_status s = check_matmul(p, m, n, k, A, lda, B, ldb, C, ldc, algo);
+  if (s != FP_OK) return s;
   return launch_matmul(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, algo, as_stream(stream));
+}
+
+extern "C" fp_status fp_matmul_grouped(fp_ctx ctx, const fp_mm_problem* problems, size_t count, int algo,
+                                       void* stream) {
+  FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_matmul_grouped: ctx is NULL");
+  FP_CHECK(count == 0 || problems != nullptr, FP_EINVAL, "fp_matmul_grouped: problems is NULL");
+  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_PLAIN_F8, FP_EINVAL, "bad algo %d", algo);
+  for (size_t i = 0; i < count; ++i) {
+    const fp_mm_problem& x = problems[i];
+    fp_status s = check_matmul(x.p, x.m, x.n, x.k, x.A, x.lda, x.B, x.ldb, x.C, x.ldc, algo);
+    if (s != FP_OK) return s;
+  }
+  cudaStream_t st = as_stream(stream);
+  std::vector<const fp_mm_problem*> direct;
+  const bool f8 = algo == FP_MM_AUTO || algo == FP_MM_PLAIN_F8;
+  for (size_t i = 0; i < count; ++i)
+    if (f8 && f8_direct_ok(problems[i].p, problems[i].k, problems[i].A, problems[i].lda, problems[i].B,
+                           problems[i].ldb))
+      direct.push_back(&problems[i]);
+  if (!direct.empty()) {
+    fp_status s = launch_mm_f8_grouped(ctx, direct.data(), direct.size(), st);
+    if (s != FP_OK) return s;
+  }
+  for (size_t i = 0; i < count; ++i) {
+    const fp_mm_problem& x = problems[i];
+    if (f8 && f8_direct_ok(x.p, x.k, x.A, x.lda, x.B, x.ldb)) continue;
+    fp_status s = launch_matmul(ctx, x.p, x.m, x.n, x.k, x.A, x.lda, x.B, x.ldb, x.C, x.ldc, algo, st);
+    if (s != FP_OK) return s;
+  }
+  return FP_OK;
 }
 
 extern "C" fp_status fp_pack_cb(fp_ctx ctx, uint32_t p, int k, int n, const uint8_t* B, int ldb,

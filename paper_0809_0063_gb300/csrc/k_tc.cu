@@ -13,10 +13,9 @@
 //  PLAIN_F8  C = A B mod p on kind::f8f6f4 with e4m3 operands, p <= 17.  Residues 0..16 read
 //            as e4m3 bit patterns are exactly r 2^-9 (codes 0..7 subnormal, 8..15 the first
 //            binade, 16 = 2^-5), so when A and B are 16-byte aligned with leading dimensions
-//            a multiple of 16 the kernel streams the caller's bytes directly: A K-major, B
-//            MN-major (its rows are k), no conversion pass.  The fp32 sums are then
-//            2^-18 times the integer sums (exact below 2^24) and the epilogue scales back.
-//            Other layouts go through a conversion to e4m3 of the integer values.
+//            a multiple of 16 the persistent grouped kernel streams the caller's bytes
+//            directly (k_tcg.cu).  Other layouts are converted here to e4m3 of the integer
+//            values (K-major, zero padded) for the kernel below.
 //
 // Kernel roles (one CTA = one 128 x 256 output tile of words, 1 CTA per SM):
 //   warp 0       TMA producer: A tile 128 x 64 and B tile 256 x 64 (bf16/fp16, 128-byte
@@ -33,6 +32,7 @@
 #include <cuda_fp16.h>
 
 #include "fpdqt_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace fpd {
 
@@ -42,133 +42,6 @@ static constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;            // 32 KB
 static constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;  // 48 KB
 static constexpr int TC_THREADS = 320;                          // 10 warps
 static constexpr int TC_CHUNK_KT = 7;                           // 448 inner steps per packed chunk
-static constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;             // try_wait polls before giving up
-static constexpr uint32_t TC_DRAIN_LIMIT = 1u << 20;            // polls for own in-flight work
-
-// ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
-      : "=r"(ok)
-      : "r"(su32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: false (and the abort flag set) if the phase did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag,
-                                          uint32_t limit = TC_WAIT_LIMIT) {
-  for (uint32_t i = 0; i < limit; ++i) {
-    if (mbar_try(bar, parity)) return true;
-    if ((i & 1023u) == 1023u && *abort_flag) return false;
-  }
-  *abort_flag = 1;
-  return false;
-}
-
-// Drain wait: bounded, does not give up early on the abort flag (own copies / MMAs in flight).
-__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < TC_DRAIN_LIMIT; ++i)
-    if (mbar_try(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          su32(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(su32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor for a K-major tile with 128-byte swizzle: 8-row core
-// groups 1024 bytes apart (stride byte offset), descriptor version 1, layout SWIZZLE_128B.
-__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
-  uint64_t a = (su32(p) & 0x3FFFFu) >> 4;
-  uint64_t d = a;
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;            // version
-  d |= (uint64_t)2 << 61;            // SWIZZLE_128B
-  return d;
-}
-
-// Shared-memory matrix descriptor for an MN-major tile with 128-byte swizzle: 128-byte rows
-// along MN, one row per k; 8-row core groups 1024 bytes apart along K (stride byte offset)
-// and 128-element MN blocks `mn_block_bytes` apart (leading byte offset).
-__device__ __forceinline__ uint64_t smem_desc_mn_sw128(const void* p, uint32_t mn_block_bytes) {
-  uint64_t d = (su32(p) & 0x3FFFFu) >> 4;
-  d |= (uint64_t)((mn_block_bytes >> 4) & 0x3FFFu) << 16;  // leading byte offset
-  d |= (uint64_t)(1024 >> 4) << 32;                       // stride byte offset
-  d |= (uint64_t)1 << 46;                                 // version
-  d |= (uint64_t)2 << 61;                                 // SWIZZLE_128B
-  return d;
-}
-
-// Instruction descriptor, kind::f16: fp32 accumulate, A/B type (0 f16, 1 bf16), both K-major.
-__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_type, int M, int N) {
-  return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-// kind::f8f6f4 with e4m3 A and B (format code 0), fp32 accumulate; b_mn: B is MN-major.
-__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N, bool b_mn = false) {
-  return (1u << 4) | ((b_mn ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// 16 columns per thread, no wait (the caller waits with tmem_wait before using v).
-__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------------- operand conversion
 
@@ -401,11 +274,7 @@ __global__ void __launch_bounds__(256) k_tc_convert_b8(const uint8_t* __restrict
 // ---------------------------------------------------------------- the GEMM kernel
 
 // MODE 0: bf16 plain, 1: fp16 packed (two centred residues per word), 2: e4m3 plain from
-// converted operands, 3: e4m3 plain on the caller's residue bytes (A K-major, B MN-major; the
-// values are r 2^-9).  In MODE 3 warp 2 also checks a slice of every stage for residues >= p
-// before releasing it: the A tile of (row block, k tile) is loaded by gridDim.x CTAs and the
-// B tile by gridDim.y CTAs, so each CTA checks 1/gridDim.x of its A bytes and 1/gridDim.y of
-// its B bytes and every input byte is checked once.
+// converted operands.
 template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_mm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, uint8_t* __restrict__ C,
@@ -424,8 +293,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ uint8_t ptab[1024];
 
   constexpr bool PACKED = MODE == 1;
-  constexpr bool RAW = MODE == 3;
-  constexpr int KT_ELEMS = MODE >= 2 ? 128 : 64;   // elements per 128-byte k-tile row
+  constexpr int KT_ELEMS = MODE == 2 ? 128 : 64;   // elements per 128-byte k-tile row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
   constexpr uint32_t TMEM_COLS = PACKED ? 512 : 256;
@@ -434,7 +302,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], RAW ? 2 : 1);   // MODE 3: the MMA commit and the range checker
+      mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -468,12 +336,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint8_t* sb = sa + TC_A_BYTES;
         mbar_expect_tx(&full[s], TC_STAGE_BYTES);
         tma_load_2d(sa, &tmA, kt * KT_ELEMS, m0, &full[s]);
-        if (RAW) {   // B rows are k: two 128-column boxes of 128 rows
-          tma_load_2d(sb, &tmB, n0, kt * KT_ELEMS, &full[s]);
-          tma_load_2d(sb + TC_B_BYTES / 2, &tmB, n0 + 128, kt * KT_ELEMS, &full[s]);
-        } else {
-          tma_load_2d(sb, &tmB, kt * KT_ELEMS, n0, &full[s]);
-        }
+        tma_load_2d(sb, &tmB, kt * KT_ELEMS, n0, &full[s]);
         armed = kt + 1;
       }
       // every armed stage must have landed before the CTA may exit (its shared memory is reused)
@@ -485,7 +348,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc =
-          MODE >= 2 ? idesc_e4m3(TC_BM, TC_BN, RAW) : idesc_f16(PACKED ? 0u : 1u, TC_BM, TC_BN);
+          MODE == 2 ? idesc_e4m3(TC_BM, TC_BN) : idesc_f16(PACKED ? 0u : 1u, TC_BM, TC_BN);
       int kt = 0;
       for (int c = 0; c < nchunks && !*abort_flag; ++c) {
         const int buf = c & 1;
@@ -500,15 +363,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tc_fence_after();
           const uint8_t* sa = smem + s * TC_STAGE_BYTES;
           const uint8_t* sb = sa + TC_A_BYTES;
-          const uint64_t ad = smem_desc_sw128(sa);
-          const uint64_t bd = RAW ? smem_desc_mn_sw128(sb, TC_B_BYTES / 2) : smem_desc_sw128(sb);
+          const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sb);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            // K-major: advance 32 bytes along K inside the swizzled 128-byte rows (16 x 16-bit
-            // or 32 x fp8).  MN-major B: advance 32 rows of 128 bytes (4 core groups).
-            const uint64_t bk = RAW ? (uint64_t)(kk * 256) : (uint64_t)(kk * 2);
-            if (MODE >= 2) mma_f8(dtm, ad + (uint64_t)(kk * 2), bd + bk, idesc, first ? 0u : 1u);
-            else mma_f16(dtm, ad + (uint64_t)(kk * 2), bd + bk, idesc, first ? 0u : 1u);
+            // advance 32 bytes along K inside the swizzled 128-byte rows (16 x 16-bit or 32 x fp8)
+            if (MODE == 2) mma_f8(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, first ? 0u : 1u);
+            else mma_f16(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, first ? 0u : 1u);
             first = false;
           }
           mma_commit(&empty[s]);    // stage s free once these MMAs have read it
@@ -529,32 +389,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int half = (warp - 2) >> 2;            // column half (0: 0..127, 1: 128..255)
     const int row = m0 + q * 32 + lane;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    if (RAW && warp == 2) {
-      // range check of this CTA's slice of every stage, then release the stage
-      const uint32_t a_units = TC_A_BYTES / 16, b_units = TC_B_BYTES / 16;
-      const uint32_t a_per = (a_units + gridDim.x - 1) / gridDim.x, b_per = (b_units + gridDim.y - 1) / gridDim.y;
-      const uint32_t a_lo = min(a_units, blockIdx.x * a_per), a_hi = min(a_units, a_lo + a_per);
-      const uint32_t b_lo = min(b_units, blockIdx.y * b_per), b_hi = min(b_units, b_lo + b_per);
-      const uint32_t pp = 0x01010101u * P.p;
-      uint32_t bad = 0;
-      for (int kt = 0; kt < ktiles; ++kt) {
-        const int s = kt % TC_STAGES;
-        if (!mbar_wait(&full[s], (uint32_t)(kt / TC_STAGES) & 1u, abort_flag)) break;
-        const uint4* sa = reinterpret_cast<const uint4*>(smem + s * TC_STAGE_BYTES);
-        const uint4* sb = reinterpret_cast<const uint4*>(smem + s * TC_STAGE_BYTES + TC_A_BYTES);
-        for (uint32_t u = a_lo + lane; u < a_hi; u += 32) {
-          const uint4 x = sa[u];
-          bad |= __vcmpgeu4(x.x, pp) | __vcmpgeu4(x.y, pp) | __vcmpgeu4(x.z, pp) | __vcmpgeu4(x.w, pp);
-        }
-        for (uint32_t u = b_lo + lane; u < b_hi; u += 32) {
-          const uint4 x = sb[u];
-          bad |= __vcmpgeu4(x.x, pp) | __vcmpgeu4(x.y, pp) | __vcmpgeu4(x.z, pp) | __vcmpgeu4(x.w, pp);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-      }
-      if (bad) flag_error(err, ERR_RANGE);
-    }
     if (!PACKED) {
       bool ok = mbar_wait(&tfull[0], 0, abort_flag);
       tc_fence_after();
@@ -568,9 +402,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           uint32_t w = 0;
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
-            // MODE 3 sums are 2^-18 times the integer sums (operands r 2^-9): scale back exactly
-            const float f = RAW ? __uint_as_float(v[j + t]) * 262144.0f : __uint_as_float(v[j + t]);
-            uint32_t x = __float2uint_rn(f);
+            uint32_t x = __float2uint_rn(__uint_as_float(v[j + t]));
             w |= modp32(x, P.dv, P.p) << (8 * t);
           }
           packed[j >> 2] = w;
@@ -725,48 +557,6 @@ __global__ void k_selftest_wait(uint32_t polls, uint32_t* err) {
   __syncthreads();
 }
 
-// ---------------------------------------------------------------- host side
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn get_encode() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
-  return fn;
-}
-
-// 2-D map of a rows x cols row-major matrix of 16-bit (esize 2) or 8-bit (esize 1) elements
-// with leading dimension ld elements (ld * esize a multiple of 16, base 16-byte aligned),
-// box = box_rows x (128 bytes of elements), 128-byte swizzle; reads past cols or rows return 0.
-static fp_status make_map_ld(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
-                             uint32_t box_rows, uint32_t esize) {
-  EncodeTiledFn enc = get_encode();
-  FP_CHECK(enc != nullptr, FP_ECUDA, "cuTensorMapEncodeTiled is not available");
-  cuuint64_t dims[2] = {cols, rows};
-  cuuint64_t strides[1] = {ld * esize};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / esize), box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
-                   const_cast<void*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  FP_CHECK(r == CUDA_SUCCESS, FP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-  return FP_OK;
-}
-static fp_status make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t kp, uint32_t box_rows,
-                          uint32_t esize = 2) {
-  return make_map_ld(map, base, rows, kp, kp, box_rows, esize);
-}
 
 fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda, const uint8_t* B,
                        int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st) {
@@ -780,19 +570,10 @@ fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_
     const size_t smem8 = 1024 + TC_STAGES * TC_STAGE_BYTES + 256;
     dim3 grid8((n + TC_BN - 1) / TC_BN, (m + TC_BM - 1) / TC_BM);
     RedqParams P8 = make_redq(p, 16, 1);
-    if ((((uintptr_t)A | (uintptr_t)B) & 15u) == 0 && (lda & 15) == 0 && (ldb & 15) == 0) {
-      // the caller's bytes are the e4m3 operands (r 2^-9): A K-major, B MN-major, no conversion
-      CUtensorMap mar, mbr;
-      fp_status sr = make_map_ld(&mar, A, (uint64_t)m, (uint64_t)k, (uint64_t)lda, TC_BM, 1);
-      if (sr != FP_OK) return sr;
-      sr = make_map_ld(&mbr, B, (uint64_t)k, (uint64_t)n, (uint64_t)ldb, 128, 1);
-      if (sr != FP_OK) return sr;
-      FP_CUDA(cudaFuncSetAttribute(k_mm_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem8));
-      FP_LAUNCH(ctx, "k_mm_tc", st,
-                k_mm_tc<3><<<grid8, TC_THREADS, smem8, st>>>(mar, mbr, C, ldc, nullptr, m, n, n, kp8 / 128, P8, 0,
-                                                          ctx->d_err));
-      FP_CUDA(cudaGetLastError());
-      return FP_OK;
+    if (f8_direct_ok(p, k, A, lda, B, ldb)) {
+      // the caller's bytes are the e4m3 operands (r 2^-9): the persistent grouped kernel
+      const fp_mm_problem x = {p, m, n, k, A, lda, B, ldb, C, ldc};
+      return launch_mm_f8_direct(ctx, x, st);
     }
     const size_t ab = ((size_t)m * kp8 + 1023) & ~(size_t)1023, bb = ((size_t)n * kp8 + 1023) & ~(size_t)1023;
     fp_status s8 = ensure_scratch(ctx, ab + bb + 1024);

@@ -1,0 +1,337 @@
+// Grouped, persistent plain product C = A B mod p on the tcgen05 tensor cores with e4m3
+// operands (kind::f8f6f4, fp32 accumulation in TMEM) for several independent problems in one
+// launch.
+//
+// Residues 0..16 read as e4m3 bit patterns are exactly r 2^-9 (codes 0..7 are subnormals
+// m 2^-9, codes 8..15 the binade [2^-6, 2^-5) with step 2^-9, code 16 is 2^-5), so the
+// caller's uint8 arrays are the MMA operands as they stand: A K-major (rows of k bytes), B
+// MN-major (rows of n bytes, one per k).  Each fp32 sum is 2^-18 times the integer sum
+// sum_l a_il b_lj, exact while that integer stays below 2^24 (k (p-1)^2 < 2^24); the epilogue
+// scales it back by 2^18 and reduces it mod p (delayed reduction, Sec. 2.2, with a single
+// reduction at the end).
+//
+// Persistent schedule: one CTA per SM walks the global list of 128 x 256 output tiles (all
+// problems, those with the longest inner dimension first) with stride gridDim.x.  Roles:
+//   warp 0       TMA producer: per k tile, A 128 x 128 bytes and B two boxes of 128 x 128
+//                bytes (128-byte swizzle) into a 4-stage shared-memory ring,
+//   warp 1       TMEM allocation (512 columns = two 128 x 256 fp32 accumulators) and the
+//                single MMA-issuing thread; tile i accumulates into buffer i & 1,
+//   warps 2..9   epilogue of tile i (tcgen05.ld, scale, mod p, stores) while the MMAs of tile
+//                i + 1 run into the other buffer,
+//   warp 10      range check: the A tile of (problem, row block, k tile) is loaded by the
+//                tiles of every column block and the B tile by those of every row block, so
+//                the tile in column block nb checks slice nb of its A bytes and the tile in row
+//                block mb slice mb of its B bytes: every input byte is checked exactly once.
+// A stage is released when the MMAs that read it have completed (tcgen05.commit) and the
+// range checker has passed it (two arrivals).  Every wait is bounded: a wait that gives up
+// sets the abort flag, the roles stop, in-flight copies and MMAs are drained, TMEM is freed and
+// the context's sticky flag reports ERR_TIMEOUT.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "fpdqt_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fpd {
+
+static constexpr int G_BM = 128, G_BN = 256, G_BK = 128, G_STAGES = 4;
+static constexpr int G_A_BYTES = G_BM * G_BK;                 // 16 KB
+static constexpr int G_B_BYTES = G_BN * G_BK;                 // 32 KB (two 128-column boxes)
+static constexpr int G_STAGE_BYTES = G_A_BYTES + G_B_BYTES;   // 48 KB
+static constexpr int G_THREADS = 352;                         // 11 warps
+static constexpr size_t G_SMEM = 1024 + G_STAGES * G_STAGE_BYTES + 256;
+
+struct GProb {
+  CUtensorMap ta;   // A: m rows x k columns, leading dimension lda
+  CUtensorMap tb;   // B: k rows x n columns, leading dimension ldb
+  uint8_t* C;
+  int ldc, m, n;
+  int ktiles;       // ceil(k / 128)
+  int tm, tn;       // row blocks ceil(m / 128), column blocks ceil(n / 256)
+  int tile0;        // index of this problem's first tile in the global list
+  uint32_t p;
+  DivP dv;
+};
+
+struct GParams {
+  GProb prob[FP_GROUP_MAX];
+  int nprob;
+  int total;        // tiles over all problems
+};
+
+struct GTile {
+  const GProb* pr;
+  int m0, n0, mb, nb;
+};
+
+__device__ __forceinline__ GTile g_tile(const GParams& g, int t) {
+  int i = 0;
+  while (i + 1 < g.nprob && t >= g.prob[i + 1].tile0) ++i;
+  const GProb& pr = g.prob[i];
+  const int local = t - pr.tile0;
+  GTile x;
+  x.pr = &pr;
+  x.mb = local / pr.tn;
+  x.nb = local - x.mb * pr.tn;
+  x.m0 = x.mb * G_BM;
+  x.n0 = x.nb * G_BN;
+  return x;
+}
+
+__global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__ GParams g, uint32_t* err) {
+  extern __shared__ __align__(1024) uint8_t g_smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)g_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + G_STAGES * G_STAGE_BYTES);
+  uint64_t* empty = full + G_STAGES;
+  uint64_t* tfull = empty + G_STAGES;    // [2] accumulator buffer ready
+  uint64_t* tempty = tfull + 2;          // [2] accumulator buffer drained
+  uint64_t* drainb = tempty + 2;         // MMA completion on the abort path
+  uint64_t* doneb = drainb + 1;          // every epilogue warp finished with TMEM
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(doneb + 1);
+  volatile uint32_t* abort_flag = tmem_slot + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr uint32_t TMEM_COLS = 512;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < G_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 2);        // MMA commit + range checker
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 8);       // one arrival per epilogue warp
+    }
+    mbar_init(drainb, 1);
+    mbar_init(doneb, 8);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t it = 0;              // k tiles issued by this CTA (all its tiles)
+      bool stop = false;
+      for (int t = blockIdx.x; t < g.total && !stop; t += gridDim.x) {
+        const GTile x = g_tile(g, t);
+        for (int kt = 0; kt < x.pr->ktiles; ++kt, ++it) {
+          const int s = (int)(it % G_STAGES);
+          if (*abort_flag || !mbar_wait(&empty[s], ((it / G_STAGES) & 1u) ^ 1u, abort_flag)) {
+            stop = true;
+            break;
+          }
+          uint8_t* sa = smem + s * G_STAGE_BYTES;
+          uint8_t* sb = sa + G_A_BYTES;
+          mbar_expect_tx(&full[s], G_STAGE_BYTES);
+          tma_load_2d(sa, &x.pr->ta, kt * G_BK, x.m0, &full[s]);
+          tma_load_2d(sb, &x.pr->tb, x.n0, kt * G_BK, &full[s]);
+          tma_load_2d(sb + G_B_BYTES / 2, &x.pr->tb, x.n0 + 128, kt * G_BK, &full[s]);
+        }
+      }
+      // every armed stage must have landed before the CTA may exit (its shared memory is reused)
+      for (uint32_t j = (it > (uint32_t)G_STAGES ? it - G_STAGES : 0u); j < it; ++j)
+        mbar_drain(&full[j % G_STAGES], (j / G_STAGES) & 1u);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_e4m3(G_BM, G_BN, true);
+      uint32_t it = 0;
+      bool stop = false;
+      int lt = 0;                   // tiles of this CTA so far
+      for (int t = blockIdx.x; t < g.total && !stop; t += gridDim.x, ++lt) {
+        const GTile x = g_tile(g, t);
+        const int buf = lt & 1;
+        if (lt >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((lt - 2) >> 1) & 1u, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t dtm = tmem + (uint32_t)(buf * 256);
+        for (int kt = 0; kt < x.pr->ktiles; ++kt, ++it) {
+          const int s = (int)(it % G_STAGES);
+          if (!mbar_wait(&full[s], (it / G_STAGES) & 1u, abort_flag)) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint8_t* sa = smem + s * G_STAGE_BYTES;
+          const uint8_t* sb = sa + G_A_BYTES;
+          const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_mn_sw128(sb, G_B_BYTES / 2);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)   // K = 32 per MMA: A +32 bytes in the row, B +32 rows
+            mma_f8(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 256), idesc, (kt | kk) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        if (!stop) mma_commit(&tfull[buf]);
+      }
+      if (*abort_flag) {            // every MMA issued so far completes before TMEM is freed
+        mma_commit(drainb);
+        mbar_drain(drainb, 0);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 10) {
+    // ------------------------------------------------ range check of the inputs
+    uint32_t it = 0, bad = 0;
+    bool stop = false;
+    for (int t = blockIdx.x; t < g.total && !stop; t += gridDim.x) {
+      const GTile x = g_tile(g, t);
+      const uint32_t a_units = G_A_BYTES / 16, b_units = G_B_BYTES / 16;
+      const uint32_t a_per = (a_units + x.pr->tn - 1) / x.pr->tn, b_per = (b_units + x.pr->tm - 1) / x.pr->tm;
+      const uint32_t a_lo = min(a_units, (uint32_t)x.nb * a_per), a_hi = min(a_units, a_lo + a_per);
+      const uint32_t b_lo = min(b_units, (uint32_t)x.mb * b_per), b_hi = min(b_units, b_lo + b_per);
+      const uint32_t pv = 0x01010101u * x.pr->p;
+      for (int kt = 0; kt < x.pr->ktiles; ++kt, ++it) {
+        const int s = (int)(it % G_STAGES);
+        if (!mbar_wait(&full[s], (it / G_STAGES) & 1u, abort_flag)) {
+          stop = true;
+          break;
+        }
+        const uint4* sa = reinterpret_cast<const uint4*>(smem + s * G_STAGE_BYTES);
+        const uint4* sb = reinterpret_cast<const uint4*>(smem + s * G_STAGE_BYTES + G_A_BYTES);
+        for (uint32_t u = a_lo + lane; u < a_hi; u += 32) {
+          const uint4 v = sa[u];
+          bad |= __vcmpgeu4(v.x, pv) | __vcmpgeu4(v.y, pv) | __vcmpgeu4(v.z, pv) | __vcmpgeu4(v.w, pv);
+        }
+        for (uint32_t u = b_lo + lane; u < b_hi; u += 32) {
+          const uint4 v = sb[u];
+          bad |= __vcmpgeu4(v.x, pv) | __vcmpgeu4(v.y, pv) | __vcmpgeu4(v.z, pv) | __vcmpgeu4(v.w, pv);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+      }
+    }
+    if (bad) flag_error(err, ERR_RANGE);
+  } else {
+    // ------------------------------------------------ epilogue (warps 2..9)
+    const int q = warp & 3;                      // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;            // column half (0: 0..127, 1: 128..255)
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    int lt = 0;
+    for (int t = blockIdx.x; t < g.total; t += gridDim.x, ++lt) {
+      const int buf = lt & 1;
+      if (!mbar_wait(&tfull[buf], (uint32_t)(lt >> 1) & 1u, abort_flag)) break;
+      tc_fence_after();
+      const GTile x = g_tile(g, t);
+      const GProb& pr = *x.pr;
+      const DivP dv = pr.dv;
+      const uint32_t p = pr.p;
+      const int row = x.m0 + q * 32 + lane;
+      for (int cb = 0; cb < 4; ++cb) {
+        const int col0 = half * 128 + cb * 32;
+        uint32_t v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(buf * 256 + col0), v);
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          uint32_t w = 0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            // the sum is 2^-18 times the integer sum: scaling back by 2^18 is exact
+            const uint32_t s = __float2uint_rn(__uint_as_float(v[j + u]) * 262144.0f);
+            w |= modp32(s, dv, p) << (8 * u);
+          }
+          packed[j >> 2] = w;
+        }
+        const int c0 = x.n0 + col0;
+        if (row < pr.m && c0 < pr.n) {
+          uint8_t* dst = pr.C + (size_t)row * pr.ldc + c0;
+          if (c0 + 32 <= pr.n && ((((uintptr_t)dst) & 15u) == 0)) {
+            reinterpret_cast<uint4*>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            reinterpret_cast<uint4*>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+          } else {
+            for (int j = 0; j < 32 && c0 + j < pr.n; ++j) dst[j] = (uint8_t)(packed[j >> 2] >> (8 * (j & 3)));
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
+    __syncwarp();
+    tc_fence_before();
+    if (lane == 0) mbar_arrive(doneb);
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) flag_error(err, ERR_TIMEOUT);
+  if (warp == 1) {
+    // TMEM is freed only after every epilogue warp has signalled that it is done with it
+    if (lane == 0) mbar_drain(doneb, 0);
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+bool f8_direct_ok(uint32_t p, int k, const uint8_t* A, int lda, const uint8_t* B, int ldb) {
+  const uint64_t pp = (uint64_t)(p - 1) * (p - 1);
+  return p <= 17 && (uint64_t)k * pp < (1ull << 24) && (((uintptr_t)A | (uintptr_t)B) & 15u) == 0 &&
+         (lda & 15) == 0 && (ldb & 15) == 0;
+}
+
+// One launch over up to FP_GROUP_MAX problems, each already validated and f8_direct_ok.
+static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int count, cudaStream_t st) {
+  GParams hp;          // passed by value as the kernel's (grid-constant) parameter block
+  std::memset(&hp, 0, sizeof hp);
+  int tile = 0;
+  for (int i = 0; i < count; ++i) {
+    const fp_mm_problem& x = *pr[i];
+    GProb& g = hp.prob[i];
+    fp_status s = make_map_ld(&g.ta, x.A, (uint64_t)x.m, (uint64_t)x.k, (uint64_t)x.lda, G_BM, 1);
+    if (s != FP_OK) return s;
+    s = make_map_ld(&g.tb, x.B, (uint64_t)x.k, (uint64_t)x.n, (uint64_t)x.ldb, 128, 1);
+    if (s != FP_OK) return s;
+    g.C = x.C;
+    g.ldc = x.ldc;
+    g.m = x.m;
+    g.n = x.n;
+    g.ktiles = (x.k + G_BK - 1) / G_BK;
+    g.tm = (x.m + G_BM - 1) / G_BM;
+    g.tn = (x.n + G_BN - 1) / G_BN;
+    g.tile0 = tile;
+    g.p = x.p;
+    g.dv = make_divp(x.p);
+    tile += g.tm * g.tn;
+  }
+  hp.nprob = count;
+  hp.total = tile;
+  const int grid = std::min(tile, ctx->num_sms);
+  FP_CUDA(cudaFuncSetAttribute(k_mm_f8g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G_SMEM));
+  FP_LAUNCH(ctx, "k_mm_f8g", st, k_mm_f8g<<<grid, G_THREADS, G_SMEM, st>>>(hp, ctx->d_err));
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
+// One problem (the caller holds the context lock).
+fp_status launch_mm_f8_direct(fp_ctx ctx, const fp_mm_problem& x, cudaStream_t st) {
+  const fp_mm_problem* one = &x;
+  return launch_group(ctx, &one, 1, st);
+}
+
+// Problems that pass f8_direct_ok, in launches of up to FP_GROUP_MAX problems; within a
+// launch the problems with the most k tiles come first so the longest tiles start earliest.
+fp_status launch_mm_f8_grouped(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st) {
+  std::vector<const fp_mm_problem*> v(pr, pr + count);
+  std::stable_sort(v.begin(), v.end(), [](const fp_mm_problem* a, const fp_mm_problem* b) { return a->k > b->k; });
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  for (size_t i = 0; i < v.size(); i += FP_GROUP_MAX) {
+    const int c = (int)std::min<size_t>(FP_GROUP_MAX, v.size() - i);
+    fp_status s = launch_group(ctx, v.data() + i, c, st);
+    if (s != FP_OK) return s;
+  }
+  return FP_OK;
+}
+
+}  // namespace fpd

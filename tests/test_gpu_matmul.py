@@ -167,8 +167,9 @@ def _padded(torch, dev, x, ld, fill):
                                      (17, 257, 255, 96), (5, 1, 1, 1), (13, 300, 600, 129)])
 def test_matmul_f8_direct_operands(env, p, m, n, k):
     """PLAIN_F8 on 16-byte aligned leading dimensions streams the caller's residue bytes as
-    e4m3 (r 2^-9) with B MN-major: ragged m, n, k, the pad bytes past k and n set to 255
-    (out of range, so reading them would also raise the range error), no conversion pass."""
+    e4m3 (r 2^-9) with B MN-major in the persistent kernel: ragged m, n, k, the pad bytes past
+    k and n set to 255 (out of range, so reading them would also raise the range error), no
+    conversion pass."""
     fp, torch, dev, ctx = env
     a, b = workloads.matmul_inputs(p * 77 + k, p, m, k, n)
     lda, ldb, ldc = -(-k // 16) * 16 + 16, -(-n // 16) * 16, n + 3
@@ -179,7 +180,7 @@ def test_matmul_f8_direct_operands(env, p, m, n, k):
     fp.fp_matmul(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, fp.FP_MM_PLAIN_F8)
     fp.fp_ctx_status(ctx)
     conv, _ = fp.fp_ctx_profile_read(ctx, "k_tc_convert")
-    mm, _ = fp.fp_ctx_profile_read(ctx, "k_mm_tc")
+    mm, _ = fp.fp_ctx_profile_read(ctx, "k_mm_f8g")
     fp.fp_ctx_profile(ctx, 0)
     got = C.cpu().numpy()
     assert (conv, mm) == (0, 1)
