@@ -17,13 +17,15 @@
 //   warp 1       TMEM allocation (512 columns = two 128 x 256 fp32 accumulators) and the
 //                single MMA-issuing thread; tile i accumulates into buffer i & 1,
 //   warps 2..9   epilogue of tile i (tcgen05.ld, scale, mod p, stores) while the MMAs of tile
-//                i + 1 run into the other buffer,
-//   warp 10      range check: the A tile of (problem, row block, k tile) is loaded by the
-//                tiles of every column block and the B tile by those of every row block, so
-//                the tile in column block nb checks slice nb of its A bytes and the tile in row
-//                block mb slice mb of its B bytes: every input byte is checked exactly once.
-// A stage is released when the MMAs that read it have completed (tcgen05.commit) and the
-// range checker has passed it (two arrivals).  Every wait is bounded: a wait that gives up
+//                i + 1 run into the other buffer.  Before waiting for a tile's accumulator they
+//                range-check a slice of its inputs with plain global loads (off the shared-
+//                memory pipeline, whose stages they never touch): the A panel of (problem, row
+//                block) is used by the tiles of every column block and the B panel of (problem,
+//                column block) by those of every row block, so the tile in column block nb
+//                checks slice nb of its A panel and the tile in row block mb slice mb of its B
+//                panel: every input byte is checked exactly once.
+// A stage is released when the MMAs that read it have completed (tcgen05.commit).  Every wait
+// is bounded: a wait that gives up
 // sets the abort flag, the roles stop, in-flight copies and MMAs are drained, TMEM is freed and
 // the context's sticky flag reports ERR_TIMEOUT.
 #include <algorithm>
@@ -39,14 +41,16 @@ static constexpr int G_BM = 128, G_BN = 256, G_BK = 128, G_STAGES = 4;
 static constexpr int G_A_BYTES = G_BM * G_BK;                 // 16 KB
 static constexpr int G_B_BYTES = G_BN * G_BK;                 // 32 KB (two 128-column boxes)
 static constexpr int G_STAGE_BYTES = G_A_BYTES + G_B_BYTES;   // 48 KB
-static constexpr int G_THREADS = 352;                         // 11 warps
+static constexpr int G_THREADS = 320;                         // 10 warps
 static constexpr size_t G_SMEM = 1024 + G_STAGES * G_STAGE_BYTES + 256;
 
 struct GProb {
   CUtensorMap ta;   // A: m rows x k columns, leading dimension lda
   CUtensorMap tb;   // B: k rows x n columns, leading dimension ldb
+  const uint8_t* A;
+  const uint8_t* B;
   uint8_t* C;
-  int ldc, m, n;
+  int lda, ldb, ldc, m, n, k;
   int ktiles;       // ceil(k / 128)
   int tm, tn;       // row blocks ceil(m / 128), column blocks ceil(n / 256)
   int tile0;        // index of this problem's first tile in the global list
@@ -79,6 +83,31 @@ __device__ __forceinline__ GTile g_tile(const GParams& g, int t) {
   return x;
 }
 
+// Bit 7 of a byte of the result is set where one of the `valid` bytes at src (at most 16;
+// src 16-byte aligned when valid >= 16) is >= p, with pk = 0x01010101 (128 - p): for bytes
+// below 128, r + 128 - p has bit 7 set exactly when r >= p and carries into no other byte.
+// Bytes past `valid` (the caller's padding, possibly unallocated) are not read.
+__device__ __forceinline__ uint32_t range_bits(const uint8_t* src, int valid, uint32_t pk) {
+  uint32_t w[4];
+  if (valid >= 16) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(src));
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t x = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (4 * j + b < valid) x |= (uint32_t)__ldg(src + 4 * j + b) << (8 * b);
+      w[j] = x;
+    }
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) acc |= w[j] | (w[j] + pk);
+  return acc;
+}
+
 __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__ GParams g, uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t g_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)g_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -97,7 +126,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
   if (threadIdx.x == 0) {
     for (int s = 0; s < G_STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 2);        // MMA commit + range checker
+      mbar_init(&empty[s], 1);        // MMA commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -180,50 +209,40 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
       }
     }
     __syncwarp();
-  } else if (warp == 10) {
-    // ------------------------------------------------ range check of the inputs
-    uint32_t it = 0, bad = 0;
-    bool stop = false;
-    for (int t = blockIdx.x; t < g.total && !stop; t += gridDim.x) {
-      const GTile x = g_tile(g, t);
-      const uint32_t a_units = G_A_BYTES / 16, b_units = G_B_BYTES / 16;
-      const uint32_t a_per = (a_units + x.pr->tn - 1) / x.pr->tn, b_per = (b_units + x.pr->tm - 1) / x.pr->tm;
-      const uint32_t a_lo = min(a_units, (uint32_t)x.nb * a_per), a_hi = min(a_units, a_lo + a_per);
-      const uint32_t b_lo = min(b_units, (uint32_t)x.mb * b_per), b_hi = min(b_units, b_lo + b_per);
-      const uint32_t pv = 0x01010101u * x.pr->p;
-      for (int kt = 0; kt < x.pr->ktiles; ++kt, ++it) {
-        const int s = (int)(it % G_STAGES);
-        if (!mbar_wait(&full[s], (it / G_STAGES) & 1u, abort_flag)) {
-          stop = true;
-          break;
-        }
-        const uint4* sa = reinterpret_cast<const uint4*>(smem + s * G_STAGE_BYTES);
-        const uint4* sb = reinterpret_cast<const uint4*>(smem + s * G_STAGE_BYTES + G_A_BYTES);
-        for (uint32_t u = a_lo + lane; u < a_hi; u += 32) {
-          const uint4 v = sa[u];
-          bad |= __vcmpgeu4(v.x, pv) | __vcmpgeu4(v.y, pv) | __vcmpgeu4(v.z, pv) | __vcmpgeu4(v.w, pv);
-        }
-        for (uint32_t u = b_lo + lane; u < b_hi; u += 32) {
-          const uint4 v = sb[u];
-          bad |= __vcmpgeu4(v.x, pv) | __vcmpgeu4(v.y, pv) | __vcmpgeu4(v.z, pv) | __vcmpgeu4(v.w, pv);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-      }
-    }
-    if (bad) flag_error(err, ERR_RANGE);
   } else {
     // ------------------------------------------------ epilogue (warps 2..9)
     const int q = warp & 3;                      // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;            // column half (0: 0..127, 1: 128..255)
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const uint32_t tid = threadIdx.x - 64;       // 0..255 over the epilogue warps
+    uint32_t bad = 0;
     int lt = 0;
     for (int t = blockIdx.x; t < g.total; t += gridDim.x, ++lt) {
       const int buf = lt & 1;
-      if (!mbar_wait(&tfull[buf], (uint32_t)(lt >> 1) & 1u, abort_flag)) break;
-      tc_fence_after();
       const GTile x = g_tile(g, t);
       const GProb& pr = *x.pr;
+      {
+        // range check: a residue byte r >= p (p <= 17) has bit 7 set in r | (r + 128 - p),
+        // with no carry between bytes unless bit 7 of the lower byte is already set
+        const uint32_t pk = 0x01010101u * (128u - pr.p);
+        const uint32_t kc = (uint32_t)(pr.k + 15) >> 4;                  // 16-byte chunks per A row
+        const uint32_t a_rows = (uint32_t)min(G_BM, pr.m - x.m0);
+        const uint32_t a_units = a_rows * kc, a_per = (a_units + pr.tn - 1) / pr.tn;
+        const uint32_t a_lo = min(a_units, (uint32_t)x.nb * a_per), a_hi = min(a_units, a_lo + a_per);
+        for (uint32_t u = a_lo + tid; u < a_hi; u += 256) {
+          const uint32_t r = u / kc, c = u - r * kc;
+          bad |= range_bits(pr.A + (size_t)(x.m0 + r) * pr.lda + 16 * c, pr.k - 16 * (int)c, pk);
+        }
+        const uint32_t bc = (uint32_t)(min(G_BN, pr.n - x.n0) + 15) >> 4;  // 16-byte chunks per B row
+        const uint32_t b_units = (uint32_t)pr.k * bc, b_per = (b_units + pr.tm - 1) / pr.tm;
+        const uint32_t b_lo = min(b_units, (uint32_t)x.mb * b_per), b_hi = min(b_units, b_lo + b_per);
+        for (uint32_t u = b_lo + tid; u < b_hi; u += 256) {
+          const uint32_t r = u / bc, c = u - r * bc;
+          bad |= range_bits(pr.B + (size_t)r * pr.ldb + x.n0 + 16 * c, pr.n - x.n0 - 16 * (int)c, pk);
+        }
+      }
+      if (!mbar_wait(&tfull[buf], (uint32_t)(lt >> 1) & 1u, abort_flag)) break;
+      tc_fence_after();
       const DivP dv = pr.dv;
       const uint32_t p = pr.p;
       const int row = x.m0 + q * 32 + lane;
@@ -258,6 +277,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[buf]);
     }
+    if (bad & 0x80808080u) flag_error(err, ERR_RANGE);
     __syncwarp();
     tc_fence_before();
     if (lane == 0) mbar_arrive(doneb);
@@ -293,10 +313,15 @@ static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int co
     if (s != FP_OK) return s;
     s = make_map_ld(&g.tb, x.B, (uint64_t)x.k, (uint64_t)x.n, (uint64_t)x.ldb, 128, 1);
     if (s != FP_OK) return s;
+    g.A = x.A;
+    g.B = x.B;
     g.C = x.C;
+    g.lda = x.lda;
+    g.ldb = x.ldb;
     g.ldc = x.ldc;
     g.m = x.m;
     g.n = x.n;
+    g.k = x.k;
     g.ktiles = (x.k + G_BK - 1) / G_BK;
     g.tm = (x.m + G_BM - 1) / G_BM;
     g.tn = (x.n + G_BN - 1) / G_BN;

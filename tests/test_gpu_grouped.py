@@ -175,3 +175,29 @@ def test_grouped_host_checks(env):
     with pytest.raises(fp.FpError) as ei:
         fp.fp_matmul_grouped(ctx, [ok], fp.FP_MM_LEFT_F32 + 10)
     assert ei.value.status == fp.FP_EINVAL
+
+
+def test_grouped_range_check_covers_every_position(env):
+    """One out-of-range byte at each of 80 random positions of A and B (one at a time, in a
+    group of two products of different shapes): each is caught, so the slices the tiles check
+    cover the whole of both inputs, including partial 16-byte chunks at row ends."""
+    fp, torch, dev, ctx = env
+    other = Prob(fp, torch, dev, 51, 13, 100, 200, 300)
+    q = Prob(fp, torch, dev, 52, 11, 300, 600, 333, pad_fill=0)
+    rng = np.random.default_rng(5)
+    spots = [("A", int(rng.integers(q.m)), int(rng.integers(q.k))) for _ in range(40)] + \
+            [("B", int(rng.integers(q.k)), int(rng.integers(q.n))) for _ in range(40)]
+    spots += [("A", q.m - 1, q.k - 1), ("B", q.k - 1, q.n - 1), ("A", 0, 0), ("B", 0, 0)]
+    for which, r, c in spots:
+        T = q.A if which == "A" else q.B
+        old = int(T[r, c].item())
+        T[r, c] = 200 if r % 2 else q.p
+        fp.fp_matmul_grouped(ctx, [other.desc, q.desc])
+        with pytest.raises(fp.FpError) as ei:
+            fp.fp_ctx_status(ctx)
+        assert ei.value.status == fp.FP_EINVAL, (which, r, c)
+        T[r, c] = old
+    fp.fp_matmul_grouped(ctx, [other.desc, q.desc])
+    fp.fp_ctx_status(ctx)
+    other.check()
+    q.check()
