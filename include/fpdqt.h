@@ -61,7 +61,10 @@ enum {
 
 /* Algorithm selectors for fp_matmul. */
 enum {
-  FP_MM_AUTO = 0,       /* planner: fastest packed (DQT + REDQ) variant valid for (p, k) */
+  FP_MM_AUTO = 0,       /* fastest exact variant: PLAIN_F8 on the caller's bytes when p <= 17,
+                           k (p-1)^2 < 2^24, A and B 16-byte aligned with lda, ldb multiples of 16
+                           (fastest measured on GB300 at every size); otherwise the candidate the
+                           autotuner measured fastest (packed or plain) */
   FP_MM_RIGHT_F64 = 1,  /* right compression (Sec. 7.4), FP64 words, FP64 tensor cores (DMMA) */
   FP_MM_RIGHT_F32 = 2,  /* right compression, FP32 words, FFMA, inner dimension split so the
                            digit bound holds per chunk; chunks folded into an integer word */
@@ -121,7 +124,7 @@ fp_status fp_ctx_profile_read(fp_ctx ctx, const char* prefix, uint64_t* launches
 fp_status fp_ctx_launches(fp_ctx ctx, uint64_t* count);
 
 /* AUTO-algorithm tuning for fp_matmul.  When enabled (the default), the first FP_MM_AUTO call
- * for a new (p, size class) times every exact candidate (packed tensor-core, plain
+ * for a new (p, size class) that cannot take the direct e4m3 path times every exact candidate (packed tensor-core, plain
  * tensor-core, u8 tensor-core, packed FP32) once on the caller's own buffers -- all produce the
  * same C -- synchronising the stream, and caches the fastest in the context; later calls of
  * that class use the cached choice without timing.  Do not make that first call inside a

@@ -548,6 +548,8 @@ fp_status launch_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8
                         const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(ctx->mu);  // scratch is shared by calls on this context
   if (algo != FP_MM_AUTO) return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, algo, st);
+  // the caller's bytes as e4m3 operands: fastest measured at every size where the layout allows it
+  if (f8_direct_ok(p, k, A, lda, B, ldb)) return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, FP_MM_PLAIN_F8, st);
   int cand[8];
   const int nc = candidates(p, m, n, k, cand);
   if (!ctx->autotune || nc == 1) return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, cand[0], st);

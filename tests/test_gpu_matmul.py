@@ -212,3 +212,35 @@ def test_matmul_f8_direct_range_check(env, where):
     fp.fp_matmul(ctx, p, m, n, k, A, lda, B, ldb, C, n, fp.FP_MM_PLAIN_F8)
     fp.fp_ctx_status(ctx)
     assert np.array_equal(C.cpu().numpy(), field.matmul_mod(a, b, p))
+
+
+def test_auto_direct_and_autotuned(env):
+    """AUTO: an aligned p <= 17 product takes the direct e4m3 kernel with no tuning runs; a
+    p = 31 product is timed once over the exact candidates, the winner is cached and reused."""
+    fp, torch, dev, ctx = env
+    p, n = 7, 512
+    a, b = workloads.matmul_inputs(71, p, n, n, n)
+    A, B = to_dev(torch, dev, a), to_dev(torch, dev, b)
+    C = torch.empty((n, n), dtype=torch.uint8, device=dev)
+    fp.fp_ctx_profile(ctx, 2)
+    fp.fp_ctx_profile(ctx, 1)
+    fp.fp_matmul(ctx, p, n, n, n, A, n, B, n, C, n, fp.FP_MM_AUTO)
+    fp.fp_ctx_status(ctx)
+    total, _ = fp.fp_ctx_profile_read(ctx, "")
+    direct, _ = fp.fp_ctx_profile_read(ctx, "k_mm_f8g")
+    fp.fp_ctx_profile(ctx, 0)
+    assert (total, direct) == (1, 1)
+    assert fp.fp_ctx_autotune_choice(ctx, p, n, n, n) == -1
+    assert np.array_equal(C.cpu().numpy(), field.matmul_mod(a, b, p))
+    p = 31
+    a, b = workloads.matmul_inputs(72, p, n, n, n)
+    A, B = to_dev(torch, dev, a), to_dev(torch, dev, b)
+    fp.fp_matmul(ctx, p, n, n, n, A, n, B, n, C, n, fp.FP_MM_AUTO)
+    fp.fp_ctx_status(ctx)
+    choice = fp.fp_ctx_autotune_choice(ctx, p, n, n, n)
+    assert choice in (fp.FP_MM_RIGHT_F64, fp.FP_MM_PLAIN_I8, fp.FP_MM_PLAIN_TC, fp.FP_MM_RIGHT_F32)
+    l0 = fp.fp_ctx_launches(ctx)
+    fp.fp_matmul(ctx, p, n, n, n, A, n, B, n, C, n, fp.FP_MM_AUTO)
+    fp.fp_ctx_status(ctx)
+    assert fp.fp_ctx_launches(ctx) - l0 <= 3       # the cached variant only, no timing runs
+    assert np.array_equal(C.cpu().numpy(), field.matmul_mod(a, b, p))
