@@ -61,8 +61,7 @@ enum {
 
 /* Algorithm selectors for fp_matmul. */
 enum {
-  FP_MM_AUTO = 0,       /* fastest exact variant: PLAIN_F8 on the caller's bytes when p <= 17,
-                           k (p-1)^2 < 2^24, A and B 16-byte aligned with lda, ldb multiples of 16
+  FP_MM_AUTO = 0,       /* fastest exact variant: PLAIN_F8 when p <= 17 and k (p-1)^2 < 2^24
                            (fastest measured on GB300 at every size); otherwise the candidate the
                            autotuner measured fastest (packed or plain) */
   FP_MM_RIGHT_F64 = 1,  /* right compression (Sec. 7.4), FP64 words, FP64 tensor cores (DMMA) */
@@ -75,8 +74,10 @@ enum {
   FP_MM_RIGHT_TC = 7,   /* right compression on tcgen05 kind::f16: fp16 operands holding two
                            centred residues at Q = 2^10, inner dimension chunked (p <= 3) */
   FP_MM_LEFT_F32 = 8,   /* left compression (Sec. 7.4, by transposition), FP32 words */
-  FP_MM_PLAIN_F8 = 9    /* unpacked, tcgen05 kind::f8f6f4 (e4m3 operands, exact for residues
-                           <= 16), fp32 accumulate: p <= 17 and k (p-1)^2 < 2^24 */
+  FP_MM_PLAIN_F8 = 9    /* unpacked, tcgen05 kind::f8f6f4, fp32 accumulate: the residue bytes
+                           are read as e4m3 (r 2^-9, exact for r <= 16); p <= 17 and
+                           k (p-1)^2 < 2^24.  A and B 16-byte aligned with lda, ldb multiples
+                           of 16 are read in place; other layouts are first copied padded */
 };
 
 /* Parameters of one packed representation (Sec. 2.3): q = 2^b, k residues packed per
@@ -124,7 +125,7 @@ fp_status fp_ctx_profile_read(fp_ctx ctx, const char* prefix, uint64_t* launches
 fp_status fp_ctx_launches(fp_ctx ctx, uint64_t* count);
 
 /* AUTO-algorithm tuning for fp_matmul.  When enabled (the default), the first FP_MM_AUTO call
- * for a new (p, size class) that cannot take the direct e4m3 path times every exact candidate (packed tensor-core, plain
+ * for a new (p, size class) outside PLAIN_F8's rule times every exact candidate (packed tensor-core, plain
  * tensor-core, u8 tensor-core, packed FP32) once on the caller's own buffers -- all produce the
  * same C -- synchronising the stream, and caches the fastest in the context; later calls of
  * that class use the cached choice without timing.  Do not make that first call inside a
@@ -236,15 +237,18 @@ typedef struct {
 /* Several independent products C_i = A_i B_i mod p_i (the paper has no counterpart: it treats
  * one product at a time; this call schedules Sec. 7's plain product, with the delayed
  * reduction of Sec. 2.2, over many of them).  `problems` is a HOST array of `count` entries
- * (count = 0 is a no-op); every entry is checked as fp_matmul checks its arguments before
- * anything is enqueued.  Output ranges must not overlap one another or any input.
+ * (count = 0 is a no-op); every entry is checked as fp_matmul checks its arguments, including
+ * the forced algorithm's exactness rule (FP_EBOUND), before anything is enqueued.  Output ranges must not overlap one another or any input.
  * With algo FP_MM_AUTO or FP_MM_PLAIN_F8, the problems with p <= 17, k (p-1)^2 < 2^24, A and
  * B 16-byte aligned and lda, ldb multiples of 16 run together in persistent tensor-core
  * launches of up to FP_GROUP_MAX problems: one CTA per SM takes 128 x 256 output tiles from
  * all of them (longest inner dimension first), its epilogue overlapping the next tile's
  * multiplications; the residue bytes are read in place as e4m3 operands.  Every other problem
  * runs through fp_matmul with the same algo, in order, on the same stream.  Residues >= p set
- * the context's range error (fp_ctx_status). */
+ * the context's range error (fp_ctx_status).  With algo FP_MM_RIGHT_TC (packed fp16, two
+ * residues of C per MMA column, Sec. 7.4) or FP_MM_PLAIN_TC (bf16) every problem runs in the
+ * persistent 16-bit kernel's grouped launches, after a conversion of each A and B into
+ * context scratch. */
 fp_status fp_matmul_grouped(fp_ctx ctx, const fp_mm_problem* problems, size_t count, int algo,
                             void* stream);
 

@@ -457,22 +457,29 @@ extern "C" fp_status fp_matmul_grouped(fp_ctx ctx, const fp_mm_problem* problems
   for (size_t i = 0; i < count; ++i) {
     const fp_mm_problem& x = problems[i];
     fp_status s = check_matmul(x.p, x.m, x.n, x.k, x.A, x.lda, x.B, x.ldb, x.C, x.ldc, algo);
+    if (s == FP_OK) s = mm_bound_check(x.p, x.k, algo);
     if (s != FP_OK) return s;
   }
   cudaStream_t st = as_stream(stream);
-  std::vector<const fp_mm_problem*> direct;
+  // which problems run grouped: the direct e4m3 kernel (AUTO, PLAIN_F8) or the 16-bit kernel
+  // (RIGHT_TC packed, PLAIN_TC plain); the rest one by one through fp_matmul's path
+  // (every problem passed mm_bound_check, so RIGHT_TC / PLAIN_TC problems all qualify)
   const bool f8 = algo == FP_MM_AUTO || algo == FP_MM_PLAIN_F8;
+  const bool t16 = algo == FP_MM_RIGHT_TC || algo == FP_MM_PLAIN_TC;
+  auto grouped = [&](const fp_mm_problem& x) {
+    return (f8 && f8_direct_ok(x.p, x.k, x.A, x.lda, x.B, x.ldb)) || t16;
+  };
+  std::vector<const fp_mm_problem*> grp;
   for (size_t i = 0; i < count; ++i)
-    if (f8 && f8_direct_ok(problems[i].p, problems[i].k, problems[i].A, problems[i].lda, problems[i].B,
-                           problems[i].ldb))
-      direct.push_back(&problems[i]);
-  if (!direct.empty()) {
-    fp_status s = launch_mm_f8_grouped(ctx, direct.data(), direct.size(), st);
+    if (grouped(problems[i])) grp.push_back(&problems[i]);
+  if (!grp.empty()) {
+    fp_status s = f8 ? launch_mm_f8_grouped(ctx, grp.data(), grp.size(), st)
+                     : launch_mm_t16_grouped(ctx, grp.data(), grp.size(), algo == FP_MM_RIGHT_TC, st);
     if (s != FP_OK) return s;
   }
   for (size_t i = 0; i < count; ++i) {
     const fp_mm_problem& x = problems[i];
-    if (f8 && f8_direct_ok(x.p, x.k, x.A, x.lda, x.B, x.ldb)) continue;
+    if (grouped(x)) continue;
     fp_status s = launch_matmul(ctx, x.p, x.m, x.n, x.k, x.A, x.lda, x.B, x.ldb, x.C, x.ldc, algo, st);
     if (s != FP_OK) return s;
   }

@@ -389,8 +389,15 @@ fp_status launch_pack_cb(fp_ctx ctx, uint32_t p, int k, int n, const uint8_t* B,
                          uint32_t e, uint32_t word, void* CB, cudaStream_t st);
 fp_status launch_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v, size_t n,
                      uint32_t* out, int algo, cudaStream_t st);
+fp_status mm_bound_check(uint32_t p, int k, int algo);
 // grouped e4m3 tensor-core product (k_tcg.cu)
 bool f8_direct_ok(uint32_t p, int k, const uint8_t* A, int lda, const uint8_t* B, int ldb);
 fp_status launch_mm_f8_direct(fp_ctx ctx, const fp_mm_problem& x, cudaStream_t st);   // lock held
 fp_status launch_mm_f8_grouped(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st);
+// grouped 16-bit tensor-core products (k_tcp.cu): packed fp16 (right compression, p <= 3)
+// or plain bf16
+bool f16p_ok(uint32_t p, int k);
+fp_status launch_mm_t16_direct(fp_ctx ctx, const fp_mm_problem& x, bool packed, cudaStream_t st);   // lock held
+fp_status launch_mm_t16_grouped(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, bool packed,
+                                cudaStream_t st);
 }  // namespace fpd

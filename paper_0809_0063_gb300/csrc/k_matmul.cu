@@ -525,6 +525,31 @@ static fp_status run_algo(fp_ctx ctx, uint32_t p, int m, int n, int k, const uin
 // Exact candidates for (p, k), fastest first by the fixed rule measured on GB300: packed
 // tensor-core words (p <= 3, large products), plain tensor cores, u8 tensor cores, packed FP32
 // words, packed FP64 words (always valid for k (p-1)^2 < 2^52).
+// The exactness rule of a forced algorithm, checked on the host (the same conditions the
+// launch paths enforce), so a group can be refused before anything is enqueued.
+fp_status mm_bound_check(uint32_t p, int k, int algo) {
+  const uint64_t pp = (uint64_t)(p - 1) * (p - 1);
+  uint32_t b, e, c;
+  switch (algo) {
+    case FP_MM_RIGHT_F64:
+    case FP_MM_RIGHT_F32: return mm_choose(p, (uint64_t)k, (uint32_t)algo, &b, &e, &c);
+    case FP_MM_PLAIN_I8:
+      FP_CHECK((uint64_t)k * pp < (1ull << 31), FP_EBOUND, "PLAIN_I8 needs k (p-1)^2 < 2^31");
+      return FP_OK;
+    case FP_MM_PLAIN_TC:
+      FP_CHECK((uint64_t)k * pp < (1ull << 24), FP_EBOUND, "PLAIN_TC needs k (p-1)^2 < 2^24");
+      return FP_OK;
+    case FP_MM_PLAIN_F8:
+      FP_CHECK(p <= 17 && (uint64_t)k * pp < (1ull << 24), FP_EBOUND, "PLAIN_F8 needs p <= 17, k (p-1)^2 < 2^24");
+      return FP_OK;
+    case FP_MM_RIGHT_TC:
+      FP_CHECK(p <= 3 && k <= 32767, FP_EBOUND, "RIGHT_TC needs p <= 3 and k <= 32767");
+      return FP_OK;
+    case FP_MM_LEFT_F32: FP_CHECK(false, FP_EUNSUPPORTED, "LEFT_F32 is not implemented");
+    default: return FP_OK;   // AUTO, PLAIN_F64, PLAIN_F32: every p <= 251, k <= 2^20
+  }
+}
+
 static int candidates(uint32_t p, int m, int n, int k, int* out) {
   uint64_t pp = (uint64_t)(p - 1) * (p - 1);
   int c = 0;
@@ -548,8 +573,10 @@ fp_status launch_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8
                         const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(ctx->mu);  // scratch is shared by calls on this context
   if (algo != FP_MM_AUTO) return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, algo, st);
-  // the caller's bytes as e4m3 operands: fastest measured at every size where the layout allows it
-  if (f8_direct_ok(p, k, A, lda, B, ldb)) return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, FP_MM_PLAIN_F8, st);
+  // e4m3 operands (the caller's bytes, or a padded copy of them): fastest measured at every
+  // size wherever its exactness rule holds
+  if (p <= 17 && (uint64_t)k * (p - 1) * (p - 1) < (1ull << 24))
+    return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, FP_MM_PLAIN_F8, st);
   int cand[8];
   const int nc = candidates(p, m, n, k, cand);
   if (!ctx->autotune || nc == 1) return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, cand[0], st);

@@ -241,7 +241,10 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
           bad |= range_bits(pr.B + (size_t)r * pr.ldb + x.n0 + 16 * c, pr.n - x.n0 - 16 * (int)c, pk);
         }
       }
-      if (!mbar_wait(&tfull[buf], (uint32_t)(lt >> 1) & 1u, abort_flag)) break;
+      // one lane waits, the warp follows (tcgen05.ld needs all 32 lanes on the same path)
+      uint32_t got = 1;
+      if (lane == 0) got = mbar_wait(&tfull[buf], (uint32_t)(lt >> 1) & 1u, abort_flag) ? 1u : 0u;
+      if (!__shfl_sync(0xffffffffu, got, 0)) break;
       tc_fence_after();
       const DivP dv = pr.dv;
       const uint32_t p = pr.p;

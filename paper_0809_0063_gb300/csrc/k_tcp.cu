@@ -1,0 +1,566 @@
+// 16-bit matrix products mod p on the tcgen05 tensor cores, persistent and grouped, in two
+// forms that share one kernel template:
+//
+//  packed (RIGHT_TC, right compression, Sec. 7.4), p <= 3: B's columns are paired into one fp16
+//    operand word b0 + 2^10 b1 of centred residues (c(0) = 0, c(1) = 1, c(2) = -1), A is
+//    converted to centred fp16, so one MMA column accumulates D0 + 2^10 D1 with D0 = sum_l
+//    c(a_l) c(b0_l) and D1 likewise: two residues of C per column.  Over a chunk of 448 inner
+//    steps both digits stay in (-512, 512) (Eq. lower per chunk, centred), so the fp32 sum is
+//    exact and its digits separate.  Each chunk's TMEM accumulator is drained by the epilogue
+//    warps into a 32-bit word R = D0 + 2^16 D1 (wrapping, exact since every |digit| <= k <
+//    2^15) while the MMA warp fills the other TMEM buffer (delayed reduction, Sec. 2.2).  At the
+//    end of a tile an offset k makes both digits of R non-negative and REDQ_2 (Algorithm 2,
+//    q = 2^16) recovers them mod p; the residues go straight to C.
+//  plain (PLAIN_TC): A and B converted to bf16 (residues < 256 are exact), one residue per
+//    column, fp32 sums exact while k (p-1)^2 < 2^24, mod p in the epilogue.  It is the plain
+//    product on the same pipe as the packed one.
+//
+// B is stored MN-major for the MMA (k rows of words or residues), so its conversion is a
+// row-by-row map with no transpose; A is K-major.  Schedule: one CTA per SM walks the global
+// list of output tiles (128 rows x 256 MMA columns) of up to FP_GROUP_MAX problems, longest
+// inner dimension first, with stride gridDim.x.  Roles: warp 0 TMA producer (A 128 x 64 and
+// B 64 x 256 per stage, 4-stage ring), warp 1 TMEM allocation (2 x 256 columns) and the
+// MMA-issuing thread, warps 2..9 (two per TMEM lane quarter, 128 columns each) the
+// accumulator drains, REDQ / mod p and the stores, the drains of one tile overlapping the MMAs
+// of the next.  Every wait is bounded (ERR_TIMEOUT on
+// give-up, with the drain-and-free exit of the other tensor-core kernels).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "fpdqt_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fpd {
+
+static constexpr int P_BM = 128, P_BNW = 256, P_BK = 64, P_STAGES = 4, P_CHUNK_KT = 7;
+static constexpr int P_A_BYTES = P_BM * P_BK * 2;             // 16 KB
+static constexpr int P_B_BOX = 64 * P_BK * 2;                 // 8 KB: 64 words x 64 rows
+static constexpr int P_B_BYTES = 4 * P_B_BOX;                 // 32 KB
+static constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;   // 48 KB
+static constexpr int P_EPI_WARPS = 8;                         // 2 per TMEM lane quarter
+static constexpr int P_CW = 4 * P_BNW / P_EPI_WARPS;            // MMA columns per epilogue thread
+static constexpr int P_THREADS = 32 * (2 + P_EPI_WARPS);
+static constexpr size_t P_SMEM = 1024 + P_STAGES * P_STAGE_BYTES + 256;
+
+// kind::f16, A (K-major) and B (MN-major) both fp16 (ab_type 0) or both bf16 (1), fp32 accumulate.
+__host__ __device__ constexpr uint32_t idesc_16_bmn(uint32_t ab_type, int M, int N) {
+  return (1u << 4) | (ab_type << 7) | (ab_type << 10) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+struct PProb {
+  CUtensorMap ta;    // A16: m rows x kp 16-bit, K-major
+  CUtensorMap tb;    // B16: k rows x nw 16-bit (pair words or residues), MN-major
+  uint8_t* C;
+  int ldc, m, n, nw;
+  int ktiles;        // kp / 64
+  int nchunks;       // packed: ceil(ktiles / 7); plain: 1
+  int tn;            // MMA-column blocks ceil(nw / 256)
+  int tile0;
+  uint32_t koffset;  // k: added to both digits before REDQ
+  uint32_t off_mod_p;
+  RedqParams P;      // REDQ_2 at q = 2^16
+};
+
+struct PParams {
+  PProb prob[FP_GROUP_MAX];
+  int nprob;
+  int total;
+};
+
+struct PTile {
+  const PProb* pr;
+  int m0, w0;        // first row, first MMA column
+};
+
+__device__ __forceinline__ PTile p_tile(const PParams& g, int t) {
+  int i = 0;
+  while (i + 1 < g.nprob && t >= g.prob[i + 1].tile0) ++i;
+  const PProb& pr = g.prob[i];
+  const int local = t - pr.tile0;
+  const int mb = local / pr.tn;
+  PTile x;
+  x.pr = &pr;
+  x.m0 = mb * P_BM;
+  x.w0 = (local - mb * pr.tn) * P_BNW;
+  return x;
+}
+
+// REDQ_2 (Algorithm 2) at q = 2^16 for a compile-time p <= 3, on the words of one thread:
+// one division s = floor(w / p), the compression residues u_i = (floor(w / q^i) -
+// p floor(s / q^i)) mod q, then one shuffle of a lane-held table indexed by u_0 + p u_1 (the
+// Q_2 table of the correction, Sec. 3.4) that returns both final residues at once: byte 0 =
+// (u_0 - q u_1 - k) mod p, byte 1 = (u_1 - k) mod p, the offset k (om = k mod p) that made the
+// digits non-negative removed in the same lookup.
+template <uint32_t PP>
+__device__ __forceinline__ uint32_t redq2_pair(uint32_t w, uint32_t table) {
+  const uint32_t s = w / PP;
+  const uint32_t u0 = (w - PP * s) & 0xFFFFu;
+  const uint32_t u1 = ((w >> 16) - PP * (s >> 16)) & 0xFFFFu;
+  return __shfl_sync(0xffffffffu, table, u0 + PP * u1) & 0xFFFFu;
+}
+
+// This lane's entry of that table: lane = u0 + p u1 < p^2.
+__device__ __forceinline__ uint32_t redq2_pair_table(uint32_t p, uint32_t om) {
+  const uint32_t lane = threadIdx.x & 31u;
+  if (lane >= p * p) return 0;
+  const uint32_t u0 = lane % p, u1 = lane / p;
+  const uint32_t c = (p - (65536u % p)) % p;           // (-q) mod p
+  const uint32_t mu0 = (u0 + c * u1) % p;
+  return ((mu0 + p - om) % p) | (((u1 + p - om) % p) << 8);
+}
+
+// The end of a packed tile for one thread: its NW words R (= D0 + 2^16 D1 + conversion
+// constants, cancelled by `fix`, which also offsets both digits by k >= |digit|) reduced by
+// REDQ_2, 2 NW residues stored from dst.  A rolled loop (unrolled it is thousands of
+// instructions and crowds the MMA and TMA warps' loops out of the instruction cache): each
+// pass reduces R[0..15] and moves R down by 16.
+template <uint32_t PP, int NW>
+__device__ __forceinline__ void final_redq(uint32_t (&R)[NW], uint32_t fix, uint32_t table, uint8_t* dst, int c0,
+                                           int n, bool in, bool vec) {
+#pragma unroll 1
+  for (int blk = 0; blk < NW / 16; ++blk) {    // 16 words -> 32 residues -> two 16-byte stores
+    uint32_t o[8];
+#pragma unroll
+    for (int j = 0; j < 16; j += 2)
+      o[j >> 1] = redq2_pair<PP>(R[j] + fix, table) | (redq2_pair<PP>(R[j + 1] + fix, table) << 16);
+    if (vec) {
+      reinterpret_cast<uint4*>(dst + 32 * blk)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+      reinterpret_cast<uint4*>(dst + 32 * blk)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    } else if (in) {
+      for (int j = 0; j < 32 && c0 + 32 * blk + j < n; ++j) dst[32 * blk + j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
+    }
+#pragma unroll
+    for (int j = 0; j < NW - 16; ++j) R[j] = R[j + 16];
+  }
+}
+
+template <bool PACKED>
+__global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__ PParams g, uint32_t* err) {
+  extern __shared__ __align__(1024) uint8_t p_smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)p_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + P_STAGES * P_STAGE_BYTES);
+  uint64_t* empty = full + P_STAGES;
+  uint64_t* tfull = empty + P_STAGES;    // [2] chunk accumulator ready
+  uint64_t* tempty = tfull + 2;          // [2] chunk accumulator drained
+  uint64_t* drainb = tempty + 2;
+  uint64_t* doneb = drainb + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(doneb + 1);
+  volatile uint32_t* abort_flag = tmem_slot + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr uint32_t TMEM_COLS = 512;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], P_EPI_WARPS);
+    }
+    mbar_init(drainb, 1);
+    mbar_init(doneb, P_EPI_WARPS);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < g.total && !stop; t += gridDim.x) {
+        const PTile x = p_tile(g, t);
+        for (int kt = 0; kt < x.pr->ktiles; ++kt, ++it) {
+          const int s = (int)(it % P_STAGES);
+          if (*abort_flag || !mbar_wait(&empty[s], ((it / P_STAGES) & 1u) ^ 1u, abort_flag)) {
+            stop = true;
+            break;
+          }
+          uint8_t* sa = smem + s * P_STAGE_BYTES;
+          uint8_t* sb = sa + P_A_BYTES;
+          mbar_expect_tx(&full[s], P_STAGE_BYTES);
+          tma_load_2d(sa, &x.pr->ta, kt * P_BK, x.m0, &full[s]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) tma_load_2d(sb + j * P_B_BOX, &x.pr->tb, x.w0 + 64 * j, kt * P_BK, &full[s]);
+        }
+      }
+      for (uint32_t j = (it > (uint32_t)P_STAGES ? it - P_STAGES : 0u); j < it; ++j)
+        mbar_drain(&full[j % P_STAGES], (j / P_STAGES) & 1u);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_16_bmn(PACKED ? 0u : 1u, P_BM, P_BNW);
+      uint32_t it = 0, gc = 0;      // k tiles and chunks of this CTA so far
+      bool stop = false;
+      for (int t = blockIdx.x; t < g.total && !stop; t += gridDim.x) {
+        const PTile x = p_tile(g, t);
+        int kt = 0;
+        for (int c = 0; c < x.pr->nchunks && !stop; ++c, ++gc) {
+          const int buf = (int)(gc & 1u);
+          if (gc >= 2 && !mbar_wait(&tempty[buf], ((gc - 2) >> 1) & 1u, abort_flag)) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dtm = tmem + (uint32_t)(buf * 256);
+          const int kend = PACKED ? min(x.pr->ktiles, kt + P_CHUNK_KT) : x.pr->ktiles;
+          bool first = true;
+          for (; kt < kend; ++kt, ++it) {
+            const int s = (int)(it % P_STAGES);
+            if (!mbar_wait(&full[s], (it / P_STAGES) & 1u, abort_flag)) {
+              stop = true;
+              break;
+            }
+            tc_fence_after();
+            const uint8_t* sa = smem + s * P_STAGE_BYTES;
+            const uint8_t* sb = sa + P_A_BYTES;
+            const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_mn_sw128(sb, P_B_BOX);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {   // K = 16: A +32 bytes in the row, B +16 rows of 128 bytes
+              mma_f16(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 128), idesc, first ? 0u : 1u);
+              first = false;
+            }
+            mma_commit(&empty[s]);
+          }
+          if (!stop) mma_commit(&tfull[buf]);
+        }
+      }
+      if (*abort_flag) {
+        mma_commit(drainb);
+        mbar_drain(drainb, 0);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------ drains, REDQ / mod p, stores (warps 2..)
+    const int q = warp & 3;                      // TMEM lane quarter
+    const int part = (warp - 2) >> 2;            // MMA columns part * P_CW .. + P_CW - 1
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    uint32_t gc = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < g.total && ok && !PACKED; t += gridDim.x, ++gc) {
+      // plain: one accumulator per tile, mod p of each fp32 sum (an exact integer)
+      const PTile x = p_tile(g, t);
+      const PProb& pr = *x.pr;
+      const int buf = (int)(gc & 1u);
+      uint32_t got = 1;
+      if (lane == 0) got = mbar_wait(&tfull[buf], (gc >> 1) & 1u, abort_flag) ? 1u : 0u;
+      if (!__shfl_sync(0xffffffffu, got, 0)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const DivP dv = pr.P.dv;
+      const uint32_t p = pr.P.p;
+      const int row = x.m0 + q * 32 + lane;
+      for (int cb = 0; cb < P_CW / 32; ++cb) {
+        const int col0 = part * P_CW + cb * 32;
+        uint32_t v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(buf * 256 + col0), v);
+        uint32_t o[8];
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          uint32_t w = 0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) w |= modp32(__float2uint_rn(__uint_as_float(v[j + u])), dv, p) << (8 * u);
+          o[j >> 2] = w;
+        }
+        const int c0 = x.w0 + col0;
+        if (row < pr.m && c0 < pr.n) {
+          uint8_t* dst = pr.C + (size_t)row * pr.ldc + c0;
+          if (c0 + 32 <= pr.n && ((((uintptr_t)dst) & 15u) == 0)) {
+            reinterpret_cast<uint4*>(dst)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+            reinterpret_cast<uint4*>(dst)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+          } else {
+            for (int j = 0; j < 32 && c0 + j < pr.n; ++j) dst[j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
+    for (int t = blockIdx.x; t < g.total && ok && PACKED; t += gridDim.x) {
+      const PTile x = p_tile(g, t);
+      const PProb& pr = *x.pr;
+      uint32_t R[P_CW];   // unsigned: wraps modulo 2^32 (the conversion offsets cancel at the end)
+#pragma unroll
+      for (int j = 0; j < P_CW; ++j) R[j] = 0;
+      for (int c = 0; c < pr.nchunks; ++c, ++gc) {
+        const int buf = (int)(gc & 1u);
+        // one lane waits, the warp follows: the tcgen05.ld below and the shuffles of REDQ need
+        // all 32 lanes on the same path even if the wait gives up
+        uint32_t got = 1;
+        if (lane == 0) got = mbar_wait(&tfull[buf], (gc >> 1) & 1u, abort_flag) ? 1u : 0u;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // blocks of 16 columns, loads double-buffered.  Chunk word v = d0 + 2^10 d1 with
+        // |d0|, |d1| < 512: adding 1.5 2^23 makes the float's bits 0x4B400000 + v exactly, so
+        // y - 0x4B400000 = v with no conversion instruction; d1 = round(v / 2^10).
+        const uint32_t base = tmem + lane_base + (uint32_t)(buf * 256 + part * P_CW);
+        uint32_t va[16], vb[16];
+        tmem_ld16_nowait(base, va);
+        tmem_wait();
+#pragma unroll
+        for (int blk = 0; blk < P_CW / 16; ++blk) {
+          if (blk + 1 < P_CW / 16) {
+            if (blk & 1) tmem_ld16_nowait(base + (uint32_t)((blk + 1) * 16), va);
+            else tmem_ld16_nowait(base + (uint32_t)((blk + 1) * 16), vb);
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const uint32_t raw = (blk & 1) ? vb[j] : va[j];
+            const int32_t y = __float_as_int(__uint_as_float(raw) + 12582912.0f);
+            const int32_t d1 = (y - (0x4B400000 - 512)) >> 10;
+            R[blk * 16 + j] += (uint32_t)y + (uint32_t)(d1 * (65536 - 1024));
+          }
+          tmem_wait();
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+      }
+      if (!ok) break;
+      // R = D0 + 2^16 D1 (+ the per-chunk constants); offset both digits by k, REDQ_2, store
+      // parameters copied to registers (read through the grid-constant block they would be
+      // reloaded after every store to C)
+      const uint32_t fix = pr.koffset * 65537u - (uint32_t)pr.nchunks * 0x4B400000u;
+      const uint32_t p = pr.P.p;
+      const uint32_t table = redq2_pair_table(p, pr.off_mod_p);
+      const int row = x.m0 + q * 32 + lane;
+      const int c0 = 2 * (x.w0 + part * P_CW);   // first column of C for this thread
+      const int n = pr.n;
+      const bool in = row < pr.m && c0 < n;
+      uint8_t* dst = pr.C + (size_t)row * pr.ldc + c0;
+      const bool vec = in && c0 + 2 * P_CW <= n && ((((uintptr_t)dst) & 15u) == 0);
+      if (p == 3) final_redq<3, P_CW>(R, fix, table, dst, c0, n, in, vec);
+      else final_redq<2, P_CW>(R, fix, table, dst, c0, n, in, vec);
+    }
+    __syncwarp();
+    tc_fence_before();
+    if (lane == 0) mbar_arrive(doneb);
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) flag_error(err, ERR_TIMEOUT);
+  if (warp == 1) {
+    if (lane == 0) mbar_drain(doneb, 0);
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// bf16 bits of a residue v <= 255: the float 2^23 + v has v in its low mantissa bits, so
+// subtracting 2^23 gives float(v) exactly; its top 16 bits are the bf16 (exact, 8 bits).
+__device__ __forceinline__ uint32_t bf16_of(uint32_t v) {
+  return __float_as_uint(__uint_as_float(0x4B000000u | v) - 8388608.0f) >> 16;
+}
+
+// A16[r][c] (m x kp, zero padded) = centred fp16 (PACKED) or bf16 of A[r][c]; one thread per
+// 16 columns.  Residues >= p set ERR_RANGE.
+template <bool PACKED>
+__global__ void __launch_bounds__(256) k_t16_convert_a(const uint8_t* __restrict__ A, int lda, uint16_t* __restrict__ dst,
+                                                       int m, int k, int kp, uint32_t p, uint32_t* err) {
+  const int chunks = kp >> 4;
+  uint32_t bad = 0;
+  const bool vec = (((uintptr_t)A) & 15u) == 0 && (lda & 15) == 0;
+  for (int r = blockIdx.x; r < m; r += gridDim.x)
+    for (int ch = threadIdx.x; ch < chunks; ch += blockDim.x) {
+      const int c0 = ch * 16;
+      uint32_t w[4];
+      const uint8_t* src = A + (size_t)r * lda + c0;
+      if (vec && c0 + 16 <= k) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
+        w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint32_t t = 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) t |= (uint32_t)(c0 + 4 * q + j < k ? src[4 * q + j] : 0) << (8 * j);
+          w[q] = t;
+        }
+      }
+      uint32_t o[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        bad |= __vcmpgeu4(w[q], 0x01010101u * p);
+        const uint32_t x = w[q];
+        if (PACKED) {
+          o[2 * q] = h16_centred(x & 0xffu) | (h16_centred((x >> 8) & 0xffu) << 16);
+          o[2 * q + 1] = h16_centred((x >> 16) & 0xffu) | (h16_centred(x >> 24) << 16);
+        } else {
+          o[2 * q] = bf16_of(x & 0xffu) | (bf16_of((x >> 8) & 0xffu) << 16);
+          o[2 * q + 1] = bf16_of((x >> 16) & 0xffu) | (bf16_of(x >> 24) << 16);
+        }
+      }
+      uint4* d = reinterpret_cast<uint4*>(dst + (size_t)r * kp + c0);
+      d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+      d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// B16 (k x ldw 16-bit, zero past nw) row by row from B (k x n), no transpose.  PACKED: word
+// j = fp16 of c(B[l][2j]) + 2^10 c(B[l][2j+1]) (the second residue 0 past column n), one
+// thread per 16 bytes of B (8 words); plain: bf16 of B[l][j], one thread per 8 bytes of B
+// (8 elements).  Residues >= p set ERR_RANGE.
+template <bool PACKED>
+__global__ void __launch_bounds__(256) k_t16_convert_b(const uint8_t* __restrict__ B, int ldb, uint16_t* __restrict__ dst,
+                                                       int k, int n, int ldw, uint32_t p, uint32_t* err) {
+  constexpr int IN = PACKED ? 16 : 8;            // input bytes per thread (8 output words)
+  const int groups = ldw >> 3;
+  uint32_t bad = 0;
+  const bool vec = (((uintptr_t)B) & (IN - 1)) == 0 && (ldb & (IN - 1)) == 0;
+  const uint32_t pp = 0x01010101u * p;
+  for (int r = blockIdx.x; r < k; r += gridDim.x)
+    for (int gi = threadIdx.x; gi < groups; gi += blockDim.x) {
+      const int c0 = gi * IN;                    // first byte column of B
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      const uint8_t* src = B + (size_t)r * ldb + c0;
+      if (vec && c0 + IN <= n) {
+        if (PACKED) {
+          const uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
+          w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+        } else {
+          const uint2 x = __ldg(reinterpret_cast<const uint2*>(src));
+          w[0] = x.x; w[1] = x.y;
+        }
+      } else if (c0 < n) {
+#pragma unroll
+        for (int q = 0; q < IN / 4; ++q) {
+          uint32_t t = 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) t |= (uint32_t)(c0 + 4 * q + j < n ? src[4 * q + j] : 0) << (8 * j);
+          w[q] = t;
+        }
+      }
+      uint32_t o[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        bad |= __vcmpgeu4(w[q], pp);
+        const uint32_t x = w[q];
+        if (PACKED) {
+          o[q] = h16_pair_word(x & 0xffu, (x >> 8) & 0xffu) | (h16_pair_word((x >> 16) & 0xffu, x >> 24) << 16);
+        } else {
+          const uint32_t y = w[q >> 1] >> (16 * (q & 1));
+          o[q] = bf16_of(y & 0xffu) | (bf16_of((y >> 8) & 0xffu) << 16);
+        }
+      }
+      *reinterpret_cast<uint4*>(dst + (size_t)r * ldw + gi * 8) = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// ---------------------------------------------------------------- host side
+
+bool f16p_ok(uint32_t p, int k) { return p <= 3 && k <= 32767; }
+
+// Convert the problems' operands into context scratch and launch the grouped kernel(s); the
+// caller holds the context lock.  Every problem passed fp_matmul's checks and the variant's
+// exactness rule (packed: f16p_ok; plain: k (p-1)^2 < 2^24).
+static fp_status launch_t16_locked(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, bool packed,
+                                   cudaStream_t st) {
+  std::vector<const fp_mm_problem*> v(pr, pr + count);
+  std::stable_sort(v.begin(), v.end(), [](const fp_mm_problem* a, const fp_mm_problem* b) { return a->k > b->k; });
+  auto words = [packed](int n) { return packed ? (n + 1) / 2 : n; };
+  for (size_t base = 0; base < v.size(); base += FP_GROUP_MAX) {
+    const int cnt = (int)std::min<size_t>(FP_GROUP_MAX, v.size() - base);
+    // scratch layout: per problem A16 (m x kp) then B16 (k x ldw), 1024-byte aligned
+    size_t off[FP_GROUP_MAX][2], total = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const fp_mm_problem& x = *v[base + i];
+      const size_t kp = (size_t)(x.k + P_BK - 1) / P_BK * P_BK, ldw = ((size_t)words(x.n) + 7) / 8 * 8;
+      off[i][0] = total;
+      total += (x.m * kp * 2 + 1023) & ~(size_t)1023;
+      off[i][1] = total;
+      total += (x.k * ldw * 2 + 1023) & ~(size_t)1023;
+    }
+    fp_status s = ensure_scratch(ctx, total + 1024);
+    if (s != FP_OK) return s;
+    PParams hp;
+    std::memset(&hp, 0, sizeof hp);
+    int tile = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const fp_mm_problem& x = *v[base + i];
+      const int kp = (x.k + P_BK - 1) / P_BK * P_BK, nw = words(x.n), ldw = (nw + 7) / 8 * 8;
+      uint16_t* A16 = (uint16_t*)((uint8_t*)ctx->scratch + off[i][0]);
+      uint16_t* B16 = (uint16_t*)((uint8_t*)ctx->scratch + off[i][1]);
+      const int ga = std::min(x.m, ctx->num_sms * 16), gb = std::min(x.k, ctx->num_sms * 16);
+      if (packed) {
+        FP_LAUNCH(ctx, "k_t16_convert_a", st,
+                  k_t16_convert_a<true><<<ga, 256, 0, st>>>(x.A, x.lda, A16, x.m, x.k, kp, x.p, ctx->d_err));
+        FP_LAUNCH(ctx, "k_t16_convert_b", st,
+                  k_t16_convert_b<true><<<gb, 256, 0, st>>>(x.B, x.ldb, B16, x.k, x.n, ldw, x.p, ctx->d_err));
+      } else {
+        FP_LAUNCH(ctx, "k_t16_convert_a", st,
+                  k_t16_convert_a<false><<<ga, 256, 0, st>>>(x.A, x.lda, A16, x.m, x.k, kp, x.p, ctx->d_err));
+        FP_LAUNCH(ctx, "k_t16_convert_b", st,
+                  k_t16_convert_b<false><<<gb, 256, 0, st>>>(x.B, x.ldb, B16, x.k, x.n, ldw, x.p, ctx->d_err));
+      }
+      FP_CUDA(cudaGetLastError());
+      PProb& g = hp.prob[i];
+      s = make_map_ld(&g.ta, A16, (uint64_t)x.m, (uint64_t)kp, (uint64_t)kp, P_BM, 2);
+      if (s != FP_OK) return s;
+      s = make_map_ld(&g.tb, B16, (uint64_t)x.k, (uint64_t)nw, (uint64_t)ldw, 64, 2);
+      if (s != FP_OK) return s;
+      g.C = x.C;
+      g.ldc = x.ldc;
+      g.m = x.m;
+      g.n = x.n;
+      g.nw = nw;
+      g.ktiles = kp / P_BK;
+      g.nchunks = packed ? (g.ktiles + P_CHUNK_KT - 1) / P_CHUNK_KT : 1;
+      g.tn = (nw + P_BNW - 1) / P_BNW;
+      g.tile0 = tile;
+      g.koffset = (uint32_t)x.k;
+      g.off_mod_p = (uint32_t)x.k % x.p;
+      g.P = make_redq(x.p, 16, packed ? 2 : 1);
+      tile += ((x.m + P_BM - 1) / P_BM) * g.tn;
+    }
+    hp.nprob = cnt;
+    hp.total = tile;
+    const int grid = std::min(tile, ctx->num_sms);
+    if (packed) {
+      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
+      FP_LAUNCH(ctx, "k_mm_t16_packed", st, k_mm_t16<true><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err));
+    } else {
+      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
+      FP_LAUNCH(ctx, "k_mm_t16_plain", st, k_mm_t16<false><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err));
+    }
+    FP_CUDA(cudaGetLastError());
+  }
+  return FP_OK;
+}
+
+fp_status launch_mm_t16_direct(fp_ctx ctx, const fp_mm_problem& x, bool packed, cudaStream_t st) {
+  const fp_mm_problem* one = &x;
+  return launch_t16_locked(ctx, &one, 1, packed, st);
+}
+
+fp_status launch_mm_t16_grouped(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, bool packed,
+                                cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return launch_t16_locked(ctx, pr, count, packed, st);
+}
+
+}  // namespace fpd

@@ -3,10 +3,19 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include "fpdqt_internal.cuh"
 
 namespace fpd {
+
+// fp16 bits of a centred residue of p <= 3 ({0,1,2} -> {0,1,-1}) and of a packed pair
+// c(v0) + 2^10 c(v1) (|value| <= 1025 < 2^11: exact in fp16).
+__device__ __forceinline__ uint32_t h16_centred(uint32_t v) { return v == 0 ? 0u : (v == 1 ? 0x3C00u : 0xBC00u); }
+__device__ __forceinline__ uint32_t h16_pair_word(uint32_t v0, uint32_t v1) {
+  const float c0 = v0 == 2 ? -1.0f : (float)v0, c1 = v1 == 2 ? -1.0f : (float)v1;
+  return __half_as_ushort(__float2half_rn(fmaf(1024.0f, c1, c0)));
+}
 
 static constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;             // try_wait polls before giving up
 static constexpr uint32_t TC_DRAIN_LIMIT = 1u << 20;            // polls for own in-flight work

@@ -61,21 +61,21 @@ def _launches(fp, ctx, fn):
     fp.fp_ctx_profile(ctx, 1)
     fn()
     fp.fp_ctx_status(ctx)
-    out = {name: fp.fp_ctx_profile_read(ctx, name)[0] for name in ("k_mm_f8g", "k_tc_convert")}
+    out = {name: fp.fp_ctx_profile_read(ctx, name)[0] for name in ("k_mm_f8g", "")}
     fp.fp_ctx_profile(ctx, 0)
     return out
 
 
 def test_grouped_mixed(env):
     """Eligible problems (p <= 17, aligned) share one launch; p = 31, an unaligned layout and
-    p = 17 beyond the fp8 bound go through fp_matmul one by one; every result is exact."""
+    p = 17 beyond the fp8 bound go through fp_matmul (AUTO) one by one; every result is exact."""
     fp, torch, dev, ctx = env
     probs = [Prob(fp, torch, dev, 1, 3, 200, 333, 517), Prob(fp, torch, dev, 2, 7, 130, 70, 1000),
              Prob(fp, torch, dev, 3, 2, 64, 129, 4100), Prob(fp, torch, dev, 4, 17, 257, 255, 96),
              Prob(fp, torch, dev, 5, 31, 33, 300, 300), Prob(fp, torch, dev, 6, 5, 77, 91, 333, align=False),
              Prob(fp, torch, dev, 7, 13, 1, 1, 1), Prob(fp, torch, dev, 8, 17, 40, 50, 70000)]
     n = _launches(fp, ctx, lambda: fp.fp_matmul_grouped(ctx, [q.desc for q in probs]))
-    assert n["k_mm_f8g"] == 1
+    assert n["k_mm_f8g"] == 2          # the group, and the unaligned p = 5 product (padded copy)
     for q in probs:
         q.check()
 
@@ -89,7 +89,7 @@ def test_grouped_more_than_one_launch(env):
     probs = [Prob(fp, torch, dev, 100 + i, primes[i % 7], int(rng.integers(1, 300)), int(rng.integers(1, 600)),
                   int(rng.integers(1, 900))) for i in range(cnt)]
     n = _launches(fp, ctx, lambda: fp.fp_matmul_grouped(ctx, [q.desc for q in probs], fp.FP_MM_PLAIN_F8))
-    assert n["k_mm_f8g"] == 2 and n["k_tc_convert"] == 0
+    assert n["k_mm_f8g"] == 2 and n[""] == 2         # nothing but the two grouped launches
     for q in probs:
         q.check()
 
@@ -201,3 +201,42 @@ def test_grouped_range_check_covers_every_position(env):
     fp.fp_ctx_status(ctx)
     other.check()
     q.check()
+
+
+@pytest.mark.parametrize("algo", ["RIGHT_TC", "PLAIN_TC"])
+def test_grouped_16bit(env, algo):
+    """RIGHT_TC (packed fp16, two residues per MMA column) and PLAIN_TC (bf16) groups: ragged
+    shapes, odd n (a last word with one residue), several chunks of 448 inner steps, unaligned
+    leading dimensions (the conversions read any layout); one persistent launch each."""
+    fp, torch, dev, ctx = env
+    if algo == "RIGHT_TC":
+        shapes = [(3, 200, 333, 517), (2, 64, 129, 4100), (3, 130, 71, 1000), (3, 1, 1, 1), (2, 257, 600, 448),
+                  (3, 100, 513, 449)]
+    else:
+        shapes = [(7, 200, 333, 517), (251, 64, 129, 200), (31, 130, 71, 1000), (3, 1, 1, 1), (13, 257, 600, 4096)]
+    probs = [Prob(fp, torch, dev, 60 + i, p, m, n, k, align=(i % 2 == 0)) for i, (p, m, n, k) in enumerate(shapes)]
+    name = "k_mm_t16_packed" if algo == "RIGHT_TC" else "k_mm_t16_plain"
+    fp.fp_ctx_profile(ctx, 2)
+    fp.fp_ctx_profile(ctx, 1)
+    fp.fp_matmul_grouped(ctx, [q.desc for q in probs], getattr(fp, "FP_MM_" + algo))
+    fp.fp_ctx_status(ctx)
+    launches, _ = fp.fp_ctx_profile_read(ctx, name)
+    fp.fp_ctx_profile(ctx, 0)
+    assert launches == 1
+    for q in probs:
+        q.check()
+
+
+def test_grouped_bound_refused_before_enqueue(env):
+    """A group whose forced algorithm is inexact for one problem (RIGHT_TC with p = 5) is
+    refused with FP_EBOUND and nothing runs, not even the problems that would fit."""
+    fp, torch, dev, ctx = env
+    fine = Prob(fp, torch, dev, 81, 3, 64, 64, 64)
+    bad = Prob(fp, torch, dev, 82, 5, 64, 64, 64)
+    l0 = fp.fp_ctx_launches(ctx)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_matmul_grouped(ctx, [fine.desc, bad.desc], fp.FP_MM_RIGHT_TC)
+    assert ei.value.status == fp.FP_EBOUND
+    fp.fp_ctx_status(ctx)
+    assert fp.fp_ctx_launches(ctx) == l0
+    assert np.all(fine.C.cpu().numpy() == 253)
