@@ -236,6 +236,278 @@ def run_reference(args, ws, rank):
     }))
 
 
+def _timed(torch, stream, fn, reps, flush=None):
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a0.elapsed_time(a1))
+    return ts
+
+
+def run_polymul(args, ws, rank, local):
+    """Batched polynomial products over F_3, degree 2 x degree 2 (the paper's Kronecker
+    example size), DQT-packed: a step is 2^20 pairs; 48 input/output sets rotate so every step
+    reads cold data (48 x 11.5 MB > 4 x L2), plus a scaled row of 2^26 pairs in one call."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_0809_0063_gb300 as fp
+    from oracle import field
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    hbm, bf16, _, peak_src = peaks()
+    ctx = fp.fp_ctx_create(local)
+    stream = torch.cuda.current_stream()
+    p, da, db, batch, nsets = 3, 2, 2, 1 << 20, 48
+    bpp = (da + 1) + (db + 1) + (da + db + 1)          # algorithmic bytes per pair (11)
+    mpp = (da + 1) * (db + 1)                          # F_p MACs per pair (9)
+    sets = []
+    for i in range(nsets):
+        a, b = workloads.polymul_inputs(500 + i, p, batch, da, db)
+        sets.append((a, b, torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev),
+                     torch.empty((batch, da + db + 1), dtype=torch.uint8, device=dev)))
+    algo = getattr(fp, "FP_ALGO_" + (args.algo if args.algo != "AUTO" else "AUTO"))
+    it = [0]
+
+    def step(al=algo):
+        a, b, A, B, C = sets[it[0] % nsets]
+        it[0] += 1
+        fp.fp_polymul_batched(ctx, p, A, da, B, db, C, batch, al)
+
+    for i in range(nsets):                             # parity gate: every set, sampled pairs
+        step()
+    torch.cuda.synchronize()
+    fp.fp_ctx_status(ctx)
+    rows = np.random.default_rng(3).choice(batch, 4096, replace=False)
+    for a, b, A, B, C in sets[:4]:
+        assert np.array_equal(C[torch.from_numpy(rows).to(dev)].cpu().numpy(), field.polymul_mod(a[rows], b[rows], p))
+    for _ in range(max(3, args.warmup)):
+        step()
+    # a step is ~2 us of device work: one CUDA graph holds a pass over the nsets rotating sets
+    # (one library call each) and the step time is a replay's time / nsets
+    torch.cuda.synchronize()
+    l_a = fp.fp_ctx_launches(ctx)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for _ in range(nsets):
+            step()
+    per_pass = fp.fp_ctx_launches(ctx) - l_a
+    graph.replay()
+    torch.cuda.synchronize()
+    fp.fp_ctx_status(ctx)
+    t_pass = statistics.median(_timed(torch, stream, graph.replay, 3))
+    passes = max(3, args.steps // 4, int(1000.0 / max(t_pass, 1e-3)))   # about a second under load (clocks)
+    clk = Clocks(local).__enter__()
+    ts = [t / nsets for t in _timed(torch, stream, graph.replay, passes)]
+    clk.__exit__(None, None, None)
+    launches = per_pass * passes
+    # per-kernel times from the library's own events over plain calls
+    fp.fp_ctx_profile(ctx, 2)
+    fp.fp_ctx_profile(ctx, 1)
+    for _ in range(nsets):
+        step()
+    torch.cuda.synchronize()
+    fp.fp_ctx_profile(ctx, 0)
+    names = ["k_polymul_small", "k_polymul_word_bulk", "k_polymul_word", "k_polymul_plain_small", "k_polymul_fqt",
+             "k_polymul_plain_big"]
+    dom, dms, dn = None, 0.0, 0
+    for nm in names:
+        c, ms = fp.fp_ctx_profile_read(ctx, nm)
+        if nm == "k_polymul_word":   # prefix of k_polymul_word_bulk: subtract the bulk launches
+            cb, msb = fp.fp_ctx_profile_read(ctx, "k_polymul_word_bulk")
+            c, ms = c - cb, ms - msb
+        if c and ms > dms:
+            dom, dms, dn = nm, ms, c
+    t_ms = statistics.median(ts)
+    value = ws * batch * mpp / (t_ms / 1e3)
+    # scaled row: 2^26 pairs in one call
+    big = 1 << 26
+    ab, bb = workloads.polymul_inputs(900, p, big, da, db)
+    Ab, Bb = torch.from_numpy(ab).to(dev), torch.from_numpy(bb).to(dev)
+    Cb = torch.empty((big, da + db + 1), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    fn_big = lambda al=algo: fp.fp_polymul_batched(ctx, p, Ab, da, Bb, db, Cb, big, al)
+    fn_big()
+    torch.cuda.synchronize()
+    fp.fp_ctx_status(ctx)
+    rb = np.random.default_rng(4).choice(big, 4096, replace=False)
+    assert np.array_equal(Cb[torch.from_numpy(rb).to(dev)].cpu().numpy(), field.polymul_mod(ab[rb], bb[rb], p))
+    tb = statistics.median(_timed(torch, stream, fn_big, 5, flush))
+    compare = {}
+    if not args.no_compare:
+        for nm in ("PLAIN", "DQT_U32", "DQT_F32", "DQT_U64", "DQT_F64"):
+            al = getattr(fp, "FP_ALGO_" + nm)
+            try:
+                fn_big(al)
+                torch.cuda.synchronize()
+                fp.fp_ctx_status(ctx)
+                compare[nm] = big * mpp / (statistics.median(_timed(torch, stream, lambda: fn_big(al), 3, flush)) / 1e3)
+            except fp.FpError as ex:
+                compare[nm] = f"unavailable: {ex.args[0][:60]}"
+        if isinstance(compare.get("PLAIN"), float):
+            compare["best_packed_over_plain"] = max(v for k, v in compare.items()
+                                                    if k.startswith("DQT") and isinstance(v, float)) / compare["PLAIN"]
+    # end to end: pinned host inputs in, results out, each step
+    ha, hb = torch.from_numpy(sets[0][0]).pin_memory(), torch.from_numpy(sets[0][1]).pin_memory()
+    hc = torch.empty((batch, da + db + 1), dtype=torch.uint8).pin_memory()
+    A0, B0, C0 = sets[0][2], sets[0][3], sets[0][4]
+
+    def e2e():
+        A0.copy_(ha, non_blocking=True)
+        B0.copy_(hb, non_blocking=True)
+        fp.fp_polymul_batched(ctx, p, A0, da, B0, db, C0, batch, algo)
+        hc.copy_(C0, non_blocking=True)
+
+    e2e()
+    torch.cuda.synchronize()
+    te = statistics.median(_timed(torch, stream, e2e, 10))
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        n_cpu = 1 << 22
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 10.0:
+            field.polymul_mod(ab[:n_cpu], bb[:n_cpu], p)
+            reps += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": reps * n_cpu * mpp / dt, "unit": "F_p MAC/s", "cores": 1, "kind": "oracle",
+               "sample": f"{reps} x 2^22 pairs ({dt:.1f} s, numpy int64 schoolbook + % p, single thread)"}
+    roof = None
+    if dom:
+        per_launch_ms = dms / dn
+        achieved = batch * bpp / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "peak_source": f"HBM copy ({peak_src})", "launches": dn, "avg_launch_ms": per_launch_ms,
+                "scaled_2^26": {"achieved": big * bpp / (tb / 1e3) / 1e9, "frac": big * bpp / (tb / 1e3) / 1e9 / hbm,
+                                "ms": tb}}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "F_p MAC/s", "n_gpus": ws, "steps": len(ts) * nsets,
+            "warmup": max(3, args.warmup), "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "packed word (planner: u32/f32/u64/f64)", "data": "synthetic",
+            "timing": f"CUDA graph of {nsets} steps (one per rotating set), replayed {len(ts)} times",
+            "config": {"workload": "batched polynomial product over F_3, 2^20 pairs of degree 2 x degree 2 per step",
+                       "algo": args.algo, "l2": f"{nsets} rotating input/output sets ({nsets * batch * bpp / 1e6:.0f} MB)",
+                       "scaled_row": "2^26 pairs per call, L2 flushed between calls",
+                       "value_scaled_2^26": big * mpp / (tb / 1e3)},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": ws * batch * mpp / (te / 1e3), "unit": "F_p MAC/s",
+                    "h2d_bytes_per_step": batch * (da + db + 2), "d2h_bytes_per_step": batch * (da + db + 1)},
+            "gpu_launches": launches, "clocks": clk.summary(), "compare_same_inputs_2^26": compare,
+        }))
+    fp.fp_ctx_destroy(ctx)
+
+
+def run_gf(args, ws, rank, local):
+    """GF(p^k) multiplication (Algorithm FGDP with n = 1): 2^24 random pairs in each of
+    GF(3^5), GF(7^4), GF(2^8) per step (201 MB of indices moved, L2 flushed between steps).
+    F_p MACs per multiply = k^2 (the schoolbook product; the reduction is not counted)."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_0809_0063_gb300 as fp
+    from oracle import field
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    hbm, bf16, _, peak_src = peaks()
+    ctx = fp.fp_ctx_create(local)
+    stream = torch.cuda.current_stream()
+    count = 1 << 24
+    fields = []
+    for p, k in workloads.GF_FIELDS:
+        a, b = workloads.gf_inputs(700 + p, p, k, count)
+        gfh = fp.fp_gf_create(ctx, p, k)
+        A, B = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+        fields.append((p, k, a, b, gfh, A, B, torch.empty_like(A)))
+    macs = sum(k * k for _, k in workloads.GF_FIELDS) * count
+    nbytes = sum(3 * workloads.gf_index_dtype(p, k)(0).itemsize for p, k in workloads.GF_FIELDS) * count
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        for p, k, a, b, gfh, A, B, C in fields:
+            fp.fp_gf_mul_batched(ctx, gfh, A, B, C, count)
+
+    step()
+    torch.cuda.synchronize()
+    fp.fp_ctx_status(ctx)
+    idx = np.random.default_rng(5).choice(count, 8192, replace=False)
+    for p, k, a, b, gfh, A, B, C in fields:
+        mod = field.smallest_monic_irreducible(p, k)
+        want = field.gf_mul(a[idx].astype(np.int64), b[idx].astype(np.int64), p, k, mod)
+        assert np.array_equal(C.cpu().numpy()[idx].astype(np.int64), want), f"GF({p}^{k}) parity"
+    for _ in range(max(3, args.warmup)):
+        step()
+    l0 = fp.fp_ctx_launches(ctx)
+    fp.fp_ctx_profile(ctx, 2)
+    fp.fp_ctx_profile(ctx, 1)
+    clk = Clocks(local).__enter__()
+    ts = _timed(torch, stream, step, max(args.steps, 10), flush)
+    clk.__exit__(None, None, None)
+    fp.fp_ctx_profile(ctx, 0)
+    launches = fp.fp_ctx_launches(ctx) - l0
+    t_ms = statistics.median(ts)
+    nk, kms = fp.fp_ctx_profile_read(ctx, "k_gf_mul")
+    per_field = {}
+    for p, k, a, b, gfh, A, B, C in fields:
+        fn = lambda gfh=gfh, A=A, B=B, C=C: fp.fp_gf_mul_batched(ctx, gfh, A, B, C, count)
+        t = statistics.median(_timed(torch, stream, fn, 5, flush))
+        eb = 3 * A.element_size() * count
+        per_field[f"GF({p}^{k})"] = {"ms": t, "GB/s": eb / (t / 1e3) / 1e9, "frac_hbm": eb / (t / 1e3) / 1e9 / hbm,
+                                     "F_p MAC/s": k * k * count / (t / 1e3)}
+    hin = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory(), torch.empty(count, dtype=A.dtype).pin_memory())
+           for p, k, a, b, gfh, A, B, C in fields]
+
+    def e2e():
+        for (p, k, a, b, gfh, A, B, C), (ha, hb, hc) in zip(fields, hin):
+            A.copy_(ha, non_blocking=True)
+            B.copy_(hb, non_blocking=True)
+            fp.fp_gf_mul_batched(ctx, gfh, A, B, C, count)
+            hc.copy_(C, non_blocking=True)
+
+    e2e()
+    torch.cuda.synchronize()
+    te = statistics.median(_timed(torch, stream, e2e, 5))
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        n_cpu = 1 << 18
+        t0 = time.perf_counter()
+        m_done = 0
+        while time.perf_counter() - t0 < 10.0:
+            for p, k, a, b, *_ in fields:
+                field.gf_mul(a[:n_cpu].astype(np.int64), b[:n_cpu].astype(np.int64), p, k,
+                             field.smallest_monic_irreducible(p, k))
+                m_done += k * k * n_cpu
+        dt = time.perf_counter() - t0
+        cpu = {"value": m_done / dt, "unit": "F_p MAC/s", "cores": 1, "kind": "oracle",
+               "sample": f"2^18 pairs per field, round robin ({dt:.1f} s, numpy schoolbook + remainder, single thread)"}
+    kper = kms / max(1, nk)
+    roof = {"bound": "hbm", "kernel": "k_gf_mul_fixed", "achieved": nbytes / len(fields) / (kper / 1e3) / 1e9,
+            "peak": hbm, "unit": "GB/s", "frac": nbytes / len(fields) / (kper / 1e3) / 1e9 / hbm, "traffic": None,
+            "peak_source": f"HBM copy ({peak_src})", "launches": nk, "avg_launch_ms": kper,
+            "note": "achieved = average index bytes per field launch / average launch time"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": ws * macs / (t_ms / 1e3), "unit": "F_p MAC/s", "n_gpus": ws,
+            "steps": len(ts), "warmup": max(3, args.warmup), "ms_per_step": t_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64 / f64 packed words, u32 tables",
+            "data": "synthetic",
+            "config": {"workload": "GF(p^k) multiply, 2^24 pairs each in GF(3^5), GF(7^4), GF(2^8) per step",
+                       "l2": "flushed between steps (512 MiB write)", "per_field": per_field},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": ws * macs / (te / 1e3), "unit": "F_p MAC/s", "h2d_bytes_per_step": 2 * nbytes // 3,
+                    "d2h_bytes_per_step": nbytes // 3},
+            "gpu_launches": launches, "clocks": clk.summary(),
+        }))
+    fp.fp_ctx_destroy(ctx)
+
+
 def run_batch(args, ws, rank, local):
     """Uneven batch: 4096 matmul / dot instances (p in {2,3,5,7,17,31}, sizes log-uniform in
     [16, 2048]) in one persistent launch, against one fp_matmul / fp_dot call per instance."""
@@ -451,7 +723,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="matmul", choices=["matmul", "batch", "serve"],
+    ap.add_argument("--workload", default="matmul", choices=["matmul", "batch", "serve", "polymul", "gf"],
                     help="matmul: the compressed-matmul configuration (default line); batch: 4096 uneven instances")
     ap.add_argument("--algo", default="AUTO")
     ap.add_argument("--no-compare", action="store_true", help="skip the per-variant comparison block")
@@ -476,6 +748,12 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args, ws, rank, local)
+        return
+    if args.workload == "polymul":
+        run_polymul(args, ws, rank, local)
+        return
+    if args.workload == "gf":
+        run_gf(args, ws, rank, local)
         return
 
     import torch

@@ -6,6 +6,7 @@
 // accesses and runs a grid-stride loop over tiles of 256 items (grid = a multiple of the SM
 // count), so HBM traffic is coalesced whatever the number of coefficients per item.
 #include <algorithm>
+#include <type_traits>
 
 #include "fpdqt_internal.cuh"
 #include "stream.cuh"
@@ -187,6 +188,130 @@ __global__ void __launch_bounds__(256) k_polymul_word_bulk(const uint8_t* __rest
   op.C.init(P, ptab);
   stream_tiles(op, A, B, Cout, ntiles, ka, kb, ka + kb - 1, sm, err);
   if (op.bad) flag_error(err, ERR_RANGE);
+}
+
+// Products of small fixed degrees (ka, kb <= 4) in 32-bit words, four pairs per item so that
+// every shared-memory access is a whole word: the 4 ka residues of A (and of B) arrive as ka
+// words, the 4 kc residues of C leave as kc words.  Per pair: DQT of both operands at q = 2^b
+// (Eq. dqt), one 32-bit product, REDQ_kc (Algorithm 2: one division by the invariant p, then
+// u_i = ((r >> ib) - p (s >> ib)) mod q) and the correction through the lane-held table (MODE:
+// CORR_NONE when p | q, CORR_SHFL3 two residues per lookup, CORR_SHFL2 one).  Residues >= p
+// (p < 128) are caught with r | (r + 128 - p) per input word.
+template <int KA, int KB, int MODE>
+struct PolySmallOp {
+  static constexpr int KC = KA + KB - 1;
+  static constexpr uint32_t IPT = 2;
+  static constexpr uint32_t UNROLL = 1;
+  uint32_t b, p, pk, qmask, lane_val, bad;
+  DivP dv;
+  __device__ __forceinline__ void item(const uint8_t* a, const uint8_t* bb, uint8_t* out) {
+    uint32_t wa[KA], wb[KB], wc[KC];
+#pragma unroll
+    for (int i = 0; i < KA; ++i) {
+      wa[i] = reinterpret_cast<const uint32_t*>(a)[i];
+      bad |= wa[i] | (wa[i] + pk);
+    }
+#pragma unroll
+    for (int i = 0; i < KB; ++i) {
+      wb[i] = reinterpret_cast<const uint32_t*>(bb)[i];
+      bad |= wb[i] | (wb[i] + pk);
+    }
+#pragma unroll
+    for (int i = 0; i < KC; ++i) wc[i] = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t xa = 0, xb = 0;
+#pragma unroll
+      for (int i = KA - 1; i >= 0; --i) xa = (xa << b) | ((wa[(j * KA + i) >> 2] >> (8 * ((j * KA + i) & 3))) & 0xffu);
+#pragma unroll
+      for (int i = KB - 1; i >= 0; --i) xb = (xb << b) | ((wb[(j * KB + i) >> 2] >> (8 * ((j * KB + i) & 3))) & 0xffu);
+      const uint32_t r = xa * xb;
+      const uint32_t s = divp32(r, dv);
+      uint32_t u[KC], mu[KC];
+#pragma unroll
+      for (int i = 0; i < KC; ++i) u[i] = ((r >> (i * b)) - p * (s >> (i * b))) & qmask;
+      if (MODE == CORR_NONE) {
+#pragma unroll
+        for (int i = 0; i < KC; ++i) mu[i] = u[i];
+      } else if (MODE == CORR_SHFL3) {
+#pragma unroll
+        for (int i = 0; i + 1 < KC; i += 2) {
+          const uint32_t u2 = (i + 2 < KC) ? u[i + 2] : 0u;
+          const uint32_t v = __shfl_sync(0xffffffffu, lane_val, u[i] + p * u[i + 1] + p * p * u2);
+          mu[i] = v & 0xffu;
+          mu[i + 1] = (i + 2 < KC) ? (v >> 8) : u[i + 1];
+        }
+        if (KC & 1) mu[KC - 1] = u[KC - 1];
+      } else {
+#pragma unroll
+        for (int i = 0; i + 1 < KC; ++i) mu[i] = __shfl_sync(0xffffffffu, lane_val, u[i] + p * u[i + 1]);
+        mu[KC - 1] = u[KC - 1];
+      }
+#pragma unroll
+      for (int i = 0; i < KC; ++i) wc[(j * KC + i) >> 2] |= mu[i] << (8 * ((j * KC + i) & 3));
+    }
+#pragma unroll
+    for (int i = 0; i < KC; ++i) reinterpret_cast<uint32_t*>(out)[i] = wc[i];
+  }
+};
+
+template <int KA, int KB, int MODE>
+__global__ void __launch_bounds__(256) k_polymul_small(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
+                                                       uint8_t* __restrict__ Cout, uint64_t ntiles, RedqParams P,
+                                                       uint32_t* err) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  PolySmallOp<KA, KB, MODE> op;
+  op.b = P.b;
+  op.p = P.p;
+  op.pk = 0x01010101u * (128u - P.p);
+  op.qmask = (1u << P.b) - 1u;
+  op.dv = P.dv;
+  op.bad = 0;
+  Corrector c;
+  c.init(P, nullptr);
+  op.lane_val = c.lane_val;
+  constexpr int KC = KA + KB - 1;
+  stream_tiles(op, A, B, Cout, ntiles, 4 * KA, 4 * KB, 4 * KC, sm, err);
+  if (op.bad & 0x80808080u) flag_error(err, ERR_RANGE);
+}
+
+template <int KA, int KB>
+static bool launch_polymul_small_k(fp_ctx ctx, const uint8_t* A, const uint8_t* B, uint8_t* C, uint64_t ntiles,
+                                   const RedqParams& P, cudaStream_t st) {
+  constexpr int KC = KA + KB - 1;
+  constexpr uint64_t PAIRS = 4 * 256 * 2;   // 4 pairs per item, 256 threads, IPT = 2
+  const size_t smem = 2 * PAIRS * (KA + KB + KC) + 64;
+  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 4);
+  switch (P.mode) {
+    case CORR_NONE:
+      cudaFuncSetAttribute(k_polymul_small<KA, KB, CORR_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      FP_LAUNCH(ctx, "k_polymul_small", st, (k_polymul_small<KA, KB, CORR_NONE><<<grid, 256, smem, st>>>(A, B, C, ntiles, P, ctx->d_err)));
+      return true;
+    case CORR_SHFL3:
+      cudaFuncSetAttribute(k_polymul_small<KA, KB, CORR_SHFL3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      FP_LAUNCH(ctx, "k_polymul_small", st, (k_polymul_small<KA, KB, CORR_SHFL3><<<grid, 256, smem, st>>>(A, B, C, ntiles, P, ctx->d_err)));
+      return true;
+    case CORR_SHFL2:
+      cudaFuncSetAttribute(k_polymul_small<KA, KB, CORR_SHFL2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      FP_LAUNCH(ctx, "k_polymul_small", st, (k_polymul_small<KA, KB, CORR_SHFL2><<<grid, 256, smem, st>>>(A, B, C, ntiles, P, ctx->d_err)));
+      return true;
+    default: return false;
+  }
+}
+
+// Full tiles of 2048 pairs through k_polymul_small when the shape is instantiated (ka = kb in
+// {2, 3, 4}), the word is 32-bit, p < 128, the correction is a lane table and the arrays are
+// 16-byte aligned; returns the number of pairs done (0 if the path does not apply).
+static uint64_t polymul_small(fp_ctx ctx, const uint8_t* A, uint32_t ka, const uint8_t* B, uint32_t kb, uint8_t* C,
+                              uint64_t batch, const RedqParams& P, cudaStream_t st) {
+  const bool aligned = ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15u) == 0;
+  const uint64_t ntiles = batch / 2048;
+  if (!aligned || ntiles == 0 || P.p >= 128 || ka != kb) return 0;
+  bool ok = false;
+  if (ka == 2) ok = launch_polymul_small_k<2, 2>(ctx, A, B, C, ntiles, P, st);
+  else if (ka == 3) ok = launch_polymul_small_k<3, 3>(ctx, A, B, C, ntiles, P, st);
+  else if (ka == 4) ok = launch_polymul_small_k<4, 4>(ctx, A, B, C, ntiles, P, st);
+  return ok ? ntiles * 2048 : 0;
 }
 
 // Plain baseline: c_j = sum_i a_i b_{j-i} accumulated without reduction (delayed reduction,
@@ -381,6 +506,15 @@ static fp_status polymul_word_t(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32
   RedqParams P = make_redq(p, bq, kc);
   // full tiles of 2048 pairs on the bulk-copy path when the arrays are 16-byte aligned and a
   // tile pair of buffers fits comfortably in shared memory; the rest on the per-thread path
+  if (std::is_same<W, uint32_t>::value) {
+    const uint64_t done = polymul_small(ctx, A, ka, B, kb, C, batch, P, st);
+    FP_CUDA(cudaGetLastError());
+    A += done * ka;
+    B += done * kb;
+    C += done * kc;
+    batch -= done;
+    if (batch == 0) return FP_OK;
+  }
   constexpr uint64_t ITEMS = 256 * PolymulWordOp<W>::IPT;
   const bool aligned = ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15u) == 0;
   const size_t tile_bytes = ITEMS * (ka + kb + kc);

@@ -171,6 +171,98 @@ __global__ void __launch_bounds__(256) k_gf_mul_bulk(const E* __restrict__ a, co
   if (op.bad) flag_error(err, ERR_RANGE);
 }
 
+// ------------------------------------------------------------------ compile-time fields
+
+// The parameters fp_gf_create chooses for GF(P^K), as compile-time constants (same rules).
+template <uint32_t P, uint32_t K>
+struct GfConst {
+  static constexpr uint32_t order() { uint32_t o = 1; for (uint32_t i = 0; i < K; ++i) o *= P; return o; }
+  static constexpr uint32_t cbits() { uint32_t c = 0; while ((1u << c) < P) ++c; return c; }
+  static constexpr uint32_t fbits() {
+    uint32_t f = 1;
+    while ((1u << (f - 1)) < P || (1u << f) <= 2 * P - 2 + (1u << (f - 1)) - P) ++f;
+    return f;
+  }
+  static constexpr uint32_t qbits() {
+    uint32_t b = 1;
+    while ((1ull << b) <= (uint64_t)K * (P - 1) * (P - 1) || (1ull << b) < P) ++b;
+    return b;
+  }
+  static constexpr uint32_t ORDER = order(), CB = cbits(), FB = fbits(), B = qbits();
+  static constexpr uint32_t ONES = [] { uint32_t o = 0; for (uint32_t i = 0; i < K; ++i) o |= 1u << (i * FB); return o; }();
+};
+
+// One product by Algorithm FGDP (n = 1) with every shift, mask and loop bound fixed at
+// compile time: the same steps as gf_mul_one.
+template <uint32_t P, uint32_t K>
+__device__ __forceinline__ uint32_t gf_mul_fixed(uint32_t xa, uint32_t xb, const uint64_t* sw, const uint32_t* sL,
+                                                 const uint32_t* sH, uint32_t& bad) {
+  using F = GfConst<P, K>;
+  bad |= (xa >= F::ORDER) | (xb >= F::ORDER);
+  xa = xa < F::ORDER ? xa : 0u;
+  xb = xb < F::ORDER ? xb : 0u;
+  const uint64_t r = sw[xa] * sw[xb];             // table DQT of both operands, one word product
+  const uint64_t s = r / P;                       // REDQ compression quotient
+  uint32_t il = 0, ih = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < 2 * K - 1; ++j) {
+    const uint32_t uj = ((uint32_t)(r >> (j * F::B)) - P * (uint32_t)(s >> (j * F::B))) & ((1u << F::B) - 1u);
+    if (j < K) il |= uj << (j * F::CB);
+    if (j + 1 >= K) ih |= uj << ((j + 1 - K) * F::CB);
+  }
+  constexpr uint32_t HB = F::FB - 1;
+  uint32_t x = sL[il] + sH[ih];                    // two lookups, one field addition
+  const uint32_t ge = ((x + ((1u << HB) - P) * F::ONES) >> HB) & F::ONES;
+  x -= P * ge;
+  uint32_t idx = 0;
+#pragma unroll
+  for (int j = (int)K - 1; j >= 0; --j) idx = idx * P + ((x >> (j * F::FB)) & ((1u << F::FB) - 1u));
+  return idx;
+}
+
+// Four products per item, so that every shared-memory access of the stream is a whole
+// 32-bit word (uint8 elements) or a pair of words (uint16).
+template <uint32_t P, uint32_t K, typename E>
+struct GfFixedOp {
+  static constexpr uint32_t IPT = 4;
+  static constexpr uint32_t UNROLL = 2;
+  const uint64_t* sw;
+  const uint32_t *sL, *sH;
+  uint32_t bad;
+  __device__ __forceinline__ void item(const uint8_t* a, const uint8_t* b, uint8_t* out) {
+    if (sizeof(E) == 1) {
+      const uint32_t wa = *reinterpret_cast<const uint32_t*>(a), wb = *reinterpret_cast<const uint32_t*>(b);
+      uint32_t wc = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        wc |= gf_mul_fixed<P, K>((wa >> (8 * j)) & 0xffu, (wb >> (8 * j)) & 0xffu, sw, sL, sH, bad) << (8 * j);
+      *reinterpret_cast<uint32_t*>(out) = wc;
+    } else {
+      const uint2 wa = *reinterpret_cast<const uint2*>(a), wb = *reinterpret_cast<const uint2*>(b);
+      const uint32_t c0 = gf_mul_fixed<P, K>(wa.x & 0xffffu, wb.x & 0xffffu, sw, sL, sH, bad);
+      const uint32_t c1 = gf_mul_fixed<P, K>(wa.x >> 16, wb.x >> 16, sw, sL, sH, bad);
+      const uint32_t c2 = gf_mul_fixed<P, K>(wa.y & 0xffffu, wb.y & 0xffffu, sw, sL, sH, bad);
+      const uint32_t c3 = gf_mul_fixed<P, K>(wa.y >> 16, wb.y >> 16, sw, sL, sH, bad);
+      *reinterpret_cast<uint2*>(out) = make_uint2(c0 | (c1 << 16), c2 | (c3 << 16));
+    }
+  }
+};
+
+template <uint32_t P, uint32_t K, typename E>
+__global__ void __launch_bounds__(256) k_gf_mul_fixed(const E* __restrict__ a, const E* __restrict__ b,
+                                                      E* __restrict__ c, uint64_t ntiles, uint32_t table_bytes,
+                                                      GfDev G, uint32_t* err) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint64_t* sw;
+  uint32_t *sL, *sH;
+  gf_load_tables(G, sm, sw, sL, sH);
+  GfFixedOp<P, K, E> op{sw, sL, sH, 0};
+  stream_tiles(op, reinterpret_cast<const uint8_t*>(a), reinterpret_cast<const uint8_t*>(b),
+               reinterpret_cast<uint8_t*>(c), ntiles, 4 * sizeof(E), 4 * sizeof(E), 4 * sizeof(E), sm + table_bytes,
+               err);
+  if (op.bad) flag_error(err, ERR_RANGE);
+}
+
 // Segmented form for the serving loop: segment s multiplies count[s] pairs at byte offsets
 // a/b/c from `base`; one block per segment.
 struct GfSeg { uint64_t a, b, c; uint32_t count, pad; };
@@ -317,9 +409,38 @@ extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const
   int grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)ctx->num_sms * 4);
   GfDev G{g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb, 0};
   for (uint32_t i = 0; i < g->k; ++i) G.ones |= 1u << (i * g->fb);
+  const bool aligned = ((((uintptr_t)a) | ((uintptr_t)b) | ((uintptr_t)c)) & 15u) == 0;
+  // fields with compile-time parameters: full tiles of 4096 pairs (4 per item) on k_gf_mul_fixed
+  {
+    const uint64_t FITEMS = 256 * 4 * 4;
+    const uint64_t fnt = aligned ? count / FITEMS : 0;
+    const size_t tb = ((smem + 127) / 128) * 128, smem_f = tb + 6 * FITEMS * g->elem_bytes + 64;
+    const int grid_f = (int)std::min<uint64_t>(fnt, (uint64_t)ctx->num_sms * 2);
+    bool launched = false;
+#define FP_GF_FIXED(PP, KK, E)                                                                                        \
+    if (!launched && g->p == PP && g->k == KK && g->b == GfConst<PP, KK>::B && g->c == GfConst<PP, KK>::CB &&       \
+        g->fb == GfConst<PP, KK>::FB && fnt) {                                                                         \
+      FP_CUDA(cudaFuncSetAttribute(k_gf_mul_fixed<PP, KK, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f)); \
+      FP_LAUNCH(ctx, "k_gf_mul_fixed", st, (k_gf_mul_fixed<PP, KK, E><<<grid_f, 256, smem_f, st>>>(                 \
+                    (const E*)a, (const E*)b, (E*)c, fnt, (uint32_t)tb, G, ctx->d_err)));                             \
+      launched = true;                                                                                                 \
+    }
+    FP_GF_FIXED(3, 5, uint8_t)
+    FP_GF_FIXED(7, 4, uint16_t)
+    FP_GF_FIXED(2, 8, uint8_t)
+#undef FP_GF_FIXED
+    if (launched) {
+      FP_CUDA(cudaGetLastError());
+      const uint64_t fd = fnt * FITEMS, eb = g->elem_bytes;
+      if (fd == count) return FP_OK;
+      a = (const uint8_t*)a + fd * eb;
+      b = (const uint8_t*)b + fd * eb;
+      c = (uint8_t*)c + fd * eb;
+      count -= fd;
+    }
+  }
   // full tiles of 4096 pairs through the bulk-copy loop, the tail per thread
   const uint64_t ITEMS = 256 * 16;
-  const bool aligned = ((((uintptr_t)a) | ((uintptr_t)b) | ((uintptr_t)c)) & 15u) == 0;
   const uint64_t ntiles = aligned ? count / ITEMS : 0;
   const size_t tbytes = ((smem + 127) / 128) * 128;
   const size_t smem_b = tbytes + 6 * ITEMS * g->elem_bytes + 64;

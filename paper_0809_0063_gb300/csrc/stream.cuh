@@ -65,9 +65,10 @@ __device__ void stream_tiles(Op& op, const uint8_t* __restrict__ A, const uint8_
                              uint8_t* smem, uint32_t* err) {
   constexpr uint32_t ITEMS = 256 * Op::IPT;
   const uint32_t ta = ITEMS * sa, tb = ITEMS * sb, to = ITEMS * so;
-  uint8_t* inA[2] = {smem, smem + ta};
-  uint8_t* inB[2] = {smem + 2 * ta, smem + 2 * ta + tb};
-  uint8_t* out[2] = {smem + 2 * ta + 2 * tb, smem + 2 * ta + 2 * tb + to};
+  // buffer x of each double pair, by arithmetic (an indexed local array would live in memory)
+  auto inA = [&](int x) { return smem + x * ta; };
+  auto inB = [&](int x) { return smem + 2 * ta + x * tb; };
+  auto out = [&](int x) { return smem + 2 * ta + 2 * tb + x * to; };
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * (ta + tb + to));
   __shared__ uint32_t s_abort;
   const uint32_t tid = threadIdx.x;
@@ -84,8 +85,8 @@ __device__ void stream_tiles(Op& op, const uint8_t* __restrict__ A, const uint8_
   auto issue = [&](uint64_t i, int buf) {
     const uint64_t t = first + i * stride;
     st_expect_tx(&full[buf], ta + tb);
-    st_load(inA[buf], A + t * ta, ta, &full[buf]);
-    if (tb) st_load(inB[buf], B + t * tb, tb, &full[buf]);
+    st_load(inA(buf), A + t * ta, ta, &full[buf]);
+    if (tb) st_load(inB(buf), B + t * tb, tb, &full[buf]);
   };
   if (tid == 0) {
     if (mine > 0) issue(0, 0);
@@ -106,13 +107,13 @@ __device__ void stream_tiles(Op& op, const uint8_t* __restrict__ A, const uint8_
 #pragma unroll Op::UNROLL
     for (uint32_t j = 0; j < Op::IPT; ++j) {
       const uint32_t it = j * 256 + tid;
-      op.item(inA[buf] + it * sa, inB[buf] + it * sb, out[buf] + it * so);
+      op.item(inA(buf) + it * sa, inB(buf) + it * sb, out(buf) + it * so);
     }
     st_fence_async();                        // generic-proxy writes of out[buf] -> async proxy
     __syncthreads();                         // all threads done with inA/inB[buf], out[buf] written
     if (tid == 0) {
       const uint64_t t = first + i * stride;
-      st_store(C + t * to, out[buf], to);
+      st_store(C + t * to, out(buf), to);
       st_commit();
       if (i + 2 < mine) issue(i + 2, buf);
     }

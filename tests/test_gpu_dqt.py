@@ -143,3 +143,39 @@ def test_polymul_empty_batch_and_bad_input(env):
     fp.fp_ctx_status(ctx)                                                # flag was cleared
     with pytest.raises(fp.FpError):
         fp.fp_polymul_batched(ctx, 4, A, 2, A, 2, C, 4, fp.FP_ALGO_AUTO)  # not prime: host check
+
+
+@pytest.mark.parametrize("p,d", [(2, 1), (3, 2), (5, 1), (3, 3), (7, 2), (2, 3), (3, 1)])
+@pytest.mark.parametrize("algo", ["AUTO", "DQT_U32"])
+def test_polymul_word_granular_path(env, p, d, algo):
+    """Full tiles of 2048 pairs on the word-granular small-degree kernel (p = 2: no correction,
+    p = 3: two residues per table lookup, p = 5: one; p = 7 takes the shared-table path) plus a
+    ragged tail on the per-pair kernel; every coefficient compared."""
+    fp, torch, dev, ctx = env
+    batch = 3 * 2048 + 777
+    a, b = workloads.polymul_inputs(40 + p * d, p, batch, d, d)
+    a[-1], b[0] = p - 1, p - 1                        # bound edges in the tail and the first tile
+    C = torch.empty((batch, 2 * d + 1), dtype=torch.uint8, device=dev)
+    try:
+        fp.fp_polymul_batched(ctx, p, to_dev(torch, dev, a), d, to_dev(torch, dev, b), d, C, batch,
+                              getattr(fp, "FP_ALGO_" + algo))
+    except fp.FpError as e:
+        if e.status == fp.FP_EBOUND:
+            pytest.skip("the product does not fit a 32-bit word")
+        raise
+    fp.fp_ctx_status(ctx)
+    assert np.array_equal(C.cpu().numpy(), field.polymul_mod(a, b, p))
+
+
+@pytest.mark.parametrize("pos", [0, 1000, 2047, 4095, 6143, 6144 + 700])
+def test_polymul_word_granular_range_check(env, pos):
+    """A coefficient equal to p anywhere (each full tile, the tail) raises the range error."""
+    fp, torch, dev, ctx = env
+    p, d, batch = 3, 2, 3 * 2048 + 777
+    a, b = workloads.polymul_inputs(91, p, batch, d, d)
+    a[pos, pos % 3] = p
+    C = torch.empty((batch, 5), dtype=torch.uint8, device=dev)
+    fp.fp_polymul_batched(ctx, p, to_dev(torch, dev, a), d, to_dev(torch, dev, b), d, C, batch, fp.FP_ALGO_AUTO)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_ctx_status(ctx)
+    assert ei.value.status == fp.FP_EINVAL

@@ -107,3 +107,21 @@ def test_dot_unaligned_and_all_max(env):
         fp.fp_dot(ctx, p, buf[1:], buf[1:], n, out, algo)    # 1-byte offset: unaligned path
         fp.fp_ctx_status(ctx)
         assert int(out.item()) == (n * (p - 1) ** 2) % p
+
+
+@pytest.mark.parametrize("p,k,pos", [(3, 5, 5000), (7, 4, 4095), (3, 5, 3 * 4096 + 7)])
+def test_gf_bad_index_in_full_tiles(env, p, k, pos):
+    """An index >= p^k inside a full tile of the compile-time field kernel, or in the tail,
+    raises the range error; the other products are still exact."""
+    fp, torch, dev, ctx = env
+    n = 3 * 4096 + 100
+    a, b = workloads.gf_inputs(17, p, k, n)
+    a = a.copy()
+    a[pos] = p ** k if p ** k < 256 or a.dtype == np.uint16 else 255
+    gf = fp.fp_gf_create(ctx, p, k)
+    try:
+        with pytest.raises(fp.FpError) as ei:
+            gf_run(fp, torch, dev, ctx, gf, a, b)
+        assert ei.value.status == fp.FP_EINVAL
+    finally:
+        fp.fp_gf_destroy(gf)
