@@ -383,7 +383,8 @@ def run_polymul(args, ws, rank, local):
         per_launch_ms = dms / dn
         achieved = batch * bpp / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
+                "frac": achieved / hbm,
+                "traffic": stored_traffic(dom, [(args.algo, batch)], 1) if dom == "k_polymul_small" else None,
                 "peak_source": f"HBM copy ({peak_src})", "launches": dn, "avg_launch_ms": per_launch_ms,
                 "scaled_2^26": {"achieved": big * bpp / (tb / 1e3) / 1e9, "frac": big * bpp / (tb / 1e3) / 1e9 / hbm,
                                 "ms": tb}}
@@ -489,7 +490,9 @@ def run_gf(args, ws, rank, local):
                "sample": f"2^18 pairs per field, round robin ({dt:.1f} s, numpy schoolbook + remainder, single thread)"}
     kper = kms / max(1, nk)
     roof = {"bound": "hbm", "kernel": "k_gf_mul_fixed", "achieved": nbytes / len(fields) / (kper / 1e3) / 1e9,
-            "peak": hbm, "unit": "GB/s", "frac": nbytes / len(fields) / (kper / 1e3) / 1e9 / hbm, "traffic": None,
+            "peak": hbm, "unit": "GB/s", "frac": nbytes / len(fields) / (kper / 1e3) / 1e9 / hbm,
+            "traffic": stored_traffic("k_gf_mul_fixed", [(f"GF({p}^{k})", count) for p, k in workloads.GF_FIELDS],
+                                      len(fields)),
             "peak_source": f"HBM copy ({peak_src})", "launches": nk, "avg_launch_ms": kper,
             "note": "achieved = average index bytes per field launch / average launch time"}
     if rank == 0:
