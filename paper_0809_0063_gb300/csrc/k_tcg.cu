@@ -56,6 +56,9 @@ struct GProb {
   int tile0;        // index of this problem's first tile in the global list
   uint32_t p;
   DivP dv;
+  uint32_t fdiv;    // 1 when k (p-1)^2 < 2^23: reduce with FDIV in fp32 (Table fdiv, case 3)
+  float c18;        // 2^18 RU(1/p)
+  float pm18;       // -p 2^-18
 };
 
 struct GParams {
@@ -246,33 +249,56 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
       if (lane == 0) got = mbar_wait(&tfull[buf], (uint32_t)(lt >> 1) & 1u, abort_flag) ? 1u : 0u;
       if (!__shfl_sync(0xffffffffu, got, 0)) break;
       tc_fence_after();
+      // parameters in registers (read through the grid-constant block they would be reloaded
+      // after every store to C)
       const DivP dv = pr.dv;
-      const uint32_t p = pr.p;
+      const uint32_t p = pr.p, fdiv = pr.fdiv;
+      const float c18 = pr.c18, pm18 = pr.pm18;
+      const int m = pr.m, n = pr.n, ldc = pr.ldc;
+      uint8_t* const Cb = pr.C;
       const int row = x.m0 + q * 32 + lane;
       for (int cb = 0; cb < 4; ++cb) {
         const int col0 = half * 128 + cb * 32;
         uint32_t v[32];
         tmem_ld32(tmem + lane_base + (uint32_t)(buf * 256 + col0), v);
         uint32_t packed[8];
+        if (fdiv) {
+          // Each sum is x 2^-18 with x < 2^23.  Algorithm FDIV, case 3 of Table fdiv (beta = 24):
+          // floor(x / p) = RD(x RU(1/p)), exact below 2^23; the floor of the product is taken by
+          // a round-down addition of 2^23, and x - p floor(x / p) is formed exactly in fp32.
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-          uint32_t w = 0;
+          for (int j = 0; j < 32; j += 4) {
+            uint32_t w = 0;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            // the sum is 2^-18 times the integer sum: scaling back by 2^18 is exact
-            const uint32_t s = __float2uint_rn(__uint_as_float(v[j + u]) * 262144.0f);
-            w |= modp32(s, dv, p) << (8 * u);
+            for (int u = 0; u < 4; ++u) {
+              const float vs = __uint_as_float(v[j + u]);
+              const float qf = __fadd_rd(__fmul_rd(vs, c18), 8388608.0f) - 8388608.0f;
+              const float rs = fmaf(pm18, qf, vs);                   // (x - p q) 2^-18, exact
+              w |= (__float_as_uint(fmaf(rs, 262144.0f, 8388608.0f)) - 0x4B000000u) << (8 * u);
+            }
+            packed[j >> 2] = w;
           }
-          packed[j >> 2] = w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            uint32_t w = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              // the sum is 2^-18 times the integer sum: scaling back by 2^18 is exact
+              const uint32_t s = __float2uint_rn(__uint_as_float(v[j + u]) * 262144.0f);
+              w |= modp32(s, dv, p) << (8 * u);
+            }
+            packed[j >> 2] = w;
+          }
         }
         const int c0 = x.n0 + col0;
-        if (row < pr.m && c0 < pr.n) {
-          uint8_t* dst = pr.C + (size_t)row * pr.ldc + c0;
-          if (c0 + 32 <= pr.n && ((((uintptr_t)dst) & 15u) == 0)) {
+        if (row < m && c0 < n) {
+          uint8_t* dst = Cb + (size_t)row * ldc + c0;
+          if (c0 + 32 <= n && ((((uintptr_t)dst) & 15u) == 0)) {
             reinterpret_cast<uint4*>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
             reinterpret_cast<uint4*>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
           } else {
-            for (int j = 0; j < 32 && c0 + j < pr.n; ++j) dst[j] = (uint8_t)(packed[j >> 2] >> (8 * (j & 3)));
+            for (int j = 0; j < 32 && c0 + j < n; ++j) dst[j] = (uint8_t)(packed[j >> 2] >> (8 * (j & 3)));
           }
         }
       }
@@ -331,6 +357,9 @@ static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int co
     g.tile0 = tile;
     g.p = x.p;
     g.dv = make_divp(x.p);
+    g.fdiv = (uint64_t)x.k * (x.p - 1) * (x.p - 1) < (1ull << 23) ? 1u : 0u;
+    g.c18 = make_redq(x.p, 1, 1).invp_f * 262144.0f;   // RU(1/p) scaled by 2^18 (exact)
+    g.pm18 = -(float)x.p / 262144.0f;
     tile += g.tm * g.tn;
   }
   hp.nprob = count;

@@ -120,10 +120,13 @@ def test_grouped_many_tiles_per_cta(env):
     q.check(rows)
 
 
-@pytest.mark.parametrize("p,k", [(17, 65535), (2, 1 << 20), (3, 4194303)])
+@pytest.mark.parametrize("p,k", [(17, 65535), (2, 1 << 20), (3, 4194303), (17, 32767), (17, 32768), (13, 58253)])
 def test_grouped_exactness_edge(env, p, k):
     """All entries p-1 with k (p-1)^2 just below 2^24 (p = 3: k = 2^22 - 1 is beyond the
-    fp_matmul size limit, so it must be refused): every fp32 sum is the largest exact one."""
+    fp_matmul size limit, so it must be refused): every fp32 sum is the largest exact one.
+    k (p-1)^2 = 2^23 - 256 (p = 17, k = 32767) and 2^23 - 176 (p = 13, k = 58253) are at the
+    edge of the sums the epilogue reduces by FDIV (Table fdiv case 3 in binary32); 2^23
+    (k = 32768) takes the integer reduction."""
     fp, torch, dev, ctx = env
     m, n = 40, 300
     if k > (1 << 20):
