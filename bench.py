@@ -353,6 +353,43 @@ def run_polymul(args, ws, rank, local):
         if isinstance(compare.get("PLAIN"), float):
             compare["best_packed_over_plain"] = max(v for k, v in compare.items()
                                                     if k.startswith("DQT") and isinstance(v, float)) / compare["PLAIN"]
+    # the other HBM-bound steps of the path on their own (a2 DQT pack, a4-a5 REDQ unpack, and
+    # the dot product): GB/s of algorithmic bytes, L2 flushed before each call
+    hbm_rows = {}
+    if not args.no_compare:
+        prm = fp.fp_dqt_choose(p, da + 1, 1, fp.FP_WORD_U32)            # 3 coefficients per u32 word at q = 16
+        W = torch.empty(big, dtype=torch.int32, device=dev)
+        fn = lambda: fp.fp_dqt_pack(ctx, prm, Ab, W, big)
+        fn()
+        torch.cuda.synchronize()
+        t = statistics.median(_timed(torch, stream, fn, 5, flush))
+        hbm_rows["dqt_pack (2^26 x 3 residues -> u32)"] = {"ms": t, "GB/s": big * (3 + 4) / (t / 1e3) / 1e9,
+                                                            "frac_hbm": big * (3 + 4) / (t / 1e3) / 1e9 / hbm}
+        prm5 = fp.fp_dqt_choose(p, da + 1, 1, fp.FP_WORD_U32)
+        prm5.ndig = 2 * (da + 1) - 1                                   # unpack the 5 digits of a product word
+        fn = lambda: fp.fp_dqt_unpack_redq(ctx, prm5, W, Cb, big)
+        fn()
+        torch.cuda.synchronize()
+        t = statistics.median(_timed(torch, stream, fn, 5, flush))
+        hbm_rows["dqt_unpack_redq (2^26 u32 -> 5 residues)"] = {"ms": t, "GB/s": big * (4 + 5) / (t / 1e3) / 1e9,
+                                                                 "frac_hbm": big * (4 + 5) / (t / 1e3) / 1e9 / hbm}
+        nd = 1 << 28
+        u = torch.randint(0, p, (nd,), dtype=torch.uint8, device=dev)
+        vv = torch.randint(0, p, (nd,), dtype=torch.uint8, device=dev)
+        out = torch.empty(1, dtype=torch.int32, device=dev)
+        for nm in ("AUTO", "PLAIN"):
+            fn = lambda nm=nm: fp.fp_dot(ctx, p, u, vv, nd, out, getattr(fp, "FP_ALGO_" + nm))
+            fn()
+            torch.cuda.synchronize()
+            t = statistics.median(_timed(torch, stream, fn, 5, flush))
+            hbm_rows[f"dot {nm} (2^28 residue pairs)"] = {"ms": t, "GB/s": 2 * nd / (t / 1e3) / 1e9,
+                                                          "frac_hbm": 2 * nd / (t / 1e3) / 1e9 / hbm}
+        fp.fp_ctx_status(ctx)
+        want = int((u.to(torch.int64) * vv.to(torch.int64)).sum().item()) % p
+        fp.fp_dot(ctx, p, u, vv, nd, out, fp.FP_ALGO_AUTO)
+        fp.fp_ctx_status(ctx)
+        assert int(out.item()) == want, "dot parity"
+        del u, vv, W
     # end to end: pinned host inputs in, results out, each step
     ha, hb = torch.from_numpy(sets[0][0]).pin_memory(), torch.from_numpy(sets[0][1]).pin_memory()
     hc = torch.empty((batch, da + db + 1), dtype=torch.uint8).pin_memory()
@@ -402,6 +439,7 @@ def run_polymul(args, ws, rank, local):
             "e2e": {"value": ws * batch * mpp / (te / 1e3), "unit": "F_p MAC/s",
                     "h2d_bytes_per_step": batch * (da + db + 2), "d2h_bytes_per_step": batch * (da + db + 1)},
             "gpu_launches": launches, "clocks": clk.summary(), "compare_same_inputs_2^26": compare,
+            "other_hbm_steps": hbm_rows,
         }))
     fp.fp_ctx_destroy(ctx)
 

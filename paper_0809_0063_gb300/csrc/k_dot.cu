@@ -91,6 +91,136 @@ __global__ void __launch_bounds__(256) k_dot_dqt(const uint8_t* __restrict__ u, 
   if (bad) flag_error(err, ERR_RANGE);
 }
 
+// The same middle product on 16-byte vectors: each thread takes 16 entries of u and of v at a
+// time (16 / D1 blocks of D1 entries, D1 in {2, 4, 8}), packs every block reversed (u) and
+// forward (v) at Q = 2^b from the bytes in registers, and accumulates the u64 word products;
+// every F blocks the digit of Q^(D1-1) -- the block dot products summed -- is moved out to a
+// u64 sum.  Range check on whole words.  The < 16 entries past the last full vector are added
+// plainly by thread 0 of block 0.
+template <int D1>
+__global__ void __launch_bounds__(256) k_dot_dqt_vec(const uint8_t* __restrict__ u, const uint8_t* __restrict__ v,
+                                                     uint64_t n, uint64_t* __restrict__ partial, uint32_t p,
+                                                     uint32_t b, uint32_t F, uint32_t* err) {
+  constexpr int BPV = 16 / D1;                         // blocks per vector
+  const uint64_t nv = n / 16;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t mask = (1ull << b) - 1;
+  const uint32_t mid = (D1 - 1) * b;
+  const uint32_t pp = 0x01010101u * p;
+  uint64_t sum = 0, acc = 0;
+  uint32_t cnt = 0, bad = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(u) + i);
+    const uint4 c = __ldg(reinterpret_cast<const uint4*>(v) + i);
+    const uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bad |= __vcmpgeu4(wa[q], pp) | __vcmpgeu4(wc[q], pp);
+    if (cnt + BPV > F) {                               // the next BPV blocks would overflow a digit
+      sum += (acc >> mid) & mask;
+      acc = 0;
+      cnt = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < BPV; ++j) {
+      uint64_t wl = 0, wr = 0;
+#pragma unroll
+      for (int t = 0; t < D1; ++t) {
+        const int e = j * D1 + t;                      // entry within the vector
+        const uint64_t ea = (wa[e >> 2] >> (8 * (e & 3))) & 0xffu, ec = (wc[e >> 2] >> (8 * (e & 3))) & 0xffu;
+        wl |= ea << ((D1 - 1 - t) * b);                // reversed: entry t gets Q^(D1-1-t)
+        wr |= ec << (t * b);                           // forward
+      }
+      acc += wl * wr;
+    }
+    cnt += BPV;
+  }
+  sum += (acc >> mid) & mask;
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (uint64_t i = nv * 16; i < n; ++i) {
+      const uint32_t x = u[i], y = v[i];
+      bad |= (x >= p) | (y >= p);
+      sum += x * y;
+    }
+  for (int o = 16; o; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+  __shared__ uint64_t ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    partial[blockIdx.x] = t;
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// The middle product at a byte-aligned Q, where packing is a byte permutation of the loaded
+// words.  QB = 8: blocks of 4 entries (one 32-bit word), Q = 2^8: the forward word of v is the
+// little-endian word as loaded, the reversed word of u is its byte reversal, and the digit of
+// Q^3 of their product is the block dot product (p <= 7).  QB = 16: blocks of 2 entries, each
+// spread to 16-bit fields by one permutation (p <= 181).  One 32 x 32 -> 64-bit multiply-add per
+// block; every F blocks the middle digit is moved out.  Tail entries as in k_dot_dqt_vec.
+template <int QB>
+__global__ void __launch_bounds__(256) k_dot_dqt_bytes(const uint8_t* __restrict__ u, const uint8_t* __restrict__ v,
+                                                       uint64_t n, uint64_t* __restrict__ partial, uint32_t p,
+                                                       uint32_t F, uint32_t* err) {
+  const uint64_t nv = n / 16;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  constexpr uint32_t MID = QB == 8 ? 24 : 16;
+  constexpr uint64_t MASK = QB == 8 ? 0xffull : 0xffffull;
+  const uint32_t pp = 0x01010101u * p;
+  uint64_t sum = 0, acc = 0;
+  uint32_t cnt = 0, bad = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(u) + i);
+    const uint4 c = __ldg(reinterpret_cast<const uint4*>(v) + i);
+    const uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      bad |= __vcmpgeu4(wa[q], pp) | __vcmpgeu4(wc[q], pp);
+      if (QB == 8) {
+        if (cnt == F) {
+          sum += (acc >> MID) & MASK;
+          acc = 0;
+          cnt = 0;
+        }
+        acc += (uint64_t)__byte_perm(wa[q], 0, 0x0123) * wc[q];
+        ++cnt;
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (cnt == F) {
+            sum += (acc >> MID) & MASK;
+            acc = 0;
+            cnt = 0;
+          }
+          // entries 2h, 2h+1: u reversed (u_2h at Q), v forward (v_2h at 1), 16-bit fields
+          const uint32_t wl = __byte_perm(wa[q], 0, h ? 0x4243u : 0x4041u);
+          const uint32_t wr = __byte_perm(wc[q], 0, h ? 0x4342u : 0x4140u);
+          acc += (uint64_t)wl * wr;
+          ++cnt;
+        }
+      }
+    }
+  }
+  sum += (acc >> MID) & MASK;
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (uint64_t i = nv * 16; i < n; ++i) {
+      const uint32_t x = u[i], y = v[i];
+      bad |= (x >= p) | (y >= p);
+      sum += x * y;
+    }
+  for (int o = 16; o; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+  __shared__ uint64_t ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    partial[blockIdx.x] = t;
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
 __global__ void k_dot_final(const uint64_t* __restrict__ partial, int nparts, uint32_t* out, uint32_t p) {
   uint64_t t = 0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) t += partial[i] % p;
@@ -127,6 +257,47 @@ static bool dot_dqt_params(uint32_t p, uint32_t& D1, uint32_t& b, uint32_t& F) {
   return false;
 }
 
+// Parameters for the vector kernel: the largest D1 in {8, 4, 2} with at least one vector's
+// 16 / D1 blocks per accumulation (F >= 16 / D1) and the 2 D1 - 1 digits within 64 bits.
+static bool dot_dqt_vec_params(uint32_t p, uint32_t& D1, uint32_t& b, uint32_t& F) {
+  uint64_t pp = (uint64_t)(p - 1) * (p - 1);
+  if (pp == 0) pp = 1;
+  for (uint32_t d1 = 8; d1 >= 2; d1 /= 2) {
+    uint32_t bb = 64 / (2 * d1 - 1);
+    if (bb > 32) bb = 32;
+    const uint64_t f = ((1ull << bb) - 1) / (d1 * pp);
+    if (f >= 16 / d1) {
+      D1 = d1;
+      b = bb;
+      F = (uint32_t)(f > 1024 ? 1024 : f);
+      return true;
+    }
+  }
+  return false;
+}
+
+// The packed stream: the vector kernel when both arrays are 16-byte aligned and a vector
+// packing fits, else the entry-by-entry kernel.
+static void dot_dqt_launch(const uint8_t* u, const uint8_t* v, size_t n, uint64_t* partial, uint32_t p, uint32_t D1,
+                           uint32_t b, uint32_t F, int grid, cudaStream_t st, uint32_t* err) {
+  uint32_t vD1, vb, vF;
+  const bool aligned = ((((uintptr_t)u) | ((uintptr_t)v)) & 15u) == 0;
+  const uint64_t pp = (uint64_t)(p - 1) * (p - 1);
+  // byte-aligned Q: F blocks with F D1 (p-1)^2 < Q (every digit of the accumulated word)
+  if (aligned && p <= 7 && 4 * pp < 256) {
+    k_dot_dqt_bytes<8><<<grid, 256, 0, st>>>(u, v, n, partial, p, (uint32_t)(255 / (4 * (pp ? pp : 1))), err);
+  } else if (aligned && 2 * pp < 65536) {
+    const uint64_t f = 65535 / (2 * (pp ? pp : 1));
+    k_dot_dqt_bytes<16><<<grid, 256, 0, st>>>(u, v, n, partial, p, (uint32_t)(f > 4096 ? 4096 : f), err);
+  } else if (aligned && dot_dqt_vec_params(p, vD1, vb, vF)) {
+    if (vD1 == 8) k_dot_dqt_vec<8><<<grid, 256, 0, st>>>(u, v, n, partial, p, vb, vF, err);
+    else if (vD1 == 4) k_dot_dqt_vec<4><<<grid, 256, 0, st>>>(u, v, n, partial, p, vb, vF, err);
+    else k_dot_dqt_vec<2><<<grid, 256, 0, st>>>(u, v, n, partial, p, vb, vF, err);
+  } else {
+    k_dot_dqt<<<grid, 256, 0, st>>>(u, v, n, partial, p, D1, b, F, err);
+  }
+}
+
 fp_status launch_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v, size_t n, uint32_t* out,
                      int algo, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -145,12 +316,12 @@ fp_status launch_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v,
     return FP_EBOUND;
   }
   if (dqt && algo != FP_ALGO_AUTO) {
-    FP_LAUNCH(ctx, "k_dot_dqt", st, k_dot_dqt<<<grid, 256, 0, st>>>(u, v, n, partial, p, D1, b, F, ctx->d_err));
+    FP_LAUNCH(ctx, "k_dot_dqt", st, dot_dqt_launch(u, v, n, partial, p, D1, b, F, grid, st, ctx->d_err));
   } else if (algo == FP_ALGO_AUTO && dqt) {
     // both are HBM streams; the packed one issues fewer multiplies per byte only for small p,
     // the plain dp4a stream is the cheaper instruction mix: AUTO takes the packed route
     // (the method) when it packs at least 4 entries per word.
-    if (D1 >= 4) FP_LAUNCH(ctx, "k_dot_dqt", st, k_dot_dqt<<<grid, 256, 0, st>>>(u, v, n, partial, p, D1, b, F, ctx->d_err));
+    if (D1 >= 4) FP_LAUNCH(ctx, "k_dot_dqt", st, dot_dqt_launch(u, v, n, partial, p, D1, b, F, grid, st, ctx->d_err));
     else FP_LAUNCH(ctx, "k_dot_plain", st, k_dot_plain<<<grid, 256, 0, st>>>(u, v, n, partial, p, ctx->d_err));
   } else {
     FP_LAUNCH(ctx, "k_dot_plain", st, k_dot_plain<<<grid, 256, 0, st>>>(u, v, n, partial, p, ctx->d_err));
@@ -244,7 +415,7 @@ extern "C" fp_status fp_dot_noalloc(uint32_t p, const uint8_t* u, const uint8_t*
     return FP_EBOUND;
   }
   if (dqt && (algo != FP_ALGO_AUTO || D1 >= 4))
-    k_dot_dqt<<<grid, 256, 0, st>>>(u, v, n, partial, p, D1, b, F, err);
+    dot_dqt_launch(u, v, n, partial, p, D1, b, F, grid, st, err);
   else
     k_dot_plain<<<grid, 256, 0, st>>>(u, v, n, partial, p, err);
   FP_CUDA(cudaGetLastError());

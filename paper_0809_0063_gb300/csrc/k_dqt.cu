@@ -197,6 +197,34 @@ __global__ void __launch_bounds__(256) k_polymul_word_bulk(const uint8_t* __rest
 // u_i = ((r >> ib) - p (s >> ib)) mod q) and the correction through the lane-held table (MODE:
 // CORR_NONE when p | q, CORR_SHFL3 two residues per lookup, CORR_SHFL2 one).  Residues >= p
 // (p < 128) are caught with r | (r + 128 - p) per input word.
+// REDQ_KC of a 32-bit word r (Algorithm 2) with the correction through the lane-held table:
+// one division s = floor(r / p), u_i = ((r >> ib) - p (s >> ib)) mod q, then mu_i.
+template <int KC, int MODE>
+__device__ __forceinline__ void redq32_fixed(uint32_t r, uint32_t b, uint32_t p, uint32_t qmask, const DivP& dv,
+                                             uint32_t lane_val, uint32_t (&mu)[KC]) {
+  const uint32_t s = divp32(r, dv);
+  uint32_t u[KC];
+#pragma unroll
+  for (int i = 0; i < KC; ++i) u[i] = ((r >> (i * b)) - p * (s >> (i * b))) & qmask;
+  if (MODE == CORR_NONE) {
+#pragma unroll
+    for (int i = 0; i < KC; ++i) mu[i] = u[i];
+  } else if (MODE == CORR_SHFL3) {
+#pragma unroll
+    for (int i = 0; i + 1 < KC; i += 2) {
+      const uint32_t u2 = (i + 2 < KC) ? u[i + 2] : 0u;
+      const uint32_t v = __shfl_sync(0xffffffffu, lane_val, u[i] + p * u[i + 1] + p * p * u2);
+      mu[i] = v & 0xffu;
+      mu[i + 1] = (i + 2 < KC) ? (v >> 8) : u[i + 1];
+    }
+    if (KC & 1) mu[KC - 1] = u[KC - 1];
+  } else {
+#pragma unroll
+    for (int i = 0; i + 1 < KC; ++i) mu[i] = __shfl_sync(0xffffffffu, lane_val, u[i] + p * u[i + 1]);
+    mu[KC - 1] = u[KC - 1];
+  }
+}
+
 template <int KA, int KB, int MODE>
 struct PolySmallOp {
   static constexpr int KC = KA + KB - 1;
@@ -225,28 +253,8 @@ struct PolySmallOp {
       for (int i = KA - 1; i >= 0; --i) xa = (xa << b) | ((wa[(j * KA + i) >> 2] >> (8 * ((j * KA + i) & 3))) & 0xffu);
 #pragma unroll
       for (int i = KB - 1; i >= 0; --i) xb = (xb << b) | ((wb[(j * KB + i) >> 2] >> (8 * ((j * KB + i) & 3))) & 0xffu);
-      const uint32_t r = xa * xb;
-      const uint32_t s = divp32(r, dv);
-      uint32_t u[KC], mu[KC];
-#pragma unroll
-      for (int i = 0; i < KC; ++i) u[i] = ((r >> (i * b)) - p * (s >> (i * b))) & qmask;
-      if (MODE == CORR_NONE) {
-#pragma unroll
-        for (int i = 0; i < KC; ++i) mu[i] = u[i];
-      } else if (MODE == CORR_SHFL3) {
-#pragma unroll
-        for (int i = 0; i + 1 < KC; i += 2) {
-          const uint32_t u2 = (i + 2 < KC) ? u[i + 2] : 0u;
-          const uint32_t v = __shfl_sync(0xffffffffu, lane_val, u[i] + p * u[i + 1] + p * p * u2);
-          mu[i] = v & 0xffu;
-          mu[i + 1] = (i + 2 < KC) ? (v >> 8) : u[i + 1];
-        }
-        if (KC & 1) mu[KC - 1] = u[KC - 1];
-      } else {
-#pragma unroll
-        for (int i = 0; i + 1 < KC; ++i) mu[i] = __shfl_sync(0xffffffffu, lane_val, u[i] + p * u[i + 1]);
-        mu[KC - 1] = u[KC - 1];
-      }
+      uint32_t mu[KC];
+      redq32_fixed<KC, MODE>(xa * xb, b, p, qmask, dv, lane_val, mu);
 #pragma unroll
       for (int i = 0; i < KC; ++i) wc[(j * KC + i) >> 2] |= mu[i] << (8 * ((j * KC + i) & 3));
     }
@@ -312,6 +320,83 @@ static uint64_t polymul_small(fp_ctx ctx, const uint8_t* A, uint32_t ka, const u
   else if (ka == 3) ok = launch_polymul_small_k<3, 3>(ctx, A, B, C, ntiles, P, st);
   else if (ka == 4) ok = launch_polymul_small_k<4, 4>(ctx, A, B, C, ntiles, P, st);
   return ok ? ntiles * 2048 : 0;
+}
+
+// DQT pack into 32-bit words, K residues per word, four words per item (every shared-memory
+// access a whole word): Horner at q = 2^b from the K residue bytes in registers.
+template <int K>
+struct PackSmallOp {
+  static constexpr uint32_t IPT = 4;
+  static constexpr uint32_t UNROLL = 1;
+  uint32_t b, pk, bad;
+  __device__ __forceinline__ void item(const uint8_t* a, const uint8_t*, uint8_t* out) {
+    uint32_t wa[K], wo[4];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      wa[i] = reinterpret_cast<const uint32_t*>(a)[i];
+      bad |= wa[i] | (wa[i] + pk);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t x = 0;
+#pragma unroll
+      for (int i = K - 1; i >= 0; --i) x = (x << b) | ((wa[(j * K + i) >> 2] >> (8 * ((j * K + i) & 3))) & 0xffu);
+      wo[j] = x;
+    }
+    *reinterpret_cast<uint4*>(out) = make_uint4(wo[0], wo[1], wo[2], wo[3]);
+  }
+};
+
+template <int K>
+__global__ void __launch_bounds__(256) k_pack_small(const uint8_t* __restrict__ coeffs, uint32_t* __restrict__ words,
+                                                    uint64_t ntiles, uint32_t b, uint32_t p, uint32_t* err) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  PackSmallOp<K> op;
+  op.b = b;
+  op.pk = 0x01010101u * (128u - p);
+  op.bad = 0;
+  stream_tiles(op, coeffs, nullptr, reinterpret_cast<uint8_t*>(words), ntiles, 4 * K, 0, 16, sm, err);
+  if (op.bad & 0x80808080u) flag_error(err, ERR_RANGE);
+}
+
+// REDQ_ND unpack of 32-bit words, four words per item (ND output words).
+template <int ND, int MODE>
+struct UnpackSmallOp {
+  static constexpr uint32_t IPT = 4;
+  static constexpr uint32_t UNROLL = 1;
+  uint32_t b, p, qmask, lane_val;
+  DivP dv;
+  __device__ __forceinline__ void item(const uint8_t* a, const uint8_t*, uint8_t* out) {
+    const uint4 w = *reinterpret_cast<const uint4*>(a);
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+    uint32_t wc[ND];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) wc[i] = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t mu[ND];
+      redq32_fixed<ND, MODE>(ws[j], b, p, qmask, dv, lane_val, mu);
+#pragma unroll
+      for (int i = 0; i < ND; ++i) wc[(j * ND + i) >> 2] |= mu[i] << (8 * ((j * ND + i) & 3));
+    }
+#pragma unroll
+    for (int i = 0; i < ND; ++i) reinterpret_cast<uint32_t*>(out)[i] = wc[i];
+  }
+};
+
+template <int ND, int MODE>
+__global__ void __launch_bounds__(256) k_unpack_small(const uint32_t* __restrict__ words, uint8_t* __restrict__ coeffs,
+                                                      uint64_t ntiles, RedqParams P, uint32_t* err) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  UnpackSmallOp<ND, MODE> op;
+  op.b = P.b;
+  op.p = P.p;
+  op.qmask = (1u << P.b) - 1u;
+  op.dv = P.dv;
+  Corrector c;
+  c.init(P, nullptr);
+  op.lane_val = c.lane_val;
+  stream_tiles(op, reinterpret_cast<const uint8_t*>(words), nullptr, coeffs, ntiles, 16, 0, 4 * ND, sm, err);
 }
 
 // Plain baseline: c_j = sum_i a_i b_{j-i} accumulated without reduction (delayed reduction,
@@ -432,9 +517,67 @@ static int grid_for(fp_ctx ctx, uint64_t ntiles, int per_sm) {
   return (int)(g ? g : 1);
 }
 
+// Full tiles of 4096 words through k_pack_small (32-bit words, k in 2..5, p < 128, aligned);
+// returns the number of words done.
+static uint64_t pack_small(fp_ctx ctx, const fp_dqt_params& prm, const uint8_t* coeffs, uint32_t* words,
+                           uint64_t count, cudaStream_t st) {
+  const uint64_t ntiles = count / 4096;
+  if (ntiles == 0 || prm.p >= 128 || prm.k < 2 || prm.k > 5 || ((((uintptr_t)coeffs) | ((uintptr_t)words)) & 15u))
+    return 0;
+  const size_t smem = 2 * 4096 * (prm.k + 4) + 64;
+  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 4);
+#define FP_PACK_K(KK)                                                                                          \
+  case KK:                                                                                                     \
+    cudaFuncSetAttribute(k_pack_small<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
+    FP_LAUNCH(ctx, "k_pack_small", st, (k_pack_small<KK><<<grid, 256, smem, st>>>(coeffs, words, ntiles, prm.b, \
+                                                                                    prm.p, ctx->d_err)));       \
+    break;
+  switch (prm.k) {
+    FP_PACK_K(2)
+    FP_PACK_K(3)
+    FP_PACK_K(4)
+    FP_PACK_K(5)
+  }
+#undef FP_PACK_K
+  return ntiles * 4096;
+}
+
+// Full tiles of 4096 words through k_unpack_small (32-bit words, ndig in {3, 5, 7}, a lane-table
+// correction mode, aligned); returns the number of words done.
+static uint64_t unpack_small(fp_ctx ctx, const RedqParams& P, const uint32_t* words, uint8_t* coeffs,
+                             uint64_t count, cudaStream_t st) {
+  const uint64_t ntiles = count / 4096;
+  const uint32_t nd = P.ndig;
+  if (ntiles == 0 || (nd != 3 && nd != 5 && nd != 7) ||
+      (P.mode != CORR_NONE && P.mode != CORR_SHFL3 && P.mode != CORR_SHFL2) ||
+      ((((uintptr_t)coeffs) | ((uintptr_t)words)) & 15u))
+    return 0;
+  const size_t smem = 2 * 4096 * (4 + nd) + 64;
+  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 4);
+#define FP_UNPACK_K(ND, MODE)                                                                                    \
+  if (nd == ND && P.mode == MODE) {                                                                              \
+    cudaFuncSetAttribute(k_unpack_small<ND, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+    FP_LAUNCH(ctx, "k_unpack_small", st,                                                                         \
+              (k_unpack_small<ND, MODE><<<grid, 256, smem, st>>>(words, coeffs, ntiles, P, ctx->d_err)));        \
+  }
+  FP_UNPACK_K(3, CORR_NONE) FP_UNPACK_K(3, CORR_SHFL3) FP_UNPACK_K(3, CORR_SHFL2)
+  FP_UNPACK_K(5, CORR_NONE) FP_UNPACK_K(5, CORR_SHFL3) FP_UNPACK_K(5, CORR_SHFL2)
+  FP_UNPACK_K(7, CORR_NONE) FP_UNPACK_K(7, CORR_SHFL3) FP_UNPACK_K(7, CORR_SHFL2)
+#undef FP_UNPACK_K
+  return ntiles * 4096;
+}
+
 template <typename W>
 static fp_status pack_t(fp_ctx ctx, const fp_dqt_params& prm, const uint8_t* coeffs, void* words,
                         size_t count, cudaStream_t st) {
+  if (std::is_same<W, uint32_t>::value) {
+    const uint64_t done = pack_small(ctx, prm, coeffs, (uint32_t*)words, count, st);
+    FP_CUDA(cudaGetLastError());
+    coeffs += done * prm.k;
+    words = (W*)words + done;
+    count -= done;
+    if (count == 0) return FP_OK;
+  }
   size_t smem = TILE * prm.k;
   int grid = grid_for(ctx, (count + TILE - 1) / TILE, 8);
   FP_LAUNCH(ctx, "k_pack", st, k_pack<W><<<grid, TILE, smem, st>>>(coeffs, (W*)words, count, prm.k, prm.b, prm.p, ctx->d_err));
@@ -456,6 +599,14 @@ template <typename W>
 static fp_status unpack_t(fp_ctx ctx, const fp_dqt_params& prm, const void* words, uint8_t* coeffs,
                           size_t count, cudaStream_t st) {
   RedqParams P = make_redq(prm.p, prm.b, prm.ndig);
+  if (std::is_same<W, uint32_t>::value) {
+    const uint64_t done = unpack_small(ctx, P, (const uint32_t*)words, coeffs, count, st);
+    FP_CUDA(cudaGetLastError());
+    words = (const W*)words + done;
+    coeffs += done * prm.ndig;
+    count -= done;
+    if (count == 0) return FP_OK;
+  }
   size_t smem = TILE * prm.ndig;
   int grid = grid_for(ctx, (count + TILE - 1) / TILE, 8);
   FP_LAUNCH(ctx, "k_unpack", st, k_unpack<W><<<grid, TILE, smem, st>>>((const W*)words, coeffs, count, P));

@@ -298,7 +298,10 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
             reinterpret_cast<uint4*>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
             reinterpret_cast<uint4*>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
           } else {
-            for (int j = 0; j < 32 && c0 + j < n; ++j) dst[j] = (uint8_t)(packed[j >> 2] >> (8 * (j & 3)));
+            // unrolled with a predicate: a runtime index into packed[] would put it in memory
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (c0 + j < n) dst[j] = (uint8_t)(packed[j >> 2] >> (8 * (j & 3)));
           }
         }
       }

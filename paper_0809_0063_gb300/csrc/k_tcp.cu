@@ -113,26 +113,36 @@ __device__ __forceinline__ uint32_t redq2_pair_table(uint32_t p, uint32_t om) {
 
 // The end of a packed tile for one thread: its NW words R (= D0 + 2^16 D1 + conversion
 // constants, cancelled by `fix`, which also offsets both digits by k >= |digit|) reduced by
-// REDQ_2, 2 NW residues stored from dst.  A rolled loop (unrolled it is thousands of
-// instructions and crowds the MMA and TMA warps' loops out of the instruction cache): each
-// pass reduces R[0..15] and moves R down by 16.
-template <uint32_t PP, int NW>
+// REDQ_2, 2 NW residues stored from dst.  Processed in passes of BW words, each reducing
+// R[0..BW-1] and moving R down by BW.  With the divisor, the table and the loop bounds all
+// fixed at compile time one unrolled pass over all NW words measured fastest (a rolled
+// version with run-time parameters was 1.8x slower: parameters reloaded after every store and
+// branches on the correction mode in the inner loop).
+static constexpr int P_REDQ_BW = 128;
+template <uint32_t PP, int NW, int BW = P_REDQ_BW>
 __device__ __forceinline__ void final_redq(uint32_t (&R)[NW], uint32_t fix, uint32_t table, uint8_t* dst, int c0,
                                            int n, bool in, bool vec) {
 #pragma unroll 1
-  for (int blk = 0; blk < NW / 16; ++blk) {    // 16 words -> 32 residues -> two 16-byte stores
-    uint32_t o[8];
+  for (int blk = 0; blk < NW / BW; ++blk) {
 #pragma unroll
-    for (int j = 0; j < 16; j += 2)
-      o[j >> 1] = redq2_pair<PP>(R[j] + fix, table) | (redq2_pair<PP>(R[j + 1] + fix, table) << 16);
-    if (vec) {
-      reinterpret_cast<uint4*>(dst + 32 * blk)[0] = make_uint4(o[0], o[1], o[2], o[3]);
-      reinterpret_cast<uint4*>(dst + 32 * blk)[1] = make_uint4(o[4], o[5], o[6], o[7]);
-    } else if (in) {
-      for (int j = 0; j < 32 && c0 + 32 * blk + j < n; ++j) dst[32 * blk + j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
+    for (int h = 0; h < BW / 16; ++h) {        // 16 words -> 32 residues -> two 16-byte stores
+      uint32_t o[8];
+#pragma unroll
+      for (int j = 0; j < 16; j += 2)
+        o[j >> 1] = redq2_pair<PP>(R[h * 16 + j] + fix, table) | (redq2_pair<PP>(R[h * 16 + j + 1] + fix, table) << 16);
+      uint8_t* d = dst + 2 * (blk * BW + h * 16);
+      const int c = c0 + 2 * (blk * BW + h * 16);
+      if (vec) {
+        reinterpret_cast<uint4*>(d)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        reinterpret_cast<uint4*>(d)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+      } else if (in) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)   // unrolled: a runtime index into o[] would put it in memory
+          if (c + j < n) d[j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
+      }
     }
 #pragma unroll
-    for (int j = 0; j < NW - 16; ++j) R[j] = R[j + 16];
+    for (int j = 0; j < NW - BW; ++j) R[j] = R[j + BW];
   }
 }
 
@@ -287,7 +297,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
             reinterpret_cast<uint4*>(dst)[0] = make_uint4(o[0], o[1], o[2], o[3]);
             reinterpret_cast<uint4*>(dst)[1] = make_uint4(o[4], o[5], o[6], o[7]);
           } else {
-            for (int j = 0; j < 32 && c0 + j < pr.n; ++j) dst[j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
+#pragma unroll
+            for (int j = 0; j < 32; ++j)   // unrolled: a runtime index into o[] would put it in memory
+              if (c0 + j < pr.n) dst[j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
           }
         }
       }

@@ -179,3 +179,48 @@ def test_polymul_word_granular_range_check(env, pos):
     with pytest.raises(fp.FpError) as ei:
         fp.fp_ctx_status(ctx)
     assert ei.value.status == fp.FP_EINVAL
+
+
+@pytest.mark.parametrize("p,k", [(2, 5), (3, 3), (5, 4), (7, 2), (3, 2), (13, 2)])
+def test_pack_u32_word_granular(env, p, k):
+    """32-bit DQT pack through the word-granular kernel (full tiles of 4096 words) and the
+    per-word kernel (the ragged tail); a residue equal to p in a full tile is caught."""
+    fp, torch, dev, ctx = env
+    b = max(1, (p - 1).bit_length())
+    count = 2 * 4096 + 123
+    prm = fp.fp_dqt_params(p=p, k=k, b=b, ndig=1, word=3, reserved=0, n_accum=1)
+    c = workloads.uniform_mod(k * 1000 + p, p, (count, k))
+    c[0] = p - 1
+    words = torch.empty(count, dtype=torch.int32, device=dev)
+    C = to_dev(torch, dev, c)
+    fp.fp_dqt_pack(ctx, prm, C, words, count)
+    fp.fp_ctx_status(ctx)
+    got = words.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got.astype(np.int64), np.array([int(x) for x in odqt.dqt(c, 1 << b)], np.int64))
+    C[5000, k - 1] = p
+    fp.fp_dqt_pack(ctx, prm, C, words, count)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_ctx_status(ctx)
+    assert ei.value.status == fp.FP_EINVAL
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 7])
+@pytest.mark.parametrize("ndig", [3, 5, 7])
+def test_unpack_u32_word_granular(env, p, ndig):
+    """32-bit REDQ unpack through the word-granular kernel (ndig in {3, 5, 7}; p = 2 no
+    correction, 3 two residues per lookup, 5 one, 7 the shared-table fallback) and the tail."""
+    fp, torch, dev, ctx = env
+    b = 32 // ndig
+    count = 2 * 4096 + 99
+    g = np.random.default_rng(p * 31 + ndig)
+    lo = g.integers(0, 1 << b, size=(count, ndig - 1))
+    top = g.integers(0, ((1 << 32) - 1) >> (b * (ndig - 1)), size=count)
+    r = [int(odqt.dqt(list(lo[i]) + [int(top[i])], 1 << b)) for i in range(count)]
+    words = torch.tensor(np.array(r, dtype=np.uint64).astype(np.uint32).view(np.int32), device=dev)
+    out = torch.empty((count, ndig), dtype=torch.uint8, device=dev)
+    prm = fp.fp_dqt_params(p=p, k=1, b=b, ndig=ndig, word=3, reserved=0, n_accum=1)
+    fp.fp_dqt_unpack_redq(ctx, prm, words, out, count)
+    fp.fp_ctx_status(ctx)
+    got = out.cpu().numpy()
+    for i in list(range(0, count, 7)) + list(range(count - 110, count)):
+        assert list(got[i]) == odqt.dqt_inverse(r[i], 1 << b, ndig, p), (p, b, ndig, i)

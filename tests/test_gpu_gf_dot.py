@@ -125,3 +125,28 @@ def test_gf_bad_index_in_full_tiles(env, p, k, pos):
         assert ei.value.status == fp.FP_EINVAL
     finally:
         fp.fp_gf_destroy(gf)
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 7, 31, 251])
+@pytest.mark.parametrize("algo", ["AUTO", "DQT_U64"])
+def test_dot_vector_path_all_max_and_range(env, p, algo):
+    """Aligned arrays take the 16-byte vector middle product: all entries p-1 (every digit at
+    its bound, accumulated F blocks at a time) with a ragged tail of 7 entries; then one entry
+    equal to p inside a vector raises the range error."""
+    fp, torch, dev, ctx = env
+    n = 16 * 5003 + 7
+    u = torch.full((n,), p - 1, dtype=torch.uint8, device=dev)
+    out = torch.zeros((1,), dtype=torch.int32, device=dev)
+    fp.fp_dot(ctx, p, u, u, n, out, getattr(fp, "FP_ALGO_" + algo))
+    fp.fp_ctx_status(ctx)
+    assert int(out.item()) == (n * (p - 1) ** 2) % p
+    a, b = workloads.dot_inputs(p, p, n)
+    A, B = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+    fp.fp_dot(ctx, p, A, B, n, out, getattr(fp, "FP_ALGO_" + algo))
+    fp.fp_ctx_status(ctx)
+    assert int(out.item()) == field.dot_mod(a, b, p)
+    u[12345] = p
+    fp.fp_dot(ctx, p, u, u, n, out, getattr(fp, "FP_ALGO_" + algo))
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_ctx_status(ctx)
+    assert ei.value.status == fp.FP_EINVAL
