@@ -533,6 +533,25 @@ def run_gf(args, ws, rank, local):
                                       len(fields)),
             "peak_source": f"HBM copy ({peak_src})", "launches": nk, "avg_launch_ms": kper,
             "note": "achieved = average index bytes per field launch / average launch time"}
+    # the kernel is instruction-issue bound: its roof is the issue rate (152 SMs x 4 schedulers x
+    # 1 warp instruction per clock x 32 lanes x 2.07 GHz), with the per-product instruction counts
+    # of the committed ncu capture (null once the kernel's source changed since)
+    issue_roof = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tg = json.load(f).get("k_gf_mul_fixed", {})
+        if tg.get("source_hash") == kernel_source_hash("k_gf_mul_fixed") and "thread_instr_per_product" in tg:
+            peak_i = 152 * 4 * 32 * 2.07e9
+            per = {}
+            for fk, v in per_field.items():
+                ins = tg["thread_instr_per_product"].get(fk)
+                if ins:
+                    ach = ins * count / (v["ms"] / 1e3)
+                    per[fk] = {"thread_instr_per_s": ach, "frac": ach / peak_i}
+            issue_roof = {"bound": "issue", "peak_thread_instr_per_s": peak_i, "per_field": per,
+                          "source": tg.get("instr_source")}
+    except (OSError, ValueError):
+        pass
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": ws * macs / (t_ms / 1e3), "unit": "F_p MAC/s", "n_gpus": ws,
@@ -544,7 +563,7 @@ def run_gf(args, ws, rank, local):
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": ws * macs / (te / 1e3), "unit": "F_p MAC/s", "h2d_bytes_per_step": 2 * nbytes // 3,
                     "d2h_bytes_per_step": nbytes // 3},
-            "gpu_launches": launches, "clocks": clk.summary(),
+            "gpu_launches": launches, "clocks": clk.summary(), "issue_roof": issue_roof,
         }))
     fp.fp_ctx_destroy(ctx)
 
