@@ -262,7 +262,7 @@ __device__ void run_tile(const BInst& I, int tm, int tn, uint8_t* smem, uint32_t
       }
 }
 
-__global__ void __launch_bounds__(BT_THREADS) k_batch(const BInst* __restrict__ insts, const BItem* __restrict__ items,
+__global__ void __launch_bounds__(BT_THREADS, 4) k_batch(const BInst* __restrict__ insts, const BItem* __restrict__ items,
                                                       uint32_t nitems, uint32_t* counter, uint32_t* err) {
   __shared__ __align__(128) uint8_t smem[4 * 4096];
   __shared__ uint32_t s_item;
