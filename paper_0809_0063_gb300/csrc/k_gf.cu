@@ -8,7 +8,10 @@
 //   6. one field addition.
 // L and H entries hold the coefficient vector "spread" in 4-bit fields (p <= 7) or 8-bit fields,
 // so the field addition is one integer add and a per-field conditional subtraction of p.
+// These generic kernels serve every field; GF(2^8), GF(3^5) and GF(7^4) also have word-level
+// kernels (k_gf_mul_fixed, below) with the same steps on 32-bit words.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "fpdqt_internal.cuh"
@@ -22,6 +25,8 @@ struct fp_gf_s {
   uint64_t* d_word = nullptr;                    // [p^k]
   uint32_t* d_L = nullptr;                       // [2^{c k}]
   uint32_t* d_H = nullptr;                       // [2^{c k}]
+  uint4* d_img = nullptr;                        // word-level tables (GF(2^8), GF(3^5), GF(7^4))
+  uint32_t img_bytes = 0;
   fpd::RedqParams P{};
   int device = 0;
 };
@@ -171,96 +176,304 @@ __global__ void __launch_bounds__(256) k_gf_mul_bulk(const E* __restrict__ a, co
   if (op.bad) flag_error(err, ERR_RANGE);
 }
 
-// ------------------------------------------------------------------ compile-time fields
+// ------------------------------------------------------------------ word-level fields
+//
+// GF(2^8), GF(3^5) and GF(7^4) take the steps of Algorithm FGDP (n = 1) with every constant
+// fixed at compile time and the data kept in 32-bit registers:
+//  * the DQT word of an element (q = 2^b, k digits) fits 32 bits, so the product r is one
+//    32 x 32 -> 64-bit multiply;
+//  * REDQ compression of r runs on two 32-bit pieces split at digit m.  Since
+//    u_i = floor(r / q^i) mod p (Algorithm 2 computes exactly these), the high piece
+//    r_hi = floor(r / q^m) gives u_m..u_{2k-2}, and r' = u_m q^m + (r mod q^m) has the same
+//    floor(r' / q^i) mod p as r for every i < m (r enters through r_hi mod p = u_m only).
+//    Each piece takes one 32-bit division by p: a multiply-high by ceil(2^32 / p), exact
+//    below 2^31 (p = 3) and 2^32 / 3 (p = 7), which the pieces stay under;
+//  * u_i = (r_i - p s_i) mod q for the base-q digits r_i, s_i of a piece x and s = floor(x/p)
+//    (the low b bits of floor(x/q^i) - p floor(s/q^i)), formed for all digits at once: even and
+//    odd digits in separate lanes of 2b bits, p q added to every lane so that none borrows;
+//  * the split of Theorem fgdp is taken at digit m (the proof holds for any split point): the
+//    low table, indexed by u_0..u_m, gives sum_{i<m} mu_i X^i; the high table, indexed by
+//    u_m..u_{2k-2}, gives sum_{i>=m} mu_i X^i reduced by the modulus.  The u's are packed into
+//    c-bit index fields by merging the odd lanes into the even ones and one multiply that moves
+//    every field to the top bits of the word (its cross products fall on distinct bits below the
+//    index, so nothing carries into it, or above bit 31);
+//  * the field addition of the two parts, in the index representation, is table-driven:
+//    GF(2^8) XOR; GF(3^5) one lookup of the spread coefficient sums; GF(7^4) the sum of the two
+//    parts' indices minus 7^(i+1) for each coefficient i whose sum reached 7.
+// The tables live in one shared-memory image per field (gfw_image), copied whole into every
+// block.  Word tables indexed by a byte are replicated 32 times (entry x of lane l at
+// 32 x + l) so that the two random word lookups of a warp never meet a bank conflict.
 
-// The parameters fp_gf_create chooses for GF(P^K), as compile-time constants (same rules).
-template <uint32_t P, uint32_t K>
-struct GfConst {
-  static constexpr uint32_t order() { uint32_t o = 1; for (uint32_t i = 0; i < K; ++i) o *= P; return o; }
-  static constexpr uint32_t cbits() { uint32_t c = 0; while ((1u << c) < P) ++c; return c; }
-  static constexpr uint32_t fbits() {
-    uint32_t f = 1;
-    while ((1u << (f - 1)) < P || (1u << f) <= 2 * P - 2 + (1u << (f - 1)) - P) ++f;
-    return f;
-  }
-  static constexpr uint32_t qbits() {
-    uint32_t b = 1;
-    while ((1ull << b) <= (uint64_t)K * (P - 1) * (P - 1) || (1ull << b) < P) ++b;
-    return b;
-  }
-  static constexpr uint32_t ORDER = order(), CB = cbits(), FB = fbits(), B = qbits();
-  static constexpr uint32_t ONES = [] { uint32_t o = 0; for (uint32_t i = 0; i < K; ++i) o |= 1u << (i * FB); return o; }();
+template <uint32_t P, uint32_t K> struct Gfw;
+// GF(2^8): q = 2^4, r < 2^60 (15 digits <= 8).  p divides q, so u_i = floor(r / q^i) mod 2 is bit
+// 4i of r (the division by p is a shift, and mu_i = u_i).  Split at m = 8: the low part is
+// u_0..u_7 itself (degree <= 7 needs no reduction); the high part is one lookup.
+template <> struct Gfw<2, 8> {
+  static constexpr uint32_t W = 0, H = 32768, BYTES = H + 128;
+};
+// GF(3^5): q = 2^5, r < 2^45 (9 digits <= 20), m = 5; c = 2 index bits per residue.
+template <> struct Gfw<3, 5> {
+  static constexpr uint32_t W = 0, L = 32768, H = L + 8192, T = H + 512, BYTES = T + 32768;
+};
+// GF(7^4): q = 2^8, r < 2^54 (7 digits <= 144), m = 3 = k - 1; c = 3.
+template <> struct Gfw<7, 4> {
+  static constexpr uint32_t W = 0, L = 16384, H = 32768, CT = 49152, BYTES = CT + 2048;
 };
 
-// One product by Algorithm FGDP (n = 1) with every shift, mask and loop bound fixed at
-// compile time: the same steps as gf_mul_one.
-template <uint32_t P, uint32_t K>
-__device__ __forceinline__ uint32_t gf_mul_fixed(uint32_t xa, uint32_t xb, const uint64_t* sw, const uint32_t* sL,
-                                                 const uint32_t* sH, uint32_t& bad) {
-  using F = GfConst<P, K>;
-  bad |= (xa >= F::ORDER) | (xb >= F::ORDER);
-  xa = xa < F::ORDER ? xa : 0u;
-  xb = xb < F::ORDER ? xb : 0u;
-  const uint64_t r = sw[xa] * sw[xb];             // table DQT of both operands, one word product
-  const uint64_t s = r / P;                       // REDQ compression quotient
-  uint32_t il = 0, ih = 0;
-#pragma unroll
-  for (uint32_t j = 0; j < 2 * K - 1; ++j) {
-    const uint32_t uj = ((uint32_t)(r >> (j * F::B)) - P * (uint32_t)(s >> (j * F::B))) & ((1u << F::B) - 1u);
-    if (j < K) il |= uj << (j * F::CB);
-    if (j + 1 >= K) ih |= uj << ((j + 1 - K) * F::CB);
-  }
-  constexpr uint32_t HB = F::FB - 1;
-  uint32_t x = sL[il] + sH[ih];                    // two lookups, one field addition
-  const uint32_t ge = ((x + ((1u << HB) - P) * F::ONES) >> HB) & F::ONES;
-  x -= P * ge;
-  uint32_t idx = 0;
-#pragma unroll
-  for (int j = (int)K - 1; j >= 0; --j) idx = idx * P + ((x >> (j * F::FB)) & ((1u << F::FB) - 1u));
-  return idx;
+// bits 0, 4, ..., 28 of w -> bits 0..7: bits 8j and 8j + 4 paired at 8j, then a multiply by
+// 2^24 + 2^18 + 2^12 + 2^6 moves pair j to bit 24 + 2j (cross products: distinct bits below 24,
+// or 32 and above).
+__device__ __forceinline__ uint32_t gfw_gather4(uint32_t w) {
+  const uint32_t x = (w & 0x01010101u) | ((w >> 3) & 0x02020202u);
+  return (x * 0x01041040u) >> 24;
 }
 
-// Four products per item, so that every shared-memory access of the stream is a whole
-// 32-bit word (uint8 elements) or a pair of words (uint16).
-template <uint32_t P, uint32_t K, typename E>
-struct GfFixedOp {
-  static constexpr uint32_t IPT = 4;
-  static constexpr uint32_t UNROLL = 2;
-  const uint64_t* sw;
-  const uint32_t *sL, *sH;
+// u_i for the six 5-bit digits of x < 2^30, s = floor(x / 3) (GF(3^5) pieces): lanes of 10 bits
+// holding digits 0, 2, 4 (even) and 1, 3, 5 (odd); 96 = p q per lane keeps each lane in [3, 127].
+// Returned as pairs u_{2j} + 4 u_{2j+1} (each u < 3) at bit 10 j: a lane holds u + 32 j' with the
+// multiple of q in its bits 5-6, so the odd lanes shifted down by 3 add onto the even ones without
+// touching a u and one mask keeps the pairs.
+__device__ __forceinline__ uint32_t gfw_pairs_3(uint32_t x, uint32_t s) {
+  constexpr uint32_t ME = 0x01F07C1Fu, CE = 0x06018060u, MO = ME << 5, CO = CE << 5;
+  const uint32_t te = ((x & ME) | CE) - 3u * (s & ME);
+  const uint32_t to = ((x & MO) | CO) - 3u * (s & MO);
+  return (te + (to >> 3)) & 0x00F03C0Fu;
+}
+
+// u_i for the four byte digits of x, s = floor(x / 7) (GF(7^4) pieces): lanes of 16 bits, 1792 =
+// p q per lane keeps each lane in [7, 2047].  Returned as pairs u_{2j} + 8 u_{2j+1} at bit 16 j
+// (the multiples of q sit in bits 8-13 of the lane sum, below the next lane, and are masked off).
+__device__ __forceinline__ uint32_t gfw_pairs_7(uint32_t x, uint32_t s) {
+  constexpr uint32_t ME = 0x00FF00FFu, CE = 0x07000700u;
+  const uint32_t te = ((x & ME) | CE) - 7u * (s & ME);
+  const uint32_t to = (((x >> 8) & ME) | CE) - 7u * ((s >> 8) & ME);
+  return (te + (to << 3)) & 0x003F003Fu;
+}
+
+// One product in GF(2^8): wl = replicated word table + lane, H = high-part table.
+__device__ __forceinline__ uint32_t gfw_mul_2_8(uint32_t a, uint32_t b, const uint32_t* wl, const uint8_t* H) {
+  const uint64_t r = (uint64_t)wl[a * 32] * wl[b * 32];
+  return gfw_gather4((uint32_t)r) ^ H[gfw_gather4((uint32_t)(r >> 32))];
+}
+
+// One product in GF(3^5).
+__device__ __forceinline__ uint32_t gfw_mul_3_5(uint32_t a, uint32_t b, const uint32_t* wl, const uint16_t* L,
+                                                const uint16_t* H, const uint8_t* T) {
+  const uint64_t r = (uint64_t)wl[a * 32] * wl[b * 32];
+  const uint32_t lo = (uint32_t)r;
+  const uint32_t rh = __funnelshift_r(lo, (uint32_t)(r >> 32), 25);    // digits 5..8
+  const uint32_t sh = __umulhi(rh, 0x55555556u);                         // floor(rh / 3)
+  const uint32_t rl = (lo & 0x01FFFFFFu) + ((rh - 3u * sh) << 25);       // u_5 q^5 + r mod q^5
+  const uint32_t sl = __umulhi(rl, 0x55555556u);
+  // pairs (u0,u1) (u2,u3) (u4,u5) at bits 0, 10, 20 -> bits 28, 24, 20; (u5,u6) (u7,u8) at
+  // bits 0, 10 -> bits 24, 28
+  const uint32_t il = (gfw_pairs_3(rl, sl) * 0x10004001u) >> 20;   // (u4+4u5) + 16 (u2+4u3) + 256 (u0+4u1)
+  const uint32_t ih = (gfw_pairs_3(rh, sh) * 0x01040000u) >> 24;   // sum_{t<=3} u_{5+t} 4^t
+  return T[L[il] + H[ih]];
+}
+
+// One product in GF(7^4): W word table, L/H entries = spread (4-bit fields) | index << 16,
+// ctl = replicated carry table + lane.
+__device__ __forceinline__ uint32_t gfw_mul_7_4(uint32_t a, uint32_t b, const uint32_t* W, const uint32_t* L,
+                                                const uint32_t* H, const uint32_t* ctl) {
+  const uint64_t r = (uint64_t)W[a] * W[b];
+  const uint32_t lo = (uint32_t)r;
+  const uint32_t rh = __funnelshift_r(lo, (uint32_t)(r >> 32), 24);    // digits 3..6
+  const uint32_t sh = __umulhi(rh, 0x24924925u);                         // floor(rh / 7)
+  const uint32_t rl = (lo & 0x00FFFFFFu) + ((rh - 7u * sh) << 24);       // u_3 q^3 + r mod q^3
+  const uint32_t sl = __umulhi(rl, 0x24924925u);
+  // pairs at bits 0 and 16 -> bits 20 and 26
+  const uint32_t il = (gfw_pairs_7(rl, sl) * 0x00100400u) >> 20;   // sum_{t<=3} u_t 8^t
+  const uint32_t ih = (gfw_pairs_7(rh, sh) * 0x00100400u) >> 20;   // sum_{t<=3} u_{3+t} 8^t
+  const uint32_t x = L[il] + H[ih];
+  // bit 4i + 3 of x + 0x1111: coefficient sum i >= 7; the multiply moves those four bits to bits
+  // 28..31 (cross products on distinct bits below 28, or above 31)
+  const uint32_t g = (((x + 0x1111u) & 0x8888u) * 0x02490000u) >> 28;
+  return (x >> 16) - ctl[g * 32];
+}
+
+// The products of one 32-bit word of indices (four uint8 or two uint16).  Index checks:
+// GF(2^8) has none to make; GF(3^5) flags a byte >= 243 (its lookups stay inside the 256-entry
+// table); GF(7^4) flags a uint16 >= 2401 and looks up its low 12 bits.
+template <uint32_t P, uint32_t K>
+struct Gfw32 {
+  const uint8_t* tab;
+  uint32_t lane;
   uint32_t bad;
-  __device__ __forceinline__ void item(const uint8_t* a, const uint8_t* b, uint8_t* out) {
-    if (sizeof(E) == 1) {
-      const uint32_t wa = *reinterpret_cast<const uint32_t*>(a), wb = *reinterpret_cast<const uint32_t*>(b);
-      uint32_t wc = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        wc |= gf_mul_fixed<P, K>((wa >> (8 * j)) & 0xffu, (wb >> (8 * j)) & 0xffu, sw, sL, sH, bad) << (8 * j);
-      *reinterpret_cast<uint32_t*>(out) = wc;
+  __device__ __forceinline__ uint32_t word(uint32_t wa, uint32_t wb) {
+    using G = Gfw<P, K>;
+    if constexpr (P == 7) {
+      bad |= wa | ((wa & 0x7FFF7FFFu) + 0x769F769Fu) | wb | ((wb & 0x7FFF7FFFu) + 0x769F769Fu);
+      const uint32_t* W = reinterpret_cast<const uint32_t*>(tab + G::W);
+      const uint32_t* L = reinterpret_cast<const uint32_t*>(tab + G::L);
+      const uint32_t* H = reinterpret_cast<const uint32_t*>(tab + G::H);
+      const uint32_t* ctl = reinterpret_cast<const uint32_t*>(tab + G::CT) + lane;
+      const uint32_t c0 = gfw_mul_7_4(wa & 0xFFFu, wb & 0xFFFu, W, L, H, ctl);
+      const uint32_t c1 = gfw_mul_7_4((wa >> 16) & 0xFFFu, (wb >> 16) & 0xFFFu, W, L, H, ctl);
+      return c0 | (c1 << 16);
     } else {
-      const uint2 wa = *reinterpret_cast<const uint2*>(a), wb = *reinterpret_cast<const uint2*>(b);
-      const uint32_t c0 = gf_mul_fixed<P, K>(wa.x & 0xffffu, wb.x & 0xffffu, sw, sL, sH, bad);
-      const uint32_t c1 = gf_mul_fixed<P, K>(wa.x >> 16, wb.x >> 16, sw, sL, sH, bad);
-      const uint32_t c2 = gf_mul_fixed<P, K>(wa.y & 0xffffu, wb.y & 0xffffu, sw, sL, sH, bad);
-      const uint32_t c3 = gf_mul_fixed<P, K>(wa.y >> 16, wb.y >> 16, sw, sL, sH, bad);
-      *reinterpret_cast<uint2*>(out) = make_uint2(c0 | (c1 << 16), c2 | (c3 << 16));
+      const uint32_t* wl = reinterpret_cast<const uint32_t*>(tab + G::W) + lane;
+      uint32_t wc = 0;
+      if constexpr (P == 3) {
+        // a byte >= 243 has its top bit set and its low 7 bits + 13 >= 128
+        bad |= (wa & ((wa & 0x7F7F7F7Fu) + 0x0D0D0D0Du)) | (wb & ((wb & 0x7F7F7F7Fu) + 0x0D0D0D0Du));
+        const uint16_t* L = reinterpret_cast<const uint16_t*>(tab + G::L);
+        const uint16_t* H = reinterpret_cast<const uint16_t*>(tab + G::H);
+        const uint8_t* T = tab + G::T;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          wc |= gfw_mul_3_5((wa >> (8 * j)) & 0xFFu, (wb >> (8 * j)) & 0xFFu, wl, L, H, T) << (8 * j);
+      } else {
+        const uint8_t* H = tab + G::H;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          wc |= gfw_mul_2_8((wa >> (8 * j)) & 0xFFu, (wb >> (8 * j)) & 0xFFu, wl, H) << (8 * j);
+      }
+      return wc;
     }
+  }
+  __device__ __forceinline__ bool any_bad() const {
+    return (bad & (P == 7 ? 0x80008000u : P == 3 ? 0x80808080u : 0u)) != 0;
   }
 };
 
-template <uint32_t P, uint32_t K, typename E>
-__global__ void __launch_bounds__(256) k_gf_mul_fixed(const E* __restrict__ a, const E* __restrict__ b,
-                                                      E* __restrict__ c, uint64_t ntiles, uint32_t table_bytes,
-                                                      GfDev G, uint32_t* err) {
+// One 16-byte vector of each operand per thread and trip (coalesced 512 bytes per warp), no
+// staging: the arithmetic per byte is high enough that a few loads in flight per warp keep up,
+// and the shared memory goes to the tables, whose one copy serves 32 warps.
+static constexpr int GFW_THREADS = 1024;
+template <uint32_t P, uint32_t K>
+__global__ void __launch_bounds__(GFW_THREADS, 2) k_gf_mul_fixed(const uint4* __restrict__ a, const uint4* __restrict__ b,
+                                                                 uint4* __restrict__ c, uint64_t nvec,
+                                                                 const uint4* __restrict__ image, uint32_t* err) {
   extern __shared__ __align__(128) uint8_t sm[];
-  uint64_t* sw;
-  uint32_t *sL, *sH;
-  gf_load_tables(G, sm, sw, sL, sH);
-  GfFixedOp<P, K, E> op{sw, sL, sH, 0};
-  stream_tiles(op, reinterpret_cast<const uint8_t*>(a), reinterpret_cast<const uint8_t*>(b),
-               reinterpret_cast<uint8_t*>(c), ntiles, 4 * sizeof(E), 4 * sizeof(E), 4 * sizeof(E), sm + table_bytes,
-               err);
-  if (op.bad) flag_error(err, ERR_RANGE);
+  constexpr uint32_t IB = Gfw<P, K>::BYTES;
+  for (uint32_t i = threadIdx.x; i < IB / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = image[i];
+  __syncthreads();
+  Gfw32<P, K> op{sm, threadIdx.x & 31u, 0};
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if constexpr (P == 2) {
+    // the lightest field: two vectors of each operand in flight per thread
+    for (; i + stride < nvec; i += 2 * stride) {
+      const uint4 va = a[i], vb = b[i], wa = a[i + stride], wb = b[i + stride];
+      c[i] = make_uint4(op.word(va.x, vb.x), op.word(va.y, vb.y), op.word(va.z, vb.z), op.word(va.w, vb.w));
+      c[i + stride] = make_uint4(op.word(wa.x, wb.x), op.word(wa.y, wb.y), op.word(wa.z, wb.z), op.word(wa.w, wb.w));
+    }
+  }
+  for (; i < nvec; i += stride) {
+    const uint4 va = a[i], vb = b[i];
+    c[i] = make_uint4(op.word(va.x, vb.x), op.word(va.y, vb.y), op.word(va.z, vb.z), op.word(va.w, vb.w));
+  }
+  if (op.any_bad()) flag_error(err, ERR_RANGE);
+}
+
+// Host: the shared-memory image of the word-level tables of the field, empty when the field has
+// no word-level kernel.  `word` holds the DQT words, `index`/`rem` the representation helpers.
+static std::vector<uint8_t> gfw_image(uint32_t p, uint32_t k, uint32_t b, const std::vector<uint32_t>& modulus) {
+  std::vector<uint8_t> img;
+  auto digits = [&](uint64_t x) {
+    std::vector<uint32_t> c(k);
+    for (uint32_t i = 0; i < k; ++i) { c[i] = (uint32_t)(x % p); x /= p; }
+    return c;
+  };
+  auto word = [&](uint64_t x) {
+    const std::vector<uint32_t> c = digits(x);
+    uint32_t w = 0;
+    for (int i = (int)k - 1; i >= 0; --i) w = (w << b) | c[i];
+    return w;
+  };
+  auto index = [&](const std::vector<uint32_t>& c) {
+    uint32_t x = 0;
+    for (int i = (int)c.size() - 1; i >= 0; --i) x = x * p + c[i];
+    return x;
+  };
+  auto put32 = [&](uint32_t off, uint32_t v) { std::memcpy(img.data() + off, &v, 4); };
+  auto put16 = [&](uint32_t off, uint16_t v) { std::memcpy(img.data() + off, &v, 2); };
+  const uint32_t cq = (p - ((1u << b) % p)) % p;   // -q mod p
+  uint32_t order = 1;
+  for (uint32_t i = 0; i < k; ++i) order *= p;
+  if (p == 2 && k == 8 && b == 4) {
+    using G = Gfw<2, 8>;
+    img.assign(G::BYTES, 0);
+    for (uint32_t x = 0; x < 256; ++x)
+      for (uint32_t l = 0; l < 32; ++l) put32(G::W + 4 * (32 * x + l), word(x));
+    for (uint32_t g = 0; g < 128; ++g) {
+      std::vector<uint32_t> ph(2 * k - 1, 0);
+      for (uint32_t t = 0; t < 7; ++t) ph[8 + t] = (g >> t) & 1u;
+      img[G::H + g] = (uint8_t)index(poly_rem(ph, modulus, p));
+    }
+  } else if (p == 3 && k == 5 && b == 5) {
+    using G = Gfw<3, 5>;
+    img.assign(G::BYTES, 0);
+    for (uint32_t x = 0; x < 256; ++x)
+      for (uint32_t l = 0; l < 32; ++l) put32(G::W + 4 * (32 * x + l), x < order ? word(x) : 0u);
+    for (uint32_t il = 0; il < 4096; ++il) {   // u_0..u_5 -> spread of sum_{i<5} mu_i X^i
+      // index layout of gfw_mul_3_5: (u4 + 4 u5) + 16 (u2 + 4 u3) + 256 (u0 + 4 u1)
+      uint32_t u[6], v = 0;
+      bool ok = true;
+      for (uint32_t j = 0; j < 3; ++j) {
+        const uint32_t pair = (il >> (4 * (2 - j))) & 15u;
+        u[2 * j] = pair & 3u;
+        u[2 * j + 1] = pair >> 2;
+        ok &= u[2 * j] < p && u[2 * j + 1] < p;
+      }
+      if (!ok) continue;
+      for (uint32_t i = 0; i < 5; ++i) v |= ((u[i] + cq * u[i + 1]) % p) << (3 * i);
+      put16(G::L + 2 * il, (uint16_t)v);
+    }
+    for (uint32_t ih = 0; ih < 256; ++ih) {    // u_5..u_8 -> spread of (sum_{i>=5} mu_i X^i mod P)
+      uint32_t u[9] = {0};
+      bool ok = true;
+      for (uint32_t t = 0; t < 4; ++t) { u[5 + t] = (ih >> (2 * t)) & 3u; ok &= u[5 + t] < p; }
+      if (!ok) continue;
+      std::vector<uint32_t> ph(2 * k - 1, 0);
+      ph[8] = u[8];
+      for (uint32_t i = 5; i < 8; ++i) ph[i] = (u[i] + cq * u[i + 1]) % p;
+      const std::vector<uint32_t> r = poly_rem(ph, modulus, p);
+      uint32_t v = 0;
+      for (uint32_t i = 0; i < k; ++i) v |= r[i] << (3 * i);
+      put16(G::H + 2 * ih, (uint16_t)v);
+    }
+    for (uint32_t x = 0; x < 32768; ++x) {     // spread coefficient sums -> index
+      uint32_t v = 0, w = 1;
+      for (uint32_t i = 0; i < k; ++i, w *= p) v += (((x >> (3 * i)) & 7u) % p) * w;
+      img[G::T + x] = (uint8_t)v;
+    }
+  } else if (p == 7 && k == 4 && b == 8) {
+    using G = Gfw<7, 4>;
+    img.assign(G::BYTES, 0);
+    for (uint32_t x = 0; x < 4096; ++x) put32(G::W + 4 * x, x < order ? word(x) : 0u);
+    for (uint32_t il = 0; il < 4096; ++il) {   // u_0..u_3 -> sum_{i<3} mu_i X^i
+      uint32_t u[4];
+      bool ok = true;
+      for (uint32_t t = 0; t < 4; ++t) { u[t] = (il >> (3 * t)) & 7u; ok &= u[t] < p; }
+      if (!ok) continue;
+      std::vector<uint32_t> mu(k, 0);
+      for (uint32_t i = 0; i < 3; ++i) mu[i] = (u[i] + cq * u[i + 1]) % p;
+      uint32_t v = 0;
+      for (uint32_t i = 0; i < k; ++i) v |= mu[i] << (4 * i);
+      put32(G::L + 4 * il, v | (index(mu) << 16));
+    }
+    for (uint32_t ih = 0; ih < 4096; ++ih) {   // u_3..u_6 -> sum_{i>=3} mu_i X^i mod P
+      uint32_t u[7] = {0};
+      bool ok = true;
+      for (uint32_t t = 0; t < 4; ++t) { u[3 + t] = (ih >> (3 * t)) & 7u; ok &= u[3 + t] < p; }
+      if (!ok) continue;
+      std::vector<uint32_t> ph(2 * k - 1, 0);
+      ph[6] = u[6];
+      for (uint32_t i = 3; i < 6; ++i) ph[i] = (u[i] + cq * u[i + 1]) % p;
+      const std::vector<uint32_t> r = poly_rem(ph, modulus, p);
+      uint32_t v = 0;
+      for (uint32_t i = 0; i < k; ++i) v |= r[i] << (4 * i);
+      put32(G::H + 4 * ih, v | (index(r) << 16));
+    }
+    for (uint32_t g = 0; g < 16; ++g) {        // 7^(i+1) for every coefficient i that wrapped
+      uint32_t v = 0, w = p;
+      for (uint32_t i = 0; i < k; ++i, w *= p) v += ((g >> i) & 1u) * w;
+      for (uint32_t l = 0; l < 32; ++l) put32(G::CT + 4 * (32 * g + l), v);
+    }
+  }
+  return img;
 }
 
 // Segmented form for the serving loop: segment s multiplies count[s] pairs at byte offsets
@@ -371,6 +584,12 @@ extern "C" fp_status fp_gf_create(fp_ctx ctx, uint32_t p, uint32_t k, fp_gf* out
   if (e == cudaSuccess) e = cudaMemcpy(g->d_word, word.data(), order * sizeof(uint64_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_L, L.data(), tsz * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_H, H.data(), tsz * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  const std::vector<uint8_t> img = gfw_image(p, k, b, g->modulus);
+  if (e == cudaSuccess && !img.empty()) {
+    g->img_bytes = (uint32_t)img.size();
+    e = cudaMalloc(&g->d_img, img.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_img, img.data(), img.size(), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     fp_gf_destroy(g);
     return cuda_fail(e, "fp_gf_create tables");
@@ -385,6 +604,7 @@ extern "C" void fp_gf_destroy(fp_gf g) {
   if (g->d_word) cudaFree(g->d_word);
   if (g->d_L) cudaFree(g->d_L);
   if (g->d_H) cudaFree(g->d_H);
+  if (g->d_img) cudaFree(g->d_img);
   delete g;
 }
 
@@ -410,28 +630,29 @@ extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const
   GfDev G{g->d_word, g->d_L, g->d_H, g->order, g->k, g->c, g->fb, 0};
   for (uint32_t i = 0; i < g->k; ++i) G.ones |= 1u << (i * g->fb);
   const bool aligned = ((((uintptr_t)a) | ((uintptr_t)b) | ((uintptr_t)c)) & 15u) == 0;
-  // fields with compile-time parameters: full tiles of 4096 pairs (4 per item) on k_gf_mul_fixed
-  {
-    const uint64_t FITEMS = 256 * 4 * 4;
-    const uint64_t fnt = aligned ? count / FITEMS : 0;
-    const size_t tb = ((smem + 127) / 128) * 128, smem_f = tb + 6 * FITEMS * g->elem_bytes + 64;
-    const int grid_f = (int)std::min<uint64_t>(fnt, (uint64_t)ctx->num_sms * 2);
+  // word-level fields: whole 16-byte vectors on k_gf_mul_fixed, the rest below
+  if (g->d_img && aligned && count * g->elem_bytes >= 16) {
+    const uint64_t nvec = count * g->elem_bytes / 16;
+    const size_t smem_f = g->img_bytes;
     bool launched = false;
-#define FP_GF_FIXED(PP, KK, E)                                                                                        \
-    if (!launched && g->p == PP && g->k == KK && g->b == GfConst<PP, KK>::B && g->c == GfConst<PP, KK>::CB &&       \
-        g->fb == GfConst<PP, KK>::FB && fnt) {                                                                         \
-      FP_CUDA(cudaFuncSetAttribute(k_gf_mul_fixed<PP, KK, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f)); \
-      FP_LAUNCH(ctx, "k_gf_mul_fixed", st, (k_gf_mul_fixed<PP, KK, E><<<grid_f, 256, smem_f, st>>>(                 \
-                    (const E*)a, (const E*)b, (E*)c, fnt, (uint32_t)tb, G, ctx->d_err)));                             \
+#define FP_GF_FIXED(PP, KK)                                                                                           \
+    if (!launched && g->p == PP && g->k == KK) {                                                                      \
+      FP_CUDA(cudaFuncSetAttribute(k_gf_mul_fixed<PP, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));  \
+      int per_sm = 0;                                                                                                  \
+      FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gf_mul_fixed<PP, KK>, GFW_THREADS, smem_f));    \
+      const uint64_t want = (nvec + GFW_THREADS - 1) / GFW_THREADS;                                                    \
+      const int grid_f = (int)std::min<uint64_t>(want, (uint64_t)ctx->num_sms * (uint64_t)std::max(per_sm, 1));    \
+      FP_LAUNCH(ctx, "k_gf_mul_fixed", st, (k_gf_mul_fixed<PP, KK><<<grid_f, GFW_THREADS, smem_f, st>>>(            \
+                    (const uint4*)a, (const uint4*)b, (uint4*)c, nvec, g->d_img, ctx->d_err)));                        \
       launched = true;                                                                                                 \
     }
-    FP_GF_FIXED(3, 5, uint8_t)
-    FP_GF_FIXED(7, 4, uint16_t)
-    FP_GF_FIXED(2, 8, uint8_t)
+    FP_GF_FIXED(3, 5)
+    FP_GF_FIXED(7, 4)
+    FP_GF_FIXED(2, 8)
 #undef FP_GF_FIXED
     if (launched) {
       FP_CUDA(cudaGetLastError());
-      const uint64_t fd = fnt * FITEMS, eb = g->elem_bytes;
+      const uint64_t fd = nvec * 16 / g->elem_bytes, eb = g->elem_bytes;
       if (fd == count) return FP_OK;
       a = (const uint8_t*)a + fd * eb;
       b = (const uint8_t*)b + fd * eb;

@@ -72,6 +72,26 @@ def test_gf_config_2_24_sampled(env, p, k):
     assert np.array_equal(got[idx].astype(np.int64), want)
 
 
+def test_gf_7_4_every_pair(env):
+    """GF(7^4): all 2401^2 products (1407 full tiles of the word-level kernel and a ragged tail),
+    checked against the oracle in slices."""
+    fp, torch, dev, ctx = env
+    p, k = 7, 4
+    order = p ** k
+    a = np.repeat(np.arange(order, dtype=np.uint16), order)
+    b = np.tile(np.arange(order, dtype=np.uint16), order)
+    gf = fp.fp_gf_create(ctx, p, k)
+    try:
+        got = gf_run(fp, torch, dev, ctx, gf, a, b)
+    finally:
+        fp.fp_gf_destroy(gf)
+    m = field.smallest_monic_irreducible(p, k)
+    step = 600 * order
+    for s in range(0, len(a), step):
+        want = field.gf_mul(a[s:s + step].astype(np.int64), b[s:s + step].astype(np.int64), p, k, m)
+        assert np.array_equal(got[s:s + step].astype(np.int64), want), s
+
+
 def test_gf_bad_index(env):
     fp, torch, dev, ctx = env
     gf = fp.fp_gf_create(ctx, 3, 5)
@@ -109,15 +129,18 @@ def test_dot_unaligned_and_all_max(env):
         assert int(out.item()) == (n * (p - 1) ** 2) % p
 
 
-@pytest.mark.parametrize("p,k,pos", [(3, 5, 5000), (7, 4, 4095), (3, 5, 3 * 4096 + 7)])
-def test_gf_bad_index_in_full_tiles(env, p, k, pos):
-    """An index >= p^k inside a full tile of the compile-time field kernel, or in the tail,
-    raises the range error; the other products are still exact."""
+@pytest.mark.parametrize("p,k,pos,bad", [(3, 5, 5000, 243), (3, 5, 6001, 255), (7, 4, 4095, 2401),
+                                         (7, 4, 4094, 4096 + 5), (7, 4, 9000, 32768), (7, 4, 9001, 65535),
+                                         (3, 5, 3 * 4096 + 7, 243)])
+def test_gf_bad_index_in_full_tiles(env, p, k, pos, bad):
+    """An index >= p^k inside a full tile of the word-level kernel (including values whose low
+    12 bits are a valid index, and values with the top bit set), or in the tail, raises the
+    range error."""
     fp, torch, dev, ctx = env
     n = 3 * 4096 + 100
     a, b = workloads.gf_inputs(17, p, k, n)
     a = a.copy()
-    a[pos] = p ** k if p ** k < 256 or a.dtype == np.uint16 else 255
+    a[pos] = bad
     gf = fp.fp_gf_create(ctx, p, k)
     try:
         with pytest.raises(fp.FpError) as ei:
