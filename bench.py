@@ -527,43 +527,40 @@ def run_gf(args, ws, rank, local):
         cpu = {"value": m_done / dt, "unit": "F_p MAC/s", "cores": 1, "kind": "oracle",
                "sample": f"2^18 pairs per field, round robin ({dt:.1f} s, numpy schoolbook + remainder, single thread)"}
     kper = kms / max(1, nk)
-    roof = {"bound": "hbm", "kernel": "k_gf_mul_fixed", "achieved": nbytes / len(fields) / (kper / 1e3) / 1e9,
-            "peak": hbm, "unit": "GB/s", "frac": nbytes / len(fields) / (kper / 1e3) / 1e9 / hbm,
-            "traffic": stored_traffic("k_gf_mul_fixed", [(f"GF({p}^{k})", count) for p, k in workloads.GF_FIELDS],
-                                      len(fields)),
-            "peak_source": f"HBM copy ({peak_src})", "launches": nk, "avg_launch_ms": kper,
-            "note": "achieved = average index bytes per field launch / average launch time"}
-    # the kernel is instruction-issue bound: its roof is the issue rate (152 SMs x 4 schedulers x
-    # 1 warp instruction per clock x 32 lanes x 2.07 GHz), with the per-product instruction counts
-    # of the committed ncu capture (null once the kernel's source changed since)
-    issue_roof = None
+    # The kernel is bound by the integer ALU pipe (shifts, masks, logic): its roof is that pipe's
+    # rate from unit counts, 152 SMs x 64 lanes x 2.07 GHz, and `achieved` the ALU-pipe operations
+    # of the committed ncu capture (per product, per field) over the live launch time.  Null when
+    # the kernel's source changed since the capture.  The HBM view stays in per_field.
+    alu_peak = 152 * 64 * 2.07e9
+    alu_ops = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tg = json.load(f).get("k_gf_mul_fixed", {})
-        if tg.get("source_hash") == kernel_source_hash("k_gf_mul_fixed") and "thread_instr_per_product" in tg:
-            peak_i = 152 * 4 * 32 * 2.07e9
-            per = {}
-            for fk, v in per_field.items():
-                ins = tg["thread_instr_per_product"].get(fk)
-                if ins:
-                    ach = ins * count / (v["ms"] / 1e3)
-                    per[fk] = {"thread_instr_per_s": ach, "frac": ach / peak_i}
-            issue_roof = {"bound": "issue", "peak_thread_instr_per_s": peak_i, "per_field": per,
-                          "source": tg.get("instr_source")}
-    except (OSError, ValueError):
-        pass
+        if tg.get("source_hash") == kernel_source_hash("k_gf_mul_fixed") and "alu_ops_per_product" in tg:
+            alu_ops = sum(tg["alu_ops_per_product"][f"GF({p}^{k})"] * count for p, k in workloads.GF_FIELDS)
+    except (OSError, ValueError, KeyError):
+        alu_ops = None
+    ach = alu_ops / len(fields) / (kper / 1e3) if alu_ops else None
+    roof = {"bound": "alu", "kernel": "k_gf_mul_fixed", "achieved": ach / 1e12 if ach else None,
+            "peak": alu_peak / 1e12, "unit": "T int32 ops/s", "frac": ach / alu_peak if ach else None,
+            "traffic": stored_traffic("k_gf_mul_fixed", [(f"GF({p}^{k})", count) for p, k in workloads.GF_FIELDS],
+                                      len(fields)),
+            "peak_source": "integer ALU pipe from unit counts: 152 SMs x 64 lanes x 2.07 GHz",
+            "launches": nk, "avg_launch_ms": kper,
+            "hbm_frac": nbytes / len(fields) / (kper / 1e3) / 1e9 / hbm,
+            "note": "achieved = ALU-pipe operations per launch (committed ncu capture) / average launch time"}
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": ws * macs / (t_ms / 1e3), "unit": "F_p MAC/s", "n_gpus": ws,
             "steps": len(ts), "warmup": max(3, args.warmup), "ms_per_step": t_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64 / f64 packed words, u32 tables",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32 DQT words, u64 products",
             "data": "synthetic",
             "config": {"workload": "GF(p^k) multiply, 2^24 pairs each in GF(3^5), GF(7^4), GF(2^8) per step",
                        "l2": "flushed between steps (512 MiB write)", "per_field": per_field},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": ws * macs / (te / 1e3), "unit": "F_p MAC/s", "h2d_bytes_per_step": 2 * nbytes // 3,
                     "d2h_bytes_per_step": nbytes // 3},
-            "gpu_launches": launches, "clocks": clk.summary(), "issue_roof": issue_roof,
+            "gpu_launches": launches, "clocks": clk.summary(),
         }))
     fp.fp_ctx_destroy(ctx)
 

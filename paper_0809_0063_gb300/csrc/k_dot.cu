@@ -11,6 +11,29 @@
 
 namespace fpd {
 
+// Grid-stride walk over the 16-byte vectors of u and v with four vector pairs loaded before any
+// is used: 128 bytes in flight per thread, enough across the grid to cover HBM latency at full
+// bandwidth (one pair per thread is not).  The vectors are visited in a different order than a
+// plain stride loop; every consumer only sums exact integers.
+template <typename Fn>
+__device__ __forceinline__ void dot_vectors(const uint8_t* u, const uint8_t* v, uint64_t nv, Fn&& fn) {
+  const uint4* U = reinterpret_cast<const uint4*>(u);
+  const uint4* V = reinterpret_cast<const uint4*>(v);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < nv; i += 4 * stride) {
+    uint4 a[4], c[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      a[j] = __ldg(U + i + j * stride);
+      c[j] = __ldg(V + i + j * stride);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) fn(a[j], c[j]);
+  }
+  for (; i < nv; i += stride) fn(__ldg(U + i), __ldg(V + i));
+}
+
 __global__ void __launch_bounds__(256) k_dot_plain(const uint8_t* __restrict__ u, const uint8_t* __restrict__ v,
                                                    uint64_t n, uint64_t* __restrict__ partial, uint32_t p,
                                                    uint32_t* err) {
@@ -18,20 +41,18 @@ __global__ void __launch_bounds__(256) k_dot_plain(const uint8_t* __restrict__ u
   uint32_t bad = 0;
   bool aligned = ((((uintptr_t)u) | ((uintptr_t)v)) & 15u) == 0;
   uint64_t nv = aligned ? n / 16 : 0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nv; i += (uint64_t)gridDim.x * blockDim.x) {
-    uint4 a = __ldg(reinterpret_cast<const uint4*>(u) + i);
-    uint4 b = __ldg(reinterpret_cast<const uint4*>(v) + i);
+  const uint32_t pp = 0x01010101u * p;
+  dot_vectors(u, v, nv, [&](const uint4& a, const uint4& b) {
     uint32_t s = 0;
     s = __dp4a(a.x, b.x, s);
     s = __dp4a(a.y, b.y, s);
     s = __dp4a(a.z, b.z, s);
     s = __dp4a(a.w, b.w, s);
     acc += s;
-    // range check: a byte >= p exists iff max byte >= p; use __vcmpgeu4
-    uint32_t pp = 0x01010101u * p;
+    // range check: some byte >= p
     bad |= __vcmpgeu4(a.x, pp) | __vcmpgeu4(a.y, pp) | __vcmpgeu4(a.z, pp) | __vcmpgeu4(a.w, pp);
     bad |= __vcmpgeu4(b.x, pp) | __vcmpgeu4(b.y, pp) | __vcmpgeu4(b.z, pp) | __vcmpgeu4(b.w, pp);
-  }
+  });
   for (uint64_t i = nv * 16 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t a = u[i], b = v[i];
@@ -103,15 +124,12 @@ __global__ void __launch_bounds__(256) k_dot_dqt_vec(const uint8_t* __restrict__
                                                      uint32_t b, uint32_t F, uint32_t* err) {
   constexpr int BPV = 16 / D1;                         // blocks per vector
   const uint64_t nv = n / 16;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t mask = (1ull << b) - 1;
   const uint32_t mid = (D1 - 1) * b;
   const uint32_t pp = 0x01010101u * p;
   uint64_t sum = 0, acc = 0;
   uint32_t cnt = 0, bad = 0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nv; i += stride) {
-    const uint4 a = __ldg(reinterpret_cast<const uint4*>(u) + i);
-    const uint4 c = __ldg(reinterpret_cast<const uint4*>(v) + i);
+  dot_vectors(u, v, nv, [&](const uint4& a, const uint4& c) {
     const uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wc[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) bad |= __vcmpgeu4(wa[q], pp) | __vcmpgeu4(wc[q], pp);
@@ -133,7 +151,7 @@ __global__ void __launch_bounds__(256) k_dot_dqt_vec(const uint8_t* __restrict__
       acc += wl * wr;
     }
     cnt += BPV;
-  }
+  });
   sum += (acc >> mid) & mask;
   if (blockIdx.x == 0 && threadIdx.x == 0)
     for (uint64_t i = nv * 16; i < n; ++i) {
@@ -164,15 +182,12 @@ __global__ void __launch_bounds__(256) k_dot_dqt_bytes(const uint8_t* __restrict
                                                        uint64_t n, uint64_t* __restrict__ partial, uint32_t p,
                                                        uint32_t F, uint32_t* err) {
   const uint64_t nv = n / 16;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   constexpr uint32_t MID = QB == 8 ? 24 : 16;
   constexpr uint64_t MASK = QB == 8 ? 0xffull : 0xffffull;
   const uint32_t pp = 0x01010101u * p;
   uint64_t sum = 0, acc = 0;
   uint32_t cnt = 0, bad = 0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nv; i += stride) {
-    const uint4 a = __ldg(reinterpret_cast<const uint4*>(u) + i);
-    const uint4 c = __ldg(reinterpret_cast<const uint4*>(v) + i);
+  dot_vectors(u, v, nv, [&](const uint4& a, const uint4& c) {
     const uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wc[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -201,7 +216,7 @@ __global__ void __launch_bounds__(256) k_dot_dqt_bytes(const uint8_t* __restrict
         }
       }
     }
-  }
+  });
   sum += (acc >> MID) & MASK;
   if (blockIdx.x == 0 && threadIdx.x == 0)
     for (uint64_t i = nv * 16; i < n; ++i) {

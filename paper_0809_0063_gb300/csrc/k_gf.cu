@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(256) k_gf_mul_bulk(const E* __restrict__ a, co
 //    every field to the top bits of the word (its cross products fall on distinct bits below the
 //    index, so nothing carries into it, or above bit 31);
 //  * the field addition of the two parts, in the index representation, is table-driven:
-//    GF(2^8) XOR; GF(3^5) one lookup of the spread coefficient sums; GF(7^4) the sum of the two
+//    GF(2^8) XOR; GF(3^5) one lookup of the coefficient sums (the parts hold their coefficients
+//    as base-5 digits, and sums of two residues < 3 never carry); GF(7^4) the sum of the two
 //    parts' indices minus 7^(i+1) for each coefficient i whose sum reached 7.
 // The tables live in one shared-memory image per field (gfw_image), copied whole into every
 // block.  Word tables indexed by a byte are replicated 32 times (entry x of lane l at
@@ -213,7 +214,7 @@ template <> struct Gfw<2, 8> {
 };
 // GF(3^5): q = 2^5, r < 2^45 (9 digits <= 20), m = 5; c = 2 index bits per residue.
 template <> struct Gfw<3, 5> {
-  static constexpr uint32_t W = 0, L = 32768, H = L + 8192, T = H + 512, BYTES = T + 32768;
+  static constexpr uint32_t W = 0, L = 32768, H = L + 8192, T = H + 512, BYTES = T + 3200;   // T: 5^5 entries
 };
 // GF(7^4): q = 2^8, r < 2^54 (7 digits <= 144), m = 3 = k - 1; c = 3.
 template <> struct Gfw<7, 4> {
@@ -256,7 +257,7 @@ __device__ __forceinline__ uint32_t gfw_mul_2_8(uint32_t a, uint32_t b, const ui
   return gfw_gather4((uint32_t)r) ^ H[gfw_gather4((uint32_t)(r >> 32))];
 }
 
-// One product in GF(3^5).
+// One product in GF(3^5): L/H entries = sum mu_i 5^i, T maps a sum of two of them to the index.
 __device__ __forceinline__ uint32_t gfw_mul_3_5(uint32_t a, uint32_t b, const uint32_t* wl, const uint16_t* L,
                                                 const uint16_t* H, const uint8_t* T) {
   const uint64_t r = (uint64_t)wl[a * 32] * wl[b * 32];
@@ -337,33 +338,43 @@ struct Gfw32 {
   }
 };
 
-// One 16-byte vector of each operand per thread and trip (coalesced 512 bytes per warp), no
-// staging: the arithmetic per byte is high enough that a few loads in flight per warp keep up,
-// and the shared memory goes to the tables, whose one copy serves 32 warps.
+// Eight indices of each operand per thread and trip (a 16-byte vector of uint16, an 8-byte one of
+// uint8), no staging: the arithmetic per byte is high enough that a few loads in flight per warp
+// keep up, and the shared memory goes to the tables, whose one copy serves 32 warps.  Eight per
+// trip rather than sixteen keeps the grid's threads within one trip of each other at the end.
 static constexpr int GFW_THREADS = 1024;
+template <uint32_t P> struct GfwVec { using T = uint2; };
+template <> struct GfwVec<7> { using T = uint4; };
+template <typename Fn>
+__device__ __forceinline__ uint2 gfw_apply(const uint2& x, const uint2& y, Fn&& f) {
+  return make_uint2(f(x.x, y.x), f(x.y, y.y));
+}
+template <typename Fn>
+__device__ __forceinline__ uint4 gfw_apply(const uint4& x, const uint4& y, Fn&& f) {
+  return make_uint4(f(x.x, y.x), f(x.y, y.y), f(x.z, y.z), f(x.w, y.w));
+}
 template <uint32_t P, uint32_t K>
-__global__ void __launch_bounds__(GFW_THREADS, 2) k_gf_mul_fixed(const uint4* __restrict__ a, const uint4* __restrict__ b,
-                                                                 uint4* __restrict__ c, uint64_t nvec,
+__global__ void __launch_bounds__(GFW_THREADS, 2) k_gf_mul_fixed(const typename GfwVec<P>::T* __restrict__ a,
+                                                                 const typename GfwVec<P>::T* __restrict__ b,
+                                                                 typename GfwVec<P>::T* __restrict__ c, uint64_t nvec,
                                                                  const uint4* __restrict__ image, uint32_t* err) {
   extern __shared__ __align__(128) uint8_t sm[];
   constexpr uint32_t IB = Gfw<P, K>::BYTES;
   for (uint32_t i = threadIdx.x; i < IB / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = image[i];
   __syncthreads();
   Gfw32<P, K> op{sm, threadIdx.x & 31u, 0};
+  auto word = [&](uint32_t x, uint32_t y) { return op.word(x, y); };
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if constexpr (P == 2) {
     // the lightest field: two vectors of each operand in flight per thread
     for (; i + stride < nvec; i += 2 * stride) {
-      const uint4 va = a[i], vb = b[i], wa = a[i + stride], wb = b[i + stride];
-      c[i] = make_uint4(op.word(va.x, vb.x), op.word(va.y, vb.y), op.word(va.z, vb.z), op.word(va.w, vb.w));
-      c[i + stride] = make_uint4(op.word(wa.x, wb.x), op.word(wa.y, wb.y), op.word(wa.z, wb.z), op.word(wa.w, wb.w));
+      const auto va = a[i], vb = b[i], wa = a[i + stride], wb = b[i + stride];
+      c[i] = gfw_apply(va, vb, word);
+      c[i + stride] = gfw_apply(wa, wb, word);
     }
   }
-  for (; i < nvec; i += stride) {
-    const uint4 va = a[i], vb = b[i];
-    c[i] = make_uint4(op.word(va.x, vb.x), op.word(va.y, vb.y), op.word(va.z, vb.z), op.word(va.w, vb.w));
-  }
+  for (; i < nvec; i += stride) c[i] = gfw_apply(a[i], b[i], word);
   if (op.any_bad()) flag_error(err, ERR_RANGE);
 }
 
@@ -407,7 +418,7 @@ static std::vector<uint8_t> gfw_image(uint32_t p, uint32_t k, uint32_t b, const 
     img.assign(G::BYTES, 0);
     for (uint32_t x = 0; x < 256; ++x)
       for (uint32_t l = 0; l < 32; ++l) put32(G::W + 4 * (32 * x + l), x < order ? word(x) : 0u);
-    for (uint32_t il = 0; il < 4096; ++il) {   // u_0..u_5 -> spread of sum_{i<5} mu_i X^i
+    for (uint32_t il = 0; il < 4096; ++il) {   // u_0..u_5 -> sum_{i<5} mu_i X^i (base-5 digits)
       // index layout of gfw_mul_3_5: (u4 + 4 u5) + 16 (u2 + 4 u3) + 256 (u0 + 4 u1)
       uint32_t u[6], v = 0;
       bool ok = true;
@@ -418,10 +429,10 @@ static std::vector<uint8_t> gfw_image(uint32_t p, uint32_t k, uint32_t b, const 
         ok &= u[2 * j] < p && u[2 * j + 1] < p;
       }
       if (!ok) continue;
-      for (uint32_t i = 0; i < 5; ++i) v |= ((u[i] + cq * u[i + 1]) % p) << (3 * i);
+      for (uint32_t i = 0, w = 1; i < 5; ++i, w *= 5) v += ((u[i] + cq * u[i + 1]) % p) * w;
       put16(G::L + 2 * il, (uint16_t)v);
     }
-    for (uint32_t ih = 0; ih < 256; ++ih) {    // u_5..u_8 -> spread of (sum_{i>=5} mu_i X^i mod P)
+    for (uint32_t ih = 0; ih < 256; ++ih) {    // u_5..u_8 -> (sum_{i>=5} mu_i X^i mod P), base-5 digits
       uint32_t u[9] = {0};
       bool ok = true;
       for (uint32_t t = 0; t < 4; ++t) { u[5 + t] = (ih >> (2 * t)) & 3u; ok &= u[5 + t] < p; }
@@ -431,12 +442,12 @@ static std::vector<uint8_t> gfw_image(uint32_t p, uint32_t k, uint32_t b, const 
       for (uint32_t i = 5; i < 8; ++i) ph[i] = (u[i] + cq * u[i + 1]) % p;
       const std::vector<uint32_t> r = poly_rem(ph, modulus, p);
       uint32_t v = 0;
-      for (uint32_t i = 0; i < k; ++i) v |= r[i] << (3 * i);
+      for (uint32_t i = 0, w = 1; i < k; ++i, w *= 5) v += r[i] * w;
       put16(G::H + 2 * ih, (uint16_t)v);
     }
-    for (uint32_t x = 0; x < 32768; ++x) {     // spread coefficient sums -> index
-      uint32_t v = 0, w = 1;
-      for (uint32_t i = 0; i < k; ++i, w *= p) v += (((x >> (3 * i)) & 7u) % p) * w;
+    for (uint32_t x = 0; x < 3125; ++x) {      // base-5 coefficient sums -> index
+      uint32_t v = 0, w = 1, y = x;
+      for (uint32_t i = 0; i < k; ++i, w *= p, y /= 5) v += ((y % 5) % p) * w;
       img[G::T + x] = (uint8_t)v;
     }
   } else if (p == 7 && k == 4 && b == 8) {
@@ -631,8 +642,9 @@ extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const
   for (uint32_t i = 0; i < g->k; ++i) G.ones |= 1u << (i * g->fb);
   const bool aligned = ((((uintptr_t)a) | ((uintptr_t)b) | ((uintptr_t)c)) & 15u) == 0;
   // word-level fields: whole 16-byte vectors on k_gf_mul_fixed, the rest below
-  if (g->d_img && aligned && count * g->elem_bytes >= 16) {
-    const uint64_t nvec = count * g->elem_bytes / 16;
+  const uint64_t vbytes = g->elem_bytes == 2 ? 16 : 8;   // eight indices per vector
+  if (g->d_img && aligned && count * g->elem_bytes >= vbytes) {
+    const uint64_t nvec = count * g->elem_bytes / vbytes;
     const size_t smem_f = g->img_bytes;
     bool launched = false;
 #define FP_GF_FIXED(PP, KK)                                                                                           \
@@ -642,8 +654,9 @@ extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const
       FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gf_mul_fixed<PP, KK>, GFW_THREADS, smem_f));    \
       const uint64_t want = (nvec + GFW_THREADS - 1) / GFW_THREADS;                                                    \
       const int grid_f = (int)std::min<uint64_t>(want, (uint64_t)ctx->num_sms * (uint64_t)std::max(per_sm, 1));    \
+      using VT = typename GfwVec<PP>::T;                                                                              \
       FP_LAUNCH(ctx, "k_gf_mul_fixed", st, (k_gf_mul_fixed<PP, KK><<<grid_f, GFW_THREADS, smem_f, st>>>(            \
-                    (const uint4*)a, (const uint4*)b, (uint4*)c, nvec, g->d_img, ctx->d_err)));                        \
+                    (const VT*)a, (const VT*)b, (VT*)c, nvec, g->d_img, ctx->d_err)));                                 \
       launched = true;                                                                                                 \
     }
     FP_GF_FIXED(3, 5)
@@ -652,7 +665,7 @@ extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const
 #undef FP_GF_FIXED
     if (launched) {
       FP_CUDA(cudaGetLastError());
-      const uint64_t fd = nvec * 16 / g->elem_bytes, eb = g->elem_bytes;
+      const uint64_t fd = nvec * vbytes / g->elem_bytes, eb = g->elem_bytes;
       if (fd == count) return FP_OK;
       a = (const uint8_t*)a + fd * eb;
       b = (const uint8_t*)b + fd * eb;
