@@ -167,6 +167,30 @@ def test_polymul_word_granular_path(env, p, d, algo):
     assert np.array_equal(C.cpu().numpy(), field.polymul_mod(a, b, p))
 
 
+@pytest.mark.parametrize("p,d", [(2, 2), (3, 2), (5, 3)])
+def test_polymul_word_granular_staged(env, p, d):
+    """Above 512 full tiles (2^20 pairs) the word-granular kernel stages tiles through shared
+    memory by bulk copies instead of reading in place; 600 tiles plus a ragged tail, every
+    coefficient compared, plus a coefficient equal to p in the last full tile."""
+    fp, torch, dev, ctx = env
+    batch = 600 * 2048 + 333
+    a, b = workloads.polymul_inputs(7 + p * d, p, batch, d, d)
+    C = torch.empty((batch, 2 * d + 1), dtype=torch.uint8, device=dev)
+    try:
+        fp.fp_polymul_batched(ctx, p, to_dev(torch, dev, a), d, to_dev(torch, dev, b), d, C, batch, fp.FP_ALGO_AUTO)
+    except fp.FpError as e:
+        if e.status == fp.FP_EBOUND:
+            pytest.skip("the product does not fit a 32-bit word")
+        raise
+    fp.fp_ctx_status(ctx)
+    assert np.array_equal(C.cpu().numpy(), field.polymul_mod(a, b, p))
+    a[600 * 2048 - 5, 1] = p
+    fp.fp_polymul_batched(ctx, p, to_dev(torch, dev, a), d, to_dev(torch, dev, b), d, C, batch, fp.FP_ALGO_AUTO)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_ctx_status(ctx)
+    assert ei.value.status == fp.FP_EINVAL
+
+
 @pytest.mark.parametrize("pos", [0, 1000, 2047, 4095, 6143, 6144 + 700])
 def test_polymul_word_granular_range_check(env, pos):
     """A coefficient equal to p anywhere (each full tile, the tail) raises the range error."""
