@@ -295,11 +295,15 @@ typedef struct {
   uint8_t* C;
 } fp_instance;
 
-/* Run all `count` instances in ONE persistent kernel launch: CTAs take tiles from a device
- * work queue (an atomic counter over a tile list the host planner sorts by cost); packing
- * degree e and word are chosen per (p, k) by the planner; per-instance tile shapes by the
- * autotuner cache in the context.  `instances` is a HOST array; it is copied to context
- * scratch.  Errors: FP_EINVAL, FP_EBOUND, FP_ECUDA. */
+/* Run all `count` instances: matrix products with p <= 17, k (p-1)^2 < 2^24, m, n >= 64 and
+ * m n k >= 2^21 go to the grouped e4m3 tensor-core kernel (their operands first copied to
+ * 16-byte row strides and range-checked in one launch, then up to 64 products per launch);
+ * everything else runs in ONE persistent kernel launch whose CTAs take tiles from a device
+ * work queue (an atomic counter over a tile list the host planner sorts by cost), packing
+ * degree e and word chosen per (p, k) by the planner and the autotuner cache in the context.
+ * `instances` is a HOST array; every instance is checked before anything is enqueued; the
+ * plan is copied to context scratch through pinned staging (the call does not wait for earlier
+ * work on the stream).  Errors: FP_EINVAL, FP_EBOUND, FP_ECUDA, FP_ENOMEM. */
 fp_status fp_batch_run(fp_ctx ctx, const fp_instance* instances, size_t count, void* stream);
 
 /* Diagnostic (no counterpart in the paper): launches one warp that waits on a device barrier

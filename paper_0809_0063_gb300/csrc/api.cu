@@ -4,6 +4,8 @@
 #include <stdarg.h>
 #include <string.h>
 
+#include <cstring>
+
 #include "fpdqt_internal.cuh"
 
 namespace fpd {
@@ -113,6 +115,24 @@ fp_status ensure_scratch(fp_ctx ctx, size_t bytes, int which) {
     return FP_ENOMEM;
   }
   *cap = want;
+  return FP_OK;
+}
+
+fp_status upload_staged(fp_ctx ctx, int slot, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return FP_OK;
+  if (ctx->pin_ev[slot]) FP_CUDA(cudaEventSynchronize(ctx->pin_ev[slot]));
+  else FP_CUDA(cudaEventCreateWithFlags(&ctx->pin_ev[slot], cudaEventDisableTiming));
+  if (ctx->pin_bytes[slot] < bytes) {
+    if (ctx->pin[slot]) FP_CUDA(cudaFreeHost(ctx->pin[slot]));
+    ctx->pin[slot] = nullptr;
+    ctx->pin_bytes[slot] = 0;
+    const size_t want = bytes < (1u << 16) ? (1u << 16) : bytes + bytes / 4;
+    FP_CUDA(cudaMallocHost(&ctx->pin[slot], want));
+    ctx->pin_bytes[slot] = want;
+  }
+  std::memcpy(ctx->pin[slot], src, bytes);
+  FP_CUDA(cudaMemcpyAsync(dst, ctx->pin[slot], bytes, cudaMemcpyHostToDevice, st));
+  FP_CUDA(cudaEventRecord(ctx->pin_ev[slot], st));
   return FP_OK;
 }
 
@@ -246,6 +266,10 @@ extern "C" void fp_ctx_destroy(fp_ctx ctx) {
   if (ctx->scratch2) cudaFree(ctx->scratch2);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
+  for (int i = 0; i < fp_ctx_s::PIN_SLOTS; ++i) {
+    if (ctx->pin[i]) cudaFreeHost(ctx->pin[i]);
+    if (ctx->pin_ev[i]) cudaEventDestroy(ctx->pin_ev[i]);
+  }
   delete ctx;
 }
 

@@ -82,10 +82,20 @@ struct fp_ctx_s {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   std::mutex pmu;
+  // pinned host staging for per-call uploads (batch plans, job lists), one buffer per use slot:
+  // a slot is rewritten only after the copy that last read it has run (its event), so an upload
+  // never waits for the kernels before it in the stream (a pageable copy would)
+  static constexpr int PIN_SLOTS = 4;
+  void* pin[PIN_SLOTS] = {};
+  size_t pin_bytes[PIN_SLOTS] = {};
+  cudaEvent_t pin_ev[PIN_SLOTS] = {};
 };
 
 namespace fpd {
 fp_status ensure_scratch(fp_ctx ctx, size_t bytes, int which = 0);
+// Asynchronous host-to-device copy of `bytes` from `src` through the context's pinned staging
+// slot `slot` (0 .. PIN_SLOTS-1); `src` may be reused as soon as the call returns.
+fp_status upload_staged(fp_ctx ctx, int slot, void* dst, const void* src, size_t bytes, cudaStream_t st);
 void launch_begin(fp_ctx ctx, const char* name, cudaStream_t st);
 void launch_end(fp_ctx ctx, cudaStream_t st);
 // Launch a kernel through the context's instrumentation (launch count, optional events).
@@ -394,6 +404,9 @@ fp_status mm_bound_check(uint32_t p, int k, int algo);
 bool f8_direct_ok(uint32_t p, int k, const uint8_t* A, int lda, const uint8_t* B, int ldb);
 fp_status launch_mm_f8_direct(fp_ctx ctx, const fp_mm_problem& x, cudaStream_t st);   // lock held
 fp_status launch_mm_f8_grouped(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st);
+// lock held; prechecked: the caller has range-checked every A and B (the kernel skips its check)
+fp_status launch_mm_f8_grouped_locked(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st,
+                                      bool prechecked);
 // grouped 16-bit tensor-core products (k_tcp.cu): packed fp16 (right compression, p <= 3)
 // or plain bf16
 bool f16p_ok(uint32_t p, int k);

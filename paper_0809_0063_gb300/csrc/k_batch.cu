@@ -293,6 +293,22 @@ static uint32_t kclass(uint32_t k) {
 // Packed (two residues per word) or plain for this (p, k class): measured once per class.
 static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st);
 
+// The checks batch_prepare applies to instance i (returns FP_OK or the error, message set).
+fp_status batch_check(const fp_instance& x, size_t i) {
+  FP_CHECK(x.kind <= 1, FP_EINVAL, "fp_batch_run: instance %zu has kind %u", i, x.kind);
+  FP_CHECK(x.p >= 2 && x.p <= 251 && is_prime(x.p), FP_EINVAL, "fp_batch_run: instance %zu p=%u", i, x.p);
+  FP_CHECK(x.A && x.B && x.C, FP_EINVAL, "fp_batch_run: instance %zu has a null pointer", i);
+  if (x.kind == 1) {
+    FP_CHECK(x.k >= 1, FP_EINVAL, "fp_batch_run: dot instance %zu has length 0", i);
+    return FP_OK;
+  }
+  FP_CHECK(x.m >= 1 && x.n >= 1 && x.k >= 1 && x.m <= 65535u * BT_M && x.n <= 65535u * BT_N, FP_EINVAL,
+           "fp_batch_run: instance %zu sizes m=%u n=%u k=%u", i, x.m, x.n, x.k);
+  FP_CHECK((uint64_t)x.k * (x.p - 1) * (x.p - 1) < (1ull << 32), FP_EBOUND,
+           "fp_batch_run: instance %zu k (p-1)^2 >= 2^32", i);
+  return FP_OK;
+}
+
 fp_status batch_prepare(fp_ctx ctx, const fp_instance* in, size_t count, cudaStream_t st, bool measure_only,
                         std::vector<BInst>& insts, std::vector<BItem>& items) {
   insts.assign(count, BInst{});
@@ -300,23 +316,18 @@ fp_status batch_prepare(fp_ctx ctx, const fp_instance* in, size_t count, cudaStr
   items.reserve(count * 4);
   for (size_t i = 0; i < count; ++i) {
     const fp_instance& x = in[i];
-    FP_CHECK(x.kind <= 1, FP_EINVAL, "fp_batch_run: instance %zu has kind %u", i, x.kind);
-    FP_CHECK(x.p >= 2 && x.p <= 251 && is_prime(x.p), FP_EINVAL, "fp_batch_run: instance %zu p=%u", i, x.p);
-    FP_CHECK(x.A && x.B && x.C, FP_EINVAL, "fp_batch_run: instance %zu has a null pointer", i);
+    fp_status cs = batch_check(x, i);
+    if (cs != FP_OK) return cs;
     BInst b{};
     b.A = x.A; b.B = x.B; b.C = x.C; b.kind = x.kind; b.p = x.p;
     const uint64_t pp = (uint64_t)(x.p - 1) * (x.p - 1);
     if (x.kind == 1) {
-      FP_CHECK(x.k >= 1, FP_EINVAL, "fp_batch_run: dot instance %zu has length 0", i);
       b.m = b.n = 1; b.k = x.k;
       b.P = make_redq(x.p, 16, 1);
       insts[i] = b;
       items.push_back(BItem{(uint32_t)i, 0, 0});
       continue;
     }
-    FP_CHECK(x.m >= 1 && x.n >= 1 && x.k >= 1 && x.m <= 65535u * BT_M && x.n <= 65535u * BT_N, FP_EINVAL,
-             "fp_batch_run: instance %zu sizes m=%u n=%u k=%u", i, x.m, x.n, x.k);
-    FP_CHECK((uint64_t)x.k * pp < (1ull << 32), FP_EBOUND, "fp_batch_run: instance %zu k (p-1)^2 >= 2^32", i);
     b.m = x.m; b.n = x.n; b.k = x.k;
     b.packed = (!measure_only && x.p <= 3 && x.k <= 32767 && choose_packed(ctx, x.p, x.k, st)) ? 1u : 0u;
     if (measure_only) b.packed = x.reserved ? 1u : 0u;  // the autotuner's probe sets it explicitly
@@ -430,6 +441,118 @@ static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st) {
   return packed;
 }
 
+// ---------------------------------------------------------------- tensor-core share of a batch
+//
+// Matrix products whose residues are exact e4m3 values (p <= 17), whose fp32 sums stay below
+// 2^24 (k (p-1)^2 < 2^24) and that fill at least part of a 128 x 256 tile run on the grouped
+// tcgen05 kernel (k_mm_f8g) instead of the mma.sync tiles of k_batch: in the uneven benchmark
+// batch they hold two thirds of the MACs.  TMA needs operand rows at 16-byte strides, so one
+// launch of k_pad_rows first copies every such A (m x k) and B (k x n) that is not already laid
+// out that way into context scratch with rows rounded up to 16 bytes (the pad bytes are never
+// read: the tensor maps' extents stop at k and n).  The same launch range-checks every routed
+// operand (those used in place by a read-only pass), so k_mm_f8g skips its own check: with few
+// tiles per problem that check would read whole panels from one CTA.
+
+static constexpr uint64_t BT_TC_MIN_MACS = 1ull << 21;
+
+struct PadJob {
+  const uint8_t* src;
+  uint8_t* dst;       // null: range check only
+  uint32_t row_bytes, src_ld, dst_ld, p;
+  uint64_t row0;      // first row of this job in the launch's flat row numbering
+};
+
+// One warp per row (grid-stride over all jobs' rows).  Destination words are built by funnel
+// shifts of the aligned source words that hold them; a source word is read only if it holds a
+// byte of the row, so no read leaves the source allocation.  Range check of the row's bytes: a
+// residue r >= p (p <= 17) has bit 7 set in r | (r + 128 - p); bytes past the row are masked.
+__global__ void __launch_bounds__(256) k_pad_rows(const PadJob* __restrict__ jobs, uint32_t njobs, uint64_t rows,
+                                                  uint32_t* err) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t bad = 0;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t r = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    uint32_t lo = 0, hi = njobs - 1;             // the last job with row0 <= r
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].row0 <= r) lo = mid;
+      else hi = mid - 1;
+    }
+    const PadJob J = jobs[lo];
+    const uint64_t row = r - J.row0;
+    const uint8_t* src = J.src + row * J.src_ld;
+    uint32_t* dst = J.dst ? reinterpret_cast<uint32_t*>(J.dst + row * J.dst_ld) : nullptr;
+    const uint32_t off = (uint32_t)((uintptr_t)src & 3u);
+    const uint32_t* base = reinterpret_cast<const uint32_t*>(src - off);
+    const uint32_t nw = (J.row_bytes + 3) / 4;
+    const uint32_t pk = 0x01010101u * (128u - J.p);
+    for (uint32_t c = lane; c < nw; c += 32) {
+      const uint32_t a0 = base[c];
+      const uint32_t a1 = (off != 0 && 4 * c + 4 - off < J.row_bytes) ? base[c + 1] : 0u;
+      const uint32_t w = off ? __funnelshift_r(a0, a1, 8 * off) : a0;
+      const uint32_t nb = J.row_bytes - 4 * c;                       // >= 1
+      const uint32_t wv = nb >= 4 ? w : w & ((1u << (8 * nb)) - 1u);
+      bad |= wv | (wv + pk);
+      if (J.dst) dst[c] = w;
+    }
+  }
+  if (bad & 0x80808080u) flag_error(err, ERR_RANGE);
+}
+
+static bool batch_tc_route(const fp_instance& x) {
+  return x.kind == 0 && x.A && x.B && x.C && x.p >= 2 && x.p <= 17 && is_prime(x.p) && x.m >= 64 && x.n >= 64 &&
+         x.k >= 1 && x.m <= (1u << 30) && x.n <= (1u << 30) && x.k <= (1u << 30) &&
+         (uint64_t)x.k * (x.p - 1) * (x.p - 1) < (1ull << 24) && (uint64_t)x.m * x.n * x.k >= BT_TC_MIN_MACS;
+}
+
+// The tensor-core share: pad copies (one launch) and grouped k_mm_f8g launches.  Lock held.
+static fp_status batch_run_tc(fp_ctx ctx, const std::vector<const fp_instance*>& tc, cudaStream_t st) {
+  auto up16 = [](uint64_t x) { return (x + 15) & ~(uint64_t)15; };
+  auto up256 = [](uint64_t x) { return (x + 255) & ~(uint64_t)255; };
+  std::vector<fp_mm_problem> prob(tc.size());
+  std::vector<PadJob> jobs;
+  std::vector<uint64_t> a_off(tc.size(), 0), b_off(tc.size(), 0);   // scratch offsets, 0 = in place
+  uint64_t bytes = up256(2 * tc.size() * sizeof(PadJob)), rows = 0;
+  for (size_t i = 0; i < tc.size(); ++i) {
+    const fp_instance& x = *tc[i];
+    fp_mm_problem& q = prob[i];
+    q = fp_mm_problem{x.p, (int)x.m, (int)x.n, (int)x.k, x.A, (int)x.k, x.B, (int)x.n, x.C, (int)x.n};
+    // every operand gets a job: a padded copy, or (already 16-byte rows) a range check only
+    if (((uintptr_t)x.A & 15u) != 0 || x.k % 16 != 0) {
+      a_off[i] = bytes;
+      q.lda = (int)up16(x.k);
+      bytes += up256((uint64_t)x.m * up16(x.k));
+    }
+    jobs.push_back(PadJob{x.A, nullptr, x.k, x.k, (uint32_t)q.lda, x.p, rows});
+    rows += x.m;
+    if (((uintptr_t)x.B & 15u) != 0 || x.n % 16 != 0) {
+      b_off[i] = bytes;
+      q.ldb = (int)up16(x.n);
+      bytes += up256((uint64_t)x.k * up16(x.n));
+    }
+    jobs.push_back(PadJob{x.B, nullptr, x.n, x.n, (uint32_t)q.ldb, x.p, rows});
+    rows += x.k;
+  }
+  {
+    fp_status s = ensure_scratch(ctx, bytes, 0);
+    if (s != FP_OK) return s;
+    uint8_t* base = (uint8_t*)ctx->scratch;
+    for (size_t i = 0; i < tc.size(); ++i) {   // jobs 2i (A) and 2i + 1 (B)
+      if (a_off[i]) { prob[i].A = base + a_off[i]; jobs[2 * i].dst = base + a_off[i]; }
+      if (b_off[i]) { prob[i].B = base + b_off[i]; jobs[2 * i + 1].dst = base + b_off[i]; }
+    }
+    s = upload_staged(ctx, 0, base, jobs.data(), jobs.size() * sizeof(PadJob), st);
+    if (s != FP_OK) return s;
+    const int grid = (int)std::min<uint64_t>((rows + 7) / 8, (uint64_t)ctx->num_sms * 8);
+    FP_LAUNCH(ctx, "k_pad_rows", st,
+              k_pad_rows<<<grid, 256, 0, st>>>((const PadJob*)base, (uint32_t)jobs.size(), rows, ctx->d_err));
+    FP_CUDA(cudaGetLastError());
+  }
+  std::vector<const fp_mm_problem*> ptr(prob.size());
+  for (size_t i = 0; i < prob.size(); ++i) ptr[i] = &prob[i];
+  return launch_mm_f8_grouped_locked(ctx, ptr.data(), ptr.size(), st, true);
+}
+
 }  // namespace fpd
 
 extern "C" fp_status fp_batch_run(fp_ctx ctx, const fp_instance* instances, size_t count, void* stream) {
@@ -438,5 +561,38 @@ extern "C" fp_status fp_batch_run(fp_ctx ctx, const fp_instance* instances, size
   if (count == 0) return FP_OK;
   FP_CHECK(instances != nullptr, FP_EINVAL, "fp_batch_run: instances is NULL");
   std::lock_guard<std::mutex> lk(ctx->mu);
-  return plan_and_launch(ctx, instances, count, as_stream(stream), false);
+  cudaStream_t st = as_stream(stream);
+  std::vector<const fp_instance*> tc;
+  std::vector<fp_instance> rest;
+  rest.reserve(count);
+  // every instance checked before anything is enqueued (the routed ones satisfy the checks by
+  // construction); the batch kernel's plan is built while the GPU runs the tensor-core share
+  for (size_t i = 0; i < count; ++i) {
+    if (batch_tc_route(instances[i])) {
+      tc.push_back(&instances[i]);
+    } else {
+      fp_status s = batch_check(instances[i], i);
+      if (s != FP_OK) return s;
+      rest.push_back(instances[i]);
+    }
+  }
+  if (!tc.empty()) {
+    fp_status s = batch_run_tc(ctx, tc, st);
+    if (s != FP_OK) return s;
+  }
+  if (rest.empty()) return FP_OK;
+  std::vector<BInst> insts;
+  std::vector<BItem> items;
+  {
+    fp_status s = batch_prepare(ctx, rest.data(), rest.size(), st, false, insts, items);
+    if (s != FP_OK) return s;
+  }
+  const size_t bytes = batch_plan_bytes(insts.size(), items.size());
+  fp_status s = ensure_scratch(ctx, bytes, 1);
+  if (s != FP_OK) return s;
+  std::vector<uint8_t> h(bytes);
+  batch_plan_write(insts, items, h.data());
+  s = upload_staged(ctx, 1, ctx->scratch2, h.data(), bytes, st);
+  if (s != FP_OK) return s;
+  return batch_launch_plan(ctx, insts.size(), items.size(), (uint8_t*)ctx->scratch2, st);
 }

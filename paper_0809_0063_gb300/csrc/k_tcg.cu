@@ -42,7 +42,9 @@ static constexpr int G_A_BYTES = G_BM * G_BK;                 // 16 KB
 static constexpr int G_B_BYTES = G_BN * G_BK;                 // 32 KB (two 128-column boxes)
 static constexpr int G_STAGE_BYTES = G_A_BYTES + G_B_BYTES;   // 48 KB
 static constexpr int G_THREADS = 320;                         // 10 warps
-static constexpr size_t G_SMEM = 1024 + G_STAGES * G_STAGE_BYTES + 256;
+// per epilogue warp: 32 rows x 32 output bytes (row stride 36 bytes: conflict-free word writes)
+static constexpr int G_EPI_STAGE_BYTES = 8 * 32 * 36;
+static constexpr size_t G_SMEM = 1024 + G_STAGES * G_STAGE_BYTES + 256 + G_EPI_STAGE_BYTES;
 
 struct GProb {
   CUtensorMap ta;   // A: m rows x k columns, leading dimension lda
@@ -59,22 +61,34 @@ struct GProb {
   uint32_t fdiv;    // 1 when k (p-1)^2 < 2^23: reduce with FDIV in fp32 (Table fdiv, case 3)
   float c18;        // 2^18 RU(1/p)
   float pm18;       // -p 2^-18
+  uint32_t checked; // 1: the caller range-checked A and B already (the epilogue skips its check)
 };
 
-struct GParams {
-  GProb prob[FP_GROUP_MAX];
+// CAP problems per launch: FP_GROUP_MAX for the public grouped call, G_BATCH_CAP for the
+// tensor-core share of an uneven batch (the parameter block stays under the 32 KB limit).
+static constexpr int G_BATCH_CAP = 64;
+template <int CAP>
+struct GParamsT {
+  GProb prob[CAP];
   int nprob;
   int total;        // tiles over all problems
 };
+using GParams = GParamsT<FP_GROUP_MAX>;
+static_assert(sizeof(GParamsT<G_BATCH_CAP>) < 32000, "kernel parameter block limit");
 
 struct GTile {
   const GProb* pr;
   int m0, n0, mb, nb;
 };
 
-__device__ __forceinline__ GTile g_tile(const GParams& g, int t) {
-  int i = 0;
-  while (i + 1 < g.nprob && t >= g.prob[i + 1].tile0) ++i;
+template <int CAP>
+__device__ __forceinline__ GTile g_tile(const GParamsT<CAP>& g, int t) {
+  int i = 0, hi = g.nprob - 1;      // the last problem whose first tile is <= t
+  while (i < hi) {
+    const int mid = (i + hi + 1) >> 1;
+    if (g.prob[mid].tile0 <= t) i = mid;
+    else hi = mid - 1;
+  }
   const GProb& pr = g.prob[i];
   const int local = t - pr.tile0;
   GTile x;
@@ -111,7 +125,8 @@ __device__ __forceinline__ uint32_t range_bits(const uint8_t* src, int valid, ui
   return acc;
 }
 
-__global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__ GParams g, uint32_t* err) {
+template <int CAP>
+__global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__ GParamsT<CAP> g, uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t g_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)g_smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + G_STAGES * G_STAGE_BYTES);
@@ -218,13 +233,15 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
     const int half = (warp - 2) >> 2;            // column half (0: 0..127, 1: 128..255)
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const uint32_t tid = threadIdx.x - 64;       // 0..255 over the epilogue warps
+    uint32_t* const epi_stage =                 // this warp's 32 x 36-byte store buffer
+        reinterpret_cast<uint32_t*>(smem + G_STAGES * G_STAGE_BYTES + 256) + (warp - 2) * (32 * 9);
     uint32_t bad = 0;
     int lt = 0;
     for (int t = blockIdx.x; t < g.total; t += gridDim.x, ++lt) {
       const int buf = lt & 1;
       const GTile x = g_tile(g, t);
       const GProb& pr = *x.pr;
-      {
+      if (!pr.checked) {
         // range check: a residue byte r >= p (p <= 17) has bit 7 set in r | (r + 128 - p),
         // with no carry between bytes unless bit 7 of the lower byte is already set
         const uint32_t pk = 0x01010101u * (128u - pr.p);
@@ -291,18 +308,25 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
             packed[j >> 2] = w;
           }
         }
-        const int c0 = x.n0 + col0;
-        if (row < m && c0 < n) {
-          uint8_t* dst = Cb + (size_t)row * ldc + c0;
-          if (c0 + 32 <= n && ((((uintptr_t)dst) & 15u) == 0)) {
-            reinterpret_cast<uint4*>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-            reinterpret_cast<uint4*>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-          } else {
-            // unrolled with a predicate: a runtime index into packed[] would put it in memory
+        const int c0 = x.n0 + col0;                 // the same for the whole warp
+        uint8_t* dst = Cb + (size_t)row * ldc + c0;
+        const bool vec = row < m && c0 + 32 <= n && ((((uintptr_t)dst) & 15u) == 0);
+        if (__all_sync(0xffffffffu, vec)) {
+          reinterpret_cast<uint4*>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          reinterpret_cast<uint4*>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        } else if (c0 < n) {
+          // rows not 16-byte aligned (ldc not a multiple of 16) or a ragged edge: the warp's
+          // 32 rows x 32 bytes go through shared memory and out one row at a time, the 32 lanes
+          // on consecutive bytes (one or two 32-byte sectors per store, not 32)
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (c0 + j < n) dst[j] = (uint8_t)(packed[j >> 2] >> (8 * (j & 3)));
-          }
+          for (int j = 0; j < 8; ++j) epi_stage[lane * 9 + j] = packed[j];
+          __syncwarp();
+          const uint8_t* sb = reinterpret_cast<const uint8_t*>(epi_stage);
+          const int r0 = x.m0 + q * 32;
+          const bool col_in = c0 + lane < n;
+          for (int r = 0; r < 32 && r0 + r < m; ++r)
+            if (col_in) Cb[(size_t)(r0 + r) * ldc + c0 + lane] = sb[r * 36 + lane];
+          __syncwarp();
         }
       }
       tc_fence_before();
@@ -333,9 +357,11 @@ bool f8_direct_ok(uint32_t p, int k, const uint8_t* A, int lda, const uint8_t* B
          (lda & 15) == 0 && (ldb & 15) == 0;
 }
 
-// One launch over up to FP_GROUP_MAX problems, each already validated and f8_direct_ok.
-static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int count, cudaStream_t st) {
-  GParams hp;          // passed by value as the kernel's (grid-constant) parameter block
+// One launch over up to CAP problems, each already validated and f8_direct_ok.
+template <int CAP>
+static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int count, cudaStream_t st,
+                              bool prechecked) {
+  GParamsT<CAP> hp;    // passed by value as the kernel's (grid-constant) parameter block
   std::memset(&hp, 0, sizeof hp);
   int tile = 0;
   for (int i = 0; i < count; ++i) {
@@ -363,13 +389,14 @@ static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int co
     g.fdiv = (uint64_t)x.k * (x.p - 1) * (x.p - 1) < (1ull << 23) ? 1u : 0u;
     g.c18 = make_redq(x.p, 1, 1).invp_f * 262144.0f;   // RU(1/p) scaled by 2^18 (exact)
     g.pm18 = -(float)x.p / 262144.0f;
+    g.checked = prechecked ? 1u : 0u;
     tile += g.tm * g.tn;
   }
   hp.nprob = count;
   hp.total = tile;
   const int grid = std::min(tile, ctx->num_sms);
-  FP_CUDA(cudaFuncSetAttribute(k_mm_f8g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G_SMEM));
-  FP_LAUNCH(ctx, "k_mm_f8g", st, k_mm_f8g<<<grid, G_THREADS, G_SMEM, st>>>(hp, ctx->d_err));
+  FP_CUDA(cudaFuncSetAttribute(k_mm_f8g<CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G_SMEM));
+  FP_LAUNCH(ctx, "k_mm_f8g", st, k_mm_f8g<CAP><<<grid, G_THREADS, G_SMEM, st>>>(hp, ctx->d_err));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }
@@ -377,18 +404,27 @@ static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int co
 // One problem (the caller holds the context lock).
 fp_status launch_mm_f8_direct(fp_ctx ctx, const fp_mm_problem& x, cudaStream_t st) {
   const fp_mm_problem* one = &x;
-  return launch_group(ctx, &one, 1, st);
+  return launch_group<FP_GROUP_MAX>(ctx, &one, 1, st, false);
 }
 
-// Problems that pass f8_direct_ok, in launches of up to FP_GROUP_MAX problems; within a
-// launch the problems with the most k tiles come first so the longest tiles start earliest.
+// Problems that pass f8_direct_ok, in launches of up to FP_GROUP_MAX problems (G_BATCH_CAP for
+// an uneven batch's prechecked share: its many small problems need several tiles per CTA and
+// launch to overlap their pipelines); within a launch the problems with the most k tiles come
+// first so the longest tiles start earliest.
 fp_status launch_mm_f8_grouped(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return launch_mm_f8_grouped_locked(ctx, pr, count, st, false);
+}
+
+fp_status launch_mm_f8_grouped_locked(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st,
+                                      bool prechecked) {
   std::vector<const fp_mm_problem*> v(pr, pr + count);
   std::stable_sort(v.begin(), v.end(), [](const fp_mm_problem* a, const fp_mm_problem* b) { return a->k > b->k; });
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  for (size_t i = 0; i < v.size(); i += FP_GROUP_MAX) {
-    const int c = (int)std::min<size_t>(FP_GROUP_MAX, v.size() - i);
-    fp_status s = launch_group(ctx, v.data() + i, c, st);
+  const size_t cap = prechecked ? G_BATCH_CAP : FP_GROUP_MAX;
+  for (size_t i = 0; i < v.size(); i += cap) {
+    const int c = (int)std::min<size_t>(cap, v.size() - i);
+    fp_status s = prechecked ? launch_group<G_BATCH_CAP>(ctx, v.data() + i, c, st, true)
+                             : launch_group<FP_GROUP_MAX>(ctx, v.data() + i, c, st, false);
     if (s != FP_OK) return s;
   }
   return FP_OK;

@@ -2,6 +2,9 @@
 // sm_103a) and the host-side tensor-map encoder.
 #pragma once
 
+#include <mutex>
+#include <unordered_map>
+
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -167,8 +170,44 @@ inline EncodeTiledFn get_encode() {
 // 2-D map of a rows x cols row-major matrix of 16-bit (esize 2) or 8-bit (esize 1) elements
 // with leading dimension ld elements (ld * esize a multiple of 16, base 16-byte aligned),
 // box = box_rows x (128 bytes of elements), 128-byte swizzle; reads past cols or rows return 0.
+// A map is a pure function of its arguments, so encoded maps are kept in a process-wide cache
+// (a batch that repeats its operands skips the driver call; bounded, cleared when full).
+struct MapKey {
+  const void* base;
+  uint64_t rows, cols, ld;
+  uint32_t box_rows, esize;
+  bool operator==(const MapKey& o) const {
+    return base == o.base && rows == o.rows && cols == o.cols && ld == o.ld && box_rows == o.box_rows &&
+           esize == o.esize;
+  }
+};
+struct MapKeyHash {
+  size_t operator()(const MapKey& k) const {
+    uint64_t h = (uint64_t)(uintptr_t)k.base * 0x9E3779B97F4A7C15ull;
+    for (uint64_t v : {k.rows, k.cols, k.ld, (uint64_t)k.box_rows << 8 | k.esize}) h = (h ^ v) * 0x100000001B3ull;
+    return (size_t)h;
+  }
+};
+inline std::mutex& map_cache_mu() {
+  static std::mutex m;
+  return m;
+}
+inline std::unordered_map<MapKey, CUtensorMap, MapKeyHash>& map_cache() {
+  static std::unordered_map<MapKey, CUtensorMap, MapKeyHash> c;
+  return c;
+}
+
 inline fp_status make_map_ld(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
                              uint32_t box_rows, uint32_t esize) {
+  const MapKey key{base, rows, cols, ld, box_rows, esize};
+  {
+    std::lock_guard<std::mutex> lk(map_cache_mu());
+    auto it = map_cache().find(key);
+    if (it != map_cache().end()) {
+      *map = it->second;
+      return FP_OK;
+    }
+  }
   EncodeTiledFn enc = get_encode();
   FP_CHECK(enc != nullptr, FP_ECUDA, "cuTensorMapEncodeTiled is not available");
   cuuint64_t dims[2] = {cols, rows};
@@ -180,6 +219,9 @@ inline fp_status make_map_ld(CUtensorMap* map, const void* base, uint64_t rows, 
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   FP_CHECK(r == CUDA_SUCCESS, FP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  std::lock_guard<std::mutex> lk(map_cache_mu());
+  if (map_cache().size() >= 65536) map_cache().clear();
+  map_cache().emplace(key, *map);
   return FP_OK;
 }
 inline fp_status make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t kp, uint32_t box_rows,

@@ -139,3 +139,79 @@ def test_batch_rejects_bad_instances(env):
     with pytest.raises(fp.FpError) as ei:
         fp.fp_batch_run(ctx, [fp.fp_instance(kind=0, p=3, m=1, n=1, k=1, reserved=0, A=0, B=1, C=1)])
     assert ei.value.status == fp.FP_EINVAL
+
+
+def _mm(p, m, k, n, seed):
+    g = np.random.default_rng(seed)
+    x = workloads.Instance("matmul", p, m, k, n)
+    x.a = g.integers(0, p, (m, k), dtype=np.uint8)
+    x.b = g.integers(0, p, (k, n), dtype=np.uint8)
+    return x
+
+
+@pytest.mark.parametrize("off_a,off_b", [(0, 0), (1, 2), (3, 1), (2, 3)])
+def test_batch_tensor_core_share_unaligned(env, off_a, off_b):
+    """Large products with p <= 17 run on the grouped e4m3 kernel after their operands are copied
+    to 16-byte row strides; operands starting 1-3 bytes past an aligned address and inner
+    dimensions / widths that are not multiples of 4 exercise every shift of that copy.  Mixed
+    with products and dots that stay on the batch kernel; every entry compared."""
+    fp, torch, dev, ctx = env
+    shapes = [(3, 130, 449, 257), (17, 200, 1021, 67), (5, 64, 512, 64), (2, 333, 2047, 129), (7, 96, 33, 700),
+              (31, 150, 300, 200), (3, 40, 900, 900)]
+    insts = [_mm(p, m, k, n, 100 + i) for i, (p, m, k, n) in enumerate(shapes)]
+    d = workloads.Instance("dot", 7, 1, 999, 1)
+    g = np.random.default_rng(5)
+    d.a = g.integers(0, 7, 999, dtype=np.uint8)
+    d.b = g.integers(0, 7, 999, dtype=np.uint8)
+    insts.append(d)
+    bufs, arr = [], []
+    for x in insts:
+        if x.kind == "matmul":
+            ra = torch.zeros(x.a.size + 16, dtype=torch.uint8, device=dev)
+            rb = torch.zeros(x.b.size + 16, dtype=torch.uint8, device=dev)
+            A = ra[off_a:off_a + x.a.size]
+            B = rb[off_b:off_b + x.b.size]
+            A.copy_(torch.from_numpy(x.a.reshape(-1)).to(dev))
+            B.copy_(torch.from_numpy(x.b.reshape(-1)).to(dev))
+            C = torch.full((x.m, x.n), 255, dtype=torch.uint8, device=dev)
+            arr.append(fp.fp_instance(kind=0, p=x.p, m=x.m, n=x.n, k=x.k, reserved=0,
+                                      A=A.data_ptr(), B=B.data_ptr(), C=C.data_ptr()))
+        else:
+            A, B = to_dev(torch, dev, x.a), to_dev(torch, dev, x.b)
+            C = torch.full((4,), 255, dtype=torch.uint8, device=dev)
+            arr.append(fp.fp_instance(kind=1, p=x.p, m=1, n=1, k=x.k, reserved=0,
+                                      A=A.data_ptr(), B=B.data_ptr(), C=C.data_ptr()))
+        bufs.append((A, B, C))
+    fp.fp_batch_run(ctx, arr)
+    fp.fp_ctx_status(ctx)
+    for x, (A, B, C) in zip(insts, bufs):
+        assert np.array_equal(result(x, C), oracle(x)), (x.kind, x.p, x.m, x.n, x.k)
+
+
+def test_batch_tensor_core_share_range_error(env):
+    """An entry equal to p inside a product routed to the tensor cores raises the range error."""
+    fp, torch, dev, ctx = env
+    x = _mm(5, 128, 300, 129, 7)
+    x.a = x.a.copy()
+    x.a[77, 250] = 5
+    bufs, arr = make_instances(fp, torch, dev, [x, _mm(3, 10, 10, 10, 8)])
+    fp.fp_batch_run(ctx, arr)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_ctx_status(ctx)
+    assert ei.value.status == fp.FP_EINVAL
+
+
+def test_batch_invalid_instance_enqueues_nothing(env):
+    """A rejected instance anywhere in the batch: the call fails before any launch, so the
+    outputs of the valid instances (including one bound for the tensor cores) stay untouched."""
+    fp, torch, dev, ctx = env
+    good = [_mm(3, 256, 256, 256, 9), _mm(7, 20, 20, 20, 10)]
+    bufs, arr = make_instances(fp, torch, dev, good)
+    bad = fp.fp_instance(kind=0, p=9, m=4, n=4, k=4, reserved=0, A=arr[0].A, B=arr[0].B, C=arr[0].C)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_batch_run(ctx, arr + [bad])
+    assert ei.value.status == fp.FP_EINVAL
+    torch.cuda.synchronize()
+    fp.fp_ctx_status(ctx)
+    for A, B, C in bufs:
+        assert int(C.min().item()) == 255 and int(C.max().item()) == 255
