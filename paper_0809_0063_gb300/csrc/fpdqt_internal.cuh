@@ -404,6 +404,11 @@ fp_status mm_bound_check(uint32_t p, int k, int algo);
 bool f8_direct_ok(uint32_t p, int k, const uint8_t* A, int lda, const uint8_t* B, int ldb);
 fp_status launch_mm_f8_direct(fp_ctx ctx, const fp_mm_problem& x, cudaStream_t st);   // lock held
 fp_status launch_mm_f8_grouped(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st);
+// Plain bf16 tensor-core products of an uneven batch (k (p-1)^2 < 2^24): operands converted and
+// range-checked in one launch into `scratch` (t16_batch_bytes long), then grouped launches.  Lock held.
+uint64_t t16_batch_bytes(const fp_mm_problem* const* pr, size_t count);
+fp_status launch_mm_t16_plain_batch(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, uint8_t* scratch,
+                                    cudaStream_t st);
 // lock held; prechecked: the caller has range-checked every A and B (the kernel skips its check)
 fp_status launch_mm_f8_grouped_locked(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st,
                                       bool prechecked);

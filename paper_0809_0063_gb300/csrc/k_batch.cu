@@ -499,14 +499,20 @@ __global__ void __launch_bounds__(256) k_pad_rows(const PadJob* __restrict__ job
   if (bad & 0x80808080u) flag_error(err, ERR_RANGE);
 }
 
-static bool batch_tc_route(const fp_instance& x) {
-  return x.kind == 0 && x.A && x.B && x.C && x.p >= 2 && x.p <= 17 && is_prime(x.p) && x.m >= 64 && x.n >= 64 &&
-         x.k >= 1 && x.m <= (1u << 30) && x.n <= (1u << 30) && x.k <= (1u << 30) &&
-         (uint64_t)x.k * (x.p - 1) * (x.p - 1) < (1ull << 24) && (uint64_t)x.m * x.n * x.k >= BT_TC_MIN_MACS;
+// 1: e4m3 products (p <= 17); 2: bf16 products (17 < p <= 127, residues exact in bf16 and the
+// conversion's range check valid); 0: the batch kernel.
+static int batch_tc_route(const fp_instance& x) {
+  const bool big = x.kind == 0 && x.A && x.B && x.C && x.p >= 2 && x.p <= 127 && is_prime(x.p) && x.m >= 64 &&
+                   x.n >= 64 && x.k >= 1 && x.m <= (1u << 30) && x.n <= (1u << 30) && x.k <= (1u << 30) &&
+                   (uint64_t)x.k * (x.p - 1) * (x.p - 1) < (1ull << 24) && (uint64_t)x.m * x.n * x.k >= BT_TC_MIN_MACS;
+  return big ? (x.p <= 17 ? 1 : 2) : 0;
 }
 
-// The tensor-core share: pad copies (one launch) and grouped k_mm_f8g launches.  Lock held.
-static fp_status batch_run_tc(fp_ctx ctx, const std::vector<const fp_instance*>& tc, cudaStream_t st) {
+// The tensor-core share: e4m3 products (pad copies in one launch, grouped k_mm_f8g launches) and
+// bf16 products (conversion in one launch, grouped k_mm_t16 launches), both from one scratch
+// allocation.  Lock held.
+static fp_status batch_run_tc(fp_ctx ctx, const std::vector<const fp_instance*>& tc,
+                              const std::vector<const fp_instance*>& t16, cudaStream_t st) {
   auto up16 = [](uint64_t x) { return (x + 15) & ~(uint64_t)15; };
   auto up256 = [](uint64_t x) { return (x + 255) & ~(uint64_t)255; };
   std::vector<fp_mm_problem> prob(tc.size());
@@ -533,9 +539,21 @@ static fp_status batch_run_tc(fp_ctx ctx, const std::vector<const fp_instance*>&
     jobs.push_back(PadJob{x.B, nullptr, x.n, x.n, (uint32_t)q.ldb, x.p, rows});
     rows += x.k;
   }
+  std::vector<fp_mm_problem> prob16(t16.size());
+  std::vector<const fp_mm_problem*> ptr16(t16.size());
+  for (size_t i = 0; i < t16.size(); ++i) {
+    const fp_instance& x = *t16[i];
+    prob16[i] = fp_mm_problem{x.p, (int)x.m, (int)x.n, (int)x.k, x.A, (int)x.k, x.B, (int)x.n, x.C, (int)x.n};
+    ptr16[i] = &prob16[i];
+  }
+  const uint64_t off16 = (bytes + 1023) & ~(uint64_t)1023;
+  const uint64_t total = t16.empty() ? bytes : off16 + t16_batch_bytes(ptr16.data(), ptr16.size());
   {
-    fp_status s = ensure_scratch(ctx, bytes, 0);
+    fp_status s = ensure_scratch(ctx, total + 1024, 0);
     if (s != FP_OK) return s;
+  }
+  if (!tc.empty()) {
+    fp_status s = FP_OK;
     uint8_t* base = (uint8_t*)ctx->scratch;
     for (size_t i = 0; i < tc.size(); ++i) {   // jobs 2i (A) and 2i + 1 (B)
       if (a_off[i]) { prob[i].A = base + a_off[i]; jobs[2 * i].dst = base + a_off[i]; }
@@ -548,9 +566,14 @@ static fp_status batch_run_tc(fp_ctx ctx, const std::vector<const fp_instance*>&
               k_pad_rows<<<grid, 256, 0, st>>>((const PadJob*)base, (uint32_t)jobs.size(), rows, ctx->d_err));
     FP_CUDA(cudaGetLastError());
   }
-  std::vector<const fp_mm_problem*> ptr(prob.size());
-  for (size_t i = 0; i < prob.size(); ++i) ptr[i] = &prob[i];
-  return launch_mm_f8_grouped_locked(ctx, ptr.data(), ptr.size(), st, true);
+  if (!tc.empty()) {
+    std::vector<const fp_mm_problem*> ptr(prob.size());
+    for (size_t i = 0; i < prob.size(); ++i) ptr[i] = &prob[i];
+    fp_status s = launch_mm_f8_grouped_locked(ctx, ptr.data(), ptr.size(), st, true);
+    if (s != FP_OK) return s;
+  }
+  if (t16.empty()) return FP_OK;
+  return launch_mm_t16_plain_batch(ctx, ptr16.data(), ptr16.size(), (uint8_t*)ctx->scratch + off16, st);
 }
 
 }  // namespace fpd
@@ -562,22 +585,25 @@ extern "C" fp_status fp_batch_run(fp_ctx ctx, const fp_instance* instances, size
   FP_CHECK(instances != nullptr, FP_EINVAL, "fp_batch_run: instances is NULL");
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaStream_t st = as_stream(stream);
-  std::vector<const fp_instance*> tc;
+  std::vector<const fp_instance*> tc, t16;
   std::vector<fp_instance> rest;
   rest.reserve(count);
   // every instance checked before anything is enqueued (the routed ones satisfy the checks by
   // construction); the batch kernel's plan is built while the GPU runs the tensor-core share
   for (size_t i = 0; i < count; ++i) {
-    if (batch_tc_route(instances[i])) {
+    const int route = batch_tc_route(instances[i]);
+    if (route == 1) {
       tc.push_back(&instances[i]);
+    } else if (route == 2) {
+      t16.push_back(&instances[i]);
     } else {
       fp_status s = batch_check(instances[i], i);
       if (s != FP_OK) return s;
       rest.push_back(instances[i]);
     }
   }
-  if (!tc.empty()) {
-    fp_status s = batch_run_tc(ctx, tc, st);
+  if (!tc.empty() || !t16.empty()) {
+    fp_status s = batch_run_tc(ctx, tc, t16, st);
     if (s != FP_OK) return s;
   }
   if (rest.empty()) return FP_OK;

@@ -41,7 +41,9 @@ static constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;   // 48 KB
 static constexpr int P_EPI_WARPS = 8;                         // 2 per TMEM lane quarter
 static constexpr int P_CW = 4 * P_BNW / P_EPI_WARPS;            // MMA columns per epilogue thread
 static constexpr int P_THREADS = 32 * (2 + P_EPI_WARPS);
-static constexpr size_t P_SMEM = 1024 + P_STAGES * P_STAGE_BYTES + 256;
+// per epilogue warp: 32 rows x 32 output bytes (row stride 36 bytes: conflict-free word writes)
+static constexpr int P_EPI_STAGE_BYTES = P_EPI_WARPS * 32 * 36;
+static constexpr size_t P_SMEM = 1024 + P_STAGES * P_STAGE_BYTES + 256 + P_EPI_STAGE_BYTES;
 
 // kind::f16, A (K-major) and B (MN-major) both fp16 (ab_type 0) or both bf16 (1), fp32 accumulate.
 __host__ __device__ constexpr uint32_t idesc_16_bmn(uint32_t ab_type, int M, int N) {
@@ -63,20 +65,31 @@ struct PProb {
   RedqParams P;      // REDQ_2 at q = 2^16
 };
 
-struct PParams {
-  PProb prob[FP_GROUP_MAX];
+// CAP problems per launch: FP_GROUP_MAX for the public calls, P_BATCH_CAP for the large p > 17
+// products of an uneven batch.
+static constexpr int P_BATCH_CAP = 64;
+template <int CAP>
+struct PParamsT {
+  PProb prob[CAP];
   int nprob;
   int total;
 };
+using PParams = PParamsT<FP_GROUP_MAX>;
+static_assert(sizeof(PParamsT<P_BATCH_CAP>) < 32000, "kernel parameter block limit");
 
 struct PTile {
   const PProb* pr;
   int m0, w0;        // first row, first MMA column
 };
 
-__device__ __forceinline__ PTile p_tile(const PParams& g, int t) {
-  int i = 0;
-  while (i + 1 < g.nprob && t >= g.prob[i + 1].tile0) ++i;
+template <int CAP>
+__device__ __forceinline__ PTile p_tile(const PParamsT<CAP>& g, int t) {
+  int i = 0, hi = g.nprob - 1;      // the last problem whose first tile is <= t
+  while (i < hi) {
+    const int mid = (i + hi + 1) >> 1;
+    if (g.prob[mid].tile0 <= t) i = mid;
+    else hi = mid - 1;
+  }
   const PProb& pr = g.prob[i];
   const int local = t - pr.tile0;
   const int mb = local / pr.tn;
@@ -146,8 +159,8 @@ __device__ __forceinline__ void final_redq(uint32_t (&R)[NW], uint32_t fix, uint
   }
 }
 
-template <bool PACKED>
-__global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__ PParams g, uint32_t* err) {
+template <bool PACKED, int CAP = FP_GROUP_MAX>
+__global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__ PParamsT<CAP> g, uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t p_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)p_smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + P_STAGES * P_STAGE_BYTES);
@@ -261,6 +274,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
     const int q = warp & 3;                      // TMEM lane quarter
     const int part = (warp - 2) >> 2;            // MMA columns part * P_CW .. + P_CW - 1
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    uint32_t* const epi_stage =                 // this warp's 32 x 36-byte store buffer
+        reinterpret_cast<uint32_t*>(smem + P_STAGES * P_STAGE_BYTES + 256) + (warp - 2) * (32 * 9);
     uint32_t gc = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < g.total && ok && !PACKED; t += gridDim.x, ++gc) {
@@ -290,17 +305,24 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
           for (int u = 0; u < 4; ++u) w |= modp32(__float2uint_rn(__uint_as_float(v[j + u])), dv, p) << (8 * u);
           o[j >> 2] = w;
         }
-        const int c0 = x.w0 + col0;
-        if (row < pr.m && c0 < pr.n) {
-          uint8_t* dst = pr.C + (size_t)row * pr.ldc + c0;
-          if (c0 + 32 <= pr.n && ((((uintptr_t)dst) & 15u) == 0)) {
-            reinterpret_cast<uint4*>(dst)[0] = make_uint4(o[0], o[1], o[2], o[3]);
-            reinterpret_cast<uint4*>(dst)[1] = make_uint4(o[4], o[5], o[6], o[7]);
-          } else {
+        const int c0 = x.w0 + col0;                 // the same for the whole warp
+        uint8_t* dst = pr.C + (size_t)row * pr.ldc + c0;
+        const bool vec = row < pr.m && c0 + 32 <= pr.n && ((((uintptr_t)dst) & 15u) == 0);
+        if (__all_sync(0xffffffffu, vec)) {
+          reinterpret_cast<uint4*>(dst)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+          reinterpret_cast<uint4*>(dst)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        } else if (c0 < pr.n) {
+          // rows not 16-byte aligned or a ragged edge: the warp's 32 rows x 32 bytes go through
+          // shared memory and out one row at a time, the 32 lanes on consecutive bytes
 #pragma unroll
-            for (int j = 0; j < 32; ++j)   // unrolled: a runtime index into o[] would put it in memory
-              if (c0 + j < pr.n) dst[j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
-          }
+          for (int j = 0; j < 8; ++j) epi_stage[lane * 9 + j] = o[j];
+          __syncwarp();
+          const uint8_t* sb = reinterpret_cast<const uint8_t*>(epi_stage);
+          const int r0 = x.m0 + q * 32;
+          const bool col_in = c0 + lane < pr.n;
+          for (int r = 0; r < 32 && r0 + r < pr.m; ++r)
+            if (col_in) pr.C[(size_t)(r0 + r) * pr.ldc + c0 + lane] = sb[r * 36 + lane];
+          __syncwarp();
         }
       }
       tc_fence_before();
@@ -559,6 +581,132 @@ static fp_status launch_t16_locked(fp_ctx ctx, const fp_mm_problem* const* pr, s
       FP_CUDA(cudaFuncSetAttribute(k_mm_t16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
       FP_LAUNCH(ctx, "k_mm_t16_plain", st, k_mm_t16<false><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err));
     }
+    FP_CUDA(cudaGetLastError());
+  }
+  return FP_OK;
+}
+
+// ---------------------------------------------------------------- plain products of an uneven batch
+
+// One conversion job: rows of `row_bytes` residue bytes at src (leading dimension src_ld) to bf16
+// at dst (leading dimension dst_ld elements, dst 16-byte aligned, dst_ld a multiple of 4).
+struct T16Job {
+  const uint8_t* src;
+  uint16_t* dst;
+  uint32_t row_bytes, src_ld, dst_ld, p;
+  uint64_t row0;      // first row of this job in the launch's flat row numbering
+};
+
+// One warp per row of all jobs: four residues per lane and step (read as the aligned source
+// words that hold them, never past the row's last byte's word), range-checked, written as four
+// bf16.  Bytes past the row are masked to 0 (their bf16 lands in the row's padding, which the
+// tensor maps' extents exclude).
+__global__ void __launch_bounds__(256) k_t16_convert_jobs(const T16Job* __restrict__ jobs, uint32_t njobs,
+                                                          uint64_t rows, uint32_t* err) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  uint32_t bad = 0;
+  for (uint64_t r = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    uint32_t lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].row0 <= r) lo = mid;
+      else hi = mid - 1;
+    }
+    const T16Job J = jobs[lo];
+    const uint64_t row = r - J.row0;
+    const uint8_t* src = J.src + row * J.src_ld;
+    uint2* dst = reinterpret_cast<uint2*>(J.dst + row * J.dst_ld);
+    const uint32_t off = (uint32_t)((uintptr_t)src & 3u);
+    const uint32_t* base = reinterpret_cast<const uint32_t*>(src - off);
+    const uint32_t pk = 0x01010101u * (128u - J.p);
+    const uint32_t nw = (J.row_bytes + 3) / 4;
+    for (uint32_t c = lane; c < nw; c += 32) {
+      const uint32_t a0 = base[c];
+      const uint32_t a1 = (off != 0 && 4 * c + 4 - off < J.row_bytes) ? base[c + 1] : 0u;
+      uint32_t w = off ? __funnelshift_r(a0, a1, 8 * off) : a0;
+      const uint32_t nb = J.row_bytes - 4 * c;
+      if (nb < 4) w &= (1u << (8 * nb)) - 1u;
+      bad |= w | ((w & 0x7F7F7F7Fu) + (pk & 0x7F7F7F7Fu));
+      dst[c] = make_uint2(bf16_of(w & 0xffu) | (bf16_of((w >> 8) & 0xffu) << 16),
+                          bf16_of((w >> 16) & 0xffu) | (bf16_of(w >> 24) << 16));
+    }
+  }
+  if (bad & 0x80808080u) flag_error(err, ERR_RANGE);
+}
+
+// Plain products (k (p-1)^2 < 2^24, p <= 251) of an uneven batch: operands converted to bf16 in
+// one launch into `scratch` (at least t16_batch_bytes(...) bytes, 1024-byte aligned), then grouped
+// launches of up to P_BATCH_CAP products.  The caller holds the context lock.
+static uint64_t t16_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+uint64_t t16_batch_bytes(const fp_mm_problem* const* pr, size_t count) {
+  uint64_t bytes = t16_up(count * 2 * sizeof(T16Job), 1024);
+  for (size_t i = 0; i < count; ++i) {
+    const fp_mm_problem& x = *pr[i];
+    bytes += t16_up((uint64_t)x.m * t16_up(x.k, P_BK) * 2, 1024) + t16_up((uint64_t)x.k * t16_up(x.n, 8) * 2, 1024);
+  }
+  return bytes;
+}
+
+fp_status launch_mm_t16_plain_batch(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, uint8_t* scratch,
+                                    cudaStream_t st) {
+  std::vector<const fp_mm_problem*> v(pr, pr + count);
+  std::stable_sort(v.begin(), v.end(), [](const fp_mm_problem* a, const fp_mm_problem* b) { return a->k > b->k; });
+  std::vector<T16Job> jobs;
+  std::vector<uint16_t*> a16(v.size()), b16(v.size());
+  uint64_t off = t16_up(v.size() * 2 * sizeof(T16Job), 1024), rows = 0;
+  for (size_t i = 0; i < v.size(); ++i) {
+    const fp_mm_problem& x = *v[i];
+    const uint64_t kp = t16_up(x.k, P_BK), ldw = t16_up(x.n, 8);
+    a16[i] = (uint16_t*)(scratch + off);
+    off += t16_up((uint64_t)x.m * kp * 2, 1024);
+    b16[i] = (uint16_t*)(scratch + off);
+    off += t16_up((uint64_t)x.k * ldw * 2, 1024);
+    jobs.push_back(T16Job{x.A, a16[i], (uint32_t)x.k, (uint32_t)x.lda, (uint32_t)kp, x.p, rows});
+    rows += x.m;
+    jobs.push_back(T16Job{x.B, b16[i], (uint32_t)x.n, (uint32_t)x.ldb, (uint32_t)ldw, x.p, rows});
+    rows += x.k;
+  }
+  fp_status s = upload_staged(ctx, 2, scratch, jobs.data(), jobs.size() * sizeof(T16Job), st);
+  if (s != FP_OK) return s;
+  const int cgrid = (int)std::min<uint64_t>((rows + 7) / 8, (uint64_t)ctx->num_sms * 8);
+  FP_LAUNCH(ctx, "k_t16_convert_jobs", st,
+            k_t16_convert_jobs<<<cgrid, 256, 0, st>>>((const T16Job*)scratch, (uint32_t)jobs.size(), rows, ctx->d_err));
+  FP_CUDA(cudaGetLastError());
+  FP_CUDA(cudaFuncSetAttribute(k_mm_t16<false, P_BATCH_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
+  for (size_t base = 0; base < v.size(); base += P_BATCH_CAP) {
+    const int cnt = (int)std::min<size_t>(P_BATCH_CAP, v.size() - base);
+    PParamsT<P_BATCH_CAP> hp;
+    std::memset(&hp, 0, sizeof hp);
+    int tile = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const fp_mm_problem& x = *v[base + i];
+      const uint64_t kp = t16_up(x.k, P_BK), ldw = t16_up(x.n, 8);
+      PProb& g = hp.prob[i];
+      // extents k and n: the pad columns past them are never read (the TMA fills zeros)
+      s = make_map_ld(&g.ta, a16[base + i], (uint64_t)x.m, (uint64_t)x.k, kp, P_BM, 2);
+      if (s != FP_OK) return s;
+      s = make_map_ld(&g.tb, b16[base + i], (uint64_t)x.k, (uint64_t)x.n, ldw, 64, 2);
+      if (s != FP_OK) return s;
+      g.C = x.C;
+      g.ldc = x.ldc;
+      g.m = x.m;
+      g.n = x.n;
+      g.nw = x.n;
+      g.ktiles = (int)(kp / P_BK);
+      g.nchunks = 1;
+      g.tn = (x.n + P_BNW - 1) / P_BNW;
+      g.tile0 = tile;
+      g.koffset = (uint32_t)x.k;
+      g.off_mod_p = (uint32_t)x.k % x.p;
+      g.P = make_redq(x.p, 16, 1);
+      tile += ((x.m + P_BM - 1) / P_BM) * g.tn;
+    }
+    hp.nprob = cnt;
+    hp.total = tile;
+    const int grid = std::min(tile, ctx->num_sms);
+    FP_LAUNCH(ctx, "k_mm_t16_plain", st, (k_mm_t16<false, P_BATCH_CAP><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err)));
     FP_CUDA(cudaGetLastError());
   }
   return FP_OK;

@@ -152,12 +152,14 @@ def _mm(p, m, k, n, seed):
 @pytest.mark.parametrize("off_a,off_b", [(0, 0), (1, 2), (3, 1), (2, 3)])
 def test_batch_tensor_core_share_unaligned(env, off_a, off_b):
     """Large products with p <= 17 run on the grouped e4m3 kernel after their operands are copied
-    to 16-byte row strides; operands starting 1-3 bytes past an aligned address and inner
-    dimensions / widths that are not multiples of 4 exercise every shift of that copy.  Mixed
-    with products and dots that stay on the batch kernel; every entry compared."""
+    to 16-byte row strides, those with 17 < p <= 127 on the bf16 kernel after a conversion;
+    operands starting 1-3 bytes past an aligned address and inner dimensions / widths that are
+    not multiples of 4 exercise every shift of those copies (k (p-1)^2 up to 0.86 x 2^24 for
+    p = 61).  Mixed with products (p = 131, small shapes) and dots that stay on the batch kernel;
+    every entry compared."""
     fp, torch, dev, ctx = env
     shapes = [(3, 130, 449, 257), (17, 200, 1021, 67), (5, 64, 512, 64), (2, 333, 2047, 129), (7, 96, 33, 700),
-              (31, 150, 300, 200), (3, 40, 900, 900)]
+              (31, 150, 300, 200), (3, 40, 900, 900), (127, 100, 500, 90), (61, 64, 4000, 64), (131, 80, 700, 80)]
     insts = [_mm(p, m, k, n, 100 + i) for i, (p, m, k, n) in enumerate(shapes)]
     d = workloads.Instance("dot", 7, 1, 999, 1)
     g = np.random.default_rng(5)
@@ -188,12 +190,18 @@ def test_batch_tensor_core_share_unaligned(env, off_a, off_b):
         assert np.array_equal(result(x, C), oracle(x)), (x.kind, x.p, x.m, x.n, x.k)
 
 
-def test_batch_tensor_core_share_range_error(env):
-    """An entry equal to p inside a product routed to the tensor cores raises the range error."""
+@pytest.mark.parametrize("p,where", [(5, "a"), (31, "a"), (31, "b"), (127, "b")])
+def test_batch_tensor_core_share_range_error(env, p, where):
+    """An entry equal to p inside a product routed to the tensor cores (e4m3 for p = 5, bf16
+    otherwise) raises the range error."""
     fp, torch, dev, ctx = env
-    x = _mm(5, 128, 300, 129, 7)
-    x.a = x.a.copy()
-    x.a[77, 250] = 5
+    x = _mm(p, 128, 300, 129, 7)
+    if where == "a":
+        x.a = x.a.copy()
+        x.a[77, 250] = p
+    else:
+        x.b = x.b.copy()
+        x.b[299, 128] = p
     bufs, arr = make_instances(fp, torch, dev, [x, _mm(3, 10, 10, 10, 8)])
     fp.fp_batch_run(ctx, arr)
     with pytest.raises(fp.FpError) as ei:
