@@ -295,9 +295,10 @@ typedef struct {
   uint8_t* C;
 } fp_instance;
 
-/* Run all `count` instances: matrix products with p <= 17, k (p-1)^2 < 2^24, m, n >= 64 and
- * m n k >= 2^21 go to the grouped e4m3 tensor-core kernel (their operands first copied to
- * 16-byte row strides and range-checked in one launch, then up to 64 products per launch);
+/* Run all `count` instances: matrix products with k (p-1)^2 < 2^24, m, n >= 64 and
+ * m n k >= 2^21 go to the tensor cores -- p <= 17 to the grouped e4m3 kernel (operands first
+ * copied to 16-byte row strides and range-checked in one launch), 17 < p <= 127 to the bf16
+ * kernel (operands converted and range-checked in one launch), up to 64 products per launch;
  * everything else runs in ONE persistent kernel launch whose CTAs take tiles from a device
  * work queue (an atomic counter over a tile list the host planner sorts by cost), packing
  * degree e and word chosen per (p, k) by the planner and the autotuner cache in the context.
