@@ -455,6 +455,8 @@ static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st) {
 
 static constexpr uint64_t BT_TC_MIN_MACS = 1ull << 21;
 
+static constexpr uint32_t JOB_SMEM_MAX = 8192;   // 64 KB of first rows
+
 struct PadJob {
   const uint8_t* src;
   uint8_t* dst;       // null: range check only
@@ -470,12 +472,19 @@ __global__ void __launch_bounds__(256) k_pad_rows(const PadJob* __restrict__ job
                                                   uint32_t* err) {
   const uint32_t lane = threadIdx.x & 31u;
   uint32_t bad = 0;
+  // the jobs' first rows in shared memory (when they fit the launch's dynamic allocation) so
+  // that the per-row search for its job stays on chip
+  extern __shared__ uint64_t s_row0[];
+  const bool in_smem = njobs <= JOB_SMEM_MAX;
+  if (in_smem)
+    for (uint32_t i = threadIdx.x; i < njobs; i += blockDim.x) s_row0[i] = jobs[i].row0;
+  __syncthreads();
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t r = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
     uint32_t lo = 0, hi = njobs - 1;             // the last job with row0 <= r
     while (lo < hi) {
       const uint32_t mid = (lo + hi + 1) >> 1;
-      if (jobs[mid].row0 <= r) lo = mid;
+      if ((in_smem ? s_row0[mid] : jobs[mid].row0) <= r) lo = mid;
       else hi = mid - 1;
     }
     const PadJob J = jobs[lo];
@@ -562,8 +571,10 @@ static fp_status batch_run_tc(fp_ctx ctx, const std::vector<const fp_instance*>&
     s = upload_staged(ctx, 0, base, jobs.data(), jobs.size() * sizeof(PadJob), st);
     if (s != FP_OK) return s;
     const int grid = (int)std::min<uint64_t>((rows + 7) / 8, (uint64_t)ctx->num_sms * 8);
+    const size_t jsm = std::min<size_t>(jobs.size(), JOB_SMEM_MAX) * sizeof(uint64_t);
+    FP_CUDA(cudaFuncSetAttribute(k_pad_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(JOB_SMEM_MAX * 8)));
     FP_LAUNCH(ctx, "k_pad_rows", st,
-              k_pad_rows<<<grid, 256, 0, st>>>((const PadJob*)base, (uint32_t)jobs.size(), rows, ctx->d_err));
+              k_pad_rows<<<grid, 256, jsm, st>>>((const PadJob*)base, (uint32_t)jobs.size(), rows, ctx->d_err));
     FP_CUDA(cudaGetLastError());
   }
   if (!tc.empty()) {

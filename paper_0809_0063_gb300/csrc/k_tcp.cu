@@ -590,6 +590,8 @@ static fp_status launch_t16_locked(fp_ctx ctx, const fp_mm_problem* const* pr, s
 
 // One conversion job: rows of `row_bytes` residue bytes at src (leading dimension src_ld) to bf16
 // at dst (leading dimension dst_ld elements, dst 16-byte aligned, dst_ld a multiple of 4).
+static constexpr uint32_t JOB_SMEM_MAX = 8192;   // 64 KB of first rows
+
 struct T16Job {
   const uint8_t* src;
   uint16_t* dst;
@@ -604,13 +606,20 @@ struct T16Job {
 __global__ void __launch_bounds__(256) k_t16_convert_jobs(const T16Job* __restrict__ jobs, uint32_t njobs,
                                                           uint64_t rows, uint32_t* err) {
   const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   uint32_t bad = 0;
+  // the jobs' first rows in shared memory (when they fit the launch's dynamic allocation) so
+  // that the per-row search for its job stays on chip
+  extern __shared__ uint64_t s_row0[];
+  const bool in_smem = njobs <= JOB_SMEM_MAX;
+  if (in_smem)
+    for (uint32_t i = threadIdx.x; i < njobs; i += blockDim.x) s_row0[i] = jobs[i].row0;
+  __syncthreads();
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t r = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
-    uint32_t lo = 0, hi = njobs - 1;
+    uint32_t lo = 0, hi = njobs - 1;             // the last job with row0 <= r
     while (lo < hi) {
       const uint32_t mid = (lo + hi + 1) >> 1;
-      if (jobs[mid].row0 <= r) lo = mid;
+      if ((in_smem ? s_row0[mid] : jobs[mid].row0) <= r) lo = mid;
       else hi = mid - 1;
     }
     const T16Job J = jobs[lo];
@@ -671,8 +680,10 @@ fp_status launch_mm_t16_plain_batch(fp_ctx ctx, const fp_mm_problem* const* pr, 
   fp_status s = upload_staged(ctx, 2, scratch, jobs.data(), jobs.size() * sizeof(T16Job), st);
   if (s != FP_OK) return s;
   const int cgrid = (int)std::min<uint64_t>((rows + 7) / 8, (uint64_t)ctx->num_sms * 8);
+  const size_t jsm = std::min<size_t>(jobs.size(), JOB_SMEM_MAX) * sizeof(uint64_t);
+  FP_CUDA(cudaFuncSetAttribute(k_t16_convert_jobs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(JOB_SMEM_MAX * 8)));
   FP_LAUNCH(ctx, "k_t16_convert_jobs", st,
-            k_t16_convert_jobs<<<cgrid, 256, 0, st>>>((const T16Job*)scratch, (uint32_t)jobs.size(), rows, ctx->d_err));
+            k_t16_convert_jobs<<<cgrid, 256, jsm, st>>>((const T16Job*)scratch, (uint32_t)jobs.size(), rows, ctx->d_err));
   FP_CUDA(cudaGetLastError());
   FP_CUDA(cudaFuncSetAttribute(k_mm_t16<false, P_BATCH_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
   for (size_t base = 0; base < v.size(); base += P_BATCH_CAP) {
