@@ -268,6 +268,70 @@ struct PolySmallOp {
   }
 };
 
+// The same item for the paper's own example shape with every parameter fixed: F_3, degree 2 x
+// degree 2, q = 16 (the smallest power of two above 3 (p-1)^2 = 12).  Per pair: the three
+// coefficient bytes gathered by one byte permutation and packed to nibbles (the DQT at q = 16),
+// one product, s = floor(r / 3) by one multiply-high (r < 16^5), all five u_i = (r_i - 3 s_i) mod
+// 16 at once in byte lanes (even and odd digits apart, p q = 48 added per lane so none borrows),
+// and the correction mu_i = (u_i + c u_{i+1}) mod 3 with c = (-16) mod 3 = 2 for mu_0..mu_3 at
+// once in the bytes of one word (sums <= 6, reduced by two per-byte comparisons); mu_4 = u_4.
+struct PolyF3Op {
+  static constexpr uint32_t IPT = 2;
+  static constexpr uint32_t UNROLL = 1;
+  uint32_t bad;
+  __device__ __forceinline__ static uint32_t pack3(uint32_t t) {   // bytes c0 c1 c2 (< 16) -> c0 + 16 c1 + 256 c2
+    return (t & 0xFu) | ((t >> 4) & 0xF0u) | ((t >> 8) & 0xF00u);
+  }
+  // one product: returns mu_0..mu_3 as bytes; te keeps u_4 in its byte 2
+  __device__ __forceinline__ static uint32_t mul(uint32_t ta, uint32_t tb, uint32_t& te) {
+    constexpr uint32_t ME = 0x000F0F0Fu, CE = 0x00303030u;
+    const uint32_t r = pack3(ta) * pack3(tb);
+    const uint32_t s = __umulhi(r, 0x55555556u);
+    te = (((r & ME) | CE) - 3u * (s & ME)) & ME;                       // u0 u2 u4
+    const uint32_t to = ((((r >> 4) & ME) | CE) - 3u * ((s >> 4) & ME)) & ME;   // u1 u3
+    const uint32_t u = __byte_perm(te, to, 0x5140u);                  // u0 u1 u2 u3
+    const uint32_t un = __byte_perm(te, to, 0x2514u);                 // u1 u2 u3 u4
+    const uint32_t v = u + 2u * un;                                   // bytes <= 6
+    const uint32_t ge = (((v + 0x7D7D7D7Du) >> 7) & 0x01010101u) + (((v + 0x7A7A7A7Au) >> 7) & 0x01010101u);
+    return v - 3u * ge;
+  }
+  __device__ __forceinline__ void item(const uint8_t* a, const uint8_t* b, uint8_t* out) {
+    const uint32_t* pa = reinterpret_cast<const uint32_t*>(a);
+    const uint32_t* pb = reinterpret_cast<const uint32_t*>(b);
+    const uint32_t a0 = pa[0], a1 = pa[1], a2 = pa[2], b0 = pb[0], b1 = pb[1], b2 = pb[2];
+    constexpr uint32_t PK = 0x7D7D7D7Du;                              // 0x01010101 (128 - 3)
+    bad |= a0 | (a0 + PK) | a1 | (a1 + PK) | a2 | (a2 + PK) | b0 | (b0 + PK) | b1 | (b1 + PK) | b2 | (b2 + PK);
+    uint32_t e0, e1, e2, e3;                                          // byte 2: u_4 = mu_4
+    const uint32_t m0 = mul(a0, b0, e0);                              // pair 0: bytes 0-2
+    const uint32_t m1 = mul(__byte_perm(a0, a1, 0x5543u), __byte_perm(b0, b1, 0x5543u), e1);   // bytes 3-5
+    const uint32_t m2 = mul(__byte_perm(a1, a2, 0x4432u), __byte_perm(b1, b2, 0x4432u), e2);   // bytes 6-8
+    const uint32_t m3 = mul(a2 >> 8, b2 >> 8, e3);                    // bytes 9-11
+    uint32_t* o = reinterpret_cast<uint32_t*>(out);
+    o[0] = m0;
+    o[1] = __byte_perm(e0, m1, 0x6542u);                              // mu4(0) mu0..mu2(1)
+    o[2] = __byte_perm(__byte_perm(m1, e1, 0x6663u), m2, 0x5410u);    // mu3(1) mu4(1) mu0 mu1(2)
+    o[3] = __byte_perm(__byte_perm(m2, e2, 0x6632u), m3, 0x4210u);    // mu2 mu3(2) mu4(2) mu0(3)
+    o[4] = __byte_perm(m3, e3, 0x6321u);                              // mu1..mu3(3) mu4(3)
+  }
+};
+
+__global__ void __launch_bounds__(256) k_polymul_f3(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
+                                                    uint8_t* __restrict__ Cout, uint64_t ntiles, uint32_t* err) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  PolyF3Op op{0};
+  stream_tiles(op, A, B, Cout, ntiles, 12, 12, 20, sm, err);
+  if (op.bad & 0x80808080u) flag_error(err, ERR_RANGE);
+}
+
+__global__ void __launch_bounds__(256) k_polymul_f3_direct(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
+                                                           uint8_t* __restrict__ Cout, uint64_t nitems, uint32_t* err) {
+  PolyF3Op op{0};
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nitems; i += stride)
+    op.item(A + i * 12, B + i * 12, Cout + i * 20);
+  if (op.bad & 0x80808080u) flag_error(err, ERR_RANGE);
+}
+
 template <int KA, int KB, int MODE>
 __global__ void __launch_bounds__(256) k_polymul_small(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
                                                        uint8_t* __restrict__ Cout, uint64_t ntiles, RedqParams P,
@@ -319,6 +383,17 @@ static bool launch_polymul_small_k(fp_ctx ctx, const uint8_t* A, const uint8_t* 
   constexpr uint64_t PAIRS = 4 * 256 * 2;   // 4 pairs per item, 256 threads, IPT = 2
   const size_t smem = 2 * PAIRS * (KA + KB + KC) + 64;
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 4);
+  if (KA == 3 && KB == 3 && P.p == 3 && P.b == 4) {   // the fixed F_3 degree-2 form
+    if (ntiles <= POLY_DIRECT_TILES) {
+      const uint64_t nitems = ntiles * (PAIRS / 4);
+      FP_LAUNCH(ctx, "k_polymul_small", st,
+                (k_polymul_f3_direct<<<(int)((nitems + 255) / 256), 256, 0, st>>>(A, B, C, nitems, ctx->d_err)));
+    } else {
+      cudaFuncSetAttribute(k_polymul_f3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      FP_LAUNCH(ctx, "k_polymul_small", st, (k_polymul_f3<<<grid, 256, smem, st>>>(A, B, C, ntiles, ctx->d_err)));
+    }
+    return true;
+  }
   if (ntiles <= POLY_DIRECT_TILES) {
     // one item (4 pairs) per thread: 512 threads per tile of 2048 pairs
     const uint64_t nitems = ntiles * (PAIRS / 4);
