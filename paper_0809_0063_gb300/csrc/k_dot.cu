@@ -12,9 +12,10 @@
 namespace fpd {
 
 // Grid-stride walk over the 16-byte vectors of u and v with four vector pairs loaded before any
-// is used: 128 bytes in flight per thread, enough across the grid to cover HBM latency at full
-// bandwidth (one pair per thread is not).  The vectors are visited in a different order than a
-// plain stride loop; every consumer only sums exact integers.
+// is used (128 bytes in flight per thread), as streaming loads that are evicted first: 2^28 pairs
+// measured 0.77 / 0.82 of the HBM copy rate (packed / plain) against 0.70 / 0.71 with plain
+// read-only loads, and eight pairs per thread ran slower (occupancy).  The vectors are visited
+// in a different order than a plain stride loop; every consumer only sums exact integers.
 template <typename Fn>
 __device__ __forceinline__ void dot_vectors(const uint8_t* u, const uint8_t* v, uint64_t nv, Fn&& fn) {
   const uint4* U = reinterpret_cast<const uint4*>(u);
@@ -25,13 +26,13 @@ __device__ __forceinline__ void dot_vectors(const uint8_t* u, const uint8_t* v, 
     uint4 a[4], c[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      a[j] = __ldg(U + i + j * stride);
-      c[j] = __ldg(V + i + j * stride);
+      a[j] = __ldcs(U + i + j * stride);     // streaming: read once, evict first
+      c[j] = __ldcs(V + i + j * stride);
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) fn(a[j], c[j]);
   }
-  for (; i < nv; i += stride) fn(__ldg(U + i), __ldg(V + i));
+  for (; i < nv; i += stride) fn(__ldcs(U + i), __ldcs(V + i));
 }
 
 __global__ void __launch_bounds__(256) k_dot_plain(const uint8_t* __restrict__ u, const uint8_t* __restrict__ v,
