@@ -314,7 +314,8 @@ struct Gfw32 {
       return c0 | (c1 << 16);
     } else {
       const uint32_t* wl = reinterpret_cast<const uint32_t*>(tab + G::W) + lane;
-      uint32_t wc = 0;
+      // index byte j by one byte permutation; the four results packed by three
+      uint32_t c[4];
       if constexpr (P == 3) {
         // a byte >= 243 has its top bit set and its low 7 bits + 13 >= 128
         bad |= (wa & ((wa & 0x7F7F7F7Fu) + 0x0D0D0D0Du)) | (wb & ((wb & 0x7F7F7F7Fu) + 0x0D0D0D0Du));
@@ -323,14 +324,14 @@ struct Gfw32 {
         const uint8_t* T = tab + G::T;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          wc |= gfw_mul_3_5((wa >> (8 * j)) & 0xFFu, (wb >> (8 * j)) & 0xFFu, wl, L, H, T) << (8 * j);
+          c[j] = gfw_mul_3_5(__byte_perm(wa, 0u, 0x4440u + j), __byte_perm(wb, 0u, 0x4440u + j), wl, L, H, T);
       } else {
         const uint8_t* H = tab + G::H;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          wc |= gfw_mul_2_8((wa >> (8 * j)) & 0xFFu, (wb >> (8 * j)) & 0xFFu, wl, H) << (8 * j);
+          c[j] = gfw_mul_2_8(__byte_perm(wa, 0u, 0x4440u + j), __byte_perm(wb, 0u, 0x4440u + j), wl, H);
       }
-      return wc;
+      return __byte_perm(__byte_perm(c[0], c[1], 0x0040u), __byte_perm(c[2], c[3], 0x0040u), 0x5410u);
     }
   }
   __device__ __forceinline__ bool any_bad() const {
