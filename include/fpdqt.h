@@ -15,6 +15,11 @@
  *  - Every compute call is asynchronous on the given CUDA stream (NULL = legacy default).
  *    Host-side argument checks happen before anything is enqueued; a failing check returns
  *    its status and enqueues nothing.
+ *  - A context owns scratch memory that calls reuse (padded or converted operands, plans,
+ *    partial sums): calls on one context are ordered by their stream, so calls issued on
+ *    different streams with one context must be ordered by the caller (an event or a
+ *    synchronisation between them), or use one context per stream.  The serving loop keeps
+ *    its own device arena and is exempt.
  *  - Residue inputs must lie in [0, p-1].  Kernels check this on the device; a violation
  *    sets the context's sticky error flag (results are then unspecified but every memory
  *    access stays in bounds).  fp_ctx_status() synchronises the stream and reports it.
