@@ -573,7 +573,8 @@ def run_gf(args, ws, rank, local):
 
 def run_batch(args, ws, rank, local):
     """Uneven batch: 4096 matmul / dot instances (p in {2,3,5,7,17,31}, sizes log-uniform in
-    [16, 2048]) in one persistent launch, against one fp_matmul / fp_dot call per instance."""
+    [16, 2048]) in one fp_batch_run call (large products on the tensor-core kernels, the rest in
+    one persistent launch), against one fp_matmul / fp_dot call per instance."""
     import torch
     import __graft_entry__ as g
     g.build()

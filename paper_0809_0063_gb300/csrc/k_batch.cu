@@ -1,6 +1,8 @@
-// Uneven batches of modular matrix products and dot products in ONE persistent launch.
+// Uneven batches of modular matrix products and dot products.
 //
-// The host planner cuts every matmul instance into 64 x 64 output tiles (64 x 64 packed words
+// Large products whose sums stay exact in fp32 go to the tensor-core kernels (p <= 17: e4m3,
+// 17 < p <= 127: bf16; see "tensor-core share" below).  Everything else runs in ONE persistent
+// launch of k_batch: the host planner cuts every matmul instance into 64 x 64 output tiles (64 x 64 packed words
 // when the instance is packed), lists dot instances as single items, sorts the items by
 // their inner dimension (longest first) and uploads the list; persistent CTAs (a multiple of
 // the SM count) take items from an atomic counter until the list is exhausted -- no waiting,

@@ -1,6 +1,6 @@
-"""GPU parity of the uneven batch (one persistent launch over matmul and dot instances of
-mixed p and size): every result bit-exact against the oracle, and identical to the same
-instance run alone through fp_matmul / fp_dot."""
+"""GPU parity of the uneven batch (matmul and dot instances of mixed p and size: the large
+products on the tensor-core kernels, the rest in one persistent launch): every result bit-exact
+against the oracle, and identical to the same instance run alone through fp_matmul / fp_dot."""
 import numpy as np
 import pytest
 
