@@ -78,11 +78,15 @@ enum {
   FP_MM_PLAIN_TC = 6,   /* unpacked, tcgen05 kind::f16 (bf16 operands, fp32 accumulate) */
   FP_MM_RIGHT_TC = 7,   /* right compression on tcgen05 kind::f16: fp16 operands holding two
                            centred residues at Q = 2^10, inner dimension chunked (p <= 3) */
-  FP_MM_LEFT_F32 = 8,   /* left compression (Sec. 7.4, by transposition), FP32 words */
-  FP_MM_PLAIN_F8 = 9    /* unpacked, tcgen05 kind::f8f6f4, fp32 accumulate: the residue bytes
+  FP_MM_LEFT_F32 = 8,   /* left compression (Sec. 7.4): by transposition, (A B)^T = B^T A^T with
+                           the right compression (FP32 words) of A^T, i.e. each word packs two
+                           consecutive rows of A; A^T, B^T and C^T go through context scratch */
+  FP_MM_PLAIN_F8 = 9,   /* unpacked, tcgen05 kind::f8f6f4, fp32 accumulate: the residue bytes
                            are read as e4m3 (r 2^-9, exact for r <= 16); p <= 17 and
                            k (p-1)^2 < 2^24.  A and B 16-byte aligned with lda, ldb multiples
                            of 16 are read in place; other layouts are first copied padded */
+  FP_MM_LEFT_F64 = 10   /* left compression by transposition with FP64 words (DMMA), e rows of A
+                           per word as RIGHT_F64 packs e columns of B */
 };
 
 /* Parameters of one packed representation (Sec. 2.3): q = 2^b, k residues packed per

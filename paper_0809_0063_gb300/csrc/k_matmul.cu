@@ -67,6 +67,24 @@ __global__ void k_copy_pad(const uint8_t* __restrict__ src, int lds, uint8_t* __
   if (bad) flag_error(err, ERR_RANGE);
 }
 
+// dst (rows x cols, leading dimension ldd) = src^T, src (cols x rows, leading dimension lds); only
+// the rows x cols entries of dst are written.
+__global__ void k_transpose_u8(const uint8_t* __restrict__ src, int lds, uint8_t* __restrict__ dst, int ldd,
+                               int rows, int cols) {
+  __shared__ uint8_t tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int sr = c0 + yy, sc = r0 + tx;   // src row = dst column
+    tile[tx][yy] = (sr < cols && sc < rows) ? src[(size_t)sr * lds + sc] : 0;
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int r = r0 + yy, c = c0 + tx;
+    if (r < rows && c < cols) dst[(size_t)r * ldd + c] = tile[yy][tx];
+  }
+}
+
 // ------------------------------------------------------------------ FP64 DMMA
 
 template <int TM, int TN>
@@ -505,9 +523,42 @@ static fp_status mm_imma(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
   return FP_OK;
 }
 
+// Left compression (Sec. 7.4) by transposition: (A B)^T = B^T A^T, whose right compression packs
+// consecutive columns of A^T, i.e. consecutive rows of A, into one word.  A^T (k x m) and B^T
+// (n x k) are written to context scratch slot 1 (range-checked on the way), the right-compressed
+// product (which packs its words in slot 0) computes C^T (n x m) there, and one transpose writes
+// the m x n entries of C.
+static fp_status mm_left(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda, const uint8_t* B,
+                         int ldb, uint8_t* C, int ldc, bool f64, cudaStream_t st) {
+  uint32_t b, e, c;
+  fp_status s = mm_choose(p, (uint64_t)k, f64 ? FP_MM_RIGHT_F64 : FP_MM_RIGHT_F32, &b, &e, &c);
+  if (s != FP_OK) return s;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t at = al((size_t)k * m), bt = al((size_t)n * k), ct = al((size_t)n * m);
+  s = ensure_scratch(ctx, at + bt + ct, 1);
+  if (s != FP_OK) return s;
+  uint8_t* At = (uint8_t*)ctx->scratch2;
+  uint8_t* Bt = At + at;
+  uint8_t* Ct = Bt + bt;
+  dim3 ga((m + 31) / 32, (k + 31) / 32);
+  FP_LAUNCH(ctx, "k_copy_pad", st, k_copy_pad<<<ga, 256, 0, st>>>(A, lda, At, k, m, m, 1, p, ctx->d_err));
+  dim3 gb((k + 31) / 32, (n + 31) / 32);
+  FP_LAUNCH(ctx, "k_copy_pad", st, k_copy_pad<<<gb, 256, 0, st>>>(B, ldb, Bt, n, k, k, 1, p, ctx->d_err));
+  FP_CUDA(cudaGetLastError());
+  s = f64 ? mm_dmma(ctx, p, n, m, k, Bt, k, At, m, Ct, m, false, st)
+          : mm_ffma(ctx, p, n, m, k, Bt, k, At, m, Ct, m, false, st);
+  if (s != FP_OK) return s;
+  dim3 gc((n + 31) / 32, (m + 31) / 32);
+  FP_LAUNCH(ctx, "k_transpose_u8", st, k_transpose_u8<<<gc, 256, 0, st>>>(Ct, m, C, ldc, m, n));
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
 static fp_status run_algo(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
                           const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st) {
   switch (algo) {
+    case FP_MM_LEFT_F64: return mm_left(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, true, st);
+    case FP_MM_LEFT_F32: return mm_left(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, false, st);
     case FP_MM_RIGHT_F64: return mm_dmma(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, false, st);
     case FP_MM_PLAIN_F64: return mm_dmma(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, true, st);
     case FP_MM_RIGHT_F32: return mm_ffma(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, false, st);
@@ -533,6 +584,8 @@ fp_status mm_bound_check(uint32_t p, int k, int algo) {
   switch (algo) {
     case FP_MM_RIGHT_F64:
     case FP_MM_RIGHT_F32: return mm_choose(p, (uint64_t)k, (uint32_t)algo, &b, &e, &c);
+    case FP_MM_LEFT_F64: return mm_choose(p, (uint64_t)k, FP_MM_RIGHT_F64, &b, &e, &c);
+    case FP_MM_LEFT_F32: return mm_choose(p, (uint64_t)k, FP_MM_RIGHT_F32, &b, &e, &c);
     case FP_MM_PLAIN_I8:
       FP_CHECK((uint64_t)k * pp < (1ull << 31), FP_EBOUND, "PLAIN_I8 needs k (p-1)^2 < 2^31");
       return FP_OK;
@@ -545,7 +598,6 @@ fp_status mm_bound_check(uint32_t p, int k, int algo) {
     case FP_MM_RIGHT_TC:
       FP_CHECK(p <= 3 && k <= 32767, FP_EBOUND, "RIGHT_TC needs p <= 3 and k <= 32767");
       return FP_OK;
-    case FP_MM_LEFT_F32: FP_CHECK(false, FP_EUNSUPPORTED, "LEFT_F32 is not implemented");
     default: return FP_OK;   // AUTO, PLAIN_F64, PLAIN_F32: every p <= 251, k <= 2^20
   }
 }

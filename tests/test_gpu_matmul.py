@@ -244,3 +244,55 @@ def test_auto_direct_and_autotuned(env):
     fp.fp_ctx_status(ctx)
     assert fp.fp_ctx_launches(ctx) - l0 <= 3       # the cached variant only, no timing runs
     assert np.array_equal(C.cpu().numpy(), field.matmul_mod(a, b, p))
+
+
+@pytest.mark.parametrize("algo", ["LEFT_F32", "LEFT_F64"])
+@pytest.mark.parametrize("p,m,n,k", [(3, 200, 70, 517), (7, 333, 129, 64), (2, 64, 1, 1000), (31, 1, 50, 300),
+                                     (13, 130, 257, 129)])
+def test_matmul_left_compression(env, algo, p, m, n, k):
+    """Left compression (Sec. 7.4) by transposition: ragged m != n, C with a leading dimension
+    past n whose pad bytes must stay untouched; every entry compared."""
+    fp, torch, dev, ctx = env
+    a, b = workloads.matmul_inputs(p * 31 + m, p, m, k, n)
+    ldc = n + 5
+    C = torch.full((m, ldc), 254, dtype=torch.uint8, device=dev)
+    try:
+        fp.fp_matmul(ctx, p, m, n, k, to_dev(torch, dev, a), k, to_dev(torch, dev, b), n, C, ldc,
+                     getattr(fp, "FP_MM_" + algo))
+    except fp.FpError as e:
+        if e.status == fp.FP_EBOUND:
+            pytest.skip("no packing fits the word for this p, k")
+        raise
+    fp.fp_ctx_status(ctx)
+    got = C.cpu().numpy()
+    assert np.array_equal(got[:, :n], field.matmul_mod(a, b, p))
+    assert np.all(got[:, n:] == 254)
+
+
+@pytest.mark.parametrize("algo", ["LEFT_F32", "LEFT_F64"])
+def test_matmul_left_compression_range_and_grouped(env, algo):
+    """A residue equal to p in A or in B raises the range error; the same algorithm through a
+    grouped call gives the products of its problems."""
+    fp, torch, dev, ctx = env
+    p, m, n, k = 5, 90, 60, 300
+    al = getattr(fp, "FP_MM_" + algo)
+    for which in ("a", "b"):
+        a, b = workloads.matmul_inputs(3, p, m, k, n)
+        a, b = a.copy(), b.copy()
+        (a if which == "a" else b)[5, 7] = p
+        C = torch.empty((m, n), dtype=torch.uint8, device=dev)
+        fp.fp_matmul(ctx, p, m, n, k, to_dev(torch, dev, a), k, to_dev(torch, dev, b), n, C, n, al)
+        with pytest.raises(fp.FpError) as ei:
+            fp.fp_ctx_status(ctx)
+        assert ei.value.status == fp.FP_EINVAL
+    probs, keep = [], []
+    for i, (pp, mm, nn, kk) in enumerate([(3, 70, 40, 200), (7, 33, 99, 150)]):
+        a, b = workloads.matmul_inputs(50 + i, pp, mm, kk, nn)
+        A, B = to_dev(torch, dev, a), to_dev(torch, dev, b)
+        C = torch.empty((mm, nn), dtype=torch.uint8, device=dev)
+        probs.append(fp.fp_mm_problem_of(pp, mm, nn, kk, A, kk, B, nn, C, nn))
+        keep.append((a, b, pp, A, B, C))
+    fp.fp_matmul_grouped(ctx, probs, al)
+    fp.fp_ctx_status(ctx)
+    for a, b, pp, A, B, C in keep:
+        assert np.array_equal(C.cpu().numpy(), field.matmul_mod(a, b, pp))
