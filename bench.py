@@ -1084,12 +1084,12 @@ def main():
     compare = None
     if not args.no_compare and rank == 0:
         compare = {}
-        for name in ["RIGHT_F32", "LEFT_F32", "PLAIN_F32", "RIGHT_F64", "LEFT_F64", "PLAIN_F64", "PLAIN_I8", "PLAIN_TC",
-                     "RIGHT_TC", "PLAIN_F8"]:
+        for name in ["RIGHT_F32", "LEFT_F32", "PLAIN_F32", "RIGHT_F64", "LEFT_F64", "CMM_F64", "PLAIN_F64", "PLAIN_I8",
+                     "PLAIN_TC", "RIGHT_TC", "PLAIN_F8"]:
             row = {}
             for q in prob:
                 al = getattr(fp, "FP_MM_" + name)
-                if name in ("PLAIN_F64", "LEFT_F64") and q["n"] > 1024:
+                if name in ("PLAIN_F64", "LEFT_F64", "CMM_F64") and q["n"] > 1024:
                     continue
                 try:
                     fn = (lambda q=q, al=al: fp.fp_matmul(ctx, q["p"], q["n"], q["n"], q["n"], q["A"], q["n"],
@@ -1109,7 +1109,7 @@ def main():
             compare[name] = row
         # packed DQT+REDQ against the plain product on the same pipe, same inputs
         pairs = (("RIGHT_TC", "PLAIN_TC"), ("RIGHT_F32", "PLAIN_F32"), ("LEFT_F32", "PLAIN_F32"),
-                 ("RIGHT_F64", "PLAIN_F64"), ("LEFT_F64", "PLAIN_F64"))
+                 ("RIGHT_F64", "PLAIN_F64"), ("LEFT_F64", "PLAIN_F64"), ("CMM_F64", "PLAIN_F64"))
         pvp = {}
         for packed, plain in pairs:
             for key, v in compare.get(packed, {}).items():

@@ -85,8 +85,13 @@ enum {
                            are read as e4m3 (r 2^-9, exact for r <= 16); p <= 17 and
                            k (p-1)^2 < 2^24.  A and B 16-byte aligned with lda, ldb multiples
                            of 16 are read in place; other layouts are first copied padded */
-  FP_MM_LEFT_F64 = 10   /* left compression by transposition with FP64 words (DMMA), e rows of A
+  FP_MM_LEFT_F64 = 10,  /* left compression by transposition with FP64 words (DMMA), e rows of A
                            per word as RIGHT_F64 packs e columns of B */
+  FP_MM_CMM_F64 = 11    /* compressed matrix multiplication by the middle product (Sec. 7.1):
+                           d+1 entries of the inner dimension per FP64 word, A reversed, B
+                           forward, q = 2^b > k (p-1)^2, d the largest with (2d+1) b <= 52 so
+                           every word product is exact; C_ij is the digit of q^d mod p.  Needs
+                           d >= 1, i.e. k (p-1)^2 < 2^17, else FP_EBOUND */
 };
 
 /* Parameters of one packed representation (Sec. 2.3): q = 2^b, k residues packed per

@@ -461,7 +461,7 @@ static fp_status check_matmul(uint32_t p, int m, int n, int k, const uint8_t* A,
            FP_EINVAL, "fp_matmul: sizes m=%d n=%d k=%d outside [1, 2^20]", m, n, k);
   FP_CHECK(lda >= k && ldb >= n && ldc >= n, FP_EINVAL, "fp_matmul: leading dimensions too small");
   FP_CHECK(A && B && C, FP_EINVAL, "fp_matmul: null array");
-  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_LEFT_F64, FP_EINVAL, "bad algo %d", algo);
+  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_CMM_F64, FP_EINVAL, "bad algo %d", algo);
   return FP_OK;
 }
 
@@ -477,7 +477,7 @@ extern "C" fp_status fp_matmul_grouped(fp_ctx ctx, const fp_mm_problem* problems
                                        void* stream) {
   FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_matmul_grouped: ctx is NULL");
   FP_CHECK(count == 0 || problems != nullptr, FP_EINVAL, "fp_matmul_grouped: problems is NULL");
-  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_LEFT_F64, FP_EINVAL, "bad algo %d", algo);
+  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_CMM_F64, FP_EINVAL, "bad algo %d", algo);
   for (size_t i = 0; i < count; ++i) {
     const fp_mm_problem& x = problems[i];
     fp_status s = check_matmul(x.p, x.m, x.n, x.k, x.A, x.lda, x.B, x.ldb, x.C, x.ldc, algo);

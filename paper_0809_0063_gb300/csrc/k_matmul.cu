@@ -156,6 +156,99 @@ __global__ void __launch_bounds__(128) k_mm_dmma(const uint8_t* __restrict__ A, 
   }
 }
 
+// ------------------------------------------------------------------ CMM: middle product (Sec. 7.1)
+//
+// A m x k packed along rows, d+1 consecutive entries of the inner dimension per FP64 word and
+// REVERSED (entry j(d+1)+i at q^(d-i)); B k x n packed along columns, FORWARD (entry j(d+1)+i at
+// q^i).  The word product of a row block and a column block then holds the block's dot product
+// as its digit of q^d, and summing the word products over the kw = ceil(k/(d+1)) blocks sums the
+// dot products there.  q = 2^b > k (p-1)^2 keeps every digit below q, and (2d+1) b <= 52 keeps
+// every word product and partial sum an exact integer below 2^52, so the digit is read off
+// exactly: C_ij = ((w >> d b) & (q - 1)) mod p.
+
+// CA[r][j] = sum_i A[r][j(d+1)+i] q^(d-i)  (m x kw); CB[j][c] = sum_i B[j(d+1)+i][c] q^i  (kw x n).
+__global__ void k_cmm_pack(const uint8_t* __restrict__ A, int lda, const uint8_t* __restrict__ B, int ldb,
+                           double* __restrict__ CA, double* __restrict__ CB, int m, int n, int k, int kw, uint32_t d1,
+                           uint32_t b, uint32_t p, uint32_t* err) {
+  const uint64_t na = (uint64_t)m * kw, total = na + (uint64_t)kw * n;
+  uint32_t bad = 0;
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t w = 0;
+    if (idx < na) {
+      const int r = (int)(idx / kw), j = (int)(idx % kw);
+      for (uint32_t i = 0; i < d1; ++i) {          // Horner from entry 0: reversed order
+        const int l = j * (int)d1 + (int)i;
+        const uint32_t v = l < k ? A[(size_t)r * lda + l] : 0u;
+        bad |= v >= p;
+        w = (w << b) | v;
+      }
+      CA[idx] = (double)w;
+    } else {
+      const uint64_t i2 = idx - na;
+      const int j = (int)(i2 / n), c = (int)(i2 % n);
+      for (int i = (int)d1 - 1; i >= 0; --i) {     // forward: entry 0 lowest
+        const int l = j * (int)d1 + i;
+        const uint32_t v = l < k ? B[(size_t)l * ldb + c] : 0u;
+        bad |= v >= p;
+        w = (w << b) | v;
+      }
+      CB[i2] = (double)w;
+    }
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// C = (CA x CB) digit d mod p on DMMA (mma.sync m8n8k4 f64), the same warp tiling as k_mm_dmma.
+template <int TM, int TN>
+__global__ void __launch_bounds__(128) k_mm_cmm(const double* __restrict__ CA, const double* __restrict__ CB,
+                                                uint8_t* __restrict__ C, int ldc, int m, int n, int kw,
+                                                uint32_t shift, uint64_t qmask, DivP dv, uint32_t p) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int r0 = (blockIdx.y * 2 + (warp >> 1)) * (8 * TM);
+  const int c0 = (blockIdx.x * 2 + (warp & 1)) * (8 * TN);
+  double acc[TM][TN][2];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+  for (int k0 = 0; k0 < kw; k0 += 4) {
+    const int kk = k0 + t;
+    double a[TM], bf[TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int row = r0 + 8 * i + g;
+      a[i] = (row < m && kk < kw) ? CA[(size_t)row * kw + kk] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int col = c0 + 8 * j + g;
+      bf[j] = (col < n && kk < kw) ? CB[(size_t)kk * n + col] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                     : "+d"(acc[i][j][0]), "+d"(acc[i][j][1])
+                     : "d"(a[i]), "d"(bf[j]));
+  }
+  // accumulator (i, j, h) holds row r0 + 8i + g, column c0 + 8j + 2t + h
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = r0 + 8 * i + g, col = c0 + 8 * j + 2 * t + h;
+        if (row < m && col < n) {
+          const uint64_t w = (uint64_t)acc[i][j][h];        // exact integer < 2^52
+          C[(size_t)row * ldc + col] = (uint8_t)modp32((uint32_t)((w >> shift) & qmask), dv, p);
+        }
+      }
+}
+
 // ------------------------------------------------------------------ FP32 FFMA (packed e=2 / plain e=1)
 
 static constexpr int FF_BM = 128, FF_BN = 128, FF_BK = 8;
@@ -523,6 +616,50 @@ static fp_status mm_imma(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
   return FP_OK;
 }
 
+// The middle-product parameters: b with 2^b > k (p-1)^2 (strict, Eq. lower), d + 1 entries per
+// word, d the largest with (2d+1) b <= 52 (every word product and sum an exact FP64 integer).
+static fp_status cmm_choose(uint32_t p, uint64_t k, uint32_t* b_out, uint32_t* d1_out) {
+  const uint64_t D = k * (uint64_t)(p - 1) * (p - 1);
+  uint32_t b = 1;
+  while (b < 64 && (1ull << b) <= D) ++b;
+  const uint32_t d = b <= 52 ? (52 / b - 1) / 2 : 0;
+  FP_CHECK(d >= 1, FP_EBOUND, "CMM_F64 needs k (p-1)^2 < 2^17 (k=%llu p=%u)", (unsigned long long)k, p);
+  *b_out = b;
+  *d1_out = d + 1;
+  return FP_OK;
+}
+
+static fp_status mm_cmm(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda, const uint8_t* B,
+                        int ldb, uint8_t* C, int ldc, cudaStream_t st) {
+  uint32_t b, d1;
+  fp_status s = cmm_choose(p, (uint64_t)k, &b, &d1);
+  if (s != FP_OK) return s;
+  const int kw = (k + (int)d1 - 1) / (int)d1;
+  const size_t ca = (((size_t)m * kw * sizeof(double)) + 255) & ~(size_t)255;
+  s = ensure_scratch(ctx, ca + (size_t)kw * n * sizeof(double));
+  if (s != FP_OK) return s;
+  double* CA = (double*)ctx->scratch;
+  double* CB = (double*)((uint8_t*)ctx->scratch + ca);
+  const uint64_t total = (uint64_t)m * kw + (uint64_t)kw * n;
+  const int pg = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->num_sms * 16);
+  FP_LAUNCH(ctx, "k_cmm_pack", st, k_cmm_pack<<<pg, 256, 0, st>>>(A, lda, B, ldb, CA, CB, m, n, k, kw, d1, b, p,
+                                                                  ctx->d_err));
+  const uint32_t shift = (d1 - 1) * b;
+  const uint64_t qmask = (1ull << b) - 1;
+  const uint64_t warps_big = (uint64_t)((m + 31) / 32) * ((n + 31) / 32);
+  if (warps_big >= (uint64_t)ctx->num_sms * 8) {
+    dim3 grid((n + 63) / 64, (m + 63) / 64);
+    FP_LAUNCH(ctx, "k_mm_cmm", st, k_mm_cmm<4, 4><<<grid, 128, 0, st>>>(CA, CB, C, ldc, m, n, kw, shift, qmask,
+                                                                        make_divp(p), p));
+  } else {
+    dim3 grid((n + 31) / 32, (m + 31) / 32);
+    FP_LAUNCH(ctx, "k_mm_cmm", st, k_mm_cmm<2, 2><<<grid, 128, 0, st>>>(CA, CB, C, ldc, m, n, kw, shift, qmask,
+                                                                        make_divp(p), p));
+  }
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
 // Left compression (Sec. 7.4) by transposition: (A B)^T = B^T A^T, whose right compression packs
 // consecutive columns of A^T, i.e. consecutive rows of A, into one word.  A^T (k x m) and B^T
 // (n x k) are written to context scratch slot 1 (range-checked on the way), the right-compressed
@@ -557,6 +694,7 @@ static fp_status mm_left(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
 static fp_status run_algo(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
                           const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st) {
   switch (algo) {
+    case FP_MM_CMM_F64: return mm_cmm(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, st);
     case FP_MM_LEFT_F64: return mm_left(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, true, st);
     case FP_MM_LEFT_F32: return mm_left(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, false, st);
     case FP_MM_RIGHT_F64: return mm_dmma(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, false, st);
@@ -585,6 +723,7 @@ fp_status mm_bound_check(uint32_t p, int k, int algo) {
     case FP_MM_RIGHT_F64:
     case FP_MM_RIGHT_F32: return mm_choose(p, (uint64_t)k, (uint32_t)algo, &b, &e, &c);
     case FP_MM_LEFT_F64: return mm_choose(p, (uint64_t)k, FP_MM_RIGHT_F64, &b, &e, &c);
+    case FP_MM_CMM_F64: return cmm_choose(p, (uint64_t)k, &b, &e);
     case FP_MM_LEFT_F32: return mm_choose(p, (uint64_t)k, FP_MM_RIGHT_F32, &b, &e, &c);
     case FP_MM_PLAIN_I8:
       FP_CHECK((uint64_t)k * pp < (1ull << 31), FP_EBOUND, "PLAIN_I8 needs k (p-1)^2 < 2^31");

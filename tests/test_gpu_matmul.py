@@ -296,3 +296,43 @@ def test_matmul_left_compression_range_and_grouped(env, algo):
     fp.fp_ctx_status(ctx)
     for a, b, pp, A, B, C in keep:
         assert np.array_equal(C.cpu().numpy(), field.matmul_mod(a, b, pp))
+
+
+@pytest.mark.parametrize("p,m,n,k", [(3, 200, 70, 517), (7, 33, 129, 1000), (2, 64, 1, 4000), (13, 130, 257, 129),
+                                     (5, 1, 1, 1), (3, 96, 96, 16383), (2, 50, 60, 101), (3, 40, 41, 62)])
+def test_matmul_cmm_middle_product(env, p, m, n, k):
+    """Compressed matrix multiplication by the middle product (Sec. 7.1) on FP64 DMMA: ragged
+    shapes, k not a multiple of d+1 (zero-padded last block), d+1 = 2, 3 (p = 3, k = 62) and 4
+    (p = 2, k = 101) entries per word, all-(p-1) inputs at the largest k of the test, C's pad
+    columns untouched."""
+    fp, torch, dev, ctx = env
+    a, b = workloads.matmul_inputs(p * 17 + k, p, m, k, n)
+    if k == 16383:
+        a, b = np.full_like(a, p - 1), np.full_like(b, p - 1)
+    ldc = n + 3
+    C = torch.full((m, ldc), 254, dtype=torch.uint8, device=dev)
+    fp.fp_matmul(ctx, p, m, n, k, to_dev(torch, dev, a), k, to_dev(torch, dev, b), n, C, ldc, fp.FP_MM_CMM_F64)
+    fp.fp_ctx_status(ctx)
+    got = C.cpu().numpy()
+    assert np.array_equal(got[:, :n], field.matmul_mod(a, b, p))
+    assert np.all(got[:, n:] == 254)
+
+
+def test_matmul_cmm_bound_and_range(env):
+    """k (p-1)^2 >= 2^17 leaves no d >= 1 (refused on the host, nothing enqueued); an entry equal
+    to p raises the range error."""
+    fp, torch, dev, ctx = env
+    A = torch.zeros((8, 200), dtype=torch.uint8, device=dev)
+    C = torch.zeros((8, 8), dtype=torch.uint8, device=dev)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_matmul(ctx, 31, 8, 8, 200, A, 200, A, 8, C, 8, fp.FP_MM_CMM_F64)
+    assert ei.value.status == fp.FP_EBOUND
+    p, m, n, k = 7, 40, 30, 200
+    a, b = workloads.matmul_inputs(5, p, m, k, n)
+    b = b.copy()
+    b[199, 29] = p
+    C = torch.empty((m, n), dtype=torch.uint8, device=dev)
+    fp.fp_matmul(ctx, p, m, n, k, to_dev(torch, dev, a), k, to_dev(torch, dev, b), n, C, n, fp.FP_MM_CMM_F64)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_ctx_status(ctx)
+    assert ei.value.status == fp.FP_EINVAL
