@@ -315,7 +315,7 @@ def run_polymul(args, ws, rank, local):
     torch.cuda.synchronize()
     fp.fp_ctx_profile(ctx, 0)
     names = ["k_polymul_small", "k_polymul_word_bulk", "k_polymul_word", "k_polymul_plain_small", "k_polymul_fqt",
-             "k_polymul_plain_big"]
+             "k_polymul_kara", "k_polymul_plain_big"]
     dom, dms, dn = None, 0.0, 0
     for nm in names:
         c, ms = fp.fp_ctx_profile_read(ctx, nm)
@@ -353,6 +353,32 @@ def run_polymul(args, ws, rank, local):
         if isinstance(compare.get("PLAIN"), float):
             compare["best_packed_over_plain"] = max(v for k, v in compare.items()
                                                     if k.startswith("DQT") and isinstance(v, float)) / compare["PLAIN"]
+    # large degrees (blocked FQT, Sec. 5.2): the schoolbook over the u64 block words against the
+    # Karatsuba splitting of the same words and the plain product, same inputs, L2 flushed
+    large = {}
+    if not args.no_compare:
+        nl = 1 << 14
+        for dl in (511, 1023):
+            al_, bl_ = workloads.polymul_inputs(1000 + dl, p, nl, dl, dl)
+            Al, Bl = torch.from_numpy(al_).to(dev), torch.from_numpy(bl_).to(dev)
+            Cl = torch.empty((nl, 2 * dl + 1), dtype=torch.uint8, device=dev)
+            rl = np.random.default_rng(dl).choice(nl, 8, replace=False)
+            want = field.polymul_mod(al_[rl], bl_[rl], p)
+            row = {}
+            for nm in ("PLAIN", "DQT_U64", "KARATSUBA"):
+                al = getattr(fp, "FP_ALGO_" + nm)
+                fn = lambda al=al: fp.fp_polymul_batched(ctx, p, Al, dl, Bl, dl, Cl, nl, al)
+                Cl.zero_()
+                fn()
+                torch.cuda.synchronize()
+                fp.fp_ctx_status(ctx)
+                assert np.array_equal(Cl[torch.from_numpy(rl).to(dev)].cpu().numpy(), want), f"parity {nm} deg {dl}"
+                t = statistics.median(_timed(torch, stream, fn, 5, flush))
+                row[nm] = {"ms": t, "F_p MAC/s": nl * (dl + 1) ** 2 / (t / 1e3)}
+            row["karatsuba_over_schoolbook_fqt"] = row["DQT_U64"]["ms"] / row["KARATSUBA"]["ms"]
+            row["karatsuba_over_plain"] = row["PLAIN"]["ms"] / row["KARATSUBA"]["ms"]
+            large[f"2^14 pairs, degree {dl} x {dl}"] = row
+            del Al, Bl, Cl
     # the other HBM-bound steps of the path on their own (a2 DQT pack, a4-a5 REDQ unpack, and
     # the dot product): GB/s of algorithmic bytes, L2 flushed before each call
     hbm_rows = {}
@@ -445,7 +471,7 @@ def run_polymul(args, ws, rank, local):
             "e2e": {"value": ws * batch * mpp / (te / 1e3), "unit": "F_p MAC/s",
                     "h2d_bytes_per_step": batch * (da + db + 2), "d2h_bytes_per_step": batch * (da + db + 1)},
             "gpu_launches": launches, "clocks": clk.summary(), "compare_same_inputs_2^26": compare,
-            "other_hbm_steps": hbm_rows,
+            "other_hbm_steps": hbm_rows, "large_degree_same_inputs": large,
         }))
     fp.fp_ctx_destroy(ctx)
 

@@ -61,7 +61,9 @@ enum {
   FP_ALGO_DQT_F64 = 2, /* packed words of the given type */
   FP_ALGO_DQT_U64 = 3,
   FP_ALGO_DQT_F32 = 4,
-  FP_ALGO_DQT_U32 = 5
+  FP_ALGO_DQT_U32 = 5,
+  FP_ALGO_KARATSUBA = 6 /* fp_polymul_batched only: the blocked FQT's u64 words multiplied as word
+                           polynomials by Karatsuba splitting (Sec. 5.2, Fig. pmkara) */
 };
 
 /* Algorithm selectors for fp_matmul. */
@@ -193,7 +195,10 @@ fp_status fp_dqt_unpack_redq(fp_ctx ctx, const fp_dqt_params* prm, const void* w
  * A: device uint8 [batch][dega+1], B: [batch][degb+1], C: [batch][dega+degb+1], coefficients
  * lowest degree first.  DQT algos pack each operand in one word when the product fits one
  * word, else split into blocks of d+1 coefficients (FQT, Sec. 5.2) and accumulate the block
- * products in words before one REDQ per result block.  dega, degb <= 1023.
+ * products in words before one REDQ per result block.  FP_ALGO_KARATSUBA forms the same
+ * block-product words by Karatsuba splitting of the word polynomials (zero-padded to m 2^L
+ * words, 3^L leaf products, exact in Z/2^64 since every result word is below 2^64 under the
+ * FQT bound) and then reduces them the same way.  dega, degb <= 1023.
  * Errors: FP_EINVAL, FP_EBOUND (a forced word type cannot hold even d = 0). */
 fp_status fp_polymul_batched(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t dega,
                              const uint8_t* B, uint32_t degb, uint8_t* C, size_t batch, int algo,

@@ -20,7 +20,8 @@ STATUS_NAMES = ["FP_OK", "FP_EINVAL", "FP_EBOUND", "FP_ENOMEM", "FP_ECUDA", "FP_
 # word types (fp_word)
 FP_WORD_F64, FP_WORD_U64, FP_WORD_F32, FP_WORD_U32 = range(4)
 # polymul / dot algorithms
-FP_ALGO_AUTO, FP_ALGO_PLAIN, FP_ALGO_DQT_F64, FP_ALGO_DQT_U64, FP_ALGO_DQT_F32, FP_ALGO_DQT_U32 = range(6)
+FP_ALGO_AUTO, FP_ALGO_PLAIN, FP_ALGO_DQT_F64, FP_ALGO_DQT_U64, FP_ALGO_DQT_F32, FP_ALGO_DQT_U32, \
+    FP_ALGO_KARATSUBA = range(7)
 # matmul algorithms
 (FP_MM_AUTO, FP_MM_RIGHT_F64, FP_MM_RIGHT_F32, FP_MM_PLAIN_F64, FP_MM_PLAIN_F32, FP_MM_PLAIN_I8,
  FP_MM_PLAIN_TC, FP_MM_RIGHT_TC, FP_MM_LEFT_F32, FP_MM_PLAIN_F8, FP_MM_LEFT_F64, FP_MM_CMM_F64) = range(12)

@@ -437,7 +437,7 @@ extern "C" fp_status fp_polymul_batched(fp_ctx ctx, uint32_t p, const uint8_t* A
   FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_polymul_batched: ctx is NULL");
   FP_CHECK(p >= 2 && p <= 251 && is_prime(p), FP_EINVAL, "p=%u not a prime <= 251", p);
   FP_CHECK(dega <= 1023 && degb <= 1023, FP_EINVAL, "degrees must be <= 1023");
-  FP_CHECK(algo >= FP_ALGO_AUTO && algo <= FP_ALGO_DQT_U32, FP_EINVAL, "bad algo %d", algo);
+  FP_CHECK(algo >= FP_ALGO_AUTO && algo <= FP_ALGO_KARATSUBA, FP_EINVAL, "bad algo %d", algo);
   if (batch == 0) return FP_OK;
   FP_CHECK(A && B && C, FP_EINVAL, "fp_polymul_batched: null array");
   return launch_polymul(ctx, p, A, dega, B, degb, C, batch, algo, as_stream(stream));

@@ -296,6 +296,50 @@ __device__ __forceinline__ void fill_pair_table(uint8_t* T, const RedqParams& P)
   }
 }
 
+// Packs src[0..k) in blocks of d+1 coefficients: word i = sum_j src[i(d+1) + j] q^j for
+// i < nwords (zero past k), written to w[i]; residues >= p set bad.
+__device__ __forceinline__ void fqt_pack(const uint8_t* __restrict__ src, uint32_t k, uint32_t d1, uint32_t nwords,
+                                         const RedqParams& P, uint64_t* w, uint32_t& bad) {
+  for (uint32_t i = threadIdx.x; i < nwords; i += blockDim.x) {
+    uint64_t v64 = 0;
+    for (int j = (int)d1 - 1; j >= 0; --j) {
+      uint32_t idx = i * d1 + j;
+      uint32_t v = idx < k ? src[idx] : 0u;
+      bad |= v >= P.p;
+      v64 = (v64 << P.b) | v;
+    }
+    w[i] = v64;
+  }
+}
+
+// REDQ_{2d+1} of the nw product words word_at(o) into res, then the overlap of consecutive
+// blocks: coefficient j = res[j / (d+1)][j mod (d+1)] + res[j / (d+1) - 1][j mod (d+1) + d + 1]
+// mod p, for j < kc.  All threads of the block call it (whole warps run the REDQ loop, so the
+// shuffle-table lookups see 32 active lanes).
+template <typename WordAt>
+__device__ __forceinline__ void fqt_reduce_product(WordAt word_at, uint32_t nw, uint32_t kc, uint32_t d1,
+                                                   const RedqParams& P, const Corrector& C, uint8_t* res,
+                                                   uint8_t* __restrict__ Cout) {
+  const uint32_t nd = 2 * d1 - 1;               // residues per output word
+  for (uint32_t base = 0; base < nw; base += blockDim.x) {
+    uint32_t o = base + threadIdx.x;
+    const bool own = o < nw;
+    uint64_t acc = own ? word_at(o) : 0;
+    uint8_t* out = res + (own ? o : 0) * nd;
+    redq_word<uint64_t>(acc, P, C, [&](uint32_t i, uint32_t mu) { if (own) out[i] = (uint8_t)mu; });
+  }
+  __syncthreads();
+  // j / d1 = umulhi(j, ceil(2^32 / d1)), exact for j d1 < 2^32 (the multiplier needs d1 > 1)
+  const uint32_t md = d1 > 1 ? 0xffffffffu / d1 + 1u : 0u;
+  for (uint32_t j = threadIdx.x; j < kc; j += blockDim.x) {
+    uint32_t o = d1 > 1 ? __umulhi(j, md) : j, r = j - o * d1;
+    uint32_t v = o < nw ? res[o * nd + r] : 0u;
+    if (o >= 1 && r + d1 < nd) v += res[(o - 1) * nd + r + d1];
+    if (v >= P.p) v -= P.p;
+    Cout[j] = (uint8_t)v;
+  }
+}
+
 // Blocked FQT (Sec. 5.2): P = sum_i P_i (X^{d+1})^i with each P_i (d+1 coefficients) in one
 // u64 word at q = 2^b; output word t = sum_i P_i Q_{t-i} accumulated in the word (delayed
 // reduction, the planner keeps every digit below q), then REDQ_{2d+1}; the residues of words t
@@ -307,52 +351,19 @@ __device__ __forceinline__ void fqt_block_product(const uint8_t* __restrict__ A,
                                   const RedqParams& P, const Corrector& C, uint64_t* wa, uint64_t* wb,
                                   uint8_t* res, uint32_t& bad) {
   const uint32_t na = (ka + d1 - 1) / d1, nb = (kb + d1 - 1) / d1;
-  const uint32_t nw = na + nb - 1;              // output words
-  const uint32_t kc = ka + kb - 1;
-  const uint32_t nd = 2 * d1 - 1;               // residues per output word
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < na; i += blockDim.x) {
-    uint64_t w = 0;
-    for (int j = (int)d1 - 1; j >= 0; --j) {
-      uint32_t idx = i * d1 + j;
-      uint32_t v = idx < ka ? A[idx] : 0u;
-      bad |= v >= P.p;
-      w = (w << P.b) | v;
-    }
-    wa[i] = w;
-  }
-  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
-    uint64_t w = 0;
-    for (int j = (int)d1 - 1; j >= 0; --j) {
-      uint32_t idx = i * d1 + j;
-      uint32_t v = idx < kb ? B[idx] : 0u;
-      bad |= v >= P.p;
-      w = (w << P.b) | v;
-    }
-    wb[i] = w;
-  }
+  fqt_pack(A, ka, d1, na, P, wa, bad);
+  fqt_pack(B, kb, d1, nb, P, wb, bad);
   __syncthreads();
-  // whole warps iterate so that the shuffle-table lookups see 32 active lanes
-  for (uint32_t base = 0; base < nw; base += blockDim.x) {
-    uint32_t o = base + threadIdx.x;
-    uint64_t acc = 0;
-    if (o < nw) {
-      uint32_t lo = o + 1 > nb ? o + 1 - nb : 0;
-      uint32_t hi = o < na - 1 ? o : na - 1;
-      for (uint32_t i = lo; i <= hi; ++i) acc += wa[i] * wb[o - i];
-    }
-    uint8_t* out = res + (o < nw ? o : 0) * nd;
-    bool own = o < nw;
-    redq_word<uint64_t>(acc, P, C, [&](uint32_t i, uint32_t mu) { if (own) out[i] = (uint8_t)mu; });
-  }
-  __syncthreads();
-  for (uint32_t j = threadIdx.x; j < kc; j += blockDim.x) {
-    uint32_t o = j / d1, r = j - o * d1;
-    uint32_t v = o < nw ? res[o * nd + r] : 0u;
-    if (o >= 1 && r + d1 < nd) v += res[(o - 1) * nd + r + d1];
-    if (v >= P.p) v -= P.p;
-    Cout[j] = (uint8_t)v;
-  }
+  fqt_reduce_product(
+      [&](uint32_t o) {
+        uint32_t lo = o + 1 > nb ? o + 1 - nb : 0;
+        uint32_t hi = o < na - 1 ? o : na - 1;
+        uint64_t acc = 0;
+        for (uint32_t i = lo; i <= hi; ++i) acc += wa[i] * wb[o - i];
+        return acc;
+      },
+      na + nb - 1, ka + kb - 1, d1, P, C, res, Cout);
 }
 
 // Sticky error reporting from device code.

@@ -630,6 +630,208 @@ bool fqt_params(uint32_t p, uint32_t ka, uint32_t kb, uint32_t* d1_out, uint32_t
   return best_d1 >= 1;
 }
 
+// ------------------------------------------------------------------ Karatsuba FQT
+
+// Karatsuba version of the blocked FQT (Sec. 5.2; the Karatsuba timings of Fig. pmkara).  The
+// operands' word polynomials (blocks of d+1 coefficients in u64 words at q = 2^b, exactly as in
+// the blocked FQT) are zero-padded to N = m 2^L words and split L times into low half, high half
+// and their sum, giving T = 3^L leaf polynomials of m words each; the leaf products are
+// recombined by R = P0 + X^c (P2 - P0 - P1) + X^{2c} P1.  Every step is in Z / 2^64, and
+// Karatsuba's identity holds in any commutative ring, so each output word is the same integer
+// as the schoolbook sum, which the blocked FQT's digit bound keeps below 2^64: REDQ and the
+// overlap of the blocks are unchanged.
+struct KaraShape {
+  uint32_t d1, L, m, N, T;
+};
+
+constexpr uint32_t KARA_PADL = 4;   // zero words below each right-hand leaf (the window reads down to -4)
+constexpr uint32_t KARA_PADS = 8;   // zero words per right-hand leaf in all (reads go up to m + 2)
+
+// Shared memory of k_polymul_kara, in bytes: levels 0 (2N words), the leaves of A (T m) and of
+// B (T (m + 8)), the leaf products (2 T m), then the nw (2d + 1) REDQ residues.
+static size_t kara_smem_bytes(const KaraShape& S, uint32_t nw) {
+  const size_t words = 2 * (size_t)S.N + (size_t)S.T * S.m + (size_t)S.T * (S.m + KARA_PADS) + 2 * (size_t)S.T * S.m;
+  return words * 8 + (size_t)nw * (2 * S.d1 - 1);
+}
+
+__global__ void __launch_bounds__(256) k_polymul_kara(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
+                                                      uint8_t* __restrict__ Cout, uint64_t batch, uint32_t ka,
+                                                      uint32_t kb, KaraShape S, RedqParams P, uint32_t* err) {
+  extern __shared__ __align__(16) uint64_t ksm[];
+  __shared__ uint8_t ptab[1024];
+  fill_pair_table(ptab, P);
+  __syncthreads();
+  Corrector C;
+  C.init(P, ptab);
+  const uint32_t m = S.m, T = S.T, N = S.N, L = S.L, d1 = S.d1;
+  const uint32_t SE = m + KARA_PADS;
+  uint64_t* wa = ksm;                               // level 0 of A and B: [N] each
+  uint64_t* wb = wa + N;
+  uint64_t* ea = wb + N;                            // leaves of A: [T][m]
+  uint64_t* eb = ea + (size_t)T * m;                // leaves of B: [T][m + 8], values from word 4
+  uint64_t* xs = eb + (size_t)T * SE;               // [T][2m] leaf products (evaluation scratch before)
+  uint64_t* ys = ea;                                // interpolation scratch (ea, eb are dead by then)
+  uint8_t* res = (uint8_t*)(xs + 2 * (size_t)T * m);
+  const uint32_t na = (ka + d1 - 1) / d1, nb = (kb + d1 - 1) / d1;
+  const uint32_t nw = na + nb - 1, kc = ka + kb - 1;
+  const uint32_t G = (2 * m + 2) / 4;               // groups of four output words per leaf product
+  const uint32_t GH = (G + 1) / 2;                  // work items per leaf: groups g and g + GH
+  uint32_t bad = 0;
+  for (uint64_t t = blockIdx.x; t < batch; t += gridDim.x) {
+    __syncthreads();
+    fqt_pack(A + t * ka, ka, d1, N, P, wa, bad);
+    fqt_pack(B + t * kb, kb, d1, N, P, wb, bad);
+    __syncthreads();
+    // Evaluation.  Level l holds 3^l segments of h = m 2^(L-l) words; segment s is the low half
+    // (s mod 3 = 0), the high half (1) or the sum of both halves (2) of segment s / 3 of level
+    // l - 1.  Levels with L - l even live in ea / eb, the others in xs (A) and xs + T m (B).
+    uint32_t nseg = 1;
+    for (uint32_t l = 1; l <= L; ++l) {
+      const uint32_t h = m << (L - l);
+      nseg *= 3;
+      const uint64_t* sa = l == 1 ? wa : (((L - l + 1) & 1) ? xs : ea);
+      const uint64_t* sb = l == 1 ? wb : (((L - l + 1) & 1) ? xs + (size_t)T * m : eb);
+      uint64_t* da = ((L - l) & 1) ? xs : ea;
+      uint64_t* db = ((L - l) & 1) ? xs + (size_t)T * m : eb;
+      const bool last = l == L;
+      // u / h = umulhi(u, ceil(2^32 / h)), exact for u h < 2^32 (the multiplier needs h > 1)
+      const uint32_t mh = h > 1 ? 0xffffffffu / h + 1u : 0u;
+      for (uint32_t u = threadIdx.x; u < nseg * h; u += blockDim.x) {
+        const uint32_t sg = h > 1 ? __umulhi(u, mh) : u, j = u - sg * h;
+        const uint32_t par = sg / 3, dg = sg - par * 3;
+        const uint32_t src = par * 2 * h + (dg == 1 ? h : 0) + j;
+        uint64_t va = sa[src], vb = sb[src];
+        if (dg == 2) {
+          va += sa[src + h];
+          vb += sb[src + h];
+        }
+        da[u] = va;
+        db[last ? sg * SE + KARA_PADL + j : u] = vb;
+      }
+      if (last)
+        for (uint32_t u = threadIdx.x; u < T * KARA_PADS; u += blockDim.x) {
+          const uint32_t sg = u / KARA_PADS, r = u - sg * KARA_PADS;
+          eb[sg * SE + (r < KARA_PADL ? r : m + r)] = 0;
+        }
+      __syncthreads();
+    }
+    // Leaf products, four consecutive output words 4g..4g+3 per pass over a sliding window of
+    // B's leaf (w_r = b[o0 + r - i]), four steps per round (eight shared loads per sixteen word
+    // products).  Group g runs min(m - 1, 4g + 3) - max(0, 4g - m + 1) + 1 steps, about 4g + 4
+    // for g < G / 2 and 2m - 4g after, so work item u = gp T + leaf takes groups gp and gp + GH
+    // (about m + 4 steps in all) and the lanes of a warp, sharing gp or spanning a few
+    // neighbouring values, run each pass for nearly the same number of steps.  The launch gives
+    // the block T GH threads (whole warps, 128 to 256), so small products take one round.
+    const uint32_t mt = 0xffffffffu / T + 1u;       // u / T = umulhi(u, mt) (T >= 3, u T < 2^32)
+    for (uint32_t u = threadIdx.x; u < T * GH; u += blockDim.x) {
+      const uint32_t gp = __umulhi(u, mt), leaf = u - gp * T;
+      const uint64_t* a = ea + (size_t)leaf * m;
+      const uint64_t* bq = eb + (size_t)leaf * SE + KARA_PADL;
+      uint64_t* out = xs + 2 * (size_t)leaf * m;
+      const int no = 2 * (int)m - 1;
+      for (uint32_t g = gp; g < G; g += GH) {
+        const int o0 = 4 * (int)g;
+        const int ilo = max(0, o0 - (int)m + 1), ihi = min((int)m - 1, o0 + 3);
+        uint64_t w0 = bq[o0 - ilo], w1 = bq[o0 + 1 - ilo], w2 = bq[o0 + 2 - ilo], w3 = bq[o0 + 3 - ilo];
+        uint64_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        int i = ilo;
+        for (; i + 3 <= ihi; i += 4) {
+          const uint64_t a0 = a[i], a1 = a[i + 1], a2 = a[i + 2], a3 = a[i + 3];
+          const uint64_t v1 = bq[o0 - i - 1], v2 = bq[o0 - i - 2], v3 = bq[o0 - i - 3], v4 = bq[o0 - i - 4];
+          c0 += a0 * w0 + a1 * v1 + a2 * v2 + a3 * v3;
+          c1 += a0 * w1 + a1 * w0 + a2 * v1 + a3 * v2;
+          c2 += a0 * w2 + a1 * w1 + a2 * w0 + a3 * v1;
+          c3 += a0 * w3 + a1 * w2 + a2 * w1 + a3 * w0;
+          w3 = v1;
+          w2 = v2;
+          w1 = v3;
+          w0 = v4;
+        }
+        for (; i <= ihi; ++i) {
+          const uint64_t av = a[i];
+          c0 += av * w0;
+          c1 += av * w1;
+          c2 += av * w2;
+          c3 += av * w3;
+          w3 = w2;
+          w2 = w1;
+          w1 = w0;
+          w0 = bq[o0 - i - 1];
+        }
+        if (o0 < no) out[o0] = c0;
+        if (o0 + 1 < no) out[o0 + 1] = c1;
+        if (o0 + 2 < no) out[o0 + 2] = c2;
+        if (o0 + 3 < no) out[o0 + 3] = c3;
+      }
+    }
+    __syncthreads();
+    // Interpolation.  Parent u of level l - 1 from its children 3u, 3u+1, 3u+2 of level l
+    // (products of 2c - 1 words at stride 2c, c = m 2^(L-l)): R = P0 + X^c (P2 - P0 - P1) +
+    // X^(2c) P1, 4c - 1 words at stride 4c.  Level k lives in xs when L - k is even, else in ys.
+    uint32_t npar = T;
+    for (uint32_t l = L; l >= 1; --l) {
+      const uint32_t c = m << (L - l);
+      npar /= 3;
+      const uint64_t* src = ((L - l) & 1) ? ys : xs;
+      uint64_t* dst = ((L - l + 1) & 1) ? ys : xs;
+      const uint32_t len = 4 * c - 1;
+      const uint32_t ml = 0xffffffffu / len + 1u;   // u / len = umulhi(u, ml) (len >= 3, u len < 2^32)
+      for (uint32_t u = threadIdx.x; u < npar * len; u += blockDim.x) {
+        const uint32_t par = __umulhi(u, ml), x = u - par * len;
+        const uint64_t* P0 = src + 6 * (size_t)c * par;
+        const uint64_t* P1 = P0 + 2 * c;
+        const uint64_t* P2 = P1 + 2 * c;
+        uint64_t r = 0;
+        if (x < 2 * c - 1) r += P0[x];
+        if (x >= c && x < 3 * c - 1) r += P2[x - c] - P0[x - c] - P1[x - c];
+        if (x >= 2 * c) r += P1[x - 2 * c];
+        dst[4 * (size_t)c * par + x] = r;
+      }
+      __syncthreads();
+    }
+    const uint64_t* root = (L & 1) ? ys : xs;
+    fqt_reduce_product([&](uint32_t o) { return root[o]; }, nw, kc, d1, P, C, res, Cout + t * kc);
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// Karatsuba shape for ka x kb coefficients: the blocked FQT's block size and q (the same digit
+// bound, see above), and the depth L >= 1 with the least estimated instruction count -- about 4
+// per word product (three IMADs, half a shared load), 15 per evaluated word of each operand and
+// 20 per interpolated word -- whose shared memory fits in 200 KB.
+bool kara_params(uint32_t p, uint32_t ka, uint32_t kb, KaraShape* S, uint32_t* b_out, size_t* smem_out) {
+  uint32_t d1 = 0, b = 0;
+  if (!fqt_params(p, ka, kb, &d1, &b)) return false;
+  const uint32_t na = (ka + d1 - 1) / d1, nb = (kb + d1 - 1) / d1, n0 = std::max(na, nb);
+  double best = -1.0;
+  for (uint32_t L = 1; L <= 8; ++L) {
+    KaraShape c;
+    c.d1 = d1;
+    c.L = L;
+    c.m = (n0 + (1u << L) - 1) >> L;
+    c.N = c.m << L;
+    c.T = 1;
+    for (uint32_t l = 0; l < L; ++l) c.T *= 3;
+    const size_t smem = kara_smem_bytes(c, na + nb - 1);
+    if (smem > 200 * 1024) break;
+    double ev = 0.0, ip = 0.0, t3 = 1.0;
+    for (uint32_t l = 1; l <= L; ++l) {
+      const double h = (double)(c.m << (L - l));
+      ip += t3 * (4.0 * h - 1.0);
+      t3 *= 3.0;
+      ev += t3 * h;
+    }
+    const double cost = 4.0 * c.T * (double)c.m * c.m + 30.0 * ev + 20.0 * ip;
+    if (best < 0.0 || cost < best) {
+      best = cost;
+      *S = c;
+      *smem_out = smem;
+    }
+  }
+  *b_out = b;
+  return best >= 0.0;
+}
+
 // ------------------------------------------------------------------ launchers
 
 static int grid_for(fp_ctx ctx, uint64_t ntiles, int per_sm) {
@@ -825,6 +1027,27 @@ fp_status launch_polymul(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t da, 
       int grid = grid_for(ctx, batch, 16);
       FP_LAUNCH(ctx, "k_polymul_plain_big", st, k_polymul_plain_big<<<grid, 256, 0, st>>>(A, B, C, batch, ka, kb, p, dv, ctx->d_err));
     }
+    FP_CUDA(cudaGetLastError());
+    return FP_OK;
+  }
+  if (algo == FP_ALGO_KARATSUBA) {
+    KaraShape S;
+    uint32_t bk = 0;
+    size_t smem = 0;
+    FP_CHECK(kara_params(p, ka, kb, &S, &bk, &smem), FP_EBOUND,
+             "polymul: no Karatsuba FQT shape fits (p=%u, degrees %u x %u)", p, da, db);
+    RedqParams P = make_redq(p, bk, 2 * S.d1 - 1);
+    FP_CUDA(cudaFuncSetAttribute(k_polymul_kara, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // one thread per leaf-product work item in whole warps, 128 to 256 threads (larger blocks
+    // cost registers and blocks per SM and ran slower on 1023 x 1023 products)
+    const uint32_t items = S.T * (((2 * S.m + 2) / 4 + 1) / 2);
+    const int threads = (int)std::min<uint32_t>(256u, std::max<uint32_t>(128u, (items + 31u) & ~31u));
+    int per_sm = 0;
+    FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_polymul_kara, threads, smem));
+    FP_CHECK(per_sm >= 1, FP_EUNSUPPORTED, "polymul: Karatsuba block of %d threads does not fit an SM", threads);
+    const int grid = grid_for(ctx, batch, per_sm);
+    FP_LAUNCH(ctx, "k_polymul_kara", st,
+              k_polymul_kara<<<grid, threads, smem, st>>>(A, B, C, batch, ka, kb, S, P, ctx->d_err));
     FP_CUDA(cudaGetLastError());
     return FP_OK;
   }

@@ -118,6 +118,42 @@ def test_polymul_large_degrees_fqt(env, p, da, db, algo):
     assert np.array_equal(C.cpu().numpy(), field.polymul_mod(a, b, p))
 
 
+@pytest.mark.parametrize("p,da,db,batch", [(3, 512, 512, 37), (3, 1023, 1023, 9), (2, 1023, 1023, 9),
+                                           (251, 1023, 1023, 5), (127, 592, 794, 5), (7, 100, 333, 37),
+                                           (5, 64, 1, 37), (3, 1023, 0, 37), (3, 0, 1023, 37), (31, 40, 50, 37),
+                                           (3, 0, 0, 37), (2, 1, 2, 37), (17, 299, 298, 37), (3, 63, 63, 37),
+                                           (61, 260, 1014, 7), (3, 40, 40, 5000)])
+def test_polymul_karatsuba(env, p, da, db, batch):
+    """Karatsuba FQT: leaf counts 3 to 81, unequal and one-word operands, a grid-stride batch."""
+    fp, torch, dev, ctx = env
+    a, b = workloads.polymul_inputs(da + 7 * db, p, batch, da, db)
+    C = torch.empty((batch, da + db + 1), dtype=torch.uint8, device=dev)
+    fp.fp_polymul_batched(ctx, p, to_dev(torch, dev, a), da, to_dev(torch, dev, b), db, C, batch,
+                          fp.FP_ALGO_KARATSUBA)
+    fp.fp_ctx_status(ctx)
+    assert np.array_equal(C.cpu().numpy(), field.polymul_mod(a, b, p))
+
+
+def test_polymul_karatsuba_all_max_and_bad_input(env):
+    """Every coefficient p-1 (every result word at the digit bound's edge), then one residue out
+    of range, which the kernel reports through the context status."""
+    fp, torch, dev, ctx = env
+    for p, d in [(3, 1023), (7, 511), (251, 700), (2, 5)]:
+        a = np.full((19, d + 1), p - 1, np.uint8)
+        C = torch.empty((19, 2 * d + 1), dtype=torch.uint8, device=dev)
+        A = to_dev(torch, dev, a)
+        fp.fp_polymul_batched(ctx, p, A, d, A, d, C, 19, fp.FP_ALGO_KARATSUBA)
+        fp.fp_ctx_status(ctx)
+        assert np.array_equal(C.cpu().numpy(), field.polymul_mod(a, a, p))
+    A = torch.zeros((4, 600), dtype=torch.uint8, device=dev)
+    A[2, 599] = 3
+    C = torch.empty((4, 1199), dtype=torch.uint8, device=dev)
+    fp.fp_polymul_batched(ctx, 3, A, 599, A, 599, C, 4, fp.FP_ALGO_KARATSUBA)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_ctx_status(ctx)
+    assert ei.value.status == fp.FP_EINVAL
+
+
 def test_polymul_all_max_coefficients(env):
     """Every coefficient p-1: the largest digit of every word (the bound's edge)."""
     fp, torch, dev, ctx = env
