@@ -149,3 +149,60 @@ def gf_pow(a, e, p, k, modulus):
         base = gf_mul(base, base, p, k, modulus)
         e >>= 1
     return r
+
+
+def gf_dot(a, b, p, k, modulus):
+    """Dot product over GF(p^k) (the value Algorithm FGDP returns, Sec. 6): sum_i a_i b_i in the
+    field, for index vectors a, b.  Written as the sum over i of the coefficient convolutions of
+    a_i(X) b_i(X), reduced mod p and then by the modulus once (reduction is a ring homomorphism,
+    so this equals folding gf_mul with gf_add).  Returns the element index."""
+    ca = index_to_coeffs(np.asarray(a, dtype=np.int64), p, k)
+    cb = index_to_coeffs(np.asarray(b, dtype=np.int64), p, k)
+    s = np.zeros(2 * k - 1, dtype=np.int64)
+    for i in range(k):
+        for j in range(k):
+            s[i + j] = (s[i + j] + int((ca[..., i] * cb[..., j]).sum() % p)) % p
+    return int(coeffs_to_index(poly_rem_mod(s, modulus, p), p))
+
+
+def _prime_factors(n):
+    out, d = [], 2
+    while d * d <= n:
+        if n % d == 0:
+            out.append(d)
+            while n % d == 0:
+                n //= d
+        d += 1
+    if n > 1:
+        out.append(n)
+    return out
+
+
+def primitive_element(p, k, modulus):
+    """The generator used for the discrete-log element form: the smallest index g whose
+    multiplicative order is p^k - 1, tested by g^((p^k - 1) / r) != 1 for every prime r of
+    p^k - 1 (Lagrange)."""
+    n = p ** k - 1
+    if n == 1:
+        return 1
+    for g in range(2, p ** k):
+        if all(int(gf_pow(np.array(g), n // r, p, k, modulus)) != 1 for r in _prime_factors(n)):
+            return g
+    raise ValueError("no primitive element")
+
+
+def log_tables(p, k, modulus):
+    """Discrete-log form of GF(p^k) (the element representation Algorithm FGDP assumes): the
+    element g^e is written e, 0 <= e <= p^k - 2, and zero is written p^k - 1.  Returns
+    (antilog, log): antilog[e] = index of g^e (antilog[p^k - 1] = 0) and log[x] = its inverse."""
+    order = p ** k
+    g = primitive_element(p, k, modulus)
+    antilog = np.zeros(order, dtype=np.int64)
+    x = 1
+    for e in range(order - 1):
+        antilog[e] = x
+        x = int(gf_mul(np.array(x), np.array(g), p, k, modulus))
+    antilog[order - 1] = 0
+    log = np.zeros(order, dtype=np.int64)
+    log[antilog] = np.arange(order)
+    return antilog, log

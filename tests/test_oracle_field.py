@@ -143,3 +143,57 @@ def test_fgdp_theorem(p, k, q):
             for x, y in zip(v1, v2):
                 plain = int(field.gf_add(np.array(plain), field.gf_mul(np.array(x), np.array(y), p, k, m), p, k))
             assert gfpk.fgdp_dot(v1, v2, p, k, q, m, tabs) == plain
+
+
+# Smallest primitive root modulo p (number-theory tables, OEIS A001918).
+_SMALLEST_PRIMITIVE_ROOT = {2: 1, 3: 2, 5: 2, 7: 3, 11: 2, 13: 2, 17: 3, 19: 2, 23: 5, 29: 2, 31: 3, 37: 2,
+                            41: 6, 43: 3, 47: 5, 71: 7, 73: 5, 97: 5}
+
+
+def test_primitive_element_known_values():
+    """The generator of the discrete-log form is the smallest index of full order: for k = 1
+    the smallest primitive root mod p; in the AES field (x^8 + x^4 + x^3 + x + 1) x has order
+    51 and x + 1 (index 3) generates the multiplicative group."""
+    for p, g in _SMALLEST_PRIMITIVE_ROOT.items():
+        assert field.primitive_element(p, 1, field.smallest_monic_irreducible(p, 1)) == g, p
+    m = field.smallest_monic_irreducible(2, 8)
+    assert field.primitive_element(2, 8, m) == 3
+    powers = [int(field.gf_pow(np.array(2), e, 2, 8, m)) for e in range(1, 256)]
+    assert powers.index(1) + 1 == 51
+
+
+@pytest.mark.parametrize("p,k", [(3, 5), (7, 4), (2, 8), (3, 2), (5, 1), (2, 1)])
+def test_log_tables_are_a_group_isomorphism(p, k):
+    """antilog is a bijection from exponents 0..p^k-2 onto the nonzero elements with
+    antilog(e1 + e2 mod p^k - 1) = antilog(e1) antilog(e2); p^k - 1 stands for zero."""
+    m = field.smallest_monic_irreducible(p, k)
+    antilog, log = field.log_tables(p, k, m)
+    q = p ** k
+    assert antilog[q - 1] == 0 and log[0] == q - 1
+    assert sorted(antilog[: q - 1].tolist()) == list(range(1, q))
+    assert np.array_equal(antilog[log], np.arange(q))
+    rng = np.random.default_rng(q)
+    e1, e2 = rng.integers(0, q - 1, 300), rng.integers(0, q - 1, 300)
+    assert np.array_equal(antilog[(e1 + e2) % (q - 1)], field.gf_mul(antilog[e1], antilog[e2], p, k, m))
+
+
+@pytest.mark.parametrize("p,k", [(3, 5), (7, 4), (2, 8), (2, 1), (3, 1), (2, 2), (5, 2), (3, 3)])
+def test_gf_dot_closed_forms_and_fold(p, k):
+    """Sum over all x of x^2 is -1 when p^k - 1 divides 2 and 0 otherwise; the sum over the
+    nonzero x of x x^-1 is p^k - 1 = -1 (the constant p - 1); and gf_dot equals the fold of
+    gf_mul and gf_add, and is additive in its second argument."""
+    m = field.smallest_monic_irreducible(p, k)
+    q = p ** k
+    x = np.arange(q)
+    assert field.gf_dot(x, x, p, k, m) == ((p - 1) if 2 % (q - 1) == 0 else 0)
+    nz = np.arange(1, q)
+    assert field.gf_dot(nz, field.gf_pow(nz, q - 2, p, k, m), p, k, m) == p - 1
+    rng = np.random.default_rng(7 * q)
+    a, b, c = (rng.integers(0, q, 50) for _ in range(3))
+    fold = 0
+    for s, t in zip(a, b):
+        fold = int(field.gf_add(np.array(fold), field.gf_mul(np.array(s), np.array(t), p, k, m), p, k))
+    assert field.gf_dot(a, b, p, k, m) == fold
+    lhs = field.gf_dot(a, field.gf_add(b, c, p, k), p, k, m)
+    rhs = field.gf_add(np.array(field.gf_dot(a, b, p, k, m)), np.array(field.gf_dot(a, c, p, k, m)), p, k)
+    assert lhs == int(rhs)
