@@ -532,6 +532,43 @@ def run_gf(args, ws, rank, local):
         eb = 3 * A.element_size() * count
         per_field[f"GF({p}^{k})"] = {"ms": t, "GB/s": eb / (t / 1e3) / 1e9, "frac_hbm": eb / (t / 1e3) / 1e9 / hbm,
                                      "F_p MAC/s": k * k * count / (t / 1e3)}
+    # Algorithm FGDP with n > 1: the dot product of 2^26 terms per field, index and discrete-log
+    # forms, L2 flushed; parity on a 2^20-term prefix against the oracle's plain field dot.
+    dot_rows = {}
+    if not args.no_compare:
+        nd = 1 << 26
+        for p, k, a, b, gfh, A, B, C in fields:
+            q = p ** k
+            mod = field.smallest_monic_irreducible(p, k)
+            _, log = field.log_tables(p, k, mod)
+            dt = workloads.gf_index_dtype(p, k)
+            ga = torch.randint(0, q, (nd,), dtype=torch.int32, device=dev)
+            gb = torch.randint(0, q, (nd,), dtype=torch.int32, device=dev)
+            tdt = torch.uint8 if dt == np.uint8 else torch.int16
+            out = torch.empty(1, dtype=tdt, device=dev)
+            row = {"chunk": fp.fp_gf_dot_info(gfh)["chunk"]}
+            for form, nm in ((fp.FP_GF_INDEX, "index"), (fp.FP_GF_LOG, "log")):
+                if form == fp.FP_GF_LOG:
+                    lt = torch.from_numpy(log.astype(np.int32)).to(dev)
+                    xa, xb = lt[ga.long()].to(tdt), lt[gb.long()].to(tdt)
+                else:
+                    xa, xb = ga.to(tdt), gb.to(tdt)
+                pre = 1 << 20
+                fp.fp_gf_dot(ctx, gfh, xa, xb, pre, out, form)
+                torch.cuda.synchronize()
+                fp.fp_ctx_status(ctx)
+                ha = ga[:pre].cpu().numpy().astype(np.int64)
+                hb = gb[:pre].cpu().numpy().astype(np.int64)
+                want = field.gf_dot(ha, hb, p, k, mod)
+                got = int(out.cpu().numpy().view(np.uint16)[0]) if tdt == torch.int16 else int(out.item())
+                assert got == (log[want] if form == fp.FP_GF_LOG else want), f"GF({p}^{k}) dot parity ({nm})"
+                fn = lambda xa=xa, xb=xb, form=form: fp.fp_gf_dot(ctx, gfh, xa, xb, nd, out, form)
+                t = statistics.median(_timed(torch, stream, fn, 5, flush))
+                eb = 2 * nd * xa.element_size()
+                row[nm] = {"ms": t, "F_p MAC/s": k * k * nd / (t / 1e3), "GB/s": eb / (t / 1e3) / 1e9,
+                           "frac_hbm": eb / (t / 1e3) / 1e9 / hbm}
+            dot_rows[f"GF({p}^{k})"] = row
+            del ga, gb, xa, xb
     hin = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory(), torch.empty(count, dtype=A.dtype).pin_memory())
            for p, k, a, b, gfh, A, B, C in fields]
 
@@ -593,6 +630,7 @@ def run_gf(args, ws, rank, local):
             "e2e": {"value": ws * macs / (te / 1e3), "unit": "F_p MAC/s", "h2d_bytes_per_step": 2 * nbytes // 3,
                     "d2h_bytes_per_step": nbytes // 3},
             "gpu_launches": launches, "clocks": clk.summary(),
+            "dot_2^26_terms": dot_rows,
         }))
     fp.fp_ctx_destroy(ctx)
 

@@ -299,6 +299,26 @@ fp_status fp_gf_info(fp_gf gf, uint32_t* modulus, uint32_t* b, uint32_t* word,
 fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf gf, const void* a, const void* b, void* c,
                             size_t count, void* stream);
 
+/* Element forms of fp_gf_dot.  FP_GF_LOG is the discrete-log form Algorithm FGDP assumes:
+ * the element g^e is written e (0 <= e <= p^k - 2) and zero is written p^k - 1, where g is
+ * the smallest index of multiplicative order p^k - 1 (fp_gf_dot_info). */
+enum { FP_GF_INDEX = 0, FP_GF_LOG = 1 };
+
+/* Dot product over GF(p^k) by Algorithm FGDP (Sec. 6): *out = sum_i a[i] b[i] in the field.
+ * a, b: device arrays of n elements in `form` (width per fp_gf_info); out: one device element
+ * of the same width, written in the same form.  Line 1 is one table lookup from either form
+ * to the element's evaluation at the dot product's own q = 2^b_dot; the word products
+ * accumulate for `chunk` terms (every digit below q, the word below 2^64) before each REDQ and
+ * L/H lookup, and the partial results are added in the field.  n = 0 writes zero.  Codes
+ * >= p^k set FP_EINVAL on the context (read by fp_ctx_status) and count as zero.  n < 2^40.
+ * Uses context scratch for per-block partial sums. */
+fp_status fp_gf_dot(fp_ctx ctx, fp_gf gf, const void* a, const void* b, size_t n, void* out,
+                    int form, void* stream);
+
+/* The dot product's parameters: index of the generator g of the log form, exponent b_dot of
+ * its q, and the number of word products accumulated per REDQ.  Any argument may be NULL. */
+fp_status fp_gf_dot_info(fp_gf gf, uint32_t* generator, uint32_t* b_dot, uint32_t* chunk);
+
 /* ---------------------------------------------------------------- uneven batches */
 
 /* One instance of an uneven batch: kind 0 = matmul (C = A B mod p, dense row-major,

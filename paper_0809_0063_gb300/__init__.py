@@ -26,6 +26,8 @@ FP_ALGO_AUTO, FP_ALGO_PLAIN, FP_ALGO_DQT_F64, FP_ALGO_DQT_U64, FP_ALGO_DQT_F32, 
 (FP_MM_AUTO, FP_MM_RIGHT_F64, FP_MM_RIGHT_F32, FP_MM_PLAIN_F64, FP_MM_PLAIN_F32, FP_MM_PLAIN_I8,
  FP_MM_PLAIN_TC, FP_MM_RIGHT_TC, FP_MM_LEFT_F32, FP_MM_PLAIN_F8, FP_MM_LEFT_F64, FP_MM_CMM_F64) = range(12)
 FP_GROUP_MAX = 16
+# GF(p^k) element forms for fp_gf_dot
+FP_GF_INDEX, FP_GF_LOG = range(2)
 
 
 class FpError(RuntimeError):
@@ -96,6 +98,8 @@ _SIGS = {
     "fp_gf_destroy": (None, [_V]),
     "fp_gf_info": (_I, [_V, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
     "fp_gf_mul_batched": (_I, [_V, _V, _V, _V, _V, _SZ, _V]),
+    "fp_gf_dot": (_I, [_V, _V, _V, _V, _SZ, _V, ctypes.c_int, _V]),
+    "fp_gf_dot_info": (_I, [_V, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
     "fp_batch_run": (_I, [_V, ctypes.POINTER(fp_instance), _SZ, _V]),
     "fp_matmul_grouped": (_I, [_V, ctypes.POINTER(fp_mm_problem), _SZ, _I, _V]),
     "fp_selftest_bounded_wait": (_I, [_V, _U32, _V]),
@@ -270,6 +274,16 @@ def fp_gf_info(gf, k: int):
 
 def fp_gf_mul_batched(ctx, gf, a, b, c, count: int, stream=None):
     _check(lib().fp_gf_mul_batched(ctx, gf, _ptr(a), _ptr(b), _ptr(c), count, _stream(stream)))
+
+
+def fp_gf_dot(ctx, gf, a, b, n: int, out, form: int = FP_GF_INDEX, stream=None):
+    _check(lib().fp_gf_dot(ctx, gf, _ptr(a), _ptr(b), n, _ptr(out), form, _stream(stream)))
+
+
+def fp_gf_dot_info(gf):
+    g, b, c = _U32(), _U32(), _U32()
+    _check(lib().fp_gf_dot_info(gf, ctypes.byref(g), ctypes.byref(b), ctypes.byref(c)))
+    return {"generator": g.value, "b_dot": b.value, "chunk": c.value}
 
 
 def fp_selftest_bounded_wait(ctx, polls: int, stream=None):

@@ -28,6 +28,14 @@ struct fp_gf_s {
   uint4* d_img = nullptr;                        // word-level tables (GF(2^8), GF(3^5), GF(7^4))
   uint32_t img_bytes = 0;
   fpd::RedqParams P{};
+  // dot product (Algorithm FGDP with n > 1): its own q = 2^bd, nc products per REDQ
+  uint32_t bd = 0, nc = 0, gen = 0;              // gen: index of the generator of the log form
+  uint64_t* d_word_d = nullptr;                  // [p^k] index form -> word at 2^bd
+  uint64_t* d_word_dl = nullptr;                 // [p^k] log form -> word at 2^bd (p^k - 1: zero)
+  uint32_t* d_Ld = nullptr;                      // [2^{c k}] L and H at 2^bd
+  uint32_t* d_Hd = nullptr;
+  uint16_t* d_tolog = nullptr;                   // [p^k] index -> log form
+  fpd::RedqParams Pd{};
   int device = 0;
 };
 
@@ -93,15 +101,22 @@ __device__ __forceinline__ void gf_load_tables(const GfDev& G, uint8_t* sm, uint
   __syncthreads();
 }
 
-// One product by Algorithm FGDP with n = 1 (see the file comment).
-__device__ __forceinline__ uint32_t gf_mul_one(uint32_t xa, uint32_t xb, const GfDev& G, const uint64_t* sw,
-                                               const uint32_t* sL, const uint32_t* sH, const RedqParams& P,
-                                               uint32_t& bad) {
+// Field addition of two spread coefficient vectors (fields of fb bits, each < p, 2^(fb-1) >= p):
+// one add, then p is taken off every field that reached p -- adding 2^(fb-1) - p to a field
+// sets its bit fb-1 exactly when the field is >= p, and no field carries into the next.
+__device__ __forceinline__ uint32_t gf_spread_add(uint32_t x, uint32_t y, uint32_t p, uint32_t fb, uint32_t ones) {
+  const uint32_t hb = fb - 1;
+  const uint32_t t = x + y;
+  const uint32_t ge = ((t + ((1u << hb) - p) * ones) >> hb) & ones;
+  return t - p * ge;
+}
+
+// Lines 3-6 of Algorithm FGDP on an accumulated word r: REDQ compression, the two lookups and
+// the field addition of their results, returned as a spread coefficient vector (k fields of
+// fb bits, each < p).
+__device__ __forceinline__ uint32_t gf_redq_spread(uint64_t r, const GfDev& G, const uint32_t* sL,
+                                                   const uint32_t* sH, const RedqParams& P) {
   const uint32_t p = P.p, bq = P.b, k = G.k, fb = G.fb, cbits = G.cbits;
-  bad |= (xa >= G.order) | (xb >= G.order);
-  xa = xa < G.order ? xa : 0u;
-  xb = xb < G.order ? xb : 0u;
-  const uint64_t r = sw[xa] * sw[xb];             // lines 1-2
   const uint64_t s = divp64(r, P.dv);             // REDQ compression quotient (line 3)
   const uint32_t rl = (uint32_t)r, rh = (uint32_t)(r >> 32);
   const uint32_t sl = (uint32_t)s, shh = (uint32_t)(s >> 32);
@@ -115,20 +130,32 @@ __device__ __forceinline__ uint32_t gf_mul_one(uint32_t xa, uint32_t xb, const G
     if (j < k) il |= uj << (j * cbits);
     if (j + 1 >= k) ih |= uj << ((j + 1 - k) * cbits);
   }
-  const uint32_t hb = fb - 1;                     // bit tested after adding 2^hb - p per field
-  uint32_t x = sL[il] + sH[ih];                    // lines 4-6: two lookups, one field add
-  const uint32_t ge = ((x + ((1u << hb) - p) * G.ones) >> hb) & G.ones;
-  x -= p * ge;
+  return gf_spread_add(sL[il], sH[ih], p, fb, G.ones);   // lines 4-6: two lookups, one field add
+}
+
+// Index sum_j c_j p^j of a spread coefficient vector.
+__device__ __forceinline__ uint32_t gf_spread_index(uint32_t x, uint32_t p, uint32_t k, uint32_t fb) {
   const uint32_t fmask = (1u << fb) - 1u;
   uint32_t idx = 0;
   for (int j = (int)k - 1; j >= 0; --j) idx = idx * p + ((x >> (j * fb)) & fmask);
   return idx;
 }
 
+// One product by Algorithm FGDP with n = 1 (see the file comment).
+__device__ __forceinline__ uint32_t gf_mul_one(uint32_t xa, uint32_t xb, const GfDev& G, const uint64_t* sw,
+                                               const uint32_t* sL, const uint32_t* sH, const RedqParams& P,
+                                               uint32_t& bad) {
+  bad |= (xa >= G.order) | (xb >= G.order);
+  xa = xa < G.order ? xa : 0u;
+  xb = xb < G.order ? xb : 0u;
+  const uint64_t r = sw[xa] * sw[xb];             // lines 1-2
+  return gf_spread_index(gf_redq_spread(r, G, sL, sH, P), P.p, G.k, G.fb);
+}
+
 template <typename E>
 __global__ void __launch_bounds__(256) k_gf_mul(const E* __restrict__ a, const E* __restrict__ b, E* __restrict__ c,
                                                 uint64_t count, GfDev G, RedqParams P, uint32_t* err) {
-  extern __shared__ __align__(16) uint8_t sm[];
+  extern __shared__ __align__(128) uint8_t sm[];
   uint64_t* sw;
   uint32_t *sL, *sH;
   gf_load_tables(G, sm, sw, sL, sH);
@@ -174,6 +201,100 @@ __global__ void __launch_bounds__(256) k_gf_mul_bulk(const E* __restrict__ a, co
   stream_tiles(op, reinterpret_cast<const uint8_t*>(a), reinterpret_cast<const uint8_t*>(b),
                reinterpret_cast<uint8_t*>(c), ntiles, sizeof(E), sizeof(E), sizeof(E), sm + table_bytes, err);
   if (op.bad) flag_error(err, ERR_RANGE);
+}
+
+// ------------------------------------------------------------------ dot product
+//
+// Algorithm FGDP with n > 1 (the dot product it is written for).  The element arrays are in
+// index or discrete-log form; the word table of the call's form maps an element straight to its
+// evaluation at the dot product's own q = 2^bd (line 1), so the kernel never sees the form.
+// Each thread accumulates word products (line 2) while every digit stays below q: after nc
+// products (nc (p-1)^2 k < q and the word below 2^64) the word goes through lines 3-6 and the
+// resulting element, a spread coefficient vector, is added to the thread's running sum in the
+// field.  Warps and blocks combine their sums with the same spread addition; a one-block kernel
+// adds the per-block sums and writes the result in the call's form.
+
+struct GfDotDev {
+  GfDev G;           // word table of the call's form at 2^bd, L and H at 2^bd
+  uint32_t nc;       // word products per REDQ
+  uint32_t zero;     // the zero element's code in the call's form (invalid codes count as it)
+};
+
+template <typename E>
+__device__ __forceinline__ void gf_dot_step(uint32_t x, uint32_t y, const GfDotDev& D, const uint64_t* sw,
+                                            const uint32_t* sL, const uint32_t* sH, const RedqParams& P,
+                                            uint64_t& r, uint32_t& cnt, uint32_t& acc, uint32_t& bad) {
+  bad |= (x >= D.G.order) | (y >= D.G.order);
+  x = x < D.G.order ? x : D.zero;
+  y = y < D.G.order ? y : D.zero;
+  r += sw[x] * sw[y];
+  if (++cnt == D.nc) {
+    acc = gf_spread_add(acc, gf_redq_spread(r, D.G, sL, sH, P), P.p, D.G.fb, D.G.ones);
+    r = 0;
+    cnt = 0;
+  }
+}
+
+// Sum of the block's spread vectors; the result is valid in thread 0.
+__device__ __forceinline__ uint32_t gf_block_sum(uint32_t acc, uint32_t p, uint32_t fb, uint32_t ones) {
+  __shared__ uint32_t wsum[32];
+  for (int off = 16; off; off >>= 1) acc = gf_spread_add(acc, __shfl_xor_sync(0xffffffffu, acc, off), p, fb, ones);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+  if (lane == 0) wsum[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    acc = lane < nwarps ? wsum[lane] : 0u;
+    for (int off = 16; off; off >>= 1) acc = gf_spread_add(acc, __shfl_xor_sync(0xffffffffu, acc, off), p, fb, ones);
+  }
+  return acc;
+}
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_gf_dot(const E* __restrict__ a, const E* __restrict__ b, uint64_t n,
+                                                GfDotDev D, RedqParams P, uint32_t* __restrict__ partial,
+                                                uint32_t* err) {
+  extern __shared__ __align__(128) uint8_t dsm[];
+  uint64_t* sw;
+  uint32_t *sL, *sH;
+  gf_load_tables(D.G, dsm, sw, sL, sH);
+  uint32_t bad = 0, acc = 0, cnt = 0;
+  uint64_t r = 0;
+  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  constexpr uint32_t EPV = 16 / sizeof(E);          // elements per 16-byte vector
+  uint64_t done = 0;
+  if (((((uintptr_t)a) | ((uintptr_t)b)) & 15u) == 0) {
+    const uint64_t nvec = n / EPV;
+    const uint4* va = reinterpret_cast<const uint4*>(a);
+    const uint4* vb = reinterpret_cast<const uint4*>(b);
+    for (uint64_t v = tid; v < nvec; v += stride) {
+      const uint4 xa = __ldcs(va + v), xb = __ldcs(vb + v);
+      const E* ea = reinterpret_cast<const E*>(&xa);
+      const E* eb = reinterpret_cast<const E*>(&xb);
+#pragma unroll
+      for (uint32_t j = 0; j < EPV; ++j) gf_dot_step<E>(ea[j], eb[j], D, sw, sL, sH, P, r, cnt, acc, bad);
+    }
+    done = nvec * EPV;
+  }
+  for (uint64_t i = done + tid; i < n; i += stride) gf_dot_step<E>(a[i], b[i], D, sw, sL, sH, P, r, cnt, acc, bad);
+  if (cnt) acc = gf_spread_add(acc, gf_redq_spread(r, D.G, sL, sH, P), P.p, D.G.fb, D.G.ones);
+  acc = gf_block_sum(acc, P.p, D.G.fb, D.G.ones);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+// Field sum of the per-block spread vectors, written as one element in the call's form.
+template <typename E>
+__global__ void __launch_bounds__(256) k_gf_dot_final(const uint32_t* __restrict__ partial, uint32_t nparts,
+                                                      E* __restrict__ out, uint32_t p, uint32_t k, uint32_t fb,
+                                                      uint32_t ones, const uint16_t* __restrict__ to_log) {
+  uint32_t acc = 0;
+  for (uint32_t i = threadIdx.x; i < nparts; i += blockDim.x) acc = gf_spread_add(acc, partial[i], p, fb, ones);
+  acc = gf_block_sum(acc, p, fb, ones);
+  if (threadIdx.x == 0) {
+    const uint32_t idx = gf_spread_index(acc, p, k, fb);
+    *out = (E)(to_log ? to_log[idx] : idx);
+  }
 }
 
 // ------------------------------------------------------------------ word-level fields
@@ -495,7 +616,7 @@ struct GfSeg { uint64_t a, b, c; uint32_t count, pad; };
 template <typename E>
 __global__ void __launch_bounds__(256) k_gf_mul_seg(uint8_t* base, const GfSeg* __restrict__ segs, uint32_t nseg,
                                                     GfDev G, RedqParams P, uint32_t* err) {
-  extern __shared__ __align__(16) uint8_t sm[];
+  extern __shared__ __align__(128) uint8_t sm[];
   uint64_t* sw;
   uint32_t *sL, *sH;
   gf_load_tables(G, sm, sw, sL, sH);
@@ -569,33 +690,145 @@ extern "C" fp_status fp_gf_create(fp_ctx ctx, uint32_t p, uint32_t k, fp_gf* out
     word[x] = w;
   }
   const uint32_t tsz = 1u << (cbits * k);
-  const uint32_t cq = (uint32_t)((p - ((1ull << b) % p)) % p);  // -q mod p
-  std::vector<uint32_t> L(tsz, 0), H(tsz, 0);
-  for (uint32_t idx = 0; idx < tsz; ++idx) {
-    std::vector<uint32_t> u(k);
-    bool valid = true;
-    for (uint32_t i = 0; i < k; ++i) {
-      u[i] = (idx >> (i * cbits)) & ((1u << cbits) - 1);
-      valid &= u[i] < p;
+  // L and H of Theorem fgdp for q = 2^bq, binary-indexed by (u_0..u_{k-1}) / (u_{k-1}..u_{2k-2})
+  auto build_lh = [&](uint32_t bq, std::vector<uint32_t>& L, std::vector<uint32_t>& H) {
+    const uint32_t cq = (uint32_t)((p - ((1ull << bq) % p)) % p);  // -q mod p
+    L.assign(tsz, 0);
+    H.assign(tsz, 0);
+    for (uint32_t idx = 0; idx < tsz; ++idx) {
+      std::vector<uint32_t> u(k);
+      bool valid = true;
+      for (uint32_t i = 0; i < k; ++i) {
+        u[i] = (idx >> (i * cbits)) & ((1u << cbits) - 1);
+        valid &= u[i] < p;
+      }
+      if (!valid) continue;
+      // L = sum_{i=0}^{k-2} (u_i - q u_{i+1} mod p) X^i  (u = u_0..u_{k-1})
+      std::vector<uint32_t> pl(2 * k - 1, 0);
+      for (uint32_t i = 0; i + 1 < k; ++i) pl[i] = (u[i] + cq * u[i + 1]) % p;
+      L[idx] = spread(poly_rem(pl, g->modulus, p), fb);
+      // H = u_{2k-2} X^{2k-2} + sum_{i=k-1}^{2k-3} (u_i - q u_{i+1} mod p) X^i  (u = u_{k-1}..)
+      std::vector<uint32_t> ph(2 * k - 1, 0);
+      ph[2 * k - 2] = u[k - 1];
+      for (uint32_t j = 0; j + 1 < k; ++j) ph[k - 1 + j] = (u[j] + cq * u[j + 1]) % p;
+      H[idx] = spread(poly_rem(ph, g->modulus, p), fb);
     }
-    if (!valid) continue;
-    // L = sum_{i=0}^{k-2} (u_i - q u_{i+1} mod p) X^i  (u = u_0..u_{k-1})
-    std::vector<uint32_t> pl(2 * k - 1, 0);
-    for (uint32_t i = 0; i + 1 < k; ++i) pl[i] = (u[i] + cq * u[i + 1]) % p;
-    L[idx] = spread(poly_rem(pl, g->modulus, p), fb);
-    // H = u_{2k-2} X^{2k-2} + sum_{i=k-1}^{2k-3} (u_i - q u_{i+1} mod p) X^i  (u = u_{k-1}..)
-    std::vector<uint32_t> ph(2 * k - 1, 0);
-    ph[2 * k - 2] = u[k - 1];
-    for (uint32_t j = 0; j + 1 < k; ++j) ph[k - 1 + j] = (u[j] + cq * u[j + 1]) % p;
-    H[idx] = spread(poly_rem(ph, g->modulus, p), fb);
-  }
+  };
+  std::vector<uint32_t> L, H;
+  build_lh(b, L, H);
   g->P = make_redq(p, b, 2 * k - 1);
+
+  // Dot product: the q = 2^bd >= 2^b that lets the most word products accumulate between two
+  // REDQ steps: nc k (p-1)^2 < 2^bd (every digit) and nc sum_j t_j (p-1)^2 2^(j bd) < 2^64,
+  // t_j = min(j + 1, 2k - 1 - j, k) products meeting at digit j.
+  {
+    const uint64_t pp = (uint64_t)(p - 1) * (p - 1);
+    uint32_t bd = b;
+    uint64_t nc = 1;
+    for (uint32_t bb = b; bb <= 31; ++bb) {
+      if ((uint64_t)(2 * k - 2) * bb >= 64) break;
+      unsigned __int128 S = 0;
+      for (uint32_t j = 0; j < 2 * k - 1; ++j) {
+        const uint32_t t = std::min<uint32_t>(std::min<uint32_t>(j + 1, 2 * k - 1 - j), k);
+        S += ((unsigned __int128)t * pp) << (j * bb);
+      }
+      const uint64_t by_digit = ((1ull << bb) - 1) / (k * pp);
+      const unsigned __int128 by_word = ((((unsigned __int128)1) << 64) - 1) / S;
+      uint64_t c = std::min<uint64_t>(by_digit, by_word > (1u << 20) ? (uint64_t)(1u << 20) : (uint64_t)by_word);
+      if (c > nc) {
+        nc = c;
+        bd = bb;
+      }
+    }
+    g->bd = bd;
+    g->nc = (uint32_t)nc;
+  }
+  std::vector<uint32_t> Ld, Hd;
+  build_lh(g->bd, Ld, Hd);
+  g->Pd = make_redq(p, g->bd, 2 * k - 1);
+  // Discrete-log form: g^e is written e (0 <= e <= p^k - 2) and zero p^k - 1, with g the
+  // smallest index of multiplicative order p^k - 1.
+  auto coeffs_of = [&](uint64_t x) {
+    std::vector<uint32_t> cf(k);
+    for (uint32_t i = 0; i < k; ++i) { cf[i] = (uint32_t)(x % p); x /= p; }
+    return cf;
+  };
+  auto index_of = [&](const std::vector<uint32_t>& cf) {
+    uint64_t x = 0;
+    for (int i = (int)k - 1; i >= 0; --i) x = x * p + cf[i];
+    return x;
+  };
+  auto fmul = [&](uint64_t x, uint64_t y) {
+    const std::vector<uint32_t> cx = coeffs_of(x), cy = coeffs_of(y);
+    std::vector<uint32_t> pr(2 * k - 1, 0);
+    for (uint32_t i = 0; i < k; ++i)
+      for (uint32_t j = 0; j < k; ++j) pr[i + j] = (pr[i + j] + cx[i] * cy[j]) % p;
+    return index_of(poly_rem(pr, g->modulus, p));
+  };
+  auto fpow = [&](uint64_t x, uint64_t e) {
+    uint64_t r = 1;
+    while (e) {
+      if (e & 1) r = fmul(r, x);
+      x = fmul(x, x);
+      e >>= 1;
+    }
+    return r;
+  };
+  {
+    const uint64_t nn = order - 1;
+    std::vector<uint64_t> primes;
+    uint64_t m = nn;
+    for (uint64_t d = 2; d * d <= m; ++d)
+      if (m % d == 0) {
+        primes.push_back(d);
+        while (m % d == 0) m /= d;
+      }
+    if (m > 1) primes.push_back(m);
+    g->gen = 1;
+    if (nn > 1)
+      for (uint64_t cand = 2; cand < order; ++cand) {
+        bool full = true;
+        for (uint64_t r : primes) full &= fpow(cand, nn / r) != 1;
+        if (full) {
+          g->gen = (uint32_t)cand;
+          break;
+        }
+      }
+  }
+  std::vector<uint64_t> word_d(order), word_dl(order, 0);
+  std::vector<uint16_t> tolog(order, 0);
+  for (uint64_t x = 0; x < order; ++x) {
+    const std::vector<uint32_t> cf = coeffs_of(x);
+    uint64_t w = 0;
+    for (int i = (int)k - 1; i >= 0; --i) w = (w << g->bd) | cf[i];
+    word_d[x] = w;
+  }
+  {
+    uint64_t x = 1;
+    for (uint64_t e = 0; e + 1 < order; ++e) {
+      word_dl[e] = word_d[x];
+      tolog[x] = (uint16_t)e;
+      x = fmul(x, g->gen);
+    }
+    word_dl[order - 1] = 0;
+    tolog[0] = (uint16_t)(order - 1);
+  }
   cudaError_t e = cudaMalloc(&g->d_word, order * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_L, tsz * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_H, tsz * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemcpy(g->d_word, word.data(), order * sizeof(uint64_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_L, L.data(), tsz * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_H, H.data(), tsz * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_word_d, order * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_word_dl, order * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_Ld, tsz * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_Hd, tsz * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_tolog, order * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_word_d, word_d.data(), order * sizeof(uint64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_word_dl, word_dl.data(), order * sizeof(uint64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_Ld, Ld.data(), tsz * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_Hd, Hd.data(), tsz * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_tolog, tolog.data(), order * sizeof(uint16_t), cudaMemcpyHostToDevice);
   const std::vector<uint8_t> img = gfw_image(p, k, b, g->modulus);
   if (e == cudaSuccess && !img.empty()) {
     g->img_bytes = (uint32_t)img.size();
@@ -617,6 +850,11 @@ extern "C" void fp_gf_destroy(fp_gf g) {
   if (g->d_L) cudaFree(g->d_L);
   if (g->d_H) cudaFree(g->d_H);
   if (g->d_img) cudaFree(g->d_img);
+  if (g->d_word_d) cudaFree(g->d_word_d);
+  if (g->d_word_dl) cudaFree(g->d_word_dl);
+  if (g->d_Ld) cudaFree(g->d_Ld);
+  if (g->d_Hd) cudaFree(g->d_Hd);
+  if (g->d_tolog) cudaFree(g->d_tolog);
   delete g;
 }
 
@@ -628,6 +866,54 @@ extern "C" fp_status fp_gf_info(fp_gf g, uint32_t* modulus, uint32_t* b, uint32_
   if (word) *word = FP_WORD_U64;
   if (elem_bytes) *elem_bytes = g->elem_bytes;
   return FP_OK;
+}
+
+extern "C" fp_status fp_gf_dot_info(fp_gf g, uint32_t* generator, uint32_t* b_dot, uint32_t* chunk) {
+  FP_CHECK(g != nullptr, FP_EINVAL, "fp_gf_dot_info: gf is NULL");
+  if (generator) *generator = g->gen;
+  if (b_dot) *b_dot = g->bd;
+  if (chunk) *chunk = g->nc;
+  return FP_OK;
+}
+
+template <typename E>
+static fp_status gf_dot_launch(fp_ctx ctx, fp_gf g, const E* a, const E* b, size_t n, E* out, int form,
+                               cudaStream_t st) {
+  using namespace fpd;
+  const uint32_t tsz = 1u << (g->c * g->k);
+  const size_t smem = g->order * sizeof(uint64_t) + 2 * tsz * sizeof(uint32_t);
+  GfDotDev D{GfDev{form == FP_GF_LOG ? g->d_word_dl : g->d_word_d, g->d_Ld, g->d_Hd, g->order, g->k, g->c, g->fb, 0},
+             g->nc, form == FP_GF_LOG ? g->order - 1 : 0u};
+  for (uint32_t i = 0; i < g->k; ++i) D.G.ones |= 1u << (i * g->fb);
+  FP_CUDA(cudaFuncSetAttribute(k_gf_dot<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gf_dot<E>, 256, smem));
+  const uint64_t per_block = 256ull * (16 / sizeof(E));
+  const uint64_t want = (n + per_block - 1) / per_block;
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(want, (uint64_t)ctx->num_sms * (uint64_t)std::max(per_sm, 1));
+  fp_status s = ensure_scratch(ctx, (size_t)std::max<uint32_t>(grid, 1) * sizeof(uint32_t), 1);
+  if (s != FP_OK) return s;
+  uint32_t* partial = (uint32_t*)ctx->scratch2;
+  if (grid)
+    FP_LAUNCH(ctx, "k_gf_dot", st, (k_gf_dot<E><<<grid, 256, smem, st>>>(a, b, n, D, g->Pd, partial, ctx->d_err)));
+  FP_LAUNCH(ctx, "k_gf_dot_final", st,
+            (k_gf_dot_final<E><<<1, 256, 0, st>>>(partial, grid, out, g->p, g->k, g->fb, D.G.ones,
+                                                  form == FP_GF_LOG ? g->d_tolog : nullptr)));
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
+extern "C" fp_status fp_gf_dot(fp_ctx ctx, fp_gf g, const void* a, const void* b, size_t n, void* out, int form,
+                               void* stream) {
+  FP_CHECK(ctx && g, FP_EINVAL, "fp_gf_dot: null ctx or field");
+  FP_CHECK(form == FP_GF_INDEX || form == FP_GF_LOG, FP_EINVAL, "fp_gf_dot: bad form %d", form);
+  FP_CHECK(out != nullptr && (n == 0 || (a && b)), FP_EINVAL, "fp_gf_dot: null array");
+  FP_CHECK(n < (1ull << 40), FP_EINVAL, "fp_gf_dot: n = %llu above 2^40", (unsigned long long)n);
+  cudaStream_t st = as_stream(stream);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (g->elem_bytes == 1)
+    return gf_dot_launch<uint8_t>(ctx, g, (const uint8_t*)a, (const uint8_t*)b, n, (uint8_t*)out, form, st);
+  return gf_dot_launch<uint16_t>(ctx, g, (const uint16_t*)a, (const uint16_t*)b, n, (uint16_t*)out, form, st);
 }
 
 extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const void* b, void* c, size_t count,

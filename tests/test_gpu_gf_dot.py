@@ -173,3 +173,76 @@ def test_dot_vector_path_all_max_and_range(env, p, algo):
     with pytest.raises(fp.FpError) as ei:
         fp.fp_ctx_status(ctx)
     assert ei.value.status == fp.FP_EINVAL
+
+
+def _dev_elems(torch, dev, x, dt):
+    x = np.ascontiguousarray(x.astype(dt))
+    return torch.from_numpy(x.view(np.int16) if dt == np.uint16 else x).to(dev)
+
+
+def _gf_dot_run(fp, torch, dev, ctx, gf, a, b, form, dt, offset=0):
+    A = _dev_elems(torch, dev, np.concatenate([np.zeros(offset, dt), a.astype(dt)]), dt)[offset:]
+    B = _dev_elems(torch, dev, np.concatenate([np.zeros(offset, dt), b.astype(dt)]), dt)[offset:]
+    out = torch.full((1,), 7, dtype=torch.uint8 if dt == np.uint8 else torch.int16, device=dev)
+    fp.fp_gf_dot(ctx, gf, A, B, len(a), out, form)
+    fp.fp_ctx_status(ctx)
+    v = out.cpu().numpy()
+    return int((v.view(np.uint16) if dt == np.uint16 else v)[0])
+
+
+@pytest.mark.parametrize("p,k", [(3, 5), (7, 4), (2, 8), (3, 2), (5, 1), (13, 2), (251, 1), (2, 4), (3, 3)])
+def test_gf_dot_matches_oracle_both_forms(env, p, k):
+    """Algorithm FGDP with n > 1: index and discrete-log forms, lengths around the chunk size and
+    the 16-byte vector, 2^20 + 3 terms, and arrays that start one element past a 16-byte line."""
+    fp, torch, dev, ctx = env
+    gf = fp.fp_gf_create(ctx, p, k)
+    try:
+        m = field.smallest_monic_irreducible(p, k)
+        info = fp.fp_gf_dot_info(gf)
+        assert info["generator"] == field.primitive_element(p, k, m)
+        antilog, log = field.log_tables(p, k, m)
+        q, nc = p ** k, info["chunk"]
+        assert nc >= 1 and nc * k * (p - 1) ** 2 < (1 << info["b_dot"])
+        dt = workloads.gf_index_dtype(p, k)
+        rng = np.random.default_rng(q + 11)
+        for n in sorted({0, 1, 5, 16, 17, min(nc, 5000), min(nc + 1, 5001), 4096 * 16 + 5, (1 << 20) + 3}):
+            a, b = rng.integers(0, q, n), rng.integers(0, q, n)
+            want = field.gf_dot(a, b, p, k, m) if n else 0
+            assert _gf_dot_run(fp, torch, dev, ctx, gf, a, b, fp.FP_GF_INDEX, dt) == want, n
+            assert _gf_dot_run(fp, torch, dev, ctx, gf, log[a], log[b], fp.FP_GF_LOG, dt) == log[want], n
+            if n > 1:
+                assert _gf_dot_run(fp, torch, dev, ctx, gf, a, b, fp.FP_GF_INDEX, dt, offset=1) == want, n
+        # every element p^k - 1 (all coefficients p - 1): every chunk's digits at the bound's edge
+        n = min(3 * nc + 1, 1 << 20)
+        a = np.full(n, q - 1)
+        assert _gf_dot_run(fp, torch, dev, ctx, gf, a, a, fp.FP_GF_INDEX, dt) == field.gf_dot(a, a, p, k, m)
+    finally:
+        fp.fp_gf_destroy(gf)
+
+
+def test_gf_dot_whole_field_and_bad_code(env):
+    """Sum of x^2 over all of GF(3^5) is 0 and over GF(3) is 2 (power sums); a code >= p^k is
+    reported through the context status."""
+    fp, torch, dev, ctx = env
+    for p, k, want in [(3, 5, 0), (3, 1, 2), (7, 4, 0)]:
+        gf = fp.fp_gf_create(ctx, p, k)
+        try:
+            x = np.arange(p ** k)
+            dt = workloads.gf_index_dtype(p, k)
+            assert _gf_dot_run(fp, torch, dev, ctx, gf, x, x, fp.FP_GF_INDEX, dt) == want
+        finally:
+            fp.fp_gf_destroy(gf)
+    gf = fp.fp_gf_create(ctx, 3, 5)
+    try:
+        a = np.zeros(1000, np.uint8)
+        a[500] = 243
+        A = torch.from_numpy(a).to(dev)
+        out = torch.empty(1, dtype=torch.uint8, device=dev)
+        fp.fp_gf_dot(ctx, gf, A, A, 1000, out, fp.FP_GF_INDEX)
+        with pytest.raises(fp.FpError) as ei:
+            fp.fp_ctx_status(ctx)
+        assert ei.value.status == fp.FP_EINVAL
+        with pytest.raises(fp.FpError):
+            fp.fp_gf_dot(ctx, gf, A, A, 1000, out, 2)        # no such form: host check
+    finally:
+        fp.fp_gf_destroy(gf)
