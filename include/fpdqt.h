@@ -306,8 +306,8 @@ enum { FP_GF_INDEX = 0, FP_GF_LOG = 1 };
 
 /* Dot product over GF(p^k) by Algorithm FGDP (Sec. 6): *out = sum_i a[i] b[i] in the field.
  * a, b: device arrays of n elements in `form` (width per fp_gf_info); out: one device element
- * of the same width, written in the same form.  Line 1 is one table lookup from either form
- * to the element's evaluation at the dot product's own q = 2^b_dot; the word products
+ * of the same width, written in the same form.  The conversion to words is one table lookup
+ * from either form to the element's evaluation at the dot product's own q = 2^b_dot; the word products
  * accumulate for `chunk` terms (every digit below q, the word below 2^64) before each REDQ and
  * L/H lookup, and the partial results are added in the field.  n = 0 writes zero.  Codes
  * >= p^k set FP_EINVAL on the context (read by fp_ctx_status) and count as zero.  n < 2^40.

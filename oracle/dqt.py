@@ -26,7 +26,7 @@ def dqt(coeffs, q):
 
 
 def radix_digits(r, q, ndig):
-    """Radix conversion (Algorithm 1, step 3): r = sum_{i<ndig} mu~_i q^i with 0 <= mu~_i < q
+    """Radix conversion (the first inverse step of Algorithm 1): r = sum_{i<ndig} mu~_i q^i with 0 <= mu~_i < q
     for i < ndig-1; the top digit takes whatever is left (floor(r / q^(ndig-1)))."""
     out = []
     for i in range(ndig):
@@ -39,7 +39,7 @@ def radix_digits(r, q, ndig):
 
 
 def dqt_inverse(r, q, ndig, p):
-    """Inverse DQT: radix conversion then each digit mod p (Algorithm 1, steps 3-4)."""
+    """Inverse DQT: radix conversion then each digit mod p (the inverse in Algorithm 1)."""
     return [d % p for d in radix_digits(r, q, ndig)]
 
 

@@ -1,13 +1,13 @@
 """Algorithm FGDP (Sec. 6) restated over exact integers (oracle; test infrastructure only).
 
 Elements of GF(p^k) are indices sum_i c_i p^i of their coefficient vectors modulo a monic
-irreducible P of degree k.  FGDP computes a dot product (here of length n) by
-  1. mapping each element to its evaluation at q (a table in the paper),
-  2. one integer dot product r~ of those evaluations,
-  3. REDQ COMPRESSION of r~ into u_0..u_{2k-2},
-  4./5. two table lookups L[u_0..u_{k-1}] and H[u_{k-1}..u_{2k-2}] that fold the REDQ
-        correction and the reduction modulo P,
-  6. one addition in the field.
+irreducible P of degree k.  FGDP computes a dot product (here of length n), in this order, by
+  - mapping each element to its evaluation at q (a table in the paper),
+  - one integer dot product r~ of those evaluations,
+  - REDQ COMPRESSION of r~ into u_0..u_{2k-2},
+  - two table lookups L[u_0..u_{k-1}] and H[u_{k-1}..u_{2k-2}] that fold the REDQ
+    correction and the reduction modulo P,
+  - one addition in the field.
 The tables are built here from the plain field arithmetic of ``field``.
 """
 from __future__ import annotations

@@ -1,11 +1,12 @@
-// GF(p^k) multiplication by Algorithm FGDP (Sec. 6) with n = 1, on the device:
-//   1. table DQT: element index -> u64 word sum_i c_i q^i (one shared-memory lookup),
-//   2. one word product,
-//   3. REDQ COMPRESSION: u_i = floor(r/q^i) - p floor(s/q^i), i = 0..2k-2 (no correction),
-//   4./5. L[u_0..u_{k-1}] and H[u_{k-1}..u_{2k-2}] (Theorem fgdp), each already reduced modulo
-//      the field's modulus, indexed in the binary format sum u_i 2^{c i}, c = ceil(log2 p)
-//      (Note on Indexing),
-//   6. one field addition.
+// GF(p^k) multiplication by Algorithm FGDP (Sec. 6) with n = 1, on the device, in the
+// algorithm's order:
+//   - table DQT: element index -> u64 word sum_i c_i q^i (one shared-memory lookup);
+//   - one word product;
+//   - REDQ COMPRESSION: u_i = floor(r/q^i) - p floor(s/q^i), i = 0..2k-2 (no correction);
+//   - L[u_0..u_{k-1}] and H[u_{k-1}..u_{2k-2}] (Theorem fgdp), each already reduced modulo
+//     the field's modulus, indexed in the binary format sum u_i 2^{c i}, c = ceil(log2 p)
+//     (Note on Indexing);
+//   - one field addition.
 // L and H entries hold the coefficient vector "spread" in 4-bit fields (p <= 7) or 8-bit fields,
 // so the field addition is one integer add and a per-field conditional subtraction of p.
 // These generic kernels serve every field; GF(2^8), GF(3^5) and GF(7^4) also have word-level
@@ -111,13 +112,13 @@ __device__ __forceinline__ uint32_t gf_spread_add(uint32_t x, uint32_t y, uint32
   return t - p * ge;
 }
 
-// Lines 3-6 of Algorithm FGDP on an accumulated word r: REDQ compression, the two lookups and
-// the field addition of their results, returned as a spread coefficient vector (k fields of
+// The last steps of Algorithm FGDP on an accumulated word r: REDQ compression, the two lookups
+// and the field addition of their results, returned as a spread coefficient vector (k fields of
 // fb bits, each < p).
 __device__ __forceinline__ uint32_t gf_redq_spread(uint64_t r, const GfDev& G, const uint32_t* sL,
                                                    const uint32_t* sH, const RedqParams& P) {
   const uint32_t p = P.p, bq = P.b, k = G.k, fb = G.fb, cbits = G.cbits;
-  const uint64_t s = divp64(r, P.dv);             // REDQ compression quotient (line 3)
+  const uint64_t s = divp64(r, P.dv);             // REDQ compression quotient
   const uint32_t rl = (uint32_t)r, rh = (uint32_t)(r >> 32);
   const uint32_t sl = (uint32_t)s, shh = (uint32_t)(s >> 32);
   const uint32_t qmask = (1u << bq) - 1u;
@@ -130,7 +131,7 @@ __device__ __forceinline__ uint32_t gf_redq_spread(uint64_t r, const GfDev& G, c
     if (j < k) il |= uj << (j * cbits);
     if (j + 1 >= k) ih |= uj << ((j + 1 - k) * cbits);
   }
-  return gf_spread_add(sL[il], sH[ih], p, fb, G.ones);   // lines 4-6: two lookups, one field add
+  return gf_spread_add(sL[il], sH[ih], p, fb, G.ones);   // two lookups, one field addition
 }
 
 // Index sum_j c_j p^j of a spread coefficient vector.
@@ -148,7 +149,7 @@ __device__ __forceinline__ uint32_t gf_mul_one(uint32_t xa, uint32_t xb, const G
   bad |= (xa >= G.order) | (xb >= G.order);
   xa = xa < G.order ? xa : 0u;
   xb = xb < G.order ? xb : 0u;
-  const uint64_t r = sw[xa] * sw[xb];             // lines 1-2
+  const uint64_t r = sw[xa] * sw[xb];             // table conversion and the word product
   return gf_spread_index(gf_redq_spread(r, G, sL, sH, P), P.p, G.k, G.fb);
 }
 
@@ -207,9 +208,9 @@ __global__ void __launch_bounds__(256) k_gf_mul_bulk(const E* __restrict__ a, co
 //
 // Algorithm FGDP with n > 1 (the dot product it is written for).  The element arrays are in
 // index or discrete-log form; the word table of the call's form maps an element straight to its
-// evaluation at the dot product's own q = 2^bd (line 1), so the kernel never sees the form.
-// Each thread accumulates word products (line 2) while every digit stays below q: after nc
-// products (nc (p-1)^2 k < q and the word below 2^64) the word goes through lines 3-6 and the
+// evaluation at the dot product's own q = 2^bd, so the kernel never sees the form.  Each
+// thread accumulates word products while every digit stays below q: after nc products
+// (nc (p-1)^2 k < q and the word below 2^64) the word goes through REDQ and the lookups and the
 // resulting element, a spread coefficient vector, is added to the thread's running sum in the
 // field.  Warps and blocks combine their sums with the same spread addition; a one-block kernel
 // adds the per-block sums and writes the result in the call's form.
