@@ -204,6 +204,25 @@ fp_status fp_polymul_batched(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t 
                              const uint8_t* B, uint32_t degb, uint8_t* C, size_t batch, int algo,
                              void* stream);
 
+/* Kernels of fp_polymul_batched. */
+enum { FP_PM_SINGLE_WORD = 0, FP_PM_FQT = 1, FP_PM_KARATSUBA = 2, FP_PM_PLAIN = 3 };
+
+/* The representation fp_polymul_batched runs in for these degrees and this algo. */
+typedef struct {
+  uint32_t kernel;        /* FP_PM_* */
+  uint32_t word;          /* fp_word of the packed words (unused for FP_PM_PLAIN) */
+  uint32_t blk_a, blk_b;  /* coefficients per packed word of A and of B: dega+1 and degb+1 for
+                             one word per operand, d+1 for the FQT forms */
+  uint32_t b;             /* q = 2^b */
+  uint32_t ndig;          /* residues per result word: dega+degb+1, or 2d+1 for the FQT forms */
+  uint32_t L, m;          /* Karatsuba FQT: split depth and leaf length in words (0 otherwise) */
+} fp_polymul_plan_t;
+
+/* Host query of the planner (no device work; Eq. bounds with the exact largest packed value,
+ * Sec. 5.2 for the block size): the plan fp_polymul_batched follows for (p, dega, degb, algo).
+ * Errors: FP_EINVAL (arguments as in fp_polymul_batched), FP_EBOUND (as fp_polymul_batched). */
+fp_status fp_polymul_plan(uint32_t p, uint32_t dega, uint32_t degb, int algo, fp_polymul_plan_t* out);
+
 /* ---------------------------------------------------------------- dot product */
 
 /* Modular dot product (Algorithm 1 with degree-0 entries): *out = (sum u_i v_i) mod p.

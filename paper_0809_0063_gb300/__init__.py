@@ -28,6 +28,8 @@ FP_ALGO_AUTO, FP_ALGO_PLAIN, FP_ALGO_DQT_F64, FP_ALGO_DQT_U64, FP_ALGO_DQT_F32, 
 FP_GROUP_MAX = 16
 # GF(p^k) element forms for fp_gf_dot
 FP_GF_INDEX, FP_GF_LOG = range(2)
+# polynomial-product kernels (fp_polymul_plan)
+FP_PM_SINGLE_WORD, FP_PM_FQT, FP_PM_KARATSUBA, FP_PM_PLAIN = range(4)
 
 
 class FpError(RuntimeError):
@@ -41,6 +43,12 @@ class fp_dqt_params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_uint32), ("k", ctypes.c_uint32), ("b", ctypes.c_uint32),
                 ("ndig", ctypes.c_uint32), ("word", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("n_accum", ctypes.c_uint64)]
+
+
+class fp_polymul_plan_t(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_uint32), ("word", ctypes.c_uint32), ("blk_a", ctypes.c_uint32),
+                ("blk_b", ctypes.c_uint32), ("b", ctypes.c_uint32), ("ndig", ctypes.c_uint32),
+                ("L", ctypes.c_uint32), ("m", ctypes.c_uint32)]
 
 
 class fp_instance(ctypes.Structure):
@@ -86,6 +94,7 @@ _SIGS = {
     "fp_ctx_autotune": (_I, [_V, _I]),
     "fp_ctx_autotune_choice": (_I, [_V, _U32, _I, _I, _I, ctypes.POINTER(_I)]),
     "fp_dqt_choose": (_I, [_U32, _U32, _U64, _U32, ctypes.POINTER(fp_dqt_params)]),
+    "fp_polymul_plan": (_I, [_U32, _U32, _U32, ctypes.c_int, ctypes.POINTER(fp_polymul_plan_t)]),
     "fp_mm_choose": (_I, [_U32, _U64, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
     "fp_dqt_pack": (_I, [_V, ctypes.POINTER(fp_dqt_params), _V, _V, _SZ, _V]),
     "fp_dqt_unpack_redq": (_I, [_V, ctypes.POINTER(fp_dqt_params), _V, _V, _SZ, _V]),
@@ -197,6 +206,12 @@ def fp_ctx_launches(ctx) -> int:
 
 
 # ------------------------------------------------------------------ planner
+
+def fp_polymul_plan(p: int, dega: int, degb: int, algo: int = FP_ALGO_AUTO) -> dict:
+    out = fp_polymul_plan_t()
+    _check(lib().fp_polymul_plan(p, dega, degb, algo, ctypes.byref(out)))
+    return {name: getattr(out, name) for name, _ in fp_polymul_plan_t._fields_}
+
 
 def fp_dqt_choose(p: int, k: int, n_accum: int, word: int) -> fp_dqt_params:
     out = fp_dqt_params()

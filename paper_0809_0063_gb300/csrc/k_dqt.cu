@@ -1014,10 +1014,85 @@ static fp_status polymul_word_t(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32
   return FP_OK;
 }
 
+// The representation a polynomial product runs in (host only; launch_polymul follows it):
+// plain; one word per operand (the first word type, in AUTO's order, whose largest product
+// fits: Eq. bounds with the exact largest value); the blocked FQT; or its Karatsuba version.
+// Errors: FP_EBOUND when a forced word cannot hold the product or no block size fits 64 bits.
+fp_status polymul_plan(uint32_t p, uint32_t ka, uint32_t kb, int algo, fp_polymul_plan_t* pl, KaraShape* ks,
+                       size_t* kara_smem) {
+  const uint32_t kc = ka + kb - 1;
+  *pl = fp_polymul_plan_t{};
+  if (algo == FP_ALGO_PLAIN) {
+    pl->kernel = FP_PM_PLAIN;
+    return FP_OK;
+  }
+  if (algo == FP_ALGO_KARATSUBA) {
+    KaraShape S;
+    uint32_t bk = 0;
+    size_t smem = 0;
+    FP_CHECK(kara_params(p, ka, kb, &S, &bk, &smem), FP_EBOUND,
+             "polymul: no Karatsuba FQT shape fits (p=%u, %u x %u coefficients)", p, ka, kb);
+    pl->kernel = FP_PM_KARATSUBA;
+    pl->word = FP_WORD_U64;
+    pl->blk_a = pl->blk_b = S.d1;
+    pl->b = bk;
+    pl->ndig = 2 * S.d1 - 1;
+    pl->L = S.L;
+    pl->m = S.m;
+    if (ks) *ks = S;
+    if (kara_smem) *kara_smem = smem;
+    return FP_OK;
+  }
+  const uint32_t bq = poly_qbits(p, ka, kb);
+  // word order for AUTO: integer words first (no FP64 pipe, which is slow on this part)
+  static const int order_auto[4] = {FP_WORD_U32, FP_WORD_F32, FP_WORD_U64, FP_WORD_F64};
+  int forced = -1;
+  if (algo == FP_ALGO_DQT_F64) forced = FP_WORD_F64;
+  if (algo == FP_ALGO_DQT_U64) forced = FP_WORD_U64;
+  if (algo == FP_ALGO_DQT_F32) forced = FP_WORD_F32;
+  if (algo == FP_ALGO_DQT_U32) forced = FP_WORD_U32;
+  if (kc <= 64) {
+    for (int oi = 0; oi < 4; ++oi) {
+      const int w = forced >= 0 ? forced : order_auto[oi];
+      if (product_fits(p, ka, kb, bq, word_beta(w))) {
+        pl->kernel = FP_PM_SINGLE_WORD;
+        pl->word = (uint32_t)w;
+        pl->blk_a = ka;
+        pl->blk_b = kb;
+        pl->b = bq;
+        pl->ndig = kc;
+        return FP_OK;
+      }
+      if (forced >= 0) break;
+    }
+  }
+  // Blocked FQT in u64 words (Sec. 5.2): largest block size d+1 whose accumulated output word
+  // fits 64 bits; digit bound: min(#blocks) (d+1) (p-1)^2 < q.
+  if (forced == FP_WORD_F64 || forced == FP_WORD_F32 || forced == FP_WORD_U32) {
+    set_error("polymul: %u x %u coefficients do not fit one word of the forced type; use DQT_U64 or AUTO",
+              ka, kb);
+    return FP_EBOUND;
+  }
+  uint32_t best_d1 = 0, best_b = 0;
+  fqt_params(p, ka, kb, &best_d1, &best_b);
+  FP_CHECK(best_d1 >= 1, FP_EBOUND, "polymul: no FQT block size fits a 64-bit word (p=%u)", p);
+  pl->kernel = FP_PM_FQT;
+  pl->word = FP_WORD_U64;
+  pl->blk_a = pl->blk_b = best_d1;
+  pl->b = best_b;
+  pl->ndig = 2 * best_d1 - 1;
+  return FP_OK;
+}
+
 fp_status launch_polymul(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t da, const uint8_t* B,
                          uint32_t db, uint8_t* C, size_t batch, int algo, cudaStream_t st) {
-  uint32_t ka = da + 1, kb = db + 1, kc = ka + kb - 1;
-  if (algo == FP_ALGO_PLAIN) {
+  const uint32_t ka = da + 1, kb = db + 1, kc = ka + kb - 1;
+  fp_polymul_plan_t pl;
+  KaraShape S;
+  size_t ksmem = 0;
+  const fp_status ps = polymul_plan(p, ka, kb, algo, &pl, &S, &ksmem);
+  if (ps != FP_OK) return ps;
+  if (pl.kernel == FP_PM_PLAIN) {
     DivP dv = make_divp(p);
     if (kc <= 64) {
       size_t smem = ((TILE * ka + 15) & ~15u) + ((TILE * kb + 15) & ~15u) + TILE * kc;
@@ -1030,64 +1105,44 @@ fp_status launch_polymul(fp_ctx ctx, uint32_t p, const uint8_t* A, uint32_t da, 
     FP_CUDA(cudaGetLastError());
     return FP_OK;
   }
-  if (algo == FP_ALGO_KARATSUBA) {
-    KaraShape S;
-    uint32_t bk = 0;
-    size_t smem = 0;
-    FP_CHECK(kara_params(p, ka, kb, &S, &bk, &smem), FP_EBOUND,
-             "polymul: no Karatsuba FQT shape fits (p=%u, degrees %u x %u)", p, da, db);
-    RedqParams P = make_redq(p, bk, 2 * S.d1 - 1);
-    FP_CUDA(cudaFuncSetAttribute(k_polymul_kara, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (pl.kernel == FP_PM_KARATSUBA) {
+    RedqParams P = make_redq(p, pl.b, pl.ndig);
+    FP_CUDA(cudaFuncSetAttribute(k_polymul_kara, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem));
     // one thread per leaf-product work item in whole warps, 128 to 256 threads (larger blocks
     // cost registers and blocks per SM and ran slower on 1023 x 1023 products)
     const uint32_t items = S.T * (((2 * S.m + 2) / 4 + 1) / 2);
     const int threads = (int)std::min<uint32_t>(256u, std::max<uint32_t>(128u, (items + 31u) & ~31u));
     int per_sm = 0;
-    FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_polymul_kara, threads, smem));
+    FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_polymul_kara, threads, ksmem));
     FP_CHECK(per_sm >= 1, FP_EUNSUPPORTED, "polymul: Karatsuba block of %d threads does not fit an SM", threads);
     const int grid = grid_for(ctx, batch, per_sm);
     FP_LAUNCH(ctx, "k_polymul_kara", st,
-              k_polymul_kara<<<grid, threads, smem, st>>>(A, B, C, batch, ka, kb, S, P, ctx->d_err));
+              k_polymul_kara<<<grid, threads, ksmem, st>>>(A, B, C, batch, ka, kb, S, P, ctx->d_err));
     FP_CUDA(cudaGetLastError());
     return FP_OK;
   }
-  uint32_t bq = poly_qbits(p, ka, kb);
-  // word order for AUTO: integer words first (no FP64 pipe, which is slow on this part)
-  static const int order_auto[4] = {FP_WORD_U32, FP_WORD_F32, FP_WORD_U64, FP_WORD_F64};
-  int forced = -1;
-  if (algo == FP_ALGO_DQT_F64) forced = FP_WORD_F64;
-  if (algo == FP_ALGO_DQT_U64) forced = FP_WORD_U64;
-  if (algo == FP_ALGO_DQT_F32) forced = FP_WORD_F32;
-  if (algo == FP_ALGO_DQT_U32) forced = FP_WORD_U32;
-  if (kc <= 64) {
-    for (int oi = 0; oi < 4; ++oi) {
-      int w = forced >= 0 ? forced : order_auto[oi];
-      if (product_fits(p, ka, kb, bq, word_beta(w))) {
-        switch (w) {
-          case FP_WORD_F64: return polymul_word_t<double>(ctx, p, A, ka, B, kb, C, batch, bq, st);
-          case FP_WORD_F32: return polymul_word_t<float>(ctx, p, A, ka, B, kb, C, batch, bq, st);
-          case FP_WORD_U64: return polymul_word_t<uint64_t>(ctx, p, A, ka, B, kb, C, batch, bq, st);
-          default: return polymul_word_t<uint32_t>(ctx, p, A, ka, B, kb, C, batch, bq, st);
-        }
-      }
-      if (forced >= 0) break;
+  if (pl.kernel == FP_PM_SINGLE_WORD) {
+    switch (pl.word) {
+      case FP_WORD_F64: return polymul_word_t<double>(ctx, p, A, ka, B, kb, C, batch, pl.b, st);
+      case FP_WORD_F32: return polymul_word_t<float>(ctx, p, A, ka, B, kb, C, batch, pl.b, st);
+      case FP_WORD_U64: return polymul_word_t<uint64_t>(ctx, p, A, ka, B, kb, C, batch, pl.b, st);
+      default: return polymul_word_t<uint32_t>(ctx, p, A, ka, B, kb, C, batch, pl.b, st);
     }
   }
-  // Blocked FQT in u64 words (Sec. 5.2): largest block size d+1 whose accumulated output word
-  // fits 64 bits; digit bound: min(#blocks) (d+1) (p-1)^2 < q.
-  if (forced == FP_WORD_F64 || forced == FP_WORD_F32 || forced == FP_WORD_U32) {
-    set_error("polymul: degrees %u x %u do not fit one word of the forced type; use DQT_U64 or AUTO",
-              da, db);
-    return FP_EBOUND;
-  }
-  uint32_t best_d1 = 0, best_b = 0;
-  fqt_params(p, ka, kb, &best_d1, &best_b);
-  FP_CHECK(best_d1 >= 1, FP_EBOUND, "polymul: no FQT block size fits a 64-bit word (p=%u)", p);
-  RedqParams P = make_redq(p, best_b, 2 * best_d1 - 1);
+  RedqParams P = make_redq(p, pl.b, pl.ndig);
   int grid = grid_for(ctx, batch, 16);
-  FP_LAUNCH(ctx, "k_polymul_fqt", st, k_polymul_fqt<<<grid, 256, 0, st>>>(A, B, C, batch, ka, kb, best_d1, P, ctx->d_err));
+  FP_LAUNCH(ctx, "k_polymul_fqt", st, k_polymul_fqt<<<grid, 256, 0, st>>>(A, B, C, batch, ka, kb, pl.blk_a, P, ctx->d_err));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }
 
 }  // namespace fpd
+
+extern "C" fp_status fp_polymul_plan(uint32_t p, uint32_t dega, uint32_t degb, int algo, fp_polymul_plan_t* out) {
+  using namespace fpd;
+  FP_CHECK(out != nullptr, FP_EINVAL, "fp_polymul_plan: out is NULL");
+  FP_CHECK(p >= 2 && p <= 251 && is_prime(p), FP_EINVAL, "p=%u not a prime <= 251", p);
+  FP_CHECK(dega <= 1023 && degb <= 1023, FP_EINVAL, "degrees must be <= 1023");
+  FP_CHECK(algo >= FP_ALGO_AUTO && algo <= FP_ALGO_KARATSUBA, FP_EINVAL, "bad algo %d", algo);
+  return polymul_plan(p, dega + 1, degb + 1, algo, out, nullptr, nullptr);
+}

@@ -59,6 +59,68 @@ def test_dqt_choose_matches_theorem_bounds(fp):
                     assert largest < 2 ** beta
 
 
+def _q_for(p, digit_max):
+    """Smallest q = 2^b (b >= 1) above the largest digit and at least p (Eq. bounds, strict)."""
+    from oracle import bounds
+    return max(bounds.smallest_pow2_q(digit_max), bounds.smallest_pow2_q(p - 1), 2)
+
+
+def test_polymul_plan_matches_bounds(fp):
+    """The polynomial product's plan against the oracle's bounds: one word per operand when
+    the exact largest product DQT(p-1, ..)^2 fits the word (AUTO takes the first of u32, f32,
+    u64, f64 that fits), else blocks of d+1 coefficients in u64 words with q above the largest
+    digit min(#blocks) (d+1) (p-1)^2 and the largest result word min(#blocks) DQT(p-1..)^2 below
+    2^64; the Karatsuba form pads the block words to m 2^L with L >= 1."""
+    from oracle import dqt
+    beta = {fp.FP_WORD_F64: 52, fp.FP_WORD_U64: 64, fp.FP_WORD_F32: 23, fp.FP_WORD_U32: 32}
+    auto_order = [fp.FP_WORD_U32, fp.FP_WORD_F32, fp.FP_WORD_U64, fp.FP_WORD_F64]
+    forced = {fp.FP_ALGO_DQT_F64: fp.FP_WORD_F64, fp.FP_ALGO_DQT_U64: fp.FP_WORD_U64,
+              fp.FP_ALGO_DQT_F32: fp.FP_WORD_F32, fp.FP_ALGO_DQT_U32: fp.FP_WORD_U32}
+    algos = [fp.FP_ALGO_AUTO, fp.FP_ALGO_PLAIN, fp.FP_ALGO_KARATSUBA] + list(forced)
+    for p in (2, 3, 5, 7, 31, 251):
+        for da, db in ((0, 0), (2, 2), (1, 6), (10, 10), (31, 32), (100, 333), (511, 511), (1023, 1023),
+                       (1023, 0)):
+            ka, kb = da + 1, db + 1
+            q1 = _q_for(p, min(ka, kb) * (p - 1) ** 2)
+            largest1 = dqt.dqt([p - 1] * ka, q1) * dqt.dqt([p - 1] * kb, q1)
+            fits = {w: ka + kb - 1 <= 64 and largest1 < 2 ** bt for w, bt in beta.items()}
+            for algo in algos:
+                try:
+                    pl = fp.fp_polymul_plan(p, da, db, algo)
+                except fp.FpError as e:
+                    assert e.status == fp.FP_EBOUND
+                    assert algo in forced and forced[algo] != fp.FP_WORD_U64 and not fits[forced[algo]]
+                    continue
+                if algo == fp.FP_ALGO_PLAIN:
+                    assert pl["kernel"] == fp.FP_PM_PLAIN
+                    continue
+                if pl["kernel"] == fp.FP_PM_SINGLE_WORD:
+                    assert algo != fp.FP_ALGO_KARATSUBA
+                    w = pl["word"]
+                    assert fits[w] and (1 << pl["b"]) == q1
+                    assert (pl["blk_a"], pl["blk_b"], pl["ndig"]) == (ka, kb, ka + kb - 1)
+                    if algo == fp.FP_ALGO_AUTO:
+                        assert w == next(x for x in auto_order if fits[x])
+                    else:
+                        assert w == forced[algo]
+                    continue
+                # blocked FQT or its Karatsuba form, u64 words
+                assert pl["kernel"] == (fp.FP_PM_KARATSUBA if algo == fp.FP_ALGO_KARATSUBA else fp.FP_PM_FQT)
+                if algo in (fp.FP_ALGO_AUTO, fp.FP_ALGO_DQT_U64):
+                    assert not fits[fp.FP_WORD_U64] if algo == fp.FP_ALGO_DQT_U64 else not any(fits.values())
+                d1 = pl["blk_a"]
+                assert pl["word"] == fp.FP_WORD_U64 and pl["blk_b"] == d1 and pl["ndig"] == 2 * d1 - 1
+                na, nb = -(-ka // d1), -(-kb // d1)
+                q = 1 << pl["b"]
+                assert q == _q_for(p, min(na, nb) * d1 * (p - 1) ** 2)
+                assert min(na, nb) * dqt.dqt([p - 1] * d1, q) ** 2 < 2 ** 64
+                if pl["kernel"] == fp.FP_PM_KARATSUBA:
+                    L, m = pl["L"], pl["m"]
+                    assert L >= 1 and m == -(-max(na, nb) // (1 << L))
+                else:
+                    assert pl["L"] == 0 and pl["m"] == 0
+
+
 def test_mm_choose_matches_eq_lower_upper(fp):
     from oracle import bounds
     for p in (2, 3, 7, 17, 31):
