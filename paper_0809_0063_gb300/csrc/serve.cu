@@ -24,6 +24,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "arena.h"
 #include "fpdqt_internal.cuh"
 
 namespace fpd {
@@ -94,7 +95,7 @@ struct fp_server_s {
   fp_ctx ctx = nullptr;
   fp_server_config cfg{};
   uint8_t* arena = nullptr;
-  std::map<size_t, size_t> free_blocks;          // offset -> size (first fit)
+  FirstFitArena blocks;                           // free runs of the arena (first fit)
   std::vector<cudaStream_t> streams;
   std::vector<uint8_t*> h_in, h_out;              // pinned staging per stream
   size_t stage_bytes = 0;
@@ -112,35 +113,6 @@ struct fp_server_s {
   std::thread th;
   int device = 0;
 
-  bool arena_alloc(size_t bytes, size_t* off) {
-    for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it) {
-      if (it->second >= bytes) {
-        *off = it->first;
-        size_t rest = it->second - bytes;
-        size_t noff = it->first + bytes;
-        free_blocks.erase(it);
-        if (rest) free_blocks[noff] = rest;
-        return true;
-      }
-    }
-    return false;
-  }
-  void arena_free(size_t off, size_t bytes) {
-    auto it = free_blocks.emplace(off, bytes).first;
-    auto nx = std::next(it);
-    if (nx != free_blocks.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_blocks.erase(nx);
-    }
-    if (it != free_blocks.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_blocks.erase(it);
-      }
-    }
-  }
-
   void finish(Batch& b, bool ok) {
     const double t = now_s();
     for (size_t i = 0; i < b.reqs.size(); ++i) {
@@ -153,7 +125,7 @@ struct fp_server_s {
     }
     completed += b.reqs.size();
     if (!ok) failed += b.reqs.size();
-    arena_free(b.blk_off, b.blk_bytes);
+    blocks.release(b.blk_off, b.blk_bytes);
     stream_busy[b.stream] = 0;
   }
 
@@ -253,7 +225,7 @@ struct fp_server_s {
     const size_t total = al256(off);
     // total <= stage_bytes by construction (the take loop above used this exact layout)
     size_t blk = 0;
-    if (!arena_alloc(total, &blk)) {
+    if (!blocks.alloc(total, &blk)) {
       for (auto it = take.rbegin(); it != take.rend(); ++it) pending.push_front(*it);
       return false;
     }
@@ -409,7 +381,7 @@ extern "C" fp_status fp_server_create(fp_ctx ctx, const fp_server_config* cfg, f
   FP_CUDA(cudaSetDevice(ctx->device));
   cudaError_t e = cudaMalloc(&s->arena, cfg->arena_bytes);
   if (e != cudaSuccess) { delete s; set_error("fp_server_create: arena of %llu bytes", (unsigned long long)cfg->arena_bytes); return FP_ENOMEM; }
-  s->free_blocks[0] = cfg->arena_bytes;
+  s->blocks.reset(cfg->arena_bytes);
   s->stage_bytes = std::min<size_t>(cfg->arena_bytes / cfg->streams, (size_t)256 << 20);
   for (uint32_t i = 0; i < cfg->streams; ++i) {
     cudaStream_t st;
