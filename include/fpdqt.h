@@ -116,38 +116,52 @@ typedef struct fp_gf_s* fp_gf;
 /* Create a context on CUDA device `device` (made current on the calling thread).  The
  * context owns: the sticky device error flag, scratch for packed operands (grown on demand
  * with cudaMalloc), REDQ correction tables and the plan cache.  *out receives the handle.
- * Errors: FP_EINVAL (null out / bad device), FP_ECUDA, FP_ENOMEM. */
+ * Errors: FP_EINVAL (null out / bad device), FP_ECUDA, FP_ENOMEM.
+ * Resource management: no counterpart in the paper. */
 fp_status fp_ctx_create(fp_ctx* out, int device);
 
-/* Destroy a context and free everything it owns (synchronises its device first).  NULL ok. */
+/* Destroy a context and free everything it owns (synchronises its device first).  NULL ok.
+ * Resource management: no counterpart in the paper. */
 void fp_ctx_destroy(fp_ctx ctx);
 
-/* Synchronise `stream`, then read and clear the context's sticky device error flag.
+/* Synchronise `stream`, then read and clear the context's sticky device error flag (no
+ * counterpart in the paper: the range check of inputs that the paper assumes valid).
  * Returns FP_EINVAL if any kernel saw a residue outside [0, p-1] (or a GF index outside
  * [0, p^k)), FP_ETIMEOUT if a bounded device wait gave up, FP_ECUDA on a CUDA error. */
 fp_status fp_ctx_status(fp_ctx ctx, void* stream);
 
-/* Thread-local message describing the last error of the calling thread ("" if none). */
+/* Thread-local message describing the last error of the calling thread ("" if none); the
+ * pointer stays valid until the thread's next failing call (no counterpart in the paper). */
 const char* fp_last_error(void);
 
-/* Instrumentation.  fp_ctx_profile(ctx, 1) starts recording a CUDA event pair around every
- * kernel the library launches on this context (on the launch stream), 0 stops, 2 clears the
- * records.  fp_ctx_profile_read synchronises those events and returns, for the kernels whose
- * name starts with `prefix` (NULL or "" = all), the number of recorded launches and their
- * summed device time in milliseconds.  fp_ctx_launches returns the total number of kernels
- * the library has launched on this context since creation (recorded or not). */
+/* Instrumentation (no counterpart in the paper).  mode 1 starts recording a CUDA event pair
+ * around every kernel the library launches on this context (on the launch stream), 0 stops,
+ * 2 clears the records.  Errors: FP_EINVAL (null ctx, other modes). */
 fp_status fp_ctx_profile(fp_ctx ctx, int mode);
+
+/* Instrumentation (no counterpart in the paper): synchronises the recorded events and returns,
+ * for the kernels whose name starts with `prefix` (NULL or "" = all), the number of recorded
+ * launches and their summed device time in milliseconds (either output may be NULL).
+ * Errors: FP_EINVAL (null ctx), FP_ECUDA. */
 fp_status fp_ctx_profile_read(fp_ctx ctx, const char* prefix, uint64_t* launches, double* total_ms);
+
+/* Instrumentation (no counterpart in the paper): the total number of kernels the library has
+ * launched on this context since creation, recorded or not.  Errors: FP_EINVAL (null). */
 fp_status fp_ctx_launches(fp_ctx ctx, uint64_t* count);
 
-/* AUTO-algorithm tuning for fp_matmul.  When enabled (the default), the first FP_MM_AUTO call
+/* Tuning of fp_matmul's AUTO choice (no counterpart in the paper; the candidates are the
+ * packings of Sec. 7 and the plain products).  When enabled (the default), the first FP_MM_AUTO call
  * for a new (p, size class) outside PLAIN_F8's rule times every exact candidate (packed tensor-core, plain
  * tensor-core, u8 tensor-core, packed FP32) once on the caller's own buffers -- all produce the
  * same C -- synchronising the stream, and caches the fastest in the context; later calls of
  * that class use the cached choice without timing.  Do not make that first call inside a
  * stream capture.  With tuning disabled AUTO uses a fixed rule measured on GB300.
- * fp_ctx_autotune_choice reports the cached algorithm for (p, m, n, k) or -1. */
+ * fp_ctx_autotune_choice reports the cached algorithm for (p, m, n, k) or -1.
+ * fp_ctx_autotune errors: FP_EINVAL (ctx NULL). */
 fp_status fp_ctx_autotune(fp_ctx ctx, int enable);
+
+/* The cached AUTO choice for (p, m, n, k), or -1 when that class has not been tuned (no
+ * counterpart in the paper).  Errors: FP_EINVAL (null ctx or algo). */
 fp_status fp_ctx_autotune_choice(fp_ctx ctx, uint32_t p, int m, int n, int k, int* algo);
 
 /* ---------------------------------------------------------------- planner (host only) */
@@ -167,7 +181,9 @@ fp_status fp_dqt_choose(uint32_t p, uint32_t k, uint64_t n_accum, uint32_t word,
  * strict), e = the largest number of residues per word whose largest packed value fits the
  * word (Eq. upper; e = floor(beta / log2 Q) up to the exact-range refinement).  For FP32
  * words the inner dimension is chunked: *chunk receives the chunk length (kdim when no
- * chunking is needed) and b, e refer to one chunk.  Host only. */
+ * chunking is needed) and b, e refer to one chunk.  Host only.
+ * Errors: FP_EINVAL (null outputs, p not a prime <= 251, kdim = 0), FP_EBOUND (no packing
+ * fits the algo's word, or the algo's own limit on p). */
 fp_status fp_mm_choose(uint32_t p, uint64_t kdim, uint32_t algo, uint32_t* b, uint32_t* e,
                        uint32_t* chunk);
 
@@ -185,7 +201,8 @@ fp_status fp_dqt_pack(fp_ctx ctx, const fp_dqt_params* prm, const uint8_t* coeff
  * the top digit (j = ndig-1) takes all remaining high bits.  Each word must be a
  * non-negative integer < the word's exact range (2^52 for F64, 2^23 for F32) whose lower
  * ndig-1 base-q digits are < q -- which holds whenever it was produced under the planner's
- * bounds.  words: device [count] of prm->word; coeffs: device uint8 [count][ndig]. */
+ * bounds.  words: device [count] of prm->word; coeffs: device uint8 [count][ndig].
+ * Errors: FP_EINVAL (ctx or arrays NULL; p, word, b or ndig out of range), FP_ECUDA. */
 fp_status fp_dqt_unpack_redq(fp_ctx ctx, const fp_dqt_params* prm, const void* words,
                              uint8_t* coeffs, size_t count, void* stream);
 
@@ -228,7 +245,9 @@ fp_status fp_polymul_plan(uint32_t p, uint32_t dega, uint32_t degb, int algo, fp
 /* Modular dot product (Algorithm 1 with degree-0 entries): *out = (sum u_i v_i) mod p.
  * u, v: device uint8 [n]; out: device uint32 scalar.  DQT algos use the middle-product
  * packing of Sec. 7.1 (d+1 entries per word, reversed on the left), PLAIN uses delayed
- * reduction.  n <= 2^40.  Uses context scratch for per-block partial results. */
+ * reduction.  n <= 2^40.  Uses context scratch for per-block partial results.
+ * Errors: FP_EINVAL (ctx, out or arrays NULL, p not a prime <= 251, n > 2^40, bad algo;
+ * a residue >= p is reported by fp_ctx_status), FP_EBOUND (a forced packing does not fit). */
 fp_status fp_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v, size_t n,
                  uint32_t* out, int algo, void* stream);
 
@@ -292,7 +311,9 @@ fp_status fp_matmul_grouped(fp_ctx ctx, const fp_mm_problem* problems, size_t co
 
 /* Right compression of B alone (Sec. 7.4): CB[l][j] = sum_{t<e} B[l][j e + t] Q^t with
  * Q = 2^b, missing columns of the last block taken as zero (partial compression, Sec. 7.1).
- * CB: device array k x ceil(n/e) of `word` (F64 or F32 or U64).  Exposed for tests and reuse. */
+ * CB: device array k x ceil(n/e) of `word` (F64 or F32 or U64).  Exposed for tests and reuse.
+ * Errors: FP_EINVAL (sizes, b, e or word out of range), FP_EBOUND (the packed word
+ * exceeds the word's exact range). */
 fp_status fp_pack_cb(fp_ctx ctx, uint32_t p, int k, int n, const uint8_t* B, int ldb,
                      uint32_t b, uint32_t e, uint32_t word, void* CB, void* stream);
 
@@ -303,18 +324,26 @@ fp_status fp_pack_cb(fp_ctx ctx, uint32_t p, int k, int n, const uint8_t* B, int
  * irreducibility test); q = 2^b is the smallest power of two above k (p-1)^2; the tables of
  * Algorithm FGDP (element -> packed word, L and H folding the REDQ correction and the
  * reduction by the modulus) are built on the host and copied to the device.  Elements are
- * indices sum_i c_i p^i: uint8 when p^k <= 256, else uint16. */
+ * indices sum_i c_i p^i: uint8 when p^k <= 256, else uint16.
+ * Errors: FP_EINVAL (p, k or p^k out of range), FP_EUNSUPPORTED (tables or the product
+ * word too large), FP_ENOMEM, FP_ECUDA. */
 fp_status fp_gf_create(fp_ctx ctx, uint32_t p, uint32_t k, fp_gf* out);
+
+/* Free a field's host and device tables (NULL ok).  Resource management: no counterpart in
+ * the paper. */
 void fp_gf_destroy(fp_gf gf);
 
-/* Query a field: modulus coefficients (k+1 values, constant term first) into `modulus`
- * (may be NULL), q exponent b, packed word type, and element width in bytes. */
+/* Query a field (Sec. 6, the parameters of Algorithm FGDP's tables): modulus coefficients
+ * (k+1 values, constant term first) into `modulus` (may be NULL), q exponent b, packed word
+ * type, and element width in bytes.  Errors: FP_EINVAL (gf NULL). */
 fp_status fp_gf_info(fp_gf gf, uint32_t* modulus, uint32_t* b, uint32_t* word,
                      uint32_t* elem_bytes);
 
 /* Batched multiply c[i] = a[i] * b[i] in GF(p^k) by Algorithm FGDP with n = 1: table DQT,
  * one word product, REDQ compression, two lookups (L, H) and one field addition.
- * a, b, c: device arrays of `count` element indices (width per fp_gf_info). */
+ * a, b, c: device arrays of `count` element indices (width per fp_gf_info).
+ * Errors: FP_EINVAL (null ctx, field or arrays; an index >= p^k is reported by
+ * fp_ctx_status). */
 fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf gf, const void* a, const void* b, void* c,
                             size_t count, void* stream);
 
@@ -334,8 +363,9 @@ enum { FP_GF_INDEX = 0, FP_GF_LOG = 1 };
 fp_status fp_gf_dot(fp_ctx ctx, fp_gf gf, const void* a, const void* b, size_t n, void* out,
                     int form, void* stream);
 
-/* The dot product's parameters: index of the generator g of the log form, exponent b_dot of
- * its q, and the number of word products accumulated per REDQ.  Any argument may be NULL. */
+/* The dot product's parameters (Algorithm FGDP, Sec. 6): index of the generator g of the log
+ * form, exponent b_dot of its q, and the number of word products accumulated per REDQ.  Any
+ * output may be NULL.  Errors: FP_EINVAL (gf NULL). */
 fp_status fp_gf_dot_info(fp_gf gf, uint32_t* generator, uint32_t* b_dot, uint32_t* chunk);
 
 /* ---------------------------------------------------------------- uneven batches */
@@ -353,7 +383,8 @@ typedef struct {
   uint8_t* C;
 } fp_instance;
 
-/* Run all `count` instances: matrix products with k (p-1)^2 < 2^24, m, n >= 64 and
+/* Uneven batch (no counterpart in the paper as a call; each instance's packing follows
+ * Sec. 7.6.1).  Run all `count` instances: matrix products with k (p-1)^2 < 2^24, m, n >= 64 and
  * m n k >= 2^21 go to the tensor cores -- p <= 17 to the grouped e4m3 kernel (operands first
  * copied to 16-byte row strides and range-checked in one launch), 17 < p <= 127 to the bf16
  * kernel (operands converted and range-checked in one launch), up to 64 products per launch;
@@ -419,23 +450,30 @@ typedef struct fp_server_s* fp_server;
  * Errors: FP_EINVAL (bad config), FP_ENOMEM, FP_ECUDA. */
 fp_status fp_server_create(fp_ctx ctx, const fp_server_config* cfg, fp_server* out);
 
-/* Thread-safe.  Validates the request (FP_EINVAL, FP_EBOUND) and queues it; *ticket numbers
- * requests from 0 in submission order. */
+/* Serving (no counterpart in the paper).  Thread-safe.  Validates the request (FP_EINVAL,
+ * FP_EBOUND) and queues it; *ticket numbers requests from 0 in submission order. */
 fp_status fp_server_submit(fp_server s, const fp_request* req, uint64_t* ticket);
 
-/* *done = 1 once the result is in host_out (then *latency_us is set), else 0.  A request
- * that failed on the device reports done = -1. */
+/* Serving (no counterpart in the paper): *done = 1 once the result is in host_out (then
+ * *latency_us is set), else 0.  A request that failed on the device reports done = -1.
+ * Errors: FP_EINVAL (null server or outputs, unknown ticket). */
 fp_status fp_server_poll(fp_server s, uint64_t ticket, int* done, double* latency_us);
 
-/* Wait until every submitted request is done or timeout_s passes (FP_ETIMEOUT). */
+/* Serving (no counterpart in the paper): wait until every submitted request is done.
+ * Errors: FP_ETIMEOUT when timeout_s passes first, FP_EINVAL (null server). */
 fp_status fp_server_drain(fp_server s, double timeout_s);
 
-/* Latencies (microseconds) of tickets [first, first+n) into out (-1 for not done). */
+/* Serving (no counterpart in the paper): latencies in microseconds of tickets
+ * [first, first+n) into out; -1 for a ticket not done, failed or not yet issued.
+ * Errors: FP_EINVAL (null server or out). */
 fp_status fp_server_latencies(fp_server s, uint64_t first, size_t n, double* out);
 
+/* Serving (no counterpart in the paper): counters of submitted, completed and failed
+ * requests, batches and kernel launches.  Errors: FP_EINVAL (null). */
 fp_status fp_server_stats_get(fp_server s, fp_server_stats* out);
 
-/* Stops the scheduler after draining outstanding work (bounded) and frees everything. */
+/* Serving (no counterpart in the paper): stops the scheduler after draining outstanding work
+ * (bounded) and frees everything.  NULL ok. */
 void fp_server_destroy(fp_server s);
 
 #ifdef __cplusplus
