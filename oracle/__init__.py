@@ -11,7 +11,8 @@ Modules
   field   plain definitions: polynomial product, dot product and matrix product with every
           coefficient reduced by %, GF(p^k) by explicit remainder, irreducibility brute force
   dqt     Discrete Q-adic Transform (Eq. dqt), its inverse by radix conversion
-          (the inverse in Algorithm 1), REDQ (Algorithm 2) and its correction matrix/tables (Sec. 3)
+          (the inverse in Algorithm 1), REDQ (Algorithm 2) and its correction matrix/tables (Sec. 3),
+          right, middle-product and full (Q, Theta) compression (Sec. 7)
   fdiv    exact software floating point with a parametric mantissa, FDIV (Algorithm 3),
           AFDIV (Algorithm 4) and the rounding-mode table (Table "fdiv", Sec. 4)
   bounds  exactness bounds (Eq. bounds, Eq. delayed, Eq. lower, Eq. upper), compression

@@ -137,6 +137,52 @@ def right_compressed_product(A, B, p, e, Q):
     return C
 
 
+def full_compress_rows(A, dq, Q):
+    """Full compression, left operand (Sec. 7.5): word [r][l] = sum_{i<=dq} A[r(dq+1)+i][l] Q^i,
+    missing rows of a ragged last block taken as zero.  Exact integers, shape [ceil(m/(dq+1)), k]."""
+    A = np.asarray(A, dtype=np.int64)
+    m, k = A.shape
+    nr = -(-m // (dq + 1))
+    W = np.zeros((nr, k), dtype=object)
+    for r in range(nr):
+        for i in range(dq, -1, -1):
+            row = r * (dq + 1) + i
+            v = A[row, :].astype(object) if row < m else np.zeros(k, dtype=object)
+            W[r, :] = W[r, :] * Q + v
+    return W
+
+
+def full_compress_cols(B, dt, Theta):
+    """Full compression, right operand (Sec. 7.5): word [l][c] = sum_{j<=dt} B[l][c(dt+1)+j]
+    Theta^j, missing columns of a ragged last block taken as zero.  Shape [k, ceil(n/(dt+1))]."""
+    return right_compress(B, dt + 1, Theta)
+
+
+def full_compressed_product(A, B, p, dq, dt, Q, s):
+    """Full compression (Sec. 7.5) with Theta = Q^s, s >= dq + 1 (Eq. qtheta): the exact
+    integer product of the compressed operands holds C[r(dq+1)+i][c(dt+1)+j] as the coefficient
+    of Q^i Theta^j = Q^(i + s j); with every coefficient below Q (Eq. lower) the word is a base-Q
+    number and REDQ over its s dt + dq + 1 digits gives them mod p.  Returns C (m x n) mod p."""
+    assert s >= dq + 1
+    A = np.asarray(A, dtype=np.int64)
+    B = np.asarray(B, dtype=np.int64)
+    m, n = A.shape[0], B.shape[1]
+    WA = full_compress_rows(A, dq, Q)
+    WB = full_compress_cols(B, dt, Q ** s)
+    CC = WA @ WB
+    C = np.zeros((m, n), dtype=np.int64)
+    ndig = s * dt + dq + 1
+    for r in range(CC.shape[0]):
+        for c in range(CC.shape[1]):
+            mu = redq(int(CC[r, c]), p, Q, ndig - 1)
+            for i in range(dq + 1):
+                for j in range(dt + 1):
+                    row, col = r * (dq + 1) + i, c * (dt + 1) + j
+                    if row < m and col < n:
+                        C[row, col] = mu[i + s * j]
+    return C
+
+
 def middle_product_dot(u, v, p, d, Q):
     """Middle-product dot product (Sec. 7.1): blocks of d+1 entries are packed reversed on
     the left (sum_t u_{l(d+1)+t} Q^{d-t}) and forward on the right; the coefficient of Q^d of

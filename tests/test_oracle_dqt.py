@@ -144,3 +144,43 @@ def test_right_compressed_product_random_ragged():
         B = rng.integers(0, p, (k, n))
         Q = 1 << ((k * (p - 1) ** 2).bit_length())
         assert np.array_equal(dqt.right_compressed_product(A, B, p, e, Q), field.matmul_mod(A, B, p))
+
+
+def test_full_compression_2x2_identity():
+    """Sec. 7.5's example: [a+Qc, b+Qd] x [e+Theta f; g+Theta h] =
+    (ae+bg) + Q(ce+dg) + Theta(af+bh) + Q Theta(cf+dh), written out here term by term."""
+    rng = np.random.default_rng(75)
+    for _ in range(50):
+        a, b, c, d, e, f, g, h = (int(x) for x in rng.integers(0, 1000, 8))
+        Q = 1 << int(rng.integers(20, 24))
+        Theta = Q * Q
+        WA = dqt.full_compress_rows(np.array([[a, b], [c, d]]), 1, Q)
+        WB = dqt.full_compress_cols(np.array([[e, f], [g, h]]), 1, Theta)
+        assert WA.shape == (1, 2) and WB.shape == (2, 1)
+        assert int((WA @ WB)[0, 0]) == (a * e + b * g) + Q * (c * e + d * g) + Theta * (a * f + b * h) \
+            + Q * Theta * (c * f + d * h)
+
+
+@pytest.mark.parametrize("p,m,k,n,dq,dt,extra", [(3, 7, 50, 5, 1, 1, 0), (2, 5, 9, 11, 2, 3, 0), (5, 6, 20, 7, 1, 2, 1),
+                                                 (7, 3, 33, 4, 0, 2, 0), (3, 1, 1, 1, 2, 2, 0)])
+def test_full_compressed_product_matches_plain(p, m, k, n, dq, dt, extra):
+    """Full compression with Q > k (p-1)^2 (Eq. lower) and Theta = Q^(dq+1+extra) (Eq. qtheta)
+    reproduces A B mod p on ragged shapes; all-(p-1) operands reach the digit bound's edge."""
+    rng = np.random.default_rng(p * 100 + m)
+    Q = 2
+    while Q <= k * (p - 1) ** 2:
+        Q *= 2
+    for A, B in [(rng.integers(0, p, (m, k)), rng.integers(0, p, (k, n))),
+                 (np.full((m, k), p - 1), np.full((k, n), p - 1))]:
+        assert np.array_equal(dqt.full_compressed_product(A, B, p, dq, dt, Q, dq + 1 + extra),
+                              field.matmul_mod(A, B, p))
+
+
+def test_full_compression_non_strict_q_breaks():
+    """At Q = k (p-1)^2 (the non-strict reading of Eq. lower) an all-(p-1) product carries into
+    the next digit and the result is wrong; one more bit of Q fixes it."""
+    p, k = 3, 16
+    A, B = np.full((2, k), p - 1), np.full((k, 2), p - 1)
+    want = field.matmul_mod(A, B, p)
+    assert not np.array_equal(dqt.full_compressed_product(A, B, p, 1, 1, k * (p - 1) ** 2, 2), want)
+    assert np.array_equal(dqt.full_compressed_product(A, B, p, 1, 1, 2 * k * (p - 1) ** 2, 2), want)

@@ -109,3 +109,18 @@ def test_gf_dot_is_symmetric_and_bilinear(pk, n, seed):
     assert dot(field.gf_add(a, c, p, k), b) == int(field.gf_add(np.array(dot(a, b)), np.array(dot(c, b)), p, k))
     sa = field.gf_mul(np.full(n, s), a, p, k, m)
     assert dot(sa, b) == int(field.gf_mul(np.array(s), np.array(dot(a, b)), p, k, m))
+
+
+@settings(max_examples=60, deadline=None)
+@given(p=st.sampled_from(PRIMES[:5]), m=st.integers(1, 8), k=st.integers(1, 30), n=st.integers(1, 8),
+       dq=st.integers(0, 3), dt=st.integers(0, 3), extra=st.integers(0, 2), seed=st.integers(0, 2 ** 32 - 1))
+def test_full_compressed_product_matches_plain_product(p, m, k, n, dq, dt, extra, seed):
+    """Sec. 7.5: compressing A's rows by Q and B's columns by Theta = Q^(dq+1+extra) (Eq.
+    qtheta) with Q > k (p-1)^2 (Eq. lower) gives A B mod p for any shape and degrees."""
+    Q = 2
+    while Q <= k * (p - 1) ** 2:
+        Q *= 2
+    rng = np.random.default_rng(seed)
+    A = rng.integers(0, p, (m, k))
+    B = rng.integers(0, p, (k, n))
+    assert np.array_equal(dqt.full_compressed_product(A, B, p, dq, dt, Q, dq + 1 + extra), field.matmul_mod(A, B, p))
