@@ -110,7 +110,9 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: the package's build folder unless FPDQT_CLOCKS_DIR names another one
+        folder = os.environ.get("FPDQT_CLOCKS_DIR") or os.path.join(ROOT, "paper_0809_0063_gb300", "_build")
+        self.path = os.path.join(folder, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
