@@ -18,7 +18,7 @@ Modules
   bounds  exactness bounds (Eq. bounds, Eq. delayed, Eq. lower, Eq. upper), compression
           factor e (Sec. 7.6.1) and the operation-count model (Table "mulpol")
   gfpk    Algorithm FGDP's tables built from the plain field definition (Sec. 6); the plain
-          GF(p^k) dot product, the generator and the discrete-log form live in field
+          GF(p^k) dot and matrix products, the generator and the discrete-log form live in field
 
 Parity status: every function here is pinned by tests under tests/ (paper examples,
 closed forms, brute force); none is "parity unpinned".

@@ -206,3 +206,17 @@ def log_tables(p, k, modulus):
     log = np.zeros(order, dtype=np.int64)
     log[antilog] = np.arange(order)
     return antilog, log
+
+
+def gf_matmul(A, B, p, k, modulus):
+    """Matrix product over GF(p^k) (the matrix case of Algorithm FGDP's dot product, Sec. 6):
+    C[i][j] = sum_l A[i][l] B[l][j] in the field, for index matrices.  Written as the coefficient
+    convolutions of every product summed over l, reduced mod p and then by the modulus once."""
+    ca = index_to_coeffs(np.asarray(A, dtype=np.int64), p, k)        # [m][kk][k]
+    cb = index_to_coeffs(np.asarray(B, dtype=np.int64), p, k)        # [kk][n][k]
+    m, n = ca.shape[0], cb.shape[1]
+    s = np.zeros((m, n, 2 * k - 1), dtype=np.int64)
+    for i in range(k):
+        for j in range(k):
+            s[:, :, i + j] = (s[:, :, i + j] + (ca[:, :, i] @ cb[:, :, j]) % p) % p
+    return coeffs_to_index(poly_rem_mod(s, modulus, p), p)

@@ -197,3 +197,26 @@ def test_gf_dot_closed_forms_and_fold(p, k):
     lhs = field.gf_dot(a, field.gf_add(b, c, p, k), p, k, m)
     rhs = field.gf_add(np.array(field.gf_dot(a, b, p, k, m)), np.array(field.gf_dot(a, c, p, k, m)), p, k)
     assert lhs == int(rhs)
+
+
+@pytest.mark.parametrize("p,k", [(3, 5), (7, 2), (2, 8), (5, 1), (3, 2)])
+def test_gf_matmul_ring_laws(p, k):
+    """The GF(p^k) matrix product: the identity matrix is neutral, the product is associative
+    and distributes over addition, every entry is the row-by-column field dot product, and for
+    k = 1 it is the prime-field product mod p."""
+    m = field.smallest_monic_irreducible(p, k)
+    q = p ** k
+    rng = np.random.default_rng(q + 3)
+    A, B, C = rng.integers(0, q, (4, 6)), rng.integers(0, q, (6, 5)), rng.integers(0, q, (5, 3))
+    mm = lambda x, y: field.gf_matmul(x, y, p, k, m)
+    eye = np.eye(6, dtype=np.int64)                 # index 1 is the field's one
+    assert np.array_equal(mm(A, eye), A)
+    assert np.array_equal(mm(mm(A, B), C), mm(A, mm(B, C)))
+    B2 = rng.integers(0, q, (6, 5))
+    assert np.array_equal(mm(A, field.gf_add(B, B2, p, k)), field.gf_add(mm(A, B), mm(A, B2), p, k))
+    AB = mm(A, B)
+    for i in range(4):
+        for j in range(5):
+            assert AB[i, j] == field.gf_dot(A[i], B[:, j], p, k, m)
+    if k == 1:
+        assert np.array_equal(AB, field.matmul_mod(A, B, p))
