@@ -137,6 +137,31 @@ def right_compressed_product(A, B, p, e, Q):
     return C
 
 
+def split_plan(k, chunk, p, beta):
+    """Inner-dimension splitting (Sec. 7.6, after Table comprange): the inner dimension k is cut
+    into pieces of at most `chunk`; each piece gets its own Q (Eq. lower for the piece's length)
+    and compression e = floor(beta / log2 Q) (Sec. 7.6.1).  Returns [(start, length, Q, e)]."""
+    from .bounds import cmm_Q, compression_factor
+    plan = []
+    for l0 in range(0, k, chunk):
+        kc = min(chunk, k - l0)
+        Q = cmm_Q(kc, p)
+        plan.append((l0, kc, Q, compression_factor(beta, Q)))
+    return plan
+
+
+def split_right_compressed_product(A, B, p, chunk, beta):
+    """Right-compressed product with the inner dimension split by split_plan: each piece is a
+    right-compressed product reduced by REDQ (the extra modular reductions), and the pieces'
+    results are added mod p.  Returns C (m x n) mod p."""
+    A = np.asarray(A, dtype=np.int64)
+    B = np.asarray(B, dtype=np.int64)
+    C = np.zeros((A.shape[0], B.shape[1]), dtype=np.int64)
+    for l0, kc, Q, e in split_plan(A.shape[1], chunk, p, beta):
+        C = (C + right_compressed_product(A[:, l0:l0 + kc], B[l0:l0 + kc, :], p, e, Q)) % p
+    return C
+
+
 def full_compress_rows(A, dq, Q):
     """Full compression, left operand (Sec. 7.5): word [r][l] = sum_{i<=dq} A[r(dq+1)+i][l] Q^i,
     missing rows of a ragged last block taken as zero.  Exact integers, shape [ceil(m/(dq+1)), k]."""

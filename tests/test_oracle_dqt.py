@@ -184,3 +184,27 @@ def test_full_compression_non_strict_q_breaks():
     want = field.matmul_mod(A, B, p)
     assert not np.array_equal(dqt.full_compressed_product(A, B, p, 1, 1, k * (p - 1) ** 2, 2), want)
     assert np.array_equal(dqt.full_compressed_product(A, B, p, 1, 1, 2 * k * (p - 1) ** 2, 2), want)
+
+
+def test_split_inner_dimension_keeps_compression_four():
+    """Sec. 7.6: over F_3 with 53-bit words the compression drops from 4 to 3 once n (p-1)^2
+    reaches 2^13 (with the strict digit bound that is at n = 2048, one dimension before the
+    paper's table); an inner dimension of 2049 cut into pieces of 1025 and 1024 keeps
+    Q = 2^13 and compression 4 in each piece."""
+    from oracle import bounds
+    assert bounds.compression_factor(53, bounds.cmm_Q(2047, 3)) == 4
+    assert bounds.compression_factor(53, bounds.cmm_Q(2048, 3)) == 3
+    assert bounds.compression_factor(53, bounds.cmm_Q(2049, 3)) == 3
+    plan = dqt.split_plan(2049, 1025, 3, 53)
+    assert [(l0, kc) for l0, kc, _, _ in plan] == [(0, 1025), (1025, 1024)]
+    assert all(Q == 1 << 13 and e == 4 for _, _, Q, e in plan)
+
+
+@pytest.mark.parametrize("p,m,k,n,chunk", [(3, 5, 70, 9, 16), (7, 4, 33, 6, 10), (2, 3, 100, 13, 64), (5, 2, 9, 3, 1)])
+def test_split_right_compressed_product_matches_plain(p, m, k, n, chunk):
+    """Splitting the inner dimension (ragged last piece included) and adding the pieces' REDQ
+    results mod p gives A B mod p; all-(p-1) operands reach each piece's digit bound."""
+    rng = np.random.default_rng(p + k)
+    for A, B in [(rng.integers(0, p, (m, k)), rng.integers(0, p, (k, n))),
+                 (np.full((m, k), p - 1), np.full((k, n), p - 1))]:
+        assert np.array_equal(dqt.split_right_compressed_product(A, B, p, chunk, 53), field.matmul_mod(A, B, p))
