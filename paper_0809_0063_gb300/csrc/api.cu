@@ -250,6 +250,7 @@ extern "C" fp_status fp_ctx_create(fp_ctx* out, int device) {
   e = cudaMalloc(&c->d_err, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(uint32_t));
   if (e != cudaSuccess) {
+    if (c->d_err) cudaFree(c->d_err);
     delete c;
     return cuda_fail(e, "fp_ctx_create");
   }

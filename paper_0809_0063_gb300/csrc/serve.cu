@@ -378,25 +378,34 @@ extern "C" fp_status fp_server_create(fp_ctx ctx, const fp_server_config* cfg, f
   s->ctx = ctx;
   s->cfg = *cfg;
   s->device = ctx->device;
-  FP_CUDA(cudaSetDevice(ctx->device));
+  const cudaError_t de = cudaSetDevice(ctx->device);
+  if (de != cudaSuccess) {
+    delete s;
+    return cuda_fail(de, "fp_server_create: cudaSetDevice");
+  }
   cudaError_t e = cudaMalloc(&s->arena, cfg->arena_bytes);
   if (e != cudaSuccess) { delete s; set_error("fp_server_create: arena of %llu bytes", (unsigned long long)cfg->arena_bytes); return FP_ENOMEM; }
   s->blocks.reset(cfg->arena_bytes);
   s->stage_bytes = std::min<size_t>(cfg->arena_bytes / cfg->streams, (size_t)256 << 20);
+  // every resource is recorded as soon as it exists, so that fp_server_destroy frees a
+  // partly built server (its scheduler thread has not started yet)
+  auto fail = [s]() {
+    fp_server_destroy(s);
+    set_error("fp_server_create: stream / pinned staging allocation failed");
+    return FP_ENOMEM;
+  };
   for (uint32_t i = 0; i < cfg->streams; ++i) {
     cudaStream_t st;
-    cudaEvent_t ev;
-    uint8_t *hi, *ho;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(&hi, s->stage_bytes) != cudaSuccess || cudaMallocHost(&ho, s->stage_bytes) != cudaSuccess) {
-      fp_server_destroy(s);
-      set_error("fp_server_create: stream / pinned staging allocation failed");
-      return FP_ENOMEM;
-    }
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return fail();
     s->streams.push_back(st);
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return fail();
     s->events.push_back(ev);
+    uint8_t* hi;
+    if (cudaMallocHost(&hi, s->stage_bytes) != cudaSuccess) return fail();
     s->h_in.push_back(hi);
+    uint8_t* ho;
+    if (cudaMallocHost(&ho, s->stage_bytes) != cudaSuccess) return fail();
     s->h_out.push_back(ho);
     s->stream_busy.push_back(0);
   }
