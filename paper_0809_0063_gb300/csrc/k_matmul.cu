@@ -778,7 +778,11 @@ fp_status launch_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8
   // FP64 words are only timed when nothing faster is valid
   cudaEvent_t e0, e1;
   FP_CUDA(cudaEventCreate(&e0));
-  FP_CUDA(cudaEventCreate(&e1));
+  const cudaError_t ee = cudaEventCreate(&e1);
+  if (ee != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ee, "cudaEventCreate");
+  }
   int best = cand[0];
   float best_ms = 1e30f;
   for (int i = 0; i < nc; ++i) {
