@@ -410,7 +410,9 @@ static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st) {
   const size_t cper = (size_t)dim * dim;        // one C (dim x dim)
   void* buf = nullptr;
   bool packed = k >= 448;
-  if (cudaMalloc(&buf, 2 * per * nin + cper * nin) == cudaSuccess) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool timed = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  if (timed && cudaMalloc(&buf, 2 * per * nin + cper * nin) == cudaSuccess) {
     uint8_t* A = (uint8_t*)buf;
     uint8_t* Cb = A + 2 * per * nin;
     k_fill_mod<<<ctx->num_sms * 4, 256, 0, st>>>(A, 2 * per * nin, p, 12345u + p);
@@ -419,9 +421,6 @@ static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st) {
       v[i] = fp_instance{0, p, dim, dim, kk, 0, A + per * i, A + per * (nin + i), Cb + cper * i};
     }
     float best[2] = {1e30f, 1e30f};
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
     for (int rep = 0; rep < 2; ++rep)
       for (int pk = 0; pk < 2; ++pk) {
         for (auto& x : v) x.reserved = (uint32_t)pk;
@@ -433,12 +432,12 @@ static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st) {
         cudaEventElapsedTime(&ms, e0, e1);
         best[pk] = std::min(best[pk], ms);
       }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     cudaStreamSynchronize(st);
     cudaFree(buf);
     packed = best[1] < best[0];
   }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   ctx->tune[key] = packed ? 1 : 0;
   return packed;
 }
