@@ -89,22 +89,42 @@ enum {
                            of 16 are read in place; other layouts are first copied padded */
   FP_MM_LEFT_F64 = 10,  /* left compression by transposition with FP64 words (DMMA), e rows of A
                            per word as RIGHT_F64 packs e columns of B */
-  FP_MM_CMM_F64 = 11    /* compressed matrix multiplication by the middle product (Sec. 7.1):
+  FP_MM_CMM_F64 = 11,   /* compressed matrix multiplication by the middle product (Sec. 7.1):
                            d+1 entries of the inner dimension per FP64 word, A reversed, B
                            forward, q = 2^b > k (p-1)^2, d the largest with (2d+1) b <= 52 so
                            every word product is exact; C_ij is the digit of q^d mod p.  Needs
                            d >= 1, i.e. k (p-1)^2 < 2^17, else FP_EBOUND */
+  FP_MM_FULL_F64 = 12,  /* full compression (Sec. 7.5, Eq. qtheta, Eq. dq): dq1 rows of A per FP64
+                           word at Q = 2^b, dt1 columns of B per word at Theta = Q^dq1 (the
+                           smallest Theta Eq. qtheta allows), DMMA product of the packed words,
+                           REDQ over dq1 dt1 base-Q digits; dq1, dt1 >= 2 chosen by
+                           fp_mm_full_choose, the inner dimension split into pieces (as
+                           SPLIT_F64) when it is too long for a 2 x 2 packing in one piece */
+  FP_MM_SPLIT_F64 = 13  /* right compression (Sec. 7.4) with the inner dimension cut into pieces
+                           (Sec. 7.6, after Table comprange) that each keep the compression e of
+                           a shorter product: e.g. p = 3 keeps e = 4 past k = 2047, where
+                           RIGHT_F64 drops to e = 3.  Pieces' digits are added into wider fields
+                           and reduced by REDQ; see fp_mm_choose for the piece length */
 };
 
-/* Parameters of one packed representation (Sec. 2.3): q = 2^b, k residues packed per
- * operand word, ndig residues recovered per result word, n_accum products accumulated. */
+/* Forms of q in fp_dqt_params.qform. */
+enum {
+  FP_Q_POW2 = 0,    /* q = 2^b (Sec. 3, end: conversions by shifts, tabulated correction) */
+  FP_Q_P_POW2 = 1   /* q = p 2^b (the conclusion's alternative): p divides q, so REDQ needs no
+                       correction (mu_i = u_i), and floor(r / q^i) = floor(r / p^i) >> (b i)
+                       makes every division one by p */
+};
+
+/* Parameters of one packed representation (Sec. 2.3): q = 2^b (or p 2^b, see qform), k residues
+ * packed per operand word, ndig residues recovered per result word, n_accum products
+ * accumulated.  fp_dqt_choose fills qform = FP_Q_POW2. */
 typedef struct {
   uint32_t p;
   uint32_t k;
   uint32_t b;
   uint32_t ndig;
   uint32_t word;     /* fp_word */
-  uint32_t reserved;
+  uint32_t qform;    /* FP_Q_POW2 or FP_Q_P_POW2 */
   uint64_t n_accum;
 } fp_dqt_params;
 
@@ -154,8 +174,9 @@ fp_status fp_ctx_launches(fp_ctx ctx, uint64_t* count);
  * for a new (p, size class) outside PLAIN_F8's rule times every exact candidate (packed tensor-core, plain
  * tensor-core, u8 tensor-core, packed FP32) once on the caller's own buffers -- all produce the
  * same C -- synchronising the stream, and caches the fastest in the context; later calls of
- * that class use the cached choice without timing.  Do not make that first call inside a
- * stream capture.  With tuning disabled AUTO uses a fixed rule measured on GB300.
+ * that class use the cached choice without timing.  Inside a stream capture an untuned class
+ * takes the fixed rule without timing and without caching it.  With tuning disabled AUTO uses
+ * a fixed rule measured on GB300.
  * fp_ctx_autotune_choice reports the cached algorithm for (p, m, n, k) or -1.
  * fp_ctx_autotune errors: FP_EINVAL (ctx NULL). */
 fp_status fp_ctx_autotune(fp_ctx ctx, int enable);
@@ -181,18 +202,35 @@ fp_status fp_dqt_choose(uint32_t p, uint32_t k, uint64_t n_accum, uint32_t word,
  * strict), e = the largest number of residues per word whose largest packed value fits the
  * word (Eq. upper; e = floor(beta / log2 Q) up to the exact-range refinement).  For FP32
  * words the inner dimension is chunked: *chunk receives the chunk length (kdim when no
- * chunking is needed) and b, e refer to one chunk.  Host only.
+ * chunking is needed) and b, e refer to one chunk.  For FP_MM_SPLIT_F64 (Sec. 7.6) e is the
+ * largest compression that pieces of at least min(kdim, 256) entries keep, *chunk the
+ * balanced piece length (a multiple of 4, or kdim when one piece suffices) and b that of a
+ * piece; for FP_MM_FULL_F64 e = dq1 dt1 and *chunk the piece (fp_mm_full_choose).  Host only.
  * Errors: FP_EINVAL (null outputs, p not a prime <= 251, kdim = 0), FP_EBOUND (no packing
  * fits the algo's word, or the algo's own limit on p). */
 fp_status fp_mm_choose(uint32_t p, uint64_t kdim, uint32_t algo, uint32_t* b, uint32_t* e,
                        uint32_t* chunk);
 
+/* Full-compression parameters (Sec. 7.5): Q = 2^b with k' (p-1)^2 < Q for the piece length k'
+ * (Eq. lower, strict), dq1 = d_q + 1 rows per left word and dt1 = d_theta + 1 columns per right
+ * word, Theta = Q^dq1 (Eq. qtheta), the largest dq1 dt1 (then the most balanced) with
+ * dq1, dt1 >= 2 whose largest packed product, dq1 dt1 digits of at most k' (p-1)^2, is below
+ * 2^52 (Eq. dq with the exact range of FP64 words and FDIV case 3); *piece = k' (= kdim when the
+ * inner dimension is not split; otherwise pieces of at most 4 * ceil(k'/4) entries, balanced,
+ * with k' >= min(kdim, 256) where such pieces allow a 2 x 2 packing, else k' >= 16).  Host only.
+ * Errors: FP_EINVAL (null outputs, p not a prime <= 251, kdim outside [1, 2^30]), FP_EBOUND (no
+ * 2 x 2 packing fits even pieces of 16, i.e. 16 (p-1)^2 >= 2^13: p > 23). */
+fp_status fp_mm_full_choose(uint32_t p, uint64_t kdim, uint32_t* b, uint32_t* dq1, uint32_t* dt1,
+                            uint32_t* piece);
+
 /* ---------------------------------------------------------------- DQT pack / unpack */
 
-/* DQT (Eq. dqt): words[i] = sum_{j<k} coeffs[i*k + j] * q^j, for i < count.
+/* DQT (Eq. dqt): words[i] = sum_{j<k} coeffs[i*k + j] * q^j, for i < count, with q = 2^b or
+ * q = p 2^b (prm->qform; b <= 32, and p 2^b < 2^40 for the second form).
  * coeffs: device uint8 [count][k] with entries in [0, p-1]; words: device array of count
  * words of type prm->word (double, uint64_t, float or uint32_t).  prm->k <= 64 and
- * (p-1) * sum_j q^j must fit the word (else FP_EBOUND). */
+ * (p-1) * sum_j q^j must fit the word (else FP_EBOUND); qform other than the two forms:
+ * FP_EINVAL. */
 fp_status fp_dqt_pack(fp_ctx ctx, const fp_dqt_params* prm, const uint8_t* coeffs, void* words,
                       size_t count, void* stream);
 
@@ -201,8 +239,11 @@ fp_status fp_dqt_pack(fp_ctx ctx, const fp_dqt_params* prm, const uint8_t* coeff
  * the top digit (j = ndig-1) takes all remaining high bits.  Each word must be a
  * non-negative integer < the word's exact range (2^52 for F64, 2^23 for F32) whose lower
  * ndig-1 base-q digits are < q -- which holds whenever it was produced under the planner's
- * bounds.  words: device [count] of prm->word; coeffs: device uint8 [count][ndig].
- * Errors: FP_EINVAL (ctx or arrays NULL; p, word, b or ndig out of range), FP_ECUDA. */
+ * bounds.  With qform = FP_Q_P_POW2 (q = p 2^b, the conclusion's alternative) the compression
+ * takes floor(r / p^(i+1)) by ndig successive FDIV divisions by p, floor(r / q^i) as
+ * floor(r / p^i) >> (b i), and needs no correction step (p | q, Theorem REDQ).
+ * words: device [count] of prm->word; coeffs: device uint8 [count][ndig].
+ * Errors: FP_EINVAL (ctx or arrays NULL; p, word, b, qform or ndig out of range), FP_ECUDA. */
 fp_status fp_dqt_unpack_redq(fp_ctx ctx, const fp_dqt_params* prm, const void* words,
                              uint8_t* coeffs, size_t count, void* stream);
 
@@ -363,6 +404,18 @@ enum { FP_GF_INDEX = 0, FP_GF_LOG = 1 };
 fp_status fp_gf_dot(fp_ctx ctx, fp_gf gf, const void* a, const void* b, size_t n, void* out,
                     int form, void* stream);
 
+/* Matrix product over GF(p^k) by Algorithm FGDP (Sec. 6) on every entry: C = A B in the field,
+ * C[r][c] = sum_l A[r][l] B[l][c].  A: device m x k elements (leading dimension lda >= k), B:
+ * k x n (ldb >= n), C: m x n (ldc >= n), all in `form` (index or discrete log, width per
+ * fp_gf_info), leading dimensions in elements.  Each element is converted once per use tile by
+ * the dot product's word table (q = 2^b_dot of fp_gf_dot_info), word products accumulate for
+ * `chunk` inner steps before each REDQ and L/H lookup, and the partial results are added in the
+ * field.  m, n, k in [1, 2^20].  Codes >= p^k set FP_EINVAL on the context (fp_ctx_status) and
+ * count as zero.  Errors: FP_EINVAL (null ctx, field or arrays; sizes or leading dimensions),
+ * FP_EUNSUPPORTED (the field's tables do not fit one block's shared memory), FP_ECUDA. */
+fp_status fp_gf_matmul(fp_ctx ctx, fp_gf gf, int m, int n, int k, const void* A, int lda, const void* B,
+                       int ldb, void* C, int ldc, int form, void* stream);
+
 /* The dot product's parameters (Algorithm FGDP, Sec. 6): index of the generator g of the log
  * form, exponent b_dot of its q, and the number of word products accumulated per REDQ.  Any
  * output may be NULL.  Errors: FP_EINVAL (gf NULL). */
@@ -393,7 +446,13 @@ typedef struct {
  * degree e and word chosen per (p, k) by the planner and the autotuner cache in the context.
  * `instances` is a HOST array; every instance is checked before anything is enqueued; the
  * plan is copied to context scratch through pinned staging (the call does not wait for earlier
- * work on the stream).  Errors: FP_EINVAL, FP_EBOUND, FP_ECUDA, FP_ENOMEM. */
+ * work on the stream).  Stream capture: a call captured into a CUDA graph writes its plan with
+ * kernels whose parameters carry it (so each replay runs the captured batch even after other
+ * calls), takes the packing degree from the tuning cache or the fixed rule, and refuses with
+ * FP_EUNSUPPORTED if it would have to grow context scratch -- make the same call once outside
+ * the capture first.  Scratch a captured graph used is not freed before fp_ctx_destroy; replays
+ * and other calls on the context must be ordered on one stream (they share that scratch).
+ * Errors: FP_EINVAL, FP_EBOUND, FP_ECUDA, FP_ENOMEM, FP_EUNSUPPORTED. */
 fp_status fp_batch_run(fp_ctx ctx, const fp_instance* instances, size_t count, void* stream);
 
 /* Diagnostic (no counterpart in the paper): launches one warp that waits on a device barrier

@@ -19,12 +19,15 @@ FP_OK, FP_EINVAL, FP_EBOUND, FP_ENOMEM, FP_ECUDA, FP_ETIMEOUT, FP_EUNSUPPORTED =
 STATUS_NAMES = ["FP_OK", "FP_EINVAL", "FP_EBOUND", "FP_ENOMEM", "FP_ECUDA", "FP_ETIMEOUT", "FP_EUNSUPPORTED"]
 # word types (fp_word)
 FP_WORD_F64, FP_WORD_U64, FP_WORD_F32, FP_WORD_U32 = range(4)
+# forms of q (fp_dqt_params.qform)
+FP_Q_POW2, FP_Q_P_POW2 = range(2)
 # polymul / dot algorithms
 FP_ALGO_AUTO, FP_ALGO_PLAIN, FP_ALGO_DQT_F64, FP_ALGO_DQT_U64, FP_ALGO_DQT_F32, FP_ALGO_DQT_U32, \
     FP_ALGO_KARATSUBA = range(7)
 # matmul algorithms
 (FP_MM_AUTO, FP_MM_RIGHT_F64, FP_MM_RIGHT_F32, FP_MM_PLAIN_F64, FP_MM_PLAIN_F32, FP_MM_PLAIN_I8,
- FP_MM_PLAIN_TC, FP_MM_RIGHT_TC, FP_MM_LEFT_F32, FP_MM_PLAIN_F8, FP_MM_LEFT_F64, FP_MM_CMM_F64) = range(12)
+ FP_MM_PLAIN_TC, FP_MM_RIGHT_TC, FP_MM_LEFT_F32, FP_MM_PLAIN_F8, FP_MM_LEFT_F64, FP_MM_CMM_F64,
+ FP_MM_FULL_F64, FP_MM_SPLIT_F64) = range(14)
 FP_GROUP_MAX = 16
 # GF(p^k) element forms for fp_gf_dot
 FP_GF_INDEX, FP_GF_LOG = range(2)
@@ -41,7 +44,7 @@ class FpError(RuntimeError):
 
 class fp_dqt_params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_uint32), ("k", ctypes.c_uint32), ("b", ctypes.c_uint32),
-                ("ndig", ctypes.c_uint32), ("word", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("ndig", ctypes.c_uint32), ("word", ctypes.c_uint32), ("qform", ctypes.c_uint32),
                 ("n_accum", ctypes.c_uint64)]
 
 
@@ -96,6 +99,8 @@ _SIGS = {
     "fp_dqt_choose": (_I, [_U32, _U32, _U64, _U32, ctypes.POINTER(fp_dqt_params)]),
     "fp_polymul_plan": (_I, [_U32, _U32, _U32, ctypes.c_int, ctypes.POINTER(fp_polymul_plan_t)]),
     "fp_mm_choose": (_I, [_U32, _U64, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
+    "fp_mm_full_choose": (_I, [_U32, _U64, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32),
+                               ctypes.POINTER(_U32)]),
     "fp_dqt_pack": (_I, [_V, ctypes.POINTER(fp_dqt_params), _V, _V, _SZ, _V]),
     "fp_dqt_unpack_redq": (_I, [_V, ctypes.POINTER(fp_dqt_params), _V, _V, _SZ, _V]),
     "fp_polymul_batched": (_I, [_V, _U32, _V, _U32, _V, _U32, _V, _SZ, _I, _V]),
@@ -108,6 +113,8 @@ _SIGS = {
     "fp_gf_info": (_I, [_V, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
     "fp_gf_mul_batched": (_I, [_V, _V, _V, _V, _V, _SZ, _V]),
     "fp_gf_dot": (_I, [_V, _V, _V, _V, _SZ, _V, ctypes.c_int, _V]),
+    "fp_gf_matmul": (_I, [_V, _V, ctypes.c_int, ctypes.c_int, ctypes.c_int, _V, ctypes.c_int, _V, ctypes.c_int, _V,
+                          ctypes.c_int, ctypes.c_int, _V]),
     "fp_gf_dot_info": (_I, [_V, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
     "fp_batch_run": (_I, [_V, ctypes.POINTER(fp_instance), _SZ, _V]),
     "fp_matmul_grouped": (_I, [_V, ctypes.POINTER(fp_mm_problem), _SZ, _I, _V]),
@@ -225,6 +232,13 @@ def fp_mm_choose(p: int, kdim: int, algo: int):
     return b.value, e.value, c.value
 
 
+def fp_mm_full_choose(p: int, kdim: int):
+    """(b, dq1, dt1, piece) of the full-compression product (Sec. 7.5)."""
+    b, q1, t1, pc = _U32(), _U32(), _U32(), _U32()
+    _check(lib().fp_mm_full_choose(p, kdim, ctypes.byref(b), ctypes.byref(q1), ctypes.byref(t1), ctypes.byref(pc)))
+    return b.value, q1.value, t1.value, pc.value
+
+
 # ------------------------------------------------------------------ compute
 
 def fp_dqt_pack(ctx, prm: fp_dqt_params, coeffs, words, count: int, stream=None):
@@ -293,6 +307,11 @@ def fp_gf_mul_batched(ctx, gf, a, b, c, count: int, stream=None):
 
 def fp_gf_dot(ctx, gf, a, b, n: int, out, form: int = FP_GF_INDEX, stream=None):
     _check(lib().fp_gf_dot(ctx, gf, _ptr(a), _ptr(b), n, _ptr(out), form, _stream(stream)))
+
+
+def fp_gf_matmul(ctx, gf, m: int, n: int, k: int, A, lda: int, B, ldb: int, C, ldc: int,
+                 form: int = FP_GF_INDEX, stream=None):
+    _check(lib().fp_gf_matmul(ctx, gf, m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, form, _stream(stream)))
 
 
 def fp_gf_dot_info(gf):

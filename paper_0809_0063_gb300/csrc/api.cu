@@ -97,13 +97,33 @@ RedqParams make_redq(uint32_t p, uint32_t b, uint32_t ndig) {
   return P;
 }
 
-fp_status ensure_scratch(fp_ctx ctx, size_t bytes, int which) {
+bool stream_capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();   // a query that failed leaves no sticky error behind
+    return false;
+  }
+  return cs == cudaStreamCaptureStatusActive;
+}
+
+fp_status ensure_scratch(fp_ctx ctx, size_t bytes, int which, cudaStream_t st) {
   void** ptr = which ? &ctx->scratch2 : &ctx->scratch;
   size_t* cap = which ? &ctx->scratch2_bytes : &ctx->scratch_bytes;
-  if (*cap >= bytes) return FP_OK;
+  const bool capturing = stream_capturing(st);
+  if (*cap >= bytes) {
+    if (capturing) ctx->captured = true;   // a graph now refers to this buffer
+    return FP_OK;
+  }
+  FP_CHECK(!capturing, FP_EUNSUPPORTED,
+           "this call needs %zu bytes of context scratch during a stream capture (%zu held): make the same "
+           "call once outside the capture first", bytes, *cap);
   if (*ptr) {
-    FP_CUDA(cudaDeviceSynchronize());
-    FP_CUDA(cudaFree(*ptr));
+    if (ctx->captured) {
+      ctx->retired.push_back(*ptr);          // a captured graph may still use it: freed with the context
+    } else {
+      FP_CUDA(cudaDeviceSynchronize());
+      FP_CUDA(cudaFree(*ptr));
+    }
     *ptr = nullptr;
     *cap = 0;
   }
@@ -118,8 +138,35 @@ fp_status ensure_scratch(fp_ctx ctx, size_t bytes, int which) {
   return FP_OK;
 }
 
+// Bytes written to device memory by kernels whose parameters carry them: the form of an upload
+// that a stream capture records by value (a captured copy from pinned host memory would read
+// the staging buffer again at every replay, after later calls had rewritten it).
+struct InlineChunk {
+  static constexpr uint32_t CAP = 16384;
+  uint32_t n;
+  uint8_t b[CAP];
+};
+
+__global__ void k_put_bytes(uint8_t* __restrict__ dst, const __grid_constant__ InlineChunk c) {
+  for (uint32_t i = threadIdx.x; i < c.n; i += blockDim.x) dst[i] = c.b[i];
+}
+
+static fp_status upload_inline(fp_ctx ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  static InlineChunk c;   // host-side parameter block, copied into each launch
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  for (size_t off = 0; off < bytes; off += InlineChunk::CAP) {
+    c.n = (uint32_t)std::min<size_t>(InlineChunk::CAP, bytes - off);
+    std::memcpy(c.b, (const uint8_t*)src + off, c.n);
+    FP_LAUNCH(ctx, "k_put_bytes", st, k_put_bytes<<<1, 256, 0, st>>>((uint8_t*)dst + off, c));
+    FP_CUDA(cudaGetLastError());
+  }
+  return FP_OK;
+}
+
 fp_status upload_staged(fp_ctx ctx, int slot, void* dst, const void* src, size_t bytes, cudaStream_t st) {
   if (bytes == 0) return FP_OK;
+  if (stream_capturing(st)) return upload_inline(ctx, dst, src, bytes, st);
   if (ctx->pin_ev[slot]) FP_CUDA(cudaEventSynchronize(ctx->pin_ev[slot]));
   else FP_CUDA(cudaEventCreateWithFlags(&ctx->pin_ev[slot], cudaEventDisableTiming));
   if (ctx->pin_bytes[slot] < bytes) {
@@ -265,6 +312,7 @@ extern "C" void fp_ctx_destroy(fp_ctx ctx) {
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->scratch2) cudaFree(ctx->scratch2);
+  for (void* x : ctx->retired) cudaFree(x);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   for (int i = 0; i < fp_ctx_s::PIN_SLOTS; ++i) {
@@ -316,7 +364,7 @@ extern "C" fp_status fp_dqt_choose(uint32_t p, uint32_t k, uint64_t n_accum, uin
   out->b = b;
   out->ndig = 2 * k - 1;
   out->word = word;
-  out->reserved = 0;
+  out->qform = FP_Q_POW2;
   out->n_accum = n_accum;
   return FP_OK;
 }
@@ -326,6 +374,13 @@ namespace fpd {
 fp_status mm_choose(uint32_t p, uint64_t kdim, uint32_t algo, uint32_t* b_out, uint32_t* e_out,
                     uint32_t* chunk_out) {
   uint64_t pp = (uint64_t)(p - 1) * (p - 1);
+  if (algo == FP_MM_SPLIT_F64) return split_choose(p, kdim, b_out, e_out, chunk_out);
+  if (algo == FP_MM_FULL_F64) {
+    uint32_t d1 = 0, t1 = 0;
+    const fp_status s = full_choose(p, kdim, b_out, &d1, &t1, chunk_out);
+    if (s == FP_OK) *e_out = d1 * t1;
+    return s;
+  }
   if (algo == FP_MM_RIGHT_F32 || algo == FP_MM_LEFT_F32) {
     // Per chunk: two residues at Qc = 2^12 in one binary32 accumulator; chunk digits
     // kc (p-1)^2 <= 4095 < Qc (Eq. lower, strict) so the word stays <= 4095 * 4097 < 2^24.
@@ -394,18 +449,28 @@ static fp_status check_params(const fp_dqt_params* prm, bool pack) {
   FP_CHECK(prm->p >= 2 && prm->p <= 251 && is_prime(prm->p), FP_EINVAL, "p=%u not a prime <= 251", prm->p);
   int beta = word_beta(prm->word);
   FP_CHECK(beta > 0, FP_EINVAL, "bad word type %u", prm->word);
-  FP_CHECK(prm->b >= 1 && prm->b <= 32, FP_EINVAL, "b=%u outside [1, 32]", prm->b);
-  FP_CHECK((1ull << prm->b) >= prm->p, FP_EINVAL, "q=2^%u below p=%u", prm->b, prm->p);
+  FP_CHECK(prm->qform == FP_Q_POW2 || prm->qform == FP_Q_P_POW2, FP_EINVAL, "bad qform %u", prm->qform);
+  if (prm->qform == FP_Q_POW2) {
+    FP_CHECK(prm->b >= 1 && prm->b <= 32, FP_EINVAL, "b=%u outside [1, 32]", prm->b);
+    FP_CHECK((1ull << prm->b) >= prm->p, FP_EINVAL, "q=2^%u below p=%u", prm->b, prm->p);
+  } else {
+    FP_CHECK(prm->b <= 32 && ((uint64_t)prm->p << prm->b) < (1ull << 40), FP_EINVAL,
+             "q=p 2^%u outside [p, 2^40)", prm->b);
+  }
   if (pack) {
     FP_CHECK(prm->k >= 1 && prm->k <= 64, FP_EINVAL, "k=%u outside [1, 64]", prm->k);
     // largest packed operand (p-1) sum_{j<k} q^j must be < 2^beta
-    unsigned __int128 tot = 0;
+    const unsigned __int128 lim = (unsigned __int128)1 << beta;
+    const unsigned __int128 q = prm->qform == FP_Q_POW2 ? ((unsigned __int128)1 << prm->b)
+                                                        : ((unsigned __int128)prm->p << prm->b);
+    unsigned __int128 tot = 0, qj = 1;
     for (uint32_t j = 0; j < prm->k; ++j) {
-      FP_CHECK((uint64_t)j * prm->b < 100, FP_EBOUND, "packed operand exceeds the word");
-      tot += ((unsigned __int128)(prm->p - 1)) << (j * prm->b);
+      FP_CHECK(qj < lim, FP_EBOUND, "packed operand exceeds the word");
+      tot += (unsigned __int128)(prm->p - 1) * qj;
+      qj *= q;
     }
-    FP_CHECK(tot < ((unsigned __int128)1 << beta), FP_EBOUND,
-             "packing k=%u residues at q=2^%u exceeds %d exact bits", prm->k, prm->b, beta);
+    FP_CHECK(tot < lim, FP_EBOUND, "packing k=%u residues at q=%s2^%u exceeds %d exact bits", prm->k,
+             prm->qform == FP_Q_POW2 ? "" : "p ", prm->b, beta);
   } else {
     FP_CHECK(prm->ndig >= 1 && prm->ndig <= 64, FP_EINVAL, "ndig=%u outside [1, 64]", prm->ndig);
   }
@@ -462,7 +527,7 @@ static fp_status check_matmul(uint32_t p, int m, int n, int k, const uint8_t* A,
            FP_EINVAL, "fp_matmul: sizes m=%d n=%d k=%d outside [1, 2^20]", m, n, k);
   FP_CHECK(lda >= k && ldb >= n && ldc >= n, FP_EINVAL, "fp_matmul: leading dimensions too small");
   FP_CHECK(A && B && C, FP_EINVAL, "fp_matmul: null array");
-  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_CMM_F64, FP_EINVAL, "bad algo %d", algo);
+  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_SPLIT_F64, FP_EINVAL, "bad algo %d", algo);
   return FP_OK;
 }
 
@@ -478,7 +543,7 @@ extern "C" fp_status fp_matmul_grouped(fp_ctx ctx, const fp_mm_problem* problems
                                        void* stream) {
   FP_CHECK(ctx != nullptr, FP_EINVAL, "fp_matmul_grouped: ctx is NULL");
   FP_CHECK(count == 0 || problems != nullptr, FP_EINVAL, "fp_matmul_grouped: problems is NULL");
-  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_CMM_F64, FP_EINVAL, "bad algo %d", algo);
+  FP_CHECK(algo >= FP_MM_AUTO && algo <= FP_MM_SPLIT_F64, FP_EINVAL, "bad algo %d", algo);
   for (size_t i = 0; i < count; ++i) {
     const fp_mm_problem& x = problems[i];
     fp_status s = check_matmul(x.p, x.m, x.n, x.k, x.A, x.lda, x.B, x.ldb, x.C, x.ldc, algo);

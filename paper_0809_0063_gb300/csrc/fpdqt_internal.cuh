@@ -71,6 +71,10 @@ struct fp_ctx_s {
   size_t scratch_bytes = 0;
   void* scratch2 = nullptr;
   size_t scratch2_bytes = 0;
+  // set once a call has run inside a stream capture: from then on scratch that grows is not
+  // freed (a captured graph may still refer to it) but kept here until the context is destroyed
+  bool captured = false;
+  std::vector<void*> retired;
   std::mutex mu;
   // autotuner cache: key -> chosen variant
   std::unordered_map<uint64_t, int> tune;
@@ -92,7 +96,11 @@ struct fp_ctx_s {
 };
 
 namespace fpd {
-fp_status ensure_scratch(fp_ctx ctx, size_t bytes, int which = 0);
+// Context scratch slot `which` grown to at least `bytes`.  Inside a stream capture on `st` a
+// growth is refused (FP_EUNSUPPORTED: it would free memory and synchronise); a call made once
+// outside the capture sizes it.
+fp_status ensure_scratch(fp_ctx ctx, size_t bytes, int which, cudaStream_t st);
+bool stream_capturing(cudaStream_t st);
 // Asynchronous host-to-device copy of `bytes` from `src` through the context's pinned staging
 // slot `slot` (0 .. PIN_SLOTS-1); `src` may be reused as soon as the call returns.
 fp_status upload_staged(fp_ctx ctx, int slot, void* dst, const void* src, size_t bytes, cudaStream_t st);
@@ -411,6 +419,14 @@ fp_status launch_pack_cb(fp_ctx ctx, uint32_t p, int k, int n, const uint8_t* B,
 fp_status launch_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v, size_t n,
                      uint32_t* out, int algo, cudaStream_t st);
 fp_status mm_bound_check(uint32_t p, int k, int algo);
+// full compression (Sec. 7.5) and right compression with a split inner dimension (Sec. 7.6) on
+// FP64 words (k_full.cu): planners and the products
+fp_status full_choose(uint32_t p, uint64_t k, uint32_t* b, uint32_t* dq1, uint32_t* dt1, uint32_t* piece);
+fp_status split_choose(uint32_t p, uint64_t k, uint32_t* b, uint32_t* e, uint32_t* piece);
+fp_status mm_full(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda, const uint8_t* B,
+                  int ldb, uint8_t* C, int ldc, cudaStream_t st);
+fp_status mm_split(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda, const uint8_t* B,
+                   int ldb, uint8_t* C, int ldc, cudaStream_t st);
 // grouped e4m3 tensor-core product (k_tcg.cu)
 bool f8_direct_ok(uint32_t p, int k, const uint8_t* A, int lda, const uint8_t* B, int ldb);
 fp_status launch_mm_f8_direct(fp_ctx ctx, const fp_mm_problem& x, cudaStream_t st);   // lock held

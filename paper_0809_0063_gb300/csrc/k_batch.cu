@@ -380,7 +380,7 @@ static fp_status plan_and_launch(fp_ctx ctx, const fp_instance* in, size_t count
   fp_status s = batch_prepare(ctx, in, count, st, measure_only, insts, items);
   if (s != FP_OK) return s;
   const size_t bytes = batch_plan_bytes(insts.size(), items.size());
-  s = ensure_scratch(ctx, bytes, 1);
+  s = ensure_scratch(ctx, bytes, 1, st);
   if (s != FP_OK) return s;
   std::vector<uint8_t> h(bytes);
   batch_plan_write(insts, items, h.data());
@@ -404,7 +404,9 @@ static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st) {
   const uint64_t key = (0xBA7Cull << 48) | ((uint64_t)p << 16) | kclass(k);
   auto it = ctx->tune.find(key);
   if (it != ctx->tune.end()) return it->second != 0;
-  if (!ctx->autotune) return k >= 448;   // fixed rule: packing pays once a chunk is full
+  // fixed rule (packing pays once a chunk is full) with tuning off, or inside a stream capture,
+  // where the probe's allocation and synchronisation are not allowed (not cached then)
+  if (!ctx->autotune || stream_capturing(st)) return k >= 448;
   const uint32_t kk = 1u << kclass(k), dim = 256, nin = 16;
   const size_t per = (size_t)dim * kk;          // one A (dim x kk) or one B (kk x dim)
   const size_t cper = (size_t)dim * dim;        // one C (dim x dim)
@@ -421,25 +423,28 @@ static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st) {
       v[i] = fp_instance{0, p, dim, dim, kk, 0, A + per * i, A + per * (nin + i), Cb + cper * i};
     }
     float best[2] = {1e30f, 1e30f};
-    for (int rep = 0; rep < 2; ++rep)
-      for (int pk = 0; pk < 2; ++pk) {
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep)
+      for (int pk = 0; pk < 2 && ok; ++pk) {
         for (auto& x : v) x.reserved = (uint32_t)pk;
-        cudaEventRecord(e0, st);
-        plan_and_launch(ctx, v.data(), v.size(), st, true);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
         float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
+        ok = cudaEventRecord(e0, st) == cudaSuccess &&
+             plan_and_launch(ctx, v.data(), v.size(), st, true) == FP_OK &&
+             cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+             cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
         best[pk] = std::min(best[pk], ms);
       }
     cudaStreamSynchronize(st);
     cudaFree(buf);
-    packed = best[1] < best[0];
+    if (ok) {
+      packed = best[1] < best[0];
+      ctx->tune[key] = packed ? 1 : 0;
+    }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  ctx->tune[key] = packed ? 1 : 0;
-  return packed;
+  cudaGetLastError();   // a failed probe leaves no sticky error for a later, unrelated check
+  return packed;        // not cached when the probe failed: the fixed rule stands
 }
 
 // ---------------------------------------------------------------- tensor-core share of a batch
@@ -559,7 +564,7 @@ static fp_status batch_run_tc(fp_ctx ctx, const std::vector<const fp_instance*>&
   const uint64_t off16 = (bytes + 1023) & ~(uint64_t)1023;
   const uint64_t total = t16.empty() ? bytes : off16 + t16_batch_bytes(ptr16.data(), ptr16.size());
   {
-    fp_status s = ensure_scratch(ctx, total + 1024, 0);
+    fp_status s = ensure_scratch(ctx, total + 1024, 0, st);
     if (s != FP_OK) return s;
   }
   if (!tc.empty()) {
@@ -626,7 +631,7 @@ extern "C" fp_status fp_batch_run(fp_ctx ctx, const fp_instance* instances, size
     if (s != FP_OK) return s;
   }
   const size_t bytes = batch_plan_bytes(insts.size(), items.size());
-  fp_status s = ensure_scratch(ctx, bytes, 1);
+  fp_status s = ensure_scratch(ctx, bytes, 1, st);
   if (s != FP_OK) return s;
   std::vector<uint8_t> h(bytes);
   batch_plan_write(insts, items, h.data());

@@ -318,7 +318,7 @@ fp_status launch_dot(fp_ctx ctx, uint32_t p, const uint8_t* u, const uint8_t* v,
                      int algo, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   int grid = ctx->num_sms * 4;
-  fp_status s = ensure_scratch(ctx, (size_t)grid * sizeof(uint64_t), 1);
+  fp_status s = ensure_scratch(ctx, (size_t)grid * sizeof(uint64_t), 1, st);
   if (s != FP_OK) return s;
   uint64_t* partial = (uint64_t*)ctx->scratch2;
   if (n == 0) {

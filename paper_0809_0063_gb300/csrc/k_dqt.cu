@@ -111,6 +111,67 @@ __global__ void __launch_bounds__(TILE) k_unpack(const W* __restrict__ words, ui
   }
 }
 
+// ------------------------------------------------------------------ q = p 2^t (the conclusion)
+//
+// DQT at q = p 2^t is a Horner evaluation with multiplies.  Its inverse needs no correction: p
+// divides q, so -q = 0 mod p and REDQ's residues are the compression values themselves.  The
+// compression u_i = floor(r / q^i) - p floor(s / q^i) with s = floor(r / p) uses
+// floor(r / q^i) = floor(r / p^i) >> (t i) (nested floors), so with r_i = floor(r / p^i),
+// obtained by successive divisions by p (FDIV for FP words, the invariant-divisor multiply for
+// integer words), u_i = (r_i >> t i) - p (r_{i+1} >> t i); u_i < p, so 32-bit wrapping suffices.
+
+template <typename W>
+__global__ void __launch_bounds__(TILE) k_pack_pq(const uint8_t* __restrict__ coeffs, W* __restrict__ words,
+                                                  uint64_t count, uint32_t k, uint64_t q, uint32_t p,
+                                                  uint32_t* err) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  const uint64_t ntiles = (count + TILE - 1) / TILE;
+  uint32_t bad = 0;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t i0 = t * TILE;
+    const uint32_t nit = (uint32_t)((count - i0) < (uint64_t)TILE ? (count - i0) : (uint64_t)TILE);
+    __syncthreads();
+    stage_in(sm, coeffs + i0 * k, nit * k);
+    __syncthreads();
+    if (threadIdx.x < nit) {
+      const uint8_t* c = sm + threadIdx.x * k;
+      uint64_t w = 0;
+      for (int j = (int)k - 1; j >= 0; --j) {
+        const uint32_t v = c[j];
+        bad |= v >= p;
+        w = w * q + v;
+      }
+      words[i0 + threadIdx.x] = WordOps<W>::from_u64(w);
+    }
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
+template <typename W>
+__global__ void __launch_bounds__(TILE) k_unpack_pq(const W* __restrict__ words, uint8_t* __restrict__ coeffs,
+                                                    uint64_t count, RedqParams P, uint32_t t) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  const uint32_t nd = P.ndig, p = P.p;
+  const uint64_t ntiles = (count + TILE - 1) / TILE;
+  for (uint64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+    const uint64_t i0 = tt * TILE;
+    const uint32_t nit = (uint32_t)((count - i0) < (uint64_t)TILE ? (count - i0) : (uint64_t)TILE);
+    const W w = threadIdx.x < nit ? words[i0 + threadIdx.x] : W(0);
+    __syncthreads();  // previous tile's stage_out done
+    uint8_t* out = sm + threadIdx.x * nd;
+    uint64_t ri = WordOps<W>::to_u64(w);
+    for (uint32_t i = 0; i < nd; ++i) {
+      const uint64_t rn = WordOps<W>::quot(WordOps<W>::from_u64(ri), P);   // floor(r / p^(i+1))
+      const uint32_t sh = t * i;
+      const uint32_t a = sh < 64 ? (uint32_t)(ri >> sh) : 0u, bq = sh < 64 ? (uint32_t)(rn >> sh) : 0u;
+      out[i] = (uint8_t)(a - p * bq);
+      ri = rn;
+    }
+    __syncthreads();
+    stage_out(coeffs + i0 * nd, sm, nit * nd);
+  }
+}
+
 // ------------------------------------------------------------------ polymul, one word each
 
 // C = A B for small degrees: pack A and B rows (shifts), one word product, REDQ_{ka+kb-1}.
@@ -893,6 +954,15 @@ static uint64_t unpack_small(fp_ctx ctx, const RedqParams& P, const uint32_t* wo
 template <typename W>
 static fp_status pack_t(fp_ctx ctx, const fp_dqt_params& prm, const uint8_t* coeffs, void* words,
                         size_t count, cudaStream_t st) {
+  if (prm.qform == FP_Q_P_POW2) {
+    const size_t smem_q = TILE * prm.k;
+    const int grid_q = grid_for(ctx, (count + TILE - 1) / TILE, 8);
+    FP_LAUNCH(ctx, "k_pack_pq", st,
+              k_pack_pq<W><<<grid_q, TILE, smem_q, st>>>(coeffs, (W*)words, count, prm.k, (uint64_t)prm.p << prm.b,
+                                                         prm.p, ctx->d_err));
+    FP_CUDA(cudaGetLastError());
+    return FP_OK;
+  }
   if (std::is_same<W, uint32_t>::value) {
     const uint64_t done = pack_small(ctx, prm, coeffs, (uint32_t*)words, count, st);
     FP_CUDA(cudaGetLastError());
@@ -922,6 +992,14 @@ template <typename W>
 static fp_status unpack_t(fp_ctx ctx, const fp_dqt_params& prm, const void* words, uint8_t* coeffs,
                           size_t count, cudaStream_t st) {
   RedqParams P = make_redq(prm.p, prm.b, prm.ndig);
+  if (prm.qform == FP_Q_P_POW2) {
+    const size_t smem = TILE * prm.ndig;
+    const int grid = grid_for(ctx, (count + TILE - 1) / TILE, 8);
+    FP_LAUNCH(ctx, "k_unpack_pq", st,
+              k_unpack_pq<W><<<grid, TILE, smem, st>>>((const W*)words, coeffs, count, P, prm.b));
+    FP_CUDA(cudaGetLastError());
+    return FP_OK;
+  }
   if (std::is_same<W, uint32_t>::value) {
     const uint64_t done = unpack_small(ctx, P, (const uint32_t*)words, coeffs, count, st);
     FP_CUDA(cudaGetLastError());

@@ -298,6 +298,103 @@ __global__ void __launch_bounds__(256) k_gf_dot_final(const uint32_t* __restrict
   }
 }
 
+// ------------------------------------------------------------------ matrix product
+//
+// C = A B over GF(p^k) by Algorithm FGDP applied to every entry (each C[r][c] is the dot product
+// of row r of A and column c of B; Sec. 6 gives the dot product and names the matrix product as
+// its use).  A block computes a 64 x 64 tile of C, each thread 4 x 4 entries.  Tiles of 32 inner
+// steps of A and B are staged in shared memory already converted to words (one table lookup per
+// element, shared by the 64 entries of C that use it); every entry accumulates word products in
+// a 64-bit word for nc steps (the dot product's chunk: every digit below 2^bd, the word below
+// 2^64), then takes REDQ, the two lookups and the field addition into its running sum.
+
+static constexpr int GFM_TILE = 64, GFM_KT = 32;
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_gf_matmul(const E* __restrict__ A, int lda, const E* __restrict__ B,
+                                                   int ldb, E* __restrict__ C, int ldc, int m, int n, int kdim,
+                                                   GfDotDev D, RedqParams P, const uint16_t* __restrict__ to_log,
+                                                   uint32_t* err) {
+  extern __shared__ __align__(128) uint8_t gsm[];
+  uint64_t* sw;
+  uint32_t *sL, *sH;
+  gf_load_tables(D.G, gsm, sw, sL, sH);
+  const uint32_t tsz = 1u << (D.G.cbits * D.G.k);
+  const size_t tab_bytes = ((D.G.order * sizeof(uint64_t) + 2 * tsz * sizeof(uint32_t)) + 127) & ~(size_t)127;
+  uint64_t* sA = reinterpret_cast<uint64_t*>(gsm + tab_bytes);   // [GFM_KT][GFM_TILE]
+  uint64_t* sB = sA + GFM_KT * GFM_TILE;                          // [GFM_KT][GFM_TILE]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int r0 = blockIdx.y * GFM_TILE, c0 = blockIdx.x * GFM_TILE;
+  uint64_t r[4][4];
+  uint32_t acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { r[i][j] = 0; acc[i][j] = 0; }
+  uint32_t bad = 0, cnt = 0;
+  const uint32_t order = D.G.order;
+  for (int l0 = 0; l0 < kdim; l0 += GFM_KT) {
+    __syncthreads();   // the previous tile is no longer read
+    for (int e = tid; e < GFM_KT * GFM_TILE; e += 256) {
+      {  // A: consecutive threads take consecutive inner steps of a row
+        const int l = e % GFM_KT, row = e / GFM_KT;
+        uint64_t w = 0;
+        if (r0 + row < m && l0 + l < kdim) {
+          const uint32_t x = A[(size_t)(r0 + row) * lda + l0 + l];
+          bad |= x >= order;
+          w = sw[x < order ? x : D.zero];
+        }
+        sA[l * GFM_TILE + row] = w;
+      }
+      {  // B: consecutive threads take consecutive columns
+        const int col = e % GFM_TILE, l = e / GFM_TILE;
+        uint64_t w = 0;
+        if (c0 + col < n && l0 + l < kdim) {
+          const uint32_t x = B[(size_t)(l0 + l) * ldb + c0 + col];
+          bad |= x >= order;
+          w = sw[x < order ? x : D.zero];
+        }
+        sB[l * GFM_TILE + col] = w;
+      }
+    }
+    __syncthreads();
+    const int steps = min(GFM_KT, kdim - l0);
+    for (int l = 0; l < steps; ++l) {
+      uint64_t a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sA[l * GFM_TILE + ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sB[l * GFM_TILE + tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) r[i][j] += a[i] * b[j];
+      if (++cnt == D.nc) {
+        cnt = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j] = gf_spread_add(acc[i][j], gf_redq_spread(r[i][j], D.G, sL, sH, P), P.p, D.G.fb, D.G.ones);
+            r[i][j] = 0;
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (cnt) acc[i][j] = gf_spread_add(acc[i][j], gf_redq_spread(r[i][j], D.G, sL, sH, P), P.p, D.G.fb, D.G.ones);
+      const int row = r0 + ty + 16 * i, col = c0 + tx + 16 * j;
+      if (row < m && col < n) {
+        const uint32_t idx = gf_spread_index(acc[i][j], P.p, D.G.k, D.G.fb);
+        C[(size_t)row * ldc + col] = (E)(to_log ? to_log[idx] : idx);
+      }
+    }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
 // ------------------------------------------------------------------ word-level fields
 //
 // GF(2^8), GF(3^5) and GF(7^4) take the steps of Algorithm FGDP (n = 1) with every constant
@@ -892,7 +989,7 @@ static fp_status gf_dot_launch(fp_ctx ctx, fp_gf g, const E* a, const E* b, size
   const uint64_t per_block = 256ull * (16 / sizeof(E));
   const uint64_t want = (n + per_block - 1) / per_block;
   const uint32_t grid = (uint32_t)std::min<uint64_t>(want, (uint64_t)ctx->num_sms * (uint64_t)std::max(per_sm, 1));
-  fp_status s = ensure_scratch(ctx, (size_t)std::max<uint32_t>(grid, 1) * sizeof(uint32_t), 1);
+  fp_status s = ensure_scratch(ctx, (size_t)std::max<uint32_t>(grid, 1) * sizeof(uint32_t), 1, st);
   if (s != FP_OK) return s;
   uint32_t* partial = (uint32_t*)ctx->scratch2;
   if (grid)
@@ -915,6 +1012,43 @@ extern "C" fp_status fp_gf_dot(fp_ctx ctx, fp_gf g, const void* a, const void* b
   if (g->elem_bytes == 1)
     return gf_dot_launch<uint8_t>(ctx, g, (const uint8_t*)a, (const uint8_t*)b, n, (uint8_t*)out, form, st);
   return gf_dot_launch<uint16_t>(ctx, g, (const uint16_t*)a, (const uint16_t*)b, n, (uint16_t*)out, form, st);
+}
+
+template <typename E>
+static fp_status gf_matmul_launch(fp_ctx ctx, fp_gf g, int m, int n, int kdim, const E* A, int lda, const E* B,
+                                  int ldb, E* C, int ldc, int form, cudaStream_t st) {
+  using namespace fpd;
+  const uint32_t tsz = 1u << (g->c * g->k);
+  const size_t tab = ((g->order * sizeof(uint64_t) + 2 * tsz * sizeof(uint32_t)) + 127) & ~(size_t)127;
+  const size_t smem = tab + 2 * (size_t)GFM_KT * GFM_TILE * sizeof(uint64_t);
+  GfDotDev D{GfDev{form == FP_GF_LOG ? g->d_word_dl : g->d_word_d, g->d_Ld, g->d_Hd, g->order, g->k, g->c, g->fb, 0},
+             g->nc, form == FP_GF_LOG ? g->order - 1 : 0u};
+  for (uint32_t i = 0; i < g->k; ++i) D.G.ones |= 1u << (i * g->fb);
+  FP_CHECK(smem <= 227 * 1024, FP_EUNSUPPORTED, "fp_gf_matmul: field tables too large for shared memory");
+  FP_CUDA(cudaFuncSetAttribute(k_gf_matmul<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((n + GFM_TILE - 1) / GFM_TILE, (m + GFM_TILE - 1) / GFM_TILE);
+  FP_LAUNCH(ctx, "k_gf_matmul", st,
+            (k_gf_matmul<E><<<grid, 256, smem, st>>>(A, lda, B, ldb, C, ldc, m, n, kdim, D, g->Pd,
+                                                     form == FP_GF_LOG ? g->d_tolog : nullptr, ctx->d_err)));
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
+extern "C" fp_status fp_gf_matmul(fp_ctx ctx, fp_gf g, int m, int n, int k, const void* A, int lda, const void* B,
+                                  int ldb, void* C, int ldc, int form, void* stream) {
+  FP_CHECK(ctx && g, FP_EINVAL, "fp_gf_matmul: null ctx or field");
+  FP_CHECK(form == FP_GF_INDEX || form == FP_GF_LOG, FP_EINVAL, "fp_gf_matmul: bad form %d", form);
+  FP_CHECK(m >= 1 && n >= 1 && k >= 1 && m <= (1 << 20) && n <= (1 << 20) && k <= (1 << 20), FP_EINVAL,
+           "fp_gf_matmul: m, n, k must lie in [1, 2^20]");
+  FP_CHECK(lda >= k && ldb >= n && ldc >= n, FP_EINVAL, "fp_gf_matmul: leading dimension too small");
+  FP_CHECK(A && B && C, FP_EINVAL, "fp_gf_matmul: null array");
+  cudaStream_t st = fpd::as_stream(stream);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (g->elem_bytes == 1)
+    return gf_matmul_launch<uint8_t>(ctx, g, m, n, k, (const uint8_t*)A, lda, (const uint8_t*)B, ldb, (uint8_t*)C,
+                                     ldc, form, st);
+  return gf_matmul_launch<uint16_t>(ctx, g, m, n, k, (const uint16_t*)A, lda, (const uint16_t*)B, ldb,
+                                    (uint16_t*)C, ldc, form, st);
 }
 
 extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const void* b, void* c, size_t count,

@@ -541,7 +541,7 @@ static fp_status mm_dmma(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
   fp_status s = mm_choose(p, (uint64_t)k, plain ? FP_MM_PLAIN_F64 : FP_MM_RIGHT_F64, &b, &e, &chunk);
   if (s != FP_OK) return s;
   int nw = (n + (int)e - 1) / (int)e;
-  s = ensure_scratch(ctx, (size_t)k * nw * sizeof(double));
+  s = ensure_scratch(ctx, (size_t)k * nw * sizeof(double), 0, st);
   if (s != FP_OK) return s;
   double* CB = (double*)ctx->scratch;
   s = pack_cb_t<double>(ctx, p, k, n, B, ldb, b, e, CB, nw, st);
@@ -577,7 +577,7 @@ static fp_status mm_ffma(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
   }
   int nw = (n + (int)E - 1) / (int)E;
   int ldcb = (nw + 3) & ~3;
-  fp_status s = ensure_scratch(ctx, (size_t)k * ldcb * sizeof(float));
+  fp_status s = ensure_scratch(ctx, (size_t)k * ldcb * sizeof(float), 0, st);
   if (s != FP_OK) return s;
   float* CB = (float*)ctx->scratch;
   s = pack_cb_t<float>(ctx, p, k, n, B, ldb, 12, E, CB, ldcb, st);
@@ -602,7 +602,7 @@ static fp_status mm_imma(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
   FP_CHECK((uint64_t)k * pp < (1ull << 31), FP_EBOUND, "PLAIN_I8 needs k (p-1)^2 < 2^31");
   int kp = (k + IM_BK - 1) / IM_BK * IM_BK;
   size_t abytes = (size_t)m * kp, bbytes = (size_t)n * kp;
-  fp_status s = ensure_scratch(ctx, abytes + bbytes);
+  fp_status s = ensure_scratch(ctx, abytes + bbytes, 0, st);
   if (s != FP_OK) return s;
   uint8_t* A2 = (uint8_t*)ctx->scratch;
   uint8_t* Bt = A2 + abytes;
@@ -636,7 +636,7 @@ static fp_status mm_cmm(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8
   if (s != FP_OK) return s;
   const int kw = (k + (int)d1 - 1) / (int)d1;
   const size_t ca = (((size_t)m * kw * sizeof(double)) + 255) & ~(size_t)255;
-  s = ensure_scratch(ctx, ca + (size_t)kw * n * sizeof(double));
+  s = ensure_scratch(ctx, ca + (size_t)kw * n * sizeof(double), 0, st);
   if (s != FP_OK) return s;
   double* CA = (double*)ctx->scratch;
   double* CB = (double*)((uint8_t*)ctx->scratch + ca);
@@ -672,7 +672,7 @@ static fp_status mm_left(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
   if (s != FP_OK) return s;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t at = al((size_t)k * m), bt = al((size_t)n * k), ct = al((size_t)n * m);
-  s = ensure_scratch(ctx, at + bt + ct, 1);
+  s = ensure_scratch(ctx, at + bt + ct, 1, st);
   if (s != FP_OK) return s;
   uint8_t* At = (uint8_t*)ctx->scratch2;
   uint8_t* Bt = At + at;
@@ -694,6 +694,8 @@ static fp_status mm_left(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint
 static fp_status run_algo(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_t* A, int lda,
                           const uint8_t* B, int ldb, uint8_t* C, int ldc, int algo, cudaStream_t st) {
   switch (algo) {
+    case FP_MM_FULL_F64: return mm_full(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, st);
+    case FP_MM_SPLIT_F64: return mm_split(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, st);
     case FP_MM_CMM_F64: return mm_cmm(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, st);
     case FP_MM_LEFT_F64: return mm_left(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, true, st);
     case FP_MM_LEFT_F32: return mm_left(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, false, st);
@@ -724,6 +726,11 @@ fp_status mm_bound_check(uint32_t p, int k, int algo) {
     case FP_MM_RIGHT_F32: return mm_choose(p, (uint64_t)k, (uint32_t)algo, &b, &e, &c);
     case FP_MM_LEFT_F64: return mm_choose(p, (uint64_t)k, FP_MM_RIGHT_F64, &b, &e, &c);
     case FP_MM_CMM_F64: return cmm_choose(p, (uint64_t)k, &b, &e);
+    case FP_MM_FULL_F64: {
+      uint32_t d1, piece;
+      return full_choose(p, (uint64_t)k, &b, &d1, &e, &piece);
+    }
+    case FP_MM_SPLIT_F64: return split_choose(p, (uint64_t)k, &b, &e, &c);
     case FP_MM_LEFT_F32: return mm_choose(p, (uint64_t)k, FP_MM_RIGHT_F32, &b, &e, &c);
     case FP_MM_PLAIN_I8:
       FP_CHECK((uint64_t)k * pp < (1ull << 31), FP_EBOUND, "PLAIN_I8 needs k (p-1)^2 < 2^31");
@@ -770,10 +777,12 @@ fp_status launch_matmul(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8
     return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, FP_MM_PLAIN_F8, st);
   int cand[8];
   const int nc = candidates(p, m, n, k, cand);
-  if (!ctx->autotune || nc == 1) return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, cand[0], st);
   const uint64_t key = tune_key(p, m, n, k);
   auto it = ctx->tune.find(key);
   if (it != ctx->tune.end()) return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, it->second, st);
+  // no timing with tuning off or inside a stream capture (it synchronises): the fixed rule
+  if (!ctx->autotune || nc == 1 || stream_capturing(st))
+    return run_algo(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, cand[0], st);
   // autotune: time each exact candidate once (all write the same C), keep the fastest;
   // FP64 words are only timed when nothing faster is valid
   cudaEvent_t e0, e1;

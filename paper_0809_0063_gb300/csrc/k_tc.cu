@@ -50,7 +50,7 @@ fp_status launch_mm_tc(fp_ctx ctx, uint32_t p, int m, int n, int k, const uint8_
     // pad copies (no arithmetic): rows of A and B at leading dimensions rounded up to 16
     const size_t lda2 = ((size_t)k + 15) / 16 * 16, ldb2 = ((size_t)n + 15) / 16 * 16;
     const size_t abytes = ((size_t)m * lda2 + 1023) & ~(size_t)1023, bbytes = (size_t)k * ldb2;
-    s = ensure_scratch(ctx, abytes + bbytes + 1024);
+    s = ensure_scratch(ctx, abytes + bbytes + 1024, 0, st);
     if (s != FP_OK) return s;
     uint8_t* A2 = (uint8_t*)ctx->scratch;
     uint8_t* B2 = A2 + abytes;

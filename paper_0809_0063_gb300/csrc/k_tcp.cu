@@ -529,7 +529,7 @@ static fp_status launch_t16_locked(fp_ctx ctx, const fp_mm_problem* const* pr, s
       off[i][1] = total;
       total += (x.k * ldw * 2 + 1023) & ~(size_t)1023;
     }
-    fp_status s = ensure_scratch(ctx, total + 1024);
+    fp_status s = ensure_scratch(ctx, total + 1024, 0, st);
     if (s != FP_OK) return s;
     PParams hp;
     std::memset(&hp, 0, sizeof hp);

@@ -143,6 +143,42 @@ def test_mm_choose_matches_eq_lower_upper(fp):
         fp.fp_mm_choose(31, 4096, fp.FP_MM_RIGHT_F32)
 
 
+def test_full_and_split_planners_match_the_bounds(fp):
+    """Full compression (Sec. 7.5): Q = 2^b strict for the piece (Eq. lower), Theta = Q^dq1
+    (Eq. qtheta), Eq. dq at the paper's beta = 53 and the exact FP64 range (largest packed product
+    below 2^52), and no larger balanced packing fits.  Splitting (Sec. 7.6): every piece of the
+    oracle's split plan at the planner's piece length keeps at least the planner's compression."""
+    from oracle import bounds, dqt
+    for p in (2, 3, 5, 7, 13, 23):
+        for kdim in (1, 16, 100, 255, 1000, 2047, 2048, 4096, 100000):
+            b, dq1, dt1, piece = fp.fp_mm_full_choose(p, kdim)
+            Q = 1 << b
+            assert piece <= kdim and (piece == kdim or piece % 4 == 0)
+            assert Q == bounds.cmm_Q(piece, p) or (piece * (p - 1) ** 2 < Q <= 2 * max(1, piece * (p - 1) ** 2))
+            assert dq1 >= 2 and dt1 >= dq1
+            assert bounds.full_compression_ok(Q, Q ** dq1, dq1 - 1, dt1 - 1, 53)
+            D = piece * (p - 1) ** 2
+            assert D * sum(Q ** t for t in range(dq1 * dt1)) < 2 ** 52
+            if piece == kdim:   # one piece: no larger two-sided packing (both sides >= 2) fits
+                for prod in range(dq1 * dt1 + 1, 17):
+                    if any(prod % q == 0 and prod // q >= 2 for q in range(2, prod)):
+                        assert D * sum(Q ** t for t in range(prod)) >= 2 ** 52
+            if kdim > piece:
+                npieces = -(-kdim // piece)
+                assert -(-kdim // npieces) <= piece      # balanced
+            b2, e2, c2 = fp.fp_mm_choose(p, kdim, fp.FP_MM_FULL_F64)
+            assert (b2, e2, c2) == (b, dq1 * dt1, piece)
+        for kdim in (16, 300, 2047, 2048, 4096, 30000):
+            b, e, piece = fp.fp_mm_choose(p, kdim, fp.FP_MM_SPLIT_F64)
+            for l0, kc, Q, e_piece in dqt.split_plan(kdim, piece, p, 52):
+                assert e_piece >= e and Q <= (1 << b)
+            # never below the unsplit right compression
+            assert e >= fp.fp_mm_choose(p, kdim, fp.FP_MM_RIGHT_F64)[1]
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_mm_full_choose(29, 16)
+    assert ei.value.status == fp.FP_EBOUND
+
+
 def test_bad_arguments_are_rejected_on_host(fp):
     with pytest.raises(fp.FpError) as ei:
         fp.fp_dqt_choose(4, 3, 1, fp.FP_WORD_F64)       # not prime

@@ -38,7 +38,7 @@ def test_pack_matches_oracle(env, word, p, k):
     b = max(1, (p - 1).bit_length())
     while (p - 1) * sum(1 << (j * b) for j in range(k)) >= 2 ** beta:
         k -= 1
-    prm = fp.fp_dqt_params(p=p, k=k, b=b, ndig=1, word=word, reserved=0, n_accum=1)
+    prm = fp.fp_dqt_params(p=p, k=k, b=b, ndig=1, word=word, qform=0, n_accum=1)
     count = 3 * 256 + 17                              # several tiles and a ragged tail
     c = workloads.uniform_mod(k * 100 + p, p, (count, k))
     words = torch.empty(count, dtype=getattr(torch, np.dtype(dt).name), device=dev)
@@ -68,12 +68,85 @@ def test_unpack_redq_matches_radix_conversion(env, word, p):
         r[1] = min(2 ** beta - 1, r[1])
         words = torch.tensor(np.array(r, dtype=np.uint64).astype(dt), device=dev)
         out = torch.empty((count, ndig), dtype=torch.uint8, device=dev)
-        prm = fp.fp_dqt_params(p=p, k=1, b=b, ndig=ndig, word=word, reserved=0, n_accum=1)
+        prm = fp.fp_dqt_params(p=p, k=1, b=b, ndig=ndig, word=word, qform=0, n_accum=1)
         fp.fp_dqt_unpack_redq(ctx, prm, words, out, count)
         fp.fp_ctx_status(ctx)
         got = out.cpu().numpy()
         for i in range(count):
             assert list(got[i]) == odqt.dqt_inverse(r[i], 1 << b, ndig, p), (p, b, ndig, r[i])
+
+
+@pytest.mark.parametrize("word", [0, 1, 2, 3])
+@pytest.mark.parametrize("p,t", [(3, 3), (2, 4), (5, 2), (7, 5), (3, 0), (13, 1), (251, 2)])
+def test_q_p_times_pow2_pack_unpack(env, word, p, t):
+    """q = p 2^t (the conclusion's alternative, FP_Q_P_POW2): packing equals the oracle's DQT at
+    that q; unpacking (no correction step, divisions by p only) equals the oracle's radix
+    conversion and its REDQ for words whose lower digits are below q and whose top digit is free."""
+    fp, torch, dev, ctx = env
+    dt, beta = WORDS[word]
+    q = p << t
+    k = 6
+    while k > 1 and (p - 1) * sum(q ** j for j in range(k)) >= 2 ** beta:
+        k -= 1
+    if (p - 1) * sum(q ** j for j in range(k)) >= 2 ** beta:
+        pytest.skip("q too large for this word")
+    tdt = getattr(torch, np.dtype(dt).name)
+    prm = fp.fp_dqt_params(p=p, k=k, b=t, ndig=1, word=word, qform=fp.FP_Q_P_POW2, n_accum=1)
+    count = 2 * 256 + 9
+    c = workloads.uniform_mod(k * 1000 + p + t, p, (count, k))
+    c[0, :] = p - 1
+    words = torch.empty(count, dtype=tdt, device=dev)
+    fp.fp_dqt_pack(ctx, prm, to_dev(torch, dev, c), words, count)
+    fp.fp_ctx_status(ctx)
+    assert [int(x) for x in words.cpu().numpy()] == [int(x) for x in odqt.dqt(c, q)]
+    g = np.random.default_rng(p * 31 + t + word)
+    ndig = 1
+    while ndig < 8 and q ** ndig < 2 ** beta:
+        ndig += 1
+    lo = g.integers(0, q, size=(count, ndig - 1)) if ndig > 1 else np.zeros((count, 0), np.int64)
+    top_max = (2 ** beta - 1) // q ** (ndig - 1)
+    top = g.integers(0, min(top_max, 2 ** 62) + 1, size=count)
+    r = [int(odqt.dqt(list(lo[i]) + [int(top[i])], q)) for i in range(count)]
+    r = [min(x, 2 ** beta - 1) for x in r]
+    r[0] = 0
+    words = torch.tensor(np.array(r, dtype=np.uint64).astype(dt), device=dev)
+    out = torch.empty((count, ndig), dtype=torch.uint8, device=dev)
+    prm = fp.fp_dqt_params(p=p, k=1, b=t, ndig=ndig, word=word, qform=fp.FP_Q_P_POW2, n_accum=1)
+    fp.fp_dqt_unpack_redq(ctx, prm, words, out, count)
+    fp.fp_ctx_status(ctx)
+    got = out.cpu().numpy()
+    for i in range(count):
+        want = odqt.dqt_inverse(r[i], q, ndig, p)
+        assert list(got[i]) == want == list(odqt.redq(r[i], p, q, ndig - 1)), (p, t, ndig, r[i])
+
+
+def test_q_24_degree_2_products_over_f3(env):
+    """The degree-2 products over F_3 at q = 24 = 3 2^3 (the smallest q = p 2^t above the digit
+    bound 12): operands packed on the device, word products formed exactly (Python integers),
+    REDQ_5 on the device; equals the schoolbook product mod 3."""
+    fp, torch, dev, ctx = env
+    count = 4099
+    a, b = workloads.polymul_inputs(24, 3, count, 2, 2)
+    prm = fp.fp_dqt_params(p=3, k=3, b=3, ndig=1, word=0, qform=fp.FP_Q_P_POW2, n_accum=1)
+    wa = torch.empty(count, dtype=torch.float64, device=dev)
+    wb = torch.empty(count, dtype=torch.float64, device=dev)
+    fp.fp_dqt_pack(ctx, prm, to_dev(torch, dev, a), wa, count)
+    fp.fp_dqt_pack(ctx, prm, to_dev(torch, dev, b), wb, count)
+    prod = (wa * wb).contiguous()              # exact: below 24^5 < 2^23
+    out = torch.empty((count, 5), dtype=torch.uint8, device=dev)
+    prm5 = fp.fp_dqt_params(p=3, k=1, b=3, ndig=5, word=0, qform=fp.FP_Q_P_POW2, n_accum=1)
+    fp.fp_dqt_unpack_redq(ctx, prm5, prod, out, count)
+    fp.fp_ctx_status(ctx)
+    np.testing.assert_array_equal(out.cpu().numpy(), field.polymul_mod(a, b, 3))
+
+
+def test_qform_rejected(env):
+    fp, torch, dev, ctx = env
+    w = torch.zeros(4, dtype=torch.float64, device=dev)
+    c = torch.zeros((4, 2), dtype=torch.uint8, device=dev)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_dqt_pack(ctx, fp.fp_dqt_params(p=3, k=2, b=3, ndig=1, word=0, qform=2, n_accum=1), c, w, 4)
+    assert ei.value.status == fp.FP_EINVAL
 
 
 ALGOS = ["AUTO", "PLAIN", "DQT_F64", "DQT_U64", "DQT_F32", "DQT_U32"]
@@ -248,7 +321,7 @@ def test_pack_u32_word_granular(env, p, k):
     fp, torch, dev, ctx = env
     b = max(1, (p - 1).bit_length())
     count = 2 * 4096 + 123
-    prm = fp.fp_dqt_params(p=p, k=k, b=b, ndig=1, word=3, reserved=0, n_accum=1)
+    prm = fp.fp_dqt_params(p=p, k=k, b=b, ndig=1, word=3, qform=0, n_accum=1)
     c = workloads.uniform_mod(k * 1000 + p, p, (count, k))
     c[0] = p - 1
     words = torch.empty(count, dtype=torch.int32, device=dev)
@@ -278,7 +351,7 @@ def test_unpack_u32_word_granular(env, p, ndig):
     r = [int(odqt.dqt(list(lo[i]) + [int(top[i])], 1 << b)) for i in range(count)]
     words = torch.tensor(np.array(r, dtype=np.uint64).astype(np.uint32).view(np.int32), device=dev)
     out = torch.empty((count, ndig), dtype=torch.uint8, device=dev)
-    prm = fp.fp_dqt_params(p=p, k=1, b=b, ndig=ndig, word=3, reserved=0, n_accum=1)
+    prm = fp.fp_dqt_params(p=p, k=1, b=b, ndig=ndig, word=3, qform=0, n_accum=1)
     fp.fp_dqt_unpack_redq(ctx, prm, words, out, count)
     fp.fp_ctx_status(ctx)
     got = out.cpu().numpy()
