@@ -121,14 +121,80 @@ def test_batch_equals_alone_config_sample(env):
     fp.fp_ctx_status(ctx)
     for x, r, C2 in zip(insts, batch_res, alone):
         assert np.array_equal(r, result(x, C2))
+    # every instance against the oracle: one sampled row of each product (a different row per
+    # instance, across every tile row), every dot product whole; three rows of 24 of them
     g = np.random.default_rng(0)
+    for i, x in enumerate(insts):
+        if x.kind == "matmul":
+            rows = np.array([int(g.integers(0, x.m))])
+            assert np.array_equal(batch_res[i][rows], field.matmul_mod_rows(x.a, x.b, x.p, rows)), i
+        else:
+            assert batch_res[i] == field.dot_mod(x.a, x.b, x.p), i
     for i in g.choice(len(insts), 24, replace=False):
         x = insts[i]
         if x.kind == "matmul":
             rows = np.unique(np.array([0, x.m - 1, x.m // 2]))
             assert np.array_equal(batch_res[i][rows], field.matmul_mod_rows(x.a, x.b, x.p, rows))
+
+
+def test_batch_captured_in_a_cuda_graph(env):
+    """A warm batch captured into a CUDA graph replays its own instances after eager batches of
+    other instances (other sizes, so the context's scratch grows) ran on the same context: the
+    captured plan and operand copies live in the graph and in scratch that is kept for it."""
+    fp, torch, dev, ctx = env
+    insts = workloads.uneven_batch(21, count=300, lo=16, hi=700)
+    assert any(x.kind == "matmul" and min(x.m, x.n) >= 64 and x.m * x.n * x.k >= 2 ** 21 for x in insts)
+    bufs, arr = make_instances(fp, torch, dev, insts)
+    fp.fp_batch_run(ctx, arr)                      # warm: scratch sized, packing degrees tuned
+    fp.fp_ctx_status(ctx)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        fp.fp_batch_run(ctx, arr)
+    for A, B, C in bufs:
+        C.fill_(255)
+    other = workloads.uneven_batch(22, count=200, lo=200, hi=2048)
+    bufs2, arr2 = make_instances(fp, torch, dev, other)
+    fp.fp_batch_run(ctx, arr2)                     # eager, larger: scratch grows, plans differ
+    fp.fp_ctx_status(ctx)
+    for rep in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        fp.fp_ctx_status(ctx)
+        for x, (A, B, C) in zip(insts, bufs):
+            assert np.array_equal(result(x, C), oracle(x)), (rep, x.kind, x.p, x.m, x.n, x.k)
+        for A, B, C in bufs:
+            C.fill_(255)
+    for i in range(0, len(other), 9):
+        x, (A, B, C) = other[i], bufs2[i]
+        if x.kind == "matmul":
+            rows = np.array([0, x.m - 1])
+            assert np.array_equal(result(x, C)[rows], field.matmul_mod_rows(x.a, x.b, x.p, rows))
         else:
-            assert batch_res[i] == field.dot_mod(x.a, x.b, x.p)
+            assert result(x, C) == field.dot_mod(x.a, x.b, x.p)
+    del graph
+
+
+def test_batch_capture_refuses_scratch_growth(env):
+    """Inside a capture a batch that would need more scratch than the context holds is refused
+    (FP_EUNSUPPORTED) instead of freeing and allocating memory."""
+    fp, torch, dev, ctx = env
+    fresh = fp.fp_ctx_create(0)
+    try:
+        insts = workloads.uneven_batch(23, count=40, lo=16, hi=300)
+        bufs, arr = make_instances(fp, torch, dev, insts)
+        graph = torch.cuda.CUDAGraph()
+        with pytest.raises(fp.FpError) as ei:
+            with torch.cuda.graph(graph):
+                fp.fp_batch_run(fresh, arr)
+        assert ei.value.status == fp.FP_EUNSUPPORTED
+        del graph
+        torch.cuda.synchronize()
+        fp.fp_batch_run(fresh, arr)               # the same call outside a capture works
+        fp.fp_ctx_status(fresh)
+        for x, (A, B, C) in zip(insts, bufs):
+            assert np.array_equal(result(x, C), oracle(x))
+    finally:
+        fp.fp_ctx_destroy(fresh)
 
 
 def test_batch_rejects_bad_instances(env):

@@ -92,6 +92,48 @@ def test_serving_mix_equals_alone_and_oracle(env, streams, window):
         assert np.array_equal(alone(fp, torch, dev, ctx, gfs, r, code, sz, A, B, out), out), (r.kind, sz)
 
 
+def test_serving_full_size_matmuls(env):
+    """The serving configuration's matmul sizes uncapped (n log-uniform 64..1024, plus requests
+    of n = 1024 and 777 placed in the stream): every result equals the oracle -- the large
+    products on sampled rows, everything else whole -- and a sample equals the request alone."""
+    fp, torch, dev, ctx, gfs = env
+    moduli = {pk: field.smallest_monic_irreducible(*pk) for pk in workloads.GF_FIELDS}
+    reqs = workloads.serving_stream(41, rate=20000.0, duration=0.02)
+    for i, (t, n) in enumerate(((0.001, 1024), (0.005, 777), (0.011, 1024), (0.015, 513))):
+        reqs.append(workloads.Request(t, "matmul", (3, 5, 7)[i % 3], n, seed=990000 + i))
+    reqs.sort(key=lambda r: r.t_arrival)
+    big = [r for r in reqs if r.kind == "matmul" and r.size > 160]
+    assert len(big) >= 4
+    srv = fp.fp_server_create(ctx, arena_bytes=256 << 20, streams=4, max_batch=128, window_us=100)
+    keep, tickets = [], []
+    t0 = time.perf_counter()
+    for r in reqs:
+        code, sz, A, B, out = workloads.request_arrays(r)
+        while time.perf_counter() - t0 < r.t_arrival:
+            pass
+        q = fp.fp_request(kind=code, p=r.p, a=sz[0], b=sz[1], c=sz[2], reserved=0,
+                          gf=gfs[(r.p, r.gf_k)].value if code == 2 else None,
+                          host_a=A.ctypes.data, host_b=B.ctypes.data, host_out=out.ctypes.data)
+        tickets.append(fp.fp_server_submit(srv, q))
+        keep.append((r, code, sz, A, B, out))
+    fp.fp_server_drain(srv, 120.0)
+    st = fp.fp_server_stats_get(srv)
+    fp.fp_server_destroy(srv)
+    fp.fp_ctx_status(ctx)
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    for (r, code, sz, A, B, out) in keep:
+        if code == 3 and sz[0] > 160:
+            n = sz[0]
+            rows = np.unique(np.array([0, 1, n // 3, n // 2, n - 2, n - 1]))
+            assert np.array_equal(out[rows], field.matmul_mod_rows(A, B, r.p, rows)), (r.p, n)
+            continue
+        want = oracle(r, code, A, B, moduli)
+        got = out if code != 1 else out.astype(np.int64)
+        assert np.array_equal(got.astype(np.int64), np.asarray(want).astype(np.int64)), (r.kind, r.p, sz)
+    for (r, code, sz, A, B, out) in [k for k in keep if k[1] == 3] + keep[::11]:
+        assert np.array_equal(alone(fp, torch, dev, ctx, gfs, r, code, sz, A, B, out), out), (r.kind, sz)
+
+
 def test_server_rejects_bad_requests(env):
     fp, torch, dev, ctx, gfs = env
     srv = fp.fp_server_create(ctx, arena_bytes=64 << 20, streams=2)

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import workloads
+from oracle import field
 from tests._gpu import to_dev, torch_dev
 
 pytestmark = pytest.mark.gpu
@@ -40,6 +41,28 @@ def test_noalloc_matches_fp_dot_twice(env, algo, p, n):
         fp.fp_dot_noalloc(p, U, V, n, got, a)
         torch.cuda.synchronize()
         assert int(got.item()) == int(ref.item())
+        assert int(got.item()) == field.dot_mod(u, v, p)
+
+
+@pytest.mark.parametrize("algo", ["AUTO", "DQT_U64", "PLAIN"])
+@pytest.mark.parametrize("p,n", [(3, 100003), (7, 17), (2, 4096 + 5), (13, 1 << 20)])
+def test_noalloc_offset_views(env, algo, p, n):
+    """Arrays that start one byte past a 16-byte line (the entry-by-entry route) and lengths
+    that are not a multiple of 16 (the tail that block 0 adds), against fp_dot and the oracle."""
+    fp, torch, dev, ctx = env
+    a = getattr(fp, "FP_ALGO_" + algo)
+    for call in range(2):
+        u, v = workloads.dot_inputs(77 * call + n + p, p, n + 1)
+        U, V = to_dev(torch, dev, u)[1:], to_dev(torch, dev, v)[1:]
+        assert U.data_ptr() % 16 == 1
+        want = field.dot_mod(u[1:], v[1:], p)
+        ref = torch.zeros((1,), dtype=torch.int32, device=dev)
+        got = torch.full((1,), -7, dtype=torch.int32, device=dev)
+        fp.fp_dot(ctx, p, U, V, n, ref, a)
+        fp.fp_ctx_status(ctx)
+        fp.fp_dot_noalloc(p, U, V, n, got, a)
+        torch.cuda.synchronize()
+        assert int(got.item()) == int(ref.item()) == want
 
 
 def test_noalloc_flags_bad_input_then_recovers(env):
