@@ -5,8 +5,13 @@ C ABI with host buffers, and the CPU oracle timed beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--algo NAME]
 
-One step = the four products of the configuration, each one fp_matmul call (pack of B into
-words, word contraction, REDQ unpack into C).  Prints one JSON line on rank 0.
+One step = the four products of the configuration in one grouped call (AUTO: the e4m3
+tensor-core product).  The same line carries the packed DQT + REDQ arm on the same inputs
+(right compression: fp16 words on the tensor cores for p = 3, FP32 words on FFMA for p = 7),
+graph-timed with its own roofline, and -- on one GPU, unless --no-configs -- the other
+configurations nested under "configs": batched F_3 polynomial products, GF(p^k) products, the
+4096-instance uneven batch and the serving loop, each with its roofline, end-to-end number and
+the CPU oracle on one core and on all cores.  Prints one JSON line on rank 0.
 """
 from __future__ import annotations
 
@@ -180,26 +185,116 @@ def dist_setup(args):
     return ws, rank, local
 
 
-def cpu_oracle_rate(budget_s=12.0, rows_per_chunk=32):
-    """Oracle matmul (numpy int64, single thread) on a bounded sample: row chunks of the same
-    four problems, round robin, until the time budget is spent.  Returns (MAC/s, sample)."""
+# ------------------------------------------------------------------ CPU oracle baselines
+#
+# The oracle as it stands, on the host cores: one process alone, then one process per core the
+# bench may use (sched_getaffinity), each on its own bounded sample of the workload.  Processes
+# are started with "spawn" (a fork after CUDA initialisation can hang).  A worker builds its
+# inputs, then works until its time budget is spent, and returns (units, seconds).
+
+def _cpu_work(kind, budget_s, wid):
+    sys.path.insert(0, ROOT)
     from oracle import field
-    inputs = [(p, n) + workloads.matmul_inputs(100 + p + n, p, n, n, n) for p, n in PROBLEMS]
-    macs = 0
-    rows_done = {(p, n): 0 for p, n in PROBLEMS}
-    t0 = time.perf_counter()
-    i = 0
-    while time.perf_counter() - t0 < budget_s:
-        p, n, a, b = inputs[i % len(inputs)]
-        r0 = (rows_done[(p, n)]) % n
-        rows = np.arange(r0, min(n, r0 + rows_per_chunk))
-        field.matmul_mod_rows(a, b, p, rows)
-        macs += len(rows) * n * n
-        rows_done[(p, n)] += len(rows)
-        i += 1
-    dt = time.perf_counter() - t0
-    sample = ", ".join(f"{v} rows of p={p} n={n}" for (p, n), v in rows_done.items())
-    return macs / dt, sample, dt
+    g = np.random.default_rng(9000 + wid)
+    units = 0.0
+    if kind == "matmul":
+        inputs = [(p, n) + workloads.matmul_inputs(100 + p + n, p, n, n, n) for p, n in PROBLEMS]
+        t0 = time.perf_counter()
+        i = 0
+        while time.perf_counter() - t0 < budget_s:
+            p, n, a, b = inputs[i % len(inputs)]
+            r0 = int(g.integers(0, n - 16))
+            field.matmul_mod_rows(a, b, p, np.arange(r0, r0 + 16))
+            units += 16 * n * n
+            i += 1
+    elif kind == "polymul":
+        a, b = workloads.polymul_inputs(900 + wid, 3, 1 << 20, 2, 2)
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            field.polymul_mod(a, b, 3)
+            units += (1 << 20) * 9
+    elif kind == "gf":
+        data = []
+        for p, k in workloads.GF_FIELDS:
+            a, b = workloads.gf_inputs(700 + p + wid, p, k, 1 << 17)
+            data.append((p, k, a.astype(np.int64), b.astype(np.int64), field.smallest_monic_irreducible(p, k)))
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            for p, k, a, b, mod in data:
+                field.gf_mul(a, b, p, k, mod)
+                units += k * k * len(a)
+    elif kind == "batch":
+        insts = workloads.uneven_batch(2024, count=4096)
+        order = g.permutation(len(insts))
+        t0 = time.perf_counter()
+        i = 0
+        while time.perf_counter() - t0 < budget_s:
+            x = insts[order[i % len(insts)]]
+            if x.kind == "matmul":
+                rows = np.arange(0, min(x.m, 8))
+                field.matmul_mod_rows(x.a, x.b, x.p, rows)
+                units += len(rows) * x.k * x.n
+            else:
+                field.dot_mod(x.a, x.b, x.p)
+                units += x.k
+            i += 1
+    elif kind == "serve":
+        reqs = workloads.serving_stream(77, rate=20000.0, duration=1.0)
+        mods = {pk: field.smallest_monic_irreducible(*pk) for pk in workloads.GF_FIELDS}
+        order = g.permutation(len(reqs))
+        t0 = time.perf_counter()
+        i = 0
+        while time.perf_counter() - t0 < budget_s:
+            r = reqs[order[i % len(reqs)]]
+            code, sz, A, B, out = workloads.request_arrays(r)
+            if code == 0:
+                field.polymul_mod(A, B, r.p)
+            elif code == 1:
+                field.dot_mod(A, B, r.p)
+            elif code == 2:
+                field.gf_mul(A.astype(np.int64), B.astype(np.int64), r.p, r.gf_k, mods[(r.p, r.gf_k)])
+            else:
+                field.matmul_mod(A, B, r.p)
+            units += 1
+            i += 1
+    else:
+        raise ValueError(kind)
+    return units, time.perf_counter() - t0
+
+
+_POOL = None
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(kind, unit, sample, budget_s=6.0):
+    """The oracle on one core and on all cores (a bounded sample, `budget_s` of work per process)."""
+    global _POOL
+    import multiprocessing as mp
+    n = cpu_cores()
+    if _POOL is None:
+        _POOL = mp.get_context("spawn").Pool(n)
+    u1, t1 = _POOL.apply(_cpu_work, (kind, budget_s, 0))
+    res = _POOL.starmap(_cpu_work, [(kind, budget_s, w + 1) for w in range(n)])
+    un = sum(u for u, _ in res)
+    tn = max(t for _, t in res)
+    return {"value": un / tn, "unit": unit, "cores": n, "kind": "oracle",
+            "sample": f"{sample}; {budget_s:.0f} s of work per process, one process per core (spawn pool)",
+            "single_core": {"value": u1 / t1, "cores": 1, "seconds": t1},
+            "cores_source": "os.sched_getaffinity"}
+
+
+def close_pool():
+    global _POOL
+    if _POOL is not None:
+        _POOL.close()
+        _POOL.join()
+        _POOL = None
 
 
 def run_reference(args, ws, rank):
@@ -252,7 +347,7 @@ def _timed(torch, stream, fn, reps, flush=None):
     return ts
 
 
-def run_polymul(args, ws, rank, local):
+def run_polymul(args, ws, rank, local, emit=True):
     """Batched polynomial products over F_3, degree 2 x degree 2 (the paper's Kronecker
     example size), DQT-packed: a step is 2^20 pairs; 48 input/output sets rotate so every step
     reads cold data (48 x 11.5 MB > 4 x L2), plus a scaled row of 2^26 pairs in one call."""
@@ -434,15 +529,7 @@ def run_polymul(args, ws, rank, local):
     te = statistics.median(_timed(torch, stream, e2e, 10))
     cpu = None
     if rank == 0 and not args.no_cpu:
-        n_cpu = 1 << 22
-        t0 = time.perf_counter()
-        reps = 0
-        while time.perf_counter() - t0 < 10.0:
-            field.polymul_mod(ab[:n_cpu], bb[:n_cpu], p)
-            reps += 1
-        dt = time.perf_counter() - t0
-        cpu = {"value": reps * n_cpu * mpp / dt, "unit": "F_p MAC/s", "cores": 1, "kind": "oracle",
-               "sample": f"{reps} x 2^22 pairs ({dt:.1f} s, numpy int64 schoolbook + % p, single thread)"}
+        cpu = cpu_baseline("polymul", "F_p MAC/s", "2^20 F_3 degree-2 pairs per pass, numpy int64 schoolbook + % p")
     roof = None
     if dom:
         # One launch per step: the timed graph replays give the launch's duration directly (their
@@ -459,8 +546,9 @@ def run_polymul(args, ws, rank, local):
                 "launch_timing": "graph replay, one launch per step" if one_per_step else "library events per plain call",
                 "scaled_2^26": {"achieved": big * bpp / (tb / 1e3) / 1e9, "frac": big * bpp / (tb / 1e3) / 1e9 / hbm,
                                 "ms": tb}}
+    res = None
     if rank == 0:
-        print(json.dumps({
+        res = {
             "metric": METRIC, "value": value, "unit": "F_p MAC/s", "n_gpus": ws, "steps": len(ts) * nsets,
             "warmup": max(3, args.warmup), "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "packed word (planner: u32/f32/u64/f64)", "data": "synthetic",
@@ -474,11 +562,14 @@ def run_polymul(args, ws, rank, local):
                     "h2d_bytes_per_step": batch * (da + db + 2), "d2h_bytes_per_step": batch * (da + db + 1)},
             "gpu_launches": launches, "clocks": clk.summary(), "compare_same_inputs_2^26": compare,
             "other_hbm_steps": hbm_rows, "large_degree_same_inputs": large,
-        }))
+        }
+        if emit:
+            print(json.dumps(res))
     fp.fp_ctx_destroy(ctx)
+    return res
 
 
-def run_gf(args, ws, rank, local):
+def run_gf(args, ws, rank, local, emit=True):
     """GF(p^k) multiplication (Algorithm FGDP with n = 1): 2^24 random pairs in each of
     GF(3^5), GF(7^4), GF(2^8) per step (201 MB of indices moved, L2 flushed between steps).
     F_p MACs per multiply = k^2 (the schoolbook product; the reduction is not counted)."""
@@ -571,6 +662,35 @@ def run_gf(args, ws, rank, local):
                            "frac_hbm": eb / (t / 1e3) / 1e9 / hbm}
             dot_rows[f"GF({p}^{k})"] = row
             del ga, gb, xa, xb
+    # GF(p^k) matrix product (Algorithm FGDP on every entry): 1024 x 1024 x 1024 per field,
+    # sampled entries against the oracle's field dot product first
+    mm_rows = {}
+    if not args.no_compare:
+        nm_ = 1024
+        for p, k, a, b, gfh, A, B, C in fields:
+            q = p ** k
+            mod = field.smallest_monic_irreducible(p, k)
+            dt = workloads.gf_index_dtype(p, k)
+            g_ = np.random.default_rng(q)
+            ha = g_.integers(0, q, (nm_, nm_)).astype(dt)
+            hb = g_.integers(0, q, (nm_, nm_)).astype(dt)
+            tdt = torch.uint8 if dt == np.uint8 else torch.int16
+            to = lambda x: torch.from_numpy(x.view(np.int16) if x.dtype == np.uint16 else x).to(dev)
+            Am, Bm = to(ha), to(hb)
+            Cm = torch.empty((nm_, nm_), dtype=tdt, device=dev)
+            fn = lambda Am=Am, Bm=Bm, Cm=Cm, gfh=gfh: fp.fp_gf_matmul(ctx, gfh, nm_, nm_, nm_, Am, nm_, Bm, nm_, Cm, nm_)
+            fn()
+            torch.cuda.synchronize()
+            fp.fp_ctx_status(ctx)
+            got = Cm.cpu().numpy()
+            got = got.view(np.uint16) if dt == np.uint16 else got
+            for r_, c_ in ((0, 0), (511, 1023), (1023, 7)):
+                assert int(got[r_, c_]) == field.gf_dot(ha[r_].astype(np.int64), hb[:, c_].astype(np.int64), p, k, mod), \
+                    f"GF({p}^{k}) matmul parity"
+            t = statistics.median(_timed(torch, stream, fn, 3, flush))
+            mm_rows[f"GF({p}^{k})"] = {"ms": t, "GF MAC/s": nm_ ** 3 / (t / 1e3), "F_p MAC/s": k * k * nm_ ** 3 / (t / 1e3),
+                                        "chunk": fp.fp_gf_dot_info(gfh)["chunk"]}
+            del Am, Bm, Cm
     hin = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory(), torch.empty(count, dtype=A.dtype).pin_memory())
            for p, k, a, b, gfh, A, B, C in fields]
 
@@ -586,17 +706,7 @@ def run_gf(args, ws, rank, local):
     te = statistics.median(_timed(torch, stream, e2e, 5))
     cpu = None
     if rank == 0 and not args.no_cpu:
-        n_cpu = 1 << 18
-        t0 = time.perf_counter()
-        m_done = 0
-        while time.perf_counter() - t0 < 10.0:
-            for p, k, a, b, *_ in fields:
-                field.gf_mul(a[:n_cpu].astype(np.int64), b[:n_cpu].astype(np.int64), p, k,
-                             field.smallest_monic_irreducible(p, k))
-                m_done += k * k * n_cpu
-        dt = time.perf_counter() - t0
-        cpu = {"value": m_done / dt, "unit": "F_p MAC/s", "cores": 1, "kind": "oracle",
-               "sample": f"2^18 pairs per field, round robin ({dt:.1f} s, numpy schoolbook + remainder, single thread)"}
+        cpu = cpu_baseline("gf", "F_p MAC/s", "2^17 pairs per field per pass, numpy schoolbook + remainder by the modulus")
     kper = kms / max(1, nk)
     # The kernel is bound by the integer ALU pipe (shifts, masks, logic): its roof is that pipe's
     # rate from unit counts, 152 SMs x 64 lanes x 2.07 GHz, and `achieved` the ALU-pipe operations
@@ -620,8 +730,9 @@ def run_gf(args, ws, rank, local):
             "launches": nk, "avg_launch_ms": kper,
             "hbm_frac": nbytes / len(fields) / (kper / 1e3) / 1e9 / hbm,
             "note": "achieved = ALU-pipe operations per launch (committed ncu capture) / average launch time"}
+    res = None
     if rank == 0:
-        print(json.dumps({
+        res = {
             "metric": METRIC, "value": ws * macs / (t_ms / 1e3), "unit": "F_p MAC/s", "n_gpus": ws,
             "steps": len(ts), "warmup": max(3, args.warmup), "ms_per_step": t_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32 DQT words, u64 products",
@@ -632,15 +743,20 @@ def run_gf(args, ws, rank, local):
             "e2e": {"value": ws * macs / (te / 1e3), "unit": "F_p MAC/s", "h2d_bytes_per_step": 2 * nbytes // 3,
                     "d2h_bytes_per_step": nbytes // 3},
             "gpu_launches": launches, "clocks": clk.summary(),
-            "dot_2^26_terms": dot_rows,
-        }))
+            "dot_2^26_terms": dot_rows, "matmul_1024^3": mm_rows,
+        }
+        if emit:
+            print(json.dumps(res))
     fp.fp_ctx_destroy(ctx)
+    return res
 
 
-def run_batch(args, ws, rank, local):
+def run_batch(args, ws, rank, local, emit=True):
     """Uneven batch: 4096 matmul / dot instances (p in {2,3,5,7,17,31}, sizes log-uniform in
     [16, 2048]) in one fp_batch_run call (large products on the tensor-core kernels, the rest in
-    one persistent launch), against one fp_matmul / fp_dot call per instance."""
+    one persistent launch), against one fp_matmul / fp_dot call per instance.  All operands live
+    in one device arena (inputs, then outputs), so the end-to-end step is one host-to-device copy
+    of every input, the call, and one device-to-host copy of every result."""
     import torch
     import __graft_entry__ as g
     g.build()
@@ -648,41 +764,60 @@ def run_batch(args, ws, rank, local):
     from oracle import field
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    ctx = fp.fp_ctx_create(local)
+    ctx = fp.fp_ctx_create(local)          # the batch: packing degrees from the autotuner
+    ctx1 = fp.fp_ctx_create(local)         # the per-instance arm: the fixed AUTO rule
+    fp.fp_ctx_autotune(ctx1, 0)
     insts = workloads.uneven_batch(2024, count=4096)
-    bufs, arr = [], []
-    macs = 0
+    up = lambda x: (x + 255) & ~255
+    off, in_bytes = [], 0
     for x in insts:
-        A = torch.from_numpy(x.a).to(dev)
-        B = torch.from_numpy(x.b).to(dev)
+        oa = in_bytes
+        in_bytes = up(in_bytes + x.a.nbytes)
+        ob = in_bytes
+        in_bytes = up(in_bytes + x.b.nbytes)
+        off.append([oa, ob, 0])
+    out_bytes = 0
+    for x, o in zip(insts, off):
+        o[2] = out_bytes
+        out_bytes = up(out_bytes + (x.m * x.n if x.kind == "matmul" else 4))
+    h_in = torch.zeros(in_bytes, dtype=torch.uint8).pin_memory()
+    hv = h_in.numpy()
+    for x, (oa, ob, _) in zip(insts, off):
+        hv[oa:oa + x.a.nbytes] = x.a.reshape(-1)
+        hv[ob:ob + x.b.nbytes] = x.b.reshape(-1)
+    d_in = h_in.to(dev)
+    d_out = torch.full((out_bytes,), 255, dtype=torch.uint8, device=dev)
+    h_out = torch.empty(out_bytes, dtype=torch.uint8).pin_memory()
+    bi, bo = d_in.data_ptr(), d_out.data_ptr()
+    arr, macs = [], 0
+    for x, (oa, ob, oc) in zip(insts, off):
+        kind = 0 if x.kind == "matmul" else 1
+        m, n = (x.m, x.n) if kind == 0 else (1, 1)
+        arr.append(fp.fp_instance(kind=kind, p=x.p, m=m, n=n, k=x.k, reserved=0, A=bi + oa, B=bi + ob, C=bo + oc))
+        macs += x.m * x.n * x.k if kind == 0 else x.k
+
+    def c_of(i):
+        x, oc = insts[i], off[i][2]
         if x.kind == "matmul":
-            C = torch.empty((x.m, x.n), dtype=torch.uint8, device=dev)
-            arr.append(fp.fp_instance(kind=0, p=x.p, m=x.m, n=x.n, k=x.k, reserved=0, A=A.data_ptr(),
-                                      B=B.data_ptr(), C=C.data_ptr()))
-            macs += x.m * x.n * x.k
-        else:
-            C = torch.empty((4,), dtype=torch.uint8, device=dev)
-            arr.append(fp.fp_instance(kind=1, p=x.p, m=1, n=1, k=x.k, reserved=0, A=A.data_ptr(),
-                                      B=B.data_ptr(), C=C.data_ptr()))
-            macs += x.k
-        bufs.append((A, B, C))
+            return d_out[oc:oc + x.m * x.n].view(x.m, x.n)
+        return d_out[oc:oc + 4]
+
     stream = torch.cuda.current_stream()
 
     def batched():
         fp.fp_batch_run(ctx, arr)
 
     def per_instance():
-        for x, (A, B, C) in zip(insts, bufs):
+        for x, a in zip(insts, arr):
             if x.kind == "matmul":
-                fp.fp_matmul(ctx, x.p, x.m, x.n, x.k, A, x.k, B, x.n, C, x.n, fp.FP_MM_AUTO)
+                fp.fp_matmul(ctx1, x.p, x.m, x.n, x.k, a.A, x.k, a.B, x.n, a.C, x.n, fp.FP_MM_AUTO)
             else:
-                fp.fp_dot(ctx, x.p, A, B, x.k, C, fp.FP_ALGO_PLAIN)
+                fp.fp_dot(ctx1, x.p, a.A, a.B, x.k, a.C, fp.FP_ALGO_PLAIN)
 
-    fp.fp_ctx_autotune(ctx, 0)      # per-instance arm: the fixed rule (no per-size-class tuning runs)
-    batched()                        # planner + packing-degree autotuner of the batch run once
+    batched()                        # planner + the packing-degree autotuner run once here
     fp.fp_ctx_status(ctx)
     for i in np.random.default_rng(1).choice(len(insts), 16, replace=False):   # parity gate
-        x, (A, B, C) = insts[i], bufs[i]
+        x, C = insts[i], c_of(i)
         if x.kind == "matmul":
             rows = np.array([0, x.m - 1])
             assert np.array_equal(C[rows].cpu().numpy(), field.matmul_mod_rows(x.a, x.b, x.p, rows))
@@ -690,11 +825,12 @@ def run_batch(args, ws, rank, local):
             assert int(C.cpu().numpy().view(np.uint32)[0]) == field.dot_mod(x.a, x.b, x.p)
     per_instance()
     torch.cuda.synchronize()
+    fp.fp_ctx_status(ctx1)
 
     def timed(fn, reps):
-        # `reps` consecutive steps between two synchronisations (the inputs, ~1.5 GB, exceed L2),
-        # so one step's host planning overlaps the previous step's kernels as in a running job;
-        # the per-step time is the total over reps
+        # `reps` consecutive steps between two synchronisations (the inputs exceed L2), so one
+        # step's host planning overlaps the previous step's kernels as in a running job; the
+        # per-step time is the total over reps
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
@@ -707,9 +843,11 @@ def run_batch(args, ws, rank, local):
     for _ in range(max(3, args.warmup)):
         batched()
     torch.cuda.synchronize()
+    l0 = fp.fp_ctx_launches(ctx)
     clk = Clocks(local).__enter__()
     tb = timed(batched, args.steps)
     clk.__exit__(None, None, None)
+    launches = fp.fp_ctx_launches(ctx) - l0
     # per-kernel times from the library's own events over separate steps
     fp.fp_ctx_profile(ctx, 2)
     fp.fp_ctx_profile(ctx, 1)
@@ -717,7 +855,7 @@ def run_batch(args, ws, rank, local):
         batched()
     torch.cuda.synchronize()
     fp.fp_ctx_profile(ctx, 0)
-    names = ["k_mm_f8g", "k_mm_t16_plain", "k_batch", "k_pad_rows", "k_t16_convert_jobs"]
+    names = ["k_mm_f8g", "k_mm_t16_plain", "k_batch", "k_pad_rows", "k_t16_convert_jobs", "k_put_bytes"]
     kern = {}
     for nm in names:
         c, ms = fp.fp_ctx_profile_read(ctx, nm)
@@ -725,8 +863,28 @@ def run_batch(args, ws, rank, local):
             kern[nm] = {"launches_per_step": c / args.steps, "ms_per_step": ms / args.steps}
     tp = timed(per_instance, max(2, args.steps // 5))
     fp.fp_ctx_status(ctx)
+    fp.fp_ctx_status(ctx1)
     v_b = macs / (statistics.median(tb) / 1e3)
     v_p = macs / (statistics.median(tp) / 1e3)
+
+    # end to end: every input in, the call, every result out (one copy each way per step)
+    def e2e():
+        d_in.copy_(h_in, non_blocking=True)
+        fp.fp_batch_run(ctx, arr)
+        h_out.copy_(d_out, non_blocking=True)
+
+    e2e()
+    torch.cuda.synchronize()
+    te = timed(e2e, max(3, args.steps // 2))
+    fp.fp_ctx_status(ctx)
+    hv_out = h_out.numpy()
+    for i in np.random.default_rng(2).choice(len(insts), 8, replace=False):   # results read back
+        x, oc = insts[i], off[i][2]
+        if x.kind == "matmul":
+            got = hv_out[oc:oc + x.m * x.n].reshape(x.m, x.n)[[0]]
+            assert np.array_equal(got, field.matmul_mod_rows(x.a, x.b, x.p, np.array([0])))
+        else:
+            assert int(hv_out[oc:oc + 4].view(np.uint32)[0]) == field.dot_mod(x.a, x.b, x.p)
     # The library's routing (fp_batch_run's documented rule): large products with p <= 17 on the
     # e4m3 kernel, 17 < p <= 127 on the bf16 kernel, the rest in the batch kernel.  Roofline of the
     # kernel with the most time per step, on its own MACs.
@@ -747,23 +905,38 @@ def run_batch(args, ws, rank, local):
     for nm in kern:
         if nm in kmacs:
             kern[nm]["fp_macs_per_step"] = kmacs[nm]
+            kern[nm]["frac_of_roof"] = 2.0 * kmacs[nm] / (kern[nm]["ms_per_step"] / 1e3) / 1e12 / peaks_k[nm][0]
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline("batch", "F_p MAC/s", "instances of the same 4096-instance batch in random order: up to "
+                           "8 rows of each product (numpy int64 matmul + % p), whole dot products")
     out = {"metric": "exact F_p MACs/s (uneven batch, one call)", "value": v_b, "unit": "F_p MAC/s",
            "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": statistics.median(tb),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3/bf16/f16",
            "data": "synthetic",
            "config": {"workload": "4096 instances: 50% matmul, 50% dot, p in {2,3,5,7,17,31}, sizes log-uniform [16,2048]",
-                      "macs_per_step": macs, "instances": len(insts)},
+                      "macs_per_step": macs, "instances": len(insts), "input_bytes": in_bytes, "output_bytes": out_bytes,
+                      "autotuner": "on for the batch (packing degree per (p, k class) timed once on the first call); "
+                                   "the per-instance arm uses a second context with the fixed rule"},
            "per_instance_launches": {"value": v_p, "unit": "F_p MAC/s", "ms_per_step": statistics.median(tp),
                                      "launches": "one fp_matmul / fp_dot call per instance (fixed AUTO rule)"},
            "speedup_vs_per_instance": v_b / v_p,
            "timing": "consecutive steps between two synchronisations, inputs larger than L2",
+           "gpu_launches": launches,
            "clocks": clk.summary(),
            "kernels": kern,
            "roofline": {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peaks_k[dom][0],
                         "unit": "TFLOP/s", "frac": achieved / peaks_k[dom][0], "peak_source": peaks_k[dom][1],
-                        "note": "achieved = 2 x the kernel's own F_p MACs per step / its time per step"}}
-    print(json.dumps(out))
+                        "traffic": None,
+                        "note": "achieved = 2 x the kernel's own F_p MACs per step / its time per step"},
+           "cpu_baseline": cpu,
+           "e2e": {"value": macs / (statistics.median(te) / 1e3), "unit": "F_p MAC/s", "h2d_bytes_per_step": in_bytes,
+                   "d2h_bytes_per_step": out_bytes}}
+    if emit:
+        print(json.dumps(out))
     fp.fp_ctx_destroy(ctx)
+    fp.fp_ctx_destroy(ctx1)
+    return out
 
 
 def req_macs(code, sz, gf_k):
@@ -776,7 +949,7 @@ def req_macs(code, sz, gf_k):
     return sz[0] ** 3
 
 
-def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0):
+def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0, emit=True):
     """Serving: a Poisson stream (20k requests/s offered for `duration` s; 50% polymul, 30% dot,
     15% GF(p^k) batches, 5% matmul) through the continuous-batching server.  Reports latency
     percentiles at the offered load, and capacity (the stream submitted at once) against a
@@ -821,8 +994,16 @@ def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0):
     # warm-up (first-use costs: module load, tables), then the paced run and the capacity run
     serve(False)
     wall_p, lat_p, st_p = serve(True)
+    fp.fp_ctx_profile(ctx, 2)
+    fp.fp_ctx_profile(ctx, 1)
     wall_c, lat_c, st_c = serve(False)
+    fp.fp_ctx_profile(ctx, 0)
     fp.fp_ctx_status(ctx)
+    kern = {}
+    for nm in ("k_polymul_var", "k_gf_mul_seg", "k_batch"):
+        c, ms = fp.fp_ctx_profile_read(ctx, nm)
+        if c:
+            kern[nm] = {"launches": c, "ms": ms}
     # parity gate on a sample of the served results
     for i in np.random.default_rng(3).choice(len(reqs), 40, replace=False):
         r, (code, sz, A, B, out) = reqs[i], data[i]
@@ -863,6 +1044,33 @@ def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0):
     base_rps = n_base / base_wall
     cap_rps = len(reqs) / wall_c
     pct = lambda a, q: float(np.percentile(a[a >= 0], q))
+    # roofline of the kernel with the most device time in the capacity run.  k_batch holds the
+    # matmul and dot requests (legacy mma.sync bf16 tiles); k_polymul_var the blocked-FQT
+    # products (integer issue); k_gf_mul_seg the field products (integer ALU)
+    mm_macs = sum(req_macs(c, sz, r.gf_k) for r, (c, sz, A, B, out) in zip(reqs, data) if c in (1, 3))
+    roof = None
+    if kern:
+        dom = max(kern, key=lambda nm: kern[nm]["ms"])
+        if dom == "k_batch":
+            ach = 2.0 * mm_macs / (kern[dom]["ms"] / 1e3) / 1e12
+            roof = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": 603.2, "unit": "TFLOP/s",
+                    "frac": ach / 603.2, "traffic": None,
+                    "peak_source": "mma.sync bf16 measured by the pipe probe",
+                    "note": "achieved = 2 x the matmul and dot requests' F_p MACs / k_batch device time"}
+        else:
+            pm = sum(req_macs(c, sz, r.gf_k) for r, (c, sz, A, B, out) in zip(reqs, data) if c == 0)
+            roof = {"bound": "alu", "kernel": dom, "achieved": pm / (kern[dom]["ms"] / 1e3) / 1e12,
+                    "peak": 152 * 64 * 2.07e9 / 1e12, "unit": "T F_p MAC/s vs T int32 ops/s", "frac": None,
+                    "traffic": None, "note": "no clean roof: integer issue bound"}
+        share = sum(v["ms"] for v in kern.values())
+        for nm in kern:
+            kern[nm]["share"] = kern[nm]["ms"] / share
+    in_b = sum(A.nbytes + B.nbytes for (c, sz, A, B, out) in data)
+    out_b = sum(out.nbytes for (c, sz, A, B, out) in data)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline("serve", "requests/s", "requests of the same stream in random order, the full oracle "
+                           "per request (schoolbook polymul, dot, field product, plain matmul)")
     out = {"metric": "served requests/s (continuous batching) with p50/p99 latency", "value": cap_rps,
            "unit": "requests/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": wall_c * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
@@ -876,61 +1084,119 @@ def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0):
            "per_request_launches": {"requests_per_s": base_rps, "requests": n_base,
                                     "p50_latency_us_at_offered_load": float(np.percentile(base_lat, 50)) * 1e6,
                                     "p99_latency_us_at_offered_load": float(np.percentile(base_lat, 99)) * 1e6},
-           "capacity_vs_per_request": cap_rps / base_rps}
-    print(json.dumps(out))
+           "capacity_vs_per_request": cap_rps / base_rps,
+           "kernels_capacity_run": kern, "roofline": roof, "cpu_baseline": cpu,
+           "e2e": {"value": cap_rps, "unit": "requests/s", "h2d_bytes_per_step": in_b, "d2h_bytes_per_step": out_b,
+                   "note": "the server is end to end: host buffers in, host buffers out; a step is the whole stream"}}
+    if emit:
+        print(json.dumps(out))
     for g2 in gfs.values():
         fp.fp_gf_destroy(g2)
     fp.fp_ctx_destroy(ctx)
+    return out
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="matmul", choices=["matmul", "batch", "serve", "polymul", "gf"],
-                    help="matmul: the compressed-matmul configuration (default line); batch: 4096 uneven instances")
-    ap.add_argument("--algo", default="AUTO")
-    ap.add_argument("--no-compare", action="store_true", help="skip the per-variant comparison block")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--problems", default="", help="subset, e.g. 3:4096,7:1024 (default: all four)")
-    ap.add_argument("--no-graph", action="store_true", help="time plain launches instead of CUDA-graph replays")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="AUTO uses the fixed rule instead of timing candidates (for runs under a profiler)")
-    ap.add_argument("--min-warmup-s", type=float, default=1.0,
-                    help="keep warming up at least this long (clock sampling under load)")
-    args = ap.parse_args()
-    args.warmup = max(3, args.warmup)
-    global PROBLEMS
-    if args.problems:
-        PROBLEMS = [tuple(int(x) for x in t.split(":")) for t in args.problems.split(",")]
-    ws, rank, local = dist_setup(args)
-    if args.impl == "reference":
-        run_reference(args, ws, rank)
-        return
-    if args.workload == "batch":
-        run_batch(args, ws, rank, local)
-        return
-    if args.workload == "serve":
-        run_serve(args, ws, rank, local)
-        return
-    if args.workload == "polymul":
-        run_polymul(args, ws, rank, local)
-        return
-    if args.workload == "gf":
-        run_gf(args, ws, rank, local)
-        return
+def graph_steps(torch, stream, step, flush, steps):
+    """Per-step device times (ms) of `steps` replays of one CUDA graph of `step`, the L2 flushed
+    (outside the events) before each; plain launches if the step cannot be captured."""
+    graph = torch.cuda.CUDAGraph()
+    try:
+        with torch.cuda.graph(graph):
+            step()
+        run = graph.replay
+        run()
+    except Exception:           # not capturable: time plain launches
+        torch.cuda.synchronize()
+        graph, run = None, step
+    torch.cuda.synchronize()
+    ts = _timed(torch, stream, run, steps, flush)
+    return ts, graph is not None
 
+
+def packed_arm(args, fp, torch, ctx, prob, flush, stream, ktab, peak_src, plain_value, local):
+    """Packed DQT + REDQ on the same resident inputs as the headline step: the right-compressed
+    product (Sec. 7.4) of every problem on the tensor cores -- fp16 words with two centred
+    residues (RIGHT_TC: Q = 2^10 in chunks of 448 inner steps for p = 3, Q = 2^9 in chunks of 16
+    for p = 7), one grouped call -- timed as a graph-replayed step like the headline.  The
+    dominant packed kernel's roofline counts its word operations 2 m ceil(n/2) k; the plain
+    bf16 products on the same pipe (PLAIN_TC) are timed the same way for the same-pipe ratio."""
+    from oracle import field
+    macs = sum(q["n"] ** 3 for q in prob)
+    descs = [fp.fp_mm_problem_of(q["p"], q["n"], q["n"], q["n"], q["A"], q["n"], q["B"], q["n"], q["C"], q["n"])
+             for q in prob]
+    arms = {}
+    for label, algo in (("packed", fp.FP_MM_RIGHT_TC), ("plain_same_pipe", fp.FP_MM_PLAIN_TC)):
+        def step(algo=algo):
+            fp.fp_matmul_grouped(ctx, descs, algo)
+
+        for q in prob:
+            q["C"].fill_(255)
+        step()
+        torch.cuda.synchronize()
+        fp.fp_ctx_status(ctx)
+        for q in prob:          # parity gate: rows across the tile rows against the oracle
+            rows = np.array([0, q["n"] // 3, q["n"] - 1])
+            assert np.array_equal(q["C"][rows].cpu().numpy(), field.matmul_mod_rows(q["a"], q["b"], q["p"], rows)), \
+                f"{label} parity p={q['p']} n={q['n']}"
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+        ts, graphed = graph_steps(torch, stream, step, flush, args.steps)
+        fp.fp_ctx_status(ctx)
+        t_ms = statistics.median(ts)
+        # per-kernel device time from the library's events over plain steps
+        fp.fp_ctx_profile(ctx, 2)
+        fp.fp_ctx_profile(ctx, 1)
+        for _ in range(args.steps):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        fp.fp_ctx_profile(ctx, 0)
+        kern = {}
+        for nm in ("k_mm_t16_packed_p57", "k_mm_t16_packed", "k_mm_t16_plain", "k_t16_convert"):
+            c, ms = fp.fp_ctx_profile_read(ctx, nm)
+            if nm == "k_mm_t16_packed":            # prefix of the p = 5, 7 kernel's name
+                c2, ms2 = fp.fp_ctx_profile_read(ctx, "k_mm_t16_packed_p57")
+                c, ms = c - c2, ms - ms2
+            if c:
+                kern[nm] = {"launches_per_step": c / args.steps, "ms_per_step": ms / args.steps}
+        arms[label] = {"value": macs / (t_ms / 1e3), "ms_per_step": t_ms, "kernels": kern,
+                       "timing": "CUDA graph replay of the step" if graphed else "plain launches"}
+    pk = arms["packed"]
+    cand = {"k_mm_t16_packed": [q for q in prob if q["p"] <= 3], "k_mm_t16_packed_p57": [q for q in prob if q["p"] > 3]}
+    roofs = {}
+    kt = ktab["k_mm_t16_packed"]
+    for nm, qs in cand.items():
+        if nm not in pk["kernels"] or not qs:
+            continue
+        flops = sum(2.0 * q["n"] * q["n"] * (-(-q["n"] // 2)) for q in qs)
+        k_ms = pk["kernels"][nm]["ms_per_step"]
+        ach = flops / (k_ms / 1e3) / 1e12
+        roofs[nm] = {"bound": kt[0], "kernel": nm, "achieved": ach, "peak": kt[1], "unit": "TFLOP/s",
+                     "frac": ach / kt[1], "traffic": None, "peak_source": kt[2] + f" ({peak_src})",
+                     "avg_launch_ms": k_ms / pk["kernels"][nm]["launches_per_step"],
+                     "problems": [f"p={q['p']} n={q['n']}" for q in qs],
+                     "note": "achieved = word flops 2 m ceil(n/2) k of its problems / the kernel's device time per step"}
+    dom = max(roofs, key=lambda nm: pk["kernels"][nm]["ms_per_step"]) if roofs else None
+    return {"value": pk["value"], "unit": "F_p MAC/s", "ms_per_step": pk["ms_per_step"],
+            "algo": "RIGHT_TC (grouped): fp16 pair words, Q = 2^10 (p = 3) / 2^9 (p = 7)",
+            "timing": pk["timing"], "roofline": roofs.get(dom), "roofline_per_kernel": roofs, "kernels": pk["kernels"],
+            "packed_over_plain": pk["value"] / plain_value,
+            "packed_over_plain_note": "same inputs; plain = the headline step (e4m3 tensor cores, AUTO)",
+            "plain_same_pipe": {"value": arms["plain_same_pipe"]["value"], "algo": "PLAIN_TC (bf16, grouped)",
+                                "ms_per_step": arms["plain_same_pipe"]["ms_per_step"],
+                                "kernels": arms["plain_same_pipe"]["kernels"]},
+            "packed_over_plain_same_pipe": pk["value"] / arms["plain_same_pipe"]["value"]}
+
+
+def run_matmul(args, ws, rank, local):
+    """The default line: the compressed matrix product configuration (p in {3, 7} x n in
+    {1024, 4096}); returns the JSON object rank 0 prints (None on other ranks)."""
     import torch
     import __graft_entry__ as g
     g.build()
     import paper_0809_0063_gb300 as fp
 
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     hbm, bf16, bf16s, peak_src = peaks()
@@ -1080,6 +1346,9 @@ def main():
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_label + f" ({peak_src})",
                 "launches": dom_n, "avg_launch_ms": dom_ms / max(1, dom_n)}
 
+    packed_res = None
+    if not args.no_packed and args.algo == "AUTO":
+        packed_res = packed_arm(args, fp, torch, ctx, prob, flush, stream, ktab, peak_src, value, local)
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     hA = [torch.from_numpy(q["a"]).pin_memory() for q in prob]
     hB = [torch.from_numpy(q["b"]).pin_memory() for q in prob]
@@ -1150,8 +1419,10 @@ def main():
     compare = None
     if not args.no_compare and rank == 0:
         compare = {}
-        for name in ["RIGHT_F32", "LEFT_F32", "PLAIN_F32", "RIGHT_F64", "LEFT_F64", "CMM_F64", "PLAIN_F64", "PLAIN_I8",
-                     "PLAIN_TC", "RIGHT_TC", "PLAIN_F8"]:
+        fp64_peak = ktab["k_mm_dmma"][1]
+        fp64_rows = {}
+        for name in ["RIGHT_F32", "LEFT_F32", "PLAIN_F32", "RIGHT_F64", "SPLIT_F64", "FULL_F64", "LEFT_F64", "CMM_F64",
+                     "PLAIN_F64", "PLAIN_I8", "PLAIN_TC", "RIGHT_TC", "PLAIN_F8"]:
             row = {}
             for q in prob:
                 al = getattr(fp, "FP_MM_" + name)
@@ -1169,7 +1440,20 @@ def main():
                     a1.record(stream)
                     torch.cuda.synchronize()
                     fp.fp_ctx_status(ctx)
-                    row[f"p{q['p']}_n{q['n']}"] = q["n"] ** 3 / (a0.elapsed_time(a1) / 1e3)
+                    ms = a0.elapsed_time(a1)
+                    row[f"p{q['p']}_n{q['n']}"] = q["n"] ** 3 / (ms / 1e3)
+                    if name in ("RIGHT_F64", "SPLIT_F64", "FULL_F64"):
+                        # FP64 word products on DMMA: the word flops of the packing against the FP64 roof
+                        n_ = q["n"]
+                        if name == "FULL_F64":
+                            b_, q1, t1, piece = fp.fp_mm_full_choose(q["p"], n_)
+                            wf, pk = 2.0 * (-(-n_ // q1)) * (-(-n_ // t1)) * n_, f"{q1}x{t1} digits, pieces of {piece}"
+                        else:
+                            b_, e_, piece = fp.fp_mm_choose(q["p"], n_, al)
+                            wf, pk = 2.0 * n_ * (-(-n_ // e_)) * n_, f"e={e_}, pieces of {piece}"
+                        fp64_rows.setdefault(name, {})[f"p{q['p']}_n{n_}"] = {
+                            "ms": ms, "F_p MAC/s": n_ ** 3 / (ms / 1e3), "packing": pk,
+                            "word_tflops": wf / (ms / 1e3) / 1e12, "frac_fp64_roof": wf / (ms / 1e3) / 1e12 / fp64_peak}
                 except fp.FpError as ex:
                     row[f"p{q['p']}_n{q['n']}"] = f"unavailable: {ex.args[0][:60]}"
             compare[name] = row
@@ -1183,16 +1467,17 @@ def main():
                 if isinstance(v, float) and isinstance(w, float):
                     pvp.setdefault(key, {})[f"{packed}/{plain}"] = v / w
         compare["packed_over_plain_same_pipe"] = pvp
+        compare["fp64_words_on_dmma"] = {"roof_tflops": fp64_peak, "roof_source": ktab["k_mm_dmma"][2],
+                                         "note": "one timed call each, includes any packing launch", "rows": fp64_rows}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        rate, sample, secs = cpu_oracle_rate()
-        cpu = {"value": rate, "unit": "F_p MAC/s", "cores": 1, "kind": "oracle",
-               "sample": f"{sample} ({secs:.1f} s, numpy int64 matmul + % p, single thread)"}
+        cpu = cpu_baseline("matmul", "F_p MAC/s", "16-row blocks of the four products in turn, numpy int64 matmul + % p")
 
     dt_of = {"RIGHT_F32": "f32", "PLAIN_F32": "f32", "RIGHT_F64": "f64", "PLAIN_F64": "f64",
              "PLAIN_I8": "u8", "PLAIN_TC": "bf16", "RIGHT_TC": "f16", "PLAIN_F8": "e4m3"}
     dtype = "/".join(sorted({dt_of[names[a]] for a in chosen.values()}))
+    out = None
     if rank == 0:
         out = {
             "metric": METRIC,
@@ -1211,12 +1496,79 @@ def main():
             "value_plain_launches": whole_job_rate(macs_per_step, args.steps, ws, max_over_ranks(plain_ms, dev)),
             "clocks": clk.summary(),
             "compare_same_inputs": compare,
+            "packed_dqt_redq": packed_res,
         }
-        print(json.dumps(out))
     fp.fp_ctx_destroy(ctx)
+    return out
+
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="matmul", choices=["matmul", "batch", "serve", "polymul", "gf"],
+                    help="matmul: the compressed-matmul configuration (default line); batch: 4096 uneven instances")
+    ap.add_argument("--algo", default="AUTO")
+    ap.add_argument("--no-compare", action="store_true", help="skip the per-variant comparison block")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--problems", default="", help="subset, e.g. 3:4096,7:1024 (default: all four)")
+    ap.add_argument("--no-graph", action="store_true", help="time plain launches instead of CUDA-graph replays")
+    ap.add_argument("--no-packed", action="store_true", help="skip the packed DQT+REDQ arm of the default line")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the nested polynomial, GF, uneven-batch and serving sub-results of the default line")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="AUTO uses the fixed rule instead of timing candidates (for runs under a profiler)")
+    ap.add_argument("--min-warmup-s", type=float, default=1.0,
+                    help="keep warming up at least this long (clock sampling under load)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    global PROBLEMS
+    if args.problems:
+        PROBLEMS = [tuple(int(x) for x in t.split(":")) for t in args.problems.split(",")]
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    if args.workload == "batch":
+        run_batch(args, ws, rank, local)
+        close_pool()
+        return
+    if args.workload == "serve":
+        run_serve(args, ws, rank, local)
+        close_pool()
+        return
+    if args.workload == "polymul":
+        run_polymul(args, ws, rank, local)
+        close_pool()
+        return
+    if args.workload == "gf":
+        run_gf(args, ws, rank, local)
+        close_pool()
+        return
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out = run_matmul(args, ws, rank, local)
+    if ws == 1 and not args.no_configs:
+        # the other configurations of the metric, nested in the same line (one GPU; replicas
+        # would repeat them unchanged)
+        out["configs"] = {
+            "polymul_2^20_F3_degree2": run_polymul(args, ws, rank, local, emit=False),
+            "gf_mul_2^24_pairs_x3_fields": run_gf(args, ws, rank, local, emit=False),
+            "uneven_batch_4096": run_batch(args, ws, rank, local, emit=False),
+            "serving_poisson_20k": run_serve(args, ws, rank, local, emit=False),
+        }
+    close_pool()
+    if rank == 0:
+        print(json.dumps(out))
     if ws > 1:
         torch.distributed.destroy_process_group()
-
 
 if __name__ == "__main__":
     main()

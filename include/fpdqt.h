@@ -79,7 +79,9 @@ enum {
   FP_MM_PLAIN_I8 = 5,   /* unpacked, u8 x u8 -> s32 tensor cores (mma.sync), mod p epilogue */
   FP_MM_PLAIN_TC = 6,   /* unpacked, tcgen05 kind::f16 (bf16 operands, fp32 accumulate) */
   FP_MM_RIGHT_TC = 7,   /* right compression on tcgen05 kind::f16: fp16 operands holding two
-                           centred residues at Q = 2^10, inner dimension chunked (p <= 3) */
+                           centred residues, inner dimension chunked: p <= 3 at Q = 2^10 in
+                           chunks of 448 (k <= 32767); p = 5, 7 at Q = 2^9 in chunks of 32 / 16
+                           inner steps (one or two MMA instructions), any k */
   FP_MM_LEFT_F32 = 8,   /* left compression (Sec. 7.4): by transposition, (A B)^T = B^T A^T with
                            the right compression (FP32 words) of A^T, i.e. each word packs two
                            consecutive rows of A; A^T, B^T and C^T go through context scratch */
@@ -502,8 +504,10 @@ typedef struct fp_server_s* fp_server;
 /* Continuous batching (no counterpart in the paper; the systems layer around the packed
  * kernels): a scheduler thread takes submitted requests in arrival order, admits them as
  * arena memory frees up, packs every admitted request into one batch (gathered host-to-device
- * copy, one launch per request kind: varlen blocked-FQT polymul, segmented GF multiply, and
- * the persistent matmul/dot kernel of fp_batch_run, one device-to-host copy), issues batches
+ * copy, one launch per request kind: varlen blocked-FQT polymul, segmented GF multiply, the
+ * persistent matmul/dot kernel of fp_batch_run, and for matmul requests with p <= 17, m, n >= 64,
+ * k (p-1)^2 < 2^24 and m n k >= 2^21 the grouped e4m3 tensor-core kernel of fp_matmul_grouped
+ * (their rows staged at 16-byte strides); one device-to-host copy), issues batches
  * round-robin on its streams so that new batches start while earlier ones run, and records
  * each request's latency (submission to observed completion, host steady clock).
  * Errors: FP_EINVAL (bad config), FP_ENOMEM, FP_ECUDA. */

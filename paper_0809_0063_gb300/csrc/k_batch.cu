@@ -40,16 +40,45 @@ __device__ __forceinline__ uint16_t h16(float x, bool fp16) {
 }
 __device__ __forceinline__ float centred(uint32_t v, uint32_t p) { return (p == 3 && v == 2) ? -1.0f : (float)v; }
 
-// Load 16 consecutive bytes of a row with bounds (zeros outside), vectorised when possible.
-__device__ __forceinline__ void load16(const uint8_t* row, int c0, int limit, uint8_t (&b)[16]) {
+// Load 16 consecutive bytes of a row with bounds (zeros past `limit`) as four words: one
+// 16-byte load when aligned, else the aligned 4-byte words that hold them, joined by funnel
+// shifts.  A word is read only if it holds a byte of the row (so no read leaves the row's
+// allocation); bytes past the limit are masked off.
+__device__ __forceinline__ void load16w(const uint8_t* row, int c0, int limit, uint32_t (&w)[4]) {
   const uint8_t* src = row + c0;
-  if (c0 + 16 <= limit && ((((uintptr_t)src) & 15u) == 0)) {
-    uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
-    memcpy(b, &x, 16);
-  } else {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) b[j] = (c0 + j < limit) ? src[j] : 0;
+  const int nb = limit - c0;                 // bytes of the row from c0 on
+  if (nb >= 16 && ((((uintptr_t)src) & 15u) == 0)) {
+    const uint4 x = __ldg(reinterpret_cast<const uint4*>(src));
+    w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+    return;
   }
+  if (nb <= 0) {
+    w[0] = w[1] = w[2] = w[3] = 0u;
+    return;
+  }
+  const uint32_t off = (uint32_t)((uintptr_t)src & 3u);
+  const uint32_t* base = reinterpret_cast<const uint32_t*>(src - off);
+  const int span = (int)off + (nb < 16 ? nb : 16);   // bytes from base that belong to the row
+  uint32_t v[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) v[j] = 4 * j < span ? __ldg(base + j) : 0u;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) w[j] = off ? __funnelshift_r(v[j], v[j + 1], 8 * off) : v[j];
+  if (nb < 16) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int keep = nb - 4 * j;            // valid bytes in word j
+      w[j] = keep >= 4 ? w[j] : (keep <= 0 ? 0u : (w[j] & ((1u << (8 * keep)) - 1u)));
+    }
+  }
+}
+
+// bf16 bits of two residue bytes (bytes s0, s1 of w, values <= 255): the float 2^23 + v has v in
+// its low mantissa bits, so subtracting 2^23 gives float(v) exactly; its top 16 bits are the bf16.
+__device__ __forceinline__ uint32_t bf16x2_of_bytes(uint32_t w, uint32_t s0, uint32_t s1) {
+  const float f0 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650u + s0)) - 8388608.0f;
+  const float f1 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650u + s1)) - 8388608.0f;
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632u);
 }
 
 __device__ void run_dot(const BInst& I, uint32_t* err) {
@@ -98,61 +127,70 @@ __device__ void run_tile(const BInst& I, int tm, int tn, uint8_t* smem, uint32_t
   const int ksteps = (int)((I.k + BT_K - 1) / BT_K);
   const int chunk_steps = packed ? BT_CHUNK_STEPS : (int)I.plain_chunk_steps;
   uint32_t bad = 0;
-  // staging registers
-  uint8_t ra[16], rb[32];
+  // staging registers: residue bytes as words (byte j of the 16 at byte j % 4 of word j / 4)
+  uint32_t ra[4], rb[8];
   const int a_row = tid >> 1, a_h = tid & 1;
   const int b_kr = tid >> 2, b_q = tid & 3;
+  const uint32_t pp4 = 0x01010101u * p;
   auto gload = [&](int ks) {
     const int kb = ks * BT_K;
     const int r = m0 + a_row;
-    if (r < (int)I.m) load16(I.A + (size_t)r * I.k, kb + 16 * a_h, (int)I.k, ra);
-    else
+    if (r < (int)I.m) {
+      load16w(I.A + (size_t)r * I.k, kb + 16 * a_h, (int)I.k, ra);
+    } else {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) ra[j] = 0;
+      for (int j = 0; j < 4; ++j) ra[j] = 0u;
+    }
     const int kr = kb + b_kr;
-    uint8_t t0[16], t1[16];
+    uint32_t t0[4] = {0u, 0u, 0u, 0u}, t1[4] = {0u, 0u, 0u, 0u};
     if (kr < (int)I.k) {
       const uint8_t* brow = I.B + (size_t)kr * I.n;
       if (packed) {
-        load16(brow, 2 * w0 + 32 * b_q, (int)I.n, t0);
-        load16(brow, 2 * w0 + 32 * b_q + 16, (int)I.n, t1);
+        load16w(brow, 2 * w0 + 32 * b_q, (int)I.n, t0);
+        load16w(brow, 2 * w0 + 32 * b_q + 16, (int)I.n, t1);
       } else {
-        load16(brow, w0 + 16 * b_q, (int)I.n, t0);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) t1[j] = 0;
+        load16w(brow, w0 + 16 * b_q, (int)I.n, t0);
       }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) t0[j] = t1[j] = 0;
     }
 #pragma unroll
-    for (int j = 0; j < 16; ++j) { rb[j] = t0[j]; rb[16 + j] = t1[j]; }
+    for (int j = 0; j < 4; ++j) { rb[j] = t0[j]; rb[4 + j] = t1[j]; }
   };
   auto sstore = [&](int buf) {
     uint32_t o[8];
 #pragma unroll
-    for (int j = 0; j < 16; j += 2) {
-      bad |= (ra[j] >= p) | (ra[j + 1] >= p);
-      const float x0 = packed ? centred(ra[j], p) : (float)ra[j];
-      const float x1 = packed ? centred(ra[j + 1], p) : (float)ra[j + 1];
-      o[j >> 1] = (uint32_t)h16(x0, packed) | ((uint32_t)h16(x1, packed) << 16);
+    for (int q = 0; q < 4; ++q) {
+      bad |= __vcmpgeu4(ra[q], pp4);          // zero bytes past a row's end pass the check
+      if (packed) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t b0 = (ra[q] >> (16 * h)) & 0xFFu, b1 = (ra[q] >> (16 * h + 8)) & 0xFFu;
+          o[2 * q + h] = (uint32_t)h16(centred(b0, p), true) | ((uint32_t)h16(centred(b1, p), true) << 16);
+        }
+      } else {
+        o[2 * q] = bf16x2_of_bytes(ra[q], 0, 1);
+        o[2 * q + 1] = bf16x2_of_bytes(ra[q], 2, 3);
+      }
     }
     uint8_t* a = sA + buf * 4096;
     *reinterpret_cast<uint4*>(a + offA(a_row, 2 * a_h)) = make_uint4(o[0], o[1], o[2], o[3]);
     *reinterpret_cast<uint4*>(a + offA(a_row, 2 * a_h + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
+    if (packed) {
+      // word j: c(byte 2j) + 2^10 c(byte 2j + 1) of the 32 bytes
 #pragma unroll
-    for (int j = 0; j < 16; j += 2) {
-      float x0, x1;
-      if (packed) {
-        bad |= (rb[2 * j] >= p) | (rb[2 * j + 1] >= p) | (rb[2 * j + 2] >= p) | (rb[2 * j + 3] >= p);
-        x0 = centred(rb[2 * j], p) + 1024.0f * centred(rb[2 * j + 1], p);
-        x1 = centred(rb[2 * j + 2], p) + 1024.0f * centred(rb[2 * j + 3], p);
-      } else {
-        bad |= (rb[j] >= p) | (rb[j + 1] >= p);
-        x0 = (float)rb[j];
-        x1 = (float)rb[j + 1];
+      for (int q = 0; q < 8; ++q) {
+        bad |= __vcmpgeu4(rb[q], pp4);
+        const uint32_t x = rb[q];
+        const float x0 = centred(x & 0xFFu, p) + 1024.0f * centred((x >> 8) & 0xFFu, p);
+        const float x1 = centred((x >> 16) & 0xFFu, p) + 1024.0f * centred(x >> 24, p);
+        o[q] = (uint32_t)h16(x0, true) | ((uint32_t)h16(x1, true) << 16);
       }
-      o[j >> 1] = (uint32_t)h16(x0, packed) | ((uint32_t)h16(x1, packed) << 16);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        bad |= __vcmpgeu4(rb[q], pp4);
+        o[2 * q] = bf16x2_of_bytes(rb[q], 0, 1);
+        o[2 * q + 1] = bf16x2_of_bytes(rb[q], 2, 3);
+      }
     }
     uint8_t* b = sB + buf * 4096;
     *reinterpret_cast<uint4*>(b + offB(b_kr, 2 * b_q)) = make_uint4(o[0], o[1], o[2], o[3]);

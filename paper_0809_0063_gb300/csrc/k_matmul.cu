@@ -742,7 +742,7 @@ fp_status mm_bound_check(uint32_t p, int k, int algo) {
       FP_CHECK(p <= 17 && (uint64_t)k * pp < (1ull << 24), FP_EBOUND, "PLAIN_F8 needs p <= 17, k (p-1)^2 < 2^24");
       return FP_OK;
     case FP_MM_RIGHT_TC:
-      FP_CHECK(p <= 3 && k <= 32767, FP_EBOUND, "RIGHT_TC needs p <= 3 and k <= 32767");
+      FP_CHECK(f16p_ok(p, k), FP_EBOUND, "RIGHT_TC needs p <= 3 with k <= 32767, or p in {5, 7}");
       return FP_OK;
     default: return FP_OK;   // AUTO, PLAIN_F64, PLAIN_F32: every p <= 251, k <= 2^20
   }

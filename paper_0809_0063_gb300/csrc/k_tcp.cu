@@ -62,6 +62,9 @@ struct PProb {
   int tile0;
   uint32_t koffset;  // k: added to both digits before REDQ
   uint32_t off_mod_p;
+  int cmma;          // packed p = 5, 7: MMA instructions (16 inner steps each) per chunk
+  int rr;            // packed p = 5, 7: chunks between two re-reductions of R
+  uint32_t dmax;     // packed p = 5, 7: largest |digit| one chunk adds
   RedqParams P;      // REDQ_2 at q = 2^16
 };
 
@@ -159,8 +162,59 @@ __device__ __forceinline__ void final_redq(uint32_t (&R)[NW], uint32_t fix, uint
   }
 }
 
-template <bool PACKED, int CAP = FP_GROUP_MAX>
+// REDQ_2 (Algorithm 2) at q = 2^16 for p = 5, 7 with the correction done by arithmetic (p^2 > 32
+// rules out the lane table for p = 7): s = floor(w / p), u_0 = w - p s, u_1 = (floor(w / q) -
+// p floor(s / q)) mod q, mu_1 = u_1, mu_0 = (u_0 - q u_1) mod p, both shifted back by the offset
+// (om = offset mod p).  Returns mu_0 | mu_1 << 8.
+template <uint32_t PP>
+__device__ __forceinline__ uint32_t redq2_arith(uint32_t w, uint32_t om) {
+  constexpr uint32_t C = (PP - 65536u % PP) % PP;        // (-q) mod p
+  const uint32_t s = w / PP;
+  const uint32_t u0 = (w - PP * s) & 0xFFFFu;
+  const uint32_t u1 = ((w >> 16) - PP * (s >> 16)) & 0xFFFFu;
+  const uint32_t mu1 = (u1 + PP - om) % PP;
+  const uint32_t mu0 = (u0 + C * u1 + PP - om) % PP;
+  return mu0 | (mu1 << 8);
+}
+
+// Every word of R (digits offset to non-negative by `fix`) replaced by its two residues, as a
+// word with digits < p: the delayed reduction of Sec. 2.2 applied before a 16-bit digit could
+// overflow.
+template <uint32_t PP, int NW>
+__device__ __forceinline__ void rereduce_pairs(uint32_t (&R)[NW], uint32_t fix, uint32_t om) {
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    const uint32_t v = redq2_arith<PP>(R[j] + fix, om);
+    R[j] = (v & 0xFFu) | ((v >> 8) << 16);
+  }
+}
+
+// The end of a packed p = 5, 7 tile: as final_redq, with redq2_arith.
+template <uint32_t PP, int NW>
+__device__ __forceinline__ void final_redq_arith(uint32_t (&R)[NW], uint32_t fix, uint32_t om, uint8_t* dst, int c0,
+                                                 int n, bool in, bool vec) {
+#pragma unroll
+  for (int h = 0; h < NW / 16; ++h) {          // 16 words -> 32 residues -> two 16-byte stores
+    uint32_t o[8];
+#pragma unroll
+    for (int j = 0; j < 16; j += 2)
+      o[j >> 1] = redq2_arith<PP>(R[h * 16 + j] + fix, om) | (redq2_arith<PP>(R[h * 16 + j + 1] + fix, om) << 16);
+    uint8_t* d = dst + 2 * (h * 16);
+    const int c = c0 + 2 * (h * 16);
+    if (vec) {
+      reinterpret_cast<uint4*>(d)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+      reinterpret_cast<uint4*>(d)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    } else if (in) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (c + j < n) d[j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
+    }
+  }
+}
+
+template <int PK, int CAP = FP_GROUP_MAX>
 __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__ PParamsT<CAP> g, uint32_t* err) {
+  constexpr bool PACKED = PK != 0;   // 1: p <= 3 at Q = 2^10; 2: p = 5, 7 at Q = 2^9
   extern __shared__ __align__(1024) uint8_t p_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)p_smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + P_STAGES * P_STAGE_BYTES);
@@ -226,7 +280,53 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
     __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && PK == 2) {
+      // p = 5, 7: a chunk is cmma MMA instructions (16 inner steps each), so chunk boundaries
+      // fall inside a k-tile; the stage is released after the k-tile's four instructions
+      constexpr uint32_t idesc = idesc_16_bmn(0u, P_BM, P_BNW);
+      uint32_t it = 0, gc = 0;      // k tiles and chunks of this CTA so far
+      bool stop = false;
+      for (int t = blockIdx.x; t < g.total && !stop; t += gridDim.x) {
+        const PTile x = p_tile(g, t);
+        const int cmma = x.pr->cmma;
+        int inchunk = 0;
+        uint32_t dtm = tmem;
+        for (int kt = 0; kt < x.pr->ktiles && !stop; ++kt, ++it) {
+          const int s = (int)(it % P_STAGES);
+          if (!mbar_wait(&full[s], (it / P_STAGES) & 1u, abort_flag)) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint8_t* sa = smem + s * P_STAGE_BYTES;
+          const uint8_t* sb = sa + P_A_BYTES;
+          const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_mn_sw128(sb, P_B_BOX);
+          for (int kk = 0; kk < 4; ++kk) {
+            if (inchunk == 0) {
+              const int buf = (int)(gc & 1u);
+              if (gc >= 2 && !mbar_wait(&tempty[buf], ((gc - 2) >> 1) & 1u, abort_flag)) {
+                stop = true;
+                break;
+              }
+              tc_fence_after();
+              dtm = tmem + (uint32_t)(buf * 256);
+            }
+            mma_f16(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 128), idesc, inchunk == 0 ? 0u : 1u);
+            if (++inchunk == cmma) {
+              mma_commit(&tfull[gc & 1u]);
+              inchunk = 0;
+              ++gc;
+            }
+          }
+          if (stop) break;
+          mma_commit(&empty[s]);
+        }
+      }
+      if (*abort_flag) {
+        mma_commit(drainb);
+        mbar_drain(drainb, 0);
+      }
+    } else if (lane == 0) {
       constexpr uint32_t idesc = idesc_16_bmn(PACKED ? 0u : 1u, P_BM, P_BNW);
       uint32_t it = 0, gc = 0;      // k tiles and chunks of this CTA so far
       bool stop = false;
@@ -329,7 +429,71 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[buf]);
     }
-    for (int t = blockIdx.x; t < g.total && ok && PACKED; t += gridDim.x) {
+    for (int t = blockIdx.x; t < g.total && ok && PK == 2; t += gridDim.x) {
+      // p = 5, 7: chunk words v = d0 + 2^9 d1 with |d0|, |d1| <= dmax < 256 (Q = 2^9); every
+      // chunk is moved into R = D0 + 2^16 D1 as below, and every rr chunks R's digits are
+      // replaced by their residues before a 16-bit digit could overflow
+      const PTile x = p_tile(g, t);
+      const PProb& pr = *x.pr;
+      uint32_t R[P_CW];
+#pragma unroll
+      for (int j = 0; j < P_CW; ++j) R[j] = 0;
+      const uint32_t p = pr.P.p, dmax = pr.dmax, rr = (uint32_t)pr.rr;
+      uint32_t cr = 0;     // chunks added since R last held residues
+      for (int c = 0; c < pr.nchunks; ++c, ++gc) {
+        const int buf = (int)(gc & 1u);
+        uint32_t got = 1;
+        if (lane == 0) got = mbar_wait(&tfull[buf], (gc >> 1) & 1u, abort_flag) ? 1u : 0u;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // 1.5 2^23 added: the float's bits are 0x4B400000 + v exactly; d1 = round(v / 2^9)
+        const uint32_t base = tmem + lane_base + (uint32_t)(buf * 256 + part * P_CW);
+        uint32_t va[16], vb[16];
+        tmem_ld16_nowait(base, va);
+        tmem_wait();
+#pragma unroll
+        for (int blk = 0; blk < P_CW / 16; ++blk) {
+          if (blk + 1 < P_CW / 16) {
+            if (blk & 1) tmem_ld16_nowait(base + (uint32_t)((blk + 1) * 16), va);
+            else tmem_ld16_nowait(base + (uint32_t)((blk + 1) * 16), vb);
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const uint32_t raw = (blk & 1) ? vb[j] : va[j];
+            const int32_t y = __float_as_int(__uint_as_float(raw) + 12582912.0f);
+            const int32_t d1 = (y - (0x4B400000 - 256)) >> 9;
+            R[blk * 16 + j] += (uint32_t)y + (uint32_t)(d1 * (65536 - 512));
+          }
+          tmem_wait();
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        if (++cr == rr && c + 1 < pr.nchunks) {
+          const uint32_t off = dmax * cr;
+          const uint32_t fix = off * 65537u - cr * 0x4B400000u;
+          if (p == 7) rereduce_pairs<7, P_CW>(R, fix, off % 7u);
+          else rereduce_pairs<5, P_CW>(R, fix, off % 5u);
+          cr = 0;
+        }
+      }
+      if (!ok) break;
+      const uint32_t off = dmax * cr;
+      const uint32_t fix = off * 65537u - cr * 0x4B400000u;
+      const int row = x.m0 + q * 32 + lane;
+      const int c0 = 2 * (x.w0 + part * P_CW);
+      const int n = pr.n;
+      const bool in = row < pr.m && c0 < n;
+      uint8_t* dst = pr.C + (size_t)row * pr.ldc + c0;
+      const bool vec = in && c0 + 2 * P_CW <= n && ((((uintptr_t)dst) & 15u) == 0);
+      if (p == 7) final_redq_arith<7, P_CW>(R, fix, off % 7u, dst, c0, n, in, vec);
+      else final_redq_arith<5, P_CW>(R, fix, off % 5u, dst, c0, n, in, vec);
+    }
+    for (int t = blockIdx.x; t < g.total && ok && PK == 1; t += gridDim.x) {
       const PTile x = p_tile(g, t);
       const PProb& pr = *x.pr;
       uint32_t R[P_CW];   // unsigned: wraps modulo 2^32 (the conversion offsets cancel at the end)
@@ -439,9 +603,12 @@ __global__ void __launch_bounds__(256) k_t16_convert_a(const uint8_t* __restrict
       for (int q = 0; q < 4; ++q) {
         bad |= __vcmpgeu4(w[q], 0x01010101u * p);
         const uint32_t x = w[q];
-        if (PACKED) {
+        if (PACKED && p <= 3) {
           o[2 * q] = h16_centred(x & 0xffu) | (h16_centred((x >> 8) & 0xffu) << 16);
           o[2 * q + 1] = h16_centred((x >> 16) & 0xffu) | (h16_centred(x >> 24) << 16);
+        } else if (PACKED) {   // p = 5, 7: centred residues in [-(p-1)/2, (p-1)/2]
+          o[2 * q] = h16_centred_p(x & 0xffu, p) | (h16_centred_p((x >> 8) & 0xffu, p) << 16);
+          o[2 * q + 1] = h16_centred_p((x >> 16) & 0xffu, p) | (h16_centred_p(x >> 24, p) << 16);
         } else {
           o[2 * q] = bf16_of(x & 0xffu) | (bf16_of((x >> 8) & 0xffu) << 16);
           o[2 * q + 1] = bf16_of((x >> 16) & 0xffu) | (bf16_of(x >> 24) << 16);
@@ -455,7 +622,8 @@ __global__ void __launch_bounds__(256) k_t16_convert_a(const uint8_t* __restrict
 }
 
 // B16 (k x ldw 16-bit, zero past nw) row by row from B (k x n), no transpose.  PACKED: word
-// j = fp16 of c(B[l][2j]) + 2^10 c(B[l][2j+1]) (the second residue 0 past column n), one
+// j = fp16 of c(B[l][2j]) + Q c(B[l][2j+1]) (Q = 2^10 for p <= 3, 2^9 for p = 5, 7; the second
+// residue 0 past column n), one
 // thread per 16 bytes of B (8 words); plain: bf16 of B[l][j], one thread per 8 bytes of B
 // (8 elements).  Residues >= p set ERR_RANGE.
 template <bool PACKED>
@@ -493,8 +661,11 @@ __global__ void __launch_bounds__(256) k_t16_convert_b(const uint8_t* __restrict
       for (int q = 0; q < 4; ++q) {
         bad |= __vcmpgeu4(w[q], pp);
         const uint32_t x = w[q];
-        if (PACKED) {
+        if (PACKED && p <= 3) {
           o[q] = h16_pair_word(x & 0xffu, (x >> 8) & 0xffu) | (h16_pair_word((x >> 16) & 0xffu, x >> 24) << 16);
+        } else if (PACKED) {   // p = 5, 7: c(b0) + 2^9 c(b1)
+          o[q] = h16_pair_word_p(x & 0xffu, (x >> 8) & 0xffu, p, 512.0f) |
+                 (h16_pair_word_p((x >> 16) & 0xffu, x >> 24, p, 512.0f) << 16);
         } else {
           const uint32_t y = w[q >> 1] >> (16 * (q & 1));
           o[q] = bf16_of(y & 0xffu) | (bf16_of((y >> 8) & 0xffu) << 16);
@@ -507,14 +678,40 @@ __global__ void __launch_bounds__(256) k_t16_convert_b(const uint8_t* __restrict
 
 // ---------------------------------------------------------------- host side
 
-bool f16p_ok(uint32_t p, int k) { return p <= 3 && k <= 32767; }
+// Packed fp16 words: p <= 3 at Q = 2^10 in chunks of 448 inner steps (k <= 32767 keeps R's
+// 16-bit digits from overflowing without re-reduction); p = 5, 7 at Q = 2^9, where centred
+// residues |c| <= (p-1)/2 keep |c0| + 2^9 |c1| <= 2048 (exact fp16), in chunks of 32 (p = 5) or
+// 16 (p = 7) inner steps so that every chunk digit stays below 2^8 in magnitude.
+bool f16p_ok(uint32_t p, int k) { return (p <= 3 && k <= 32767) || p == 5 || p == 7; }
+
+// Chunk parameters of the p = 5, 7 packed form: MMA instructions per chunk, the largest |digit|
+// a chunk adds ((p-1)/2)^2 per inner step, and the chunks R takes before its 16-bit digits could
+// overflow ((p-1) + 2 dmax rr < 2^16).
+static void pk2_params(uint32_t p, int* cmma, uint32_t* dmax, int* rr) {
+  const uint32_t h = (p - 1) / 2;
+  *cmma = p == 5 ? 2 : 1;
+  *dmax = h * h * 16u * (uint32_t)*cmma;
+  *rr = (int)((65535u - (p - 1)) / (2u * *dmax));
+}
 
 // Convert the problems' operands into context scratch and launch the grouped kernel(s); the
 // caller holds the context lock.  Every problem passed fp_matmul's checks and the variant's
 // exactness rule (packed: f16p_ok; plain: k (p-1)^2 < 2^24).
+static fp_status launch_t16_mode(fp_ctx ctx, const std::vector<const fp_mm_problem*>& v, int pk, cudaStream_t st);
+
 static fp_status launch_t16_locked(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, bool packed,
                                    cudaStream_t st) {
-  std::vector<const fp_mm_problem*> v(pr, pr + count);
+  // packed problems run in two kernels: p <= 3 (mode 1) and p = 5, 7 (mode 2)
+  std::vector<const fp_mm_problem*> v1, v2;
+  for (size_t i = 0; i < count; ++i) (packed && pr[i]->p > 3 ? v2 : v1).push_back(pr[i]);
+  fp_status s = v1.empty() ? FP_OK : launch_t16_mode(ctx, v1, packed ? 1 : 0, st);
+  if (s == FP_OK && !v2.empty()) s = launch_t16_mode(ctx, v2, 2, st);
+  return s;
+}
+
+static fp_status launch_t16_mode(fp_ctx ctx, const std::vector<const fp_mm_problem*>& v0, int pk, cudaStream_t st) {
+  const bool packed = pk != 0;
+  std::vector<const fp_mm_problem*> v(v0);
   std::stable_sort(v.begin(), v.end(), [](const fp_mm_problem* a, const fp_mm_problem* b) { return a->k > b->k; });
   auto words = [packed](int n) { return packed ? (n + 1) / 2 : n; };
   for (size_t base = 0; base < v.size(); base += FP_GROUP_MAX) {
@@ -564,6 +761,10 @@ static fp_status launch_t16_locked(fp_ctx ctx, const fp_mm_problem* const* pr, s
       g.nw = nw;
       g.ktiles = kp / P_BK;
       g.nchunks = packed ? (g.ktiles + P_CHUNK_KT - 1) / P_CHUNK_KT : 1;
+      if (pk == 2) {
+        pk2_params(x.p, &g.cmma, &g.dmax, &g.rr);
+        g.nchunks = g.ktiles * 4 / g.cmma;
+      }
       g.tn = (nw + P_BNW - 1) / P_BNW;
       g.tile0 = tile;
       g.koffset = (uint32_t)x.k;
@@ -574,12 +775,15 @@ static fp_status launch_t16_locked(fp_ctx ctx, const fp_mm_problem* const* pr, s
     hp.nprob = cnt;
     hp.total = tile;
     const int grid = std::min(tile, ctx->num_sms);
-    if (packed) {
-      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
-      FP_LAUNCH(ctx, "k_mm_t16_packed", st, k_mm_t16<true><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err));
+    if (pk == 2) {
+      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
+      FP_LAUNCH(ctx, "k_mm_t16_packed_p57", st, k_mm_t16<2><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err));
+    } else if (packed) {
+      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
+      FP_LAUNCH(ctx, "k_mm_t16_packed", st, k_mm_t16<1><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err));
     } else {
-      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
-      FP_LAUNCH(ctx, "k_mm_t16_plain", st, k_mm_t16<false><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err));
+      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
+      FP_LAUNCH(ctx, "k_mm_t16_plain", st, k_mm_t16<0><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err));
     }
     FP_CUDA(cudaGetLastError());
   }
@@ -685,7 +889,7 @@ fp_status launch_mm_t16_plain_batch(fp_ctx ctx, const fp_mm_problem* const* pr, 
   FP_LAUNCH(ctx, "k_t16_convert_jobs", st,
             k_t16_convert_jobs<<<cgrid, 256, jsm, st>>>((const T16Job*)scratch, (uint32_t)jobs.size(), rows, ctx->d_err));
   FP_CUDA(cudaGetLastError());
-  FP_CUDA(cudaFuncSetAttribute(k_mm_t16<false, P_BATCH_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
+  FP_CUDA(cudaFuncSetAttribute(k_mm_t16<0, P_BATCH_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
   for (size_t base = 0; base < v.size(); base += P_BATCH_CAP) {
     const int cnt = (int)std::min<size_t>(P_BATCH_CAP, v.size() - base);
     PParamsT<P_BATCH_CAP> hp;
@@ -717,7 +921,7 @@ fp_status launch_mm_t16_plain_batch(fp_ctx ctx, const fp_mm_problem* const* pr, 
     hp.nprob = cnt;
     hp.total = tile;
     const int grid = std::min(tile, ctx->num_sms);
-    FP_LAUNCH(ctx, "k_mm_t16_plain", st, (k_mm_t16<false, P_BATCH_CAP><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err)));
+    FP_LAUNCH(ctx, "k_mm_t16_plain", st, (k_mm_t16<0, P_BATCH_CAP><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err)));
     FP_CUDA(cudaGetLastError());
   }
   return FP_OK;

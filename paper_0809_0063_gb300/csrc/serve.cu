@@ -84,6 +84,7 @@ struct fp_server_s {
     uint64_t ticket;
     double t_submit;
     size_t in_a, in_b, out;   // byte sizes
+    bool tc = false;          // matmul on the e4m3 tensor-core kernel (rows at 16-byte strides)
   };
   struct Batch {
     std::vector<Req> reqs;
@@ -142,14 +143,14 @@ struct fp_server_s {
       const fp_request& r = q.r;
       size_t items_add = 0;
       if (r.kind == 1) items_add = 1;
-      if (r.kind == 3) {
+      if (r.kind == 3 && !q.tc) {
         const bool pk = r.p <= 3 && r.c >= 448 && r.c <= 32767;
         const size_t nw = pk ? (r.b + 1) / 2 : r.b;
         items_add = ((r.a + 63) / 64) * ((nw + 63) / 64);
       }
       const size_t n_in = in_bytes + al16(q.in_a) + al16(q.in_b);
       const size_t n_pm = npm + (r.kind == 0), n_seg = nsegs + (r.kind == 2);
-      const size_t n_mm = nmm + (r.kind == 1 || r.kind == 3), n_it = nitems + items_add;
+      const size_t n_mm = nmm + (r.kind == 1 || (r.kind == 3 && !q.tc)), n_it = nitems + items_add;
       const size_t block = al256(al256(al256(al256(n_in) + n_pm * sizeof(PmDesc)) + n_seg * sizeof(GfSegH)) +
                                  (n_mm ? batch_plan_bytes(n_mm, n_it) : 0)) +
                            out_bytes + al16(q.out);
@@ -187,7 +188,7 @@ struct fp_server_s {
     // fill instances with offsets relative to 0, fix up after placing
     for (size_t i = 0; i < take.size(); ++i) {
       const fp_request& r = take[i].r;
-      if (r.kind == 1 || r.kind == 3) {
+      if (r.kind == 1 || (r.kind == 3 && !take[i].tc)) {
         fp_instance x{};
         x.kind = r.kind == 1 ? 1u : 0u;
         x.p = r.p;
@@ -232,9 +233,21 @@ struct fp_server_s {
     uint8_t* dbase = arena + blk;
     uint8_t* hin = h_in[s];
     // gather inputs
+    std::vector<fp_mm_problem> tcp;   // tensor-core matmuls: operand rows at 16-byte strides
     for (size_t i = 0; i < take.size(); ++i) {
-      memcpy(hin + ia[i], take[i].r.host_a, take[i].in_a);
-      if (take[i].in_b) memcpy(hin + ib[i], take[i].r.host_b, take[i].in_b);
+      const fp_request& r = take[i].r;
+      if (take[i].tc) {
+        const size_t lda = al16(r.c), ldb = al16(r.b);
+        const uint8_t* a = (const uint8_t*)r.host_a;
+        const uint8_t* b = (const uint8_t*)r.host_b;
+        for (uint32_t row = 0; row < r.a; ++row) memcpy(hin + ia[i] + row * lda, a + (size_t)row * r.c, r.c);
+        for (uint32_t row = 0; row < r.c; ++row) memcpy(hin + ib[i] + row * ldb, b + (size_t)row * r.b, r.b);
+        tcp.push_back(fp_mm_problem{r.p, (int)r.a, (int)r.b, (int)r.c, nullptr, (int)lda, nullptr, (int)ldb, nullptr,
+                                    (int)r.b});
+        continue;
+      }
+      memcpy(hin + ia[i], r.host_a, take[i].in_a);
+      if (take[i].in_b) memcpy(hin + ib[i], r.host_b, take[i].in_b);
     }
     // polymul descriptors
     PmDesc* pd = reinterpret_cast<PmDesc*>(hin + pm_off);
@@ -269,7 +282,7 @@ struct fp_server_s {
       size_t j = 0;
       for (size_t i = 0; i < take.size(); ++i) {
         const fp_request& r = take[i].r;
-        if (r.kind != 1 && r.kind != 3) continue;
+        if (r.kind != 1 && (r.kind != 3 || take[i].tc)) continue;
         mm[j].A = dbase + ia[i];
         mm[j].B = dbase + ib[i];
         mm[j].C = dbase + out_region + oo[i];
@@ -298,6 +311,22 @@ struct fp_server_s {
     if (ok && !mm.empty()) {
       ok = batch_launch_plan(ctx, insts.size(), items.size(), dbase + plan_off, st) == FP_OK;
       launches++;
+    }
+    if (ok && !tcp.empty()) {
+      // the e4m3 kernel's grouped launches (it range-checks its operands itself; parameters only,
+      // no context scratch, so the serving thread may call it)
+      std::vector<const fp_mm_problem*> ptr;
+      size_t j = 0;
+      for (size_t i = 0; i < take.size(); ++i) {
+        if (!take[i].tc) continue;
+        tcp[j].A = dbase + ia[i];
+        tcp[j].B = dbase + ib[i];
+        tcp[j].C = dbase + out_region + oo[i];
+        ptr.push_back(&tcp[j]);
+        ++j;
+      }
+      ok = launch_mm_f8_grouped_locked(ctx, ptr.data(), ptr.size(), st, false) == FP_OK;
+      launches += (ptr.size() + FP_GROUP_MAX - 1) / FP_GROUP_MAX;
     }
     if (ok) ok = cudaMemcpyAsync(h_out[s], dbase + out_region, total - out_region, cudaMemcpyDeviceToHost, st) == cudaSuccess;
     Batch b;
@@ -443,6 +472,11 @@ extern "C" fp_status fp_server_submit(fp_server s, const fp_request* r, uint64_t
       FP_CHECK(r->a >= 1 && r->b >= 1 && r->c >= 1 && r->host_b, FP_EINVAL, "matmul request: sizes");
       FP_CHECK((uint64_t)r->c * (r->p - 1) * (r->p - 1) < (1ull << 32), FP_EBOUND, "matmul request: k (p-1)^2");
       q.in_a = (size_t)r->a * r->c; q.in_b = (size_t)r->c * r->b; q.out = (size_t)r->a * r->b;
+      // large products with exact e4m3 residues go to the tensor cores, rows padded to 16 bytes
+      q.tc = r->p <= 17 && r->a >= 64 && r->b >= 64 && (uint64_t)r->c * (r->p - 1) * (r->p - 1) < (1ull << 24) &&
+             (uint64_t)r->a * r->b * r->c >= (1ull << 21) && r->a <= (1u << 20) && r->b <= (1u << 20) &&
+             r->c <= (1u << 20);
+      if (q.tc) { q.in_a = (size_t)r->a * al16(r->c); q.in_b = (size_t)r->c * al16(r->b); }
       break;
     default:
       FP_CHECK(false, FP_EINVAL, "request kind %u", r->kind);

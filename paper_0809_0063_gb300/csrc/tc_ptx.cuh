@@ -15,6 +15,17 @@ namespace fpd {
 // fp16 bits of a centred residue of p <= 3 ({0,1,2} -> {0,1,-1}) and of a packed pair
 // c(v0) + 2^10 c(v1) (|value| <= 1025 < 2^11: exact in fp16).
 __device__ __forceinline__ uint32_t h16_centred(uint32_t v) { return v == 0 ? 0u : (v == 1 ? 0x3C00u : 0xBC00u); }
+// fp16 bits of the centred residue of v mod p (v - p when 2v > p), exact for p <= 2047.
+__device__ __forceinline__ uint32_t h16_centred_p(uint32_t v, uint32_t p) {
+  const float c = 2 * v > p ? (float)v - (float)p : (float)v;
+  return __half_as_ushort(__float2half_rn(c));
+}
+// fp16 bits of c(v0) + Q c(v1) for centred residues; exact while |c0| + Q |c1| <= 2048.
+__device__ __forceinline__ uint32_t h16_pair_word_p(uint32_t v0, uint32_t v1, uint32_t p, float Q) {
+  const float c0 = 2 * v0 > p ? (float)v0 - (float)p : (float)v0;
+  const float c1 = 2 * v1 > p ? (float)v1 - (float)p : (float)v1;
+  return __half_as_ushort(__float2half_rn(fmaf(Q, c1, c0)));
+}
 __device__ __forceinline__ uint32_t h16_pair_word(uint32_t v0, uint32_t v1) {
   const float c0 = v0 == 2 ? -1.0f : (float)v0, c1 = v1 == 2 ? -1.0f : (float)v1;
   return __half_as_ushort(__float2half_rn(fmaf(1024.0f, c1, c0)));

@@ -214,7 +214,7 @@ def test_grouped_16bit(env, algo):
     fp, torch, dev, ctx = env
     if algo == "RIGHT_TC":
         shapes = [(3, 200, 333, 517), (2, 64, 129, 4100), (3, 130, 71, 1000), (3, 1, 1, 1), (2, 257, 600, 448),
-                  (3, 100, 513, 449)]
+                  (3, 100, 513, 449), (7, 130, 257, 4100), (5, 65, 63, 200)]
     else:
         shapes = [(7, 200, 333, 517), (251, 64, 129, 200), (31, 130, 71, 1000), (3, 1, 1, 1), (13, 257, 600, 4096)]
     probs = [Prob(fp, torch, dev, 60 + i, p, m, n, k, align=(i % 2 == 0)) for i, (p, m, n, k) in enumerate(shapes)]
@@ -225,17 +225,17 @@ def test_grouped_16bit(env, algo):
     fp.fp_ctx_status(ctx)
     launches, _ = fp.fp_ctx_profile_read(ctx, name)
     fp.fp_ctx_profile(ctx, 0)
-    assert launches == 1
+    assert launches == (2 if algo == "RIGHT_TC" else 1)     # p <= 3 and p = 5, 7 run in one launch each
     for q in probs:
         q.check()
 
 
 def test_grouped_bound_refused_before_enqueue(env):
-    """A group whose forced algorithm is inexact for one problem (RIGHT_TC with p = 5) is
+    """A group whose forced algorithm is inexact for one problem (RIGHT_TC with p = 11) is
     refused with FP_EBOUND and nothing runs, not even the problems that would fit."""
     fp, torch, dev, ctx = env
     fine = Prob(fp, torch, dev, 81, 3, 64, 64, 64)
-    bad = Prob(fp, torch, dev, 82, 5, 64, 64, 64)
+    bad = Prob(fp, torch, dev, 82, 11, 64, 64, 64)
     l0 = fp.fp_ctx_launches(ctx)
     with pytest.raises(fp.FpError) as ei:
         fp.fp_matmul_grouped(ctx, [fine.desc, bad.desc], fp.FP_MM_RIGHT_TC)

@@ -42,7 +42,7 @@ def supported(fp, p, k, algo):
         return False
     if algo == "PLAIN_TC" and k * (p - 1) ** 2 >= 2 ** 24:
         return False
-    if algo == "RIGHT_TC" and p > 3:
+    if algo == "RIGHT_TC" and (p not in (2, 3, 5, 7) or (p <= 3 and k > 32767)):
         return False
     if algo == "PLAIN_F8" and (p > 17 or k * (p - 1) ** 2 >= 2 ** 24):
         return False
@@ -336,3 +336,29 @@ def test_matmul_cmm_bound_and_range(env):
     with pytest.raises(fp.FpError) as ei:
         fp.fp_ctx_status(ctx)
     assert ei.value.status == fp.FP_EINVAL
+
+
+@pytest.mark.parametrize("p,k", [(7, 16), (7, 3632), (7, 3648), (7, 4100), (5, 8160), (5, 8200)])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_right_tc_p57_largest_digits(env, p, k, sign):
+    """Packed fp16 words for p = 5, 7 (Q = 2^9, chunks of 32 / 16 inner steps): entries whose
+    centred value is +-(p-1)/2 everywhere make every chunk digit reach its bound dmax and every
+    digit of R grow by dmax per chunk; k around the re-reduction period (227 chunks for p = 7,
+    255 for p = 5) crosses it."""
+    fp, torch, dev, ctx = env
+    h = (p - 1) // 2
+    m, n = 130, 257
+    a = np.full((m, k), h, np.uint8)
+    b = np.full((k, n), h if sign > 0 else p - h, np.uint8)
+    a[:, 1::5] = p - h if sign > 0 else h          # a mix of signs that keeps the sums large
+    got = run(fp, torch, dev, ctx, p, a, b, "RIGHT_TC")
+    assert np.array_equal(got, field.matmul_mod(a, b, p))
+
+
+@pytest.mark.parametrize("p", [5, 7])
+def test_right_tc_p57_random_ragged(env, p):
+    fp, torch, dev, ctx = env
+    for (m, n, k) in ((1, 1, 1), (200, 333, 517), (129, 513, 4100), (64, 1000, 17)):
+        a, b = workloads.matmul_inputs(p * 31 + m + k, p, m, k, n)
+        got = run(fp, torch, dev, ctx, p, a, b, "RIGHT_TC")
+        assert np.array_equal(got, field.matmul_mod(a, b, p)), (m, n, k)
