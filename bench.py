@@ -1000,7 +1000,7 @@ def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0, emit=True):
     fp.fp_ctx_profile(ctx, 0)
     fp.fp_ctx_status(ctx)
     kern = {}
-    for nm in ("k_polymul_var", "k_gf_mul_seg", "k_batch"):
+    for nm in ("k_polymul_var", "k_gf_mul_seg", "k_batch", "k_mm_f8g"):
         c, ms = fp.fp_ctx_profile_read(ctx, nm)
         if c:
             kern[nm] = {"launches": c, "ms": ms}
@@ -1044,19 +1044,27 @@ def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0, emit=True):
     base_rps = n_base / base_wall
     cap_rps = len(reqs) / wall_c
     pct = lambda a, q: float(np.percentile(a[a >= 0], q))
-    # roofline of the kernel with the most device time in the capacity run.  k_batch holds the
-    # matmul and dot requests (legacy mma.sync bf16 tiles); k_polymul_var the blocked-FQT
-    # products (integer issue); k_gf_mul_seg the field products (integer ALU)
-    mm_macs = sum(req_macs(c, sz, r.gf_k) for r, (c, sz, A, B, out) in zip(reqs, data) if c in (1, 3))
+    # roofline of the kernel with the most device time in the capacity run.  The server's rule:
+    # matmul requests with p <= 17, m, n >= 64, k (p-1)^2 < 2^24 and m n k >= 2^21 run on the e4m3
+    # kernel k_mm_f8g; other matmuls and the dots on k_batch (legacy mma.sync bf16 tiles);
+    # k_polymul_var the blocked-FQT products (integer issue); k_gf_mul_seg the field products
+    def tc_req(r, c, sz):
+        return c == 3 and r.p <= 17 and sz[0] >= 64 and sz[1] >= 64 and sz[2] * (r.p - 1) ** 2 < (1 << 24) \
+            and sz[0] * sz[1] * sz[2] >= (1 << 21)
+    f8_macs = sum(req_macs(c, sz, r.gf_k) for r, (c, sz, A, B, out) in zip(reqs, data) if tc_req(r, c, sz))
+    mm_macs = sum(req_macs(c, sz, r.gf_k) for r, (c, sz, A, B, out) in zip(reqs, data)
+                  if c in (1, 3) and not tc_req(r, c, sz))
     roof = None
     if kern:
         dom = max(kern, key=lambda nm: kern[nm]["ms"])
-        if dom == "k_batch":
-            ach = 2.0 * mm_macs / (kern[dom]["ms"] / 1e3) / 1e12
-            roof = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": 603.2, "unit": "TFLOP/s",
-                    "frac": ach / 603.2, "traffic": None,
-                    "peak_source": "mma.sync bf16 measured by the pipe probe",
-                    "note": "achieved = 2 x the matmul and dot requests' F_p MACs / k_batch device time"}
+        hbm_, bf16_, _, psrc_ = peaks()
+        if dom in ("k_batch", "k_mm_f8g"):
+            mac, pk_, src_ = (mm_macs, 603.2, "mma.sync bf16 measured by the pipe probe") if dom == "k_batch" else \
+                (f8_macs, 2.0 * bf16_, f"fp8 = measured bf16 x 2 ({psrc_})")
+            ach = 2.0 * mac / (kern[dom]["ms"] / 1e3) / 1e12
+            roof = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": pk_, "unit": "TFLOP/s",
+                    "frac": ach / pk_, "traffic": None, "peak_source": src_,
+                    "note": "achieved = 2 x the F_p MACs of the requests this kernel ran / its device time"}
         else:
             pm = sum(req_macs(c, sz, r.gf_k) for r, (c, sz, A, B, out) in zip(reqs, data) if c == 0)
             roof = {"bound": "alu", "kernel": dom, "achieved": pm / (kern[dom]["ms"] / 1e3) / 1e12,

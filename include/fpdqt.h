@@ -7,7 +7,8 @@
  * multiplying and accumulating those words with delayed reduction (Sec. 2.2-2.3), and
  * recovering the residues with REDQ simultaneous reduction (Algorithm 2, Sec. 3) in which the
  * one division is an FP multiply by a rounded inverse (Algorithm FDIV, Table "fdiv", Sec. 4).
- * Here q = Q = 2^b always (the restriction at the end of Sec. 3).
+ * Here q = Q = 2^b (the restriction at the end of Sec. 3), except that fp_dqt_pack and
+ * fp_dqt_unpack_redq also take q = p 2^b (the alternative the conclusion proposes).
  *
  * Conventions shared by every call
  *  - All array pointers are DEVICE pointers owned by the caller unless stated otherwise; the
@@ -400,8 +401,11 @@ enum { FP_GF_INDEX = 0, FP_GF_LOG = 1 };
  * of the same width, written in the same form.  The conversion to words is one table lookup
  * from either form to the element's evaluation at the dot product's own q = 2^b_dot; the word products
  * accumulate for `chunk` terms (every digit below q, the word below 2^64) before each REDQ and
- * L/H lookup, and the partial results are added in the field.  n = 0 writes zero.  Codes
- * >= p^k set FP_EINVAL on the context (read by fp_ctx_status) and count as zero.  n < 2^40.
+ * L/H lookup, and the partial results are added in the field.  GF(2^8) in index form with
+ * 16-byte aligned arrays takes the word-level multiply of fp_gf_mul_batched for every term
+ * (p | q: the compression values are the digits) and adds the products by XOR.  n = 0 writes
+ * zero.  Codes >= p^k set FP_EINVAL on the context (read by fp_ctx_status) and count as zero.
+ * n < 2^40.
  * Uses context scratch for per-block partial sums. */
 fp_status fp_gf_dot(fp_ctx ctx, fp_gf gf, const void* a, const void* b, size_t n, void* out,
                     int form, void* stream);

@@ -18,8 +18,9 @@
 // q = 2^w.  The last REDQ of R gives C.  The sum of the pieces' digits is the digit of the
 // unsplit product, so C is the same; the pieces add the modular reductions the paper mentions.
 //
-// Operands are read as bytes and packed on the fly (a few integer-valued FMAs per loaded word):
-// the DMMA issue rate, not the loads, bounds this kernel.
+// The packed words are formed once by integer shifts in a packing pass (B always, A for full
+// compression) and read by the DMMA loop as doubles: FP64 conversions or FMAs in the loop
+// would take the same slow FP64 pipe as the DMMA instructions themselves.
 #include <cmath>
 
 #include "fpdqt_internal.cuh"
@@ -31,15 +32,35 @@ struct FsParams {
   int mr, nw;            // word rows ceil(m / dq1), word columns ceil(n / dt1)
   uint32_t dq1, dt1, s;  // rows per A word, columns per B word, Theta = Q^s
   uint32_t b, ndig;      // Q = 2^b, digits per product word
-  double Q, Th;          // Q and Theta as doubles (exact powers of two)
   int piece_steps;       // k-steps of 4 per piece (split form only)
   uint32_t w;            // field width of R (split form only)
   int refold;            // pieces added into R between re-reductions (split form only)
 };
 
+// Packed rows of A for full compression: CA[r][l] = sum_{i < dq1} A[r dq1 + i][l] Q^i (rows past
+// m taken as zero), consecutive threads on consecutive l.  Residues >= p set ERR_RANGE.
+__global__ void k_pack_rows(const uint8_t* __restrict__ A, int lda, double* __restrict__ CA, int m, int k, int mr,
+                            uint32_t dq1, uint32_t b, uint32_t p, uint32_t* err) {
+  const uint64_t total = (uint64_t)mr * k;
+  uint32_t bad = 0;
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / k), l = (int)(idx % k);
+    uint64_t w = 0;
+    for (int i = (int)dq1 - 1; i >= 0; --i) {
+      const int row = r * (int)dq1 + i;
+      const uint32_t v = row < m ? A[(size_t)row * lda + l] : 0u;
+      bad |= v >= p;
+      w = (w << b) | v;
+    }
+    CA[idx] = __ull2double_rn(w);     // exact: below 2^52
+  }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
 template <int TM, int TN, bool SPLIT>
 __global__ void __launch_bounds__(128) k_mm_fullsplit(const uint8_t* __restrict__ A, int lda,
-                                                      const uint8_t* __restrict__ B, int ldb,
+                                                      const double* __restrict__ CA, const double* __restrict__ CB,
                                                       uint8_t* __restrict__ C, int ldc, FsParams F,
                                                       RedqParams P, RedqParams Pw, uint32_t* err) {
   __shared__ uint8_t ptab[1024];
@@ -105,26 +126,18 @@ __global__ void __launch_bounds__(128) k_mm_fullsplit(const uint8_t* __restrict_
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
       const int wr = r0 + 8 * i + g;
-      double x = 0.0;
-      for (int i2 = (int)F.dq1 - 1; i2 >= 0; --i2) {   // Horner: row wr dq1 + i2 at Q^i2
-        const int row = wr * (int)F.dq1 + i2;
-        const uint32_t v = (kin && row < F.m) ? A[(size_t)row * lda + kk] : 0u;
+      if (CA) {                                          // packed rows (full compression)
+        a[i] = (kin && wr < F.mr) ? CA[(size_t)wr * F.k + kk] : 0.0;
+      } else {                                           // one row per word (right compression)
+        const uint32_t v = (kin && wr < F.m) ? A[(size_t)wr * lda + kk] : 0u;
         bad |= v >= p;
-        x = fma(x, F.Q, (double)v);
+        a[i] = (double)v;
       }
-      a[i] = x;
     }
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int wc = c0 + 8 * j + g;
-      double x = 0.0;
-      for (int j2 = (int)F.dt1 - 1; j2 >= 0; --j2) {   // column wc dt1 + j2 at Theta^j2
-        const int col = wc * (int)F.dt1 + j2;
-        const uint32_t v = (kin && col < F.n) ? B[(size_t)kk * ldb + col] : 0u;
-        bad |= v >= p;
-        x = fma(x, F.Th, (double)v);
-      }
-      bw[j] = x;
+      bw[j] = (kin && wc < F.nw) ? CB[(size_t)kk * F.nw + wc] : 0.0;
     }
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -288,9 +301,23 @@ static fp_status launch_fs(fp_ctx ctx, uint32_t p, int m, int n, int k, const ui
   F.ndig = F.s * (dt1 - 1) + dq1;
   F.mr = (m + (int)dq1 - 1) / (int)dq1;
   F.nw = (n + (int)dt1 - 1) / (int)dt1;
-  F.Q = std::ldexp(1.0, (int)b);
-  F.Th = std::ldexp(1.0, (int)(b * F.s));
   const bool split = (uint64_t)piece < (uint64_t)k;
+  // packed operands in context scratch: B's words (dt1 columns at Theta = 2^(s b)) always, A's
+  // words (dq1 rows at Q) for full compression
+  const size_t cb_bytes = ((size_t)k * F.nw * sizeof(double) + 255) & ~(size_t)255;
+  const size_t ca_bytes = dq1 > 1 ? (size_t)F.mr * k * sizeof(double) : 0;
+  fp_status st_s = ensure_scratch(ctx, cb_bytes + ca_bytes, 0, st);
+  if (st_s != FP_OK) return st_s;
+  double* CB = (double*)ctx->scratch;
+  double* CA = dq1 > 1 ? (double*)((uint8_t*)ctx->scratch + cb_bytes) : nullptr;
+  st_s = launch_pack_cb(ctx, p, k, n, B, ldb, b * F.s, dt1, FP_WORD_F64, CB, st);
+  if (st_s != FP_OK) return st_s;
+  if (CA) {
+    const uint64_t total = (uint64_t)F.mr * k;
+    const int pg = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->num_sms * 16);
+    FP_LAUNCH(ctx, "k_pack_rows", st, k_pack_rows<<<pg, 256, 0, st>>>(A, lda, CA, m, k, F.mr, dq1, b, p, ctx->d_err));
+    FP_CUDA(cudaGetLastError());
+  }
   RedqParams P = make_redq(p, b, F.ndig);
   RedqParams Pw = P;
   if (split) {
@@ -309,11 +336,11 @@ static fp_status launch_fs(fp_ctx ctx, uint32_t p, int m, int n, int k, const ui
   FP_CHECK(grid.y <= 65535u, FP_EINVAL, "matrix too tall for the FP64 word grid");
   const char* nm = split ? "k_mm_fullsplit_split" : "k_mm_fullsplit";
   if (big) {
-    if (split) FP_LAUNCH(ctx, nm, st, k_mm_fullsplit<4, 4, true><<<grid, 128, 0, st>>>(A, lda, B, ldb, C, ldc, F, P, Pw, ctx->d_err));
-    else FP_LAUNCH(ctx, nm, st, k_mm_fullsplit<4, 4, false><<<grid, 128, 0, st>>>(A, lda, B, ldb, C, ldc, F, P, Pw, ctx->d_err));
+    if (split) FP_LAUNCH(ctx, nm, st, k_mm_fullsplit<4, 4, true><<<grid, 128, 0, st>>>(A, lda, CA, CB, C, ldc, F, P, Pw, ctx->d_err));
+    else FP_LAUNCH(ctx, nm, st, k_mm_fullsplit<4, 4, false><<<grid, 128, 0, st>>>(A, lda, CA, CB, C, ldc, F, P, Pw, ctx->d_err));
   } else {
-    if (split) FP_LAUNCH(ctx, nm, st, k_mm_fullsplit<2, 2, true><<<grid, 128, 0, st>>>(A, lda, B, ldb, C, ldc, F, P, Pw, ctx->d_err));
-    else FP_LAUNCH(ctx, nm, st, k_mm_fullsplit<2, 2, false><<<grid, 128, 0, st>>>(A, lda, B, ldb, C, ldc, F, P, Pw, ctx->d_err));
+    if (split) FP_LAUNCH(ctx, nm, st, k_mm_fullsplit<2, 2, true><<<grid, 128, 0, st>>>(A, lda, CA, CB, C, ldc, F, P, Pw, ctx->d_err));
+    else FP_LAUNCH(ctx, nm, st, k_mm_fullsplit<2, 2, false><<<grid, 128, 0, st>>>(A, lda, CA, CB, C, ldc, F, P, Pw, ctx->d_err));
   }
   FP_CUDA(cudaGetLastError());
   return FP_OK;

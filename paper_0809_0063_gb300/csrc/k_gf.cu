@@ -598,6 +598,49 @@ __global__ void __launch_bounds__(GFW_THREADS, 2) k_gf_mul_fixed(const typename 
   if (op.any_bad()) flag_error(err, ERR_RANGE);
 }
 
+// GF(2^8) dot product on the word-level multiply (Algorithm FGDP with n > 1, index form): since
+// p | q here, every product's REDQ compression values are its digits and the word-level product
+// gives the product's index directly; the field addition in GF(2^8) is XOR, so each thread XORs
+// its products, the block XOR-reduces, and the block's sum is written as a spread vector
+// (coefficient i at bit i fb) for the common final kernel.  No code can be out of range.
+__global__ void __launch_bounds__(GFW_THREADS, 2) k_gf_dot_w28(const uint4* __restrict__ a, const uint4* __restrict__ b,
+                                                              uint64_t nvec, const uint8_t* __restrict__ ta,
+                                                              const uint8_t* __restrict__ tb, uint32_t ntail,
+                                                              const uint4* __restrict__ image, uint32_t fb,
+                                                              uint32_t* __restrict__ partial) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  constexpr uint32_t IB = Gfw<2, 8>::BYTES;
+  for (uint32_t i = threadIdx.x; i < IB / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = image[i];
+  __syncthreads();
+  const uint32_t* wl = reinterpret_cast<const uint32_t*>(sm + Gfw<2, 8>::W) + (threadIdx.x & 31u);
+  const uint8_t* H = sm + Gfw<2, 8>::H;
+  auto word = [&](uint32_t x, uint32_t y) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc ^= gfw_mul_2_8(__byte_perm(x, 0u, 0x4440u + j), __byte_perm(y, 0u, 0x4440u + j), wl, H);
+    return acc;
+  };
+  uint32_t acc = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
+    const uint4 x = __ldcs(a + i), y = __ldcs(b + i);
+    acc ^= word(x.x, y.x) ^ word(x.y, y.y) ^ word(x.z, y.z) ^ word(x.w, y.w);
+  }
+  if (blockIdx.x == 0)   // the last n mod 16 elements
+    for (uint32_t i = threadIdx.x; i < ntail; i += blockDim.x) acc ^= gfw_mul_2_8(ta[i], tb[i], wl, H);
+  for (int o = 16; o; o >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ uint32_t ws[GFW_THREADS / 32];
+  if ((threadIdx.x & 31u) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) t ^= ws[w];
+    uint32_t sp = 0;
+    for (uint32_t i = 0; i < 8; ++i) sp |= ((t >> i) & 1u) << (i * fb);
+    partial[blockIdx.x] = sp;
+  }
+}
+
 // Host: the shared-memory image of the word-level tables of the field, empty when the field has
 // no word-level kernel.  `word` holds the DQT words, `index`/`rem` the representation helpers.
 static std::vector<uint8_t> gfw_image(uint32_t p, uint32_t k, uint32_t b, const std::vector<uint32_t>& modulus) {
@@ -978,6 +1021,32 @@ template <typename E>
 static fp_status gf_dot_launch(fp_ctx ctx, fp_gf g, const E* a, const E* b, size_t n, E* out, int form,
                                cudaStream_t st) {
   using namespace fpd;
+  if (sizeof(E) == 1 && g->p == 2 && g->k == 8 && g->d_img && form == FP_GF_INDEX && n >= 16 &&
+      ((((uintptr_t)a) | ((uintptr_t)b)) & 15u) == 0) {
+    // GF(2^8), index form, aligned: the word-level multiply with XOR accumulation
+    const size_t smem = Gfw<2, 8>::BYTES;
+    FP_CUDA(cudaFuncSetAttribute(k_gf_dot_w28, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gf_dot_w28, GFW_THREADS, smem));
+    const uint64_t nvec = n / 16;
+    const uint64_t want = (nvec + GFW_THREADS - 1) / GFW_THREADS;
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx->num_sms * std::max(per_sm, 1)));
+    fp_status s = ensure_scratch(ctx, (size_t)grid * sizeof(uint32_t), 1, st);
+    if (s != FP_OK) return s;
+    uint32_t* partial = (uint32_t*)ctx->scratch2;
+    const uint8_t* a8 = (const uint8_t*)a;
+    const uint8_t* b8 = (const uint8_t*)b;
+    FP_LAUNCH(ctx, "k_gf_dot_w28", st,
+              (k_gf_dot_w28<<<grid, GFW_THREADS, smem, st>>>((const uint4*)a, (const uint4*)b, nvec, a8 + nvec * 16,
+                                                              b8 + nvec * 16, (uint32_t)(n - nvec * 16), g->d_img, g->fb,
+                                                              partial)));
+    uint32_t ones = 0;
+    for (uint32_t i = 0; i < g->k; ++i) ones |= 1u << (i * g->fb);
+    FP_LAUNCH(ctx, "k_gf_dot_final", st,
+              (k_gf_dot_final<E><<<1, 256, 0, st>>>(partial, grid, out, g->p, g->k, g->fb, ones, nullptr)));
+    FP_CUDA(cudaGetLastError());
+    return FP_OK;
+  }
   const uint32_t tsz = 1u << (g->c * g->k);
   const size_t smem = g->order * sizeof(uint64_t) + 2 * tsz * sizeof(uint32_t);
   GfDotDev D{GfDev{form == FP_GF_LOG ? g->d_word_dl : g->d_word_d, g->d_Ld, g->d_Hd, g->order, g->k, g->c, g->fb, 0},

@@ -451,6 +451,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
         }
         tc_fence_after();
         // 1.5 2^23 added: the float's bits are 0x4B400000 + v exactly; d1 = round(v / 2^9)
+        // (|d0| < 2^8), and y + (2^16 - 2^9) d1 = d0 + 2^16 d1 + 0x4B400000
         const uint32_t base = tmem + lane_base + (uint32_t)(buf * 256 + part * P_CW);
         uint32_t va[16], vb[16];
         tmem_ld16_nowait(base, va);
