@@ -81,8 +81,9 @@ enum {
   FP_MM_PLAIN_TC = 6,   /* unpacked, tcgen05 kind::f16 (bf16 operands, fp32 accumulate) */
   FP_MM_RIGHT_TC = 7,   /* right compression on tcgen05 kind::f16: fp16 operands holding two
                            centred residues, inner dimension chunked: p <= 3 at Q = 2^10 in
-                           chunks of 448 (k <= 32767); p = 5, 7 at Q = 2^9 in chunks of 32 / 16
-                           inner steps (one or two MMA instructions), any k */
+                           chunks of 448 (k <= 32767); p = 5, 7 at Q = 1023 / 681 (the largest
+                           Q whose pairs are exact fp16 integers; fp_mm_choose reports b = 0) in
+                           chunks of 64 / 32 inner steps, any k */
   FP_MM_LEFT_F32 = 8,   /* left compression (Sec. 7.4): by transposition, (A B)^T = B^T A^T with
                            the right compression (FP32 words) of A^T, i.e. each word packs two
                            consecutive rows of A; A^T, B^T and C^T go through context scratch */

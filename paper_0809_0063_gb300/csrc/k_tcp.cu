@@ -11,6 +11,11 @@
 //    2^15) while the MMA warp fills the other TMEM buffer (delayed reduction, Sec. 2.2).  At the
 //    end of a tile an offset k makes both digits of R non-negative and REDQ_2 (Algorithm 2,
 //    q = 2^16) recovers them mod p; the residues go straight to C.
+//  packed, p = 5, 7: the same with centred residues |c| <= (p-1)/2 and Q = 1023 (p = 5) or 681
+//    (p = 7), the largest Q whose pair words are exact fp16 integers; chunks of 64 / 32 inner
+//    steps keep both digits below Q / 2, a chunk word's digits are separated by one rounded
+//    scaling by 1/Q, and R's 16-bit digits are re-reduced by REDQ every 127 / 113 chunks.  The
+//    drains (one per chunk, 128 x 256 values) bound this form, not the MMAs.
 //  plain (PLAIN_TC): A and B converted to bf16 (residues < 256 are exact), one residue per
 //    column, fp32 sums exact while k (p-1)^2 < 2^24, mod p in the epilogue.  It is the plain
 //    product on the same pipe as the packed one.
@@ -62,9 +67,10 @@ struct PProb {
   int tile0;
   uint32_t koffset;  // k: added to both digits before REDQ
   uint32_t off_mod_p;
-  int cmma;          // packed p = 5, 7: MMA instructions (16 inner steps each) per chunk
-  int rr;            // packed p = 5, 7: chunks between two re-reductions of R
-  uint32_t dmax;     // packed p = 5, 7: largest |digit| one chunk adds
+  uint16_t cmma;    // packed p = 5, 7: MMA instructions (16 inner steps each) per chunk
+  uint16_t rr;      // packed p = 5, 7: chunks between two re-reductions of R
+  uint32_t dmax;    // packed p = 5, 7: largest |digit| one chunk adds
+  float qinv;       // packed p = 5, 7: 1 / Q for the pair words c0 + Q c1 (Q = rint(1 / qinv))
   RedqParams P;      // REDQ_2 at q = 2^16
 };
 
@@ -164,57 +170,71 @@ __device__ __forceinline__ void final_redq(uint32_t (&R)[NW], uint32_t fix, uint
 
 // REDQ_2 (Algorithm 2) at q = 2^16 for p = 5, 7 with the correction done by arithmetic (p^2 > 32
 // rules out the lane table for p = 7): s = floor(w / p), u_0 = w - p s, u_1 = (floor(w / q) -
-// p floor(s / q)) mod q, mu_1 = u_1, mu_0 = (u_0 - q u_1) mod p, both shifted back by the offset
-// (om = offset mod p).  Returns mu_0 | mu_1 << 8.
-template <uint32_t PP>
-__device__ __forceinline__ uint32_t redq2_arith(uint32_t w, uint32_t om) {
-  constexpr uint32_t C = (PP - 65536u % PP) % PP;        // (-q) mod p
-  const uint32_t s = w / PP;
-  const uint32_t u0 = (w - PP * s) & 0xFFFFu;
-  const uint32_t u1 = ((w >> 16) - PP * (s >> 16)) & 0xFFFFu;
-  const uint32_t mu1 = (u1 + PP - om) % PP;
-  const uint32_t mu0 = (u0 + C * u1 + PP - om) % PP;
+// p floor(s / q)) mod q, mu_1 = u_1, mu_0 = (u_0 - q u_1) mod p = (u_0 + c u_1) mod p with
+// c = (-q) mod p, both shifted back by the offset (om = offset mod p).  Run-time p (one code
+// copy for both primes: these loops run once per tile or per few hundred chunks, and smaller
+// code keeps the drain loop and the MMA and TMA loops in the instruction cache).
+// Returns mu_0 | mu_1 << 8.
+__device__ __forceinline__ uint32_t redq2_arith(uint32_t w, uint32_t om, uint32_t p, uint32_t c, const DivP& dv) {
+  const uint32_t s = divp32(w, dv);
+  const uint32_t u0 = (w - p * s) & 0xFFFFu;
+  const uint32_t u1 = ((w >> 16) - p * (s >> 16)) & 0xFFFFu;
+  uint32_t mu1 = u1 + p - om;
+  mu1 = mu1 >= p ? mu1 - p : mu1;
+  const uint32_t mu0 = modp32(u0 + c * u1 + p - om, dv, p);
   return mu0 | (mu1 << 8);
 }
 
 // Every word of R (digits offset to non-negative by `fix`) replaced by its two residues, as a
 // word with digits < p: the delayed reduction of Sec. 2.2 applied before a 16-bit digit could
-// overflow.
-template <uint32_t PP, int NW>
-__device__ __forceinline__ void rereduce_pairs(uint32_t (&R)[NW], uint32_t fix, uint32_t om) {
+// overflow.  Sixteen words per pass, R rotated by sixteen after each (back in order at the end).
+template <int NW>
+__device__ __forceinline__ void rereduce_pairs(uint32_t (&R)[NW], uint32_t fix, uint32_t om, uint32_t p, uint32_t c,
+                                               const DivP& dv) {
+#pragma unroll 1
+  for (int pass = 0; pass < NW / 16; ++pass) {
+    uint32_t t[16];
 #pragma unroll
-  for (int j = 0; j < NW; ++j) {
-    const uint32_t v = redq2_arith<PP>(R[j] + fix, om);
-    R[j] = (v & 0xFFu) | ((v >> 8) << 16);
+    for (int j = 0; j < 16; ++j) {
+      const uint32_t v = redq2_arith(R[j] + fix, om, p, c, dv);
+      t[j] = (v & 0xFFu) | ((v >> 8) << 16);
+    }
+#pragma unroll
+    for (int j = 0; j < NW - 16; ++j) R[j] = R[j + 16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) R[NW - 16 + j] = t[j];
   }
 }
 
-// The end of a packed p = 5, 7 tile: as final_redq, with redq2_arith.
-template <uint32_t PP, int NW>
-__device__ __forceinline__ void final_redq_arith(uint32_t (&R)[NW], uint32_t fix, uint32_t om, uint8_t* dst, int c0,
-                                                 int n, bool in, bool vec) {
-#pragma unroll
-  for (int h = 0; h < NW / 16; ++h) {          // 16 words -> 32 residues -> two 16-byte stores
+// The end of a packed p = 5, 7 tile: as final_redq, sixteen words (two 16-byte stores) per pass
+// with R moved down by sixteen after each.
+template <int NW>
+__device__ __forceinline__ void final_redq_arith(uint32_t (&R)[NW], uint32_t fix, uint32_t om, uint32_t p, uint32_t c,
+                                                 const DivP& dv, uint8_t* dst, int c0, int n, bool in, bool vec) {
+#pragma unroll 1
+  for (int h = 0; h < NW / 16; ++h) {
     uint32_t o[8];
 #pragma unroll
     for (int j = 0; j < 16; j += 2)
-      o[j >> 1] = redq2_arith<PP>(R[h * 16 + j] + fix, om) | (redq2_arith<PP>(R[h * 16 + j + 1] + fix, om) << 16);
-    uint8_t* d = dst + 2 * (h * 16);
-    const int c = c0 + 2 * (h * 16);
+      o[j >> 1] = redq2_arith(R[j] + fix, om, p, c, dv) | (redq2_arith(R[j + 1] + fix, om, p, c, dv) << 16);
+    uint8_t* d = dst + 32 * h;
+    const int cc = c0 + 32 * h;
     if (vec) {
       reinterpret_cast<uint4*>(d)[0] = make_uint4(o[0], o[1], o[2], o[3]);
       reinterpret_cast<uint4*>(d)[1] = make_uint4(o[4], o[5], o[6], o[7]);
     } else if (in) {
 #pragma unroll
       for (int j = 0; j < 32; ++j)
-        if (c + j < n) d[j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
+        if (cc + j < n) d[j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
     }
+#pragma unroll
+    for (int j = 0; j < NW - 16; ++j) R[j] = R[j + 16];
   }
 }
 
 template <int PK, int CAP = FP_GROUP_MAX>
 __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__ PParamsT<CAP> g, uint32_t* err) {
-  constexpr bool PACKED = PK != 0;   // 1: p <= 3 at Q = 2^10; 2: p = 5, 7 at Q = 2^9
+  constexpr bool PACKED = PK != 0;   // 1: p <= 3 at Q = 2^10; 2: p = 5, 7 at Q = 1023 / 681
   extern __shared__ __align__(1024) uint8_t p_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)p_smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + P_STAGES * P_STAGE_BYTES);
@@ -430,7 +450,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
       if (lane == 0) mbar_arrive(&tempty[buf]);
     }
     for (int t = blockIdx.x; t < g.total && ok && PK == 2; t += gridDim.x) {
-      // p = 5, 7: chunk words v = d0 + 2^9 d1 with |d0|, |d1| <= dmax < 256 (Q = 2^9); every
+      // p = 5, 7: chunk words v = d0 + Q d1 with |d0|, |d1| <= dmax < Q / 2; every
       // chunk is moved into R = D0 + 2^16 D1 as below, and every rr chunks R's digits are
       // replaced by their residues before a 16-bit digit could overflow
       const PTile x = p_tile(g, t);
@@ -439,6 +459,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
 #pragma unroll
       for (int j = 0; j < P_CW; ++j) R[j] = 0;
       const uint32_t p = pr.P.p, dmax = pr.dmax, rr = (uint32_t)pr.rr;
+      const float qinv = pr.qinv;
+      const uint32_t qdec = 65536u - (uint32_t)rintf(1.0f / qinv);
       uint32_t cr = 0;     // chunks added since R last held residues
       for (int c = 0; c < pr.nchunks; ++c, ++gc) {
         const int buf = (int)(gc & 1u);
@@ -450,8 +472,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
           break;
         }
         tc_fence_after();
-        // 1.5 2^23 added: the float's bits are 0x4B400000 + v exactly; d1 = round(v / 2^9)
-        // (|d0| < 2^8), and y + (2^16 - 2^9) d1 = d0 + 2^16 d1 + 0x4B400000
+        // 1.5 2^23 added: the float's bits are 0x4B400000 + v exactly; the same after scaling
+        // by 1/Q gives 0x4B400000 + round(v / Q) = 0x4B400000 + d1 (|d0| / Q <= 0.43, far
+        // from the rounding boundary), and y + (2^16 - Q) d1 = d0 + 2^16 d1 + 0x4B400000
         const uint32_t base = tmem + lane_base + (uint32_t)(buf * 256 + part * P_CW);
         uint32_t va[16], vb[16];
         tmem_ld16_nowait(base, va);
@@ -464,10 +487,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
           }
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const uint32_t raw = (blk & 1) ? vb[j] : va[j];
-            const int32_t y = __float_as_int(__uint_as_float(raw) + 12582912.0f);
-            const int32_t d1 = (y - (0x4B400000 - 256)) >> 9;
-            R[blk * 16 + j] += (uint32_t)y + (uint32_t)(d1 * (65536 - 512));
+            const float v = __uint_as_float((blk & 1) ? vb[j] : va[j]);
+            const uint32_t y = (uint32_t)__float_as_int(v + 12582912.0f);
+            const uint32_t d1 = (uint32_t)(__float_as_int(fmaf(v, qinv, 12582912.0f)) - 0x4B400000);
+            R[blk * 16 + j] += y + d1 * qdec;
           }
           tmem_wait();
         }
@@ -477,8 +500,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
         if (++cr == rr && c + 1 < pr.nchunks) {
           const uint32_t off = dmax * cr;
           const uint32_t fix = off * 65537u - cr * 0x4B400000u;
-          if (p == 7) rereduce_pairs<7, P_CW>(R, fix, off % 7u);
-          else rereduce_pairs<5, P_CW>(R, fix, off % 5u);
+          rereduce_pairs<P_CW>(R, fix, off % p, p, pr.P.c, pr.P.dv);
           cr = 0;
         }
       }
@@ -491,8 +513,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
       const bool in = row < pr.m && c0 < n;
       uint8_t* dst = pr.C + (size_t)row * pr.ldc + c0;
       const bool vec = in && c0 + 2 * P_CW <= n && ((((uintptr_t)dst) & 15u) == 0);
-      if (p == 7) final_redq_arith<7, P_CW>(R, fix, off % 7u, dst, c0, n, in, vec);
-      else final_redq_arith<5, P_CW>(R, fix, off % 5u, dst, c0, n, in, vec);
+      final_redq_arith<P_CW>(R, fix, off % p, p, pr.P.c, pr.P.dv, dst, c0, n, in, vec);
     }
     for (int t = blockIdx.x; t < g.total && ok && PK == 1; t += gridDim.x) {
       const PTile x = p_tile(g, t);
@@ -623,7 +644,7 @@ __global__ void __launch_bounds__(256) k_t16_convert_a(const uint8_t* __restrict
 }
 
 // B16 (k x ldw 16-bit, zero past nw) row by row from B (k x n), no transpose.  PACKED: word
-// j = fp16 of c(B[l][2j]) + Q c(B[l][2j+1]) (Q = 2^10 for p <= 3, 2^9 for p = 5, 7; the second
+// j = fp16 of c(B[l][2j]) + Q c(B[l][2j+1]) (Q = 2^10 for p <= 3, 1023 / 681 for p = 5 / 7; the second
 // residue 0 past column n), one
 // thread per 16 bytes of B (8 words); plain: bf16 of B[l][j], one thread per 8 bytes of B
 // (8 elements).  Residues >= p set ERR_RANGE.
@@ -664,9 +685,10 @@ __global__ void __launch_bounds__(256) k_t16_convert_b(const uint8_t* __restrict
         const uint32_t x = w[q];
         if (PACKED && p <= 3) {
           o[q] = h16_pair_word(x & 0xffu, (x >> 8) & 0xffu) | (h16_pair_word((x >> 16) & 0xffu, x >> 24) << 16);
-        } else if (PACKED) {   // p = 5, 7: c(b0) + 2^9 c(b1)
-          o[q] = h16_pair_word_p(x & 0xffu, (x >> 8) & 0xffu, p, 512.0f) |
-                 (h16_pair_word_p((x >> 16) & 0xffu, x >> 24, p, 512.0f) << 16);
+        } else if (PACKED) {   // p = 5, 7: c(b0) + Q c(b1), Q = 1023 / 681
+          const float Q = p == 5 ? 1023.0f : 681.0f;
+          o[q] = h16_pair_word_p(x & 0xffu, (x >> 8) & 0xffu, p, Q) |
+                 (h16_pair_word_p((x >> 16) & 0xffu, x >> 24, p, Q) << 16);
         } else {
           const uint32_t y = w[q >> 1] >> (16 * (q & 1));
           o[q] = bf16_of(y & 0xffu) | (bf16_of((y >> 8) & 0xffu) << 16);
@@ -680,17 +702,19 @@ __global__ void __launch_bounds__(256) k_t16_convert_b(const uint8_t* __restrict
 // ---------------------------------------------------------------- host side
 
 // Packed fp16 words: p <= 3 at Q = 2^10 in chunks of 448 inner steps (k <= 32767 keeps R's
-// 16-bit digits from overflowing without re-reduction); p = 5, 7 at Q = 2^9, where centred
-// residues |c| <= (p-1)/2 keep |c0| + 2^9 |c1| <= 2048 (exact fp16), in chunks of 32 (p = 5) or
-// 16 (p = 7) inner steps so that every chunk digit stays below 2^8 in magnitude.
+// 16-bit digits from overflowing without re-reduction); p = 5, 7 at the largest Q whose pair
+// words stay exact in fp16 with centred residues |c| <= (p-1)/2 ((p-1)/2 (1 + Q) <= 2048: Q =
+// 1023 for p = 5, 681 for p = 7), in chunks of 64 (p = 5) or 32 (p = 7) inner steps so that
+// every chunk digit stays below Q / 2 in magnitude (256 < 511.5, 288 < 340.5).
 bool f16p_ok(uint32_t p, int k) { return (p <= 3 && k <= 32767) || p == 5 || p == 7; }
 
-// Chunk parameters of the p = 5, 7 packed form: MMA instructions per chunk, the largest |digit|
-// a chunk adds ((p-1)/2)^2 per inner step, and the chunks R takes before its 16-bit digits could
-// overflow ((p-1) + 2 dmax rr < 2^16).
-static void pk2_params(uint32_t p, int* cmma, uint32_t* dmax, int* rr) {
+// Chunk parameters of the p = 5, 7 packed form: Q, MMA instructions per chunk, the largest
+// |digit| a chunk adds ((p-1)/2)^2 per inner step, and the chunks R takes before its 16-bit
+// digits could overflow ((p-1) + 2 dmax rr < 2^16).
+static void pk2_params(uint32_t p, uint32_t* Q, int* cmma, uint32_t* dmax, int* rr) {
   const uint32_t h = (p - 1) / 2;
-  *cmma = p == 5 ? 2 : 1;
+  *Q = p == 5 ? 1023u : 681u;
+  *cmma = p == 5 ? 4 : 2;
   *dmax = h * h * 16u * (uint32_t)*cmma;
   *rr = (int)((65535u - (p - 1)) / (2u * *dmax));
 }
@@ -763,8 +787,13 @@ static fp_status launch_t16_mode(fp_ctx ctx, const std::vector<const fp_mm_probl
       g.ktiles = kp / P_BK;
       g.nchunks = packed ? (g.ktiles + P_CHUNK_KT - 1) / P_CHUNK_KT : 1;
       if (pk == 2) {
-        pk2_params(x.p, &g.cmma, &g.dmax, &g.rr);
-        g.nchunks = g.ktiles * 4 / g.cmma;
+        uint32_t Q = 0;
+        int cmma = 0, rr = 0;
+        pk2_params(x.p, &Q, &cmma, &g.dmax, &rr);
+        g.cmma = (uint16_t)cmma;
+        g.rr = (uint16_t)rr;
+        g.nchunks = g.ktiles * 4 / cmma;
+        g.qinv = 1.0f / (float)Q;
       }
       g.tn = (nw + P_BNW - 1) / P_BNW;
       g.tile0 = tile;

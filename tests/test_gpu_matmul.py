@@ -338,13 +338,13 @@ def test_matmul_cmm_bound_and_range(env):
     assert ei.value.status == fp.FP_EINVAL
 
 
-@pytest.mark.parametrize("p,k", [(7, 16), (7, 3632), (7, 3648), (7, 4100), (5, 8160), (5, 8200)])
+@pytest.mark.parametrize("p,k", [(7, 16), (7, 3600), (7, 3648), (7, 4100), (5, 8120), (5, 8200)])
 @pytest.mark.parametrize("sign", [1, -1])
 def test_right_tc_p57_largest_digits(env, p, k, sign):
-    """Packed fp16 words for p = 5, 7 (Q = 2^9, chunks of 32 / 16 inner steps): entries whose
-    centred value is +-(p-1)/2 everywhere make every chunk digit reach its bound dmax and every
-    digit of R grow by dmax per chunk; k around the re-reduction period (227 chunks for p = 7,
-    255 for p = 5) crosses it."""
+    """Packed fp16 words for p = 5, 7 (Q = 1023 / 681, chunks of 64 / 32 inner steps): entries
+    whose centred value is +-(p-1)/2 everywhere make every chunk digit reach its bound dmax and
+    every digit of R grow by dmax per chunk; k around the re-reduction period (127 chunks of 64
+    for p = 5, 113 chunks of 32 for p = 7) crosses it."""
     fp, torch, dev, ctx = env
     h = (p - 1) // 2
     m, n = 130, 257
