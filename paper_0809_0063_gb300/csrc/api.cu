@@ -398,15 +398,16 @@ fp_status mm_choose(uint32_t p, uint64_t kdim, uint32_t algo, uint32_t* b_out, u
   }
   if (algo == FP_MM_RIGHT_TC) {
     // centred residues {-1,0,1}: |digit| <= chunk < Q/2 with Q = 2^10; fp16 operands hold
-    // b0 + 2^10 b1 exactly (11 significant bits).  p = 5, 7: |c| <= (p-1)/2 at Q = 2^9 (|c0| +
-    // 2^9 |c1| <= 2048), chunks of 32 / 16 inner steps keep |digit| < 2^8.
+    // b0 + 2^10 b1 exactly (11 significant bits).  p = 5, 7: |c| <= (p-1)/2 at Q = 1023 / 681
+    // (|c0| + Q |c1| <= 2048, not a power of two: *b = 0), chunks of 64 / 32 inner steps keep
+    // |digit| < Q / 2.
     if (p > 3 && p != 5 && p != 7) {
       set_error("RIGHT_TC needs p in {2, 3, 5, 7} (p=%u)", p);
       return FP_EBOUND;
     }
-    *b_out = p <= 3 ? 10 : 9;
+    *b_out = p <= 3 ? 10 : 0;
     *e_out = 2;
-    *chunk_out = p <= 3 ? 448 : (p == 5 ? 32 : 16);
+    *chunk_out = p <= 3 ? 448 : (p == 5 ? 64 : 32);
     return FP_OK;
   }
   int beta = (algo == FP_MM_RIGHT_F64 || algo == FP_MM_PLAIN_F64 || algo == FP_MM_LEFT_F64) ? 52 : 64;

@@ -85,7 +85,22 @@ __device__ void run_dot(const BInst& I, uint32_t* err) {
   __shared__ uint64_t red[BT_THREADS / 32];
   uint64_t acc = 0;
   uint32_t bad = 0;
-  for (uint32_t i = threadIdx.x; i < I.k; i += blockDim.x) {
+  uint32_t done = 0;
+  if (((((uintptr_t)I.A) | ((uintptr_t)I.B)) & 15u) == 0) {
+    // 16 residues of each operand per load; four 4-way byte products (dp4a) per load pair, each
+    // at most 4 (p-1)^2 < 2^18, summed in 32 bits per load pair and in 64 bits across them
+    const uint32_t nv = I.k / 16, pp4 = 0x01010101u * I.p;
+    const uint4* va = reinterpret_cast<const uint4*>(I.A);
+    const uint4* vb = reinterpret_cast<const uint4*>(I.B);
+    for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x) {
+      const uint4 x = __ldg(va + i), y = __ldg(vb + i);
+      bad |= __vcmpgeu4(x.x, pp4) | __vcmpgeu4(x.y, pp4) | __vcmpgeu4(x.z, pp4) | __vcmpgeu4(x.w, pp4) |
+             __vcmpgeu4(y.x, pp4) | __vcmpgeu4(y.y, pp4) | __vcmpgeu4(y.z, pp4) | __vcmpgeu4(y.w, pp4);
+      acc += __dp4a(x.x, y.x, __dp4a(x.y, y.y, __dp4a(x.z, y.z, __dp4a(x.w, y.w, 0u))));
+    }
+    done = nv * 16;
+  }
+  for (uint32_t i = done + threadIdx.x; i < I.k; i += blockDim.x) {
     uint32_t a = I.A[i], b = I.B[i];
     bad |= (a >= I.p) | (b >= I.p);
     acc += a * b;
