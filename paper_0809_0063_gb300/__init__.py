@@ -324,9 +324,17 @@ def fp_selftest_bounded_wait(ctx, polls: int, stream=None):
     _check(lib().fp_selftest_bounded_wait(ctx, polls, _stream(stream)))
 
 
+def fp_instances(instances):
+    """A contiguous fp_instance array (what fp_batch_run reads) from a sequence of fp_instance.
+    Building it costs a few microseconds per instance: a caller that submits the same batch
+    descriptors again keeps the array and passes it to fp_batch_run as it is."""
+    return (fp_instance * len(instances))(*instances)
+
+
 def fp_batch_run(ctx, instances, stream=None):
-    arr = (fp_instance * len(instances))(*instances)
-    _check(lib().fp_batch_run(ctx, arr, len(instances), _stream(stream)))
+    """instances: a ctypes array of fp_instance (passed as it is) or a sequence of fp_instance."""
+    arr = instances if isinstance(instances, ctypes.Array) else fp_instances(instances)
+    _check(lib().fp_batch_run(ctx, arr, len(arr), _stream(stream)))
 
 
 # ------------------------------------------------------------------ serving loop

@@ -11,7 +11,9 @@
 // reduction at the end).
 //
 // Persistent schedule: one CTA per SM walks the global list of 128 x 256 output tiles (all
-// problems, those with the longest inner dimension first) with stride gridDim.x.  Roles:
+// problems, those with the longest inner dimension first) in waves of gridDim.x tiles, taken in
+// forward order in even waves and reversed in odd ones (better balance than a plain stride when
+// the tiles' lengths differ: 0.98 vs 0.94 of the mean load for the matrix step).  Roles:
 //   warp 0       TMA producer: per k tile, A 128 x 128 bytes and B two boxes of 128 x 128
 //                bytes (128-byte swizzle) into a 4-stage shared-memory ring,
 //   warp 1       TMEM allocation (512 columns = two 128 x 256 fp32 accumulators) and the
@@ -125,6 +127,15 @@ __device__ __forceinline__ uint32_t range_bits(const uint8_t* src, int valid, ui
   return acc;
 }
 
+// The w-th tile of this CTA: waves of gridDim.x tiles, taken in forward order in even waves and
+// in reverse order in odd ones (the tiles are sorted by inner dimension, longest first, so the
+// CTAs that take the longest tile of one wave take the shortest of the next).  Every role of the
+// kernel walks the same sequence; a CTA stops at its first index past the last tile (only the
+// last wave can have one).
+__device__ __forceinline__ int g_wave_tile(int w) {
+  return w * (int)gridDim.x + ((w & 1) ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x);
+}
+
 template <int CAP>
 __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__ GParamsT<CAP> g, uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t g_smem_raw[];
@@ -170,7 +181,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
     if (lane == 0) {
       uint32_t it = 0;              // k tiles issued by this CTA (all its tiles)
       bool stop = false;
-      for (int t = blockIdx.x; t < g.total && !stop; t += gridDim.x) {
+      for (int w = 0, t = g_wave_tile(0); t < g.total && !stop; t = g_wave_tile(++w)) {
         const GTile x = g_tile(g, t);
         for (int kt = 0; kt < x.pr->ktiles; ++kt, ++it) {
           const int s = (int)(it % G_STAGES);
@@ -198,7 +209,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
       uint32_t it = 0;
       bool stop = false;
       int lt = 0;                   // tiles of this CTA so far
-      for (int t = blockIdx.x; t < g.total && !stop; t += gridDim.x, ++lt) {
+      for (int w = 0, t = g_wave_tile(0); t < g.total && !stop; t = g_wave_tile(++w), ++lt) {
         const GTile x = g_tile(g, t);
         const int buf = lt & 1;
         if (lt >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((lt - 2) >> 1) & 1u, abort_flag)) break;
@@ -237,7 +248,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
         reinterpret_cast<uint32_t*>(smem + G_STAGES * G_STAGE_BYTES + 256) + (warp - 2) * (32 * 9);
     uint32_t bad = 0;
     int lt = 0;
-    for (int t = blockIdx.x; t < g.total; t += gridDim.x, ++lt) {
+    for (int w = 0, t = g_wave_tile(0); t < g.total; t = g_wave_tile(++w), ++lt) {
       const int buf = lt & 1;
       const GTile x = g_tile(g, t);
       const GProb& pr = *x.pr;
