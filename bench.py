@@ -803,9 +803,10 @@ def run_batch(args, ws, rank, local, emit=True):
         return d_out[oc:oc + 4]
 
     stream = torch.cuda.current_stream()
+    carr = fp.fp_instances(arr)      # the batch descriptors, built once (reused by every call)
 
     def batched():
-        fp.fp_batch_run(ctx, arr)
+        fp.fp_batch_run(ctx, carr)
 
     def per_instance():
         for x, a in zip(insts, arr):
@@ -855,7 +856,7 @@ def run_batch(args, ws, rank, local, emit=True):
         batched()
     torch.cuda.synchronize()
     fp.fp_ctx_profile(ctx, 0)
-    names = ["k_mm_f8g", "k_mm_t16_plain", "k_batch", "k_pad_rows", "k_t16_convert_jobs", "k_put_bytes"]
+    names = ["k_mm_f8g_pre", "k_tile_pack", "k_mm_t16_plain", "k_t16_convert_jobs", "k_batch", "k_put_bytes"]
     kern = {}
     for nm in names:
         c, ms = fp.fp_ctx_profile_read(ctx, nm)
@@ -870,7 +871,7 @@ def run_batch(args, ws, rank, local, emit=True):
     # end to end: every input in, the call, every result out (one copy each way per step)
     def e2e():
         d_in.copy_(h_in, non_blocking=True)
-        fp.fp_batch_run(ctx, arr)
+        fp.fp_batch_run(ctx, carr)
         h_out.copy_(d_out, non_blocking=True)
 
     e2e()
@@ -885,19 +886,24 @@ def run_batch(args, ws, rank, local, emit=True):
             assert np.array_equal(got, field.matmul_mod_rows(x.a, x.b, x.p, np.array([0])))
         else:
             assert int(hv_out[oc:oc + 4].view(np.uint32)[0]) == field.dot_mod(x.a, x.b, x.p)
-    # The library's routing (fp_batch_run's documented rule): large products with p <= 17 on the
-    # e4m3 kernel, 17 < p <= 127 on the bf16 kernel, the rest in the batch kernel.  Roofline of the
-    # kernel with the most time per step, on its own MACs.
+    # The library's routing (fp_batch_run's documented rule): products with p <= 17 and
+    # k (p-1)^2 < 2^23 or p <= 31 and 2 k (p/2)^2 + p < 2^23 whose 128 x 256 x 32-padded MACs are >= 2^21 and <= 32 x their own on
+    # the pre-tiled e4m3 kernel, large ones with 31 < p <= 127 and k (p-1)^2 < 2^24 on the bf16
+    # kernel, the rest in the batch kernel.  Roofline of the kernel with the most time
+    # per step, on its own MACs.
     def route(x):
-        if x.kind != "matmul" or x.m < 64 or x.n < 64 or x.m * x.n * x.k < (1 << 21) or \
-                x.k * (x.p - 1) ** 2 >= (1 << 24) or x.p > 127:
+        if x.kind != "matmul" or x.p > 127:
             return "k_batch"
-        return "k_mm_f8g" if x.p <= 17 else "k_mm_t16_plain"
-    kmacs = {nm: 0 for nm in ("k_mm_f8g", "k_mm_t16_plain", "k_batch")}
+        if (x.p <= 17 and x.k * (x.p - 1) ** 2 < (1 << 23)) or (x.p <= 31 and 2 * x.k * (x.p // 2) ** 2 + x.p < (1 << 23)):
+            padded = -(-x.m // 128) * 128 * -(-x.n // 256) * 256 * -(-x.k // 32) * 32
+            return "k_mm_f8g_pre" if (1 << 21) <= padded <= 32 * x.m * x.n * x.k else "k_batch"
+        big = x.m >= 64 and x.n >= 64 and x.m * x.n * x.k >= (1 << 21)
+        return "k_mm_t16_plain" if big and x.k * (x.p - 1) ** 2 < (1 << 24) else "k_batch"
+    kmacs = {nm: 0 for nm in ("k_mm_f8g_pre", "k_mm_t16_plain", "k_batch")}
     for x in insts:
         kmacs[route(x)] += x.m * x.n * x.k if x.kind == "matmul" else x.k
     hbm, bf16, _, peak_src = peaks()
-    peaks_k = {"k_mm_f8g": (2.0 * bf16, f"fp8 = measured bf16 x 2 ({peak_src})"),
+    peaks_k = {"k_mm_f8g_pre": (2.0 * bf16, f"fp8 = measured bf16 x 2 ({peak_src})"),
                "k_mm_t16_plain": (bf16, f"measured bf16 dense ({peak_src})"),
                "k_batch": (603.2, "mma.sync bf16 measured by the pipe probe (packed words count as 2 MACs)")}
     dom = max((nm for nm in kmacs if nm in kern), key=lambda nm: kern[nm]["ms_per_step"])

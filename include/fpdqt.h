@@ -444,11 +444,14 @@ typedef struct {
 } fp_instance;
 
 /* Uneven batch (no counterpart in the paper as a call; each instance's packing follows
- * Sec. 7.6.1).  Run all `count` instances: matrix products with k (p-1)^2 < 2^24, m, n >= 64 and
- * m n k >= 2^21 go to the tensor cores -- p <= 17 to the grouped e4m3 kernel (operands first
- * copied to 16-byte row strides and range-checked in one launch), 17 < p <= 127 to the bf16
- * kernel (operands converted and range-checked in one launch), up to 64 products per launch;
- * everything else runs in ONE persistent kernel launch whose CTAs take tiles from a device
+ * Sec. 7.6.1).  Run all `count` instances: matrix products with p <= 17 and k (p-1)^2 < 2^23, or
+ * p <= 31 and 2 k (p/2)^2 + p < 2^23, whose sizes rounded up to 128 x 256 x 32 blocks give >= 2^21
+ * and at most 32 times their own MACs go to the e4m3 tensor-core kernel (one launch first lays
+ * every such operand out as swizzled 16 KB tiles, residues range-checked and, in the second
+ * case, centred to |c| <= p/2; then
+ * one persistent launch per 4096 products; any row stride or alignment); those with
+ * 31 < p <= 127, m, n >= 64, m n k >= 2^21 and k (p-1)^2 < 2^24 to the bf16 kernel (operands
+ * converted and range-checked in one launch, up to 64 products per launch); everything else runs in ONE persistent kernel launch whose CTAs take tiles from a device
  * work queue (an atomic counter over a tile list the host planner sorts by cost), packing
  * degree e and word chosen per (p, k) by the planner and the autotuner cache in the context.
  * `instances` is a HOST array; every instance is checked before anything is enqueued; the

@@ -436,6 +436,33 @@ fp_status launch_mm_f8_grouped(fp_ctx ctx, const fp_mm_problem* const* pr, size_
 uint64_t t16_batch_bytes(const fp_mm_problem* const* pr, size_t count);
 fp_status launch_mm_t16_plain_batch(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, uint8_t* scratch,
                                     cudaStream_t st);
+// Pre-tiled e4m3 products (the tensor-core share of an uneven batch).  Each operand is laid out
+// by the batch's pack pass as 16 KB blocks of 128 x 128 bytes, each in the 128-byte swizzle of
+// a shared-memory stage (16-byte chunk c of block row r at chunk position c ^ (r & 7)), holding
+// centred residues (|c| <= p/2 <= 15) as signed e4m3 codes and zero outside the matrix:
+//   A (m x k, K-major):  block (mb, kt) = rows 128 mb.., k bytes 128 kt..
+//                        at At + (mb ktiles + kt) F8_BLOCK,
+//   B (k x n, MN-major): block (nb, kt, h) = k rows 128 kt.., columns 256 nb + 128 h..
+//                        at Bt + ((nb ktiles + kt) 2 + h) F8_BLOCK.
+static constexpr int F8_BLOCK = 16384;
+static constexpr int F8_PRE_CAP = 4096;     // problems per launch
+struct F8PreProb {
+  const uint8_t* At;
+  const uint8_t* Bt;
+  uint8_t* C;
+  int m, n, ldc;
+  int ktiles;          // ceil(k / 128)
+  int klast;           // K = 32 steps holding some of the last k tile (1..4)
+  int tn;              // column blocks ceil(n / 256)
+  uint32_t p;
+  float c18;           // 2^18 RU(1/p)
+  float pm18;          // -p 2^-18
+  float off18;         // p T 2^-18 with p T >= k (p/2)^2 (makes every sum non-negative)
+};
+// prob, tile0: nprob <= F8_PRE_CAP entries in device memory, tile0 ascending from 0 (the first
+// tile of each problem, tiles of a problem in row-block-major order), total tiles.  Lock held.
+fp_status launch_mm_f8_pretiled(fp_ctx ctx, const F8PreProb* prob, const int* tile0, int nprob, int total,
+                                cudaStream_t st);
 // lock held; prechecked: the caller has range-checked every A and B (the kernel skips its check)
 fp_status launch_mm_f8_grouped_locked(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st,
                                       bool prechecked);

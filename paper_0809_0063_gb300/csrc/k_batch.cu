@@ -502,111 +502,191 @@ static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st) {
 
 // ---------------------------------------------------------------- tensor-core share of a batch
 //
-// Matrix products whose residues are exact e4m3 values (p <= 17), whose fp32 sums stay below
-// 2^24 (k (p-1)^2 < 2^24) and that fill at least part of a 128 x 256 tile run on the grouped
-// tcgen05 kernel (k_mm_f8g) instead of the mma.sync tiles of k_batch: in the uneven benchmark
-// batch they hold two thirds of the MACs.  TMA needs operand rows at 16-byte strides, so one
-// launch of k_pad_rows first copies every such A (m x k) and B (k x n) that is not already laid
-// out that way into context scratch with rows rounded up to 16 bytes (the pad bytes are never
-// read: the tensor maps' extents stop at k and n).  The same launch range-checks every routed
-// operand (those used in place by a read-only pass), so k_mm_f8g skips its own check: with few
-// tiles per problem that check would read whole panels from one CTA.
+// Matrix products whose residues are exact e4m3 values as they stand (p <= 17, unsigned sums
+// k (p-1)^2 < 2^23) or once centred (p <= 31: |c| <= p/2 <= 15, 2 k (p/2)^2 + p < 2^23), so that
+// the sums stay in FDIV's range (see k_tcg.cu), and that fill enough of
+// their 128 x 256 x 32 blocks run on the pre-tiled tcgen05 kernel (k_mm_f8g_pre) instead of the
+// mma.sync tiles of k_batch; larger p (up to 127, k (p-1)^2 < 2^24, m, n >= 64) on the bf16
+// kernel.  One
+// launch of k_tile_pack lays every routed operand out as the 16 KB swizzled blocks that kernel's
+// stages copy (layout in fpdqt_internal.cuh): residues range-checked and centred, zero outside
+// the matrix, so the caller's arrays may have any row stride and alignment.  Then one
+// tensor-core launch takes the whole share (up to F8_PRE_CAP products per launch).
 
 static constexpr uint64_t BT_TC_MIN_MACS = 1ull << 21;
 
-static constexpr uint32_t JOB_SMEM_MAX = 8192;   // 64 KB of first rows
-
-struct PadJob {
-  const uint8_t* src;
-  uint8_t* dst;       // null: range check only
-  uint32_t row_bytes, src_ld, dst_ld, p;
-  uint64_t row0;      // first row of this job in the launch's flat row numbering
+struct TileJob {
+  const uint8_t* src;  // rows x cols residues, leading dimension ld
+  uint8_t* dst;        // the job's first 16 KB block
+  uint32_t rows, cols, ld, p;
+  uint32_t nkt;        // k tiles of the product
+  uint32_t is_b;       // 0: A, blocks (mb, kt); 1: B, blocks (nb, kt, h)
+  uint32_t blk0;       // first block of the job in the launch's numbering
+  uint32_t centre;     // 1: residues > p/2 become the codes of r - p (p > 17, or sums too large)
 };
 
-// One warp per row (grid-stride over all jobs' rows).  Destination words are built by funnel
-// shifts of the aligned source words that hold them; a source word is read only if it holds a
-// byte of the row, so no read leaves the source allocation.  Range check of the row's bytes: a
-// residue r >= p (p <= 17) has bit 7 set in r | (r + 128 - p); bytes past the row are masked.
-__global__ void __launch_bounds__(256) k_pad_rows(const PadJob* __restrict__ jobs, uint32_t njobs, uint64_t rows,
-                                                  uint32_t* err) {
-  const uint32_t lane = threadIdx.x & 31u;
+// The 16 bytes of a row from column col on (nvalid of them belong to the row; none when
+// nvalid <= 0), zero past the row.  Only the aligned 4-byte words that hold a byte of the row are
+// read (so no read leaves the row's allocation), all issued before any is used.
+__device__ __forceinline__ void chunk_load(const uint8_t* rowp, int col, int nvalid, uint32_t (&w)[4]) {
+  const uint8_t* s = rowp + col;
+  const uint32_t off = (uint32_t)((uintptr_t)s & 3u);
+  const uint32_t* b = reinterpret_cast<const uint32_t*>(s - off);
+  const int span = (int)off + min(nvalid, 16);          // bytes from b that belong to the row
+  uint32_t v[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) v[j] = 4 * j < span ? __ldg(b + j) : 0u;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t x = __funnelshift_r(v[j], v[j + 1], 8 * off);   // off = 0: v[j]
+    const int keep = nvalid - 4 * j;                               // bytes of word j in the row
+    w[j] = keep >= 4 ? x : (keep <= 0 ? 0u : x & ((1u << (8 * keep)) - 1u));
+  }
+}
+
+// One CTA per contiguous range of 16 KB blocks (its first job found once by binary search, then
+// advanced block by block).  Thread t writes chunks t, t + 256, t + 512, t + 768 of a block
+// (coalesced): chunk o is block row o / 8 at swizzled position o % 8, i.e. source chunk
+// (o % 8) ^ (row % 8) of that row.  Every byte is range-checked (r < p: r + 128 - p has bit 7
+// clear) and, for centred jobs, r > p/2 becomes the e4m3 code of -(p - r) (sign bit | (p - r)).
+// Block rows of A past m and chunks of B past n are not written: they only reach accumulator
+// rows or columns the epilogue never stores.  The inner-dimension padding (A columns, B rows
+// past k) is written as zeros: it meets every output.
+__global__ void __launch_bounds__(256) k_tile_pack(const TileJob* __restrict__ jobs, uint32_t njobs, uint32_t nblocks,
+                                                   uint32_t* err) {
+  const uint32_t per = (nblocks + gridDim.x - 1) / gridDim.x;
+  const uint32_t b0 = blockIdx.x * per, b1 = min(nblocks, b0 + per);
+  if (b0 >= b1) return;
+  uint32_t jb = 0, hi = njobs - 1;               // the last job whose first block is <= b0
+  while (jb < hi) {
+    const uint32_t mid = (jb + hi + 1) >> 1;
+    if (jobs[mid].blk0 <= b0) jb = mid;
+    else hi = mid - 1;
+  }
   uint32_t bad = 0;
-  // the jobs' first rows in shared memory (when they fit the launch's dynamic allocation) so
-  // that the per-row search for its job stays on chip
-  extern __shared__ uint64_t s_row0[];
-  const bool in_smem = njobs <= JOB_SMEM_MAX;
-  if (in_smem)
-    for (uint32_t i = threadIdx.x; i < njobs; i += blockDim.x) s_row0[i] = jobs[i].row0;
-  __syncthreads();
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t r = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
-    uint32_t lo = 0, hi = njobs - 1;             // the last job with row0 <= r
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi + 1) >> 1;
-      if ((in_smem ? s_row0[mid] : jobs[mid].row0) <= r) lo = mid;
-      else hi = mid - 1;
+  for (uint32_t bi = b0; bi < b1; ++bi) {
+    while (jb + 1 < njobs && jobs[jb + 1].blk0 <= bi) ++jb;
+    const TileJob& J = jobs[jb];
+    const uint32_t local = bi - J.blk0, nkt = J.nkt, is_b = J.is_b;
+    uint32_t rb, cb;                            // block row (128 rows), block column (128 bytes)
+    if (!is_b) {
+      rb = local / nkt;
+      cb = local - rb * nkt;
+    } else {
+      const uint32_t nb = local / (2 * nkt), rem = local - nb * 2 * nkt;
+      rb = rem >> 1;
+      cb = 2 * nb + (rem & 1u);
     }
-    const PadJob J = jobs[lo];
-    const uint64_t row = r - J.row0;
-    const uint8_t* src = J.src + row * J.src_ld;
-    uint32_t* dst = J.dst ? reinterpret_cast<uint32_t*>(J.dst + row * J.dst_ld) : nullptr;
-    const uint32_t off = (uint32_t)((uintptr_t)src & 3u);
-    const uint32_t* base = reinterpret_cast<const uint32_t*>(src - off);
-    const uint32_t nw = (J.row_bytes + 3) / 4;
-    const uint32_t pk = 0x01010101u * (128u - J.p);
-    for (uint32_t c = lane; c < nw; c += 32) {
-      const uint32_t a0 = base[c];
-      const uint32_t a1 = (off != 0 && 4 * c + 4 - off < J.row_bytes) ? base[c + 1] : 0u;
-      const uint32_t w = off ? __funnelshift_r(a0, a1, 8 * off) : a0;
-      const uint32_t nb = J.row_bytes - 4 * c;                       // >= 1
-      const uint32_t wv = nb >= 4 ? w : w & ((1u << (8 * nb)) - 1u);
-      bad |= wv | (wv + pk);
-      if (J.dst) dst[c] = w;
+    const uint8_t* src = J.src;
+    const uint32_t rows = J.rows, cols = J.cols, ld = J.ld, p = J.p, centre = J.centre;
+    uint4* dst = reinterpret_cast<uint4*>(J.dst + (size_t)local * F8_BLOCK);
+    const uint32_t pk = 0x01010101u * (128u - p), hk = 0x01010101u * (127u - (p >> 1)), P4 = 0x01010101u * p;
+    uint32_t w[4][4];
+    bool st[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t o = threadIdx.x + 256u * i;
+      const uint32_t r = o >> 3, c = (o & 7u) ^ (r & 7u);
+      const uint32_t row = rb * 128 + r, col = cb * 128 + 16 * c;
+      const bool row_in = row < rows;
+      st[i] = is_b ? (col < cols || !row_in) : row_in;
+      chunk_load(src + (size_t)(row_in ? row : 0) * ld, (int)col, row_in ? (int)cols - (int)col : -64, w[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t x = w[i][j];
+        bad |= x | (x + pk);
+        if (centre) {
+          const uint32_t gt = (((x + hk) & 0x80808080u) >> 7) * 0xFFu;   // 0xFF where r > p/2
+          w[i][j] = (gt & ((P4 - x) | 0x80808080u)) | (~gt & x);
+        }
+      }
+      if (st[i]) dst[threadIdx.x + 256u * i] = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
     }
   }
   if (bad & 0x80808080u) flag_error(err, ERR_RANGE);
 }
 
-// 1: e4m3 products (p <= 17); 2: bf16 products (17 < p <= 127, residues exact in bf16 and the
-// conversion's range check valid); 0: the batch kernel.
+// 1: pre-tiled e4m3 products (p <= 31); 2: bf16 products (31 < p <= 127, residues exact in bf16
+// and the conversion's range check valid); 0: the batch kernel.  The e4m3 kernel computes whole
+// 128 x 256 x 32 blocks: a product goes there when those padded MACs are at least 2^21 and at
+// most 32 times its own (a thin product still runs far faster there than on the mma.sync tiles
+// of the batch kernel).
+static bool f8_unsigned_ok(uint32_t p, uint64_t k) { return p <= 17 && k * (p - 1) * (p - 1) < (1ull << 23); }
+static bool f8_centred_ok(uint32_t p, uint64_t k) { return p <= 31 && 2 * k * (p / 2) * (p / 2) + p < (1ull << 23); }
+
 static int batch_tc_route(const fp_instance& x) {
-  const bool big = x.kind == 0 && x.A && x.B && x.C && x.p >= 2 && x.p <= 127 && is_prime(x.p) && x.m >= 64 &&
-                   x.n >= 64 && x.k >= 1 && x.m <= (1u << 30) && x.n <= (1u << 30) && x.k <= (1u << 30) &&
-                   (uint64_t)x.k * (x.p - 1) * (x.p - 1) < (1ull << 24) && (uint64_t)x.m * x.n * x.k >= BT_TC_MIN_MACS;
-  return big ? (x.p <= 17 ? 1 : 2) : 0;
+  const bool mm = x.kind == 0 && x.A && x.B && x.C && x.p >= 2 && x.p <= 127 && is_prime(x.p) && x.k >= 1 &&
+                  x.m <= (1u << 30) && x.n <= (1u << 30) && x.k <= (1u << 30);
+  if (!mm) return 0;
+  const unsigned __int128 macs = (unsigned __int128)((uint64_t)x.m * x.n) * x.k;
+  if (f8_unsigned_ok(x.p, x.k) || f8_centred_ok(x.p, x.k)) {
+    const unsigned __int128 padded = (unsigned __int128)(((x.m + 127ull) & ~127ull) * ((x.n + 255ull) & ~255ull)) *
+                                     ((x.k + 31ull) & ~31ull);
+    return padded >= BT_TC_MIN_MACS && padded <= 32 * macs ? 1 : 0;
+  }
+  const bool big = x.m >= 64 && x.n >= 64 && macs >= BT_TC_MIN_MACS;
+  return big && (uint64_t)x.k * (x.p - 1) * (x.p - 1) < (1ull << 24) ? 2 : 0;
 }
 
-// The tensor-core share: e4m3 products (pad copies in one launch, grouped k_mm_f8g launches) and
-// bf16 products (conversion in one launch, grouped k_mm_t16 launches), both from one scratch
-// allocation.  Lock held.
+// The tensor-core share: e4m3 products (pack in one launch, then one pre-tiled launch per
+// F8_PRE_CAP products) and bf16 products (conversion in one launch, grouped k_mm_t16 launches),
+// from one scratch allocation.  Lock held.
 static fp_status batch_run_tc(fp_ctx ctx, const std::vector<const fp_instance*>& tc,
                               const std::vector<const fp_instance*>& t16, cudaStream_t st) {
-  auto up16 = [](uint64_t x) { return (x + 15) & ~(uint64_t)15; };
   auto up256 = [](uint64_t x) { return (x + 255) & ~(uint64_t)255; };
-  std::vector<fp_mm_problem> prob(tc.size());
-  std::vector<PadJob> jobs;
-  std::vector<uint64_t> a_off(tc.size(), 0), b_off(tc.size(), 0);   // scratch offsets, 0 = in place
-  uint64_t bytes = up256(2 * tc.size() * sizeof(PadJob)), rows = 0;
-  for (size_t i = 0; i < tc.size(); ++i) {
-    const fp_instance& x = *tc[i];
-    fp_mm_problem& q = prob[i];
-    q = fp_mm_problem{x.p, (int)x.m, (int)x.n, (int)x.k, x.A, (int)x.k, x.B, (int)x.n, x.C, (int)x.n};
-    // every operand gets a job: a padded copy, or (already 16-byte rows) a range check only
-    if (((uintptr_t)x.A & 15u) != 0 || x.k % 16 != 0) {
-      a_off[i] = bytes;
-      q.lda = (int)up16(x.k);
-      bytes += up256((uint64_t)x.m * up16(x.k));
+  // longest inner dimension first: the persistent schedule starts the longest tiles earliest
+  std::vector<const fp_instance*> v(tc);
+  std::stable_sort(v.begin(), v.end(), [](const fp_instance* a, const fp_instance* b) { return a->k > b->k; });
+  const size_t np = v.size();
+  // scratch: [problems | first tiles | pack jobs] (one upload) | operand blocks | bf16 share
+  const uint64_t o_tile0 = up256(np * sizeof(F8PreProb));
+  const uint64_t o_jobs = o_tile0 + up256(np * sizeof(int));
+  const uint64_t desc = o_jobs + up256(2 * np * sizeof(TileJob));
+  const uint64_t o_blocks = (desc + 1023) & ~(uint64_t)1023;
+  std::vector<uint8_t> h(desc);
+  F8PreProb* prob = reinterpret_cast<F8PreProb*>(h.data());
+  int* tile0 = reinterpret_cast<int*>(h.data() + o_tile0);
+  TileJob* jobs = reinterpret_cast<TileJob*>(h.data() + o_jobs);
+  std::vector<int> chunk_tiles;                 // tiles of each launch of F8_PRE_CAP problems
+  uint64_t nblk = 0;
+  int tiles = 0;
+  for (size_t i = 0; i < np; ++i) {
+    const fp_instance& x = *v[i];
+    if (i % F8_PRE_CAP == 0) {
+      if (i) chunk_tiles.push_back(tiles);
+      tiles = 0;
     }
-    jobs.push_back(PadJob{x.A, nullptr, x.k, x.k, (uint32_t)q.lda, x.p, rows});
-    rows += x.m;
-    if (((uintptr_t)x.B & 15u) != 0 || x.n % 16 != 0) {
-      b_off[i] = bytes;
-      q.ldb = (int)up16(x.n);
-      bytes += up256((uint64_t)x.k * up16(x.n));
-    }
-    jobs.push_back(PadJob{x.B, nullptr, x.n, x.n, (uint32_t)q.ldb, x.p, rows});
-    rows += x.k;
+    const uint32_t kt = (x.k + 127) / 128, tm = (x.m + 127) / 128, tn = (x.n + 255) / 256;
+    const uint64_t a_blk = nblk, b_blk = a_blk + (uint64_t)tm * kt;
+    nblk = b_blk + (uint64_t)tn * kt * 2;
+    // residues as they stand (codes 0..16) while the unsigned sums stay below 2^23, else centred
+    const uint32_t centre = f8_unsigned_ok(x.p, x.k) ? 0u : 1u;
+    jobs[2 * i] = TileJob{x.A, (uint8_t*)(uintptr_t)a_blk, x.m, x.k, x.k, x.p, kt, 0u, (uint32_t)a_blk, centre};
+    jobs[2 * i + 1] = TileJob{x.B, (uint8_t*)(uintptr_t)b_blk, x.k, x.n, x.n, x.p, kt, 1u, (uint32_t)b_blk, centre};
+    const uint64_t hh = x.p / 2, bound = (uint64_t)x.k * hh * hh;
+    const uint64_t pt = centre ? (bound + x.p - 1) / x.p * x.p : 0;   // p T >= k (p/2)^2
+    F8PreProb& q = prob[i];
+    q.At = (const uint8_t*)(uintptr_t)a_blk;
+    q.Bt = (const uint8_t*)(uintptr_t)b_blk;
+    q.C = x.C;
+    q.m = (int)x.m;
+    q.n = (int)x.n;
+    q.ldc = (int)x.n;
+    q.ktiles = (int)kt;
+    q.klast = (int)((x.k - 128 * (kt - 1) + 31) / 32);
+    q.tn = (int)tn;
+    q.p = x.p;
+    q.c18 = make_redq(x.p, 1, 1).invp_f * 262144.0f;   // RU(1/p) scaled by 2^18 (exact)
+    q.pm18 = -(float)x.p / 262144.0f;
+    q.off18 = (float)pt / 262144.0f;                   // exact: p T < 2^23
+    tile0[i] = tiles;
+    tiles += (int)(tm * tn);
   }
+  if (np) chunk_tiles.push_back(tiles);
+  FP_CHECK(nblk < (1ull << 32), FP_EINVAL, "fp_batch_run: tensor-core share too large for one call");
   std::vector<fp_mm_problem> prob16(t16.size());
   std::vector<const fp_mm_problem*> ptr16(t16.size());
   for (size_t i = 0; i < t16.size(); ++i) {
@@ -614,36 +694,38 @@ static fp_status batch_run_tc(fp_ctx ctx, const std::vector<const fp_instance*>&
     prob16[i] = fp_mm_problem{x.p, (int)x.m, (int)x.n, (int)x.k, x.A, (int)x.k, x.B, (int)x.n, x.C, (int)x.n};
     ptr16[i] = &prob16[i];
   }
-  const uint64_t off16 = (bytes + 1023) & ~(uint64_t)1023;
-  const uint64_t total = t16.empty() ? bytes : off16 + t16_batch_bytes(ptr16.data(), ptr16.size());
+  const uint64_t f8_end = o_blocks + nblk * F8_BLOCK;
+  const uint64_t off16 = (f8_end + 1023) & ~(uint64_t)1023;
+  const uint64_t total = t16.empty() ? f8_end : off16 + t16_batch_bytes(ptr16.data(), ptr16.size());
   {
     fp_status s = ensure_scratch(ctx, total + 1024, 0, st);
     if (s != FP_OK) return s;
   }
-  if (!tc.empty()) {
-    fp_status s = FP_OK;
-    uint8_t* base = (uint8_t*)ctx->scratch;
-    for (size_t i = 0; i < tc.size(); ++i) {   // jobs 2i (A) and 2i + 1 (B)
-      if (a_off[i]) { prob[i].A = base + a_off[i]; jobs[2 * i].dst = base + a_off[i]; }
-      if (b_off[i]) { prob[i].B = base + b_off[i]; jobs[2 * i + 1].dst = base + b_off[i]; }
+  uint8_t* base = (uint8_t*)ctx->scratch;
+  if (np) {
+    uint8_t* blocks = base + o_blocks;
+    for (size_t i = 0; i < np; ++i) {   // block indices -> device addresses
+      prob[i].At = blocks + (uintptr_t)prob[i].At * F8_BLOCK;
+      prob[i].Bt = blocks + (uintptr_t)prob[i].Bt * F8_BLOCK;
+      jobs[2 * i].dst = blocks + (uintptr_t)jobs[2 * i].dst * F8_BLOCK;
+      jobs[2 * i + 1].dst = blocks + (uintptr_t)jobs[2 * i + 1].dst * F8_BLOCK;
     }
-    s = upload_staged(ctx, 0, base, jobs.data(), jobs.size() * sizeof(PadJob), st);
+    fp_status s = upload_staged(ctx, 0, base, h.data(), desc, st);
     if (s != FP_OK) return s;
-    const int grid = (int)std::min<uint64_t>((rows + 7) / 8, (uint64_t)ctx->num_sms * 8);
-    const size_t jsm = std::min<size_t>(jobs.size(), JOB_SMEM_MAX) * sizeof(uint64_t);
-    FP_CUDA(cudaFuncSetAttribute(k_pad_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(JOB_SMEM_MAX * 8)));
-    FP_LAUNCH(ctx, "k_pad_rows", st,
-              k_pad_rows<<<grid, 256, jsm, st>>>((const PadJob*)base, (uint32_t)jobs.size(), rows, ctx->d_err));
+    const uint32_t njobs = (uint32_t)(2 * np);
+    const int grid = (int)std::min<uint64_t>(nblk, (uint64_t)ctx->num_sms * 8);
+    FP_LAUNCH(ctx, "k_tile_pack", st,
+              k_tile_pack<<<grid, 256, 0, st>>>((const TileJob*)(base + o_jobs), njobs, (uint32_t)nblk, ctx->d_err));
     FP_CUDA(cudaGetLastError());
-  }
-  if (!tc.empty()) {
-    std::vector<const fp_mm_problem*> ptr(prob.size());
-    for (size_t i = 0; i < prob.size(); ++i) ptr[i] = &prob[i];
-    fp_status s = launch_mm_f8_grouped_locked(ctx, ptr.data(), ptr.size(), st, true);
-    if (s != FP_OK) return s;
+    for (size_t c = 0; c < chunk_tiles.size(); ++c) {
+      const size_t i0 = c * F8_PRE_CAP, cnt = std::min<size_t>(F8_PRE_CAP, np - i0);
+      s = launch_mm_f8_pretiled(ctx, (const F8PreProb*)base + i0, (const int*)(base + o_tile0) + i0, (int)cnt,
+                                chunk_tiles[c], st);
+      if (s != FP_OK) return s;
+    }
   }
   if (t16.empty()) return FP_OK;
-  return launch_mm_t16_plain_batch(ctx, ptr16.data(), ptr16.size(), (uint8_t*)ctx->scratch + off16, st);
+  return launch_mm_t16_plain_batch(ctx, ptr16.data(), ptr16.size(), base + off16, st);
 }
 
 }  // namespace fpd

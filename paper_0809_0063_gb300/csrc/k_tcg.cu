@@ -32,6 +32,7 @@
 // the context's sticky flag reports ERR_TIMEOUT.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "fpdqt_internal.cuh"
@@ -78,6 +79,19 @@ struct GParamsT {
 using GParams = GParamsT<FP_GROUP_MAX>;
 static_assert(sizeof(GParamsT<G_BATCH_CAP>) < 32000, "kernel parameter block limit");
 
+// Pre-tiled problems (the tensor-core share of an uneven batch, layout in fpdqt_internal.cuh):
+// a stage is two plain bulk copies, no tensor map, so any row stride or alignment of the
+// caller's arrays is allowed; the problem list lives in global memory and its first-tile
+// indices in shared memory after the stages, so one launch takes up to F8_PRE_CAP problems.
+using BProb = F8PreProb;
+struct BParams {
+  const BProb* prob;
+  const int* tile0;
+  int nprob;
+  int total;
+};
+static_assert(G_A_BYTES == F8_BLOCK && G_B_BYTES == 2 * F8_BLOCK, "pre-tiled block size");
+
 struct GTile {
   const GProb* pr;
   int m0, n0, mb, nb;
@@ -100,6 +114,36 @@ __device__ __forceinline__ GTile g_tile(const GParamsT<CAP>& g, int t) {
   x.m0 = x.mb * G_BM;
   x.n0 = x.nb * G_BN;
   return x;
+}
+
+struct BTile {
+  const BProb* pr;
+  int m0, n0, mb, nb;
+};
+
+__device__ __forceinline__ BTile b_tile(const BParams& g, const int* s_tile0, int t) {
+  int i = 0, hi = g.nprob - 1;      // the last problem whose first tile is <= t
+  while (i < hi) {
+    const int mid = (i + hi + 1) >> 1;
+    if (s_tile0[mid] <= t) i = mid;
+    else hi = mid - 1;
+  }
+  BTile x;
+  x.pr = g.prob + i;
+  const int local = t - s_tile0[i];
+  const int tn = __ldg(&x.pr->tn);
+  x.mb = local / tn;
+  x.nb = local - x.mb * tn;
+  x.m0 = x.mb * G_BM;
+  x.n0 = x.nb * G_BN;
+  return x;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(bar))
+               : "memory");
 }
 
 // Bit 7 of a byte of the result is set where one of the `valid` bytes at src (at most 16;
@@ -136,8 +180,13 @@ __device__ __forceinline__ int g_wave_tile(int w) {
   return w * (int)gridDim.x + ((w & 1) ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x);
 }
 
-template <int CAP>
-__global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__ GParamsT<CAP> g, uint32_t* err) {
+// PRE = false: problems in the grid-constant block, operands loaded by TMA from the caller's
+// arrays.  PRE = true: pre-tiled problems from global memory (BParams), stages by bulk copies.
+template <int CAP, bool PRE>
+using GPar = typename std::conditional<PRE, BParams, GParamsT<CAP>>::type;
+
+template <int CAP, bool PRE>
+__global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__ GPar<CAP, PRE> g, uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t g_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)g_smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + G_STAGES * G_STAGE_BYTES);
@@ -148,9 +197,13 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
   uint64_t* doneb = drainb + 1;          // every epilogue warp finished with TMEM
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(doneb + 1);
   volatile uint32_t* abort_flag = tmem_slot + 1;
+  // PRE: the problems' first tiles, after the epilogue's store buffers
+  int* const s_tile0 = reinterpret_cast<int*>(smem + G_STAGES * G_STAGE_BYTES + 256 + G_EPI_STAGE_BYTES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr uint32_t TMEM_COLS = 512;
+  if constexpr (PRE)
+    for (int i = threadIdx.x; i < g.nprob; i += G_THREADS) s_tile0[i] = __ldg(g.tile0 + i);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < G_STAGES; ++s) {
@@ -182,19 +235,37 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
       uint32_t it = 0;              // k tiles issued by this CTA (all its tiles)
       bool stop = false;
       for (int w = 0, t = g_wave_tile(0); t < g.total && !stop; t = g_wave_tile(++w)) {
-        const GTile x = g_tile(g, t);
-        for (int kt = 0; kt < x.pr->ktiles; ++kt, ++it) {
-          const int s = (int)(it % G_STAGES);
-          if (*abort_flag || !mbar_wait(&empty[s], ((it / G_STAGES) & 1u) ^ 1u, abort_flag)) {
-            stop = true;
-            break;
+        if constexpr (PRE) {
+          const BTile x = b_tile(g, s_tile0, t);
+          const int ktiles = __ldg(&x.pr->ktiles);
+          const uint8_t* a = x.pr->At + (size_t)x.mb * ktiles * G_A_BYTES;
+          const uint8_t* b = x.pr->Bt + (size_t)x.nb * ktiles * G_B_BYTES;
+          for (int kt = 0; kt < ktiles; ++kt, ++it) {
+            const int s = (int)(it % G_STAGES);
+            if (*abort_flag || !mbar_wait(&empty[s], ((it / G_STAGES) & 1u) ^ 1u, abort_flag)) {
+              stop = true;
+              break;
+            }
+            uint8_t* sa = smem + s * G_STAGE_BYTES;
+            mbar_expect_tx(&full[s], G_STAGE_BYTES);
+            bulk_load(sa, a + (size_t)kt * G_A_BYTES, G_A_BYTES, &full[s]);
+            bulk_load(sa + G_A_BYTES, b + (size_t)kt * G_B_BYTES, G_B_BYTES, &full[s]);
           }
-          uint8_t* sa = smem + s * G_STAGE_BYTES;
-          uint8_t* sb = sa + G_A_BYTES;
-          mbar_expect_tx(&full[s], G_STAGE_BYTES);
-          tma_load_2d(sa, &x.pr->ta, kt * G_BK, x.m0, &full[s]);
-          tma_load_2d(sb, &x.pr->tb, x.n0, kt * G_BK, &full[s]);
-          tma_load_2d(sb + G_B_BYTES / 2, &x.pr->tb, x.n0 + 128, kt * G_BK, &full[s]);
+        } else {
+          const GTile x = g_tile(g, t);
+          for (int kt = 0; kt < x.pr->ktiles; ++kt, ++it) {
+            const int s = (int)(it % G_STAGES);
+            if (*abort_flag || !mbar_wait(&empty[s], ((it / G_STAGES) & 1u) ^ 1u, abort_flag)) {
+              stop = true;
+              break;
+            }
+            uint8_t* sa = smem + s * G_STAGE_BYTES;
+            uint8_t* sb = sa + G_A_BYTES;
+            mbar_expect_tx(&full[s], G_STAGE_BYTES);
+            tma_load_2d(sa, &x.pr->ta, kt * G_BK, x.m0, &full[s]);
+            tma_load_2d(sb, &x.pr->tb, x.n0, kt * G_BK, &full[s]);
+            tma_load_2d(sb + G_B_BYTES / 2, &x.pr->tb, x.n0 + 128, kt * G_BK, &full[s]);
+          }
         }
       }
       // every armed stage must have landed before the CTA may exit (its shared memory is reused)
@@ -210,12 +281,20 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
       bool stop = false;
       int lt = 0;                   // tiles of this CTA so far
       for (int w = 0, t = g_wave_tile(0); t < g.total && !stop; t = g_wave_tile(++w), ++lt) {
-        const GTile x = g_tile(g, t);
+        int ktiles, klast;
+        if constexpr (PRE) {
+          const BTile x = b_tile(g, s_tile0, t);
+          ktiles = __ldg(&x.pr->ktiles);
+          klast = __ldg(&x.pr->klast);
+        } else {
+          ktiles = g_tile(g, t).pr->ktiles;
+          klast = 4;
+        }
         const int buf = lt & 1;
         if (lt >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((lt - 2) >> 1) & 1u, abort_flag)) break;
         tc_fence_after();
         const uint32_t dtm = tmem + (uint32_t)(buf * 256);
-        for (int kt = 0; kt < x.pr->ktiles; ++kt, ++it) {
+        for (int kt = 0; kt < ktiles; ++kt, ++it) {
           const int s = (int)(it % G_STAGES);
           if (!mbar_wait(&full[s], (it / G_STAGES) & 1u, abort_flag)) {
             stop = true;
@@ -225,9 +304,13 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
           const uint8_t* sa = smem + s * G_STAGE_BYTES;
           const uint8_t* sb = sa + G_A_BYTES;
           const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_mn_sw128(sb, G_B_BYTES / 2);
+          // K = 32 per MMA: A +32 bytes in the row, B +32 rows; the last k tile of a pre-tiled
+          // problem issues only the steps that hold some of its k (the rest are zero padding)
+          const int nk = kt == ktiles - 1 ? klast : 4;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)   // K = 32 per MMA: A +32 bytes in the row, B +32 rows
-            mma_f8(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 256), idesc, (kt | kk) ? 1u : 0u);
+          for (int kk = 0; kk < 4; ++kk)
+            if (kk < nk)
+              mma_f8(dtm, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 256), idesc, (kt | kk) ? 1u : 0u);
           mma_commit(&empty[s]);
         }
         if (!stop) mma_commit(&tfull[buf]);
@@ -250,26 +333,37 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
     int lt = 0;
     for (int w = 0, t = g_wave_tile(0); t < g.total; t = g_wave_tile(++w), ++lt) {
       const int buf = lt & 1;
-      const GTile x = g_tile(g, t);
-      const GProb& pr = *x.pr;
-      if (!pr.checked) {
-        // range check: a residue byte r >= p (p <= 17) has bit 7 set in r | (r + 128 - p),
-        // with no carry between bytes unless bit 7 of the lower byte is already set
-        const uint32_t pk = 0x01010101u * (128u - pr.p);
-        const uint32_t kc = (uint32_t)(pr.k + 15) >> 4;                  // 16-byte chunks per A row
-        const uint32_t a_rows = (uint32_t)min(G_BM, pr.m - x.m0);
-        const uint32_t a_units = a_rows * kc, a_per = (a_units + pr.tn - 1) / pr.tn;
-        const uint32_t a_lo = min(a_units, (uint32_t)x.nb * a_per), a_hi = min(a_units, a_lo + a_per);
-        for (uint32_t u = a_lo + tid; u < a_hi; u += 256) {
-          const uint32_t r = u / kc, c = u - r * kc;
-          bad |= range_bits(pr.A + (size_t)(x.m0 + r) * pr.lda + 16 * c, pr.k - 16 * (int)c, pk);
-        }
-        const uint32_t bc = (uint32_t)(min(G_BN, pr.n - x.n0) + 15) >> 4;  // 16-byte chunks per B row
-        const uint32_t b_units = (uint32_t)pr.k * bc, b_per = (b_units + pr.tm - 1) / pr.tm;
-        const uint32_t b_lo = min(b_units, (uint32_t)x.mb * b_per), b_hi = min(b_units, b_lo + b_per);
-        for (uint32_t u = b_lo + tid; u < b_hi; u += 256) {
-          const uint32_t r = u / bc, c = u - r * bc;
-          bad |= range_bits(pr.B + (size_t)r * pr.ldb + x.n0 + 16 * c, pr.n - x.n0 - 16 * (int)c, pk);
+      int m0, n0;
+      const BProb* bpr = nullptr;
+      if constexpr (PRE) {
+        const BTile x = b_tile(g, s_tile0, t);
+        m0 = x.m0;
+        n0 = x.n0;
+        bpr = x.pr;
+      } else {
+        const GTile x = g_tile(g, t);
+        m0 = x.m0;
+        n0 = x.n0;
+        const GProb& pr = *x.pr;
+        if (!pr.checked) {
+          // range check: a residue byte r >= p (p <= 17) has bit 7 set in r | (r + 128 - p),
+          // with no carry between bytes unless bit 7 of the lower byte is already set
+          const uint32_t pk = 0x01010101u * (128u - pr.p);
+          const uint32_t kc = (uint32_t)(pr.k + 15) >> 4;                  // 16-byte chunks per A row
+          const uint32_t a_rows = (uint32_t)min(G_BM, pr.m - x.m0);
+          const uint32_t a_units = a_rows * kc, a_per = (a_units + pr.tn - 1) / pr.tn;
+          const uint32_t a_lo = min(a_units, (uint32_t)x.nb * a_per), a_hi = min(a_units, a_lo + a_per);
+          for (uint32_t u = a_lo + tid; u < a_hi; u += 256) {
+            const uint32_t r = u / kc, c = u - r * kc;
+            bad |= range_bits(pr.A + (size_t)(x.m0 + r) * pr.lda + 16 * c, pr.k - 16 * (int)c, pk);
+          }
+          const uint32_t bc = (uint32_t)(min(G_BN, pr.n - x.n0) + 15) >> 4;  // 16-byte chunks per B row
+          const uint32_t b_units = (uint32_t)pr.k * bc, b_per = (b_units + pr.tm - 1) / pr.tm;
+          const uint32_t b_lo = min(b_units, (uint32_t)x.mb * b_per), b_hi = min(b_units, b_lo + b_per);
+          for (uint32_t u = b_lo + tid; u < b_hi; u += 256) {
+            const uint32_t r = u / bc, c = u - r * bc;
+            bad |= range_bits(pr.B + (size_t)r * pr.ldb + x.n0 + 16 * c, pr.n - x.n0 - 16 * (int)c, pk);
+          }
         }
       }
       // one lane waits, the warp follows (tcgen05.ld needs all 32 lanes on the same path)
@@ -277,16 +371,47 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
       if (lane == 0) got = mbar_wait(&tfull[buf], (uint32_t)(lt >> 1) & 1u, abort_flag) ? 1u : 0u;
       if (!__shfl_sync(0xffffffffu, got, 0)) break;
       tc_fence_after();
-      // parameters in registers (read through the grid-constant block they would be reloaded
-      // after every store to C)
-      const DivP dv = pr.dv;
-      const uint32_t p = pr.p, fdiv = pr.fdiv;
-      const float c18 = pr.c18, pm18 = pr.pm18;
-      const int m = pr.m, n = pr.n, ldc = pr.ldc;
-      uint8_t* const Cb = pr.C;
-      const int row = x.m0 + q * 32 + lane;
+      // parameters in registers (read through the parameter block or the global problem list
+      // they would be reloaded after every store to C)
+      DivP dv;
+      uint32_t p, fdiv;
+      float c18, pm18, off18;
+      int m, n, ldc;
+      uint8_t* Cb;
+      if constexpr (PRE) {
+        // centred operands: the sum is signed, |sum| <= k (p/2)^2; adding p T >= that makes it
+        // non-negative and below 2^23, where FDIV applies (the router guarantees it)
+        const BProb* pr = bpr;
+        p = __ldg(&pr->p);
+        fdiv = 1u;
+        c18 = __ldg(&pr->c18);
+        pm18 = __ldg(&pr->pm18);
+        off18 = __ldg(&pr->off18);
+        m = __ldg(&pr->m);
+        n = __ldg(&pr->n);
+        ldc = __ldg(&pr->ldc);
+        Cb = pr->C;
+        dv = DivP{};
+      } else {
+        const GProb& pr = *g_tile(g, t).pr;
+        dv = pr.dv;
+        p = pr.p;
+        fdiv = pr.fdiv;
+        c18 = pr.c18;
+        pm18 = pr.pm18;
+        off18 = 0.0f;
+        m = pr.m;
+        n = pr.n;
+        ldc = pr.ldc;
+        Cb = pr.C;
+      }
+      const int row = m0 + q * 32 + lane;
+      const bool rows_in = m0 + q * 32 < m;      // some row of this warp's quarter is in C
       for (int cb = 0; cb < 4; ++cb) {
         const int col0 = half * 128 + cb * 32;
+        // a block wholly in the tile's padding (thin products) is neither read nor stored
+        // (warp-uniform, so tcgen05.ld stays converged)
+        if (!rows_in || n0 + col0 >= n) continue;
         uint32_t v[32];
         tmem_ld32(tmem + lane_base + (uint32_t)(buf * 256 + col0), v);
         uint32_t packed[8];
@@ -299,7 +424,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
             uint32_t w = 0;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const float vs = __uint_as_float(v[j + u]);
+              const float vs = PRE ? __uint_as_float(v[j + u]) + off18 : __uint_as_float(v[j + u]);
               const float qf = __fadd_rd(__fmul_rd(vs, c18), 8388608.0f) - 8388608.0f;
               const float rs = fmaf(pm18, qf, vs);                   // (x - p q) 2^-18, exact
               w |= (__float_as_uint(fmaf(rs, 262144.0f, 8388608.0f)) - 0x4B000000u) << (8 * u);
@@ -319,7 +444,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
             packed[j >> 2] = w;
           }
         }
-        const int c0 = x.n0 + col0;                 // the same for the whole warp
+        const int c0 = n0 + col0;                   // the same for the whole warp
         uint8_t* dst = Cb + (size_t)row * ldc + c0;
         const bool vec = row < m && c0 + 32 <= n && ((((uintptr_t)dst) & 15u) == 0);
         if (__all_sync(0xffffffffu, vec)) {
@@ -328,15 +453,23 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
         } else if (c0 < n) {
           // rows not 16-byte aligned (ldc not a multiple of 16) or a ragged edge: the warp's
           // 32 rows x 32 bytes go through shared memory and out one row at a time, the 32 lanes
-          // on consecutive bytes (one or two 32-byte sectors per store, not 32)
+          // on consecutive bytes (one or two 32-byte sectors per store, not 32).  All 32 bytes
+          // are read before the first store, so the loads overlap instead of each waiting for
+          // the store before it.
 #pragma unroll
           for (int j = 0; j < 8; ++j) epi_stage[lane * 9 + j] = packed[j];
           __syncwarp();
           const uint8_t* sb = reinterpret_cast<const uint8_t*>(epi_stage);
-          const int r0 = x.m0 + q * 32;
+          const int r0 = m0 + q * 32;
+          const int rn = min(32, m - r0);
           const bool col_in = c0 + lane < n;
-          for (int r = 0; r < 32 && r0 + r < m; ++r)
-            if (col_in) Cb[(size_t)(r0 + r) * ldc + c0 + lane] = sb[r * 36 + lane];
+          uint8_t b[32];
+#pragma unroll
+          for (int r = 0; r < 32; ++r) b[r] = sb[r * 36 + lane];
+          uint8_t* dcol = Cb + (size_t)r0 * ldc + c0 + lane;
+#pragma unroll
+          for (int r = 0; r < 32; ++r)
+            if (col_in && r < rn) dcol[(size_t)r * ldc] = b[r];
           __syncwarp();
         }
       }
@@ -406,8 +539,23 @@ static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int co
   hp.nprob = count;
   hp.total = tile;
   const int grid = std::min(tile, ctx->num_sms);
-  FP_CUDA(cudaFuncSetAttribute(k_mm_f8g<CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G_SMEM));
-  FP_LAUNCH(ctx, "k_mm_f8g", st, k_mm_f8g<CAP><<<grid, G_THREADS, G_SMEM, st>>>(hp, ctx->d_err));
+  FP_CUDA(cudaFuncSetAttribute(k_mm_f8g<CAP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G_SMEM));
+  FP_LAUNCH(ctx, "k_mm_f8g", st, k_mm_f8g<CAP, false><<<grid, G_THREADS, G_SMEM, st>>>(hp, ctx->d_err));
+  FP_CUDA(cudaGetLastError());
+  return FP_OK;
+}
+
+fp_status launch_mm_f8_pretiled(fp_ctx ctx, const F8PreProb* prob, const int* tile0, int nprob, int total,
+                                cudaStream_t st) {
+  if (nprob <= 0 || total <= 0) return FP_OK;
+  FP_CHECK(nprob <= F8_PRE_CAP, FP_EINVAL, "pre-tiled e4m3 launch: too many problems");
+  const BParams hp{prob, tile0, nprob, total};
+  const size_t smem = G_SMEM + sizeof(int) * (size_t)F8_PRE_CAP;
+  static_assert(G_SMEM + sizeof(int) * F8_PRE_CAP <= 227 * 1024, "shared memory per block");
+  const int grid = std::min(total, ctx->num_sms);
+  FP_CUDA(cudaFuncSetAttribute(k_mm_f8g<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FP_LAUNCH(ctx, "k_mm_f8g_pre", st,
+            k_mm_f8g<1, true><<<grid, G_THREADS, G_SMEM + sizeof(int) * (size_t)nprob, st>>>(hp, ctx->d_err));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }

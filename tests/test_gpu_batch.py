@@ -217,11 +217,11 @@ def _mm(p, m, k, n, seed):
 
 @pytest.mark.parametrize("off_a,off_b", [(0, 0), (1, 2), (3, 1), (2, 3)])
 def test_batch_tensor_core_share_unaligned(env, off_a, off_b):
-    """Large products with p <= 17 run on the grouped e4m3 kernel after their operands are copied
-    to 16-byte row strides, those with 17 < p <= 127 on the bf16 kernel after a conversion;
-    operands starting 1-3 bytes past an aligned address and inner dimensions / widths that are
-    not multiples of 4 exercise every shift of those copies (k (p-1)^2 up to 0.86 x 2^24 for
-    p = 61).  Mixed with products (p = 131, small shapes) and dots that stay on the batch kernel;
+    """Large products with p <= 31 run on the e4m3 kernel after their operands are laid out as
+    swizzled tiles of centred residues, those with 31 < p <= 127 on the bf16 kernel after a
+    conversion; operands starting 1-3 bytes past an aligned address and inner dimensions / widths
+    that are not multiples of 4 exercise every shift of those copies (k (p-1)^2 up to 0.86 x 2^24
+    for p = 61).  Mixed with products (p = 131, small shapes) and dots that stay on the batch kernel;
     every entry compared."""
     fp, torch, dev, ctx = env
     shapes = [(3, 130, 449, 257), (17, 200, 1021, 67), (5, 64, 512, 64), (2, 333, 2047, 129), (7, 96, 33, 700),
@@ -258,8 +258,8 @@ def test_batch_tensor_core_share_unaligned(env, off_a, off_b):
 
 @pytest.mark.parametrize("p,where", [(5, "a"), (31, "a"), (31, "b"), (127, "b")])
 def test_batch_tensor_core_share_range_error(env, p, where):
-    """An entry equal to p inside a product routed to the tensor cores (e4m3 for p = 5, bf16
-    otherwise) raises the range error."""
+    """An entry equal to p inside a product routed to the tensor cores (e4m3 for p = 5, 31, bf16
+    for p = 127) raises the range error."""
     fp, torch, dev, ctx = env
     x = _mm(p, 128, 300, 129, 7)
     if where == "a":
@@ -289,3 +289,91 @@ def test_batch_invalid_instance_enqueues_nothing(env):
     fp.fp_ctx_status(ctx)
     for A, B, C in bufs:
         assert int(C.min().item()) == 255 and int(C.max().item()) == 255
+
+
+def _mm_const(p, m, k, n, ra, rb):
+    x = workloads.Instance("matmul", p, m, k, n)
+    x.a = np.full((m, k), ra, dtype=np.uint8)
+    x.b = np.full((k, n), rb, dtype=np.uint8)
+    return x
+
+
+@pytest.mark.parametrize("k", [2, 31, 32, 33, 97, 127, 128, 129, 255, 385])
+def test_batch_pretiled_ragged_inner(env, k):
+    """The e4m3 share at inner lengths around the 128-byte k tile and its four K = 32 steps (the
+    last k tile issues only the steps that hold some of k, the rest of the tile is zero): ragged
+    row and column blocks, every entry against the oracle."""
+    fp, torch, dev, ctx = env
+    m, n = (1400, 1500) if k < 40 else (200, 330)
+    assert m * n * k >= 2 ** 21
+    x = _mm(7, m, k, n, 1000 + k)
+    bufs, arr = make_instances(fp, torch, dev, [x])
+    fp.fp_batch_run(ctx, arr)
+    fp.fp_ctx_status(ctx)
+    assert np.array_equal(result(x, bufs[0][2]), oracle(x))
+
+
+@pytest.mark.parametrize("ra,rb", [(15, 15), (15, 16), (16, 16), (30, 30), (0, 17)])
+@pytest.mark.parametrize("k", [18641, 18642])
+def test_batch_pretiled_fdiv_bound_p31(env, ra, rb, k):
+    """p = 31 at the largest k the e4m3 route takes (2 k 15^2 + 31 < 2^23 holds for k = 18641, not
+    for 18642, which goes elsewhere): all entries of A equal ra and of B rb, so the centred
+    values +-15 (or -1) make every sum +-k 225 (or k), the ends of FDIV's range once the offset
+    is added.  Every entry equals k ra rb mod 31."""
+    fp, torch, dev, ctx = env
+    p, m, n = 31, 64, 70
+    x = _mm_const(p, m, k, n, ra, rb)
+    bufs, arr = make_instances(fp, torch, dev, [x])
+    fp.fp_batch_run(ctx, arr)
+    fp.fp_ctx_status(ctx)
+    assert np.array_equal(result(x, bufs[0][2]), np.full((m, n), k * ra * rb % p, dtype=np.uint8))
+
+
+def test_batch_pretiled_more_than_one_launch(env):
+    """4100 products routed to the e4m3 kernel (64 x 512 x 64, p cycling over the primes up to
+    31): the share takes two launches (4096 + 4 products).  The first and last rows of every
+    product against the oracle, all of the products around the boundary in full."""
+    fp, torch, dev, ctx = env
+    primes = [2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31]
+    insts = [_mm(primes[i % len(primes)], 64, 512, 64, 20000 + i) for i in range(4100)]
+    bufs, arr = make_instances(fp, torch, dev, insts)
+    fp.fp_batch_run(ctx, arr)
+    fp.fp_ctx_status(ctx)
+    rows = np.array([0, 63])
+    for i, (x, (A, B, C)) in enumerate(zip(insts, bufs)):
+        got = result(x, C)
+        if 4090 <= i or i < 4:
+            assert np.array_equal(got, oracle(x)), i
+        else:
+            assert np.array_equal(got[rows], field.matmul_mod_rows(x.a, x.b, x.p, rows)), i
+
+
+@pytest.mark.parametrize("m,n,k", [(8, 256, 1024), (20, 1500, 300), (1500, 17, 700), (63, 63, 2048), (4, 2048, 512)])
+def test_batch_pretiled_thin_products(env, m, n, k):
+    """Products with fewer than 64 rows or columns whose 128 x 256 x 32-padded MACs are at most 32
+    times their own run on the e4m3 kernel (most of each tile is zero padding); every entry
+    against the oracle, alone and beside a product that fills its tiles."""
+    fp, torch, dev, ctx = env
+    pad = -(-m // 128) * 128 * -(-n // 256) * 256 * -(-k // 32) * 32
+    assert 2 ** 21 <= pad <= 32 * m * n * k
+    insts = [_mm(13, m, k, n, m * 7 + n), _mm(29, 300, 400, 500, 3)]
+    bufs, arr = make_instances(fp, torch, dev, insts)
+    fp.fp_batch_run(ctx, arr)
+    fp.fp_ctx_status(ctx)
+    for x, (A, B, C) in zip(insts, bufs):
+        assert np.array_equal(result(x, C), oracle(x)), (x.p, x.m, x.n, x.k)
+
+
+@pytest.mark.parametrize("k", [32767, 32768])
+@pytest.mark.parametrize("r", [16, 9, 8])
+def test_batch_pretiled_unsigned_to_centred_p17(env, k, r):
+    """p = 17: residues go to the e4m3 kernel as they stand while k 16^2 < 2^23 (k = 32767, every
+    sum up to 32767 x 256, just below FDIV's 2^23), centred past it (k = 32768: 16 -> -1, 9 -> -8).
+    All entries of A and B equal r; every entry equals k r^2 mod 17."""
+    fp, torch, dev, ctx = env
+    p, m, n = 17, 64, 80
+    x = _mm_const(p, m, k, n, r, r)
+    bufs, arr = make_instances(fp, torch, dev, [x])
+    fp.fp_batch_run(ctx, arr)
+    fp.fp_ctx_status(ctx)
+    assert np.array_equal(result(x, bufs[0][2]), np.full((m, n), k * r * r % p, dtype=np.uint8))
