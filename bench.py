@@ -887,16 +887,18 @@ def run_batch(args, ws, rank, local, emit=True):
         else:
             assert int(hv_out[oc:oc + 4].view(np.uint32)[0]) == field.dot_mod(x.a, x.b, x.p)
     # The library's routing (fp_batch_run's documented rule): products with p <= 17 and
-    # k (p-1)^2 < 2^23 or p <= 31 and 2 k (p/2)^2 + p < 2^23 whose 128 x 256 x 32-padded MACs are >= 2^21 and <= 32 x their own on
-    # the pre-tiled e4m3 kernel, large ones with 31 < p <= 127 and k (p-1)^2 < 2^24 on the bf16
-    # kernel, the rest in the batch kernel.  Roofline of the kernel with the most time
+    # k (p-1)^2 < 2^23 or p <= 31 and 2 k (p/2)^2 + p < 2^23 whose 128 x 256 x 32-padded MACs
+    # are >= 2^21 and <= 32 x their own (or any such with k >= 128) on the pre-tiled e4m3
+    # kernel, large ones with 31 < p <= 127 and k (p-1)^2 < 2^24 on the bf16 kernel, the rest
+    # in the batch kernel.  Roofline of the kernel with the most time
     # per step, on its own MACs.
     def route(x):
         if x.kind != "matmul" or x.p > 127:
             return "k_batch"
         if (x.p <= 17 and x.k * (x.p - 1) ** 2 < (1 << 23)) or (x.p <= 31 and 2 * x.k * (x.p // 2) ** 2 + x.p < (1 << 23)):
             padded = -(-x.m // 128) * 128 * -(-x.n // 256) * 256 * -(-x.k // 32) * 32
-            return "k_mm_f8g_pre" if (1 << 21) <= padded <= 32 * x.m * x.n * x.k else "k_batch"
+            return "k_mm_f8g_pre" if padded >= (1 << 21) and (padded <= 32 * x.m * x.n * x.k or x.k >= 128) \
+                else "k_batch"
         big = x.m >= 64 and x.n >= 64 and x.m * x.n * x.k >= (1 << 21)
         return "k_mm_t16_plain" if big and x.k * (x.p - 1) ** 2 < (1 << 24) else "k_batch"
     kmacs = {nm: 0 for nm in ("k_mm_f8g_pre", "k_mm_t16_plain", "k_batch")}

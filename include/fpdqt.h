@@ -444,16 +444,18 @@ typedef struct {
 } fp_instance;
 
 /* Uneven batch (no counterpart in the paper as a call; each instance's packing follows
- * Sec. 7.6.1).  Run all `count` instances: matrix products with p <= 17 and k (p-1)^2 < 2^23, or
- * p <= 31 and 2 k (p/2)^2 + p < 2^23, whose sizes rounded up to 128 x 256 x 32 blocks give >= 2^21
- * and at most 32 times their own MACs go to the e4m3 tensor-core kernel (one launch first lays
- * every such operand out as swizzled 16 KB tiles, residues range-checked and, in the second
- * case, centred to |c| <= p/2; then
- * one persistent launch per 4096 products; any row stride or alignment); those with
- * 31 < p <= 127, m, n >= 64, m n k >= 2^21 and k (p-1)^2 < 2^24 to the bf16 kernel (operands
- * converted and range-checked in one launch, up to 64 products per launch); everything else runs in ONE persistent kernel launch whose CTAs take tiles from a device
- * work queue (an atomic counter over a tile list the host planner sorts by cost), packing
- * degree e and word chosen per (p, k) by the planner and the autotuner cache in the context.
+ * Sec. 7.6.1).  Runs all `count` instances, routed by size:
+ *  - matrix products with p <= 17 and k (p-1)^2 < 2^23, or p <= 31 and 2 k (p/2)^2 + p < 2^23,
+ *    whose sizes rounded up to 128 x 256 x 32 blocks give >= 2^21 MACs and at most 32 times
+ *    their own (or any such with k >= 128): the e4m3 tensor-core kernel.  One launch first lays
+ *    every such operand out as swizzled 16 KB tiles (residues range-checked and, in the second
+ *    case, centred to |c| <= p/2), then one persistent launch takes up to 4096 products; any
+ *    row stride and alignment of the caller's arrays;
+ *  - those with 31 < p <= 127, m, n >= 64, m n k >= 2^21 and k (p-1)^2 < 2^24: the bf16 kernel
+ *    (operands converted and range-checked in one launch, up to 64 products per launch);
+ *  - everything else: ONE persistent kernel launch whose CTAs take tiles from a device work
+ *    queue (an atomic counter over a tile list the host planner sorts by cost), packing degree
+ *    e and word chosen per (p, k) by the planner and the autotuner cache in the context.
  * `instances` is a HOST array; every instance is checked before anything is enqueued; the
  * plan is copied to context scratch through pinned staging (the call does not wait for earlier
  * work on the stream).  Stream capture: a call captured into a CUDA graph writes its plan with

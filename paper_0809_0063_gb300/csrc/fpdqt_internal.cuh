@@ -455,9 +455,7 @@ struct F8PreProb {
   int klast;           // K = 32 steps holding some of the last k tile (1..4)
   int tn;              // column blocks ceil(n / 256)
   uint32_t p;
-  float c18;           // 2^18 RU(1/p)
-  float pm18;          // -p 2^-18
-  float off18;         // p T 2^-18 with p T >= k (p/2)^2 (makes every sum non-negative)
+  float off18;         // p T 2^-18 with p T >= k (p/2)^2 (makes every sum non-negative), or 0
 };
 // prob, tile0: nprob <= F8_PRE_CAP entries in device memory, tile0 ascending from 0 (the first
 // tile of each problem, tiles of a problem in row-block-major order), total tiles.  Lock held.

@@ -503,12 +503,11 @@ static bool choose_packed(fp_ctx ctx, uint32_t p, uint32_t k, cudaStream_t st) {
 // ---------------------------------------------------------------- tensor-core share of a batch
 //
 // Matrix products whose residues are exact e4m3 values as they stand (p <= 17, unsigned sums
-// k (p-1)^2 < 2^23) or once centred (p <= 31: |c| <= p/2 <= 15, 2 k (p/2)^2 + p < 2^23), so that
-// the sums stay in FDIV's range (see k_tcg.cu), and that fill enough of
-// their 128 x 256 x 32 blocks run on the pre-tiled tcgen05 kernel (k_mm_f8g_pre) instead of the
-// mma.sync tiles of k_batch; larger p (up to 127, k (p-1)^2 < 2^24, m, n >= 64) on the bf16
-// kernel.  One
-// launch of k_tile_pack lays every routed operand out as the 16 KB swizzled blocks that kernel's
+// k (p-1)^2 < 2^23) or once centred (p <= 31: |c| <= p/2 <= 15, 2 k (p/2)^2 + p < 2^23), so
+// that the sums stay below 2^23 (the range of the e4m3 epilogue's reduction, see k_tcg.cu), and
+// that fill enough of their 128 x 256 x 32 blocks run on the pre-tiled tcgen05 kernel
+// (k_mm_f8g_pre) instead of the mma.sync tiles of k_batch; larger p (up to 127,
+// k (p-1)^2 < 2^24, m, n >= 64) on the bf16 kernel.  One launch of k_tile_pack lays every routed operand out as the 16 KB swizzled blocks that kernel's
 // stages copy (layout in fpdqt_internal.cuh): residues range-checked and centred, zero outside
 // the matrix, so the caller's arrays may have any row stride and alignment.  Then one
 // tensor-core launch takes the whole share (up to F8_PRE_CAP products per launch).
@@ -549,7 +548,7 @@ __device__ __forceinline__ void chunk_load(const uint8_t* rowp, int col, int nva
 // (coalesced): chunk o is block row o / 8 at swizzled position o % 8, i.e. source chunk
 // (o % 8) ^ (row % 8) of that row.  Every byte is range-checked (r < p: r + 128 - p has bit 7
 // clear) and, for centred jobs, r > p/2 becomes the e4m3 code of -(p - r) (sign bit | (p - r)).
-// Block rows of A past m and chunks of B past n are not written: they only reach accumulator
+// Block rows of A past m and sectors of B past n are not written: they only reach accumulator
 // rows or columns the epilogue never stores.  The inner-dimension padding (A columns, B rows
 // past k) is written as zeros: it meets every output.
 __global__ void __launch_bounds__(256) k_tile_pack(const TileJob* __restrict__ jobs, uint32_t njobs, uint32_t nblocks,
@@ -589,7 +588,10 @@ __global__ void __launch_bounds__(256) k_tile_pack(const TileJob* __restrict__ j
       const uint32_t r = o >> 3, c = (o & 7u) ^ (r & 7u);
       const uint32_t row = rb * 128 + r, col = cb * 128 + 16 * c;
       const bool row_in = row < rows;
-      st[i] = is_b ? (col < cols || !row_in) : row_in;
+      // chunks c and c ^ 1 share a 32-byte sector (at positions o % 8 and (o % 8) ^ 1): a B
+      // chunk past n is still written (zeros) when its partner is not, so that no sector is
+      // half written (which would cost a read-modify-write in DRAM)
+      st[i] = is_b ? (cb * 128 + 16 * (c & ~1u) < cols || !row_in) : row_in;
       chunk_load(src + (size_t)(row_in ? row : 0) * ld, (int)col, row_in ? (int)cols - (int)col : -64, w[i]);
     }
 #pragma unroll
@@ -613,7 +615,9 @@ __global__ void __launch_bounds__(256) k_tile_pack(const TileJob* __restrict__ j
 // and the conversion's range check valid); 0: the batch kernel.  The e4m3 kernel computes whole
 // 128 x 256 x 32 blocks: a product goes there when those padded MACs are at least 2^21 and at
 // most 32 times its own (a thin product still runs far faster there than on the mma.sync tiles
-// of the batch kernel).
+// of the batch kernel), or when k >= 128 however thin it is (the batch kernel takes k in steps
+// of 32 with one step of prefetch, so a long k would make one of its items the longest part of
+// the whole launch).
 static bool f8_unsigned_ok(uint32_t p, uint64_t k) { return p <= 17 && k * (p - 1) * (p - 1) < (1ull << 23); }
 static bool f8_centred_ok(uint32_t p, uint64_t k) { return p <= 31 && 2 * k * (p / 2) * (p / 2) + p < (1ull << 23); }
 
@@ -625,7 +629,7 @@ static int batch_tc_route(const fp_instance& x) {
   if (f8_unsigned_ok(x.p, x.k) || f8_centred_ok(x.p, x.k)) {
     const unsigned __int128 padded = (unsigned __int128)(((x.m + 127ull) & ~127ull) * ((x.n + 255ull) & ~255ull)) *
                                      ((x.k + 31ull) & ~31ull);
-    return padded >= BT_TC_MIN_MACS && padded <= 32 * macs ? 1 : 0;
+    return padded >= BT_TC_MIN_MACS && (padded <= 32 * macs || x.k >= 128) ? 1 : 0;
   }
   const bool big = x.m >= 64 && x.n >= 64 && macs >= BT_TC_MIN_MACS;
   return big && (uint64_t)x.k * (x.p - 1) * (x.p - 1) < (1ull << 24) ? 2 : 0;
@@ -679,8 +683,6 @@ static fp_status batch_run_tc(fp_ctx ctx, const std::vector<const fp_instance*>&
     q.klast = (int)((x.k - 128 * (kt - 1) + 31) / 32);
     q.tn = (int)tn;
     q.p = x.p;
-    q.c18 = make_redq(x.p, 1, 1).invp_f * 262144.0f;   // RU(1/p) scaled by 2^18 (exact)
-    q.pm18 = -(float)x.p / 262144.0f;
     q.off18 = (float)pt / 262144.0f;                   // exact: p T < 2^23
     tile0[i] = tiles;
     tiles += (int)(tm * tn);

@@ -14,22 +14,28 @@
 // problems, those with the longest inner dimension first) in waves of gridDim.x tiles, taken in
 // forward order in even waves and reversed in odd ones (better balance than a plain stride when
 // the tiles' lengths differ: 0.98 vs 0.94 of the mean load for the matrix step).  Roles:
-//   warp 0       TMA producer: per k tile, A 128 x 128 bytes and B two boxes of 128 x 128
-//                bytes (128-byte swizzle) into a 4-stage shared-memory ring,
+//   warp 0       producer: computes each tile's parameters once (the next tile's while the
+//                current tile's copies are issued) and hands them to the other roles through a
+//                4-slot ring in shared memory; per k tile, A 128 x 128 bytes and B two boxes of
+//                128 x 128 bytes (128-byte swizzle) into the stage ring (4 stages; TMA from the
+//                caller's arrays, or 3 stages of plain bulk copies of pre-tiled operands),
 //   warp 1       TMEM allocation (512 columns = two 128 x 256 fp32 accumulators) and the
 //                single MMA-issuing thread; tile i accumulates into buffer i & 1,
-//   warps 2..9   epilogue of tile i (tcgen05.ld, scale, mod p, stores) while the MMAs of tile
-//                i + 1 run into the other buffer.  Before waiting for a tile's accumulator they
-//                range-check a slice of its inputs with plain global loads (off the shared-
-//                memory pipeline, whose stages they never touch): the A panel of (problem, row
-//                block) is used by the tiles of every column block and the B panel of (problem,
-//                column block) by those of every row block, so the tile in column block nb
-//                checks slice nb of its A panel and the tile in row block mb slice mb of its B
-//                panel: every input byte is checked exactly once.
+//   warps 2..    epilogue of tile i (tcgen05.ld, scale, mod p, stores: 16-byte stores where a
+//                row is 16-byte aligned, else through a small per-warp buffer with the lanes
+//                on consecutive bytes of a row) while the MMAs of tile i + 1 run into the other
+//                buffer; 2 (TMA problems) or 3 (pre-tiled) warps per TMEM lane quarter, taking
+//                its 32-column blocks in turn.  Before
+//                waiting for a tile's accumulator they range-check a slice of its inputs with
+//                plain global loads (off the shared-memory pipeline): the A panel of (problem,
+//                row block) is used by the tiles of every column block and the B panel of
+//                (problem, column block) by those of every row block, so the tile in column
+//                block nb checks slice nb of its A panel and the tile in row block mb slice mb of
+//                its B panel: every input byte is checked exactly once (pre-tiled operands were
+//                checked when packed).
 // A stage is released when the MMAs that read it have completed (tcgen05.commit).  Every wait
-// is bounded: a wait that gives up
-// sets the abort flag, the roles stop, in-flight copies and MMAs are drained, TMEM is freed and
-// the context's sticky flag reports ERR_TIMEOUT.
+// is bounded: a wait that gives up sets the abort flag, the roles stop, in-flight copies and MMAs
+// are drained, TMEM is freed and the context's sticky flag reports ERR_TIMEOUT.
 #include <algorithm>
 #include <cstring>
 #include <type_traits>
@@ -44,10 +50,23 @@ static constexpr int G_BM = 128, G_BN = 256, G_BK = 128, G_STAGES = 4;
 static constexpr int G_A_BYTES = G_BM * G_BK;                 // 16 KB
 static constexpr int G_B_BYTES = G_BN * G_BK;                 // 32 KB (two 128-column boxes)
 static constexpr int G_STAGE_BYTES = G_A_BYTES + G_B_BYTES;   // 48 KB
-static constexpr int G_THREADS = 320;                         // 10 warps
-// per epilogue warp: 32 rows x 32 output bytes (row stride 36 bytes: conflict-free word writes)
-static constexpr int G_EPI_STAGE_BYTES = 8 * 32 * 36;
-static constexpr size_t G_SMEM = 1024 + G_STAGES * G_STAGE_BYTES + 256 + G_EPI_STAGE_BYTES;
+// epilogue warps: 2 per TMEM lane quarter for TMA problems (long tiles, the epilogue hidden
+// behind the MMAs), 3 for pre-tiled ones (short tiles of uneven batches: the epilogue is
+// latency-bound and more warps hide more of it)
+__host__ __device__ constexpr int g_epi_warps(bool pre) { return pre ? 12 : 8; }
+__host__ __device__ constexpr int g_threads(bool pre) { return 64 + 32 * g_epi_warps(pre); }
+// Shared memory: the stage ring, barriers, tmem address and abort flag (G_BAR_BYTES), the tile
+// parameter ring (G_RING_BYTES), the epilogue warps' store buffers (32 rows x 36 bytes each: row
+// stride 9 words, conflict-free), then (pre-tiled launches) the problems' first tiles and
+// column-block counts.
+static constexpr int G_STAGES_PRE = 3;
+static constexpr int G_BAR_BYTES = 256, G_RING_BYTES = 512;
+__host__ __device__ constexpr int g_stages(bool pre) { return pre ? G_STAGES_PRE : G_STAGES; }
+__host__ __device__ constexpr int g_off_tail(bool pre) {
+  return g_stages(pre) * G_STAGE_BYTES + G_BAR_BYTES + G_RING_BYTES + g_epi_warps(pre) * 32 * 36;
+}
+static constexpr size_t G_SMEM = 1024 + g_off_tail(false);
+static constexpr size_t G_SMEM_PRE = 1024 + g_off_tail(true);
 
 struct GProb {
   CUtensorMap ta;   // A: m rows x k columns, leading dimension lda
@@ -60,10 +79,7 @@ struct GProb {
   int tm, tn;       // row blocks ceil(m / 128), column blocks ceil(n / 256)
   int tile0;        // index of this problem's first tile in the global list
   uint32_t p;
-  DivP dv;
-  uint32_t fdiv;    // 1 when k (p-1)^2 < 2^23: reduce with FDIV in fp32 (Table fdiv, case 3)
-  float c18;        // 2^18 RU(1/p)
-  float pm18;       // -p 2^-18
+  uint32_t fdiv;    // 1 when k (p-1)^2 < 2^23: the epilogue forms each sum with one FFMA
   uint32_t checked; // 1: the caller range-checked A and B already (the epilogue skips its check)
 };
 
@@ -116,29 +132,6 @@ __device__ __forceinline__ GTile g_tile(const GParamsT<CAP>& g, int t) {
   return x;
 }
 
-struct BTile {
-  const BProb* pr;
-  int m0, n0, mb, nb;
-};
-
-__device__ __forceinline__ BTile b_tile(const BParams& g, const int* s_tile0, int t) {
-  int i = 0, hi = g.nprob - 1;      // the last problem whose first tile is <= t
-  while (i < hi) {
-    const int mid = (i + hi + 1) >> 1;
-    if (s_tile0[mid] <= t) i = mid;
-    else hi = mid - 1;
-  }
-  BTile x;
-  x.pr = g.prob + i;
-  const int local = t - s_tile0[i];
-  const int tn = __ldg(&x.pr->tn);
-  x.mb = local / tn;
-  x.nb = local - x.mb * tn;
-  x.m0 = x.mb * G_BM;
-  x.n0 = x.nb * G_BN;
-  return x;
-}
-
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    su32(dst)),
@@ -180,42 +173,139 @@ __device__ __forceinline__ int g_wave_tile(int w) {
   return w * (int)gridDim.x + ((w & 1) ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x);
 }
 
+// One tile's parameters, computed once by the producer and handed to the MMA issuer and the
+// epilogue through a ring of G_RING slots in shared memory (so those roles never wait on a
+// lookup in global memory between tiles).
+struct TInfo {
+  uint8_t* C;
+  int pi;           // problem index
+  int m0, n0, mb, nb;
+  int m, n, ldc;
+  int ktiles, klast;
+  uint32_t p, fdiv, mp;   // fdiv: every sum + offset < 2^23; mp = ceil(2^32 / p)
+  float mo;         // 2^23 + the offset added to every sum
+};
+static constexpr int G_RING = 4;
+static_assert(G_RING * sizeof(TInfo) <= G_RING_BYTES, "tile parameter ring");
+static_assert((2 * G_STAGES + 2 * 2 + 2 + 2 * G_RING) * 8 + 8 <= G_BAR_BYTES, "barrier area");
+static_assert(G_SMEM <= 227 * 1024, "shared memory per block");
+
+// The producer's view of a tile: its parameters and, for pre-tiled problems, the first A and B
+// blocks of its row and column block.
+struct TLoad {
+  TInfo x;
+  const uint8_t* a;
+  const uint8_t* b;
+};
+
+template <int CAP>
+__device__ __forceinline__ TLoad tile_load(const GParamsT<CAP>& g, const int*, const int*, int t) {
+  const GTile gt = g_tile(g, t);
+  const GProb& pr = *gt.pr;
+  TLoad L;
+  L.x.C = pr.C;
+  L.x.pi = (int)(gt.pr - g.prob);
+  L.x.m0 = gt.m0;
+  L.x.n0 = gt.n0;
+  L.x.mb = gt.mb;
+  L.x.nb = gt.nb;
+  L.x.m = pr.m;
+  L.x.n = pr.n;
+  L.x.ldc = pr.ldc;
+  L.x.ktiles = pr.ktiles;
+  L.x.klast = 4;
+  L.x.p = pr.p;
+  L.x.fdiv = pr.fdiv;
+  L.x.mp = 0xFFFFFFFFu / pr.p + 1u;
+  L.x.mo = 8388608.0f;
+  L.a = L.b = nullptr;
+  return L;
+}
+
+__device__ __forceinline__ TLoad tile_load(const BParams& g, const int* s_tile0, const int* s_tn, int t) {
+  int i = 0, hi = g.nprob - 1;      // the last problem whose first tile is <= t
+  while (i < hi) {
+    const int mid = (i + hi + 1) >> 1;
+    if (s_tile0[mid] <= t) i = mid;
+    else hi = mid - 1;
+  }
+  const int local = t - s_tile0[i], tn = s_tn[i];
+  const int mb = local / tn, nb = local - mb * tn;
+  const BProb* pr = g.prob + i;
+  TLoad L;
+  const int ktiles = __ldg(&pr->ktiles);
+  const uint32_t p = __ldg(&pr->p);
+  L.x.C = pr->C;
+  L.x.pi = i;
+  L.x.m0 = mb * G_BM;
+  L.x.n0 = nb * G_BN;
+  L.x.mb = mb;
+  L.x.nb = nb;
+  L.x.m = __ldg(&pr->m);
+  L.x.n = __ldg(&pr->n);
+  L.x.ldc = __ldg(&pr->ldc);
+  L.x.ktiles = ktiles;
+  L.x.klast = __ldg(&pr->klast);
+  L.x.p = p;
+  L.x.fdiv = 1u;
+  L.x.mp = 0xFFFFFFFFu / p + 1u;
+  // centred operands: the sum is signed, |sum| <= k (p/2)^2; adding p T >= that makes it
+  // non-negative and below 2^23 (the router guarantees it); exact: 2^23 + p T < 2^24
+  L.x.mo = 8388608.0f + __ldg(&pr->off18) * 262144.0f;
+  L.a = pr->At + (size_t)mb * ktiles * G_A_BYTES;
+  L.b = pr->Bt + (size_t)nb * ktiles * G_B_BYTES;
+  return L;
+}
+
 // PRE = false: problems in the grid-constant block, operands loaded by TMA from the caller's
 // arrays.  PRE = true: pre-tiled problems from global memory (BParams), stages by bulk copies.
 template <int CAP, bool PRE>
 using GPar = typename std::conditional<PRE, BParams, GParamsT<CAP>>::type;
 
 template <int CAP, bool PRE>
-__global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__ GPar<CAP, PRE> g, uint32_t* err) {
+__global__ void __launch_bounds__(g_threads(PRE), 1) k_mm_f8g(const __grid_constant__ GPar<CAP, PRE> g, uint32_t* err) {
+  constexpr int NST = g_stages(PRE), EW = g_epi_warps(PRE), NTH = g_threads(PRE);
   extern __shared__ __align__(1024) uint8_t g_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)g_smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + G_STAGES * G_STAGE_BYTES);
-  uint64_t* empty = full + G_STAGES;
-  uint64_t* tfull = empty + G_STAGES;    // [2] accumulator buffer ready
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * G_STAGE_BYTES);
+  uint64_t* empty = full + NST;
+  uint64_t* tfull = empty + NST;         // [2] accumulator buffer ready
   uint64_t* tempty = tfull + 2;          // [2] accumulator buffer drained
   uint64_t* drainb = tempty + 2;         // MMA completion on the abort path
   uint64_t* doneb = drainb + 1;          // every epilogue warp finished with TMEM
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(doneb + 1);
+  uint64_t* ifull = doneb + 1;           // [G_RING] tile parameters written
+  uint64_t* iempty = ifull + G_RING;     // [G_RING] tile parameters consumed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(iempty + G_RING);
   volatile uint32_t* abort_flag = tmem_slot + 1;
-  // PRE: the problems' first tiles, after the epilogue's store buffers
-  int* const s_tile0 = reinterpret_cast<int*>(smem + G_STAGES * G_STAGE_BYTES + 256 + G_EPI_STAGE_BYTES);
+  TInfo* ring = reinterpret_cast<TInfo*>(smem + NST * G_STAGE_BYTES + G_BAR_BYTES);
+  uint32_t* const epi_base = reinterpret_cast<uint32_t*>(smem + NST * G_STAGE_BYTES + G_BAR_BYTES + G_RING_BYTES);
+  // PRE: the problems' first tiles and column-block counts
+  int* const s_tile0 = reinterpret_cast<int*>(smem + g_off_tail(PRE));
+  int* const s_tn = s_tile0 + (PRE ? g.nprob : 0);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr uint32_t TMEM_COLS = 512;
   if constexpr (PRE)
-    for (int i = threadIdx.x; i < g.nprob; i += G_THREADS) s_tile0[i] = __ldg(g.tile0 + i);
+    for (int i = threadIdx.x; i < g.nprob; i += NTH) {
+      s_tile0[i] = __ldg(g.tile0 + i);
+      s_tn[i] = __ldg(&g.prob[i].tn);
+    }
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < G_STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);        // MMA commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 8);       // one arrival per epilogue warp
+      mbar_init(&tempty[b], EW);      // one arrival per epilogue warp
+    }
+    for (int r = 0; r < G_RING; ++r) {
+      mbar_init(&ifull[r], 1);        // the producer
+      mbar_init(&iempty[r], EW);      // one arrival per epilogue warp
     }
     mbar_init(drainb, 1);
-    mbar_init(doneb, 8);
+    mbar_init(doneb, EW);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -230,47 +320,57 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    // ------------------------------------------------ TMA producer
+    // ------------------------------------------------ producer: tile parameters, operand stages
     if (lane == 0) {
       uint32_t it = 0;              // k tiles issued by this CTA (all its tiles)
       bool stop = false;
-      for (int w = 0, t = g_wave_tile(0); t < g.total && !stop; t = g_wave_tile(++w)) {
-        if constexpr (PRE) {
-          const BTile x = b_tile(g, s_tile0, t);
-          const int ktiles = __ldg(&x.pr->ktiles);
-          const uint8_t* a = x.pr->At + (size_t)x.mb * ktiles * G_A_BYTES;
-          const uint8_t* b = x.pr->Bt + (size_t)x.nb * ktiles * G_B_BYTES;
-          for (int kt = 0; kt < ktiles; ++kt, ++it) {
-            const int s = (int)(it % G_STAGES);
-            if (*abort_flag || !mbar_wait(&empty[s], ((it / G_STAGES) & 1u) ^ 1u, abort_flag)) {
-              stop = true;
-              break;
-            }
-            uint8_t* sa = smem + s * G_STAGE_BYTES;
-            mbar_expect_tx(&full[s], G_STAGE_BYTES);
-            bulk_load(sa, a + (size_t)kt * G_A_BYTES, G_A_BYTES, &full[s]);
-            bulk_load(sa + G_A_BYTES, b + (size_t)kt * G_B_BYTES, G_B_BYTES, &full[s]);
+      int t = g_wave_tile(0);
+      bool have = t < g.total;
+      TLoad nx;
+      if (have) nx = tile_load(g, s_tile0, s_tn, t);
+      for (int lt = 0; have && !stop; ++lt) {
+        const TLoad cur = nx;
+        // the next tile's parameters are fetched now and used one tile later
+        t = g_wave_tile(lt + 1);
+        have = t < g.total;
+        if (have) nx = tile_load(g, s_tile0, s_tn, t);
+        const int slot = lt % G_RING;
+        if (lt >= G_RING && !mbar_wait(&iempty[slot], (uint32_t)((lt - G_RING) / G_RING) & 1u, abort_flag)) break;
+        ring[slot] = cur.x;
+        mbar_arrive(&ifull[slot]);    // release: the slot's contents are visible to the waiters
+        for (int kt = 0; kt < cur.x.ktiles; ++kt, ++it) {
+          const int s = (int)(it % NST);
+          if (*abort_flag || !mbar_wait(&empty[s], ((it / NST) & 1u) ^ 1u, abort_flag)) {
+            stop = true;
+            break;
           }
-        } else {
-          const GTile x = g_tile(g, t);
-          for (int kt = 0; kt < x.pr->ktiles; ++kt, ++it) {
-            const int s = (int)(it % G_STAGES);
-            if (*abort_flag || !mbar_wait(&empty[s], ((it / G_STAGES) & 1u) ^ 1u, abort_flag)) {
-              stop = true;
-              break;
-            }
-            uint8_t* sa = smem + s * G_STAGE_BYTES;
-            uint8_t* sb = sa + G_A_BYTES;
+          uint8_t* sa = smem + s * G_STAGE_BYTES;
+          if constexpr (PRE) {
+            // only what the MMAs' kept outputs read: A rows up to m (in whole 8-row groups), the
+            // B rows of the K = 32 steps issued, the second 128-column half of B only if n
+            // reaches it (the rest of the stage holds older bytes, which reach only accumulator
+            // rows and columns the epilogue never stores)
+            const uint32_t a_bytes = (uint32_t)((min(G_BM, cur.x.m - cur.x.m0) + 7) & ~7) * 128u;
+            const uint32_t b_rows = kt == cur.x.ktiles - 1 ? 32u * (uint32_t)cur.x.klast : 128u;
+            const uint32_t halves = cur.x.n - cur.x.n0 > 128 ? 2u : 1u;
+            mbar_expect_tx(&full[s], a_bytes + halves * b_rows * 128u);
+            bulk_load(sa, cur.a + (size_t)kt * G_A_BYTES, a_bytes, &full[s]);
+            const uint8_t* bsrc = cur.b + (size_t)kt * G_B_BYTES;
+            for (uint32_t h = 0; h < halves; ++h)
+              bulk_load(sa + G_A_BYTES + h * (G_B_BYTES / 2), bsrc + h * (G_B_BYTES / 2), b_rows * 128u, &full[s]);
+          } else {
             mbar_expect_tx(&full[s], G_STAGE_BYTES);
-            tma_load_2d(sa, &x.pr->ta, kt * G_BK, x.m0, &full[s]);
-            tma_load_2d(sb, &x.pr->tb, x.n0, kt * G_BK, &full[s]);
-            tma_load_2d(sb + G_B_BYTES / 2, &x.pr->tb, x.n0 + 128, kt * G_BK, &full[s]);
+            const GProb& pr = g.prob[cur.x.pi];
+            uint8_t* sb = sa + G_A_BYTES;
+            tma_load_2d(sa, &pr.ta, kt * G_BK, cur.x.m0, &full[s]);
+            tma_load_2d(sb, &pr.tb, cur.x.n0, kt * G_BK, &full[s]);
+            tma_load_2d(sb + G_B_BYTES / 2, &pr.tb, cur.x.n0 + 128, kt * G_BK, &full[s]);
           }
         }
       }
       // every armed stage must have landed before the CTA may exit (its shared memory is reused)
-      for (uint32_t j = (it > (uint32_t)G_STAGES ? it - G_STAGES : 0u); j < it; ++j)
-        mbar_drain(&full[j % G_STAGES], (j / G_STAGES) & 1u);
+      for (uint32_t j = (it > (uint32_t)NST ? it - NST : 0u); j < it; ++j)
+        mbar_drain(&full[j % NST], (j / NST) & 1u);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -279,24 +379,17 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
       constexpr uint32_t idesc = idesc_e4m3(G_BM, G_BN, true);
       uint32_t it = 0;
       bool stop = false;
-      int lt = 0;                   // tiles of this CTA so far
-      for (int w = 0, t = g_wave_tile(0); t < g.total && !stop; t = g_wave_tile(++w), ++lt) {
-        int ktiles, klast;
-        if constexpr (PRE) {
-          const BTile x = b_tile(g, s_tile0, t);
-          ktiles = __ldg(&x.pr->ktiles);
-          klast = __ldg(&x.pr->klast);
-        } else {
-          ktiles = g_tile(g, t).pr->ktiles;
-          klast = 4;
-        }
+      for (int lt = 0; g_wave_tile(lt) < g.total && !stop; ++lt) {
+        const int slot = lt % G_RING;
+        if (!mbar_wait(&ifull[slot], (uint32_t)(lt / G_RING) & 1u, abort_flag)) break;
+        const int ktiles = ring[slot].ktiles, klast = ring[slot].klast;
         const int buf = lt & 1;
         if (lt >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((lt - 2) >> 1) & 1u, abort_flag)) break;
         tc_fence_after();
         const uint32_t dtm = tmem + (uint32_t)(buf * 256);
         for (int kt = 0; kt < ktiles; ++kt, ++it) {
-          const int s = (int)(it % G_STAGES);
-          if (!mbar_wait(&full[s], (it / G_STAGES) & 1u, abort_flag)) {
+          const int s = (int)(it % NST);
+          if (!mbar_wait(&full[s], (it / NST) & 1u, abort_flag)) {
             stop = true;
             break;
           }
@@ -322,29 +415,24 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
     }
     __syncwarp();
   } else {
-    // ------------------------------------------------ epilogue (warps 2..9)
+    // ------------------------------------------------ epilogue (warps 2 .. 2 + EW - 1)
+    const int ew = warp - 2;                     // 0 .. EW - 1
     const int q = warp & 3;                      // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;            // column half (0: 0..127, 1: 128..255)
+    const int cg = ew >> 2;                      // 32-column blocks cg, cg + EW / 4, ... (< 8)
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    const uint32_t tid = threadIdx.x - 64;       // 0..255 over the epilogue warps
-    uint32_t* const epi_stage =                 // this warp's 32 x 36-byte store buffer
-        reinterpret_cast<uint32_t*>(smem + G_STAGES * G_STAGE_BYTES + 256) + (warp - 2) * (32 * 9);
+    const uint32_t tid = threadIdx.x - 64;       // 0..511 over the epilogue warps
+    constexpr uint32_t ET = 32 * EW;
+    uint32_t* const epi_stage = epi_base + ew * (32 * 9);   // this warp's 32 x 36-byte buffer
     uint32_t bad = 0;
-    int lt = 0;
-    for (int w = 0, t = g_wave_tile(0); t < g.total; t = g_wave_tile(++w), ++lt) {
-      const int buf = lt & 1;
-      int m0, n0;
-      const BProb* bpr = nullptr;
-      if constexpr (PRE) {
-        const BTile x = b_tile(g, s_tile0, t);
-        m0 = x.m0;
-        n0 = x.n0;
-        bpr = x.pr;
-      } else {
-        const GTile x = g_tile(g, t);
-        m0 = x.m0;
-        n0 = x.n0;
-        const GProb& pr = *x.pr;
+    for (int lt = 0; g_wave_tile(lt) < g.total; ++lt) {
+      const int buf = lt & 1, slot = lt % G_RING;
+      // one lane waits, the warp follows (tcgen05.ld needs all 32 lanes on the same path)
+      uint32_t got = 1;
+      if (lane == 0) got = mbar_wait(&ifull[slot], (uint32_t)(lt / G_RING) & 1u, abort_flag) ? 1u : 0u;
+      if (!__shfl_sync(0xffffffffu, got, 0)) break;
+      const TInfo x = ring[slot];
+      if constexpr (!PRE) {
+        const GProb& pr = g.prob[x.pi];
         if (!pr.checked) {
           // range check: a residue byte r >= p (p <= 17) has bit 7 set in r | (r + 128 - p),
           // with no carry between bytes unless bit 7 of the lower byte is already set
@@ -353,93 +441,67 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
           const uint32_t a_rows = (uint32_t)min(G_BM, pr.m - x.m0);
           const uint32_t a_units = a_rows * kc, a_per = (a_units + pr.tn - 1) / pr.tn;
           const uint32_t a_lo = min(a_units, (uint32_t)x.nb * a_per), a_hi = min(a_units, a_lo + a_per);
-          for (uint32_t u = a_lo + tid; u < a_hi; u += 256) {
+          for (uint32_t u = a_lo + tid; u < a_hi; u += ET) {
             const uint32_t r = u / kc, c = u - r * kc;
             bad |= range_bits(pr.A + (size_t)(x.m0 + r) * pr.lda + 16 * c, pr.k - 16 * (int)c, pk);
           }
           const uint32_t bc = (uint32_t)(min(G_BN, pr.n - x.n0) + 15) >> 4;  // 16-byte chunks per B row
           const uint32_t b_units = (uint32_t)pr.k * bc, b_per = (b_units + pr.tm - 1) / pr.tm;
           const uint32_t b_lo = min(b_units, (uint32_t)x.mb * b_per), b_hi = min(b_units, b_lo + b_per);
-          for (uint32_t u = b_lo + tid; u < b_hi; u += 256) {
+          for (uint32_t u = b_lo + tid; u < b_hi; u += ET) {
             const uint32_t r = u / bc, c = u - r * bc;
             bad |= range_bits(pr.B + (size_t)r * pr.ldb + x.n0 + 16 * c, pr.n - x.n0 - 16 * (int)c, pk);
           }
         }
       }
-      // one lane waits, the warp follows (tcgen05.ld needs all 32 lanes on the same path)
-      uint32_t got = 1;
+      got = 1;
       if (lane == 0) got = mbar_wait(&tfull[buf], (uint32_t)(lt >> 1) & 1u, abort_flag) ? 1u : 0u;
       if (!__shfl_sync(0xffffffffu, got, 0)) break;
       tc_fence_after();
-      // parameters in registers (read through the parameter block or the global problem list
-      // they would be reloaded after every store to C)
-      DivP dv;
-      uint32_t p, fdiv;
-      float c18, pm18, off18;
-      int m, n, ldc;
-      uint8_t* Cb;
-      if constexpr (PRE) {
-        // centred operands: the sum is signed, |sum| <= k (p/2)^2; adding p T >= that makes it
-        // non-negative and below 2^23, where FDIV applies (the router guarantees it)
-        const BProb* pr = bpr;
-        p = __ldg(&pr->p);
-        fdiv = 1u;
-        c18 = __ldg(&pr->c18);
-        pm18 = __ldg(&pr->pm18);
-        off18 = __ldg(&pr->off18);
-        m = __ldg(&pr->m);
-        n = __ldg(&pr->n);
-        ldc = __ldg(&pr->ldc);
-        Cb = pr->C;
-        dv = DivP{};
-      } else {
-        const GProb& pr = *g_tile(g, t).pr;
-        dv = pr.dv;
-        p = pr.p;
-        fdiv = pr.fdiv;
-        c18 = pr.c18;
-        pm18 = pr.pm18;
-        off18 = 0.0f;
-        m = pr.m;
-        n = pr.n;
-        ldc = pr.ldc;
-        Cb = pr.C;
-      }
+      // the MMA issuer read this slot before it committed the tile: the producer may reuse it
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&iempty[slot]);
+      const int m0 = x.m0, n0 = x.n0, m = x.m, n = x.n, ldc = x.ldc;
+      const uint32_t p = x.p, mp = x.mp;
+      const float mo = x.mo;
+      uint8_t* const Cb = x.C;
       const int row = m0 + q * 32 + lane;
       const bool rows_in = m0 + q * 32 < m;      // some row of this warp's quarter is in C
-      for (int cb = 0; cb < 4; ++cb) {
-        const int col0 = half * 128 + cb * 32;
+      for (int cb = cg; cb < 8; cb += EW / 4) {
+        const int col0 = cb * 32;
         // a block wholly in the tile's padding (thin products) is neither read nor stored
         // (warp-uniform, so tcgen05.ld stays converged)
         if (!rows_in || n0 + col0 >= n) continue;
         uint32_t v[32];
         tmem_ld32(tmem + lane_base + (uint32_t)(buf * 256 + col0), v);
         uint32_t packed[8];
-        if (fdiv) {
-          // Each sum is x 2^-18 with x < 2^23.  Algorithm FDIV, case 3 of Table fdiv (beta = 24):
-          // floor(x / p) = RD(x RU(1/p)), exact below 2^23; the floor of the product is taken by
-          // a round-down addition of 2^23, and x - p floor(x / p) is formed exactly in fp32.
+        if (x.fdiv) {
+          // Each sum is x 2^-18 with 0 <= y = x + off < 2^23 (off = p T for centred operands, else
+          // 0).  One FFMA forms 2^23 + y exactly (an integer in [2^23, 2^24): its low 23 bits are
+          // y), and y mod p comes from an invariant-divisor multiply: floor(y / p) =
+          // floor(y mp / 2^32) with mp = ceil(2^32 / p), exact for y < 2^23 and p < 2^9 (the
+          // product exceeds y / p by less than 2^-9 < 1 / p).
 #pragma unroll
           for (int j = 0; j < 32; j += 4) {
             uint32_t w = 0;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const float vs = PRE ? __uint_as_float(v[j + u]) + off18 : __uint_as_float(v[j + u]);
-              const float qf = __fadd_rd(__fmul_rd(vs, c18), 8388608.0f) - 8388608.0f;
-              const float rs = fmaf(pm18, qf, vs);                   // (x - p q) 2^-18, exact
-              w |= (__float_as_uint(fmaf(rs, 262144.0f, 8388608.0f)) - 0x4B000000u) << (8 * u);
+              const uint32_t y = __float_as_uint(fmaf(__uint_as_float(v[j + u]), 262144.0f, mo)) & 0x7FFFFFu;
+              w += (y - p * __umulhi(y, mp)) << (8 * u);
             }
             packed[j >> 2] = w;
           }
         } else {
+          // sums below 2^24 (TMA problems with k (p-1)^2 >= 2^23): the sum is 2^-18 times the
+          // integer y, so y = 2^18 x its value exactly; the same multiply-high gives y mod p
+          // (its error is below 2^24 / 2^32 = 2^-8 < 1 / p for p < 2^8)
 #pragma unroll
           for (int j = 0; j < 32; j += 4) {
             uint32_t w = 0;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              // the sum is 2^-18 times the integer sum: scaling back by 2^18 is exact
-              const uint32_t s = __float2uint_rn(__uint_as_float(v[j + u]) * 262144.0f);
-              w |= modp32(s, dv, p) << (8 * u);
+              const uint32_t y = __float2uint_rn(__uint_as_float(v[j + u]) * 262144.0f);
+              w += (y - p * __umulhi(y, mp)) << (8 * u);
             }
             packed[j >> 2] = w;
           }
@@ -450,12 +512,12 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
         if (__all_sync(0xffffffffu, vec)) {
           reinterpret_cast<uint4*>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
           reinterpret_cast<uint4*>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-        } else if (c0 < n) {
+        } else {
           // rows not 16-byte aligned (ldc not a multiple of 16) or a ragged edge: the warp's
           // 32 rows x 32 bytes go through shared memory and out one row at a time, the 32 lanes
-          // on consecutive bytes (one or two 32-byte sectors per store, not 32).  All 32 bytes
-          // are read before the first store, so the loads overlap instead of each waiting for
-          // the store before it.
+          // on consecutive bytes (one or two 32-byte sectors per store, not 32).  Eight rows'
+          // bytes are read before they are stored, so the loads overlap instead of each waiting
+          // for the store before it.
 #pragma unroll
           for (int j = 0; j < 8; ++j) epi_stage[lane * 9 + j] = packed[j];
           __syncwarp();
@@ -463,13 +525,16 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_mm_f8g(const __grid_constant__
           const int r0 = m0 + q * 32;
           const int rn = min(32, m - r0);
           const bool col_in = c0 + lane < n;
-          uint8_t b[32];
-#pragma unroll
-          for (int r = 0; r < 32; ++r) b[r] = sb[r * 36 + lane];
           uint8_t* dcol = Cb + (size_t)r0 * ldc + c0 + lane;
 #pragma unroll
-          for (int r = 0; r < 32; ++r)
-            if (col_in && r < rn) dcol[(size_t)r * ldc] = b[r];
+          for (int g8 = 0; g8 < 32; g8 += 8) {
+            uint8_t b[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) b[r] = sb[(g8 + r) * 36 + lane];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+              if (col_in && g8 + r < rn) dcol[(size_t)(g8 + r) * ldc] = b[r];
+          }
           __syncwarp();
         }
       }
@@ -529,10 +594,7 @@ static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int co
     g.tn = (x.n + G_BN - 1) / G_BN;
     g.tile0 = tile;
     g.p = x.p;
-    g.dv = make_divp(x.p);
     g.fdiv = (uint64_t)x.k * (x.p - 1) * (x.p - 1) < (1ull << 23) ? 1u : 0u;
-    g.c18 = make_redq(x.p, 1, 1).invp_f * 262144.0f;   // RU(1/p) scaled by 2^18 (exact)
-    g.pm18 = -(float)x.p / 262144.0f;
     g.checked = prechecked ? 1u : 0u;
     tile += g.tm * g.tn;
   }
@@ -540,7 +602,7 @@ static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int co
   hp.total = tile;
   const int grid = std::min(tile, ctx->num_sms);
   FP_CUDA(cudaFuncSetAttribute(k_mm_f8g<CAP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G_SMEM));
-  FP_LAUNCH(ctx, "k_mm_f8g", st, k_mm_f8g<CAP, false><<<grid, G_THREADS, G_SMEM, st>>>(hp, ctx->d_err));
+  FP_LAUNCH(ctx, "k_mm_f8g", st, k_mm_f8g<CAP, false><<<grid, g_threads(false), G_SMEM, st>>>(hp, ctx->d_err));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }
@@ -550,12 +612,13 @@ fp_status launch_mm_f8_pretiled(fp_ctx ctx, const F8PreProb* prob, const int* ti
   if (nprob <= 0 || total <= 0) return FP_OK;
   FP_CHECK(nprob <= F8_PRE_CAP, FP_EINVAL, "pre-tiled e4m3 launch: too many problems");
   const BParams hp{prob, tile0, nprob, total};
-  const size_t smem = G_SMEM + sizeof(int) * (size_t)F8_PRE_CAP;
-  static_assert(G_SMEM + sizeof(int) * F8_PRE_CAP <= 227 * 1024, "shared memory per block");
+  const size_t smem = G_SMEM_PRE + 2 * sizeof(int) * (size_t)F8_PRE_CAP;
+  static_assert(G_SMEM_PRE + 2 * sizeof(int) * F8_PRE_CAP <= 227 * 1024, "shared memory per block");
   const int grid = std::min(total, ctx->num_sms);
   FP_CUDA(cudaFuncSetAttribute(k_mm_f8g<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FP_LAUNCH(ctx, "k_mm_f8g_pre", st,
-            k_mm_f8g<1, true><<<grid, G_THREADS, G_SMEM + sizeof(int) * (size_t)nprob, st>>>(hp, ctx->d_err));
+            k_mm_f8g<1, true><<<grid, g_threads(true), G_SMEM_PRE + 2 * sizeof(int) * (size_t)nprob, st>>>(
+                hp, ctx->d_err));
   FP_CUDA(cudaGetLastError());
   return FP_OK;
 }
