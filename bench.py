@@ -824,9 +824,10 @@ def run_batch(args, ws, rank, local, emit=True):
             assert np.array_equal(C[rows].cpu().numpy(), field.matmul_mod_rows(x.a, x.b, x.p, rows))
         else:
             assert int(C.cpu().numpy().view(np.uint32)[0]) == field.dot_mod(x.a, x.b, x.p)
-    per_instance()
-    torch.cuda.synchronize()
-    fp.fp_ctx_status(ctx1)
+    if not args.no_compare:
+        per_instance()
+        torch.cuda.synchronize()
+        fp.fp_ctx_status(ctx1)
 
     def timed(fn, reps):
         # `reps` consecutive steps between two synchronisations (the inputs exceed L2), so one
@@ -862,11 +863,11 @@ def run_batch(args, ws, rank, local, emit=True):
         c, ms = fp.fp_ctx_profile_read(ctx, nm)
         if c:
             kern[nm] = {"launches_per_step": c / args.steps, "ms_per_step": ms / args.steps}
-    tp = timed(per_instance, max(2, args.steps // 5))
+    tp = None if args.no_compare else timed(per_instance, max(2, args.steps // 5))
     fp.fp_ctx_status(ctx)
     fp.fp_ctx_status(ctx1)
     v_b = macs / (statistics.median(tb) / 1e3)
-    v_p = macs / (statistics.median(tp) / 1e3)
+    v_p = None if tp is None else macs / (statistics.median(tp) / 1e3)
 
     # end to end: every input in, the call, every result out (one copy each way per step)
     def e2e():
@@ -926,16 +927,19 @@ def run_batch(args, ws, rank, local, emit=True):
                       "macs_per_step": macs, "instances": len(insts), "input_bytes": in_bytes, "output_bytes": out_bytes,
                       "autotuner": "on for the batch (packing degree per (p, k class) timed once on the first call); "
                                    "the per-instance arm uses a second context with the fixed rule"},
-           "per_instance_launches": {"value": v_p, "unit": "F_p MAC/s", "ms_per_step": statistics.median(tp),
-                                     "launches": "one fp_matmul / fp_dot call per instance (fixed AUTO rule)"},
-           "speedup_vs_per_instance": v_b / v_p,
+           "per_instance_launches": None if tp is None else {
+               "value": v_p, "unit": "F_p MAC/s", "ms_per_step": statistics.median(tp),
+               "launches": "one fp_matmul / fp_dot call per instance (fixed AUTO rule)"},
+           "speedup_vs_per_instance": None if v_p is None else v_b / v_p,
            "timing": "consecutive steps between two synchronisations, inputs larger than L2",
            "gpu_launches": launches,
            "clocks": clk.summary(),
            "kernels": kern,
            "roofline": {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peaks_k[dom][0],
                         "unit": "TFLOP/s", "frac": achieved / peaks_k[dom][0], "peak_source": peaks_k[dom][1],
-                        "traffic": None,
+                        "traffic": stored_traffic(dom, [("uneven_batch", len(insts))], 1),
+                        "traffic_source": "profiles/traffic.json (ncu capture of the same step; null if the "
+                                          "kernel's source changed since)",
                         "note": "achieved = 2 x the kernel's own F_p MACs per step / its time per step"},
            "cpu_baseline": cpu,
            "e2e": {"value": macs / (statistics.median(te) / 1e3), "unit": "F_p MAC/s", "h2d_bytes_per_step": in_bytes,
@@ -1532,7 +1536,8 @@ def main():
     ap.add_argument("--workload", default="matmul", choices=["matmul", "batch", "serve", "polymul", "gf"],
                     help="matmul: the compressed-matmul configuration (default line); batch: 4096 uneven instances")
     ap.add_argument("--algo", default="AUTO")
-    ap.add_argument("--no-compare", action="store_true", help="skip the per-variant comparison block")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the per-variant comparison block (batch: the per-instance arm)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--problems", default="", help="subset, e.g. 3:4096,7:1024 (default: all four)")
     ap.add_argument("--no-graph", action="store_true", help="time plain launches instead of CUDA-graph replays")
