@@ -472,38 +472,43 @@ __global__ void __launch_bounds__(g_threads(PRE), 1) k_mm_f8g(const __grid_const
         // a block wholly in the tile's padding (thin products) is neither read nor stored
         // (warp-uniform, so tcgen05.ld stays converged)
         if (!rows_in || n0 + col0 >= n) continue;
-        uint32_t v[32];
-        tmem_ld32(tmem + lane_base + (uint32_t)(buf * 256 + col0), v);
+        // two loads of 16 columns (fewer live registers than one of 32)
         uint32_t packed[8];
-        if (x.fdiv) {
-          // Each sum is x 2^-18 with 0 <= y = x + off < 2^23 (off = p T for centred operands, else
-          // 0).  One FFMA forms 2^23 + y exactly (an integer in [2^23, 2^24): its low 23 bits are
-          // y), and y mod p comes from an invariant-divisor multiply: floor(y / p) =
-          // floor(y mp / 2^32) with mp = ceil(2^32 / p), exact for y < 2^23 and p < 2^9 (the
-          // product exceeds y / p by less than 2^-9 < 1 / p).
 #pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            uint32_t w = 0;
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t v[16];
+          tmem_ld16_nowait(tmem + lane_base + (uint32_t)(buf * 256 + col0 + 16 * hh), v);
+          tmem_wait();
+          if (x.fdiv) {
+            // Each sum is x 2^-18 with 0 <= y = x + off < 2^23 (off = p T for centred operands,
+            // else 0).  One FFMA forms 2^23 + y exactly (an integer in [2^23, 2^24): its low 23
+            // bits are y), and y mod p comes from an invariant-divisor multiply: floor(y / p) =
+            // floor(y mp / 2^32) with mp = ceil(2^32 / p), exact for y < 2^23 and p < 2^9 (the
+            // product exceeds y / p by less than 2^-9 < 1 / p).
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const uint32_t y = __float_as_uint(fmaf(__uint_as_float(v[j + u]), 262144.0f, mo)) & 0x7FFFFFu;
-              w += (y - p * __umulhi(y, mp)) << (8 * u);
+            for (int j = 0; j < 16; j += 4) {
+              uint32_t w = 0;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const uint32_t y = __float_as_uint(fmaf(__uint_as_float(v[j + u]), 262144.0f, mo)) & 0x7FFFFFu;
+                w += (y - p * __umulhi(y, mp)) << (8 * u);
+              }
+              packed[4 * hh + (j >> 2)] = w;
             }
-            packed[j >> 2] = w;
-          }
-        } else {
-          // sums below 2^24 (TMA problems with k (p-1)^2 >= 2^23): the sum is 2^-18 times the
-          // integer y, so y = 2^18 x its value exactly; the same multiply-high gives y mod p
-          // (its error is below 2^24 / 2^32 = 2^-8 < 1 / p for p < 2^8)
+          } else {
+            // sums below 2^24 (TMA problems with k (p-1)^2 >= 2^23): the sum is 2^-18 times the
+            // integer y, so y = 2^18 x its value exactly; the same multiply-high gives y mod p
+            // (its error is below 2^24 / 2^32 = 2^-8 < 1 / p for p < 2^8)
 #pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            uint32_t w = 0;
+            for (int j = 0; j < 16; j += 4) {
+              uint32_t w = 0;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const uint32_t y = __float2uint_rn(__uint_as_float(v[j + u]) * 262144.0f);
-              w += (y - p * __umulhi(y, mp)) << (8 * u);
+              for (int u = 0; u < 4; ++u) {
+                const uint32_t y = __float2uint_rn(__uint_as_float(v[j + u]) * 262144.0f);
+                w += (y - p * __umulhi(y, mp)) << (8 * u);
+              }
+              packed[4 * hh + (j >> 2)] = w;
             }
-            packed[j >> 2] = w;
           }
         }
         const int c0 = n0 + col0;                   // the same for the whole warp
@@ -514,26 +519,70 @@ __global__ void __launch_bounds__(g_threads(PRE), 1) k_mm_f8g(const __grid_const
           reinterpret_cast<uint4*>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
         } else {
           // rows not 16-byte aligned (ldc not a multiple of 16) or a ragged edge: the warp's
-          // 32 rows x 32 bytes go through shared memory and out one row at a time, the 32 lanes
-          // on consecutive bytes (one or two 32-byte sectors per store, not 32).  Eight rows'
-          // bytes are read before they are stored, so the loads overlap instead of each waiting
-          // for the store before it.
+          // 32 rows x 32 bytes go through shared memory and out with the lanes along the rows
+          // (one or two 32-byte sectors per row, not 32 rows per store), each lane writing the
+          // widest unit C's alignment allows: 4 bytes (8 lanes per row, 4 rows per store) when
+          // C and ldc are multiples of 4, 2 bytes (2 rows per store) when even, else 1.  Each
+          // group's values are read before they are stored, so the loads overlap.
 #pragma unroll
           for (int j = 0; j < 8; ++j) epi_stage[lane * 9 + j] = packed[j];
           __syncwarp();
           const uint8_t* sb = reinterpret_cast<const uint8_t*>(epi_stage);
           const int r0 = m0 + q * 32;
           const int rn = min(32, m - r0);
-          const bool col_in = c0 + lane < n;
-          uint8_t* dcol = Cb + (size_t)r0 * ldc + c0 + lane;
+          const int nv = n - c0;                       // valid columns of the block (>= 1)
+          uint8_t* const dblk = Cb + (size_t)r0 * ldc + c0;
+          const uint32_t al = (uint32_t)(((uintptr_t)Cb) | (uintptr_t)ldc);
+          if ((al & 3u) == 0) {
+            const int lr = lane >> 3, lc = 4 * (lane & 7);   // row in the group, first column
+            const bool col_ok = lc < nv, whole = lc + 4 <= nv;
+            uint8_t* d = dblk + (size_t)lr * ldc + lc;
+            const size_t step = (size_t)4 * ldc;
+#pragma unroll 1
+            for (int h = 0; h < 8; h += 4) {
+              uint32_t wv[4];
 #pragma unroll
-          for (int g8 = 0; g8 < 32; g8 += 8) {
-            uint8_t b[8];
+              for (int g = 0; g < 4; ++g) wv[g] = epi_stage[(4 * (h + g) + lr) * 9 + (lane & 7)];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) b[r] = sb[(g8 + r) * 36 + lane];
+              for (int g = 0; g < 4; ++g, d += step) {
+                if (4 * (h + g) + lr >= rn || !col_ok) continue;
+                if (whole) {
+                  *reinterpret_cast<uint32_t*>(d) = wv[g];
+                } else {
+                  for (int e = 0; lc + e < nv; ++e) d[e] = (uint8_t)(wv[g] >> (8 * e));
+                }
+              }
+            }
+          } else if ((al & 1u) == 0) {
+            const int lr = lane >> 4, lc = 2 * (lane & 15);
+            const bool col_ok = lc < nv, whole = lc + 2 <= nv;
+            uint8_t* d = dblk + (size_t)lr * ldc + lc;
+            const size_t step = (size_t)2 * ldc;
+#pragma unroll 1
+            for (int h = 0; h < 16; h += 4) {
+              uint32_t hv[4];
 #pragma unroll
-            for (int r = 0; r < 8; ++r)
-              if (col_in && g8 + r < rn) dcol[(size_t)(g8 + r) * ldc] = b[r];
+              for (int g = 0; g < 4; ++g)
+                hv[g] = *reinterpret_cast<const uint16_t*>(sb + (2 * (h + g) + lr) * 36 + lc);
+#pragma unroll
+              for (int g = 0; g < 4; ++g, d += step) {
+                if (2 * (h + g) + lr >= rn || !col_ok) continue;
+                if (whole) *reinterpret_cast<uint16_t*>(d) = (uint16_t)hv[g];
+                else d[0] = (uint8_t)hv[g];
+              }
+            }
+          } else {
+            const bool col_ok = lane < nv;
+            uint8_t* d = dblk + lane;
+#pragma unroll 1
+            for (int g8 = 0; g8 < 32; g8 += 8) {
+              uint8_t b[8];
+#pragma unroll
+              for (int r = 0; r < 8; ++r) b[r] = sb[(g8 + r) * 36 + lane];
+#pragma unroll
+              for (int r = 0; r < 8; ++r, d += ldc)
+                if (col_ok && g8 + r < rn) *d = b[r];
+            }
           }
           __syncwarp();
         }
