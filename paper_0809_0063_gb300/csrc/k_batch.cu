@@ -715,7 +715,11 @@ static fp_status batch_run_tc(fp_ctx ctx, const std::vector<const fp_instance*>&
     fp_status s = upload_staged(ctx, 0, base, h.data(), desc, st);
     if (s != FP_OK) return s;
     const uint32_t njobs = (uint32_t)(2 * np);
-    const int grid = (int)std::min<uint64_t>(nblk, (uint64_t)ctx->num_sms * 8);
+    // one wave of resident CTAs: each takes a fixed contiguous range of blocks, so a CTA that
+    // had to wait for a free slot would finish a whole range after the others
+    static int per_sm = 0;
+    if (per_sm == 0) FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pack, 256, 0));
+    const int grid = (int)std::min<uint64_t>(nblk, (uint64_t)ctx->num_sms * std::max(1, per_sm));
     FP_LAUNCH(ctx, "k_tile_pack", st,
               k_tile_pack<<<grid, 256, 0, st>>>((const TileJob*)(base + o_jobs), njobs, (uint32_t)nblk, ctx->d_err));
     FP_CUDA(cudaGetLastError());
