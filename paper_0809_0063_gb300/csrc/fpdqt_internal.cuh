@@ -461,9 +461,8 @@ struct F8PreProb {
 // tile of each problem, tiles of a problem in row-block-major order), total tiles.  Lock held.
 fp_status launch_mm_f8_pretiled(fp_ctx ctx, const F8PreProb* prob, const int* tile0, int nprob, int total,
                                 cudaStream_t st);
-// lock held; prechecked: the caller has range-checked every A and B (the kernel skips its check)
-fp_status launch_mm_f8_grouped_locked(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st,
-                                      bool prechecked);
+// lock held
+fp_status launch_mm_f8_grouped_locked(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st);
 // grouped 16-bit tensor-core products (k_tcp.cu): packed fp16 (right compression, p <= 3)
 // or plain bf16
 bool f16p_ok(uint32_t p, int k);

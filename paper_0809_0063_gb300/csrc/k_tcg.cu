@@ -80,12 +80,9 @@ struct GProb {
   int tile0;        // index of this problem's first tile in the global list
   uint32_t p;
   uint32_t fdiv;    // 1 when k (p-1)^2 < 2^23: the epilogue forms each sum with one FFMA
-  uint32_t checked; // 1: the caller range-checked A and B already (the epilogue skips its check)
 };
 
-// CAP problems per launch: FP_GROUP_MAX for the public grouped call, G_BATCH_CAP for the
-// tensor-core share of an uneven batch (the parameter block stays under the 32 KB limit).
-static constexpr int G_BATCH_CAP = 64;
+// CAP problems per launch (FP_GROUP_MAX: the parameter block stays under the 32 KB limit).
 template <int CAP>
 struct GParamsT {
   GProb prob[CAP];
@@ -93,7 +90,7 @@ struct GParamsT {
   int total;        // tiles over all problems
 };
 using GParams = GParamsT<FP_GROUP_MAX>;
-static_assert(sizeof(GParamsT<G_BATCH_CAP>) < 32000, "kernel parameter block limit");
+static_assert(sizeof(GParamsT<FP_GROUP_MAX>) < 32000, "kernel parameter block limit");
 
 // Pre-tiled problems (the tensor-core share of an uneven batch, layout in fpdqt_internal.cuh):
 // a stage is two plain bulk copies, no tensor map, so any row stride or alignment of the
@@ -433,7 +430,7 @@ __global__ void __launch_bounds__(g_threads(PRE), 1) k_mm_f8g(const __grid_const
       const TInfo x = ring[slot];
       if constexpr (!PRE) {
         const GProb& pr = g.prob[x.pi];
-        if (!pr.checked) {
+        {
           // range check: a residue byte r >= p (p <= 17) has bit 7 set in r | (r + 128 - p),
           // with no carry between bytes unless bit 7 of the lower byte is already set
           const uint32_t pk = 0x01010101u * (128u - pr.p);
@@ -617,8 +614,7 @@ bool f8_direct_ok(uint32_t p, int k, const uint8_t* A, int lda, const uint8_t* B
 
 // One launch over up to CAP problems, each already validated and f8_direct_ok.
 template <int CAP>
-static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int count, cudaStream_t st,
-                              bool prechecked) {
+static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int count, cudaStream_t st) {
   GParamsT<CAP> hp;    // passed by value as the kernel's (grid-constant) parameter block
   std::memset(&hp, 0, sizeof hp);
   int tile = 0;
@@ -644,7 +640,6 @@ static fp_status launch_group(fp_ctx ctx, const fp_mm_problem* const* pr, int co
     g.tile0 = tile;
     g.p = x.p;
     g.fdiv = (uint64_t)x.k * (x.p - 1) * (x.p - 1) < (1ull << 23) ? 1u : 0u;
-    g.checked = prechecked ? 1u : 0u;
     tile += g.tm * g.tn;
   }
   hp.nprob = count;
@@ -675,27 +670,22 @@ fp_status launch_mm_f8_pretiled(fp_ctx ctx, const F8PreProb* prob, const int* ti
 // One problem (the caller holds the context lock).
 fp_status launch_mm_f8_direct(fp_ctx ctx, const fp_mm_problem& x, cudaStream_t st) {
   const fp_mm_problem* one = &x;
-  return launch_group<FP_GROUP_MAX>(ctx, &one, 1, st, false);
+  return launch_group<FP_GROUP_MAX>(ctx, &one, 1, st);
 }
 
-// Problems that pass f8_direct_ok, in launches of up to FP_GROUP_MAX problems (G_BATCH_CAP for
-// an uneven batch's prechecked share: its many small problems need several tiles per CTA and
-// launch to overlap their pipelines); within a launch the problems with the most k tiles come
-// first so the longest tiles start earliest.
+// Problems that pass f8_direct_ok, in launches of up to FP_GROUP_MAX problems; within a launch
+// the problems with the most k tiles come first so the longest tiles start earliest.
 fp_status launch_mm_f8_grouped(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(ctx->mu);
-  return launch_mm_f8_grouped_locked(ctx, pr, count, st, false);
+  return launch_mm_f8_grouped_locked(ctx, pr, count, st);
 }
 
-fp_status launch_mm_f8_grouped_locked(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st,
-                                      bool prechecked) {
+fp_status launch_mm_f8_grouped_locked(fp_ctx ctx, const fp_mm_problem* const* pr, size_t count, cudaStream_t st) {
   std::vector<const fp_mm_problem*> v(pr, pr + count);
   std::stable_sort(v.begin(), v.end(), [](const fp_mm_problem* a, const fp_mm_problem* b) { return a->k > b->k; });
-  const size_t cap = prechecked ? G_BATCH_CAP : FP_GROUP_MAX;
-  for (size_t i = 0; i < v.size(); i += cap) {
-    const int c = (int)std::min<size_t>(cap, v.size() - i);
-    fp_status s = prechecked ? launch_group<G_BATCH_CAP>(ctx, v.data() + i, c, st, true)
-                             : launch_group<FP_GROUP_MAX>(ctx, v.data() + i, c, st, false);
+  for (size_t i = 0; i < v.size(); i += FP_GROUP_MAX) {
+    const int c = (int)std::min<size_t>(FP_GROUP_MAX, v.size() - i);
+    fp_status s = launch_group<FP_GROUP_MAX>(ctx, v.data() + i, c, st);
     if (s != FP_OK) return s;
   }
   return FP_OK;

@@ -325,7 +325,7 @@ struct fp_server_s {
         ptr.push_back(&tcp[j]);
         ++j;
       }
-      ok = launch_mm_f8_grouped_locked(ctx, ptr.data(), ptr.size(), st, false) == FP_OK;
+      ok = launch_mm_f8_grouped_locked(ctx, ptr.data(), ptr.size(), st) == FP_OK;
       launches += (ptr.size() + FP_GROUP_MAX - 1) / FP_GROUP_MAX;
     }
     if (ok) ok = cudaMemcpyAsync(h_out[s], dbase + out_region, total - out_region, cudaMemcpyDeviceToHost, st) == cudaSuccess;
