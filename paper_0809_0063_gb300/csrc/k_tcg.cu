@@ -24,8 +24,9 @@
 //   warps 2..    epilogue of tile i (tcgen05.ld, scale, mod p, stores: 16-byte stores where a
 //                row is 16-byte aligned, else through a small per-warp buffer with the lanes
 //                on consecutive bytes of a row) while the MMAs of tile i + 1 run into the other
-//                buffer; 2 (TMA problems) or 3 (pre-tiled) warps per TMEM lane quarter, taking
-//                its 32-column blocks in turn.  Before
+//                buffer; 2 (TMA problems) or 4 (pre-tiled) warps per TMEM lane quarter, taking
+//                its 32-column blocks in turn (pre-tiled: all of a warp's blocks are reduced
+//                into shared memory and the accumulator released before the stores).  Before
 //                waiting for a tile's accumulator they range-check a slice of its inputs with
 //                plain global loads (off the shared-memory pipeline): the A panel of (problem,
 //                row block) is used by the tiles of every column block and the B panel of
@@ -51,9 +52,10 @@ static constexpr int G_A_BYTES = G_BM * G_BK;                 // 16 KB
 static constexpr int G_B_BYTES = G_BN * G_BK;                 // 32 KB (two 128-column boxes)
 static constexpr int G_STAGE_BYTES = G_A_BYTES + G_B_BYTES;   // 48 KB
 // epilogue warps: 2 per TMEM lane quarter for TMA problems (long tiles, the epilogue hidden
-// behind the MMAs), 3 for pre-tiled ones (short tiles of uneven batches: the epilogue is
-// latency-bound and more warps hide more of it)
-__host__ __device__ constexpr int g_epi_warps(bool pre) { return pre ? 12 : 8; }
+// behind the MMAs), 4 for pre-tiled ones (short tiles of uneven batches: the epilogue is
+// latency-bound and more warps hide more of it; 8, 12, 16 warps: 0.58, 0.556, 0.486 ms on the
+// benchmark batch, the last with the stores after the accumulator's release)
+__host__ __device__ constexpr int g_epi_warps(bool pre) { return pre ? 16 : 8; }
 __host__ __device__ constexpr int g_threads(bool pre) { return 64 + 32 * g_epi_warps(pre); }
 // Shared memory: the stage ring, barriers, tmem address and abort flag (G_BAR_BYTES), the tile
 // parameter ring (G_RING_BYTES), the epilogue warps' store buffers (32 rows x 36 bytes each: row
@@ -62,8 +64,13 @@ __host__ __device__ constexpr int g_threads(bool pre) { return 64 + 32 * g_epi_w
 static constexpr int G_STAGES_PRE = 3;
 static constexpr int G_BAR_BYTES = 256, G_RING_BYTES = 512;
 __host__ __device__ constexpr int g_stages(bool pre) { return pre ? G_STAGES_PRE : G_STAGES; }
+// 32 x 32-byte blocks each epilogue warp stages at once: pre-tiled, all of a tile's (8 blocks per
+// lane quarter shared by g_epi_warps / 4 warps)
+__host__ __device__ constexpr int g_stage_blocks(bool pre) {
+  return pre ? (8 + g_epi_warps(pre) / 4 - 1) / (g_epi_warps(pre) / 4) : 1;
+}
 __host__ __device__ constexpr int g_off_tail(bool pre) {
-  return g_stages(pre) * G_STAGE_BYTES + G_BAR_BYTES + G_RING_BYTES + g_epi_warps(pre) * 32 * 36;
+  return g_stages(pre) * G_STAGE_BYTES + G_BAR_BYTES + G_RING_BYTES + g_epi_warps(pre) * g_stage_blocks(pre) * 32 * 36;
 }
 static constexpr size_t G_SMEM = 1024 + g_off_tail(false);
 static constexpr size_t G_SMEM_PRE = 1024 + g_off_tail(true);
@@ -134,6 +141,78 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                    su32(dst)),
                "l"(src), "r"(bytes), "r"(su32(bar))
                : "memory");
+}
+
+// Stores one 32 x 32-byte block of C (rows r0 .. r0 + rn - 1, columns c0 .. c0 + nv - 1 of the
+// block) whose bytes sit in `stg` (row r at stg + 9 r words), one warp.  16-byte stores from each
+// lane's row when all 32 rows are whole and 16-byte aligned; else the lanes along the rows (one
+// or two 32-byte sectors per row, not 32 rows per store), each lane writing the widest unit C's
+// alignment allows: 4 bytes (8 lanes per row, 4 rows per store) when C and ldc are multiples of
+// 4, 2 bytes (2 rows per store) when even, else 1.  Each group's values are read before they are
+// stored, so the loads overlap; a running row pointer keeps few addresses live.
+__device__ __forceinline__ void store_block(const uint32_t* stg, uint8_t* Cb, int ldc, int r0, int rn, int c0,
+                                            int nv, int lane) {
+  uint8_t* const dblk = Cb + (size_t)r0 * ldc + c0;
+  const bool vec = lane < rn && nv >= 32 && ((((uintptr_t)(dblk + (size_t)lane * ldc)) & 15u) == 0);
+  if (__all_sync(0xffffffffu, vec)) {
+    const uint32_t* w = stg + lane * 9;
+    uint4* d = reinterpret_cast<uint4*>(dblk + (size_t)lane * ldc);
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    return;
+  }
+  const uint8_t* sb = reinterpret_cast<const uint8_t*>(stg);
+  const uint32_t al = (uint32_t)(((uintptr_t)Cb) | (uintptr_t)ldc);
+  if ((al & 3u) == 0) {
+    const int lr = lane >> 3, lc = 4 * (lane & 7);   // row in the group, first column
+    const bool col_ok = lc < nv, whole = lc + 4 <= nv;
+    uint8_t* d = dblk + (size_t)lr * ldc + lc;
+    const size_t step = (size_t)4 * ldc;
+#pragma unroll 1
+    for (int h = 0; h < 8; h += 4) {
+      uint32_t wv[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) wv[g] = stg[(4 * (h + g) + lr) * 9 + (lane & 7)];
+#pragma unroll
+      for (int g = 0; g < 4; ++g, d += step) {
+        if (4 * (h + g) + lr >= rn || !col_ok) continue;
+        if (whole) {
+          *reinterpret_cast<uint32_t*>(d) = wv[g];
+        } else {
+          for (int e = 0; lc + e < nv; ++e) d[e] = (uint8_t)(wv[g] >> (8 * e));
+        }
+      }
+    }
+  } else if ((al & 1u) == 0) {
+    const int lr = lane >> 4, lc = 2 * (lane & 15);
+    const bool col_ok = lc < nv, whole = lc + 2 <= nv;
+    uint8_t* d = dblk + (size_t)lr * ldc + lc;
+    const size_t step = (size_t)2 * ldc;
+#pragma unroll 1
+    for (int h = 0; h < 16; h += 4) {
+      uint32_t hv[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) hv[g] = *reinterpret_cast<const uint16_t*>(sb + (2 * (h + g) + lr) * 36 + lc);
+#pragma unroll
+      for (int g = 0; g < 4; ++g, d += step) {
+        if (2 * (h + g) + lr >= rn || !col_ok) continue;
+        if (whole) *reinterpret_cast<uint16_t*>(d) = (uint16_t)hv[g];
+        else d[0] = (uint8_t)hv[g];
+      }
+    }
+  } else {
+    const bool col_ok = lane < nv;
+    uint8_t* d = dblk + lane;
+#pragma unroll 1
+    for (int g8 = 0; g8 < 32; g8 += 8) {
+      uint8_t b[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) b[r] = sb[(g8 + r) * 36 + lane];
+#pragma unroll
+      for (int r = 0; r < 8; ++r, d += ldc)
+        if (col_ok && g8 + r < rn) *d = b[r];
+    }
+  }
 }
 
 // Bit 7 of a byte of the result is set where one of the `valid` bytes at src (at most 16;
@@ -419,7 +498,8 @@ __global__ void __launch_bounds__(g_threads(PRE), 1) k_mm_f8g(const __grid_const
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const uint32_t tid = threadIdx.x - 64;       // 0..511 over the epilogue warps
     constexpr uint32_t ET = 32 * EW;
-    uint32_t* const epi_stage = epi_base + ew * (32 * 9);   // this warp's 32 x 36-byte buffer
+    // this warp's stage: g_stage_blocks(PRE) blocks of 32 rows x 36 bytes
+    uint32_t* const epi_stage = epi_base + ew * (g_stage_blocks(PRE) * 32 * 9);
     uint32_t bad = 0;
     for (int lt = 0; g_wave_tile(lt) < g.total; ++lt) {
       const int buf = lt & 1, slot = lt % G_RING;
@@ -463,8 +543,14 @@ __global__ void __launch_bounds__(g_threads(PRE), 1) k_mm_f8g(const __grid_const
       const float mo = x.mo;
       uint8_t* const Cb = x.C;
       const int row = m0 + q * 32 + lane;
-      const bool rows_in = m0 + q * 32 < m;      // some row of this warp's quarter is in C
-      for (int cb = cg; cb < 8; cb += EW / 4) {
+      const int r0 = m0 + q * 32, rn = min(32, m - r0);
+      const bool rows_in = rn > 0;               // some row of this warp's quarter is in C
+      // Pre-tiled (short tiles): every block of this warp is reduced into its stage first, the
+      // accumulator buffer is released, and only then are the blocks stored, so the MMAs of the
+      // tile after next need not wait for the stores.  TMA problems (long tiles): each block is
+      // stored as soon as it is reduced (16-byte stores straight from registers when aligned).
+      int jb = 0;
+      for (int cb = cg; cb < 8; cb += EW / 4, ++jb) {
         const int col0 = cb * 32;
         // a block wholly in the tile's padding (thin products) is neither read nor stored
         // (warp-uniform, so tcgen05.ld stays converged)
@@ -509,84 +595,38 @@ __global__ void __launch_bounds__(g_threads(PRE), 1) k_mm_f8g(const __grid_const
           }
         }
         const int c0 = n0 + col0;                   // the same for the whole warp
-        uint8_t* dst = Cb + (size_t)row * ldc + c0;
-        const bool vec = row < m && c0 + 32 <= n && ((((uintptr_t)dst) & 15u) == 0);
-        if (__all_sync(0xffffffffu, vec)) {
-          reinterpret_cast<uint4*>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-          reinterpret_cast<uint4*>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        if constexpr (PRE) {
+          uint32_t* const stg = epi_stage + jb * (32 * 9);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) stg[lane * 9 + j] = packed[j];
         } else {
-          // rows not 16-byte aligned (ldc not a multiple of 16) or a ragged edge: the warp's
-          // 32 rows x 32 bytes go through shared memory and out with the lanes along the rows
-          // (one or two 32-byte sectors per row, not 32 rows per store), each lane writing the
-          // widest unit C's alignment allows: 4 bytes (8 lanes per row, 4 rows per store) when
-          // C and ldc are multiples of 4, 2 bytes (2 rows per store) when even, else 1.  Each
-          // group's values are read before they are stored, so the loads overlap.
-#pragma unroll
-          for (int j = 0; j < 8; ++j) epi_stage[lane * 9 + j] = packed[j];
-          __syncwarp();
-          const uint8_t* sb = reinterpret_cast<const uint8_t*>(epi_stage);
-          const int r0 = m0 + q * 32;
-          const int rn = min(32, m - r0);
-          const int nv = n - c0;                       // valid columns of the block (>= 1)
-          uint8_t* const dblk = Cb + (size_t)r0 * ldc + c0;
-          const uint32_t al = (uint32_t)(((uintptr_t)Cb) | (uintptr_t)ldc);
-          if ((al & 3u) == 0) {
-            const int lr = lane >> 3, lc = 4 * (lane & 7);   // row in the group, first column
-            const bool col_ok = lc < nv, whole = lc + 4 <= nv;
-            uint8_t* d = dblk + (size_t)lr * ldc + lc;
-            const size_t step = (size_t)4 * ldc;
-#pragma unroll 1
-            for (int h = 0; h < 8; h += 4) {
-              uint32_t wv[4];
-#pragma unroll
-              for (int g = 0; g < 4; ++g) wv[g] = epi_stage[(4 * (h + g) + lr) * 9 + (lane & 7)];
-#pragma unroll
-              for (int g = 0; g < 4; ++g, d += step) {
-                if (4 * (h + g) + lr >= rn || !col_ok) continue;
-                if (whole) {
-                  *reinterpret_cast<uint32_t*>(d) = wv[g];
-                } else {
-                  for (int e = 0; lc + e < nv; ++e) d[e] = (uint8_t)(wv[g] >> (8 * e));
-                }
-              }
-            }
-          } else if ((al & 1u) == 0) {
-            const int lr = lane >> 4, lc = 2 * (lane & 15);
-            const bool col_ok = lc < nv, whole = lc + 2 <= nv;
-            uint8_t* d = dblk + (size_t)lr * ldc + lc;
-            const size_t step = (size_t)2 * ldc;
-#pragma unroll 1
-            for (int h = 0; h < 16; h += 4) {
-              uint32_t hv[4];
-#pragma unroll
-              for (int g = 0; g < 4; ++g)
-                hv[g] = *reinterpret_cast<const uint16_t*>(sb + (2 * (h + g) + lr) * 36 + lc);
-#pragma unroll
-              for (int g = 0; g < 4; ++g, d += step) {
-                if (2 * (h + g) + lr >= rn || !col_ok) continue;
-                if (whole) *reinterpret_cast<uint16_t*>(d) = (uint16_t)hv[g];
-                else d[0] = (uint8_t)hv[g];
-              }
-            }
+          uint8_t* dst = Cb + (size_t)row * ldc + c0;
+          const bool vec = row < m && c0 + 32 <= n && ((((uintptr_t)dst) & 15u) == 0);
+          if (__all_sync(0xffffffffu, vec)) {
+            reinterpret_cast<uint4*>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            reinterpret_cast<uint4*>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
           } else {
-            const bool col_ok = lane < nv;
-            uint8_t* d = dblk + lane;
-#pragma unroll 1
-            for (int g8 = 0; g8 < 32; g8 += 8) {
-              uint8_t b[8];
 #pragma unroll
-              for (int r = 0; r < 8; ++r) b[r] = sb[(g8 + r) * 36 + lane];
-#pragma unroll
-              for (int r = 0; r < 8; ++r, d += ldc)
-                if (col_ok && g8 + r < rn) *d = b[r];
-            }
+            for (int j = 0; j < 8; ++j) epi_stage[lane * 9 + j] = packed[j];
+            __syncwarp();
+            store_block(epi_stage, Cb, ldc, r0, rn, c0, n - c0, lane);
+            __syncwarp();
           }
-          __syncwarp();
         }
       }
+      // TMEM buffer drained: the MMAs of the tile after next may start
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[buf]);
+      if constexpr (PRE) {
+        jb = 0;
+        for (int cb = cg; cb < 8; cb += EW / 4, ++jb) {
+          const int c0 = n0 + cb * 32;
+          if (!rows_in || c0 >= n) continue;
+          store_block(epi_stage + jb * (32 * 9), Cb, ldc, r0, rn, c0, n - c0, lane);
+        }
+        __syncwarp();                            // the stage is reused by the next tile
+      }
     }
     if (bad & 0x80808080u) flag_error(err, ERR_RANGE);
     __syncwarp();
