@@ -866,6 +866,16 @@ def run_batch(args, ws, rank, local, emit=True):
     tp = None if args.no_compare else timed(per_instance, max(2, args.steps // 5))
     fp.fp_ctx_status(ctx)
     fp.fp_ctx_status(ctx1)
+    # the same call captured once into a CUDA graph (plans written by kernels inside the graph)
+    # and replayed: no host work per step
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batched()
+    for _ in range(2):
+        graph.replay()
+    tg = timed(graph.replay, args.steps)
+    fp.fp_ctx_status(ctx)
+    del graph
     v_b = macs / (statistics.median(tb) / 1e3)
     v_p = None if tp is None else macs / (statistics.median(tp) / 1e3)
 
@@ -932,6 +942,9 @@ def run_batch(args, ws, rank, local, emit=True):
                "launches": "one fp_matmul / fp_dot call per instance (fixed AUTO rule)"},
            "speedup_vs_per_instance": None if v_p is None else v_b / v_p,
            "timing": "consecutive steps between two synchronisations, inputs larger than L2",
+           "graph_replay": {"value": macs / (statistics.median(tg) / 1e3), "unit": "F_p MAC/s",
+                            "ms_per_step": statistics.median(tg),
+                            "note": "the same call captured once in a CUDA graph, replayed"},
            "gpu_launches": launches,
            "clocks": clk.summary(),
            "kernels": kern,

@@ -142,13 +142,24 @@ fp_status ensure_scratch(fp_ctx ctx, size_t bytes, int which, cudaStream_t st) {
 // that a stream capture records by value (a captured copy from pinned host memory would read
 // the staging buffer again at every replay, after later calls had rewritten it).
 struct InlineChunk {
-  static constexpr uint32_t CAP = 16384;
+  static constexpr uint32_t CAP = 32000;   // the parameter block stays under the 32 KB limit
   uint32_t n;
   uint8_t b[CAP];
 };
 
+// One 4-byte word per thread over as many CTAs as the chunk needs: kernel parameters are read
+// through the constant cache, which serves one address per cycle, so one CTA reading a whole
+// chunk (a byte per load) took ~19 us per chunk; spread over CTAs (one SM's cache each) and read
+// by words it takes a few.
 __global__ void k_put_bytes(uint8_t* __restrict__ dst, const __grid_constant__ InlineChunk c) {
-  for (uint32_t i = threadIdx.x; i < c.n; i += blockDim.x) dst[i] = c.b[i];
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nw = c.n / 4;
+  if ((((uintptr_t)dst) & 3u) == 0) {
+    if (i < nw) reinterpret_cast<uint32_t*>(dst)[i] = reinterpret_cast<const uint32_t*>(c.b)[i];
+    if (i < c.n - 4 * nw) dst[4 * nw + i] = c.b[4 * nw + i];
+  } else {
+    for (uint32_t j = i; j < c.n; j += gridDim.x * blockDim.x) dst[j] = c.b[j];
+  }
 }
 
 static fp_status upload_inline(fp_ctx ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
@@ -158,7 +169,8 @@ static fp_status upload_inline(fp_ctx ctx, void* dst, const void* src, size_t by
   for (size_t off = 0; off < bytes; off += InlineChunk::CAP) {
     c.n = (uint32_t)std::min<size_t>(InlineChunk::CAP, bytes - off);
     std::memcpy(c.b, (const uint8_t*)src + off, c.n);
-    FP_LAUNCH(ctx, "k_put_bytes", st, k_put_bytes<<<1, 256, 0, st>>>((uint8_t*)dst + off, c));
+    const int grid = (int)((c.n / 4 + 255) / 256) + 1;
+    FP_LAUNCH(ctx, "k_put_bytes", st, k_put_bytes<<<grid, 256, 0, st>>>((uint8_t*)dst + off, c));
     FP_CUDA(cudaGetLastError());
   }
   return FP_OK;
