@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import gc
 import json
 import os
 import statistics
@@ -1016,9 +1017,16 @@ def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0, emit=True):
         fp.fp_server_destroy(srv)
         return wall, lat, st
 
-    # warm-up (first-use costs: module load, tables), then the paced run and the capacity run
+    # warm-up (first-use costs: module load, tables), then the paced run and the capacity run;
+    # the collector is run once and held off during the paced run (a collection in the
+    # submitting thread would delay arrivals by milliseconds)
     serve(False)
-    wall_p, lat_p, st_p = serve(True)
+    gc.collect()
+    gc.disable()
+    try:
+        wall_p, lat_p, st_p = serve(True)
+    finally:
+        gc.enable()
     fp.fp_ctx_profile(ctx, 2)
     fp.fp_ctx_profile(ctx, 1)
     wall_c, lat_c, st_c = serve(False)

@@ -243,3 +243,27 @@ def test_grouped_bound_refused_before_enqueue(env):
     fp.fp_ctx_status(ctx)
     assert fp.fp_ctx_launches(ctx) == l0
     assert np.all(fine.C.cpu().numpy() == 253)
+
+
+@pytest.mark.parametrize("c_off", [0, 1, 2, 4])
+@pytest.mark.parametrize("ldc_extra", [0, 1, 2, 4, 8, 16])
+def test_plain_f8_stores_any_c_alignment(env, c_off, ldc_extra):
+    """The e4m3 epilogue stores rows of C 16 bytes per lane when they are 16-byte aligned, else
+    4, 2 or 1 bytes per lane as C's address and ldc allow: a product with C starting 0, 1, 2 or 4
+    bytes past an aligned address and ldc = n + 0 .. 16 reaches every path, with ragged row and
+    column blocks; every entry against the oracle, and nothing written outside the n columns."""
+    fp, torch, dev, ctx = env
+    p, m, n, k = 7, 150, 304, 208          # A and B rows 16-byte aligned: read in place by TMA
+    a, b = workloads.matmul_inputs(900 + c_off * 31 + ldc_extra, p, m, k, n)
+    ldc = n + ldc_extra
+    A = torch.from_numpy(a).to(dev)
+    B = torch.from_numpy(b).to(dev)
+    buf = torch.full((c_off + m * ldc + 64,), 251, dtype=torch.uint8, device=dev)
+    C = buf[c_off:c_off + m * ldc]
+    fp.fp_matmul(ctx, p, m, n, k, A, k, B, n, C, ldc, fp.FP_MM_PLAIN_F8)
+    fp.fp_ctx_status(ctx)
+    out = buf.cpu().numpy()
+    assert (out[:c_off] == 251).all() and (out[c_off + m * ldc:] == 251).all()
+    got = out[c_off:c_off + m * ldc].reshape(m, ldc)
+    np.testing.assert_array_equal(got[:, :n], field.matmul_mod(a, b, p))
+    assert (got[:, n:] == 251).all()
