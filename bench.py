@@ -1001,7 +1001,7 @@ def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0, emit=True):
                              host_a=A.ctypes.data, host_b=B.ctypes.data, host_out=out.ctypes.data)
 
     def serve(paced):
-        srv = fp.fp_server_create(ctx, arena_bytes=8 << 30, streams=4, max_batch=512, window_us=100)
+        srv = fp.fp_server_create(ctx, arena_bytes=8 << 30, streams=4, max_batch=512, window_us=args.serve_window_us)
         t0 = time.perf_counter()
         first = None
         for r, d in zip(reqs, data):
@@ -1121,7 +1121,7 @@ def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0, emit=True):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
            "config": {"workload": f"Poisson {rate:.0f} req/s for {duration} s: 50% polymul (deg 2-512, p in 3,5,7), "
                                   "30% dot (64-65536), 15% GF(3^5)/GF(7^4)/GF(2^8) batches (1-4096), 5% matmul (64-1024)",
-                      "requests": len(reqs), "fp_macs": macs, "server": "4 streams, 8 GiB arena, max_batch 512, 100 us window"},
+                      "requests": len(reqs), "fp_macs": macs, "server": f"4 streams, 8 GiB arena, max_batch 512, {args.serve_window_us} us window"},
            "latency_us_at_offered_load": {"p50": pct(lat_p, 50), "p99": pct(lat_p, 99), "p999": pct(lat_p, 99.9),
                                           "max": float(lat_p.max()), "wall_s": wall_p, "batches": st_p["batches"]},
            "capacity": {"requests_per_s": cap_rps, "fp_macs_per_s": macs / wall_c, "batches": st_c["batches"],
@@ -1565,6 +1565,8 @@ def main():
     ap.add_argument("--no-packed", action="store_true", help="skip the packed DQT+REDQ arm of the default line")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the nested polynomial, GF, uneven-batch and serving sub-results of the default line")
+    ap.add_argument("--serve-window-us", type=int, default=100,
+                    help="serving: how long a forming batch may wait to grow while the GPU is busy")
     ap.add_argument("--no-autotune", action="store_true",
                     help="AUTO uses the fixed rule instead of timing candidates (for runs under a profiler)")
     ap.add_argument("--min-warmup-s", type=float, default=1.0,
