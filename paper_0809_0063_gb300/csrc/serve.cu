@@ -24,6 +24,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <sys/prctl.h>
+
 #include "arena.h"
 #include "fpdqt_internal.cuh"
 
@@ -352,6 +354,9 @@ struct fp_server_s {
 
   void loop() {
     cudaSetDevice(device);
+    // the idle wait below is a few microseconds: with the default 50 us timer slack every idle
+    // iteration would sleep ~55 us, late both for new requests and for completed batches
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
     double oldest_wait_start = 0;
     while (true) {
       {
@@ -391,7 +396,7 @@ struct fp_server_s {
         std::lock_guard<std::mutex> lk(qmu);
         if (incoming.empty()) break;
       }
-      if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(5));
+      if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(2));
     }
   }
 };
