@@ -384,8 +384,13 @@ __global__ void __launch_bounds__(256) k_polymul_f3(const uint8_t* __restrict__ 
   if (op.bad & 0x80808080u) flag_error(err, ERR_RANGE);
 }
 
+// Launched with programmatic dependent launch: the launch of the next kernel on the stream (and
+// its blocks' scheduling) overlaps this one, while griddepcontrol.wait, before any global access,
+// keeps every read and write after the previous kernel's have completed.
 __global__ void __launch_bounds__(256) k_polymul_f3_direct(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
                                                            uint8_t* __restrict__ Cout, uint64_t nitems, uint32_t* err) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   PolyF3Op op{0};
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nitems; i += stride)
@@ -447,8 +452,18 @@ static bool launch_polymul_small_k(fp_ctx ctx, const uint8_t* A, const uint8_t* 
   if (KA == 3 && KB == 3 && P.p == 3 && P.b == 4) {   // the fixed F_3 degree-2 form
     if (ntiles <= POLY_DIRECT_TILES) {
       const uint64_t nitems = ntiles * (PAIRS / 4);
-      FP_LAUNCH(ctx, "k_polymul_small", st,
-                (k_polymul_f3_direct<<<(int)((nitems + 255) / 256), 256, 0, st>>>(A, B, C, nitems, ctx->d_err)));
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)((nitems + 255) / 256));
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      uint32_t* err = ctx->d_err;
+      FP_LAUNCH(ctx, "k_polymul_small", st, (cudaLaunchKernelEx(&cfg, k_polymul_f3_direct, A, B, C, nitems, err)));
     } else {
       cudaFuncSetAttribute(k_polymul_f3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       FP_LAUNCH(ctx, "k_polymul_small", st, (k_polymul_f3<<<grid, 256, smem, st>>>(A, B, C, ntiles, ctx->d_err)));
