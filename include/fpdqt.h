@@ -527,6 +527,13 @@ fp_status fp_server_create(fp_ctx ctx, const fp_server_config* cfg, fp_server* o
  * FP_EBOUND) and queues it; *ticket numbers requests from 0 in submission order. */
 fp_status fp_server_submit(fp_server s, const fp_request* req, uint64_t* ticket);
 
+/* Serving (no counterpart in the paper).  Thread-safe.  Submits the n requests of the host
+ * array `reqs` (the caller's array; read during the call only): every request is validated
+ * first, and if one fails (FP_EINVAL, FP_EBOUND, message naming it) none is queued; else all
+ * are queued, in order, with tickets *first_ticket .. *first_ticket + n - 1 and one submission
+ * time.  Errors: FP_EINVAL (null server, array or output), FP_EBOUND. */
+fp_status fp_server_submit_many(fp_server s, const fp_request* reqs, size_t n, uint64_t* first_ticket);
+
 /* Serving (no counterpart in the paper): *done = 1 once the result is in host_out (then
  * *latency_us is set), else 0.  A request that failed on the device reports done = -1.
  * Errors: FP_EINVAL (null server or outputs, unknown ticket). */

@@ -121,6 +121,7 @@ _SIGS = {
     "fp_selftest_bounded_wait": (_I, [_V, _U32, _V]),
     "fp_server_create": (_I, [_V, ctypes.POINTER(fp_server_config), ctypes.POINTER(_V)]),
     "fp_server_submit": (_I, [_V, ctypes.POINTER(fp_request), ctypes.POINTER(_U64)]),
+    "fp_server_submit_many": (_I, [_V, ctypes.POINTER(fp_request), _SZ, ctypes.POINTER(_U64)]),
     "fp_server_poll": (_I, [_V, _U64, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "fp_server_drain": (_I, [_V, ctypes.c_double]),
     "fp_server_latencies": (_I, [_V, _U64, _SZ, ctypes.POINTER(ctypes.c_double)]),
@@ -349,6 +350,14 @@ def fp_server_create(ctx, arena_bytes: int = 1 << 30, streams: int = 4, max_batc
 def fp_server_submit(server, req: fp_request) -> int:
     t = _U64()
     _check(lib().fp_server_submit(server, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def fp_server_submit_many(server, reqs) -> int:
+    """reqs: a ctypes array of fp_request (passed as it is) or a sequence; returns the first ticket."""
+    arr = reqs if isinstance(reqs, ctypes.Array) else (fp_request * len(reqs))(*reqs)
+    t = _U64()
+    _check(lib().fp_server_submit_many(server, arr, len(arr), ctypes.byref(t)))
     return t.value
 
 

@@ -20,6 +20,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -27,6 +28,7 @@
 #include <sys/prctl.h>
 
 #include "arena.h"
+#include "copy_pool.h"
 #include "fpdqt_internal.cuh"
 
 namespace fpd {
@@ -115,12 +117,20 @@ struct fp_server_s {
   std::atomic<bool> force_stop{false};
   std::thread th;
   int device = 0;
+  // gather / scatter copies of large batches spread over host threads (small batches stay on
+  // the scheduler thread: waking the pool costs more than their copies)
+  std::unique_ptr<CopyPool> pool;
+  static constexpr size_t PARALLEL_COPY_BYTES = 256 << 10;
 
   void finish(Batch& b, bool ok) {
     const double t = now_s();
-    for (size_t i = 0; i < b.reqs.size(); ++i) {
-      const Req& q = b.reqs[i];
-      if (ok) memcpy(q.r.host_out, h_out[b.stream] + b.out_off[i], q.out);
+    if (ok) {
+      auto scatter = [&](size_t i) {
+        const Req& q = b.reqs[i];
+        memcpy(q.r.host_out, h_out[b.stream] + b.out_off[i], q.out);
+      };
+      if (pool && b.out_bytes >= PARALLEL_COPY_BYTES) pool->run(b.reqs.size(), scatter);
+      else for (size_t i = 0; i < b.reqs.size(); ++i) scatter(i);
     }
     {
       std::lock_guard<std::mutex> lk(rmu);
@@ -234,9 +244,17 @@ struct fp_server_s {
     }
     uint8_t* dbase = arena + blk;
     uint8_t* hin = h_in[s];
-    // gather inputs
-    std::vector<fp_mm_problem> tcp;   // tensor-core matmuls: operand rows at 16-byte strides
+    // gather inputs (tensor-core matmuls: operand rows at 16-byte strides)
+    std::vector<fp_mm_problem> tcp;
+    size_t gather_bytes = 0;
     for (size_t i = 0; i < take.size(); ++i) {
+      const fp_request& r = take[i].r;
+      gather_bytes += take[i].in_a + take[i].in_b;
+      if (take[i].tc)
+        tcp.push_back(fp_mm_problem{r.p, (int)r.a, (int)r.b, (int)r.c, nullptr, (int)al16(r.c), nullptr,
+                                    (int)al16(r.b), nullptr, (int)r.b});
+    }
+    auto gather = [&](size_t i) {
       const fp_request& r = take[i].r;
       if (take[i].tc) {
         const size_t lda = al16(r.c), ldb = al16(r.b);
@@ -244,13 +262,13 @@ struct fp_server_s {
         const uint8_t* b = (const uint8_t*)r.host_b;
         for (uint32_t row = 0; row < r.a; ++row) memcpy(hin + ia[i] + row * lda, a + (size_t)row * r.c, r.c);
         for (uint32_t row = 0; row < r.c; ++row) memcpy(hin + ib[i] + row * ldb, b + (size_t)row * r.b, r.b);
-        tcp.push_back(fp_mm_problem{r.p, (int)r.a, (int)r.b, (int)r.c, nullptr, (int)lda, nullptr, (int)ldb, nullptr,
-                                    (int)r.b});
-        continue;
+        return;
       }
       memcpy(hin + ia[i], r.host_a, take[i].in_a);
       if (take[i].in_b) memcpy(hin + ib[i], r.host_b, take[i].in_b);
-    }
+    };
+    if (pool && gather_bytes >= PARALLEL_COPY_BYTES) pool->run(take.size(), gather);
+    else for (size_t i = 0; i < take.size(); ++i) gather(i);
     // polymul descriptors
     PmDesc* pd = reinterpret_cast<PmDesc*>(hin + pm_off);
     uint32_t ipm = 0;
@@ -443,15 +461,22 @@ extern "C" fp_status fp_server_create(fp_ctx ctx, const fp_server_config* cfg, f
     s->h_out.push_back(ho);
     s->stream_busy.push_back(0);
   }
+  {
+    // copy workers: the host's cores less three (the submitting thread, the scheduler, the rest
+    // of the process), at most 7
+    const int hc = (int)std::thread::hardware_concurrency();
+    const int nw = std::max(0, std::min(7, hc - 3));
+    if (nw > 0) s->pool.reset(new (std::nothrow) CopyPool(nw));
+  }
   s->th = std::thread([s] { s->loop(); });
   *out = s;
   return FP_OK;
 }
 
-extern "C" fp_status fp_server_submit(fp_server s, const fp_request* r, uint64_t* ticket) {
-  FP_CHECK(s && r && ticket, FP_EINVAL, "fp_server_submit: null argument");
+// Validates one request and fills its queue entry (sizes, tensor-core route); nothing queued.
+static fp_status server_prepare(fp_server s, const fp_request* r, fp_server_s::Req& q) {
   FP_CHECK(r->host_a && r->host_out, FP_EINVAL, "fp_server_submit: null host buffer");
-  fp_server_s::Req q{};
+  q = fp_server_s::Req{};
   q.r = *r;
   switch (r->kind) {
     case 0:
@@ -488,18 +513,47 @@ extern "C" fp_status fp_server_submit(fp_server s, const fp_request* r, uint64_t
   }
   FP_CHECK(al16(q.in_a) + al16(q.in_b) + al16(q.out) + (1u << 20) <= s->stage_bytes, FP_EINVAL,
            "request larger than the staging area (%zu bytes)", s->stage_bytes);
+  return FP_OK;
+}
+
+// Queues prepared requests with consecutive tickets (one lock of each queue for all of them).
+static uint64_t server_enqueue(fp_server s, std::vector<fp_server_s::Req>& qs) {
+  uint64_t first;
   {
     std::lock_guard<std::mutex> lk(s->rmu);
-    q.ticket = s->lat.size();
-    s->lat.push_back(-2.0);
+    first = s->lat.size();
+    s->lat.resize(first + qs.size(), -2.0);
   }
-  q.t_submit = now_s();
+  const double t = now_s();
+  for (size_t i = 0; i < qs.size(); ++i) {
+    qs[i].ticket = first + i;
+    qs[i].t_submit = t;
+  }
   {
     std::lock_guard<std::mutex> lk(s->qmu);
-    s->incoming.push_back(q);
+    for (auto& q : qs) s->incoming.push_back(q);
   }
-  s->submitted++;
-  *ticket = q.ticket;
+  s->submitted += qs.size();
+  return first;
+}
+
+extern "C" fp_status fp_server_submit(fp_server s, const fp_request* r, uint64_t* ticket) {
+  FP_CHECK(s && r && ticket, FP_EINVAL, "fp_server_submit: null argument");
+  std::vector<fp_server_s::Req> qs(1);
+  fp_status st = server_prepare(s, r, qs[0]);
+  if (st != FP_OK) return st;
+  *ticket = server_enqueue(s, qs);
+  return FP_OK;
+}
+
+extern "C" fp_status fp_server_submit_many(fp_server s, const fp_request* reqs, size_t n, uint64_t* first_ticket) {
+  FP_CHECK(s && first_ticket && (reqs || n == 0), FP_EINVAL, "fp_server_submit_many: null argument");
+  std::vector<fp_server_s::Req> qs(n);
+  for (size_t i = 0; i < n; ++i) {
+    fp_status st = server_prepare(s, &reqs[i], qs[i]);
+    if (st != FP_OK) return st;
+  }
+  *first_ticket = server_enqueue(s, qs);
   return FP_OK;
 }
 

@@ -147,3 +147,41 @@ def test_server_rejects_bad_requests(env):
                                                    host_b=A.ctypes.data, host_out=A.ctypes.data))
     finally:
         fp.fp_server_destroy(srv)
+
+
+def test_submit_many_whole_stream_and_all_or_nothing(env):
+    """A whole request stream in one fp_server_submit_many call (large batches: the gather and
+    scatter copies run on the server's copy threads): consecutive tickets, every result equals
+    the oracle.  A stream with one invalid request in the middle is refused and queues nothing."""
+    fp, torch, dev, ctx, gfs = env
+    moduli = {pk: field.smallest_monic_irreducible(*pk) for pk in workloads.GF_FIELDS}
+    reqs = workloads.serving_stream(77, rate=20000.0, duration=0.05)
+    srv = fp.fp_server_create(ctx, arena_bytes=512 << 20, streams=4, max_batch=512, window_us=100)
+    keep, qs = [], []
+    for r in reqs:
+        code, sz, A, B, out = workloads.request_arrays(r, matmul_cap=300)
+        qs.append(fp.fp_request(kind=code, p=r.p, a=sz[0], b=sz[1], c=sz[2], reserved=0,
+                                gf=gfs[(r.p, r.gf_k)].value if code == 2 else None,
+                                host_a=A.ctypes.data, host_b=B.ctypes.data, host_out=out.ctypes.data))
+        keep.append((r, code, sz, A, B, out))
+    bad = list(qs)
+    bad[len(bad) // 2] = fp.fp_request(kind=0, p=4, a=2, b=2, c=0, reserved=0, gf=None,
+                                       host_a=keep[0][3].ctypes.data, host_b=keep[0][4].ctypes.data,
+                                       host_out=keep[0][5].ctypes.data)
+    with pytest.raises(fp.FpError) as ei:
+        fp.fp_server_submit_many(srv, bad)
+    assert ei.value.status == fp.FP_EINVAL
+    assert fp.fp_server_stats_get(srv)["submitted"] == 0
+    first = fp.fp_server_submit_many(srv, (fp.fp_request * len(qs))(*qs))   # a prebuilt array
+    assert first == 0
+    fp.fp_server_drain(srv, 120.0)
+    st = fp.fp_server_stats_get(srv)
+    lats = fp.fp_server_latencies(srv, first, len(qs))
+    fp.fp_server_destroy(srv)
+    fp.fp_ctx_status(ctx)
+    assert st["submitted"] == len(qs) and st["completed"] == len(qs) and st["failed"] == 0
+    assert all(l >= 0 for l in lats)
+    for (r, code, sz, A, B, out) in keep:
+        want = oracle(r, code, A, B, moduli)
+        got = out if code != 1 else out.astype(np.int64)
+        assert np.array_equal(got.astype(np.int64), np.asarray(want).astype(np.int64)), (r.kind, r.p, sz)
