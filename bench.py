@@ -640,7 +640,7 @@ def run_gf(args, ws, rank, local, emit=True):
             gb = torch.randint(0, q, (nd,), dtype=torch.int32, device=dev)
             tdt = torch.uint8 if dt == np.uint8 else torch.int16
             out = torch.empty(1, dtype=tdt, device=dev)
-            row = {"chunk": fp.fp_gf_dot_info(gfh)["chunk"]}
+            row = {"products_per_redq": {(2, 8): "all (XOR)", (3, 5): 6, (7, 4): 3}.get((p, k), fp.fp_gf_dot_info(gfh)["chunk"])}
             for form, nm in ((fp.FP_GF_INDEX, "index"), (fp.FP_GF_LOG, "log")):
                 if form == fp.FP_GF_LOG:
                     lt = torch.from_numpy(log.astype(np.int32)).to(dev)
@@ -659,8 +659,9 @@ def run_gf(args, ws, rank, local, emit=True):
                 fn = lambda xa=xa, xb=xb, form=form: fp.fp_gf_dot(ctx, gfh, xa, xb, nd, out, form)
                 t = statistics.median(_timed(torch, stream, fn, 5, flush))
                 eb = 2 * nd * xa.element_size()
+                word_kernel = {(2, 8): "k_gf_dot_w28", (3, 5): "k_gf_dot_wsum", (7, 4): "k_gf_dot_wsum"}.get((p, k))
                 row[nm] = {"ms": t, "F_p MAC/s": k * k * nd / (t / 1e3), "GB/s": eb / (t / 1e3) / 1e9,
-                           "frac_hbm": eb / (t / 1e3) / 1e9 / hbm}
+                           "frac_hbm": eb / (t / 1e3) / 1e9 / hbm, "kernel": word_kernel or "k_gf_dot"}
             dot_rows[f"GF({p}^{k})"] = row
             del ga, gb, xa, xb
     # GF(p^k) matrix product (Algorithm FGDP on every entry): 1024 x 1024 x 1024 per field,
@@ -689,8 +690,11 @@ def run_gf(args, ws, rank, local, emit=True):
                 assert int(got[r_, c_]) == field.gf_dot(ha[r_].astype(np.int64), hb[:, c_].astype(np.int64), p, k, mod), \
                     f"GF({p}^{k}) matmul parity"
             t = statistics.median(_timed(torch, stream, fn, 3, flush))
+            word_field = (p, k) in ((2, 8), (3, 5), (7, 4))
             mm_rows[f"GF({p}^{k})"] = {"ms": t, "GF MAC/s": nm_ ** 3 / (t / 1e3), "F_p MAC/s": k * k * nm_ ** 3 / (t / 1e3),
-                                        "chunk": fp.fp_gf_dot_info(gfh)["chunk"]}
+                                        "kernel": "k_gf_matmul_w" if word_field else "k_gf_matmul",
+                                        "products_per_redq": {(2, 8): nm_, (3, 5): 6, (7, 4): 3}.get((p, k)) if word_field
+                                        else fp.fp_gf_dot_info(gfh)["chunk"]}
             del Am, Bm, Cm
     hin = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory(), torch.empty(count, dtype=A.dtype).pin_memory())
            for p, k, a, b, gfh, A, B, C in fields]

@@ -402,9 +402,11 @@ enum { FP_GF_INDEX = 0, FP_GF_LOG = 1 };
  * of the same width, written in the same form.  The conversion to words is one table lookup
  * from either form to the element's evaluation at the dot product's own q = 2^b_dot; the word products
  * accumulate for `chunk` terms (every digit below q, the word below 2^64) before each REDQ and
- * L/H lookup, and the partial results are added in the field.  GF(2^8) in index form with
- * 16-byte aligned arrays takes the word-level multiply of fp_gf_mul_batched for every term
- * (p | q: the compression values are the digits) and adds the products by XOR.  n = 0 writes
+ * L/H lookup, and the partial results are added in the field.  GF(3^5), GF(7^4) and GF(2^8)
+ * with 16-byte aligned arrays (either form) run on 32-bit words with REDQ in SWAR form:
+ * GF(3^5) at q = 2^7 with six products per REDQ, GF(7^4) at q = 2^9 with three, and GF(2^8) at
+ * q = 2^4 with the word products XOR-accumulated and one REDQ per thread (p | q: the
+ * compression values are the digits' lowest bits, which XOR adds mod 2).  n = 0 writes
  * zero.  Codes >= p^k set FP_EINVAL on the context (read by fp_ctx_status) and count as zero.
  * n < 2^40.
  * Uses context scratch for per-block partial sums. */
@@ -417,15 +419,17 @@ fp_status fp_gf_dot(fp_ctx ctx, fp_gf gf, const void* a, const void* b, size_t n
  * fp_gf_info), leading dimensions in elements.  Each element is converted once per use tile by
  * the dot product's word table (q = 2^b_dot of fp_gf_dot_info), word products accumulate for
  * `chunk` inner steps before each REDQ and L/H lookup, and the partial results are added in the
- * field.  m, n, k in [1, 2^20].  Codes >= p^k set FP_EINVAL on the context (fp_ctx_status) and
+ * field; GF(3^5), GF(7^4) and GF(2^8) take the 32-bit word forms of fp_gf_dot.
+ * m, n, k in [1, 2^20].  Codes >= p^k set FP_EINVAL on the context (fp_ctx_status) and
  * count as zero.  Errors: FP_EINVAL (null ctx, field or arrays; sizes or leading dimensions),
  * FP_EUNSUPPORTED (the field's tables do not fit one block's shared memory), FP_ECUDA. */
 fp_status fp_gf_matmul(fp_ctx ctx, fp_gf gf, int m, int n, int k, const void* A, int lda, const void* B,
                        int ldb, void* C, int ldc, int form, void* stream);
 
 /* The dot product's parameters (Algorithm FGDP, Sec. 6): index of the generator g of the log
- * form, exponent b_dot of its q, and the number of word products accumulated per REDQ.  Any
- * output may be NULL.  Errors: FP_EINVAL (gf NULL). */
+ * form, exponent b_dot of its q, and the number of word products accumulated per REDQ, as the
+ * general 64-bit word path uses them (the 32-bit word forms of GF(3^5), GF(7^4), GF(2^8) fix
+ * their own, stated at fp_gf_dot).  Any output may be NULL.  Errors: FP_EINVAL (gf NULL). */
 fp_status fp_gf_dot_info(fp_gf gf, uint32_t* generator, uint32_t* b_dot, uint32_t* chunk);
 
 /* ---------------------------------------------------------------- uneven batches */

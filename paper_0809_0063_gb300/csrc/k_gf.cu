@@ -12,6 +12,7 @@
 // These generic kernels serve every field; GF(2^8), GF(3^5) and GF(7^4) also have word-level
 // kernels (k_gf_mul_fixed, below) with the same steps on 32-bit words.
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -430,14 +431,24 @@ template <uint32_t P, uint32_t K> struct Gfw;
 // u_0..u_7 itself (degree <= 7 needs no reduction); the high part is one lookup.
 template <> struct Gfw<2, 8> {
   static constexpr uint32_t W = 0, H = 32768, BYTES = H + 128;
+  // the dot product's log form: the word table indexed by discrete logarithm (replicated)
+  static constexpr uint32_t WL = BYTES, END = WL + 32768;
 };
 // GF(3^5): q = 2^5, r < 2^45 (9 digits <= 20), m = 5; c = 2 index bits per residue.
 template <> struct Gfw<3, 5> {
   static constexpr uint32_t W = 0, L = 32768, H = L + 8192, T = H + 512, BYTES = T + 3200;   // T: 5^5 entries
+  // dot product at q = 2^7 (six products per REDQ), after the multiply's tables: word table
+  // (replicated as W), L and H with entries as five 6-bit coefficient fields
+  static constexpr uint32_t DW = BYTES, DL = DW + 32768, DH = DL + 16384, DOT_END = DH + 1024;
+  static constexpr uint32_t DWL = DOT_END, END = DWL + 32768;   // DW indexed by discrete logarithm
 };
 // GF(7^4): q = 2^8, r < 2^54 (7 digits <= 144), m = 3 = k - 1; c = 3.
 template <> struct Gfw<7, 4> {
   static constexpr uint32_t W = 0, L = 16384, H = 32768, CT = 49152, BYTES = CT + 2048;
+  // dot product at q = 2^9 (three products per REDQ): word table, L and H with entries as four
+  // 8-bit coefficient fields
+  static constexpr uint32_t DW = BYTES, DL = DW + 16384, DH = DL + 16384, DOT_END = DH + 16384;
+  static constexpr uint32_t DWL = DOT_END, END = DWL + 16384;   // DW indexed by discrete logarithm
 };
 
 // bits 0, 4, ..., 28 of w -> bits 0..7: bits 8j and 8j + 4 paired at 8j, then a multiply by
@@ -476,9 +487,9 @@ __device__ __forceinline__ uint32_t gfw_mul_2_8(uint32_t a, uint32_t b, const ui
   return gfw_gather4((uint32_t)r) ^ H[gfw_gather4((uint32_t)(r >> 32))];
 }
 
-// One product in GF(3^5): L/H entries = sum mu_i 5^i, T maps a sum of two of them to the index.
-__device__ __forceinline__ uint32_t gfw_mul_3_5(uint32_t a, uint32_t b, const uint32_t* wl, const uint16_t* L,
-                                                const uint16_t* H, const uint8_t* T) {
+// The two table indices of one product in GF(3^5) (REDQ of the word product in SWAR form):
+// il from u_0..u_5 (the low part, u_5 q^5 folded in), ih from u_5..u_8 (the high part).
+__device__ __forceinline__ void gfw_idx_3_5(uint32_t a, uint32_t b, const uint32_t* wl, uint32_t& il, uint32_t& ih) {
   const uint64_t r = (uint64_t)wl[a * 32] * wl[b * 32];
   const uint32_t lo = (uint32_t)r;
   const uint32_t rh = __funnelshift_r(lo, (uint32_t)(r >> 32), 25);    // digits 5..8
@@ -487,15 +498,20 @@ __device__ __forceinline__ uint32_t gfw_mul_3_5(uint32_t a, uint32_t b, const ui
   const uint32_t sl = __umulhi(rl, 0x55555556u);
   // pairs (u0,u1) (u2,u3) (u4,u5) at bits 0, 10, 20 -> bits 28, 24, 20; (u5,u6) (u7,u8) at
   // bits 0, 10 -> bits 24, 28
-  const uint32_t il = (gfw_pairs_3(rl, sl) * 0x10004001u) >> 20;   // (u4+4u5) + 16 (u2+4u3) + 256 (u0+4u1)
-  const uint32_t ih = (gfw_pairs_3(rh, sh) * 0x01040000u) >> 24;   // sum_{t<=3} u_{5+t} 4^t
+  il = (gfw_pairs_3(rl, sl) * 0x10004001u) >> 20;   // (u4+4u5) + 16 (u2+4u3) + 256 (u0+4u1)
+  ih = (gfw_pairs_3(rh, sh) * 0x01040000u) >> 24;   // sum_{t<=3} u_{5+t} 4^t
+}
+
+// One product in GF(3^5): L/H entries = sum mu_i 5^i, T maps a sum of two of them to the index.
+__device__ __forceinline__ uint32_t gfw_mul_3_5(uint32_t a, uint32_t b, const uint32_t* wl, const uint16_t* L,
+                                                const uint16_t* H, const uint8_t* T) {
+  uint32_t il, ih;
+  gfw_idx_3_5(a, b, wl, il, ih);
   return T[L[il] + H[ih]];
 }
 
-// One product in GF(7^4): W word table, L/H entries = spread (4-bit fields) | index << 16,
-// ctl = replicated carry table + lane.
-__device__ __forceinline__ uint32_t gfw_mul_7_4(uint32_t a, uint32_t b, const uint32_t* W, const uint32_t* L,
-                                                const uint32_t* H, const uint32_t* ctl) {
+// The two table indices of one product in GF(7^4): il from u_0..u_3, ih from u_3..u_6.
+__device__ __forceinline__ void gfw_idx_7_4(uint32_t a, uint32_t b, const uint32_t* W, uint32_t& il, uint32_t& ih) {
   const uint64_t r = (uint64_t)W[a] * W[b];
   const uint32_t lo = (uint32_t)r;
   const uint32_t rh = __funnelshift_r(lo, (uint32_t)(r >> 32), 24);    // digits 3..6
@@ -503,8 +519,16 @@ __device__ __forceinline__ uint32_t gfw_mul_7_4(uint32_t a, uint32_t b, const ui
   const uint32_t rl = (lo & 0x00FFFFFFu) + ((rh - 7u * sh) << 24);       // u_3 q^3 + r mod q^3
   const uint32_t sl = __umulhi(rl, 0x24924925u);
   // pairs at bits 0 and 16 -> bits 20 and 26
-  const uint32_t il = (gfw_pairs_7(rl, sl) * 0x00100400u) >> 20;   // sum_{t<=3} u_t 8^t
-  const uint32_t ih = (gfw_pairs_7(rh, sh) * 0x00100400u) >> 20;   // sum_{t<=3} u_{3+t} 8^t
+  il = (gfw_pairs_7(rl, sl) * 0x00100400u) >> 20;   // sum_{t<=3} u_t 8^t
+  ih = (gfw_pairs_7(rh, sh) * 0x00100400u) >> 20;   // sum_{t<=3} u_{3+t} 8^t
+}
+
+// One product in GF(7^4): W word table, L/H entries = spread (4-bit fields) | index << 16,
+// ctl = replicated carry table + lane.
+__device__ __forceinline__ uint32_t gfw_mul_7_4(uint32_t a, uint32_t b, const uint32_t* W, const uint32_t* L,
+                                                const uint32_t* H, const uint32_t* ctl) {
+  uint32_t il, ih;
+  gfw_idx_7_4(a, b, W, il, ih);
   const uint32_t x = L[il] + H[ih];
   // bit 4i + 3 of x + 0x1111: coefficient sum i >= 7; the multiply moves those four bits to bits
   // 28..31 (cross products on distinct bits below 28, or above 31)
@@ -598,36 +622,45 @@ __global__ void __launch_bounds__(GFW_THREADS, 2) k_gf_mul_fixed(const typename 
   if (op.any_bad()) flag_error(err, ERR_RANGE);
 }
 
-// GF(2^8) dot product on the word-level multiply (Algorithm FGDP with n > 1, index form): since
-// p | q here, every product's REDQ compression values are its digits and the word-level product
-// gives the product's index directly; the field addition in GF(2^8) is XOR, so each thread XORs
-// its products, the block XOR-reduces, and the block's sum is written as a spread vector
-// (coefficient i at bit i fb) for the common final kernel.  No code can be out of range.
+// GF(2^8) dot product on the word-level multiply (Algorithm FGDP with n > 1; `words` is the word
+// table of the call's form, indexed by element index or by discrete logarithm): since
+// p | q = 2^4 here, REDQ compression of a word r gives u_i = floor(r / q^i) mod 2 = bit 0 of
+// digit i, and bit 0 of a sum of digits is the XOR of their bit 0s, so each thread XORs its
+// word products into one 64-bit r (every product is below 2^58; the bits above bit 0 of each
+// digit are then meaningless, and unused) and takes REDQ once; the field addition in GF(2^8)
+// is XOR too, so the block XOR-reduces and writes its sum as a spread vector (coefficient i at
+// bit i fb) for the common final kernel.  No code can be out of range.
 __global__ void __launch_bounds__(GFW_THREADS, 2) k_gf_dot_w28(const uint4* __restrict__ a, const uint4* __restrict__ b,
                                                               uint64_t nvec, const uint8_t* __restrict__ ta,
                                                               const uint8_t* __restrict__ tb, uint32_t ntail,
+                                                              const uint4* __restrict__ words,
                                                               const uint4* __restrict__ image, uint32_t fb,
                                                               uint32_t* __restrict__ partial) {
   extern __shared__ __align__(128) uint8_t sm[];
-  constexpr uint32_t IB = Gfw<2, 8>::BYTES;
-  for (uint32_t i = threadIdx.x; i < IB / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = image[i];
+  using G = Gfw<2, 8>;
+  for (uint32_t i = threadIdx.x; i < (G::H - G::W) / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = words[i];
+  for (uint32_t i = threadIdx.x; i < (G::BYTES - G::H) / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(sm + G::H)[i] = image[G::H / 16 + i];
   __syncthreads();
   const uint32_t* wl = reinterpret_cast<const uint32_t*>(sm + Gfw<2, 8>::W) + (threadIdx.x & 31u);
   const uint8_t* H = sm + Gfw<2, 8>::H;
+  // XOR of the word products of four index pairs
   auto word = [&](uint32_t x, uint32_t y) {
-    uint32_t acc = 0;
+    uint64_t t = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc ^= gfw_mul_2_8(__byte_perm(x, 0u, 0x4440u + j), __byte_perm(y, 0u, 0x4440u + j), wl, H);
-    return acc;
+    for (int j = 0; j < 4; ++j)
+      t ^= (uint64_t)wl[32u * __byte_perm(x, 0u, 0x4440u + j)] * wl[32u * __byte_perm(y, 0u, 0x4440u + j)];
+    return t;
   };
-  uint32_t acc = 0;
+  uint64_t r = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
     const uint4 x = __ldcs(a + i), y = __ldcs(b + i);
-    acc ^= word(x.x, y.x) ^ word(x.y, y.y) ^ word(x.z, y.z) ^ word(x.w, y.w);
+    r ^= word(x.x, y.x) ^ word(x.y, y.y) ^ word(x.z, y.z) ^ word(x.w, y.w);
   }
   if (blockIdx.x == 0)   // the last n mod 16 elements
-    for (uint32_t i = threadIdx.x; i < ntail; i += blockDim.x) acc ^= gfw_mul_2_8(ta[i], tb[i], wl, H);
+    for (uint32_t i = threadIdx.x; i < ntail; i += blockDim.x) r ^= (uint64_t)wl[32u * ta[i]] * wl[32u * tb[i]];
+  uint32_t acc = gfw_gather4((uint32_t)r) ^ H[gfw_gather4((uint32_t)(r >> 32))];
   for (int o = 16; o; o >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, o);
   __shared__ uint32_t ws[GFW_THREADS / 32];
   if ((threadIdx.x & 31u) == 0) ws[threadIdx.x >> 5] = acc;
@@ -641,9 +674,348 @@ __global__ void __launch_bounds__(GFW_THREADS, 2) k_gf_dot_w28(const uint4* __re
   }
 }
 
+// GF(3^5) and GF(7^4) dot products by Algorithm FGDP with n > 1 on 32-bit words (`words`: the
+// word table of the call's form, indexed by element index or by discrete logarithm).
+// The dot product has its own q: 2^7 for GF(3^5) (a word product's digits are at most
+// 5 (p-1)^2 = 20, six products' at most 120 < 2^7; r < 2^63) and 2^9 for GF(7^4) (digits at
+// most 3 * 144 = 432 < 2^9; r < 2^63); every word is below 2^30.  Each thread adds CH = 6 (3)
+// word products into a 64-bit r, then takes REDQ compression of r in SWAR form on 32-bit
+// pieces, as the multiply does: u_i = floor(r / q^i) mod p for every i, from the digits of a
+// piece x and of s = floor(x / p) (u_i = (x_i - p s_i) mod q; lanes of 2 b bits hold
+// x_i + p q - p s_i, which stays in [p, 4q)).  r splits three ways: the top piece r >> 5b
+// (GF(3^5)) or r >> 4b (GF(7^4)) gives the top u's; the one digit below it gives the next u
+// (floor(r / q^j) = d_j + q floor(r / q^(j+1))); the low piece u_j q^j + r mod q^j gives the
+// rest (the same floor(. / q^i) mod p below j).  The low and high parts' reduced coefficients
+// come from two tables as wide fields (five 6-bit fields for GF(3^5), four 8-bit fields for
+// GF(7^4)) and are added into one 32-bit vector of coefficient sums: the field additions are
+// deferred.  A fold keeps each field small and congruent mod p (16 = 1 mod 3: the top two bits
+// of a 6-bit field go onto its low four, leaving at most 18, and eight REDQs add at most 4
+// each; 8 = 1 mod 7: bits 3-7 of a byte go onto bits 0-2, leaving at most 38, and sixteen REDQs
+// add at most 12 each); each field is reduced mod p once, at the end, into the spread form of
+// the block sum and the common final kernel.  A code >= p^k reads a zero word, so it counts as
+// zero, and sets the range error.
+
+// (u_0 + 4 u_1) at bit 0 and (u_2 + 4 u_3) at bit 14 from the 7-bit digits of x (GF(3^5),
+// q = 2^7), s = floor(x / 3): even digits in lanes at 0 and 14, odd digits (x >> 7) likewise.
+__device__ __forceinline__ uint32_t gfd_pairs_3(uint32_t x, uint32_t s) {
+  constexpr uint32_t ME = 0x001FC07Fu, CE = 0x00600180u, MU = 0x0000C003u;   // CE: 3 q per lane
+  const uint32_t te = ((x & ME) | CE) - 3u * (s & ME);
+  const uint32_t to = (((x >> 7) & ME) | CE) - 3u * ((s >> 7) & ME);
+  return (te & MU) | ((to & MU) << 2);
+}
+
+// REDQ of r (GF(3^5), q = 2^7, r < 2^63) and the two lookups: u_5..u_8 from r >> 35, u_4 from
+// digit 4 and u_5, u_0..u_3 from u_4 q^4 + r mod q^4; L indexed by (u0 + 4 u1) + 16 (u2 + 4 u3)
+// + 256 (u4 + 4 u5), H by (u5 + 4 u6) + 16 (u7 + 4 u8).
+__device__ __forceinline__ uint32_t gfd_redq_3_5(uint64_t r, const uint32_t* L, const uint32_t* H) {
+  const uint32_t lo = (uint32_t)r, hi = (uint32_t)(r >> 32);
+  const uint32_t rhh = hi >> 3;                                          // digits 5..8, < 2^28
+  const uint32_t yh = gfd_pairs_3(rhh, __umulhi(rhh, 0x55555556u));
+  const uint32_t u5 = yh & 3u;
+  const uint32_t t4 = (__funnelshift_r(lo, hi, 28) & 0x7Fu) + (u5 << 7);   // d_4 + q u_5
+  const uint32_t u4 = t4 - 3u * __umulhi(t4, 0x55555556u);
+  const uint32_t rl = (lo & 0x0FFFFFFFu) + (u4 << 28);                  // < 3 2^28
+  const uint32_t yl = gfd_pairs_3(rl, __umulhi(rl, 0x55555556u));
+  const uint32_t il = ((yl + (yl >> 10)) & 0xFFu) + ((u4 + 4u * u5) << 8);
+  const uint32_t ih = (yh + (yh >> 10)) & 0xFFu;
+  return L[il] + H[ih];
+}
+
+// (u_0 + 8 u_1) at bit 0 and (u_2 + 8 u_3) at bit 18 from the 9-bit digits of x (GF(7^4),
+// q = 2^9), s = floor(x / 7): even digits in lanes at 0 and 18, odd digits (x >> 9) likewise.
+__device__ __forceinline__ uint32_t gfd_pairs_7(uint32_t x, uint32_t s) {
+  constexpr uint32_t ME = 0x07FC01FFu, CE = 0x38000E00u, MU = 0x001C0007u;   // CE: 7 q per lane
+  const uint32_t te = ((x & ME) | CE) - 7u * (s & ME);
+  const uint32_t to = (((x >> 9) & ME) | CE) - 7u * ((s >> 9) & ME);
+  return (te & MU) | ((to & MU) << 3);
+}
+
+// REDQ of r (GF(7^4), q = 2^9, r < 2^63) and the two lookups.  u_4..u_6 from r >> 36; u_3 from
+// digit 3 and u_4 (floor(r / q^3) = d_3 + q floor(r / q^4)); the low piece u_3 q^3 + r mod q^3
+// gives u_0..u_3.
+__device__ __forceinline__ uint32_t gfd_redq_7_4(uint64_t r, const uint32_t* L, const uint32_t* H) {
+  const uint32_t lo = (uint32_t)r, hi = (uint32_t)(r >> 32);
+  const uint32_t rhh = hi >> 4;                                          // digits 4..6, < 2^27
+  const uint32_t yh = gfd_pairs_7(rhh, __umulhi(rhh, 0x24924925u));     // (u4 + 8 u5), u6 at 18
+  const uint32_t t3 = (__funnelshift_r(lo, hi, 27) & 0x1FFu) + ((yh & 7u) << 9);
+  const uint32_t u3 = t3 - 7u * __umulhi(t3, 0x24924925u);
+  const uint32_t rl = (lo & 0x07FFFFFFu) + (u3 << 27);                  // < 7 2^27
+  const uint32_t yl = gfd_pairs_7(rl, __umulhi(rl, 0x24924925u));
+  const uint32_t il = (yl + (yl >> 12)) & 0xFFFu;                       // u0 + 8 u1 + 64 u2 + 512 u3
+  const uint32_t ih = u3 + (((yh + (yh >> 12)) & 0x1FFu) << 3);         // u3 + 8 u4 + 64 u5 + 512 u6
+  return L[il] + H[ih];
+}
+
+static constexpr int GFD_THREADS = 1024;
+template <uint32_t P, uint32_t K>
+__global__ void __launch_bounds__(GFD_THREADS, 1) k_gf_dot_wsum(const uint4* __restrict__ a, const uint4* __restrict__ b,
+                                                               uint64_t nvec, const void* __restrict__ ta,
+                                                               const void* __restrict__ tb, uint32_t ntail,
+                                                               const uint4* __restrict__ words,
+                                                               const uint4* __restrict__ image, uint32_t fb,
+                                                               uint32_t* __restrict__ partial, uint32_t* err) {
+  using G = Gfw<P, K>;
+  constexpr uint32_t WB = G::DL - G::DW, DB = G::DOT_END - G::DL;
+  constexpr uint32_t FW = P == 3 ? 6u : 8u;                    // bits per coefficient field
+  constexpr uint32_t EPV = P == 3 ? 16u : 8u;                  // elements per 16-byte vector
+  constexpr uint32_t CH = P == 3 ? 6u : 3u;                    // word products per REDQ
+  extern __shared__ __align__(128) uint8_t sm[];
+  for (uint32_t i = threadIdx.x; i < WB / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = words[i];
+  for (uint32_t i = threadIdx.x; i < DB / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm + WB)[i] = image[G::DL / 16 + i];
+  __syncthreads();
+  const uint32_t* W = reinterpret_cast<const uint32_t*>(sm);
+  const uint32_t* L = reinterpret_cast<const uint32_t*>(sm + (G::DL - G::DW));
+  const uint32_t* H = reinterpret_cast<const uint32_t*>(sm + (G::DH - G::DW));
+  const uint32_t* wl = W + (threadIdx.x & 31u);                // GF(3^5): replicated word table
+  auto fold = [](uint32_t x) {
+    if constexpr (P == 3) return ((x >> 4) & 0x030C30C3u) + (x & 0x0F3CF3CFu);
+    else return ((x >> 3) & 0x1F1F1F1Fu) + (x & 0x07070707u);
+  };
+  auto redq = [&](uint64_t r) {
+    if constexpr (P == 3) return gfd_redq_3_5(r, L, H);
+    else return gfd_redq_7_4(r, L, H);
+  };
+  // element e of a vector (as four words) and its word
+  auto elem = [](const uint32_t* w, uint32_t e) {
+    if constexpr (P == 3) return __byte_perm(w[e >> 2], 0u, 0x4440u + (e & 3u));
+    else return min((e & 1u) ? w[e >> 1] >> 16 : w[e >> 1] & 0xFFFFu, 2401u);   // >= 2401: a zero word
+  };
+  auto word = [&](uint32_t x) -> uint64_t {
+    if constexpr (P == 3) return wl[x * 32];
+    else return W[x];
+  };
+  // a byte >= 243 has its top bit set and its low 7 bits + 13 >= 128; a uint16 >= 2401 its
+  // bit 15 or (low 15 bits + 0x769F) bit 15
+  auto check = [](uint32_t x) {
+    if constexpr (P == 3) return x & ((x & 0x7F7F7F7Fu) + 0x0D0D0D0Du);
+    else return x | ((x & 0x7FFF7FFFu) + 0x769F769Fu);
+  };
+  uint32_t acc = 0, bad = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  // three vectors per trip: 3 EPV products, eight REDQs of CH products each, then one fold
+  for (; i + 2 * stride < nvec; i += 3 * stride) {
+    uint4 va[3], vb[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) { va[v] = __ldcs(a + i + v * stride); vb[v] = __ldcs(b + i + v * stride); }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) bad |= check(va[v].x) | check(va[v].y) | check(va[v].z) | check(va[v].w) |
+                                       check(vb[v].x) | check(vb[v].y) | check(vb[v].z) | check(vb[v].w);
+#pragma unroll
+    for (uint32_t g = 0; g < 3 * EPV / CH; ++g) {
+      uint64_t r = 0;
+#pragma unroll
+      for (uint32_t t = CH * g; t < CH * g + CH; ++t) {
+        const uint32_t* wa = reinterpret_cast<const uint32_t*>(&va[t / EPV]);
+        const uint32_t* wb = reinterpret_cast<const uint32_t*>(&vb[t / EPV]);
+        r += word(elem(wa, t % EPV)) * word(elem(wb, t % EPV));
+      }
+      acc += redq(r);
+    }
+    acc = fold(acc);
+  }
+  // the rest one product at a time, REDQ after every CH-th
+  uint64_t r = 0;
+  uint32_t cnt = 0;
+  auto push = [&](uint32_t x, uint32_t y) {
+    r += word(x) * word(y);
+    if (++cnt == CH) {
+      acc = fold(acc + redq(r));
+      r = 0;
+      cnt = 0;
+    }
+  };
+  for (; i < nvec; i += stride) {
+    const uint4 xa = __ldcs(a + i), xb = __ldcs(b + i);
+    bad |= check(xa.x) | check(xa.y) | check(xa.z) | check(xa.w) | check(xb.x) | check(xb.y) | check(xb.z) | check(xb.w);
+    const uint32_t* wa = reinterpret_cast<const uint32_t*>(&xa);
+    const uint32_t* wb = reinterpret_cast<const uint32_t*>(&xb);
+#pragma unroll
+    for (uint32_t e = 0; e < EPV; ++e) push(elem(wa, e), elem(wb, e));
+  }
+  if (blockIdx.x == 0)   // the last n mod EPV elements, one per thread
+    for (uint32_t j = threadIdx.x; j < ntail; j += blockDim.x) {
+      uint32_t x, y;
+      if constexpr (P == 3) {
+        x = static_cast<const uint8_t*>(ta)[j];
+        y = static_cast<const uint8_t*>(tb)[j];
+        bad |= (x >= 243u || y >= 243u) ? 0x80u : 0u;
+      } else {
+        x = static_cast<const uint16_t*>(ta)[j];
+        y = static_cast<const uint16_t*>(tb)[j];
+        bad |= (x >= 2401u || y >= 2401u) ? 0x8000u : 0u;
+        x = min(x, 2401u);
+        y = min(y, 2401u);
+      }
+      push(x, y);
+    }
+  if (cnt) acc = fold(acc + redq(r));
+  // each field mod p, into the spread form of the final kernel
+  uint32_t sp = 0, ones = 0;
+#pragma unroll
+  for (uint32_t f = 0; f < K; ++f) {
+    sp |= (((acc >> (FW * f)) & ((1u << FW) - 1u)) % P) << (f * fb);
+    ones |= 1u << (f * fb);
+  }
+  sp = gf_block_sum(sp, P, fb, ones);
+  if (threadIdx.x == 0) partial[blockIdx.x] = sp;
+  if (bad & (P == 3 ? 0x80808080u : 0x80008000u)) flag_error(err, ERR_RANGE);
+}
+
+// GF(2^8), GF(3^5), GF(7^4) matrix products on 32-bit words: C = A B with every entry a dot
+// product by Algorithm FGDP (Sec. 6), the words and REDQ of the dot products above.  A block
+// computes a 64 x 64 tile of C, each thread 4 x 4 entries; tiles of GFMW_KT inner steps of A
+// and B are staged in shared memory already as words (one table lookup per element), so an
+// inner step is two 16-byte shared loads and 16 multiply-adds of 32-bit words into 64-bit
+// accumulators.  GF(3^5) and GF(7^4): REDQ of all 16 accumulators after every CH steps, their
+// coefficient vectors added (deferred field additions, folds as in the dot product).  GF(2^8):
+// p divides q = 2^4, so u_i = floor(r / q^i) mod 2 is bit 0 of digit i, and bit 0 of a sum of
+// digits is the XOR of their bit 0s: the products are XOR-accumulated over the whole inner
+// dimension (the bits above bit 0 of each digit are then meaningless, and unused) and the one
+// REDQ at the end takes bits 0, 4, ..., 56.  Codes >= p^k read a zero word and set the range error.
+static constexpr int GFMW_TILE = 64, GFMW_KT = 32, GFMW_SP = GFMW_TILE + 4;   // row stride: 16-byte rows, fewer conflicts
+// the tables a word-level matrix product copies: word table bytes WB (from the form's word table),
+// then TB bytes of REDQ tables from image offset TOFF (H at HOFF within them)
+template <uint32_t P, uint32_t K> struct GfmwTabs;
+template <> struct GfmwTabs<2, 8> {
+  static constexpr uint32_t WB = Gfw<2, 8>::H - Gfw<2, 8>::W, TOFF = Gfw<2, 8>::H, TB = 128, HOFF = 0;
+};
+template <> struct GfmwTabs<3, 5> {
+  using G = Gfw<3, 5>;
+  static constexpr uint32_t WB = G::DL - G::DW, TOFF = G::DL, TB = G::DOT_END - G::DL, HOFF = G::DH - G::DL;
+};
+template <> struct GfmwTabs<7, 4> {
+  using G = Gfw<7, 4>;
+  static constexpr uint32_t WB = G::DL - G::DW, TOFF = G::DL, TB = G::DOT_END - G::DL, HOFF = G::DH - G::DL;
+};
+template <uint32_t P>
+using GfmwElem = typename std::conditional<P == 7, uint16_t, uint8_t>::type;
+template <uint32_t P, uint32_t K>
+__global__ void __launch_bounds__(256, 2) k_gf_matmul_w(const GfmwElem<P>* __restrict__ A, int lda,
+                                                        const GfmwElem<P>* __restrict__ B, int ldb,
+                                                        GfmwElem<P>* __restrict__ C, int ldc, int m, int n, int kdim,
+                                                        const uint4* __restrict__ words,
+                                                        const uint4* __restrict__ image, const uint16_t* __restrict__ to_log,
+                                                        uint32_t* err) {
+  using T = GfmwTabs<P, K>;
+  // shared memory: word table, the REDQ tables, then the A and B tiles
+  constexpr uint32_t WB = T::WB, TB = T::TB, TOFF = T::TOFF;
+  constexpr uint32_t CH = P == 3 ? 6u : 3u;
+  constexpr uint32_t FW = P == 3 ? 6u : 8u;
+  constexpr uint32_t ORDER = P == 2 ? 256u : P == 3 ? 243u : 2401u;
+  extern __shared__ __align__(128) uint8_t sm[];
+  for (uint32_t i = threadIdx.x; i < WB / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = words[i];
+  for (uint32_t i = threadIdx.x; i < TB / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm + WB)[i] = image[TOFF / 16 + i];
+  const uint32_t* W = reinterpret_cast<const uint32_t*>(sm);
+  const uint32_t* L = reinterpret_cast<const uint32_t*>(sm + WB);
+  const uint32_t* H = reinterpret_cast<const uint32_t*>(sm + WB + T::HOFF);
+  uint32_t* sA = reinterpret_cast<uint32_t*>(sm + WB + TB);   // [GFMW_KT][GFMW_SP]: column l of the A tile
+  uint32_t* sB = sA + GFMW_KT * GFMW_SP;                     // [GFMW_KT][GFMW_SP]: row l of the B tile
+  const uint32_t lane = threadIdx.x & 31u;
+  auto word = [&](uint32_t x) {
+    if constexpr (P == 7) return W[min(x, 2401u)];
+    else return W[32u * x + lane];                           // replicated table, x < 256
+  };
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int r0 = blockIdx.y * GFMW_TILE, c0 = blockIdx.x * GFMW_TILE;
+  uint64_t r[4][4];
+  uint32_t acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { r[i][j] = 0; acc[i][j] = 0; }
+  uint32_t bad = 0, cnt = 0, chunks = 0;
+  auto reduce_all = [&]() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if constexpr (P == 3) acc[i][j] += gfd_redq_3_5(r[i][j], L, H);
+        else acc[i][j] += gfd_redq_7_4(r[i][j], L, H);
+        r[i][j] = 0;
+      }
+    if (++chunks == 8) {   // at most 8 REDQs between folds (6-bit fields: 18 + 8 * 4 < 64)
+      chunks = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t x = acc[i][j];
+          if constexpr (P == 3) acc[i][j] = ((x >> 4) & 0x030C30C3u) + (x & 0x0F3CF3CFu);
+          else acc[i][j] = ((x >> 3) & 0x1F1F1F1Fu) + (x & 0x07070707u);
+        }
+    }
+  };
+  for (int l0 = 0; l0 < kdim; l0 += GFMW_KT) {
+    __syncthreads();   // the tables are in place; the previous tiles are no longer read
+    for (int e = tid; e < GFMW_KT * GFMW_TILE; e += 256) {
+      {  // A: consecutive threads take consecutive inner steps of a row
+        const int l = e % GFMW_KT, row = e / GFMW_KT;
+        uint32_t w = 0;
+        if (r0 + row < m && l0 + l < kdim) {
+          const uint32_t x = A[(size_t)(r0 + row) * lda + l0 + l];
+          bad |= x >= ORDER;
+          w = word(x);
+        }
+        sA[l * GFMW_SP + row] = w;
+      }
+      {  // B: consecutive threads take consecutive columns
+        const int col = e % GFMW_TILE, l = e / GFMW_TILE;
+        uint32_t w = 0;
+        if (c0 + col < n && l0 + l < kdim) {
+          const uint32_t x = B[(size_t)(l0 + l) * ldb + c0 + col];
+          bad |= x >= ORDER;
+          w = word(x);
+        }
+        sB[l * GFMW_SP + col] = w;
+      }
+    }
+    __syncthreads();
+    const int steps = min(GFMW_KT, kdim - l0);
+    for (int l = 0; l < steps; ++l) {
+      const uint4 av = *reinterpret_cast<const uint4*>(sA + l * GFMW_SP + 4 * ty);
+      const uint4 bv = *reinterpret_cast<const uint4*>(sB + l * GFMW_SP + 4 * tx);
+      const uint32_t a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if constexpr (P == 2) r[i][j] ^= (uint64_t)a[i] * b[j];
+          else r[i][j] += (uint64_t)a[i] * b[j];
+        }
+      if constexpr (P != 2) {
+        if (++cnt == CH) {
+          cnt = 0;
+          reduce_all();
+        }
+      }
+    }
+  }
+  if constexpr (P != 2)
+    if (cnt) reduce_all();
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t idx;
+      if constexpr (P == 2) {
+        const uint8_t* H8 = reinterpret_cast<const uint8_t*>(L);
+        idx = gfw_gather4((uint32_t)r[i][j]) ^ H8[gfw_gather4((uint32_t)(r[i][j] >> 32))];
+      } else {
+        idx = 0;
+#pragma unroll
+        for (int f = (int)K - 1; f >= 0; --f) idx = idx * P + ((acc[i][j] >> (FW * f)) & ((1u << FW) - 1u)) % P;
+      }
+      const int row = r0 + 4 * ty + i, col = c0 + 4 * tx + j;
+      if (row < m && col < n) C[(size_t)row * ldc + col] = (GfmwElem<P>)(to_log ? to_log[idx] : idx);
+    }
+  if (bad) flag_error(err, ERR_RANGE);
+}
+
 // Host: the shared-memory image of the word-level tables of the field, empty when the field has
 // no word-level kernel.  `word` holds the DQT words, `index`/`rem` the representation helpers.
-static std::vector<uint8_t> gfw_image(uint32_t p, uint32_t k, uint32_t b, const std::vector<uint32_t>& modulus) {
+static std::vector<uint8_t> gfw_image(uint32_t p, uint32_t k, uint32_t b, const std::vector<uint32_t>& modulus,
+                                      const std::vector<uint32_t>& antilog) {
   std::vector<uint8_t> img;
   auto digits = [&](uint64_t x) {
     std::vector<uint32_t> c(k);
@@ -662,6 +1034,8 @@ static std::vector<uint8_t> gfw_image(uint32_t p, uint32_t k, uint32_t b, const 
     return x;
   };
   auto put32 = [&](uint32_t off, uint32_t v) { std::memcpy(img.data() + off, &v, 4); };
+  // a log-form code's element: g^e for e < p^k - 1, zero for p^k - 1 (and for invalid codes)
+  auto from_log = [&](uint32_t e) { return e < antilog.size() ? antilog[e] : 0u; };
   auto put16 = [&](uint32_t off, uint16_t v) { std::memcpy(img.data() + off, &v, 2); };
   const uint32_t cq = (p - ((1u << b) % p)) % p;   // -q mod p
   uint32_t order = 1;
@@ -676,6 +1050,9 @@ static std::vector<uint8_t> gfw_image(uint32_t p, uint32_t k, uint32_t b, const 
       for (uint32_t t = 0; t < 7; ++t) ph[8 + t] = (g >> t) & 1u;
       img[G::H + g] = (uint8_t)index(poly_rem(ph, modulus, p));
     }
+    img.resize(G::END, 0);
+    for (uint32_t x = 0; x < 256; ++x)
+      for (uint32_t l = 0; l < 32; ++l) put32(G::WL + 4 * (32 * x + l), word(from_log(x)));
   } else if (p == 3 && k == 5 && b == 5) {
     using G = Gfw<3, 5>;
     img.assign(G::BYTES, 0);
@@ -713,6 +1090,51 @@ static std::vector<uint8_t> gfw_image(uint32_t p, uint32_t k, uint32_t b, const 
       for (uint32_t i = 0; i < k; ++i, w *= p, y /= 5) v += ((y % 5) % p) * w;
       img[G::T + x] = (uint8_t)v;
     }
+    // dot product at q = 2^7: words with 7-bit digits, L from u_0..u_5 (index
+    // (u0 + 4 u1) + 16 (u2 + 4 u3) + 256 (u4 + 4 u5)) and H from u_5..u_8 (index
+    // (u5 + 4 u6) + 16 (u7 + 4 u8)), entries as 6-bit coefficient fields
+    img.resize(G::DOT_END, 0);
+    const uint32_t bd = 7, cqd = (p - ((1u << bd) % p)) % p;
+    auto word_d = [&](uint64_t x) {
+      const std::vector<uint32_t> c = digits(x);
+      uint32_t w = 0;
+      for (int i = (int)k - 1; i >= 0; --i) w = (w << bd) | c[i];
+      return w;
+    };
+    auto wide = [&](const std::vector<uint32_t>& c) {
+      uint32_t w = 0;
+      for (uint32_t i = 0; i < k; ++i) w |= c[i] << (6 * i);
+      return w;
+    };
+    for (uint32_t x = 0; x < 256; ++x)
+      for (uint32_t l = 0; l < 32; ++l) put32(G::DW + 4 * (32 * x + l), x < order ? word_d(x) : 0u);
+    img.resize(G::END, 0);
+    for (uint32_t x = 0; x < 256; ++x)
+      for (uint32_t l = 0; l < 32; ++l) put32(G::DWL + 4 * (32 * x + l), word_d(from_log(x)));
+    for (uint32_t il = 0; il < 4096; ++il) {
+      uint32_t u[6];
+      bool ok = true;
+      for (uint32_t j = 0; j < 3; ++j) {
+        const uint32_t pair = (il >> (4 * j)) & 15u;
+        u[2 * j] = pair & 3u;
+        u[2 * j + 1] = pair >> 2;
+        ok &= u[2 * j] < p && u[2 * j + 1] < p;
+      }
+      if (!ok) continue;
+      std::vector<uint32_t> mu(k);
+      for (uint32_t i = 0; i < k; ++i) mu[i] = (u[i] + cqd * u[i + 1]) % p;
+      put32(G::DL + 4 * il, wide(mu));
+    }
+    for (uint32_t ih = 0; ih < 256; ++ih) {
+      uint32_t u[9] = {0};
+      bool ok = true;
+      for (uint32_t t = 0; t < 4; ++t) { u[5 + t] = (ih >> (2 * t)) & 3u; ok &= u[5 + t] < p; }
+      if (!ok) continue;
+      std::vector<uint32_t> ph(2 * k - 1, 0);
+      ph[8] = u[8];
+      for (uint32_t i = 5; i < 8; ++i) ph[i] = (u[i] + cqd * u[i + 1]) % p;
+      put32(G::DH + 4 * ih, wide(poly_rem(ph, modulus, p)));
+    }
   } else if (p == 7 && k == 4 && b == 8) {
     using G = Gfw<7, 4>;
     img.assign(G::BYTES, 0);
@@ -745,6 +1167,43 @@ static std::vector<uint8_t> gfw_image(uint32_t p, uint32_t k, uint32_t b, const 
       uint32_t v = 0, w = p;
       for (uint32_t i = 0; i < k; ++i, w *= p) v += ((g >> i) & 1u) * w;
       for (uint32_t l = 0; l < 32; ++l) put32(G::CT + 4 * (32 * g + l), v);
+    }
+    // dot product at q = 2^9: words with 9-bit digits, L from u_0..u_3 and H from u_3..u_6
+    // (indices sum_t u 8^t, as above), entries as 8-bit coefficient fields
+    img.resize(G::DOT_END, 0);
+    const uint32_t bd = 9, cqd = (p - ((1u << bd) % p)) % p;
+    auto word_d = [&](uint64_t x) {
+      const std::vector<uint32_t> c = digits(x);
+      uint32_t w = 0;
+      for (int i = (int)k - 1; i >= 0; --i) w = (w << bd) | c[i];
+      return w;
+    };
+    auto wide = [&](const std::vector<uint32_t>& c) {
+      uint32_t w = 0;
+      for (uint32_t i = 0; i < k; ++i) w |= c[i] << (8 * i);
+      return w;
+    };
+    for (uint32_t x = 0; x < 4096; ++x) put32(G::DW + 4 * x, x < order ? word_d(x) : 0u);
+    img.resize(G::END, 0);
+    for (uint32_t x = 0; x < 4096; ++x) put32(G::DWL + 4 * x, word_d(from_log(x)));
+    for (uint32_t il = 0; il < 4096; ++il) {
+      uint32_t u[4];
+      bool ok = true;
+      for (uint32_t t = 0; t < 4; ++t) { u[t] = (il >> (3 * t)) & 7u; ok &= u[t] < p; }
+      if (!ok) continue;
+      std::vector<uint32_t> mu(k, 0);
+      for (uint32_t i = 0; i < 3; ++i) mu[i] = (u[i] + cqd * u[i + 1]) % p;
+      put32(G::DL + 4 * il, wide(mu));
+    }
+    for (uint32_t ih = 0; ih < 4096; ++ih) {
+      uint32_t u[7] = {0};
+      bool ok = true;
+      for (uint32_t t = 0; t < 4; ++t) { u[3 + t] = (ih >> (3 * t)) & 7u; ok &= u[3 + t] < p; }
+      if (!ok) continue;
+      std::vector<uint32_t> ph(2 * k - 1, 0);
+      ph[6] = u[6];
+      for (uint32_t i = 3; i < 6; ++i) ph[i] = (u[i] + cqd * u[i + 1]) % p;
+      put32(G::DH + 4 * ih, wide(poly_rem(ph, modulus, p)));
     }
   }
   return img;
@@ -938,6 +1397,7 @@ extern "C" fp_status fp_gf_create(fp_ctx ctx, uint32_t p, uint32_t k, fp_gf* out
   }
   std::vector<uint64_t> word_d(order), word_dl(order, 0);
   std::vector<uint16_t> tolog(order, 0);
+  std::vector<uint32_t> antilog(order - 1);
   for (uint64_t x = 0; x < order; ++x) {
     const std::vector<uint32_t> cf = coeffs_of(x);
     uint64_t w = 0;
@@ -949,6 +1409,7 @@ extern "C" fp_status fp_gf_create(fp_ctx ctx, uint32_t p, uint32_t k, fp_gf* out
     for (uint64_t e = 0; e + 1 < order; ++e) {
       word_dl[e] = word_d[x];
       tolog[x] = (uint16_t)e;
+      antilog[e] = (uint32_t)x;
       x = fmul(x, g->gen);
     }
     word_dl[order - 1] = 0;
@@ -970,7 +1431,7 @@ extern "C" fp_status fp_gf_create(fp_ctx ctx, uint32_t p, uint32_t k, fp_gf* out
   if (e == cudaSuccess) e = cudaMemcpy(g->d_Ld, Ld.data(), tsz * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_Hd, Hd.data(), tsz * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_tolog, tolog.data(), order * sizeof(uint16_t), cudaMemcpyHostToDevice);
-  const std::vector<uint8_t> img = gfw_image(p, k, b, g->modulus);
+  const std::vector<uint8_t> img = gfw_image(p, k, b, g->modulus, antilog);
   if (e == cudaSuccess && !img.empty()) {
     g->img_bytes = (uint32_t)img.size();
     e = cudaMalloc(&g->d_img, img.size());
@@ -1021,29 +1482,49 @@ template <typename E>
 static fp_status gf_dot_launch(fp_ctx ctx, fp_gf g, const E* a, const E* b, size_t n, E* out, int form,
                                cudaStream_t st) {
   using namespace fpd;
-  if (sizeof(E) == 1 && g->p == 2 && g->k == 8 && g->d_img && form == FP_GF_INDEX && n >= 16 &&
-      ((((uintptr_t)a) | ((uintptr_t)b)) & 15u) == 0) {
-    // GF(2^8), index form, aligned: the word-level multiply with XOR accumulation
-    const size_t smem = Gfw<2, 8>::BYTES;
-    FP_CUDA(cudaFuncSetAttribute(k_gf_dot_w28, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  constexpr uint64_t EPV = 16 / sizeof(E);   // elements per 16-byte vector
+  const bool w28 = g->p == 2 && g->k == 8, w35 = g->p == 3 && g->k == 5, w74 = g->p == 7 && g->k == 4;
+  if ((w28 || w35 || w74) && g->d_img && n >= EPV && ((((uintptr_t)a) | ((uintptr_t)b)) & 15u) == 0) {
+    // GF(2^8), GF(3^5), GF(7^4), aligned: word-level products, with XOR accumulation (GF(2^8))
+    // or three products per REDQ and deferred field additions; the log form reads a word table
+    // indexed by discrete logarithm and converts the sum at the end
+    const bool lg = form == FP_GF_LOG;
+    const uint32_t woff = w28 ? (lg ? Gfw<2, 8>::WL : Gfw<2, 8>::W)
+                        : w35 ? (lg ? Gfw<3, 5>::DWL : Gfw<3, 5>::DW) : (lg ? Gfw<7, 4>::DWL : Gfw<7, 4>::DW);
+    const uint4* words = g->d_img + woff / 16;
+    const void* kern = w28 ? (const void*)k_gf_dot_w28 : w35 ? (const void*)k_gf_dot_wsum<3, 5> : (const void*)k_gf_dot_wsum<7, 4>;
+    const size_t smem = w28 ? Gfw<2, 8>::BYTES
+                      : w35 ? Gfw<3, 5>::DOT_END - Gfw<3, 5>::DW : Gfw<7, 4>::DOT_END - Gfw<7, 4>::DW;
+    const int threads = w28 ? GFW_THREADS : GFD_THREADS;
+    FP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gf_dot_w28, GFW_THREADS, smem));
-    const uint64_t nvec = n / 16;
-    const uint64_t want = (nvec + GFW_THREADS - 1) / GFW_THREADS;
+    FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    const uint64_t nvec = n / EPV;
+    const uint64_t want = (nvec + threads - 1) / threads;
     const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx->num_sms * std::max(per_sm, 1)));
     fp_status s = ensure_scratch(ctx, (size_t)grid * sizeof(uint32_t), 1, st);
     if (s != FP_OK) return s;
     uint32_t* partial = (uint32_t*)ctx->scratch2;
-    const uint8_t* a8 = (const uint8_t*)a;
-    const uint8_t* b8 = (const uint8_t*)b;
-    FP_LAUNCH(ctx, "k_gf_dot_w28", st,
-              (k_gf_dot_w28<<<grid, GFW_THREADS, smem, st>>>((const uint4*)a, (const uint4*)b, nvec, a8 + nvec * 16,
-                                                              b8 + nvec * 16, (uint32_t)(n - nvec * 16), g->d_img, g->fb,
-                                                              partial)));
+    const E* ta = a + nvec * EPV;
+    const E* tb = b + nvec * EPV;
+    const uint32_t ntail = (uint32_t)(n - nvec * EPV);
+    if (w28)
+      FP_LAUNCH(ctx, "k_gf_dot_w28", st,
+                (k_gf_dot_w28<<<grid, GFW_THREADS, smem, st>>>((const uint4*)a, (const uint4*)b, nvec, (const uint8_t*)ta,
+                                                                (const uint8_t*)tb, ntail, words, g->d_img, g->fb, partial)));
+    else if (w35)
+      FP_LAUNCH(ctx, "k_gf_dot_wsum", st,
+                (k_gf_dot_wsum<3, 5><<<grid, GFD_THREADS, smem, st>>>((const uint4*)a, (const uint4*)b, nvec, ta, tb, ntail,
+                                                                       words, g->d_img, g->fb, partial, ctx->d_err)));
+    else
+      FP_LAUNCH(ctx, "k_gf_dot_wsum", st,
+                (k_gf_dot_wsum<7, 4><<<grid, GFD_THREADS, smem, st>>>((const uint4*)a, (const uint4*)b, nvec, ta, tb, ntail,
+                                                                       words, g->d_img, g->fb, partial, ctx->d_err)));
     uint32_t ones = 0;
     for (uint32_t i = 0; i < g->k; ++i) ones |= 1u << (i * g->fb);
     FP_LAUNCH(ctx, "k_gf_dot_final", st,
-              (k_gf_dot_final<E><<<1, 256, 0, st>>>(partial, grid, out, g->p, g->k, g->fb, ones, nullptr)));
+              (k_gf_dot_final<E><<<1, 256, 0, st>>>(partial, grid, out, g->p, g->k, g->fb, ones,
+                                                    lg ? g->d_tolog : nullptr)));
     FP_CUDA(cudaGetLastError());
     return FP_OK;
   }
@@ -1087,6 +1568,32 @@ template <typename E>
 static fp_status gf_matmul_launch(fp_ctx ctx, fp_gf g, int m, int n, int kdim, const E* A, int lda, const E* B,
                                   int ldb, E* C, int ldc, int form, cudaStream_t st) {
   using namespace fpd;
+  const bool w28 = g->p == 2 && g->k == 8, w35 = g->p == 3 && g->k == 5, w74 = g->p == 7 && g->k == 4;
+  if ((w28 || w35 || w74) && g->d_img) {
+    // word-level fields: 32-bit words, SWAR REDQ (GF(3^5), GF(7^4)) or XOR accumulation (GF(2^8))
+    const bool lg = form == FP_GF_LOG;
+    const uint32_t woff = w28 ? (lg ? Gfw<2, 8>::WL : Gfw<2, 8>::W)
+                        : w35 ? (lg ? Gfw<3, 5>::DWL : Gfw<3, 5>::DW) : (lg ? Gfw<7, 4>::DWL : Gfw<7, 4>::DW);
+    const uint4* words = g->d_img + woff / 16;
+    const uint16_t* tl = lg ? g->d_tolog : nullptr;
+    const size_t tiles = 2 * (size_t)GFMW_KT * GFMW_SP * sizeof(uint32_t);
+    dim3 grid((n + GFMW_TILE - 1) / GFMW_TILE, (m + GFMW_TILE - 1) / GFMW_TILE);
+#define FP_GF_MMW(PP, KK)                                                                                         \
+    {                                                                                                           \
+      const size_t smem = GfmwTabs<PP, KK>::WB + GfmwTabs<PP, KK>::TB + tiles;                                  \
+      FP_CUDA(cudaFuncSetAttribute(k_gf_matmul_w<PP, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+      FP_LAUNCH(ctx, "k_gf_matmul_w", st,                                                                       \
+                (k_gf_matmul_w<PP, KK><<<grid, 256, smem, st>>>((const GfmwElem<PP>*)A, lda, (const GfmwElem<PP>*)B, \
+                                                                ldb, (GfmwElem<PP>*)C, ldc, m, n, kdim, words,      \
+                                                                g->d_img, tl, ctx->d_err)));                        \
+    }
+    if (w28) FP_GF_MMW(2, 8)
+    else if (w35) FP_GF_MMW(3, 5)
+    else FP_GF_MMW(7, 4)
+#undef FP_GF_MMW
+    FP_CUDA(cudaGetLastError());
+    return FP_OK;
+  }
   const uint32_t tsz = 1u << (g->c * g->k);
   const size_t tab = ((g->order * sizeof(uint64_t) + 2 * tsz * sizeof(uint32_t)) + 127) & ~(size_t)127;
   const size_t smem = tab + 2 * (size_t)GFM_KT * GFM_TILE * sizeof(uint64_t);
@@ -1136,10 +1643,10 @@ extern "C" fp_status fp_gf_mul_batched(fp_ctx ctx, fp_gf g, const void* a, const
   const uint64_t vbytes = g->elem_bytes == 2 ? 16 : 8;   // eight indices per vector
   if (g->d_img && aligned && count * g->elem_bytes >= vbytes) {
     const uint64_t nvec = count * g->elem_bytes / vbytes;
-    const size_t smem_f = g->img_bytes;
     bool launched = false;
 #define FP_GF_FIXED(PP, KK)                                                                                           \
     if (!launched && g->p == PP && g->k == KK) {                                                                      \
+      const size_t smem_f = Gfw<PP, KK>::BYTES;                                                                       \
       FP_CUDA(cudaFuncSetAttribute(k_gf_mul_fixed<PP, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));  \
       int per_sm = 0;                                                                                                  \
       FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gf_mul_fixed<PP, KK>, GFW_THREADS, smem_f));    \

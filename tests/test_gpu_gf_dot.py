@@ -246,3 +246,55 @@ def test_gf_dot_whole_field_and_bad_code(env):
             fp.fp_gf_dot(ctx, gf, A, A, 1000, out, 2)        # no such form: host check
     finally:
         fp.fp_gf_destroy(gf)
+
+
+@pytest.mark.parametrize("form", ["INDEX", "LOG"])
+@pytest.mark.parametrize("p,k,bad", [(3, 5, (243, 250, 255)), (7, 4, (2401, 4096 + 5, 32768 + 1, 65535))])
+def test_gf_dot_bad_codes_count_as_zero(env, p, k, bad, form):
+    """Codes >= p^k inside 16-byte vectors and in the ragged tail of the word-level dot product
+    (GF(7^4) codes among them whose low 12 bits are a valid code), in index and in log form,
+    count as zero and set the range error; arrays one element past a 16-byte line (the generic
+    kernel) give the same."""
+    fp, torch, dev, ctx = env
+    gf = fp.fp_gf_create(ctx, p, k)
+    try:
+        m = field.smallest_monic_irreducible(p, k)
+        _, log = field.log_tables(p, k, m)
+        dt = workloads.gf_index_dtype(p, k)
+        q = p ** k
+        rng = np.random.default_rng(q + 5)
+        n = 4096 * 16 + 5
+        a, b = rng.integers(0, q, n), rng.integers(0, q, n)
+        if form == "LOG":
+            a, b = log[a], log[b]
+        pos = (3, 777, 40000, n - 2)
+        for i, j in enumerate(pos):
+            a[j] = bad[i % len(bad)]
+            b[j + 1] = bad[(i + 1) % len(bad)]
+        keep_a = np.ones(n, bool)
+        keep_b = np.ones(n, bool)
+        keep_a[list(pos)] = False
+        keep_b[[j + 1 for j in pos]] = False
+        if form == "LOG":
+            antilog = np.zeros(q, np.int64)
+            antilog[log[np.arange(q)]] = np.arange(q)
+            ia, ib = np.where(keep_a, antilog[np.where(keep_a, a, 0)], 0), np.where(keep_b, antilog[np.where(keep_b, b, 0)], 0)
+        else:
+            ia, ib = np.where(keep_a, a, 0), np.where(keep_b, b, 0)
+        want = field.gf_dot(ia, ib, p, k, m)
+        if form == "LOG":
+            want = int(log[want])
+        for offset in (0, 1):
+            A = _dev_elems(torch, dev, np.concatenate([np.zeros(offset, dt), a.astype(dt)]), dt)[offset:]
+            B = _dev_elems(torch, dev, np.concatenate([np.zeros(offset, dt), b.astype(dt)]), dt)[offset:]
+            out = torch.full((1,), 7, dtype=torch.uint8 if dt == np.uint8 else torch.int16, device=dev)
+            fp.fp_gf_dot(ctx, gf, A, B, n, out, getattr(fp, "FP_GF_" + form))
+            torch.cuda.synchronize()
+            v = out.cpu().numpy()
+            got = int((v.view(np.uint16) if dt == np.uint16 else v)[0])
+            with pytest.raises(fp.FpError) as ei:
+                fp.fp_ctx_status(ctx)
+            assert ei.value.status == fp.FP_EINVAL
+            assert got == want, offset
+    finally:
+        fp.fp_gf_destroy(gf)

@@ -118,3 +118,68 @@ def test_gf_matmul_bad_code_and_arguments(env):
             fp.fp_gf_matmul(ctx, gf, 4, 4, 10, A, 10, A, 4, C, 4, 2)  # no such form
     finally:
         fp.fp_gf_destroy(gf)
+
+
+@pytest.mark.parametrize("p,k", [(3, 5), (7, 4), (2, 8)])
+def test_gf_matmul_long_inner_all_max(env, p, k):
+    """Inner dimension 2000 with every element p^k - 1 (every REDQ at its digit bound, many folds
+    of the deferred coefficient sums) and a random 2000-term product, in both forms."""
+    fp, torch, dev, ctx = env
+    gf = fp.fp_gf_create(ctx, p, k)
+    try:
+        mod = field.smallest_monic_irreducible(p, k)
+        q = p ** k
+        dt = workloads.gf_index_dtype(p, k)
+        antilog, log = field.log_tables(p, k, mod)
+        a = np.full((5, 2000), q - 1)
+        want = field.gf_matmul(a, a.T, p, k, mod)
+        np.testing.assert_array_equal(gf_mm(fp, torch, dev, ctx, gf, a, a.T.copy(), dt, fp.FP_GF_INDEX), want)
+        np.testing.assert_array_equal(gf_mm(fp, torch, dev, ctx, gf, log[a], log[a.T].copy(), dt, fp.FP_GF_LOG),
+                                      log[want])
+        rng = np.random.default_rng(q + 77)
+        a, b = rng.integers(0, q, (6, 2000)), rng.integers(0, q, (2000, 70))
+        want = field.gf_matmul(a, b, p, k, mod)
+        np.testing.assert_array_equal(gf_mm(fp, torch, dev, ctx, gf, a, b, dt, fp.FP_GF_INDEX), want)
+        np.testing.assert_array_equal(gf_mm(fp, torch, dev, ctx, gf, log[a], log[b], dt, fp.FP_GF_LOG), log[want])
+    finally:
+        fp.fp_gf_destroy(gf)
+
+
+@pytest.mark.parametrize("form", ["INDEX", "LOG"])
+@pytest.mark.parametrize("p,k,bad", [(3, 5, (243, 255)), (7, 4, (2401, 4096 + 3, 65535))])
+def test_gf_matmul_bad_codes_count_as_zero(env, p, k, bad, form):
+    """Codes >= p^k in A and B (GF(7^4) codes among them whose low 12 bits are a valid code)
+    count as zero and set the range error, in both forms."""
+    fp, torch, dev, ctx = env
+    gf = fp.fp_gf_create(ctx, p, k)
+    try:
+        mod = field.smallest_monic_irreducible(p, k)
+        q = p ** k
+        dt = workloads.gf_index_dtype(p, k)
+        antilog, log = field.log_tables(p, k, mod)
+        rng = np.random.default_rng(q + 91)
+        m, n, kk = 70, 66, 45
+        a, b = rng.integers(0, q, (m, kk)), rng.integers(0, q, (kk, n))
+        ca, cb = (log[a], log[b]) if form == "LOG" else (a.copy(), b.copy())
+        za, zb = a.copy(), b.copy()
+        for i, (r, c) in enumerate(((0, 0), (69, 44), (33, 7))):
+            ca[r, c] = bad[i % len(bad)]
+            za[r, c] = 0
+        for i, (r, c) in enumerate(((44, 65), (3, 64))):
+            cb[r, c] = bad[(i + 1) % len(bad)]
+            zb[r, c] = 0
+        want = field.gf_matmul(za, zb, p, k, mod)
+        if form == "LOG":
+            want = log[want]
+        C = _dev(torch, dev, np.zeros((m, n)), dt)
+        fp.fp_gf_matmul(ctx, gf, m, n, kk, _dev(torch, dev, ca, dt), kk, _dev(torch, dev, cb, dt), n, C, n,
+                        getattr(fp, "FP_GF_" + form))
+        torch.cuda.synchronize()
+        got = C.cpu().numpy()
+        got = (got.view(np.uint16) if dt == np.uint16 else got).astype(np.int64)
+        with pytest.raises(fp.FpError) as ei:
+            fp.fp_ctx_status(ctx)
+        assert ei.value.status == fp.FP_EINVAL
+        np.testing.assert_array_equal(got, want)
+    finally:
+        fp.fp_gf_destroy(gf)
