@@ -298,3 +298,31 @@ def test_gf_dot_bad_codes_count_as_zero(env, p, k, bad, form):
             assert got == want, offset
     finally:
         fp.fp_gf_destroy(gf)
+
+
+@pytest.mark.parametrize("p,k", [(3, 5), (7, 4)])
+def test_gf_dot_long_enough_for_three_vector_trips(env, p, k):
+    """n large enough that every thread of the one-wave grid (one 1024-thread block per SM) takes
+    the three-vectors-per-trip loop at least once, then per-vector trips and the ragged tail:
+    random codes in both forms and all-(p^k - 1) codes (every REDQ at its digit bound, every
+    fold), against the oracle."""
+    fp, torch, dev, ctx = env
+    gf = fp.fp_gf_create(ctx, p, k)
+    try:
+        m = field.smallest_monic_irreducible(p, k)
+        _, log = field.log_tables(p, k, m)
+        dt = workloads.gf_index_dtype(p, k)
+        q = p ** k
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        epv = 16 // np.dtype(dt).itemsize
+        n = (5 * sms * 1024 + 1000) * epv + 5
+        rng = np.random.default_rng(q + 29)
+        a, b = rng.integers(0, q, n), rng.integers(0, q, n)
+        want = field.gf_dot(a, b, p, k, m)
+        assert _gf_dot_run(fp, torch, dev, ctx, gf, a, b, fp.FP_GF_INDEX, dt) == want
+        assert _gf_dot_run(fp, torch, dev, ctx, gf, log[a], log[b], fp.FP_GF_LOG, dt) == log[want]
+        full = np.full(n, q - 1)
+        assert _gf_dot_run(fp, torch, dev, ctx, gf, full, full, fp.FP_GF_INDEX, dt) == \
+            field.gf_dot(full, full, p, k, m)
+    finally:
+        fp.fp_gf_destroy(gf)
