@@ -1235,7 +1235,7 @@ def packed_arm(args, fp, torch, ctx, prob, flush, stream, ktab, peak_src, plain_
                      "note": "achieved = word flops 2 m ceil(n/2) k of its problems / the kernel's device time per step"}
     dom = max(roofs, key=lambda nm: pk["kernels"][nm]["ms_per_step"]) if roofs else None
     return {"value": pk["value"], "unit": "F_p MAC/s", "ms_per_step": pk["ms_per_step"],
-            "algo": "RIGHT_TC (grouped): fp16 pair words, Q = 2^10 (p = 3) / 2^9 (p = 7)",
+            "algo": "RIGHT_TC (grouped): fp16 pair words, Q = 2^10 (p = 3) / 681 (p = 7)",
             "timing": pk["timing"], "roofline": roofs.get(dom), "roofline_per_kernel": roofs, "kernels": pk["kernels"],
             "packed_over_plain": pk["value"] / plain_value,
             "packed_over_plain_note": "same inputs; plain = the headline step (e4m3 tensor cores, AUTO)",

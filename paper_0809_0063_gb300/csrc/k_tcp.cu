@@ -25,9 +25,9 @@
 // list of output tiles (128 rows x 256 MMA columns) of up to FP_GROUP_MAX problems, longest
 // inner dimension first, with stride gridDim.x.  Roles: warp 0 TMA producer (A 128 x 64 and
 // B 64 x 256 per stage, 4-stage ring), warp 1 TMEM allocation (2 x 256 columns) and the
-// MMA-issuing thread, warps 2..9 (two per TMEM lane quarter, 128 columns each) the
-// accumulator drains, REDQ / mod p and the stores, the drains of one tile overlapping the MMAs
-// of the next.  Every wait is bounded (ERR_TIMEOUT on
+// MMA-issuing thread, warps 2..9 (two per TMEM lane quarter, 128 columns each; for p = 5, 7
+// warps 2..17, four per lane quarter, 64 columns each) the accumulator drains, REDQ / mod p and
+// the stores, the drains of one tile overlapping the MMAs of the next.  Every wait is bounded (ERR_TIMEOUT on
 // give-up, with the drain-and-free exit of the other tensor-core kernels).
 #include <algorithm>
 #include <cstring>
@@ -43,12 +43,16 @@ static constexpr int P_A_BYTES = P_BM * P_BK * 2;             // 16 KB
 static constexpr int P_B_BOX = 64 * P_BK * 2;                 // 8 KB: 64 words x 64 rows
 static constexpr int P_B_BYTES = 4 * P_B_BOX;                 // 32 KB
 static constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;   // 48 KB
-static constexpr int P_EPI_WARPS = 8;                         // 2 per TMEM lane quarter
-static constexpr int P_CW = 4 * P_BNW / P_EPI_WARPS;            // MMA columns per epilogue thread
-static constexpr int P_THREADS = 32 * (2 + P_EPI_WARPS);
+// Epilogue warps: 8 (2 per TMEM lane quarter) for the plain and p <= 3 forms, 16 (4 per lane
+// quarter) for p = 5, 7, whose per-chunk drains bound it: twice the warps to hide the TMEM-load
+// and arithmetic latency, half the columns (and delayed-reduction words) per thread.
+__host__ __device__ constexpr int p_epi_warps(int pk) { return pk == 2 ? 16 : 8; }
+__host__ __device__ constexpr int p_cw(int pk) { return 4 * P_BNW / p_epi_warps(pk); }   // MMA columns per epilogue thread
+__host__ __device__ constexpr int p_threads(int pk) { return 32 * (2 + p_epi_warps(pk)); }
 // per epilogue warp: 32 rows x 32 output bytes (row stride 36 bytes: conflict-free word writes)
-static constexpr int P_EPI_STAGE_BYTES = P_EPI_WARPS * 32 * 36;
-static constexpr size_t P_SMEM = 1024 + P_STAGES * P_STAGE_BYTES + 256 + P_EPI_STAGE_BYTES;
+__host__ __device__ constexpr size_t p_smem(int pk) {
+  return 1024 + (size_t)P_STAGES * P_STAGE_BYTES + 256 + (size_t)p_epi_warps(pk) * 32 * 36;
+}
 
 // kind::f16, A (K-major) and B (MN-major) both fp16 (ab_type 0) or both bf16 (1), fp32 accumulate.
 __host__ __device__ constexpr uint32_t idesc_16_bmn(uint32_t ab_type, int M, int N) {
@@ -233,8 +237,9 @@ __device__ __forceinline__ void final_redq_arith(uint32_t (&R)[NW], uint32_t fix
 }
 
 template <int PK, int CAP = FP_GROUP_MAX>
-__global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__ PParamsT<CAP> g, uint32_t* err) {
+__global__ void __launch_bounds__(p_threads(PK), 1) k_mm_t16(const __grid_constant__ PParamsT<CAP> g, uint32_t* err) {
   constexpr bool PACKED = PK != 0;   // 1: p <= 3 at Q = 2^10; 2: p = 5, 7 at Q = 1023 / 681
+  constexpr int P_EPI_WARPS = p_epi_warps(PK), P_CW = p_cw(PK);
   extern __shared__ __align__(1024) uint8_t p_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)p_smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + P_STAGES * P_STAGE_BYTES);
@@ -461,6 +466,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
       const uint32_t p = pr.P.p, dmax = pr.dmax, rr = (uint32_t)pr.rr;
       const float qinv = pr.qinv;
       const uint32_t qdec = 65536u - (uint32_t)rintf(1.0f / qinv);
+      const uint32_t cmag = 0x4B400000u * (1u + qdec);   // added to every R word per chunk
       uint32_t cr = 0;     // chunks added since R last held residues
       for (int c = 0; c < pr.nchunks; ++c, ++gc) {
         const int buf = (int)(gc & 1u);
@@ -472,9 +478,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
           break;
         }
         tc_fence_after();
-        // 1.5 2^23 added: the float's bits are 0x4B400000 + v exactly; the same after scaling
-        // by 1/Q gives 0x4B400000 + round(v / Q) = 0x4B400000 + d1 (|d0| / Q <= 0.43, far
-        // from the rounding boundary), and y + (2^16 - Q) d1 = d0 + 2^16 d1 + 0x4B400000
+        // 1.5 2^23 added: the float's bits are y = 0x4B400000 + v exactly; the same after
+        // scaling by 1/Q gives t = 0x4B400000 + round(v / Q) = 0x4B400000 + d1 (|d0| / Q <= 0.43,
+        // far from the rounding boundary), and y + (2^16 - Q) t = d0 + 2^16 d1 + cmag with the
+        // per-chunk constant cmag = 0x4B400000 (1 + 2^16 - Q) (mod 2^32), removed by `fix`
         const uint32_t base = tmem + lane_base + (uint32_t)(buf * 256 + part * P_CW);
         uint32_t va[16], vb[16];
         tmem_ld16_nowait(base, va);
@@ -489,8 +496,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
           for (int j = 0; j < 16; ++j) {
             const float v = __uint_as_float((blk & 1) ? vb[j] : va[j]);
             const uint32_t y = (uint32_t)__float_as_int(v + 12582912.0f);
-            const uint32_t d1 = (uint32_t)(__float_as_int(fmaf(v, qinv, 12582912.0f)) - 0x4B400000);
-            R[blk * 16 + j] += y + d1 * qdec;
+            const uint32_t t1 = (uint32_t)__float_as_int(fmaf(v, qinv, 12582912.0f));
+            R[blk * 16 + j] += y + t1 * qdec;
           }
           tmem_wait();
         }
@@ -499,14 +506,14 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_mm_t16(const __grid_constant__
         if (lane == 0) mbar_arrive(&tempty[buf]);
         if (++cr == rr && c + 1 < pr.nchunks) {
           const uint32_t off = dmax * cr;
-          const uint32_t fix = off * 65537u - cr * 0x4B400000u;
+          const uint32_t fix = off * 65537u - cr * cmag;
           rereduce_pairs<P_CW>(R, fix, off % p, p, pr.P.c, pr.P.dv);
           cr = 0;
         }
       }
       if (!ok) break;
       const uint32_t off = dmax * cr;
-      const uint32_t fix = off * 65537u - cr * 0x4B400000u;
+      const uint32_t fix = off * 65537u - cr * cmag;
       const int row = x.m0 + q * 32 + lane;
       const int c0 = 2 * (x.w0 + part * P_CW);
       const int n = pr.n;
@@ -806,14 +813,14 @@ static fp_status launch_t16_mode(fp_ctx ctx, const std::vector<const fp_mm_probl
     hp.total = tile;
     const int grid = std::min(tile, ctx->num_sms);
     if (pk == 2) {
-      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
-      FP_LAUNCH(ctx, "k_mm_t16_packed_p57", st, k_mm_t16<2><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err));
+      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_smem(2)));
+      FP_LAUNCH(ctx, "k_mm_t16_packed_p57", st, k_mm_t16<2><<<grid, p_threads(2), p_smem(2), st>>>(hp, ctx->d_err));
     } else if (packed) {
-      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
-      FP_LAUNCH(ctx, "k_mm_t16_packed", st, k_mm_t16<1><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err));
+      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_smem(1)));
+      FP_LAUNCH(ctx, "k_mm_t16_packed", st, k_mm_t16<1><<<grid, p_threads(1), p_smem(1), st>>>(hp, ctx->d_err));
     } else {
-      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
-      FP_LAUNCH(ctx, "k_mm_t16_plain", st, k_mm_t16<0><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err));
+      FP_CUDA(cudaFuncSetAttribute(k_mm_t16<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_smem(0)));
+      FP_LAUNCH(ctx, "k_mm_t16_plain", st, k_mm_t16<0><<<grid, p_threads(0), p_smem(0), st>>>(hp, ctx->d_err));
     }
     FP_CUDA(cudaGetLastError());
   }
@@ -919,7 +926,7 @@ fp_status launch_mm_t16_plain_batch(fp_ctx ctx, const fp_mm_problem* const* pr, 
   FP_LAUNCH(ctx, "k_t16_convert_jobs", st,
             k_t16_convert_jobs<<<cgrid, 256, jsm, st>>>((const T16Job*)scratch, (uint32_t)jobs.size(), rows, ctx->d_err));
   FP_CUDA(cudaGetLastError());
-  FP_CUDA(cudaFuncSetAttribute(k_mm_t16<0, P_BATCH_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM));
+  FP_CUDA(cudaFuncSetAttribute(k_mm_t16<0, P_BATCH_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_smem(0)));
   for (size_t base = 0; base < v.size(); base += P_BATCH_CAP) {
     const int cnt = (int)std::min<size_t>(P_BATCH_CAP, v.size() - base);
     PParamsT<P_BATCH_CAP> hp;
@@ -951,7 +958,7 @@ fp_status launch_mm_t16_plain_batch(fp_ctx ctx, const fp_mm_problem* const* pr, 
     hp.nprob = cnt;
     hp.total = tile;
     const int grid = std::min(tile, ctx->num_sms);
-    FP_LAUNCH(ctx, "k_mm_t16_plain", st, (k_mm_t16<0, P_BATCH_CAP><<<grid, P_THREADS, P_SMEM, st>>>(hp, ctx->d_err)));
+    FP_LAUNCH(ctx, "k_mm_t16_plain", st, (k_mm_t16<0, P_BATCH_CAP><<<grid, p_threads(0), p_smem(0), st>>>(hp, ctx->d_err)));
     FP_CUDA(cudaGetLastError());
   }
   return FP_OK;
