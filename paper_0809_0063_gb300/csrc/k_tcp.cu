@@ -45,7 +45,8 @@ static constexpr int P_B_BYTES = 4 * P_B_BOX;                 // 32 KB
 static constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;   // 48 KB
 // Epilogue warps: 8 (2 per TMEM lane quarter) for the plain and p <= 3 forms, 16 (4 per lane
 // quarter) for p = 5, 7, whose per-chunk drains bound it: twice the warps to hide the TMEM-load
-// and arithmetic latency, half the columns (and delayed-reduction words) per thread.
+// and arithmetic latency, half the columns (and delayed-reduction words) per thread.  (16 for
+// p <= 3 measured slower: 0.456 against 0.50 of bf16, at the 96 registers 18 warps allow.)
 __host__ __device__ constexpr int p_epi_warps(int pk) { return pk == 2 ? 16 : 8; }
 __host__ __device__ constexpr int p_cw(int pk) { return 4 * P_BNW / p_epi_warps(pk); }   // MMA columns per epilogue thread
 __host__ __device__ constexpr int p_threads(int pk) { return 32 * (2 + p_epi_warps(pk)); }
@@ -145,9 +146,10 @@ __device__ __forceinline__ uint32_t redq2_pair_table(uint32_t p, uint32_t om) {
 // version with run-time parameters was 1.8x slower: parameters reloaded after every store and
 // branches on the correction mode in the inner loop).
 static constexpr int P_REDQ_BW = 128;
-template <uint32_t PP, int NW, int BW = P_REDQ_BW>
+template <uint32_t PP, int NW, int BW = (NW < P_REDQ_BW ? NW : P_REDQ_BW)>
 __device__ __forceinline__ void final_redq(uint32_t (&R)[NW], uint32_t fix, uint32_t table, uint8_t* dst, int c0,
                                            int n, bool in, bool vec) {
+  static_assert(BW >= 16 && BW % 16 == 0 && NW % BW == 0, "passes of whole 16-word groups covering R");
 #pragma unroll 1
   for (int blk = 0; blk < NW / BW; ++blk) {
 #pragma unroll
