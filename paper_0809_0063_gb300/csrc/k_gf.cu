@@ -459,6 +459,19 @@ __device__ __forceinline__ uint32_t gfw_gather4(uint32_t w) {
   return (x * 0x01041040u) >> 24;
 }
 
+// Dot-product word tables indexed by a byte live in shared memory at a stride of 256 bytes per
+// entry (entry x of lane l at byte 256 x + 4 l; half of each row unused), so that one byte
+// permutation forms a lookup's whole offset: byte j of w above lane l's 4 l.  gfw_wide_table
+// spreads the device image's 32-way replicated table (entry x of lane l at word 32 x + l) into
+// that layout, 64 KB.
+__device__ __forceinline__ void gfw_wide_table(uint32_t* dst, const uint4* __restrict__ src) {
+  const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+  for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) dst[64 * (i >> 5) + (i & 31)] = s32[i];
+}
+__device__ __forceinline__ uint32_t gfw_wide_lookup(const uint8_t* tab, uint32_t w, uint32_t j, uint32_t lane4) {
+  return *reinterpret_cast<const uint32_t*>(tab + __byte_perm(w, lane4, 0x5504u | (j << 4)));
+}
+
 // u_i for the six 5-bit digits of x < 2^30, s = floor(x / 3) (GF(3^5) pieces): lanes of 10 bits
 // holding digits 0, 2, 4 (even) and 1, 3, 5 (odd); 96 = p q per lane keeps each lane in [3, 127].
 // Returned as pairs u_{2j} + 4 u_{2j+1} (each u < 3) at bit 10 j: a lane holds u + 32 j' with the
@@ -638,18 +651,17 @@ __global__ void __launch_bounds__(GFW_THREADS, 2) k_gf_dot_w28(const uint4* __re
                                                               uint32_t* __restrict__ partial) {
   extern __shared__ __align__(128) uint8_t sm[];
   using G = Gfw<2, 8>;
-  for (uint32_t i = threadIdx.x; i < (G::H - G::W) / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = words[i];
+  gfw_wide_table(reinterpret_cast<uint32_t*>(sm), words);   // 64 KB, then the 128-byte H table
   for (uint32_t i = threadIdx.x; i < (G::BYTES - G::H) / 16; i += blockDim.x)
-    reinterpret_cast<uint4*>(sm + G::H)[i] = image[G::H / 16 + i];
+    reinterpret_cast<uint4*>(sm + 65536)[i] = image[G::H / 16 + i];
   __syncthreads();
-  const uint32_t* wl = reinterpret_cast<const uint32_t*>(sm + Gfw<2, 8>::W) + (threadIdx.x & 31u);
-  const uint8_t* H = sm + Gfw<2, 8>::H;
+  const uint32_t lane4 = 4u * (threadIdx.x & 31u);
+  const uint8_t* H = sm + 65536;
   // XOR of the word products of four index pairs
   auto word = [&](uint32_t x, uint32_t y) {
     uint64_t t = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      t ^= (uint64_t)wl[32u * __byte_perm(x, 0u, 0x4440u + j)] * wl[32u * __byte_perm(y, 0u, 0x4440u + j)];
+    for (uint32_t j = 0; j < 4; ++j) t ^= (uint64_t)gfw_wide_lookup(sm, x, j, lane4) * gfw_wide_lookup(sm, y, j, lane4);
     return t;
   };
   uint64_t r = 0;
@@ -659,7 +671,8 @@ __global__ void __launch_bounds__(GFW_THREADS, 2) k_gf_dot_w28(const uint4* __re
     r ^= word(x.x, y.x) ^ word(x.y, y.y) ^ word(x.z, y.z) ^ word(x.w, y.w);
   }
   if (blockIdx.x == 0)   // the last n mod 16 elements
-    for (uint32_t i = threadIdx.x; i < ntail; i += blockDim.x) r ^= (uint64_t)wl[32u * ta[i]] * wl[32u * tb[i]];
+    for (uint32_t i = threadIdx.x; i < ntail; i += blockDim.x)
+      r ^= (uint64_t)gfw_wide_lookup(sm, ta[i], 0, lane4) * gfw_wide_lookup(sm, tb[i], 0, lane4);
   uint32_t acc = gfw_gather4((uint32_t)r) ^ H[gfw_gather4((uint32_t)(r >> 32))];
   for (int o = 16; o; o >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, o);
   __shared__ uint32_t ws[GFW_THREADS / 32];
@@ -755,18 +768,21 @@ __global__ void __launch_bounds__(GFD_THREADS, 1) k_gf_dot_wsum(const uint4* __r
                                                                const uint4* __restrict__ image, uint32_t fb,
                                                                uint32_t* __restrict__ partial, uint32_t* err) {
   using G = Gfw<P, K>;
-  constexpr uint32_t WB = G::DL - G::DW, DB = G::DOT_END - G::DL;
+  // shared memory: the word table (GF(3^5): spread to 256-byte entries, 64 KB), then L and H
+  constexpr uint32_t WB = P == 3 ? 65536u : G::DL - G::DW, DB = G::DOT_END - G::DL;
   constexpr uint32_t FW = P == 3 ? 6u : 8u;                    // bits per coefficient field
   constexpr uint32_t EPV = P == 3 ? 16u : 8u;                  // elements per 16-byte vector
   constexpr uint32_t CH = P == 3 ? 6u : 3u;                    // word products per REDQ
   extern __shared__ __align__(128) uint8_t sm[];
-  for (uint32_t i = threadIdx.x; i < WB / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = words[i];
+  if constexpr (P == 3) gfw_wide_table(reinterpret_cast<uint32_t*>(sm), words);
+  else
+    for (uint32_t i = threadIdx.x; i < WB / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = words[i];
   for (uint32_t i = threadIdx.x; i < DB / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm + WB)[i] = image[G::DL / 16 + i];
   __syncthreads();
   const uint32_t* W = reinterpret_cast<const uint32_t*>(sm);
-  const uint32_t* L = reinterpret_cast<const uint32_t*>(sm + (G::DL - G::DW));
-  const uint32_t* H = reinterpret_cast<const uint32_t*>(sm + (G::DH - G::DW));
-  const uint32_t* wl = W + (threadIdx.x & 31u);                // GF(3^5): replicated word table
+  const uint32_t* L = reinterpret_cast<const uint32_t*>(sm + WB);
+  const uint32_t* H = reinterpret_cast<const uint32_t*>(sm + WB + (G::DH - G::DL));
+  const uint32_t lane4 = 4u * (threadIdx.x & 31u);
   auto fold = [](uint32_t x) {
     if constexpr (P == 3) return ((x >> 4) & 0x030C30C3u) + (x & 0x0F3CF3CFu);
     else return ((x >> 3) & 0x1F1F1F1Fu) + (x & 0x07070707u);
@@ -775,13 +791,13 @@ __global__ void __launch_bounds__(GFD_THREADS, 1) k_gf_dot_wsum(const uint4* __r
     if constexpr (P == 3) return gfd_redq_3_5(r, L, H);
     else return gfd_redq_7_4(r, L, H);
   };
-  // element e of a vector (as four words) and its word
-  auto elem = [](const uint32_t* w, uint32_t e) {
-    if constexpr (P == 3) return __byte_perm(w[e >> 2], 0u, 0x4440u + (e & 3u));
-    else return min((e & 1u) ? w[e >> 1] >> 16 : w[e >> 1] & 0xFFFFu, 2401u);   // >= 2401: a zero word
+  // the word of element e of a vector (as four words); of a code x
+  auto eword = [&](const uint32_t* w, uint32_t e) -> uint64_t {
+    if constexpr (P == 3) return gfw_wide_lookup(sm, w[e >> 2], e & 3u, lane4);
+    else return W[min((e & 1u) ? w[e >> 1] >> 16 : w[e >> 1] & 0xFFFFu, 2401u)];   // >= 2401: a zero word
   };
   auto word = [&](uint32_t x) -> uint64_t {
-    if constexpr (P == 3) return wl[x * 32];
+    if constexpr (P == 3) return gfw_wide_lookup(sm, x, 0, lane4);
     else return W[x];
   };
   // a byte >= 243 has its top bit set and its low 7 bits + 13 >= 128; a uint16 >= 2401 its
@@ -808,7 +824,7 @@ __global__ void __launch_bounds__(GFD_THREADS, 1) k_gf_dot_wsum(const uint4* __r
       for (uint32_t t = CH * g; t < CH * g + CH; ++t) {
         const uint32_t* wa = reinterpret_cast<const uint32_t*>(&va[t / EPV]);
         const uint32_t* wb = reinterpret_cast<const uint32_t*>(&vb[t / EPV]);
-        r += word(elem(wa, t % EPV)) * word(elem(wb, t % EPV));
+        r += eword(wa, t % EPV) * eword(wb, t % EPV);
       }
       acc += redq(r);
     }
@@ -817,8 +833,8 @@ __global__ void __launch_bounds__(GFD_THREADS, 1) k_gf_dot_wsum(const uint4* __r
   // the rest one product at a time, REDQ after every CH-th
   uint64_t r = 0;
   uint32_t cnt = 0;
-  auto push = [&](uint32_t x, uint32_t y) {
-    r += word(x) * word(y);
+  auto push_w = [&](uint64_t wx, uint64_t wy) {
+    r += wx * wy;
     if (++cnt == CH) {
       acc = fold(acc + redq(r));
       r = 0;
@@ -831,7 +847,7 @@ __global__ void __launch_bounds__(GFD_THREADS, 1) k_gf_dot_wsum(const uint4* __r
     const uint32_t* wa = reinterpret_cast<const uint32_t*>(&xa);
     const uint32_t* wb = reinterpret_cast<const uint32_t*>(&xb);
 #pragma unroll
-    for (uint32_t e = 0; e < EPV; ++e) push(elem(wa, e), elem(wb, e));
+    for (uint32_t e = 0; e < EPV; ++e) push_w(eword(wa, e), eword(wb, e));
   }
   if (blockIdx.x == 0)   // the last n mod EPV elements, one per thread
     for (uint32_t j = threadIdx.x; j < ntail; j += blockDim.x) {
@@ -847,7 +863,7 @@ __global__ void __launch_bounds__(GFD_THREADS, 1) k_gf_dot_wsum(const uint4* __r
         x = min(x, 2401u);
         y = min(y, 2401u);
       }
-      push(x, y);
+      push_w(word(x), word(y));
     }
   if (cnt) acc = fold(acc + redq(r));
   // each field mod p, into the spread form of the final kernel
@@ -1493,8 +1509,8 @@ static fp_status gf_dot_launch(fp_ctx ctx, fp_gf g, const E* a, const E* b, size
                         : w35 ? (lg ? Gfw<3, 5>::DWL : Gfw<3, 5>::DW) : (lg ? Gfw<7, 4>::DWL : Gfw<7, 4>::DW);
     const uint4* words = g->d_img + woff / 16;
     const void* kern = w28 ? (const void*)k_gf_dot_w28 : w35 ? (const void*)k_gf_dot_wsum<3, 5> : (const void*)k_gf_dot_wsum<7, 4>;
-    const size_t smem = w28 ? Gfw<2, 8>::BYTES
-                      : w35 ? Gfw<3, 5>::DOT_END - Gfw<3, 5>::DW : Gfw<7, 4>::DOT_END - Gfw<7, 4>::DW;
+    const size_t smem = w28 ? 65536 + (Gfw<2, 8>::BYTES - Gfw<2, 8>::H)
+                      : w35 ? 65536 + (Gfw<3, 5>::DOT_END - Gfw<3, 5>::DL) : Gfw<7, 4>::DOT_END - Gfw<7, 4>::DW;
     const int threads = w28 ? GFW_THREADS : GFD_THREADS;
     FP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
