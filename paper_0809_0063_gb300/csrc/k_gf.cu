@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(GFW_THREADS, 2) k_gf_dot_w28(const uint4* __re
 // word products into a 64-bit r, then takes REDQ compression of r in SWAR form on 32-bit
 // pieces, as the multiply does: u_i = floor(r / q^i) mod p for every i, from the digits of a
 // piece x and of s = floor(x / p) (u_i = (x_i - p s_i) mod q; lanes of 2 b bits hold
-// x_i + p q - p s_i, which stays in [p, 4q)).  r splits three ways: the top piece r >> 5b
+// x_i + p q - p s_i, which stays in [p, (p + 1) q)).  r splits three ways: the top piece r >> 5b
 // (GF(3^5)) or r >> 4b (GF(7^4)) gives the top u's; the one digit below it gives the next u
 // (floor(r / q^j) = d_j + q floor(r / q^(j+1))); the low piece u_j q^j + r mod q^j gives the
 // rest (the same floor(. / q^i) mod p below j).  The low and high parts' reduced coefficients
